@@ -1,0 +1,316 @@
+"""Benchmark: DeepPot-SE velocity-Verlet NVE on one GB300, in s/step/atom and ns/day.
+
+Default workload: FCC copper, 10x10x10 cells = 4,000 atoms, seeded
+N(0, 0.1^2) displacements, r_c 8 A, r_cs 2 A, sel 512, embedding
+(25, 50, 100), M2 16, fitting (240, 240, 240), seeded N(0, 1/fan_in)
+weights, Maxwell-Boltzmann velocities at 300 K, dt 1 fs, FP64, 2 A skin
+list rebuilt on the device when needed.  One step = half kick, drift,
+list check/rebuild, list formatting, energy/force/virial, half kick.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64]
+                  [--impl mine|reference] [--workload cu4000|cu108k|water192]
+
+Prints one JSON line.  value = s/step/atom over the whole job (lower is
+better), timed with CUDA events on the library's stream, inputs resident
+on the device.  e2e = the same metric through dp_compute with host
+buffers (coordinates in from pinned memory, forces/energy/virial out) and
+the velocity-Verlet update on the host.  --impl reference times the FP64
+CPU oracle on the host cores on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import dpsynth  # noqa: E402
+
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 FLOP x 2070 MHz
+
+
+def workload(name: str):
+    if name == "cu4000":
+        cfg = dpsynth.copper_config()
+        coord, typ, box = dpsynth.copper_fcc(1, ncell=10)
+        mass = np.array([dpsynth.MASS["Cu"]])
+        return cfg, coord, typ, box, mass, 1.0, "Cu FCC 10^3 cells, 4000 atoms, rcut 8, sel 512, 300 K, dt 1 fs"
+    if name == "cu108k":
+        cfg = dpsynth.copper_config()
+        coord, typ, box = dpsynth.copper_fcc(1, ncell=30)
+        mass = np.array([dpsynth.MASS["Cu"]])
+        return cfg, coord, typ, box, mass, 1.0, "Cu FCC 30^3 cells, 108000 atoms, rcut 8, sel 512, 300 K, dt 1 fs"
+    if name == "water192":
+        cfg = dpsynth.water_config()
+        coord, typ, box = dpsynth.water_box(1)
+        mass = np.array([dpsynth.MASS["O"], dpsynth.MASS["H"]])
+        return cfg, coord, typ, box, mass, 0.5, "64 H2O, 192 atoms, rcut 6, sel 46/92, 300 K, dt 0.5 fs"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def flops_per_group(cfg, nnei_total: int, n: int):
+    """Algorithmic FLOP per evaluation (real neighbors only; padded rows are zero work)."""
+    e0, e1, e2 = cfg.embed
+    m1, m2 = e2, cfg.m2
+    f = list(cfg.fit)
+    fwd_n = 2 * (e0 + e0 * e1 + e1 * e2 + 4 * e2)
+    bwd_n = 2 * (4 * e2 + 4 * e2 + e2 * e1 + e1 * e0 + e0)
+    fit_a = 2 * 2 * (m1 * m2 * f[0] + sum(f[k] * f[k + 1] for k in range(len(f) - 1)) + f[-1])
+    return {
+        "embed_fwd": nnei_total * fwd_n + n * 2 * 4 * m1 * m2,
+        "embed_bwd": nnei_total * bwd_n + n * 2 * 8 * m1 * m2,
+        "fitting": n * fit_a,
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    def __init__(self):
+        self.p = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100", "-i", os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip() == "Active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_mine(args, rank, world):
+    import torch
+
+    import paper_2005_00223_gb300 as dp
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    cfg, coord, typ, box, mass, dt, desc = workload(args.workload)
+    n = len(typ)
+    vel = dpsynth.velocities(mass[typ], 300.0, 1)
+    model = dp.Model(cfg, seed=1)
+    stream = torch.cuda.Stream(device=dev)
+    dp.dp_model_set_stream(model.h, stream)
+    nl0 = dp.NeighborList(model, coord, typ, box)
+    nlist0, _ = nl0.get()
+    nnei_total = int((nlist0 >= 0).sum())
+    nl0.close()
+    state = dp.MDState(model, coord, vel, typ, mass, box, skin=2.0)
+    state.step(args.warmup, dt, args.precision)
+    sampler = ClockSampler()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    dp.dp_profile_enable(model.h, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    th = state.step(args.steps, dt, args.precision, thermo_every=args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop()
+    prof = dp.dp_profile_read(model.h)
+    dp.dp_profile_enable(model.h, False)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    launches = int(sum(v[0] for v in prof.values()))
+    # roofline of the dominant kernel group
+    flops = flops_per_group(cfg, nnei_total, n)
+    top = max((g for g in prof if prof[g][0] > 0), key=lambda g: prof[g][1])
+    per_launch_ms = prof[top][1] / prof[top][0]
+    groups = {g: {"launches": v[0], "ms_total": round(v[1], 4), "share": round(v[1] / ms, 4)}
+              for g, v in prof.items() if v[0] > 0}
+    roofline = None
+    if args.precision == "fp64" and top in flops:
+        # one launch processes one batch; with one batch per step a launch covers the whole system
+        batches = max(1, prof[top][0] // args.steps)
+        achieved = flops[top] / batches / (per_launch_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": top, "achieved": round(achieved, 4), "peak": round(FP64_PEAK_TFLOPS, 4),
+                    "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x 2070 MHz (nominal 1.25 TFLOP/s)"}
+    step_s = ms * 1e-3 / args.steps
+    value = step_s / (n * world)
+    total_flop = sum(flops.values())
+    # end-to-end: host buffers through dp_compute + host velocity Verlet
+    e2e = None
+    if rank == 0 and args.e2e_steps > 0:
+        e2e = run_e2e(dp, model, cfg, coord, vel, typ, box, mass, dt, args, stream)
+    state.close()
+    out = {
+        "metric": "s/step/atom", "value": value, "unit": "s/step/atom", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "ns_per_day": 86400.0 * dt * 1e-6 / step_s,
+        "dtype": "f64" if args.precision == "fp64" else args.precision,
+        "precision": args.precision, "data": "synthetic (seeded FCC copper / water, seeded random-init weights)",
+        "config": {"workload": desc, "atoms": n, "precision": args.precision, "real_neighbors": nnei_total,
+                   "l2": "working set per step > L2 (stored activations, %.2f GB)" % (
+                       nnei_total * (sum(cfg.embed) + cfg.embed[-1]) * 8 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "gflop_per_step": total_flop / 1e9, "tflops": total_flop / step_s / 1e12,
+        "roofline": roofline, "kernel_groups": groups, "gpu_launches": launches,
+        "thermo_last": [float(x) for x in th[-1]] if len(th) else None,
+        "clocks": clocks, "e2e": e2e,
+    }
+    return out
+
+
+def run_e2e(dp, model, cfg, coord, vel, typ, box, mass, dt, args, stream):
+    """dp_compute with host buffers every step; velocity Verlet on the host."""
+    import torch
+    n = len(typ)
+    x = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    x[:] = coord
+    v = vel.copy()
+    minv = (9.648533212e-3 / mass[typ])[:, None]
+    L = np.diag(box)
+    nl = dp.NeighborList(model, x, typ, box, skin=2.0)
+    ref = x.copy()
+    E, Ei, F, W = nl.compute(x, box, args.precision)
+    steps = args.e2e_steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        v += 0.5 * dt * F * minv
+        x += dt * v
+        x -= L * np.floor(x / L)
+        d = x - ref
+        d -= L * np.rint(d / L)
+        if (d * d).sum(1).max() > 1.0:          # half the 2 A skin, squared
+            nl.update(x, box)
+            ref = x.copy()
+        E, Ei, F, W = nl.compute(x, box, args.precision)
+        v += 0.5 * dt * F * minv
+    t1 = time.perf_counter()
+    nl.close()
+    step_s = (t1 - t0) / steps
+    return {"value": step_s / n, "unit": "s/step/atom", "steps": steps, "ns_per_day": 86400.0 * dt * 1e-6 / step_s,
+            "h2d_bytes_per_step": n * 3 * 8, "d2h_bytes_per_step": n * 3 * 8 + n * 8 + 10 * 8,
+            "path": "dp_compute(host coord) -> host E, E_i, F, W; host velocity Verlet"}
+
+
+def cpu_baseline(args, budget_s=15.0):
+    """The FP64 oracle on the host cores: whole NVE steps of the same workload."""
+    import oracle
+    cfg, coord, typ, box, mass, dt, desc = workload(args.workload)
+    n = len(typ)
+    import paper_2005_00223_gb300 as dp  # noqa: F401  (weights of the same seeded model)
+    params = dpsynth.model_params(cfg, 1)
+    om = oracle.Model(cfg, params)
+    vel = dpsynth.velocities(mass[typ], 300.0, 1)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    om.md_nve(coord, vel, typ, mass, box, nsteps=1, dt=dt, thermo_every=0, nthreads=cores)
+    one = time.perf_counter() - t0
+    steps = max(1, min(20, int(budget_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    om.md_nve(coord, vel, typ, mass, box, nsteps=steps, dt=dt, thermo_every=0, nthreads=cores)
+    el = time.perf_counter() - t0
+    return {"value": el / steps / n, "unit": "s/step/atom", "cores": cores, "kind": "oracle",
+            "sample": f"{steps} full NVE steps of the {desc} workload (FP64 oracle, OpenMP over atoms)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+    cfg, coord, typ, box, mass, dt, desc = workload(args.workload)
+    n = len(typ)
+    om = oracle.Model(cfg, dpsynth.model_params(cfg, 1))
+    vel = dpsynth.velocities(mass[typ], 300.0, 1)
+    cores = os.cpu_count() or 1
+    x, v = coord, vel
+    for _ in range(min(args.warmup, 1)):
+        x, v, _ = om.md_nve(x, v, typ, mass, box, nsteps=1, dt=dt, thermo_every=0, nthreads=cores)
+    # each timed step is one full oracle NVE step, bounded to the workload's own size
+    t0 = time.perf_counter()
+    x, v, th = om.md_nve(x, v, typ, mass, box, nsteps=args.steps, dt=dt, thermo_every=args.steps, nthreads=cores)
+    el = time.perf_counter() - t0
+    value = el / args.steps / n
+    base = {"value": value, "unit": "s/step/atom", "cores": cores, "kind": "oracle",
+            "sample": f"{args.steps} full NVE steps of the {desc} workload"}
+    return {"impl": "reference", "metric": "s/step/atom", "value": value, "unit": "s/step/atom", "n_gpus": world,
+            "steps": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "atoms": n, "precision": "fp64"}, "cpu_baseline": base,
+            "e2e": {"value": value, "unit": "s/step/atom", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mix32", "bf16", "fp16"])
+    ap.add_argument("--workload", default="cu4000")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "mine":
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl" if args.impl == "mine" else "gloo")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_mine(args, rank, world)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

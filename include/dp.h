@@ -1,0 +1,225 @@
+/*
+ * libdp — DeepPot-SE (se_a) energy, force and virial evaluation and
+ * velocity-Verlet NVE on one NVIDIA GB300 (sm_103a).
+ *
+ * Paper: Jia et al., "Pushing the limit of molecular dynamics with ab initio
+ * accuracy to 100 million atoms with machine learning", SC20.
+ *
+ * The method (Sec. 2, Fig. 1): the total energy is E = sum_i E_i; E_i is the
+ * output of a per-type fitting net applied to a descriptor D_i built from the
+ * environment matrix R_i of atom i's neighbors within r_c and from a
+ * per-neighbor embedding net; forces are F = -dE/dr and the virial
+ * W = -sum_ij d_ij (x) dE_i/dd_ij.  Sec. 4.1.1-4.1.2 fix the neighbor list
+ * layout (sorted by type, then distance; padded per type to sel; nearest
+ * kept on overflow); Sec. 4.1.3 the MIX-32 / MIX-16 precision schemes;
+ * Sec. 5.1 the velocity-Verlet MD loop with a skin neighbor list.
+ *
+ * Conventions for every call
+ *   - Units: A, eV, amu, fs; FP64 row-major arrays; type ids 0..ntypes-1.
+ *   - The caller owns every array it passes.  The library owns the opaque
+ *     handles and their device memory, which is allocated at create time or
+ *     when a call needs more room than before (never in steady state).
+ *   - Every call returns a dp_status and never aborts.  On error the output
+ *     arrays are left untouched (the *_dev calls excepted: device outputs may
+ *     be partly written) and dp_last_error() describes the failure.
+ *   - Boxes: orthorhombic only in this version (off-diagonal entries must be
+ *     zero) and r_c < L/2 along every axis, else DP_ERR_BOX.
+ *   - Calls on one model (or on handles made from it) must not overlap: the
+ *     model's device workspace is shared by them.
+ *   - Host-pointer calls run on the library's own stream and return after
+ *     their results are in host memory.  *_dev calls take device pointers
+ *     and a cudaStream_t (passed as void*; NULL = the legacy default stream)
+ *     and return after enqueueing; their outputs are valid once that stream
+ *     reaches the work.
+ */
+#ifndef DP_H
+#define DP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DP_OK = 0,
+    DP_ERR_ARG = -1,         /* invalid argument (NULL pointer, bad size, ...) */
+    DP_ERR_CUDA = -2,        /* a CUDA runtime call or kernel launch failed */
+    DP_ERR_OOM = -3,         /* device or host allocation failed */
+    DP_ERR_BOX = -4,         /* non-orthorhombic box, or r_c >= L/2 */
+    DP_ERR_CAPACITY = -5,    /* a candidate list exceeded its capacity; build again with more room */
+    DP_ERR_TIMEOUT = -6,     /* a bounded device wait expired */
+    DP_ERR_NONFINITE = -7,   /* a NaN or Inf appeared in energies or forces */
+    DP_ERR_UNSUPPORTED = -8  /* model shape or precision not supported by this build */
+} dp_status;
+
+/* Precision schemes (Sec. 4.1.3).  Coordinates, minimum-image differences,
+ * the environment matrix, force/virial accumulation and the integrator are
+ * FP64 in every scheme.
+ *   DP_FP64      every step in FP64.
+ *   DP_MIX32     nets in FP32 (MIX-32).
+ *   DP_MIX_BF16  MIX-16 with bf16 operands on the tensor cores, FP32
+ *                accumulation; first embedding layer, tanh and the last
+ *                fitting layer in FP32.
+ *   DP_MIX_FP16  the same with fp16 operands. */
+typedef enum { DP_FP64 = 0, DP_MIX32 = 1, DP_MIX_BF16 = 2, DP_MIX_FP16 = 3 } dp_precision;
+
+/* Model hyper-parameters (Sec. 2, Sec. 5.1).
+ *   ntypes       number of atom types (1..8)
+ *   rcut         cut-off radius r_c (A)
+ *   rcut_smth    start r_cs of the switching region (A), 0 < r_cs < r_c
+ *   sel          [ntypes] neighbors kept per type (padding size per block)
+ *   n_embed      number of embedding layers (1..4); embed[n_embed] widths
+ *                after the 1-wide input; the last width is M1 (<= 128)
+ *   axis_neuron  M2 <= M1, leading embedding channels used in D
+ *   n_fit        number of hidden fitting layers (1..4); fit[n_fit] widths
+ *                (<= 256); the output layer is linear, width 1
+ * One embedding net per (center type, neighbor type) pair, one fitting net
+ * per center type.  Each hidden layer is y = act(x W + b) with tanh and the
+ * skip rule of Fig. 1(e)-(g): y = x + t when widths are equal, (x, x) + t
+ * when the width doubles, t otherwise.  The switching function is 1/r below
+ * r_cs and (1/r)(u^3(-6u^2 + 15u - 10) + 1), u = (r - r_cs)/(r_c - r_cs),
+ * up to r_c: twice continuously differentiable as Sec. 2 requires. */
+typedef struct {
+    int32_t ntypes;
+    double rcut;
+    double rcut_smth;
+    const int32_t *sel;
+    int32_t n_embed;
+    const int32_t *embed;
+    int32_t axis_neuron;
+    int32_t n_fit;
+    const int32_t *fit;
+} dp_model_config;
+
+typedef struct dp_model dp_model;
+typedef struct dp_nlist dp_nlist;
+typedef struct dp_md_state dp_md_state;
+
+/* Human-readable name of a status, and the calling thread's last error
+ * message (empty string when none).  Both strings are owned by the library. */
+const char *dp_status_string(dp_status st);
+const char *dp_last_error(void);
+
+/* ---------------------------------------------------------------- model */
+
+/* Create a model on the current CUDA device with seeded weights: every
+ * weight and bias entry is drawn N(0, 1/fan_in) from SplitMix64(seed)
+ * uniforms (top 53 bits) through Box-Muller, cosine branch first, in the
+ * flat parameter order of dp_model_get_params.  The config is copied.
+ * Errors: DP_ERR_ARG (NULL / invalid shape), DP_ERR_UNSUPPORTED (shape
+ * beyond the limits above), DP_ERR_CUDA, DP_ERR_OOM. */
+dp_status dp_model_create(const dp_model_config *cfg, uint64_t seed, dp_model **out);
+
+/* Number of parameters.  Flat order: embedding nets for (ti, tj) in
+ * row-major pair order, then fitting nets per ti; inside a net every layer
+ * as W (fan_in x fan_out, row-major) followed by b (fan_out). */
+dp_status dp_model_n_params(const dp_model *m, int64_t *n);
+
+/* Copy the FP64 parameters out (n must equal dp_model_n_params). */
+dp_status dp_model_get_params(const dp_model *m, double *flat, int64_t n);
+
+/* Replace the parameters (FP64 master copy; lower-precision copies are
+ * re-derived).  n must equal dp_model_n_params, else DP_ERR_ARG. */
+dp_status dp_model_set_params(dp_model *m, const double *flat, int64_t n);
+
+void dp_model_destroy(dp_model *m);
+
+/* Run this model's host-pointer calls and MD steps on `stream` (a
+ * cudaStream_t passed as void*) instead of the library's own stream; NULL
+ * switches back.  The caller keeps the stream alive while the model uses it. */
+dp_status dp_model_set_stream(dp_model *m, void *stream);
+
+/* ------------------------------------------------------------- tracing */
+
+/* Kernel timing: while enabled, every kernel launch group of this model is
+ * bracketed by CUDA events on its stream (a few microseconds per group).
+ * dp_profile_enable(m, on) turns it on or off and clears the counters.
+ * dp_profile_read waits for the model's stream and returns, for one group,
+ * the kernels launched and their summed device time (ms) since the clear.
+ * dp_profile_group_name returns the group's name, NULL past the last. */
+dp_status dp_profile_enable(dp_model *m, int32_t on);
+dp_status dp_profile_read(dp_model *m, int32_t group, int64_t *launches, double *ms);
+const char *dp_profile_group_name(int32_t group);
+
+/* ---------------------------------------------------------- neighbor list */
+
+/* Build a skin neighbor list (Sec. 5.1: a buffer region around r_c):
+ * candidates are every j != i with minimum-image distance < rcut + skin,
+ * found with a cell grid of edge >= rcut + skin.  rcut must be >= the
+ * model's r_c.  cand_cap is the per-atom candidate capacity (0 = derived
+ * from the density).  The list is then formatted once at these coordinates
+ * (see dp_nlist_get).  coord [n][3], type [n], box [9] = row-major lattice
+ * vectors, host memory.  Errors: DP_ERR_ARG, DP_ERR_BOX, DP_ERR_CAPACITY
+ * (a row overflowed cand_cap: build again with a larger one), DP_ERR_CUDA,
+ * DP_ERR_OOM. */
+dp_status dp_nlist_build(const dp_model *m, int64_t n, const double *coord, const int32_t *type,
+                         const double box[9], double rcut, double skin, int32_t cand_cap, dp_nlist **out);
+
+/* Rebuild the candidates of an existing list at new coordinates (same n,
+ * types, rcut, skin and capacity) and format it there. */
+dp_status dp_nlist_update(dp_nlist *nl, const double *coord, const double box[9]);
+
+/* The formatted list of the last format (build, update or dp_compute):
+ * nlist [n][sum(sel)] int32, for each atom the type-0 block then the type-1
+ * block and so on; inside a block the neighbors with r < r_c ordered by
+ * (floor(r * 1e8), index) ascending, the first sel_t kept, the rest of the
+ * block -1 (Sec. 4.1.1).  *n_truncated = number of neighbors dropped
+ * because a block overflowed (not an error).  Either output may be NULL. */
+dp_status dp_nlist_get(const dp_nlist *nl, int32_t *nlist, int64_t *n_truncated);
+
+void dp_nlist_destroy(dp_nlist *nl);
+
+/* -------------------------------------------------------------- compute */
+
+/* Energy, per-atom energies, forces and virial at coordinates coord [n][3]
+ * (host), formatting the list from its candidates first.  energy [1] eV,
+ * atom_energy [n] eV or NULL, force [n][3] eV/A, virial [9] eV (row-major
+ * W_ab = -sum d_a g_b, symmetric) or NULL.  The candidates must still be
+ * valid for coord (no atom moved more than skin/2 since they were built).
+ * Errors: DP_ERR_ARG, DP_ERR_BOX, DP_ERR_UNSUPPORTED (precision not built),
+ * DP_ERR_NONFINITE, DP_ERR_CUDA, DP_ERR_OOM. */
+dp_status dp_compute(dp_model *m, dp_nlist *nl, const double *coord, const double box[9], dp_precision prec,
+                     double *energy, double *atom_energy, double *force, double *virial);
+
+/* Device-pointer form of dp_compute: d_coord [n][3], d_energy [1],
+ * d_atom_energy [n] or NULL, d_force [n][3], d_virial [9] or NULL, all in
+ * device memory; box stays a host array.  Enqueued on `stream`; no host
+ * synchronisation, so non-finite values are not checked here. */
+dp_status dp_compute_dev(dp_model *m, dp_nlist *nl, const double *d_coord, const double box[9],
+                         dp_precision prec, double *d_energy, double *d_atom_energy, double *d_force,
+                         double *d_virial, void *stream);
+
+/* ------------------------------------------------------------------- MD */
+
+/* MD state for velocity-Verlet NVE (Sec. 5.1): coordinates, velocities,
+ * types, per-type masses (amu) and the box are copied to the device; a skin
+ * list with `skin` A is built there and rebuilt on the device whenever an
+ * atom has moved more than skin/2 since the last build. */
+dp_status dp_md_state_create(dp_model *m, int64_t n, const double *coord, const double *vel, const int32_t *type,
+                             const double *mass_by_type, const double box[9], double skin, int32_t cand_cap,
+                             dp_md_state **out);
+
+/* Run nsteps steps of dt_fs: v += dt/2 a; x += dt v (wrapped into the box);
+ * recompute F; v += dt/2 a, with a = F/m * 9.648533212e-3 A/fs^2.  After
+ * every thermo_every-th step one row (KE eV, PE eV, T K, P bar) is written
+ * to thermo [nsteps/thermo_every][4] (NULL or thermo_every <= 0: none); T
+ * uses 3n - 3 degrees of freedom and P = (2 KE + tr W)/(3V).  The host
+ * synchronises once at the end.  Errors: as dp_compute, plus
+ * DP_ERR_CAPACITY when a rebuild overflowed the candidate capacity (the
+ * steps after the overflow used truncated lists and are not valid: create
+ * the state again with a larger cand_cap). */
+dp_status dp_md_step(dp_model *m, dp_md_state *s, int64_t nsteps, double dt_fs, dp_precision prec,
+                     int32_t thermo_every, double *thermo);
+
+/* Copy the state out: coord [n][3], vel [n][3] (either may be NULL),
+ * *step = steps taken so far, *n_rebuilds = list rebuilds so far (NULL ok). */
+dp_status dp_md_state_get(const dp_md_state *s, double *coord, double *vel, int64_t *step, int64_t *n_rebuilds);
+
+void dp_md_state_destroy(dp_md_state *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DP_H */

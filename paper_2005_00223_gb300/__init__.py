@@ -1,0 +1,103 @@
+"""DeepPot-SE energy / force / virial engine for one GB300 (sm_103a).
+
+The computation lives in the CUDA library ``libdp`` (C-ABI in
+``include/dp.h``); this package holds its build step and a thin ctypes
+binding with the same entry-point names, plus small owning wrappers.
+"""
+from __future__ import annotations
+
+from . import _lib
+from ._lib import (DP_FP64, DP_MIX32, DP_MIX_BF16, DP_MIX_FP16, DPError, EXPORTS, load,  # noqa: F401
+                   dp_compute, dp_compute_dev, dp_md_state_create, dp_md_state_destroy, dp_md_state_get,
+                   dp_md_step, dp_model_create, dp_model_destroy, dp_model_get_params, dp_model_n_params,
+                   dp_model_set_params, dp_model_set_stream, dp_nlist_build, dp_nlist_destroy, dp_nlist_get,
+                   dp_nlist_update, dp_profile_enable, dp_profile_group_name, dp_profile_read)
+
+
+def build(force: bool = False) -> str:
+    from .build import build as _build
+    return _build(force=force)
+
+
+class Model:
+    """Owning wrapper of a dp_model handle."""
+
+    def __init__(self, cfg, seed: int = 0, params=None):
+        self.cfg = cfg
+        self.h = dp_model_create(cfg, seed)
+        if params is not None:
+            dp_model_set_params(self.h, params)
+
+    @property
+    def params(self):
+        return dp_model_get_params(self.h)
+
+    @params.setter
+    def params(self, flat):
+        dp_model_set_params(self.h, flat)
+
+    def close(self):
+        if self.h:
+            dp_model_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class NeighborList:
+    """Owning wrapper of a dp_nlist handle (skin list + formatted list)."""
+
+    def __init__(self, model: Model, coord, typ, box, skin: float = 0.0, cand_cap: int = 0, rcut=None):
+        self.model = model
+        self.n = len(typ)
+        self.h = dp_nlist_build(model.h, coord, typ, box, model.cfg.rcut if rcut is None else rcut, skin, cand_cap)
+
+    def update(self, coord, box):
+        dp_nlist_update(self.h, coord, box)
+
+    def get(self):
+        return dp_nlist_get(self.h, self.n, int(sum(self.model.cfg.sel)))
+
+    def compute(self, coord, box, prec="fp64"):
+        return dp_compute(self.model.h, self.h, coord, box, prec)
+
+    def close(self):
+        if self.h:
+            dp_nlist_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class MDState:
+    """Owning wrapper of a dp_md_state handle (velocity-Verlet NVE on the device)."""
+
+    def __init__(self, model: Model, coord, vel, typ, mass_by_type, box, skin: float = 2.0, cand_cap: int = 0):
+        self.model = model
+        self.n = len(typ)
+        self.h = dp_md_state_create(model.h, coord, vel, typ, mass_by_type, box, skin, cand_cap)
+
+    def step(self, nsteps: int, dt_fs: float, prec="fp64", thermo_every: int = 0):
+        return dp_md_step(self.model.h, self.h, nsteps, dt_fs, prec, thermo_every)
+
+    def get(self):
+        return dp_md_state_get(self.h, self.n)
+
+    def close(self):
+        if self.h:
+            dp_md_state_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

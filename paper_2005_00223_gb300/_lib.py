@@ -1,0 +1,270 @@
+"""ctypes binding of libdp (include/dp.h): the same entry points, argument marshalling only.
+
+Every function here converts Python / numpy / torch arguments to the
+C-ABI's plain pointers and sizes, calls the entry point of the same name
+and turns a non-OK status into a DPError.  No step of the computation runs
+in Python.  The shared library must have been built (``build()``); loading
+fails loudly otherwise — there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdp.so")
+
+DP_OK = 0
+STATUS = {0: "DP_OK", -1: "DP_ERR_ARG", -2: "DP_ERR_CUDA", -3: "DP_ERR_OOM", -4: "DP_ERR_BOX",
+          -5: "DP_ERR_CAPACITY", -6: "DP_ERR_TIMEOUT", -7: "DP_ERR_NONFINITE", -8: "DP_ERR_UNSUPPORTED"}
+DP_FP64, DP_MIX32, DP_MIX_BF16, DP_MIX_FP16 = 0, 1, 2, 3
+PRECISION = {"fp64": DP_FP64, "mix32": DP_MIX32, "bf16": DP_MIX_BF16, "fp16": DP_MIX_FP16}
+
+# Every entry point declared in include/dp.h.
+EXPORTS = [
+    "dp_status_string", "dp_last_error", "dp_model_create", "dp_model_n_params", "dp_model_get_params",
+    "dp_model_set_params", "dp_model_destroy", "dp_model_set_stream", "dp_profile_enable", "dp_profile_read",
+    "dp_profile_group_name", "dp_nlist_build", "dp_nlist_update", "dp_nlist_get",
+    "dp_nlist_destroy", "dp_compute", "dp_compute_dev", "dp_md_state_create", "dp_md_step",
+    "dp_md_state_get", "dp_md_state_destroy",
+]
+
+
+class DPError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Config(C.Structure):
+    _fields_ = [("ntypes", C.c_int32), ("rcut", C.c_double), ("rcut_smth", C.c_double),
+                ("sel", C.POINTER(C.c_int32)), ("n_embed", C.c_int32), ("embed", C.POINTER(C.c_int32)),
+                ("axis_neuron", C.c_int32), ("n_fit", C.c_int32), ("fit", C.POINTER(C.c_int32))]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libdp.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libdp is not built ({path} missing): run paper_2005_00223_gb300.build()")
+        lib = C.CDLL(path)
+        P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        sig = {
+            "dp_status_string": ([C.c_int], C.c_char_p),
+            "dp_last_error": ([], C.c_char_p),
+            "dp_model_create": ([P, C.c_uint64, P], C.c_int),
+            "dp_model_n_params": ([P, P], C.c_int),
+            "dp_model_get_params": ([P, P, I64], C.c_int),
+            "dp_model_set_params": ([P, P, I64], C.c_int),
+            "dp_model_destroy": ([P], None),
+            "dp_model_set_stream": ([P, P], C.c_int),
+            "dp_profile_enable": ([P, I32], C.c_int),
+            "dp_profile_read": ([P, I32, P, P], C.c_int),
+            "dp_profile_group_name": ([I32], C.c_char_p),
+            "dp_nlist_build": ([P, I64, P, P, P, D, D, I32, P], C.c_int),
+            "dp_nlist_update": ([P, P, P], C.c_int),
+            "dp_nlist_get": ([P, P, P], C.c_int),
+            "dp_nlist_destroy": ([P], None),
+            "dp_compute": ([P, P, P, P, C.c_int, P, P, P, P], C.c_int),
+            "dp_compute_dev": ([P, P, P, P, C.c_int, P, P, P, P, P], C.c_int),
+            "dp_md_state_create": ([P, I64, P, P, P, P, P, D, I32, P], C.c_int),
+            "dp_md_step": ([P, P, I64, D, C.c_int, I32, P], C.c_int),
+            "dp_md_state_get": ([P, P, P, P, P], C.c_int),
+            "dp_md_state_destroy": ([P], None),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(st: int, where: str):
+    if st != DP_OK:
+        raise DPError(st, where, load().dp_last_error().decode())
+
+
+def _ptr(a):
+    """Address of a numpy array or a torch tensor (device or host); None -> NULL."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(C.c_void_p)
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a.reshape(shape) if shape is not None else a
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _box(box):
+    return _f64(box).reshape(9).copy()
+
+
+def _prec(p):
+    return PRECISION[p] if isinstance(p, str) else int(p)
+
+
+# ------------------------------------------------------------------ model
+
+def dp_model_create(cfg, seed: int):
+    """cfg: any object with ntypes, rcut, rcut_smth, sel, embed, m2, fit."""
+    lib = load()
+    sel, emb, fit = _i32(cfg.sel), _i32(cfg.embed), _i32(cfg.fit)
+    c = _Config(int(cfg.ntypes), float(cfg.rcut), float(cfg.rcut_smth), sel.ctypes.data_as(C.POINTER(C.c_int32)),
+                len(emb), emb.ctypes.data_as(C.POINTER(C.c_int32)), int(cfg.m2), len(fit),
+                fit.ctypes.data_as(C.POINTER(C.c_int32)))
+    h = C.c_void_p()
+    _check(lib.dp_model_create(C.byref(c), C.c_uint64(seed & ((1 << 64) - 1)), C.byref(h)), "dp_model_create")
+    return h.value
+
+
+def dp_model_n_params(m) -> int:
+    n = C.c_int64()
+    _check(load().dp_model_n_params(m, C.byref(n)), "dp_model_n_params")
+    return n.value
+
+
+def dp_model_get_params(m) -> np.ndarray:
+    n = dp_model_n_params(m)
+    out = np.empty(n)
+    _check(load().dp_model_get_params(m, _ptr(out), n), "dp_model_get_params")
+    return out
+
+
+def dp_model_set_params(m, flat):
+    flat = _f64(flat)
+    _check(load().dp_model_set_params(m, _ptr(flat), flat.size), "dp_model_set_params")
+
+
+def dp_model_destroy(m):
+    if m:
+        load().dp_model_destroy(m)
+
+
+def dp_model_set_stream(m, stream=None):
+    """Run the model's calls on `stream` (torch.cuda.Stream or raw handle); None = library stream."""
+    sp = None if stream is None else C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
+    _check(load().dp_model_set_stream(m, sp), "dp_model_set_stream")
+
+
+def dp_profile_enable(m, on: bool = True):
+    _check(load().dp_profile_enable(m, int(bool(on))), "dp_profile_enable")
+
+
+def dp_profile_group_name(g: int):
+    r = load().dp_profile_group_name(int(g))
+    return None if r is None else r.decode()
+
+
+def dp_profile_read(m):
+    """{group name: (launches, device ms)} since the last dp_profile_enable."""
+    out = {}
+    g = 0
+    while True:
+        name = dp_profile_group_name(g)
+        if name is None:
+            return out
+        n, ms = C.c_int64(), C.c_double()
+        _check(load().dp_profile_read(m, g, C.byref(n), C.byref(ms)), "dp_profile_read")
+        out[name] = (n.value, ms.value)
+        g += 1
+
+
+# ---------------------------------------------------------- neighbor list
+
+def dp_nlist_build(m, coord, typ, box, rcut: float, skin: float = 0.0, cand_cap: int = 0):
+    coord, typ, box = _f64(coord), _i32(typ), _box(box)
+    h = C.c_void_p()
+    _check(load().dp_nlist_build(m, typ.size, _ptr(coord), _ptr(typ), _ptr(box), float(rcut), float(skin),
+                                 int(cand_cap), C.byref(h)), "dp_nlist_build")
+    return h.value
+
+
+def dp_nlist_update(nl, coord, box):
+    coord, box = _f64(coord), _box(box)
+    _check(load().dp_nlist_update(nl, _ptr(coord), _ptr(box)), "dp_nlist_update")
+
+
+def dp_nlist_get(nl, n: int, nsel: int):
+    out = np.empty((n, nsel), dtype=np.int32)
+    ntr = C.c_int64()
+    _check(load().dp_nlist_get(nl, _ptr(out), C.byref(ntr)), "dp_nlist_get")
+    return out, ntr.value
+
+
+def dp_nlist_destroy(nl):
+    if nl:
+        load().dp_nlist_destroy(nl)
+
+
+# ----------------------------------------------------------------- compute
+
+def dp_compute(m, nl, coord, box, prec="fp64"):
+    """Host arrays in, (E, E_i[n], F[n,3], W[3,3]) out."""
+    coord, box = _f64(coord), _box(box)
+    n = coord.shape[0]
+    e = np.zeros(1)
+    ei = np.empty(n)
+    f = np.empty((n, 3))
+    w = np.empty(9)
+    _check(load().dp_compute(m, nl, _ptr(coord), _ptr(box), _prec(prec), _ptr(e), _ptr(ei), _ptr(f), _ptr(w)),
+           "dp_compute")
+    return float(e[0]), ei, f, w.reshape(3, 3)
+
+
+def dp_compute_dev(m, nl, d_coord, box, prec, d_energy, d_atom_energy, d_force, d_virial, stream=None):
+    """Device pointers (torch CUDA tensors, float64) in and out; enqueued on `stream` (a torch stream or None)."""
+    box = _box(box)
+    sp = None if stream is None else C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
+    _check(load().dp_compute_dev(m, nl, _ptr(d_coord), _ptr(box), _prec(prec), _ptr(d_energy), _ptr(d_atom_energy),
+                                 _ptr(d_force), _ptr(d_virial), sp), "dp_compute_dev")
+
+
+# ---------------------------------------------------------------------- MD
+
+def dp_md_state_create(m, coord, vel, typ, mass_by_type, box, skin: float = 2.0, cand_cap: int = 0):
+    coord, vel, typ, mass, box = _f64(coord), _f64(vel), _i32(typ), _f64(mass_by_type), _box(box)
+    h = C.c_void_p()
+    _check(load().dp_md_state_create(m, typ.size, _ptr(coord), _ptr(vel), _ptr(typ), _ptr(mass), _ptr(box),
+                                     float(skin), int(cand_cap), C.byref(h)), "dp_md_state_create")
+    return h.value
+
+
+def dp_md_step(m, s, nsteps: int, dt_fs: float, prec="fp64", thermo_every: int = 0):
+    rows = nsteps // thermo_every if thermo_every > 0 else 0
+    th = np.zeros((max(rows, 1), 4))
+    _check(load().dp_md_step(m, s, int(nsteps), float(dt_fs), _prec(prec), int(thermo_every),
+                             _ptr(th) if rows else None), "dp_md_step")
+    return th[:rows]
+
+
+def dp_md_state_get(s, n: int):
+    x = np.empty((n, 3))
+    v = np.empty((n, 3))
+    step, nreb = C.c_int64(), C.c_int64()
+    _check(load().dp_md_state_get(s, _ptr(x), _ptr(v), C.byref(step), C.byref(nreb)), "dp_md_state_get")
+    return x, v, step.value, nreb.value
+
+
+def dp_md_state_destroy(s):
+    if s:
+        load().dp_md_state_destroy(s)

@@ -1,0 +1,211 @@
+// Internal declarations of libdp: handle structs, device-side model view,
+// kernel launchers.  Not part of the public C-ABI (include/dp.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dp.h"
+
+namespace dp {
+
+constexpr int kMaxTypes = 8;
+constexpr int kMaxEmbed = 4;
+constexpr int kMaxFit = 4;
+constexpr int kMaxM1 = 128;
+constexpr int kMaxFitWidth = 256;
+constexpr int kChunk = 32;          // neighbors per chunk (one per lane)
+
+// Device-side error word bits (ModelDev::err / NlistDev::flags).
+constexpr int kErrCapacity = 1;
+
+void set_error(const char *fmt, ...);
+dp_status cuda_fail(cudaError_t e, const char *what);
+
+#define DP_CUDA(call)                                          \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return dp::cuda_fail(e_, #call); \
+    } while (0)
+
+#define DP_TRY(call)                        \
+    do {                                    \
+        dp_status s_ = (call);              \
+        if (s_ != DP_OK) return s_;         \
+    } while (0)
+
+// Offsets of one net's layers inside the flat parameter vector, relative to
+// the start of the net.  The transposed copy (pT) uses the same offsets with
+// each W (fan_in x fan_out) stored as W^T (fan_out x fan_in).
+struct NetLayout {
+    int n_layers;
+    int win[kMaxFit + 1];
+    int wout[kMaxFit + 1];
+    int64_t W[kMaxFit + 1];
+    int64_t b[kMaxFit + 1];
+    int64_t size;
+};
+
+// Everything a kernel needs to know about the model (passed by value).
+struct ModelDev {
+    int ntypes, nsel, m1, m2, n_embed, n_fit, desc_dim;
+    int sel[kMaxTypes], sel_off[kMaxTypes + 1];
+    int chunk_off[kMaxTypes + 1];   // chunk index where each type block starts
+    int chunks_per_atom;            // sum_t ceil(sel_t / 32)
+    double rcut, rcs;
+    double inv_nsel;
+    NetLayout emb;                  // layout of every embedding net (all alike)
+    NetLayout fit;                  // layout of every fitting net, incl. the output layer
+    int64_t emb_base;               // 0
+    int64_t fit_base;               // ntypes^2 * emb.size
+    const double *p;                // FP64 parameters (flat order)
+    const double *pT;               // FP64 parameters with every W transposed
+    const float *p32;               // FP32 copy (flat order)
+    const float *pT32;              // FP32 transposed copy
+    int act_stride;                 // doubles stored per neighbor for the backward pass
+};
+
+// Kernel launch groups timed by the tracing calls (dp_profile_*).
+enum ProfGroup {
+    PG_BUILD = 0,     // cell grid and skin candidates (5 kernels)
+    PG_FORMAT,        // neighbor-list formatting
+    PG_PACK,          // coordinate packing
+    PG_EMBED_FWD,     // environment rows + embedding net + descriptor
+    PG_FIT,           // fitting net forward + input gradient
+    PG_EMBED_BWD,     // embedding backward + force / virial scatter
+    PG_REDUCE,        // energy / virial reduction
+    PG_MD,            // integrator kernels (kick, drift, displacement check)
+    PG_THERMO,        // thermo rows
+    PG_CHECK,         // non-finite scans
+    PG_COUNT
+};
+
+struct Prof {
+    struct Rec {
+        int g, n;
+        cudaEvent_t a, b;
+    };
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<Rec> pending;
+    int64_t launches[PG_COUNT] = {0};
+    double ms[PG_COUNT] = {0};
+    cudaEvent_t get();
+    void drain();
+    void clear();
+    ~Prof();
+};
+
+// Brackets a group of n kernel launches on stream st with events when on.
+struct ProfScope {
+    Prof *p;
+    int g, n;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    ProfScope(Prof *p_, int g_, int n_, cudaStream_t st_);
+    ~ProfScope();
+};
+
+}  // namespace dp
+
+struct dp_model {
+    int device = 0;
+    int32_t ntypes = 0;
+    double rcut = 0, rcs = 0;
+    int32_t sel[dp::kMaxTypes] = {0};
+    int32_t n_embed = 0, embed[dp::kMaxEmbed] = {0}, m2 = 0, n_fit = 0, fit[dp::kMaxFit] = {0};
+    int64_t nparams = 0;
+    std::vector<double> h_params;
+    double *d_params = nullptr, *d_paramsT = nullptr;
+    float *d_params32 = nullptr, *d_paramsT32 = nullptr;
+    dp::ModelDev dev{};
+    cudaStream_t stream = nullptr;      // stream in use (own_stream unless the caller set one)
+    cudaStream_t own_stream = nullptr;
+    dp::Prof *prof = nullptr;
+    // device workspace (grown on demand, freed at destroy)
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    double *d_scalar = nullptr;       // [16] pinned-reduction target on device
+    double *h_pinned = nullptr;       // [16] host pinned mirror
+    int64_t batch_atoms = 0;          // atoms per batch (0 = derived from the workspace budget)
+    // per-atom scratch for the host-pointer calls: E_i [n], W_i [9n], F [3n], coord [3n], scalars [16]
+    double *d_aux = nullptr;
+    int64_t aux_n = -1;
+    int32_t *d_flag = nullptr;        // [4] non-finite flag and spare
+};
+
+struct dp_nlist {
+    const dp_model *m = nullptr;
+    int64_t n = 0;
+    double rcut = 0, skin = 0, rlist = 0;
+    int32_t cap = 0;
+    double L[3] = {0, 0, 0};
+    int nc[3] = {1, 1, 1};
+    int64_t ncell = 0;
+    int32_t *d_type = nullptr;
+    int32_t *d_cand = nullptr;        // [n][cap]
+    int32_t *d_cand_cnt = nullptr;    // [n]
+    double *d_ref = nullptr;          // [n][4] positions at the last build
+    int32_t *d_cell_of = nullptr;     // [n]
+    int32_t *d_cell_cnt = nullptr;    // [ncell + 1]
+    int32_t *d_cell_start = nullptr;  // [ncell + 1]
+    int32_t *d_cell_atoms = nullptr;  // [n]
+    int32_t *d_nlist = nullptr;       // [n][nsel]
+    int32_t *d_nnei = nullptr;        // [n][ntypes] real neighbors kept per type
+    unsigned long long *d_ntrunc = nullptr;
+    int32_t *d_flags = nullptr;       // [0] error bits, [1] rebuild needed, [2] rebuild count
+    double *d_pos = nullptr;          // [n][4] packed current coordinates (x, y, z, type)
+    double *d_coord = nullptr;        // [n][3] staging for host-pointer calls
+    int32_t *d_order = nullptr;       // [n] atom indices sorted by type (stable)
+    std::vector<int64_t> type_count, type_off;
+};
+
+struct dp_md_state {
+    dp_model *m = nullptr;
+    dp_nlist *nl = nullptr;
+    int64_t n = 0;
+    double *d_x = nullptr;            // [n][3]
+    double *d_v = nullptr;            // [n][3]
+    double *d_f = nullptr;            // [n][3]
+    double *d_minv = nullptr;         // [ntypes] 9.648533212e-3 / m
+    double *d_mass = nullptr;         // [ntypes]
+    double *d_e = nullptr;            // [n] atom energies
+    double *d_scal = nullptr;         // [16]: E, W[9], KE, ...
+    double *d_thermo = nullptr;       // ring of thermo rows
+    int64_t thermo_cap = 0;
+    double box[9] = {0};
+    int64_t step = 0;
+    bool forces_valid = false;
+    dp_precision forces_prec = DP_FP64;
+};
+
+namespace dp {
+
+// Launchers (return DP_OK or an error after recording a message).
+dp_status nlist_build_device(dp_nlist *nl, cudaStream_t st, bool conditional);
+dp_status nlist_format_device(const dp_model *m, dp_nlist *nl, const double *d_coord, cudaStream_t st);
+dp_status pack_positions(dp_nlist *nl, const double *d_coord, cudaStream_t st);
+dp_status compute_fp64(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
+                       double *d_virial, double *d_atom_virial, cudaStream_t st);
+dp_status reduce_energy_virial(const double *d_atom_energy, const double *d_atom_virial, int64_t n,
+                               double *d_energy, double *d_virial, cudaStream_t st);
+dp_status ensure_workspace(dp_model *m, size_t bytes);
+dp_status check_nonfinite(const double *d_x, int64_t n, int32_t *d_flag, cudaStream_t st);
+bool embed_shape_supported(int n_embed, const int *e);
+size_t fp64_bytes_per_atom(const ModelDev &md);
+dp_status compute_mix32(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
+                        double *d_virial, double *d_atom_virial, cudaStream_t st);
+// Full evaluation on device data: pack, format, compute in the requested precision.
+dp_status compute_device(dp_model *m, dp_nlist *nl, const double *d_coord, dp_precision prec, double *d_energy,
+                         double *d_atom_energy, double *d_force, double *d_virial, double *d_atom_virial,
+                         cudaStream_t st);
+dp_status check_box(const double box[9], double rcut, double L[3]);
+// Per-atom scratch of the model: E_i [n] at d_aux, W_i [9n] right after it.
+dp_status ensure_aux(dp_model *m, int64_t n);
+dp_status nlist_create_internal(const dp_model *m, int64_t n, const int32_t *type, const double box[9], double rcut,
+                                double skin, int32_t cand_cap, dp_nlist **out);
+
+}  // namespace dp

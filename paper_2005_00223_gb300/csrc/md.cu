@@ -1,0 +1,289 @@
+// Velocity-Verlet NVE on the device (Sec. 5.1): half kick, drift with
+// wrapping into the box, skin-list rebuild on the device when any atom has
+// moved more than skin/2 since the last build (no host round trip), force
+// evaluation, half kick, and thermo rows (KE, PE, T, P) every k steps.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "dp_internal.cuh"
+#include "geom.cuh"
+
+namespace dp {
+
+namespace {
+
+constexpr double kAccel = 9.648533212e-3;   // 1 eV/(A amu) in A/fs^2
+constexpr double kKB = 8.617333262e-5;      // eV/K
+constexpr double kEvA3ToBar = 1.602176634e6;
+constexpr int kThermoThreads = 512;
+
+__global__ void k_kick(int64_t n, double *__restrict__ v, const double *__restrict__ f,
+                       const int32_t *__restrict__ type, const double *__restrict__ minv, double half_dt)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = half_dt * minv[type[i]];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[3 * i + k] += s * f[3 * i + k];
+}
+
+// x += dt v, wrapped into [0, L); the packed position array is refreshed too.
+__global__ void k_drift(int64_t n, double *__restrict__ x, const double *__restrict__ v, const int32_t *__restrict__ type,
+                        double dt, BoxDev bx, Pos4 *__restrict__ pos)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double p[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double y = x[3 * i + k] + dt * v[3 * i + k];
+        y -= bx.L[k] * floor(y * bx.invL[k]);
+        x[3 * i + k] = y;
+        p[k] = y;
+    }
+    pos[i] = Pos4{p[0], p[1], p[2], (double)type[i]};
+}
+
+// flags[1] = 1 when some atom moved more than half the skin since the last build.
+__global__ void k_disp_check(int64_t n, const Pos4 *__restrict__ pos, const Pos4 *__restrict__ ref, BoxDev bx,
+                             double lim2, int32_t *flags)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double d[3];
+    double r = min_image_r(ref[i], pos[i], bx, d);
+    if (r * r > lim2) flags[1] = 1;
+}
+
+__global__ void __launch_bounds__(kThermoThreads) k_thermo(int64_t n, const double *__restrict__ v,
+                                                          const int32_t *__restrict__ type,
+                                                          const double *__restrict__ mass,
+                                                          const double *__restrict__ scal, double vol,
+                                                          double *__restrict__ row)
+{
+    __shared__ double s[kThermoThreads];
+    const int t = threadIdx.x;
+    double ke = 0.0;
+    for (int64_t i = t; i < n; i += kThermoThreads) {
+        double v2 = v[3 * i] * v[3 * i] + v[3 * i + 1] * v[3 * i + 1] + v[3 * i + 2] * v[3 * i + 2];
+        ke += 0.5 * mass[type[i]] * v2 / kAccel;
+    }
+    s[t] = ke;
+    __syncthreads();
+    for (int h = kThermoThreads / 2; h > 0; h >>= 1) {
+        if (t < h) s[t] += s[t + h];
+        __syncthreads();
+    }
+    if (t == 0) {
+        double k = s[0];
+        row[0] = k;
+        row[1] = scal[0];
+        row[2] = n > 1 ? 2.0 * k / ((3.0 * n - 3.0) * kKB) : 0.0;
+        row[3] = (2.0 * k + scal[1] + scal[5] + scal[9]) / (3.0 * vol) * kEvA3ToBar;
+    }
+}
+
+inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace
+}  // namespace dp
+
+using namespace dp;
+
+extern "C" {
+
+void dp_md_state_destroy(dp_md_state *s)
+{
+    if (!s) return;
+    if (s->m && s->m->stream) cudaStreamSynchronize(s->m->stream);
+    dp_nlist_destroy(s->nl);
+    cudaFree(s->d_x);
+    cudaFree(s->d_v);
+    cudaFree(s->d_f);
+    cudaFree(s->d_minv);
+    cudaFree(s->d_mass);
+    cudaFree(s->d_e);
+    cudaFree(s->d_scal);
+    cudaFree(s->d_thermo);
+    delete s;
+}
+
+dp_status dp_md_state_create(dp_model *m, int64_t n, const double *coord, const double *vel, const int32_t *type,
+                             const double *mass_by_type, const double box[9], double skin, int32_t cand_cap,
+                             dp_md_state **out)
+{
+    if (!m || !out || !mass_by_type || (n > 0 && (!coord || !vel || !type))) {
+        set_error("dp_md_state_create: NULL argument");
+        return DP_ERR_ARG;
+    }
+    *out = nullptr;
+    for (int t = 0; t < m->ntypes; ++t)
+        if (!(mass_by_type[t] > 0)) { set_error("mass of type %d is %g", t, mass_by_type[t]); return DP_ERR_ARG; }
+    dp_md_state *s = new (std::nothrow) dp_md_state();
+    if (!s) return DP_ERR_OOM;
+    s->m = m;
+    s->n = n;
+    memcpy(s->box, box, sizeof(s->box));
+    dp_status st = nlist_create_internal(m, n, type, box, m->rcut, skin, cand_cap, &s->nl);
+    if (st != DP_OK) {
+        delete s;
+        return st;
+    }
+    int64_t nn = n > 0 ? n : 1;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void **p, size_t b) { if (e == cudaSuccess) e = cudaMalloc(p, b); };
+    A((void **)&s->d_x, sizeof(double) * 3 * nn);
+    A((void **)&s->d_v, sizeof(double) * 3 * nn);
+    A((void **)&s->d_f, sizeof(double) * 3 * nn);
+    A((void **)&s->d_e, sizeof(double) * nn);
+    A((void **)&s->d_minv, sizeof(double) * kMaxTypes);
+    A((void **)&s->d_mass, sizeof(double) * kMaxTypes);
+    A((void **)&s->d_scal, sizeof(double) * 16);
+    if (e != cudaSuccess) {
+        st = cuda_fail(e, "dp_md_state_create (allocation)");
+        dp_md_state_destroy(s);
+        return st;
+    }
+    double minv[kMaxTypes] = {0}, mass[kMaxTypes] = {0};
+    for (int t = 0; t < m->ntypes; ++t) {
+        mass[t] = mass_by_type[t];
+        minv[t] = kAccel / mass_by_type[t];
+    }
+    cudaStream_t cs = m->stream;
+    if (n > 0) {
+        e = cudaMemcpyAsync(s->d_x, coord, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_v, vel, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, cs);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_minv, minv, sizeof(minv), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_mass, mass, sizeof(mass), cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) {
+        st = cuda_fail(e, "dp_md_state_create (upload)");
+        dp_md_state_destroy(s);
+        return st;
+    }
+    if (n > 0) {
+        // initial candidate list at the starting coordinates
+        dp_nlist *nl = s->nl;
+        st = pack_positions(nl, s->d_x, cs);
+        if (st == DP_OK) st = nlist_build_device(nl, cs, false);
+        if (st == DP_OK) {
+            int32_t flags[3];
+            e = cudaMemcpyAsync(flags, nl->d_flags, sizeof(flags), cudaMemcpyDeviceToHost, cs);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+            if (e != cudaSuccess) st = cuda_fail(e, "dp_md_state_create (build)");
+            else if (flags[0] & kErrCapacity) {
+                set_error("a candidate list exceeded its capacity of %d", nl->cap);
+                st = DP_ERR_CAPACITY;
+            }
+        }
+        if (st != DP_OK) {
+            dp_md_state_destroy(s);
+            return st;
+        }
+    }
+    *out = s;
+    return DP_OK;
+}
+
+dp_status dp_md_step(dp_model *m, dp_md_state *s, int64_t nsteps, double dt_fs, dp_precision prec,
+                     int32_t thermo_every, double *thermo)
+{
+    if (!m || !s || s->m != m) { set_error("dp_md_step: NULL or mismatched handle"); return DP_ERR_ARG; }
+    if (nsteps < 0 || !(dt_fs > 0) || !isfinite(dt_fs)) { set_error("need nsteps >= 0 and dt > 0"); return DP_ERR_ARG; }
+    if (prec != DP_FP64 && prec != DP_MIX32 && prec != DP_MIX_BF16 && prec != DP_MIX_FP16) {
+        set_error("unknown precision %d", (int)prec);
+        return DP_ERR_ARG;
+    }
+    const int64_t n = s->n;
+    if (n == 0 || nsteps == 0) return DP_OK;
+    dp_nlist *nl = s->nl;
+    cudaStream_t st = m->stream;
+    const int64_t rows = (thermo && thermo_every > 0) ? nsteps / thermo_every : 0;
+    if (rows > s->thermo_cap) {
+        DP_CUDA(cudaStreamSynchronize(st));
+        cudaFree(s->d_thermo);
+        s->d_thermo = nullptr;
+        DP_CUDA(cudaMalloc((void **)&s->d_thermo, sizeof(double) * 4 * rows));
+        s->thermo_cap = rows;
+    }
+    DP_TRY(ensure_aux(m, n));
+    double *Wi = m->d_aux + m->aux_n;       // per-atom virial scratch (after the E_i block)
+    BoxDev bx = make_box(nl);
+    double vol = nl->L[0] * nl->L[1] * nl->L[2];
+    DP_CUDA(cudaMemsetAsync(m->d_flag, 0, sizeof(int32_t), st));
+    DP_CUDA(cudaMemsetAsync(nl->d_flags, 0, sizeof(int32_t), st));
+    if (!s->forces_valid || s->forces_prec != prec) {
+        DP_TRY(pack_positions(nl, s->d_x, st));
+        DP_TRY(compute_device(m, nl, nullptr, prec, s->d_scal, s->d_e, s->d_f, s->d_scal + 1, Wi, st));
+        s->forces_valid = true;
+        s->forces_prec = prec;
+    }
+    const double lim = 0.5 * nl->skin;
+    int64_t row = 0;
+    for (int64_t k = 1; k <= nsteps; ++k) {
+        {
+            ProfScope ps(m->prof, PG_MD, 3, st);
+            k_kick<<<nblk(n), 256, 0, st>>>(n, s->d_v, s->d_f, nl->d_type, s->d_minv, 0.5 * dt_fs);
+            k_drift<<<nblk(n), 256, 0, st>>>(n, s->d_x, s->d_v, nl->d_type, dt_fs, bx, (Pos4 *)nl->d_pos);
+            DP_CUDA(cudaMemsetAsync(nl->d_flags + 1, 0, sizeof(int32_t), st));
+            k_disp_check<<<nblk(n), 256, 0, st>>>(n, (const Pos4 *)nl->d_pos, (const Pos4 *)nl->d_ref, bx,
+                                              lim * lim, nl->d_flags);
+        }
+        DP_CUDA(cudaGetLastError());
+        DP_TRY(nlist_build_device(nl, st, true));
+        DP_TRY(compute_device(m, nl, nullptr, prec, s->d_scal, s->d_e, s->d_f, s->d_scal + 1, Wi, st));
+        {
+            ProfScope ps(m->prof, PG_MD, 1, st);
+            k_kick<<<nblk(n), 256, 0, st>>>(n, s->d_v, s->d_f, nl->d_type, s->d_minv, 0.5 * dt_fs);
+        }
+        if (rows && k % thermo_every == 0 && row < rows) {
+            ProfScope ps(m->prof, PG_THERMO, 1, st);
+            k_thermo<<<1, kThermoThreads, 0, st>>>(n, s->d_v, nl->d_type, s->d_mass, s->d_scal, vol,
+                                                   s->d_thermo + 4 * row);
+            ++row;
+        }
+        DP_CUDA(cudaGetLastError());
+    }
+    s->step += nsteps;
+    {
+        ProfScope ps(m->prof, PG_CHECK, 2, st);
+        DP_TRY(check_nonfinite(s->d_f, 3 * n, m->d_flag, st));
+        DP_TRY(check_nonfinite(s->d_x, 3 * n, m->d_flag, st));
+    }
+    int32_t flag = 0, flags[3];
+    DP_CUDA(cudaMemcpyAsync(&flag, m->d_flag, sizeof(flag), cudaMemcpyDeviceToHost, st));
+    DP_CUDA(cudaMemcpyAsync(flags, nl->d_flags, sizeof(flags), cudaMemcpyDeviceToHost, st));
+    std::vector<double> th(4 * rows);
+    if (rows) DP_CUDA(cudaMemcpyAsync(th.data(), s->d_thermo, sizeof(double) * 4 * rows, cudaMemcpyDeviceToHost, st));
+    DP_CUDA(cudaStreamSynchronize(st));
+    if (flags[0] & kErrCapacity) {
+        set_error("a candidate list rebuild exceeded its capacity of %d; the trajectory after it is invalid", nl->cap);
+        return DP_ERR_CAPACITY;
+    }
+    if (flag) { set_error("non-finite forces or coordinates during MD"); return DP_ERR_NONFINITE; }
+    if (rows) memcpy(thermo, th.data(), sizeof(double) * 4 * rows);
+    return DP_OK;
+}
+
+dp_status dp_md_state_get(const dp_md_state *s, double *coord, double *vel, int64_t *step, int64_t *n_rebuilds)
+{
+    if (!s) { set_error("dp_md_state_get: NULL state"); return DP_ERR_ARG; }
+    cudaStream_t st = s->m->stream;
+    DP_CUDA(cudaStreamSynchronize(st));
+    if (coord && s->n) DP_CUDA(cudaMemcpy(coord, s->d_x, sizeof(double) * 3 * s->n, cudaMemcpyDeviceToHost));
+    if (vel && s->n) DP_CUDA(cudaMemcpy(vel, s->d_v, sizeof(double) * 3 * s->n, cudaMemcpyDeviceToHost));
+    if (step) *step = s->step;
+    if (n_rebuilds) {
+        int32_t f[3] = {0, 0, 0};
+        if (s->n) DP_CUDA(cudaMemcpy(f, s->nl->d_flags, sizeof(f), cudaMemcpyDeviceToHost));
+        *n_rebuilds = f[2];
+    }
+    return DP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,290 @@
+// Neighbor list on the device: cell-grid skin candidates (Sec. 5.1, a buffer
+// region around r_c) and the per-step formatting of Sec. 4.1.1-4.1.2: keep
+// r < r_c, order by neighbor type, then by floor(r * 1e8), then by index,
+// keep the first sel_t of each type block and pad with -1.
+//
+// The paper packs (type, distance, index) into one decimal 64-bit key
+// (type * 1e16 + floor(r * 1e8) * 1e6 + j) and sorts with a CUB block sort.
+// Here the key is packed in binary, type:8 | floor(r * 1e8):30 | j:26, which
+// orders exactly like the decimal key wherever both fit and holds indices up
+// to 2^26 (the decimal key stops at 10^6, below the 1.57M-atom water box).
+// Each warp owns one atom; its keys sit in shared memory and every key finds
+// its slot by counting the smaller keys (keys are distinct because j is),
+// which needs no sort network and no padding to a power of two.
+//
+// Distances use explicitly rounded FP64 operations (no contraction) in the
+// order d_k = (r_j - r_i) - L_k rint((r_j - r_i) / L_k),
+// r = sqrt((dx dx + dy dy) + dz dz), so the list is bit-identical to any
+// IEEE implementation that uses the same order.
+#include <cuda_runtime.h>
+
+#include "dp_internal.cuh"
+#include "geom.cuh"
+
+namespace dp {
+namespace {
+
+__device__ __forceinline__ int cell_coord(double x, double invL, int nc)
+{
+    double f = x * invL;
+    f -= floor(f);
+    int c = (int)(f * nc);
+    return c >= nc ? nc - 1 : (c < 0 ? 0 : c);
+}
+
+__global__ void k_pack(int64_t n, const double *__restrict__ coord, const int32_t *__restrict__ type,
+                       Pos4 *__restrict__ pos)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    pos[i] = Pos4{coord[3 * i], coord[3 * i + 1], coord[3 * i + 2], (double)type[i]};
+}
+
+// flags[1] gates the conditional (MD) rebuild: kernels return at once when
+// it is zero.
+__device__ __forceinline__ bool skip(const int32_t *flags, int cond) { return cond && flags[1] == 0; }
+
+__global__ void k_cell_zero(int64_t ncell, int32_t *cnt, const int32_t *flags, int cond)
+{
+    if (skip(flags, cond)) return;
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c <= ncell) cnt[c] = 0;
+}
+
+__global__ void k_cell_assign(int64_t n, const Pos4 *__restrict__ pos, BoxDev bx, int32_t *cell_of, int32_t *cnt,
+                              const int32_t *flags, int cond)
+{
+    if (skip(flags, cond)) return;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Pos4 p = pos[i];
+    int cx = cell_coord(p.x, bx.invL[0], bx.nc[0]);
+    int cy = cell_coord(p.y, bx.invL[1], bx.nc[1]);
+    int cz = cell_coord(p.z, bx.invL[2], bx.nc[2]);
+    int c = (cx * bx.nc[1] + cy) * bx.nc[2] + cz;
+    cell_of[i] = c;
+    atomicAdd(&cnt[c], 1);
+}
+
+// Exclusive scan of the cell counts by one block; zeroes the counts so they
+// serve as fill cursors next.
+__global__ void k_cell_scan(int64_t ncell, int32_t *cnt, int32_t *start, const int32_t *flags, int cond)
+{
+    if (skip(flags, cond)) return;
+    __shared__ int32_t part[1024];
+    int tid = threadIdx.x, nt = blockDim.x;
+    int64_t per = (ncell + nt - 1) / nt;
+    int64_t b = tid * per, e = b + per < ncell ? b + per : ncell;
+    int32_t s = 0;
+    for (int64_t c = b; c < e; ++c) s += cnt[c];
+    part[tid] = s;
+    __syncthreads();
+    for (int off = 1; off < nt; off <<= 1) {
+        int32_t v = tid >= off ? part[tid - off] : 0;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    int32_t run = part[tid] - s;
+    for (int64_t c = b; c < e; ++c) {
+        int32_t v = cnt[c];
+        start[c] = run;
+        run += v;
+        cnt[c] = 0;
+    }
+    if (tid == nt - 1) start[ncell] = part[tid];
+}
+
+__global__ void k_cell_fill(int64_t n, const int32_t *cell_of, const int32_t *start, int32_t *cursor,
+                            int32_t *atoms, const int32_t *flags, int cond)
+{
+    if (skip(flags, cond)) return;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = cell_of[i];
+    atoms[start[c] + atomicAdd(&cursor[c], 1)] = (int32_t)i;
+}
+
+// One warp per atom: every j != i in the surrounding cells with
+// minimum-image distance < rlist.
+__global__ void k_candidates(int64_t n, const Pos4 *__restrict__ pos, BoxDev bx, double rlist,
+                             const int32_t *__restrict__ cell_of, const int32_t *__restrict__ start,
+                             const int32_t *__restrict__ atoms, int32_t cap, int32_t *__restrict__ cand,
+                             int32_t *__restrict__ cand_cnt, Pos4 *__restrict__ ref, int32_t *flags, int cond)
+{
+    if (skip(flags, cond)) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    const Pos4 pi = pos[i];
+    const int c = cell_of[i];
+    const int c3[3] = {c / (bx.nc[1] * bx.nc[2]), (c / bx.nc[2]) % bx.nc[1], c % bx.nc[2]};
+    int lo[3], hi[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (bx.nc[k] >= 3) { lo[k] = -1; hi[k] = 1; }
+        else { lo[k] = -c3[k]; hi[k] = bx.nc[k] - 1 - c3[k]; }
+    }
+    int32_t count = 0;
+    int32_t *row = cand + i * (int64_t)cap;
+    for (int a = lo[0]; a <= hi[0]; ++a)
+        for (int b = lo[1]; b <= hi[1]; ++b)
+            for (int e = lo[2]; e <= hi[2]; ++e) {
+                int x = (c3[0] + a + bx.nc[0]) % bx.nc[0];
+                int y = (c3[1] + b + bx.nc[1]) % bx.nc[1];
+                int z = (c3[2] + e + bx.nc[2]) % bx.nc[2];
+                int cell = (x * bx.nc[1] + y) * bx.nc[2] + z;
+                int s0 = start[cell], s1 = start[cell + 1];
+                for (int base = s0; base < s1; base += 32) {
+                    int p = base + lane;
+                    bool ok = false;
+                    int32_t j = -1;
+                    if (p < s1) {
+                        j = atoms[p];
+                        if (j != i) {
+                            double d[3];
+                            ok = min_image_r(pi, pos[j], bx, d) < rlist;
+                        }
+                    }
+                    unsigned m = __ballot_sync(0xffffffffu, ok);
+                    int off = __popc(m & ((1u << lane) - 1u));
+                    if (ok && count + off < cap) row[count + off] = j;
+                    count += __popc(m);
+                }
+            }
+    if (lane == 0) {
+        cand_cnt[i] = count < cap ? count : cap;
+        if (count > cap) atomicOr(&flags[0], kErrCapacity);
+        ref[i] = pi;
+    }
+    if (i == 0 && lane == 0) atomicAdd(&flags[2], 1);
+}
+
+// One warp per atom; keys of the atom's real neighbors staged in shared
+// memory (cap per warp).  Slot of a key = number of smaller keys minus the
+// keys of lower types.
+__global__ void k_format(int64_t n, const Pos4 *__restrict__ pos, BoxDev bx, ModelDev md,
+                         const int32_t *__restrict__ cand, const int32_t *__restrict__ cand_cnt, int32_t cap,
+                         int32_t *__restrict__ nlist, int32_t *__restrict__ nnei, unsigned long long *ntrunc)
+{
+    extern __shared__ unsigned long long keys_all[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    unsigned long long *keys = keys_all + (int64_t)warp * cap;
+    const Pos4 pi = pos[i];
+    const int32_t nc = cand_cnt[i];
+    const int32_t *row = cand + i * (int64_t)cap;
+    int nk = 0;
+    for (int base = 0; base < nc; base += 32) {
+        int c = base + lane;
+        bool ok = false;
+        unsigned long long key = 0;
+        if (c < nc) {
+            int32_t j = row[c];
+            Pos4 pj = pos[j];
+            double d[3];
+            double r = min_image_r(pi, pj, bx, d);
+            if (j != i && r < md.rcut) {
+                ok = true;
+                unsigned long long q = (unsigned long long)floor(__dmul_rn(r, 1e8));
+                key = ((unsigned long long)(int)pj.w << 56) | (q << 26) | (unsigned long long)j;
+            }
+        }
+        unsigned m = __ballot_sync(0xffffffffu, ok);
+        int off = __popc(m & ((1u << lane) - 1u));
+        if (ok) keys[nk + off] = key;
+        nk += __popc(m);
+    }
+    __syncwarp();
+    // per-type counts
+    int tcount[kMaxTypes];
+#pragma unroll
+    for (int t = 0; t < kMaxTypes; ++t) tcount[t] = 0;
+    for (int p = lane; p < nk; p += 32) {
+        int t = (int)(keys[p] >> 56);
+#pragma unroll
+        for (int u = 0; u < kMaxTypes; ++u) tcount[u] += (t == u);
+    }
+#pragma unroll
+    for (int t = 0; t < kMaxTypes; ++t)
+        for (int o = 16; o > 0; o >>= 1) tcount[t] += __shfl_xor_sync(0xffffffffu, tcount[t], o);
+    int tstart[kMaxTypes];
+    int acc = 0;
+#pragma unroll
+    for (int t = 0; t < kMaxTypes; ++t) { tstart[t] = acc; acc += tcount[t]; }
+    int32_t *out = nlist + i * (int64_t)md.nsel;
+    for (int p = lane; p < nk; p += 32) {
+        unsigned long long k = keys[p];
+        int rank = 0;
+        for (int q = 0; q < nk; ++q) rank += keys[q] < k;
+        int t = (int)(k >> 56);
+        int local = rank - tstart[t];
+        if (local < md.sel[t]) out[md.sel_off[t] + local] = (int32_t)(k & ((1ull << 26) - 1));
+    }
+    unsigned long long dropped = 0;
+    for (int t = 0; t < md.ntypes; ++t) {
+        int kept = tcount[t] < md.sel[t] ? tcount[t] : md.sel[t];
+        for (int s = kept + lane; s < md.sel[t]; s += 32) out[md.sel_off[t] + s] = -1;
+        if (lane == 0) nnei[i * md.ntypes + t] = kept;
+        if (tcount[t] > md.sel[t]) dropped += (unsigned long long)(tcount[t] - md.sel[t]);
+    }
+    if (lane == 0 && dropped) atomicAdd(ntrunc, dropped);
+}
+
+inline unsigned blocks_for(int64_t work, int per) { return (unsigned)((work + per - 1) / per); }
+
+}  // namespace
+
+dp_status pack_positions(dp_nlist *nl, const double *d_coord, cudaStream_t st)
+{
+    if (nl->n == 0) return DP_OK;
+    ProfScope ps(nl->m->prof, PG_PACK, 1, st);
+    k_pack<<<blocks_for(nl->n, 256), 256, 0, st>>>(nl->n, d_coord, nl->d_type, (Pos4 *)nl->d_pos);
+    DP_CUDA(cudaGetLastError());
+    return DP_OK;
+}
+
+// Builds the candidate lists from d_pos.  With conditional = true every
+// kernel first reads flags[1] and does nothing when no rebuild is needed.
+dp_status nlist_build_device(dp_nlist *nl, cudaStream_t st, bool conditional)
+{
+    if (nl->n == 0) return DP_OK;
+    BoxDev bx = make_box(nl);
+    int cond = conditional ? 1 : 0;
+    const Pos4 *pos = (const Pos4 *)nl->d_pos;
+    ProfScope ps(nl->m->prof, PG_BUILD, 5, st);
+    k_cell_zero<<<blocks_for(nl->ncell + 1, 256), 256, 0, st>>>(nl->ncell, nl->d_cell_cnt, nl->d_flags, cond);
+    k_cell_assign<<<blocks_for(nl->n, 256), 256, 0, st>>>(nl->n, pos, bx, nl->d_cell_of, nl->d_cell_cnt,
+                                                         nl->d_flags, cond);
+    k_cell_scan<<<1, 1024, 0, st>>>(nl->ncell, nl->d_cell_cnt, nl->d_cell_start, nl->d_flags, cond);
+    k_cell_fill<<<blocks_for(nl->n, 256), 256, 0, st>>>(nl->n, nl->d_cell_of, nl->d_cell_start, nl->d_cell_cnt,
+                                                       nl->d_cell_atoms, nl->d_flags, cond);
+    k_candidates<<<blocks_for(nl->n * 32, 256), 256, 0, st>>>(nl->n, pos, bx, nl->rlist, nl->d_cell_of,
+                                                             nl->d_cell_start, nl->d_cell_atoms, nl->cap,
+                                                             nl->d_cand, nl->d_cand_cnt, (Pos4 *)nl->d_ref,
+                                                             nl->d_flags, cond);
+    DP_CUDA(cudaGetLastError());
+    return DP_OK;
+}
+
+dp_status nlist_format_device(const dp_model *m, dp_nlist *nl, const double *d_coord, cudaStream_t st)
+{
+    if (nl->n == 0) return DP_OK;
+    if (d_coord) DP_TRY(pack_positions(nl, d_coord, st));
+    BoxDev bx = make_box(nl);
+    DP_CUDA(cudaMemsetAsync(nl->d_ntrunc, 0, sizeof(unsigned long long), st));
+    const int warps = 4;
+    size_t smem = (size_t)warps * nl->cap * sizeof(unsigned long long);
+    if (smem > 48 * 1024)
+        DP_CUDA(cudaFuncSetAttribute(k_format, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ProfScope ps(m->prof, PG_FORMAT, 1, st);
+    k_format<<<blocks_for(nl->n, warps), warps * 32, smem, st>>>(nl->n, (const Pos4 *)nl->d_pos, bx, m->dev,
+                                                                  nl->d_cand, nl->d_cand_cnt, nl->cap, nl->d_nlist,
+                                                                  nl->d_nnei, nl->d_ntrunc);
+    DP_CUDA(cudaGetLastError());
+    return DP_OK;
+}
+
+}  // namespace dp

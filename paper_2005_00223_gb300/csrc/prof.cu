@@ -1,0 +1,119 @@
+// Tracing: CUDA-event timing of kernel launch groups (dp_profile_*), and the
+// caller-selected stream (dp_model_set_stream).
+#include <cuda_runtime.h>
+
+#include "dp_internal.cuh"
+
+namespace dp {
+
+cudaEvent_t Prof::get()
+{
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void Prof::drain()
+{
+    for (const Rec &r : pending) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.g] += t;
+        launches[r.g] += r.n;
+        pool.push_back(r.a);
+        pool.push_back(r.b);
+    }
+    pending.clear();
+}
+
+void Prof::clear()
+{
+    for (const Rec &r : pending) {
+        pool.push_back(r.a);
+        pool.push_back(r.b);
+    }
+    pending.clear();
+    for (int g = 0; g < PG_COUNT; ++g) {
+        launches[g] = 0;
+        ms[g] = 0.0;
+    }
+}
+
+Prof::~Prof()
+{
+    clear();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+}
+
+ProfScope::ProfScope(Prof *p_, int g_, int n_, cudaStream_t st_) : p(p_), g(g_), n(n_), st(st_)
+{
+    if (p && p->on) {
+        a = p->get();
+        cudaEventRecord(a, st);
+    }
+}
+
+ProfScope::~ProfScope()
+{
+    if (p && p->on && a) {
+        cudaEvent_t b = p->get();
+        cudaEventRecord(b, st);
+        p->pending.push_back({g, n, a, b});
+    }
+}
+
+}  // namespace dp
+
+using namespace dp;
+
+static const char *kGroupNames[PG_COUNT] = {"nlist_build", "nlist_format", "pack", "embed_fwd", "fitting",
+                                             "embed_bwd", "reduce", "md_update", "thermo", "nonfinite_check"};
+
+extern "C" {
+
+dp_status dp_model_set_stream(dp_model *m, void *stream)
+{
+    if (!m) {
+        set_error("dp_model_set_stream: NULL model");
+        return DP_ERR_ARG;
+    }
+    DP_CUDA(cudaStreamSynchronize(m->stream));
+    m->stream = stream ? (cudaStream_t)stream : m->own_stream;
+    return DP_OK;
+}
+
+dp_status dp_profile_enable(dp_model *m, int32_t on)
+{
+    if (!m || !m->prof) {
+        set_error("dp_profile_enable: NULL model");
+        return DP_ERR_ARG;
+    }
+    DP_CUDA(cudaStreamSynchronize(m->stream));
+    m->prof->clear();
+    m->prof->on = on != 0;
+    return DP_OK;
+}
+
+dp_status dp_profile_read(dp_model *m, int32_t group, int64_t *launches, double *ms)
+{
+    if (!m || !m->prof || group < 0 || group >= PG_COUNT) {
+        set_error("dp_profile_read: bad model or group %d", group);
+        return DP_ERR_ARG;
+    }
+    DP_CUDA(cudaStreamSynchronize(m->stream));
+    m->prof->drain();
+    if (launches) *launches = m->prof->launches[group];
+    if (ms) *ms = m->prof->ms[group];
+    return DP_OK;
+}
+
+const char *dp_profile_group_name(int32_t group)
+{
+    return (group >= 0 && group < PG_COUNT) ? kGroupNames[group] : nullptr;
+}
+
+}  // extern "C"

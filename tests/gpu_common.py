@@ -1,0 +1,33 @@
+"""Shared helpers of the GPU parity tests (inputs from dpsynth, expected values from the oracle)."""
+import numpy as np
+
+import dpsynth
+
+
+def systems():
+    """(name, cfg, coord, type, box) of the parity workloads, small enough for the oracle."""
+    out = []
+    cfg = dpsynth.water_config()
+    c, t, b = dpsynth.water_box(1)
+    out.append(("water192", cfg, c, t, b))
+    cfg = dpsynth.copper_config()
+    c, t, b = dpsynth.copper_fcc(1, ncell=5)
+    out.append(("cu500", cfg, c, t, b))
+    return out
+
+
+def rms(F):
+    return float(np.sqrt((F ** 2).sum(1).mean()))
+
+
+def assert_close_fp64(gpu, ref, rtol=1e-10):
+    """E, E_i, F, W within rtol relative (norm-wise for vectors, against the oracle's scale)."""
+    E, Ei, F, W = gpu
+    Er, Eir, Fr, Wr = ref
+    assert abs(E - Er) <= rtol * abs(Er), (E, Er)
+    escale = max(np.abs(Eir).max(), 1e-300)
+    assert np.abs(Ei - Eir).max() <= rtol * escale, np.abs(Ei - Eir).max() / escale
+    fs = rms(Fr)
+    err = np.sqrt(((F - Fr) ** 2).sum(1)).max()
+    assert err <= rtol * fs, err / fs
+    assert np.abs(W - Wr).max() <= rtol * np.abs(Wr).max(), np.abs(W - Wr).max() / np.abs(Wr).max()
