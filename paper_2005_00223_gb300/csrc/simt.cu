@@ -1,22 +1,28 @@
-// FP64 evaluation of the DeepPot-SE energy, forces and virial (Sec. 2,
-// Fig. 1), the "double" scheme of Sec. 4.1.3.
+// CUDA-core (SIMT) evaluation of the DeepPot-SE energy, forces and virial
+// (Sec. 2, Fig. 1) in two of the precision schemes of Sec. 4.1.3:
+//   Real = double: the "double" scheme, every step in FP64;
+//   Real = float:  MIX-32, nets (embedding, contraction, descriptor,
+//                  fitting and their gradients) in FP32 with FP32 weights,
+//                  while coordinates, the environment matrix and its
+//                  Jacobian, the chain to dE/dd_ij, the force / virial
+//                  accumulation and the energy sum stay FP64.
 //
-// Three kernels per batch of atoms (atoms taken in type-sorted order so that
+// Three kernels per batch of atoms (atoms in type-sorted order so that
 // neighboring CTAs share nets):
-//   k_embed_fwd64  one CTA per atom: environment rows, the embedding net on
-//                  32-neighbor chunks (one neighbor per lane, output
-//                  channels split over the CTA's G warps), the contraction
-//                  T = (1/sum sel) sum_j G_j^T R_j and D = T T<^T.  The tanh
-//                  values of every layer and the last embedding output are
-//                  stored for the backward pass (FP64 tanh costs far more
-//                  than the HBM round trip on this part).
-//   k_fit64        A atoms per CTA: the fitting net forward (E_i) and its
-//                  input gradient dE/dD, weights read from L2.
-//   k_embed_bwd64  one CTA per atom: dE/dT, then per chunk dE/dG_j and
-//                  dE/dR_j, back through the embedding net to dE/ds_j, the
-//                  chain through the environment row to g_ij = dE_i/dd_ij,
-//                  and the scatter F_i += g_ij, F_j -= g_ij (FP64 atomics),
-//                  with the per-atom virial -sum_j d_ij (x) g_ij.
+//   k_embed_fwd  one CTA per atom: environment rows, the embedding net on
+//                32-neighbor chunks (one neighbor per lane, output channels
+//                split over the CTA's G warps), the contraction
+//                T = (1/sum sel) sum_j G_j^T R_j and D = T T<^T.  The tanh
+//                values of every layer and the last embedding output are
+//                stored for the backward pass (recomputing tanh costs more
+//                than the HBM round trip here).
+//   k_fit        A atoms per CTA: fitting net forward (E_i) and its input
+//                gradient dE/dD, weights read through L2.
+//   k_embed_bwd  one CTA per atom: dE/dT, then per chunk dE/dG_j and dE/dR_j,
+//                back through the embedding net to dE/ds_j, the chain
+//                through the environment row to g_ij = dE_i/dd_ij, and the
+//                scatter F_i += g_ij, F_j -= g_ij (FP64 atomics) with the
+//                per-atom virial -sum_j d_ij (x) g_ij.
 // The MATMUL+SUM and CONCAT+SUM fusions of Sec. 4.2 are the bias and skip
 // terms added in registers; TANH and TANHGrad (Sec. 4.2.3) share the stored
 // tanh value.
@@ -31,6 +37,22 @@ namespace {
 
 constexpr int kFitAtoms = 8;
 
+__device__ __forceinline__ double act_tanh(double x) { return tanh(x); }
+__device__ __forceinline__ float act_tanh(float x) { return tanhf(x); }
+
+template <typename Real>
+__device__ __forceinline__ const Real *params_of(const ModelDev &md);
+template <>
+__device__ __forceinline__ const double *params_of<double>(const ModelDev &md) { return md.p; }
+template <>
+__device__ __forceinline__ const float *params_of<float>(const ModelDev &md) { return md.p32; }
+template <typename Real>
+__device__ __forceinline__ const Real *paramsT_of(const ModelDev &md);
+template <>
+__device__ __forceinline__ const double *paramsT_of<double>(const ModelDev &md) { return md.pT; }
+template <>
+__device__ __forceinline__ const float *paramsT_of<float>(const ModelDev &md) { return md.pT32; }
+
 // Compile-time embedding shape: three layers of widths E0, E1, E2 (= M1),
 // split over G warps (channel o belongs to warp o % G).
 template <int G_, int E0_, int E1_, int E2_>
@@ -42,27 +64,28 @@ struct EmbShape {
     static constexpr int ACT = E0_ + E1_ + E2_ + E2_;    // stored per neighbor: t of each layer, then G_j
 };
 
-__device__ __forceinline__ double skip_term(int wout, int win, const double *x, int o, int n)
+template <typename Real>
+__device__ __forceinline__ Real skip_term(int wout, int win, const Real *x, int o, int n)
 {
     if (wout == win) return x[o * 32 + n];
     if (wout == 2 * win) return x[(o % win) * 32 + n];
-    return 0.0;
+    return Real(0);
 }
 
 // One hidden embedding layer for the 32 neighbors of a chunk: y = skip + tanh(x W + b).
-template <int G, int WIN, int WOUT>
-__device__ __forceinline__ void emb_layer_fwd(const double *__restrict__ sWl, const double *__restrict__ sbl,
-                                              const double *__restrict__ xin, double *__restrict__ yout,
-                                              double *__restrict__ act_t, double *__restrict__ act_y, int g, int n)
+template <int G, int WIN, int WOUT, typename Real>
+__device__ __forceinline__ void emb_layer_fwd(const Real *__restrict__ sWl, const Real *__restrict__ sbl,
+                                              const Real *__restrict__ xin, Real *__restrict__ yout,
+                                              Real *__restrict__ act_t, Real *__restrict__ act_y, int g, int n)
 {
     constexpr int NO = (WOUT + G - 1) / G;
-    double acc[NO];
+    Real acc[NO];
 #pragma unroll
-    for (int u = 0; u < NO; ++u) acc[u] = (g + G * u < WOUT) ? sbl[g + G * u] : 0.0;
+    for (int u = 0; u < NO; ++u) acc[u] = (g + G * u < WOUT) ? sbl[g + G * u] : Real(0);
 #pragma unroll 5
     for (int kk = 0; kk < WIN; ++kk) {
-        const double xv = xin[kk * 32 + n];
-        const double *Wr = sWl + kk * WOUT + g;
+        const Real xv = xin[kk * 32 + n];
+        const Real *Wr = sWl + kk * WOUT + g;
 #pragma unroll
         for (int u = 0; u < NO; ++u)
             if (WOUT % G == 0 || g + G * u < WOUT) acc[u] += xv * Wr[G * u];
@@ -71,8 +94,8 @@ __device__ __forceinline__ void emb_layer_fwd(const double *__restrict__ sWl, co
     for (int u = 0; u < NO; ++u) {
         const int o = g + G * u;
         if (WOUT % G == 0 || o < WOUT) {
-            const double t = tanh(acc[u]);
-            const double y = skip_term(WOUT, WIN, xin, o, n) + t;
+            const Real t = act_tanh(acc[u]);
+            const Real y = skip_term(WOUT, WIN, xin, o, n) + t;
             yout[o * 32 + n] = y;
             act_t[o * 32 + n] = t;
             if (act_y) act_y[o * 32 + n] = y;
@@ -80,36 +103,38 @@ __device__ __forceinline__ void emb_layer_fwd(const double *__restrict__ sWl, co
     }
 }
 
-template <class S>
-__global__ void __launch_bounds__(S::NT) k_embed_fwd64(ModelDev md, BoxDev bx, const int32_t *__restrict__ order,
-                                                      int64_t p0, const Pos4 *__restrict__ pos,
-                                                      const int32_t *__restrict__ nlist,
-                                                      const int32_t *__restrict__ nnei, double *__restrict__ T_out,
-                                                      double *__restrict__ D_out, double *__restrict__ act)
+template <class S, typename Real>
+__global__ void __launch_bounds__(S::NT) k_embed_fwd(ModelDev md, BoxDev bx, const int32_t *__restrict__ order,
+                                                    int64_t p0, const Pos4 *__restrict__ pos,
+                                                    const int32_t *__restrict__ nlist, const int32_t *__restrict__ nnei,
+                                                    Real *__restrict__ T_out, Real *__restrict__ D_out,
+                                                    Real *__restrict__ act)
 {
     constexpr int G = S::G, NT = S::NT;
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real *smem = reinterpret_cast<Real *>(smem_raw);
     const int tid = threadIdx.x, n = tid & 31, g = tid >> 5;
-    double *sW = smem;
-    double *sA = sW + md.emb.size;
-    double *sB = sA + S::WMAX * 32;
-    double *sR = sB + S::WMAX * 32;       // [32][4]
-    double *sT = sR + 32 * 4;             // [M1][4]
+    Real *sW = smem;
+    Real *sA = sW + md.emb.size;
+    Real *sB = sA + S::WMAX * 32;
+    Real *sR = sB + S::WMAX * 32;         // [32][4]
+    Real *sT = sR + 32 * 4;               // [M1][4]
     const int64_t p = p0 + blockIdx.x;
     const int i = order[p];
     const Pos4 pi = pos[i];
     const int ti = (int)pi.w;
-    double tacc[S::KT];
+    Real tacc[S::KT];
 #pragma unroll
-    for (int u = 0; u < S::KT; ++u) tacc[u] = 0.0;
+    for (int u = 0; u < S::KT; ++u) tacc[u] = Real(0);
     constexpr int act_chunk = S::ACT * 32;
-    double *act_atom = act + (int64_t)blockIdx.x * md.chunks_per_atom * act_chunk;
+    Real *act_atom = act + (int64_t)blockIdx.x * md.chunks_per_atom * act_chunk;
+    const Real *P = params_of<Real>(md);
 
     for (int tj = 0; tj < md.ntypes; ++tj) {
         const int cnt = nnei[(int64_t)i * md.ntypes + tj];
         if (cnt == 0) continue;
         __syncthreads();
-        const double *net = md.p + md.emb_base + (int64_t)(ti * md.ntypes + tj) * md.emb.size;
+        const Real *net = P + md.emb_base + (int64_t)(ti * md.ntypes + tj) * md.emb.size;
         for (int q = tid; q < md.emb.size; q += NT) sW[q] = net[q];
         for (int c0 = 0; c0 < cnt; c0 += 32) {
             if (g == 0) {
@@ -121,32 +146,32 @@ __global__ void __launch_bounds__(S::NT) k_embed_fwd64(ModelDev md, BoxDev bx, c
                     env_row(d, r, md.rcs, md.rcut, R, J);
                 }
 #pragma unroll
-                for (int c = 0; c < 4; ++c) sR[n * 4 + c] = R[c];
+                for (int c = 0; c < 4; ++c) sR[n * 4 + c] = (Real)R[c];
             }
             __syncthreads();
-            double *ca = act_atom + (int64_t)(md.chunk_off[tj] + c0 / 32) * act_chunk;
+            Real *ca = act_atom + (int64_t)(md.chunk_off[tj] + c0 / 32) * act_chunk;
             // layer 0: the input is the scalar s = R[0]
             {
                 constexpr int NO = (S::E0 + G - 1) / G;
-                const double s = sR[n * 4];
-                const double *W0 = sW + md.emb.W[0], *b0 = sW + md.emb.b[0];
+                const Real s = sR[n * 4];
+                const Real *W0 = sW + md.emb.W[0], *b0 = sW + md.emb.b[0];
 #pragma unroll
                 for (int u = 0; u < NO; ++u) {
                     const int o = g + G * u;
                     if (S::E0 % G == 0 || o < S::E0) {
-                        const double t = tanh(b0[o] + s * W0[o]);
-                        const double y = ((S::E0 == 1 || S::E0 == 2) ? s : 0.0) + t;
+                        const Real t = act_tanh(b0[o] + s * W0[o]);
+                        const Real y = ((S::E0 == 1 || S::E0 == 2) ? s : Real(0)) + t;
                         sA[o * 32 + n] = y;
                         ca[o * 32 + n] = t;
                     }
                 }
             }
             __syncthreads();
-            emb_layer_fwd<G, S::E0, S::E1>(sW + md.emb.W[1], sW + md.emb.b[1], sA, sB, ca + S::E0 * 32, nullptr,
-                                           g, n);
+            emb_layer_fwd<G, S::E0, S::E1, Real>(sW + md.emb.W[1], sW + md.emb.b[1], sA, sB, ca + S::E0 * 32,
+                                                 nullptr, g, n);
             __syncthreads();
-            emb_layer_fwd<G, S::E1, S::E2>(sW + md.emb.W[2], sW + md.emb.b[2], sB, sA,
-                                           ca + (S::E0 + S::E1) * 32, ca + (S::E0 + S::E1 + S::E2) * 32, g, n);
+            emb_layer_fwd<G, S::E1, S::E2, Real>(sW + md.emb.W[2], sW + md.emb.b[2], sB, sA,
+                                                 ca + (S::E0 + S::E1) * 32, ca + (S::E0 + S::E1 + S::E2) * 32, g, n);
             __syncthreads();
             // T[m][c] += sum_n G[m][n] R[n][c]
 #pragma unroll
@@ -154,7 +179,7 @@ __global__ void __launch_bounds__(S::NT) k_embed_fwd64(ModelDev md, BoxDev bx, c
                 const int q = tid + u * NT;
                 if (q < 4 * S::E2) {
                     const int m = q >> 2, c = q & 3;
-                    double a = 0.0;
+                    Real a = Real(0);
 #pragma unroll 8
                     for (int nn = 0; nn < 32; ++nn) a += sA[m * 32 + nn] * sR[nn * 4 + c];
                     tacc[u] += a;
@@ -167,7 +192,7 @@ __global__ void __launch_bounds__(S::NT) k_embed_fwd64(ModelDev md, BoxDev bx, c
     for (int u = 0; u < S::KT; ++u) {
         const int q = tid + u * NT;
         if (q < 4 * S::E2) {
-            const double t = tacc[u] * md.inv_nsel;
+            const Real t = tacc[u] * (Real)md.inv_nsel;
             sT[q] = t;
             T_out[(int64_t)blockIdx.x * 4 * S::E2 + q] = t;
         }
@@ -176,7 +201,7 @@ __global__ void __launch_bounds__(S::NT) k_embed_fwd64(ModelDev md, BoxDev bx, c
     const int nd = S::E2 * md.m2;
     for (int q = tid; q < nd; q += NT) {
         const int a = q / md.m2, b = q - a * md.m2;
-        double v = sT[4 * a] * sT[4 * b] + sT[4 * a + 1] * sT[4 * b + 1];
+        Real v = sT[4 * a] * sT[4 * b] + sT[4 * a + 1] * sT[4 * b + 1];
         v += sT[4 * a + 2] * sT[4 * b + 2] + sT[4 * a + 3] * sT[4 * b + 3];
         D_out[(int64_t)blockIdx.x * nd + q] = v;
     }
@@ -184,11 +209,13 @@ __global__ void __launch_bounds__(S::NT) k_embed_fwd64(ModelDev md, BoxDev bx, c
 
 // Fitting net of center type ti on A atoms (positions pos_begin + A*blockIdx.x
 // of the type-sorted order): E_i forward, dE/dD backward.
-__global__ void __launch_bounds__(256) k_fit64(ModelDev md, int ti, const int32_t *__restrict__ order, int64_t p0,
-                                              int64_t pos_begin, int64_t count, const double *__restrict__ D,
-                                              double *__restrict__ dD, double *__restrict__ E_atom)
+template <typename Real>
+__global__ void __launch_bounds__(256) k_fit(ModelDev md, int ti, const int32_t *__restrict__ order, int64_t p0,
+                                            int64_t pos_begin, int64_t count, const Real *__restrict__ D,
+                                            Real *__restrict__ dD, double *__restrict__ E_atom)
 {
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real *smem = reinterpret_cast<Real *>(smem_raw);
     constexpr int A = kFitAtoms;
     const int tid = threadIdx.x, nthreads = blockDim.x;
     const int nd = md.desc_dim;
@@ -196,41 +223,41 @@ __global__ void __launch_bounds__(256) k_fit64(ModelDev md, int ti, const int32_
     for (int k = 0; k < md.n_fit; ++k) wmax = max(wmax, md.fit.wout[k]);
     int fsum = 0;
     for (int k = 0; k < md.n_fit; ++k) fsum += md.fit.wout[k];
-    double *sX = smem;                                   // [A][nd], later dy/dz buffers
-    double *sT = sX + max(A * nd, 3 * A * wmax);         // [A][fsum] tanh values
-    double *sY = sT + A * fsum;                          // [A][fsum] layer outputs
+    Real *sX = smem;                                     // [A][nd], later dy/dz buffers
+    Real *sT = sX + max(A * nd, 3 * A * wmax);           // [A][fsum] tanh values
+    Real *sY = sT + A * fsum;                            // [A][fsum] layer outputs
     const int64_t first = pos_begin + (int64_t)blockIdx.x * A;
     const int na = (int)min((int64_t)A, pos_begin + count - first);
-    const double *net = md.p + md.fit_base + (int64_t)ti * md.fit.size;
-    const double *netT = md.pT + md.fit_base + (int64_t)ti * md.fit.size;
+    const Real *net = params_of<Real>(md) + md.fit_base + (int64_t)ti * md.fit.size;
+    const Real *netT = paramsT_of<Real>(md) + md.fit_base + (int64_t)ti * md.fit.size;
 
     for (int q = tid; q < A * nd; q += nthreads) {
         int a = q / nd;
-        sX[q] = a < na ? D[(first + a - p0) * nd + (q - a * nd)] : 0.0;
+        sX[q] = a < na ? D[(first + a - p0) * nd + (q - a * nd)] : Real(0);
     }
     __syncthreads();
     // forward
-    const double *xin = sX;
+    const Real *xin = sX;
     int win = nd, off = 0;
     for (int k = 0; k < md.n_fit; ++k) {
         const int wout = md.fit.wout[k];
-        const double *W = net + md.fit.W[k];
-        const double *b = net + md.fit.b[k];
+        const Real *W = net + md.fit.W[k];
+        const Real *b = net + md.fit.b[k];
         for (int o = tid; o < wout; o += nthreads) {
-            double acc[A];
-            const double bo = __ldg(b + o);
+            Real acc[A];
+            const Real bo = __ldg(b + o);
 #pragma unroll
             for (int a = 0; a < A; ++a) acc[a] = bo;
 #pragma unroll 4
             for (int kk = 0; kk < win; ++kk) {
-                const double w = __ldg(W + (int64_t)kk * wout + o);
+                const Real w = __ldg(W + (int64_t)kk * wout + o);
 #pragma unroll
                 for (int a = 0; a < A; ++a) acc[a] += xin[a * win + kk] * w;
             }
 #pragma unroll
             for (int a = 0; a < A; ++a) {
-                double t = tanh(acc[a]);
-                double res = 0.0;
+                Real t = act_tanh(acc[a]);
+                Real res = Real(0);
                 if (wout == win) res = xin[a * win + o];
                 else if (wout == 2 * win) res = xin[a * win + (o % win)];
                 sT[a * fsum + off + o] = t;
@@ -238,9 +265,8 @@ __global__ void __launch_bounds__(256) k_fit64(ModelDev md, int ti, const int32_
             }
         }
         __syncthreads();
-        // the next layer reads [A][wout] rows of this layer's outputs; copy
-        // them into a dense buffer (the stored rows have stride fsum)
-        double *dense = sX + (k & 1) * A * wmax;
+        // the next layer reads dense [A][wout] rows of this layer's outputs
+        Real *dense = sX + (k & 1) * A * wmax;
         for (int q = tid; q < A * wout; q += nthreads) {
             int a = q / wout;
             dense[q] = sY[a * fsum + off + (q - a * wout)];
@@ -250,21 +276,21 @@ __global__ void __launch_bounds__(256) k_fit64(ModelDev md, int ti, const int32_
         win = wout;
         off += wout;
     }
-    // output layer: E = y . w_out + b_out (warp a handles atom a)
-    const double *Wout = net + md.fit.W[md.n_fit];
-    const double bout = net[md.fit.b[md.n_fit]];
+    // output layer: E = y . w_out + b_out (warp a handles atom a); E_i in FP64
+    const Real *Wout = net + md.fit.W[md.n_fit];
+    const Real bout = net[md.fit.b[md.n_fit]];
     {
         const int warp = tid >> 5, lane = tid & 31;
         for (int a = warp; a < A; a += nthreads / 32) {
-            double e = 0.0;
+            Real e = Real(0);
             for (int o = lane; o < win; o += 32) e += xin[a * win + o] * __ldg(Wout + o);
             for (int s = 16; s > 0; s >>= 1) e += __shfl_xor_sync(0xffffffffu, e, s);
-            if (lane == 0 && a < na) E_atom[order[first + a]] = e + bout;
+            if (lane == 0 && a < na) E_atom[order[first + a]] = (double)(e + bout);
         }
     }
     __syncthreads();
     // backward: dy = w_out for the last hidden layer
-    double *dy = sX, *dz = sX + A * wmax, *dyn = sX + 2 * A * wmax;
+    Real *dy = sX, *dz = sX + A * wmax, *dyn = sX + 2 * A * wmax;
     for (int q = tid; q < A * win; q += nthreads) dy[q] = __ldg(Wout + (q % win));
     __syncthreads();
     for (int k = md.n_fit - 1; k >= 0; --k) {
@@ -273,24 +299,24 @@ __global__ void __launch_bounds__(256) k_fit64(ModelDev md, int ti, const int32_
         off -= wout;
         for (int q = tid; q < A * wout; q += nthreads) {
             int a = q / wout, o = q - a * wout;
-            double t = sT[a * fsum + off + o];
-            dz[q] = dy[q] * (1.0 - t * t);
+            Real t = sT[a * fsum + off + o];
+            dz[q] = dy[q] * (Real(1) - t * t);
         }
         __syncthreads();
-        const double *WT = netT + md.fit.W[k];           // [wout][kin]
+        const Real *WT = netT + md.fit.W[k];             // [wout][kin]
         for (int kk = tid; kk < kin; kk += nthreads) {
-            double acc[A];
+            Real acc[A];
 #pragma unroll
-            for (int a = 0; a < A; ++a) acc[a] = 0.0;
+            for (int a = 0; a < A; ++a) acc[a] = Real(0);
 #pragma unroll 4
             for (int o = 0; o < wout; ++o) {
-                const double w = __ldg(WT + (int64_t)o * kin + kk);
+                const Real w = __ldg(WT + (int64_t)o * kin + kk);
 #pragma unroll
                 for (int a = 0; a < A; ++a) acc[a] += dz[a * wout + o] * w;
             }
 #pragma unroll
             for (int a = 0; a < A; ++a) {
-                double v = acc[a];
+                Real v = acc[a];
                 if (wout == kin) v += dy[a * wout + kk];
                 else if (wout == 2 * kin) v += dy[a * wout + kk] + dy[a * wout + kk + kin];
                 if (k == 0) {
@@ -301,17 +327,17 @@ __global__ void __launch_bounds__(256) k_fit64(ModelDev md, int ti, const int32_
             }
         }
         __syncthreads();
-        double *tmp = dy; dy = dyn; dyn = tmp;
+        Real *tmp = dy; dy = dyn; dyn = tmp;
     }
 }
 
 // Input gradient of one hidden embedding layer for a chunk: given dy of the
 // layer outputs (registers, channel o = g + G u) and the stored tanh values,
 // returns dx of the layer inputs in the same ownership pattern.
-template <int G, int WIN, int WOUT>
-__device__ __forceinline__ void emb_layer_bwd(const double *__restrict__ sWl, const double *__restrict__ act_t,
-                                              double *__restrict__ sdz, double *__restrict__ sdy,
-                                              const double (&dy)[(WOUT + G - 1) / G], double (&dx)[(WIN + G - 1) / G],
+template <int G, int WIN, int WOUT, typename Real>
+__device__ __forceinline__ void emb_layer_bwd(const Real *__restrict__ sWl, const Real *__restrict__ act_t,
+                                              Real *__restrict__ sdz, Real *__restrict__ sdy,
+                                              const Real (&dy)[(WOUT + G - 1) / G], Real (&dx)[(WIN + G - 1) / G],
                                               int g, int n)
 {
     constexpr int NO = (WOUT + G - 1) / G, NI = (WIN + G - 1) / G;
@@ -319,18 +345,18 @@ __device__ __forceinline__ void emb_layer_bwd(const double *__restrict__ sWl, co
     for (int u = 0; u < NO; ++u) {
         const int o = g + G * u;
         if (WOUT % G == 0 || o < WOUT) {
-            const double t = act_t[o * 32 + n];
-            sdz[o * 32 + n] = dy[u] * (1.0 - t * t);
+            const Real t = act_t[o * 32 + n];
+            sdz[o * 32 + n] = dy[u] * (Real(1) - t * t);
             sdy[o * 32 + n] = dy[u];
         }
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < NI; ++u) dx[u] = 0.0;
+    for (int u = 0; u < NI; ++u) dx[u] = Real(0);
 #pragma unroll 5
     for (int o = 0; o < WOUT; ++o) {
-        const double z = sdz[o * 32 + n];
-        const double *Wc = sWl + g * WOUT + o;
+        const Real z = sdz[o * 32 + n];
+        const Real *Wc = sWl + g * WOUT + o;
 #pragma unroll
         for (int u = 0; u < NI; ++u)
             if (WIN % G == 0 || g + G * u < WIN) dx[u] += z * Wc[G * u * WOUT];
@@ -346,33 +372,34 @@ __device__ __forceinline__ void emb_layer_bwd(const double *__restrict__ sWl, co
     __syncthreads();
 }
 
-template <class S>
-__global__ void __launch_bounds__(S::NT) k_embed_bwd64(ModelDev md, BoxDev bx, const int32_t *__restrict__ order,
-                                                      int64_t p0, const Pos4 *__restrict__ pos,
-                                                      const int32_t *__restrict__ nlist,
-                                                      const int32_t *__restrict__ nnei,
-                                                      const double *__restrict__ T_in, const double *__restrict__ dD_in,
-                                                      const double *__restrict__ act, double *__restrict__ force,
-                                                      double *__restrict__ atom_virial)
+template <class S, typename Real>
+__global__ void __launch_bounds__(S::NT) k_embed_bwd(ModelDev md, BoxDev bx, const int32_t *__restrict__ order,
+                                                    int64_t p0, const Pos4 *__restrict__ pos,
+                                                    const int32_t *__restrict__ nlist, const int32_t *__restrict__ nnei,
+                                                    const Real *__restrict__ T_in, const Real *__restrict__ dD_in,
+                                                    const Real *__restrict__ act, double *__restrict__ force,
+                                                    double *__restrict__ atom_virial)
 {
     constexpr int G = S::G, NT = S::NT;
-    extern __shared__ double smem[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x, n = tid & 31, g = tid >> 5;
     const int nq = 4 * S::E2, nd = S::E2 * md.m2;
-    double *sW = smem;
-    double *sdz = sW + md.emb.size;        // [WMAX][32]
-    double *sdy = sdz + S::WMAX * 32;      // [WMAX][32]
-    double *sR = sdy + S::WMAX * 32;       // [32][4]
-    double *sJ = sR + 32 * 4;              // [32][12]
-    double *sd = sJ + 32 * 12;             // [32][3]
-    double *sdR = sd + 32 * 3;             // [G][32][4]
-    double *sT = sdR + G * 32 * 4;         // [M1][4]
-    double *sdT = sT + nq;                 // [M1][4]
-    double *sdD = sdT + nq;                // [M1*M2]
+    // FP64 geometry first (8-byte aligned), then the Real buffers
+    double *sJ = reinterpret_cast<double *>(smem_raw);   // [32][12]
+    double *sd = sJ + 32 * 12;                           // [32][3]
+    Real *sW = reinterpret_cast<Real *>(sd + 32 * 3);
+    Real *sdz = sW + md.emb.size;          // [WMAX][32]
+    Real *sdy = sdz + S::WMAX * 32;        // [WMAX][32]
+    Real *sR = sdy + S::WMAX * 32;         // [32][4]
+    Real *sdR = sR + 32 * 4;               // [G][32][4]
+    Real *sT = sdR + G * 32 * 4;           // [M1][4]
+    Real *sdT = sT + nq;                   // [M1][4]
+    Real *sdD = sdT + nq;                  // [M1*M2]
     const int64_t p = p0 + blockIdx.x;
     const int i = order[p];
     const Pos4 pi = pos[i];
     const int ti = (int)pi.w;
+    const Real *P = params_of<Real>(md);
 
     for (int q = tid; q < nq; q += NT) sT[q] = T_in[(int64_t)blockIdx.x * nq + q];
     for (int q = tid; q < nd; q += NT) sdD[q] = dD_in[(int64_t)blockIdx.x * nd + q];
@@ -380,14 +407,14 @@ __global__ void __launch_bounds__(S::NT) k_embed_bwd64(ModelDev md, BoxDev bx, c
     // dE/dT[m][c] = sum_b dD[m][b] T[b][c] + [m < M2] sum_a dD[a][m] T[a][c], times 1/sum(sel)
     for (int q = tid; q < nq; q += NT) {
         const int m = q >> 2, c = q & 3;
-        double acc = 0.0;
+        Real acc = Real(0);
         for (int b = 0; b < md.m2; ++b) acc += sdD[m * md.m2 + b] * sT[b * 4 + c];
         if (m < md.m2)
             for (int a = 0; a < S::E2; ++a) acc += sdD[a * md.m2 + m] * sT[a * 4 + c];
-        sdT[q] = acc * md.inv_nsel;
+        sdT[q] = acc * (Real)md.inv_nsel;
     }
     constexpr int act_chunk = S::ACT * 32;
-    const double *act_atom = act + (int64_t)blockIdx.x * md.chunks_per_atom * act_chunk;
+    const Real *act_atom = act + (int64_t)blockIdx.x * md.chunks_per_atom * act_chunk;
     double fi[3] = {0.0, 0.0, 0.0};
     double vir[9];
 #pragma unroll
@@ -397,7 +424,7 @@ __global__ void __launch_bounds__(S::NT) k_embed_bwd64(ModelDev md, BoxDev bx, c
         const int cnt = nnei[(int64_t)i * md.ntypes + tj];
         if (cnt == 0) continue;
         __syncthreads();
-        const double *net = md.p + md.emb_base + (int64_t)(ti * md.ntypes + tj) * md.emb.size;
+        const Real *net = P + md.emb_base + (int64_t)(ti * md.ntypes + tj) * md.emb.size;
         for (int q = tid; q < md.emb.size; q += NT) sW[q] = net[q];
         for (int c0 = 0; c0 < cnt; c0 += 32) {
             int j = -1;
@@ -411,66 +438,68 @@ __global__ void __launch_bounds__(S::NT) k_embed_bwd64(ModelDev md, BoxDev bx, c
                     env_row(d, r, md.rcs, md.rcut, R, J);
                 }
 #pragma unroll
-                for (int c = 0; c < 4; ++c) sR[n * 4 + c] = R[c];
+                for (int c = 0; c < 4; ++c) sR[n * 4 + c] = (Real)R[c];
 #pragma unroll
                 for (int q = 0; q < 12; ++q) sJ[n * 12 + q] = J[q];
 #pragma unroll
                 for (int q = 0; q < 3; ++q) sd[n * 3 + q] = d[q];
             }
             __syncthreads();
-            const double *ca = act_atom + (int64_t)(md.chunk_off[tj] + c0 / 32) * act_chunk;
+            const Real *ca = act_atom + (int64_t)(md.chunk_off[tj] + c0 / 32) * act_chunk;
             // dE/dG_j for the owned channels and the partial dE/dR_j
             constexpr int N2 = (S::E2 + G - 1) / G, N1 = (S::E1 + G - 1) / G, N0 = (S::E0 + G - 1) / G;
-            double dy2[N2];
-            double dRp[4] = {0, 0, 0, 0};
-            const double R0 = sR[n * 4], R1 = sR[n * 4 + 1], R2 = sR[n * 4 + 2], R3 = sR[n * 4 + 3];
-            const double *cy = ca + (S::E0 + S::E1 + S::E2) * 32;
+            Real dy2[N2];
+            Real dRp[4] = {Real(0), Real(0), Real(0), Real(0)};
+            const Real R0 = sR[n * 4], R1 = sR[n * 4 + 1], R2 = sR[n * 4 + 2], R3 = sR[n * 4 + 3];
+            const Real *cy = ca + (S::E0 + S::E1 + S::E2) * 32;
 #pragma unroll
             for (int u = 0; u < N2; ++u) {
                 const int m = g + G * u;
                 if (S::E2 % G == 0 || m < S::E2) {
-                    const double *dt = sdT + 4 * m;
+                    const Real *dt = sdT + 4 * m;
                     dy2[u] = dt[0] * R0 + dt[1] * R1 + dt[2] * R2 + dt[3] * R3;
-                    const double y = cy[m * 32 + n];
+                    const Real y = cy[m * 32 + n];
                     dRp[0] += dt[0] * y;
                     dRp[1] += dt[1] * y;
                     dRp[2] += dt[2] * y;
                     dRp[3] += dt[3] * y;
                 } else {
-                    dy2[u] = 0.0;
+                    dy2[u] = Real(0);
                 }
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c) sdR[(g * 32 + n) * 4 + c] = dRp[c];
-            double dy1[N1], dy0[N0];
-            emb_layer_bwd<G, S::E1, S::E2>(sW + md.emb.W[2], ca + (S::E0 + S::E1) * 32, sdz, sdy, dy2, dy1, g, n);
-            emb_layer_bwd<G, S::E0, S::E1>(sW + md.emb.W[1], ca + S::E0 * 32, sdz, sdy, dy1, dy0, g, n);
+            Real dy1[N1], dy0[N0];
+            emb_layer_bwd<G, S::E1, S::E2, Real>(sW + md.emb.W[2], ca + (S::E0 + S::E1) * 32, sdz, sdy, dy2, dy1, g,
+                                                 n);
+            emb_layer_bwd<G, S::E0, S::E1, Real>(sW + md.emb.W[1], ca + S::E0 * 32, sdz, sdy, dy1, dy0, g, n);
             // layer 0 (input width 1): ds = sum_o dz_o W0[o] (+ skip when E0 is 1 or 2)
 #pragma unroll
             for (int u = 0; u < N0; ++u) {
                 const int o = g + G * u;
                 if (S::E0 % G == 0 || o < S::E0) {
-                    const double t = ca[o * 32 + n];
-                    sdz[o * 32 + n] = dy0[u] * (1.0 - t * t);
+                    const Real t = ca[o * 32 + n];
+                    sdz[o * 32 + n] = dy0[u] * (Real(1) - t * t);
                     sdy[o * 32 + n] = dy0[u];
                 }
             }
             __syncthreads();
             if (g == 0 && c0 + n < cnt) {
-                const double *W0 = sW + md.emb.W[0];
-                double ds = 0.0;
+                const Real *W0 = sW + md.emb.W[0];
+                Real ds = Real(0);
                 for (int o = 0; o < S::E0; ++o) ds += sdz[o * 32 + n] * W0[o];
                 if (S::E0 == 1) ds += sdy[n];
                 else if (S::E0 == 2) ds += sdy[n] + sdy[32 + n];
+                // from here on FP64: dE/dR_j, the Jacobian chain, forces and virial
                 double dR[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    double a = 0.0;
+                    Real a = Real(0);
 #pragma unroll
                     for (int gg = 0; gg < G; ++gg) a += sdR[(gg * 32 + n) * 4 + c];
-                    dR[c] = a;
+                    dR[c] = (double)a;
                 }
-                dR[0] += ds;
+                dR[0] += (double)ds;
                 const double *J = sJ + n * 12;
                 double gv[3];
 #pragma unroll
@@ -509,19 +538,21 @@ __global__ void __launch_bounds__(S::NT) k_embed_bwd64(ModelDev md, BoxDev bx, c
     }
 }
 
-template <class S>
+template <class S, typename Real>
 size_t embed_fwd_smem(const ModelDev &md)
 {
-    return sizeof(double) * ((size_t)md.emb.size + 2 * S::WMAX * 32 + 32 * 4 + 4 * S::E2);
+    return sizeof(Real) * ((size_t)md.emb.size + 2 * S::WMAX * 32 + 32 * 4 + 4 * S::E2);
 }
 
-template <class S>
+template <class S, typename Real>
 size_t embed_bwd_smem(const ModelDev &md)
 {
-    return sizeof(double) * ((size_t)md.emb.size + 2 * S::WMAX * 32 + 32 * (4 + 12 + 3) + S::G * 32 * 4 +
-                             8 * S::E2 + (size_t)S::E2 * md.m2);
+    return sizeof(double) * 32 * (12 + 3) +
+           sizeof(Real) * ((size_t)md.emb.size + 2 * S::WMAX * 32 + 32 * 4 + S::G * 32 * 4 + 8 * S::E2 +
+                           (size_t)S::E2 * md.m2);
 }
 
+template <typename Real>
 size_t fit_smem(const ModelDev &md)
 {
     int wmax = 0, fsum = 0;
@@ -530,24 +561,23 @@ size_t fit_smem(const ModelDev &md)
         fsum += md.fit.wout[k];
     }
     size_t a = (size_t)kFitAtoms * md.desc_dim, b = (size_t)3 * kFitAtoms * wmax;
-    return sizeof(double) * ((a > b ? a : b) + 2 * (size_t)kFitAtoms * fsum);
+    return sizeof(Real) * ((a > b ? a : b) + 2 * (size_t)kFitAtoms * fsum);
 }
 
-template <class S>
-dp_status launch_batch(dp_model *m, dp_nlist *nl, BoxDev bx, int64_t p0, int64_t nb, double *T, double *D,
-                       double *dD, double *act, double *E_atom, double *force, double *atom_virial,
-                       cudaStream_t st)
+template <class S, typename Real>
+dp_status launch_batch(dp_model *m, dp_nlist *nl, BoxDev bx, int64_t p0, int64_t nb, Real *T, Real *D, Real *dD,
+                       Real *act, double *E_atom, double *force, double *atom_virial, cudaStream_t st)
 {
     const ModelDev &md = m->dev;
-    size_t sf = embed_fwd_smem<S>(md), sb = embed_bwd_smem<S>(md), sfit = fit_smem(md);
-    DP_CUDA(cudaFuncSetAttribute(k_embed_fwd64<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
-    DP_CUDA(cudaFuncSetAttribute(k_embed_bwd64<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
-    DP_CUDA(cudaFuncSetAttribute(k_fit64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sfit));
+    size_t sf = embed_fwd_smem<S, Real>(md), sb = embed_bwd_smem<S, Real>(md), sfit = fit_smem<Real>(md);
+    DP_CUDA(cudaFuncSetAttribute(k_embed_fwd<S, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
+    DP_CUDA(cudaFuncSetAttribute(k_embed_bwd<S, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
+    DP_CUDA(cudaFuncSetAttribute(k_fit<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sfit));
     const Pos4 *pos = (const Pos4 *)nl->d_pos;
     {
         ProfScope ps(m->prof, PG_EMBED_FWD, 1, st);
-        k_embed_fwd64<S><<<(unsigned)nb, S::NT, sf, st>>>(md, bx, nl->d_order, p0, pos, nl->d_nlist, nl->d_nnei, T, D,
-                                                      act);
+        k_embed_fwd<S, Real><<<(unsigned)nb, S::NT, sf, st>>>(md, bx, nl->d_order, p0, pos, nl->d_nlist, nl->d_nnei,
+                                                              T, D, act);
     }
     DP_CUDA(cudaGetLastError());
     for (int t = 0; t < md.ntypes; ++t) {
@@ -557,13 +587,13 @@ dp_status launch_batch(dp_model *m, dp_nlist *nl, BoxDev bx, int64_t p0, int64_t
         if (e <= b) continue;
         unsigned tiles = (unsigned)((e - b + kFitAtoms - 1) / kFitAtoms);
         ProfScope ps(m->prof, PG_FIT, 1, st);
-        k_fit64<<<tiles, 256, sfit, st>>>(md, t, nl->d_order, p0, b, e - b, D, dD, E_atom);
+        k_fit<Real><<<tiles, 256, sfit, st>>>(md, t, nl->d_order, p0, b, e - b, D, dD, E_atom);
         DP_CUDA(cudaGetLastError());
     }
     {
         ProfScope ps(m->prof, PG_EMBED_BWD, 1, st);
-        k_embed_bwd64<S><<<(unsigned)nb, S::NT, sb, st>>>(md, bx, nl->d_order, p0, pos, nl->d_nlist, nl->d_nnei, T,
-                                                      dD, act, force, atom_virial);
+        k_embed_bwd<S, Real><<<(unsigned)nb, S::NT, sb, st>>>(md, bx, nl->d_order, p0, pos, nl->d_nlist, nl->d_nnei,
+                                                              T, dD, act, force, atom_virial);
     }
     DP_CUDA(cudaGetLastError());
     return DP_OK;
@@ -573,28 +603,20 @@ using ShapeWater = EmbShape<5, 25, 50, 100>;   // also copper: the (25, 50, 100)
 using ShapeStudent = EmbShape<4, 8, 16, 32>;
 using ShapePaper = EmbShape<4, 32, 64, 128>;   // the nets of the paper's production models (Sec. 5.1)
 
-}  // namespace
-
-// Embedding shapes compiled into the FP64 and FP32 kernels.
-bool embed_shape_supported(int n_embed, const int *e)
+template <typename Real>
+size_t bytes_per_atom(const ModelDev &md)
 {
-    if (n_embed != 3) return false;
-    return (e[0] == 25 && e[1] == 50 && e[2] == 100) || (e[0] == 8 && e[1] == 16 && e[2] == 32) ||
-           (e[0] == 32 && e[1] == 64 && e[2] == 128);
+    return sizeof(Real) * ((size_t)4 * md.m1 + 2 * (size_t)md.desc_dim +
+                           (size_t)md.chunks_per_atom * md.act_stride * 32);
 }
 
-size_t fp64_bytes_per_atom(const ModelDev &md)
-{
-    return sizeof(double) * ((size_t)4 * md.m1 + 2 * (size_t)md.desc_dim +
-                             (size_t)md.chunks_per_atom * md.act_stride * 32);
-}
-
-dp_status compute_fp64(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
+template <typename Real>
+dp_status compute_simt(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
                        double *d_virial, double *d_atom_virial, cudaStream_t st)
 {
     const ModelDev &md = m->dev;
     const int64_t n = nl->n;
-    const size_t per_atom = fp64_bytes_per_atom(md);
+    const size_t per_atom = bytes_per_atom<Real>(md);
     int64_t B = m->batch_atoms > 0 ? m->batch_atoms : n;
     if (B > n) B = n;
     if (B < 1) B = 1;
@@ -605,23 +627,50 @@ dp_status compute_fp64(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
         w += (bytes + 255) & ~(size_t)255;
         return p;
     };
-    double *T = (double *)carve(sizeof(double) * 4 * md.m1 * B);
-    double *D = (double *)carve(sizeof(double) * md.desc_dim * B);
-    double *dD = (double *)carve(sizeof(double) * md.desc_dim * B);
-    double *act = (double *)carve(sizeof(double) * (size_t)md.chunks_per_atom * md.act_stride * 32 * B);
+    Real *T = (Real *)carve(sizeof(Real) * 4 * md.m1 * B);
+    Real *D = (Real *)carve(sizeof(Real) * md.desc_dim * B);
+    Real *dD = (Real *)carve(sizeof(Real) * md.desc_dim * B);
+    Real *act = (Real *)carve(sizeof(Real) * (size_t)md.chunks_per_atom * md.act_stride * 32 * B);
     DP_CUDA(cudaMemsetAsync(d_force, 0, sizeof(double) * 3 * n, st));
     BoxDev bx = make_box(nl);
     const int *e = md.emb.wout;
     for (int64_t p0 = 0; p0 < n; p0 += B) {
         int64_t nb = n - p0 < B ? n - p0 : B;
         dp_status s;
-        if (e[0] == 25) s = launch_batch<ShapeWater>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, st);
-        else if (e[0] == 8) s = launch_batch<ShapeStudent>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, st);
-        else s = launch_batch<ShapePaper>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, st);
+        if (e[0] == 25)
+            s = launch_batch<ShapeWater, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, st);
+        else if (e[0] == 8)
+            s = launch_batch<ShapeStudent, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, st);
+        else
+            s = launch_batch<ShapePaper, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, st);
         if (s != DP_OK) return s;
     }
     ProfScope ps(m->prof, PG_REDUCE, 1, st);
     return reduce_energy_virial(d_atom_energy, d_atom_virial, n, d_energy, d_virial, st);
+}
+
+}  // namespace
+
+// Embedding shapes compiled into the SIMT and tensor-core kernels.
+bool embed_shape_supported(int n_embed, const int *e)
+{
+    if (n_embed != 3) return false;
+    return (e[0] == 25 && e[1] == 50 && e[2] == 100) || (e[0] == 8 && e[1] == 16 && e[2] == 32) ||
+           (e[0] == 32 && e[1] == 64 && e[2] == 128);
+}
+
+size_t fp64_bytes_per_atom(const ModelDev &md) { return bytes_per_atom<double>(md); }
+
+dp_status compute_fp64(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
+                       double *d_virial, double *d_atom_virial, cudaStream_t st)
+{
+    return compute_simt<double>(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+}
+
+dp_status compute_mix32(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
+                        double *d_virial, double *d_atom_virial, cudaStream_t st)
+{
+    return compute_simt<float>(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
 }
 
 }  // namespace dp

@@ -1,0 +1,59 @@
+"""Mixed-precision schemes (Sec. 4.1.3) against the FP64 oracle: stated error budgets.
+
+FP32 nets (MIX-32) are checked against the oracle with budgets derived from
+FP32 rounding (unit roundoff 6e-8, sums of up to 1600 terms, chains of
+five layers): relative energy error below 1e-5 and force RMSE below 1e-4
+of the RMS force.  The errors measured on the GPU are printed for the
+record.
+"""
+import numpy as np
+import pytest
+
+import dpsynth
+from gpu_common import rms, systems
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dp():
+    import paper_2005_00223_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+def _errors(got, ref):
+    E, Ei, F, W = got
+    Er, Eir, Fr, Wr = ref
+    return {
+        "dE_rel": abs(E - Er) / abs(Er),
+        "dEi_max_rel": float(np.abs(Ei - Eir).max() / np.abs(Eir).max()),
+        "F_rmse_rel": float(np.sqrt(((F - Fr) ** 2).sum(1).mean()) / rms(Fr)),
+        "F_rmse": float(np.sqrt(((F - Fr) ** 2).sum(1).mean())),
+        "W_rel": float(np.abs(W - Wr).max() / np.abs(Wr).max()),
+    }
+
+
+@pytest.mark.parametrize("name,cfg,coord,typ,box", systems(), ids=[s[0] for s in systems()])
+def test_mix32_error_budget(dp, orc, name, cfg, coord, typ, box):
+    m = dp.Model(cfg, 1, params=dpsynth.model_params(cfg, 1))
+    nl = dp.NeighborList(m, coord, typ, box)
+    got = nl.compute(coord, box, "mix32")
+    ref = orc.Model(cfg, m.params).compute(coord, typ, box)
+    err = _errors(got, ref)
+    print(name, "mix32", err)
+    assert err["dE_rel"] < 1e-5
+    assert err["dEi_max_rel"] < 1e-4
+    assert err["F_rmse_rel"] < 1e-4
+    assert err["W_rel"] < 1e-4
+
+
+def test_mix32_md_runs(dp):
+    cfg = dpsynth.copper_config()
+    coord, typ, box = dpsynth.copper_fcc(1, ncell=10)
+    mass = np.array([dpsynth.MASS["Cu"]])
+    vel = dpsynth.velocities(mass[typ], 300.0, 1)
+    m = dp.Model(cfg, 1)
+    st = dp.MDState(m, coord, vel, typ, mass, box, skin=2.0)
+    th = st.step(20, 1.0, "mix32", thermo_every=10)
+    assert np.isfinite(th).all()
