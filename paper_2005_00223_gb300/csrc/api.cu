@@ -120,6 +120,10 @@ dp_status compute_device(dp_model *m, dp_nlist *nl, const double *d_coord, dp_pr
         return compute_fp64(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
     case DP_MIX32:
         return compute_mix32(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+    case DP_MIX_BF16:
+        return compute_mix16(m, nl, 1, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+    case DP_MIX_FP16:
+        return compute_mix16(m, nl, 0, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
     default:
         set_error("precision %d is not built into this library", (int)prec);
         return DP_ERR_UNSUPPORTED;
@@ -227,7 +231,7 @@ static dp_status upload_params(dp_model *m)
     DP_CUDA(cudaMemcpyAsync(m->d_params32, p32.data(), b32, cudaMemcpyHostToDevice, m->stream));
     DP_CUDA(cudaMemcpyAsync(m->d_paramsT32, pT32.data(), b32, cudaMemcpyHostToDevice, m->stream));
     DP_CUDA(cudaStreamSynchronize(m->stream));
-    return DP_OK;
+    return pack_tc_weights(m);
 }
 
 dp_status dp_model_create(const dp_model_config *cfg, uint64_t seed, dp_model **out)
@@ -341,6 +345,8 @@ dp_status dp_model_create(const dp_model_config *cfg, uint64_t seed, dp_model **
     if (e == cudaSuccess) e = cudaMalloc((void **)&m->d_params32, sizeof(float) * m->nparams);
     if (e == cudaSuccess) e = cudaMalloc((void **)&m->d_paramsT32, sizeof(float) * m->nparams);
     if (e == cudaSuccess) e = cudaMalloc((void **)&m->d_flag, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&m->d_err, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMemset(m->d_err, 0, sizeof(int32_t) * 4);
     if (e != cudaSuccess) st = cuda_fail(e, "dp_model_create");
     if (st == DP_OK) {
         md.p = m->d_params;
@@ -401,6 +407,8 @@ void dp_model_destroy(dp_model *m)
     cudaFree(m->ws);
     cudaFree(m->d_aux);
     cudaFree(m->d_flag);
+    cudaFree(m->d_err);
+    cudaFree(m->d_tcw);
     if (m->own_stream) cudaStreamDestroy(m->own_stream);
     delete m->prof;
     delete m;
@@ -651,13 +659,19 @@ dp_status dp_compute(dp_model *m, dp_nlist *nl, const double *coord, const doubl
     DP_TRY(check_nonfinite(a.F, 3 * n, m->d_flag, st));
     DP_TRY(check_nonfinite(a.scal, 10, m->d_flag, st));
     double scal[10];
-    int32_t flag = 0;
+    int32_t flag = 0, derr = 0;
+    DP_CUDA(cudaMemcpyAsync(&derr, m->d_err, sizeof(derr), cudaMemcpyDeviceToHost, st));
     std::vector<double> F(3 * n), Ei(atom_energy ? n : 0);
     DP_CUDA(cudaMemcpyAsync(scal, a.scal, sizeof(scal), cudaMemcpyDeviceToHost, st));
     DP_CUDA(cudaMemcpyAsync(&flag, m->d_flag, sizeof(flag), cudaMemcpyDeviceToHost, st));
     if (n > 0) DP_CUDA(cudaMemcpyAsync(F.data(), a.F, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
     if (atom_energy && n > 0) DP_CUDA(cudaMemcpyAsync(Ei.data(), a.Ei, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
     DP_CUDA(cudaStreamSynchronize(st));
+    if (derr) {
+        cudaMemsetAsync(m->d_err, 0, sizeof(int32_t), st);
+        set_error("a bounded device wait gave up (tensor-core pipeline); results are invalid");
+        return DP_ERR_TIMEOUT;
+    }
     if (flag) { set_error("non-finite energy, virial or force"); return DP_ERR_NONFINITE; }
     *energy = scal[0];
     if (virial) memcpy(virial, scal + 1, 9 * sizeof(double));

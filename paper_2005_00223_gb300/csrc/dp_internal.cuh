@@ -80,6 +80,8 @@ enum ProfGroup {
     PG_MD,            // integrator kernels (kick, drift, displacement check)
     PG_THERMO,        // thermo rows
     PG_CHECK,         // non-finite scans
+    PG_CHUNKS,        // tensor-core work list
+    PG_DESC,          // descriptor D and dE/dT between the embedding passes
     PG_COUNT
 };
 
@@ -135,6 +137,9 @@ struct dp_model {
     double *d_aux = nullptr;
     int64_t aux_n = -1;
     int32_t *d_flag = nullptr;        // [4] non-finite flag and spare
+    int32_t *d_err = nullptr;         // [4] device error word (bounded waits that gave up)
+    unsigned char *d_tcw = nullptr;   // packed fp16 and bf16 embedding weights for the tensor cores
+    uint32_t tc_img_bytes = 0;
 };
 
 struct dp_nlist {
@@ -203,6 +208,11 @@ dp_status compute_device(dp_model *m, dp_nlist *nl, const double *d_coord, dp_pr
                          double *d_atom_energy, double *d_force, double *d_virial, double *d_atom_virial,
                          cudaStream_t st);
 dp_status check_box(const double box[9], double rcut, double L[3]);
+dp_status pack_tc_weights(dp_model *m);
+dp_status compute_mix16(dp_model *m, dp_nlist *nl, int bf16, double *d_energy, double *d_atom_energy,
+                        double *d_force, double *d_virial, double *d_atom_virial, cudaStream_t st);
+// FP32 fitting net over all atoms (type-sorted positions): D, dD [n][desc], E_i FP64.
+dp_status fit_f32(dp_model *m, dp_nlist *nl, const float *D, float *dD, double *d_atom_energy, cudaStream_t st);
 // Per-atom scratch of the model: E_i [n] at d_aux, W_i [9n] right after it.
 dp_status ensure_aux(dp_model *m, int64_t n);
 dp_status nlist_create_internal(const dp_model *m, int64_t n, const int32_t *type, const double box[9], double rcut,

@@ -255,12 +255,18 @@ dp_status dp_md_step(dp_model *m, dp_md_state *s, int64_t nsteps, double dt_fs, 
         DP_TRY(check_nonfinite(s->d_f, 3 * n, m->d_flag, st));
         DP_TRY(check_nonfinite(s->d_x, 3 * n, m->d_flag, st));
     }
-    int32_t flag = 0, flags[3];
+    int32_t flag = 0, flags[3], derr = 0;
     DP_CUDA(cudaMemcpyAsync(&flag, m->d_flag, sizeof(flag), cudaMemcpyDeviceToHost, st));
+    DP_CUDA(cudaMemcpyAsync(&derr, m->d_err, sizeof(derr), cudaMemcpyDeviceToHost, st));
     DP_CUDA(cudaMemcpyAsync(flags, nl->d_flags, sizeof(flags), cudaMemcpyDeviceToHost, st));
     std::vector<double> th(4 * rows);
     if (rows) DP_CUDA(cudaMemcpyAsync(th.data(), s->d_thermo, sizeof(double) * 4 * rows, cudaMemcpyDeviceToHost, st));
     DP_CUDA(cudaStreamSynchronize(st));
+    if (derr) {
+        cudaMemsetAsync(m->d_err, 0, sizeof(int32_t), st);
+        set_error("a bounded device wait gave up during MD (tensor-core pipeline); the trajectory is invalid");
+        return DP_ERR_TIMEOUT;
+    }
     if (flags[0] & kErrCapacity) {
         set_error("a candidate list rebuild exceeded its capacity of %d; the trajectory after it is invalid", nl->cap);
         return DP_ERR_CAPACITY;

@@ -71,7 +71,8 @@ ProfScope::~ProfScope()
 using namespace dp;
 
 static const char *kGroupNames[PG_COUNT] = {"nlist_build", "nlist_format", "pack", "embed_fwd", "fitting",
-                                             "embed_bwd", "reduce", "md_update", "thermo", "nonfinite_check"};
+                                             "embed_bwd", "reduce", "md_update", "thermo", "nonfinite_check",
+                                             "tc_worklist", "descriptor"};
 
 extern "C" {
 

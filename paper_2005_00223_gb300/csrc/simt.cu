@@ -661,6 +661,22 @@ bool embed_shape_supported(int n_embed, const int *e)
 
 size_t fp64_bytes_per_atom(const ModelDev &md) { return bytes_per_atom<double>(md); }
 
+dp_status fit_f32(dp_model *m, dp_nlist *nl, const float *D, float *dD, double *d_atom_energy, cudaStream_t st)
+{
+    const ModelDev &md = m->dev;
+    const size_t sfit = fit_smem<float>(md);
+    DP_CUDA(cudaFuncSetAttribute(k_fit<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sfit));
+    for (int t = 0; t < md.ntypes; ++t) {
+        const int64_t b = nl->type_off[t], cnt = nl->type_count[t];
+        if (cnt <= 0) continue;
+        unsigned tiles = (unsigned)((cnt + kFitAtoms - 1) / kFitAtoms);
+        ProfScope ps(m->prof, PG_FIT, 1, st);
+        k_fit<float><<<tiles, 256, sfit, st>>>(md, t, nl->d_order, 0, b, cnt, D, dD, d_atom_energy);
+        DP_CUDA(cudaGetLastError());
+    }
+    return DP_OK;
+}
+
 dp_status compute_fp64(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
                        double *d_virial, double *d_atom_virial, cudaStream_t st)
 {

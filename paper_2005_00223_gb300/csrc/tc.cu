@@ -1,0 +1,812 @@
+// MIX-16 scheme of Sec. 4.1.3 on the 5th-generation tensor cores (tcgen05):
+// embedding layers 2 and 3 and their input gradients run as M = 128 MMAs with
+// fp16 or bf16 operands in shared memory and FP32 accumulators in tensor
+// memory; the first embedding layer (K = 1, too small for the tensor cores),
+// tanh and its derivative run in FP32 on the CUDA cores, as the paper does.
+// Coordinates, minimum image, the environment row and its Jacobian, the
+// chain dE/dR -> dE/dd and the force / virial scatter stay FP64.
+//
+// Work unit: a tile of 128 neighbor rows = 4 chunks of 32 rows, one chunk per
+// warp; every chunk is up to 32 neighbors of one type of one atom, and the 4
+// chunks of a tile share the (center type, neighbor type) net.  Tiles are
+// listed per evaluation by k_chunk_build; persistent CTAs walk them.  Each
+// CTA keeps the packed weights of the current net in shared memory, loaded
+// by one bulk copy on the TMA engine.
+//
+// Per tile, forward (k_embed_fwd_tc):  env rows -> layer 1 (FP32) -> A2 ->
+//   MMA (A2 x W2) -> tanh / skip epilogue -> A3 -> MMA (A3 x W3) -> epilogue
+//   gives G -> contraction T_i += G^T R (FP32, per warp) -> atomics into T.
+// Backward (k_embed_bwd_tc) recomputes the forward (no activation storage),
+//   then dG = dT R, dR = dT^T G, dz3 -> MMA (dz3 x W3^T) -> dz2 -> MMA
+//   (dz2 x W2^T) -> ds -> g_ij = J^T dR -> FP64 force and virial atomics.
+// The descriptor D = T T<^T, the fitting net and dE/dT sit between the two.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "dp_internal.cuh"
+#include "geom.cuh"
+#include "tc_common.cuh"
+
+namespace dp {
+
+namespace {
+
+constexpr long kWaitLimit = 1L << 25;   // mbarrier polls (~1 s) before a kernel gives up
+constexpr int kTcThreads = 128;
+constexpr int kTmemCols = 256;
+
+template <int E0_, int E1_, int E2_>
+struct TcShape {
+    static constexpr int E0 = E0_, E1 = E1_, E2 = E2_;
+    static constexpr int K2 = (E0 + 15) / 16 * 16;   // layer-2 K (E0 padded)
+    static constexpr int N2 = (E1 + 15) / 16 * 16;   // layer-2 N, layer-3 K
+    static constexpr int N3 = (E2 + 15) / 16 * 16;   // layer-3 N
+    // packed weight image of one net (byte offsets; every part 16-byte aligned)
+    static constexpr uint32_t B2_OFF = 0;                              // W2^T [N2][K2]
+    static constexpr uint32_t B3_OFF = B2_OFF + N2 * K2 * 2;           // W3^T [N3][N2]
+    static constexpr uint32_t B3B_OFF = B3_OFF + N3 * N2 * 2;          // W3   [N2][N3]
+    static constexpr uint32_t B2B_OFF = B3B_OFF + N2 * N3 * 2;         // W2   [K2][N2]
+    static constexpr uint32_t VEC_OFF = B2B_OFF + K2 * N2 * 2;         // W1[K2], b1[K2], b2[N2], b3[N3] (FP32)
+    static constexpr uint32_t IMG = VEC_OFF + (2 * K2 + N2 + N3) * 4;
+    // shared memory after the image
+    static constexpr uint32_t A2_OFF = IMG;                            // [128][K2]
+    static constexpr uint32_t A3_OFF = A2_OFF + 128 * K2 * 2;          // [128][N2]
+    static constexpr uint32_t AB1_OFF = A3_OFF + 128 * N2 * 2;         // [128][N3] (backward)
+    static constexpr uint32_t X_OFF = AB1_OFF + 128 * N3 * 2;          // backward: dT per warp (FP32)
+    static constexpr uint32_t FX_OFF = AB1_OFF;                        // forward: G and R per warp (FP32)
+    static constexpr uint32_t FWD_SCRATCH = 4 * 32 * 17 * 4 + 4 * 32 * 4 * 4;
+    static constexpr uint32_t BWD_SCRATCH = 4 * 4 * E2 * 4;
+    // at most two CTAs per SM (each holds 256 TMEM columns of the SM's 512)
+    static constexpr uint32_t FWD_SMEM = FX_OFF + FWD_SCRATCH > 80 * 1024 ? FX_OFF + FWD_SCRATCH : 80 * 1024;
+    static constexpr uint32_t BWD_SMEM = X_OFF + BWD_SCRATCH > 80 * 1024 ? X_OFF + BWD_SCRATCH : 80 * 1024;
+    static_assert(N2 + N3 <= kTmemCols, "TMEM columns");
+};
+
+using TcWater = TcShape<25, 50, 100>;
+using TcStudent = TcShape<8, 16, 32>;
+using TcPaper = TcShape<32, 64, 128>;
+
+template <int BF>
+__device__ __forceinline__ uint32_t pack2(float a, float b)
+{
+    if (BF) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    } else {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+}
+
+// Writes 8 consecutive K values of one row into a K-major core-matrix tile.
+template <int BF>
+__device__ __forceinline__ void st_row8(unsigned char *tile, int row, int k0, int K, const float *v)
+{
+    uint4 q;
+    q.x = pack2<BF>(v[0], v[1]);
+    q.y = pack2<BF>(v[2], v[3]);
+    q.z = pack2<BF>(v[4], v[5]);
+    q.w = pack2<BF>(v[6], v[7]);
+    *reinterpret_cast<uint4 *>(tile + tc::kmaj_off(row, k0, K)) = q;
+}
+
+// Skip term of a hidden layer of widths win -> wout at output o (Fig. 1(e,f)).
+template <int WIN, int WOUT>
+__device__ __forceinline__ float skip_of(const float *x, int o)
+{
+    if (WOUT == WIN) return x[o];
+    if (WOUT == 2 * WIN) return x[o % WIN];
+    return 0.0f;
+}
+
+struct TileCtx {
+    int atom, tj, c0, net;
+};
+
+// Environment row of this thread's neighbor (FP64) plus layer 1 in FP32;
+// writes the layer-1 output row into A2.  Returns the FP32 row R.
+template <class S, int BF>
+__device__ __forceinline__ void rows_layer1(const ModelDev &md, const BoxDev &bx, const Pos4 *__restrict__ pos,
+                                            const int32_t *__restrict__ nlist, const int32_t *__restrict__ nnei,
+                                            const TileCtx &ch, int lane, int row, const float *vec,
+                                            unsigned char *A2, float Rf[4], float t1[S::E0], double d[3],
+                                            double J[12], int &j, bool &valid)
+{
+    double R[4] = {0.0, 0.0, 0.0, 0.0};
+    j = -1;
+    valid = false;
+#pragma unroll
+    for (int q = 0; q < 12; ++q) J[q] = 0.0;
+    d[0] = d[1] = d[2] = 0.0;
+    if (ch.atom >= 0 && ch.c0 + lane < nnei[(int64_t)ch.atom * md.ntypes + ch.tj]) {
+        j = nlist[(int64_t)ch.atom * md.nsel + md.sel_off[ch.tj] + ch.c0 + lane];
+        const Pos4 pi = pos[ch.atom];
+        double r = min_image_r(pi, pos[j], bx, d);
+        env_row(d, r, md.rcs, md.rcut, R, J);
+        valid = true;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) Rf[c] = (float)R[c];
+    const float *W1 = vec, *b1 = vec + S::K2;
+    const float s = Rf[0];
+    float buf[8];
+#pragma unroll
+    for (int k0 = 0; k0 < S::K2; k0 += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + u;
+            float v = 0.0f;
+            if (k < S::E0) {
+                v = tc::tanh_fast(fmaf(s, W1[k], b1[k]));
+                t1[k] = v;
+                if (S::E0 == 1 || S::E0 == 2) v += s;
+            }
+            buf[u] = v;
+        }
+        st_row8<BF>(A2, row, k0, S::K2, buf);
+    }
+}
+
+// Layer-2 epilogue: z2 from TMEM, y2 = skip(t1) + tanh(z2 + b2); writes A3.
+template <class S, int BF>
+__device__ __forceinline__ void epi_layer2(uint32_t taddr, const float *vec, const float t1[S::E0], float t2[S::E1],
+                                           unsigned char *A3, int row)
+{
+    const float *b2 = vec + 2 * S::K2;
+#pragma unroll
+    for (int c0 = 0; c0 < S::N2; c0 += 16) {
+        float z[16];
+        tc::tmem_ld16(taddr + c0, z);
+        tc::tmem_ld_wait();
+        float buf[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int k = c0 + u;
+            float v = 0.0f;
+            if (k < S::E1) {
+                const float t = tc::tanh_fast(z[u] + b2[k]);
+                t2[k] = t;
+                v = skip_of<S::E0, S::E1>(t1, k) + t;
+            }
+            buf[u] = v;
+        }
+        st_row8<BF>(A3, row, c0, S::N2, buf);
+        st_row8<BF>(A3, row, c0 + 8, S::N2, buf + 8);
+    }
+}
+
+__device__ __forceinline__ int4 load_chunk(const int4 *chunks, int64_t idx) { return chunks[idx]; }
+
+template <class S, int BF>
+__global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, BoxDev bx, const Pos4 *__restrict__ pos,
+                                                            const int32_t *__restrict__ nlist,
+                                                            const int32_t *__restrict__ nnei,
+                                                            const int4 *__restrict__ chunks,
+                                                            const int *__restrict__ ntiles_ptr,
+                                                            const unsigned char *__restrict__ wimg,
+                                                            float *__restrict__ T, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar_mma, mbar_w;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char *img = smem;
+    unsigned char *A2 = smem + S::A2_OFF;
+    unsigned char *A3 = smem + S::A3_OFF;
+    float *sG = reinterpret_cast<float *>(smem + S::FX_OFF) + warp * 32 * 17;
+    float *sR = reinterpret_cast<float *>(smem + S::FX_OFF) + 4 * 32 * 17 + warp * 32 * 4;
+    const float *vec = reinterpret_cast<const float *>(img + S::VEC_OFF);
+    if (tid == 0) {
+        tc::mbar_init(&mbar_mma, 1);
+        tc::mbar_init(&mbar_w, 1);
+        tc::mbar_init_fence();
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t id2 = tc::idesc_f16(128, S::N2, BF), id3 = tc::idesc_f16(128, S::N3, BF);
+    uint32_t ph_mma = 0, ph_w = 0;
+    int cur_net = -1;
+    const int ntiles = *ntiles_ptr;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int4 c4 = load_chunk(chunks, (int64_t)tile * 4 + warp);
+        const int net = load_chunk(chunks, (int64_t)tile * 4).w;
+        TileCtx ch{c4.x, c4.y, c4.z, c4.w};
+        if (net != cur_net) {
+            if (tid == 0) {
+                tc::mbar_expect_tx(&mbar_w, S::IMG);
+                tc::bulk_g2s(img, wimg + (size_t)net * S::IMG, S::IMG, &mbar_w);
+            }
+            bool ok = tc::mbar_wait(&mbar_w, ph_w, kWaitLimit);
+            ph_w ^= 1;
+            if (!__syncthreads_and(ok)) {
+                if (tid == 0) atomicOr(err, 1);
+                break;
+            }
+            cur_net = net;
+        }
+        float Rf[4], t1[S::E0], t2[S::E1];
+        double d[3], J[12];
+        int j;
+        bool valid;
+        rows_layer1<S, BF>(md, bx, pos, nlist, nnei, ch, lane, tid, vec, A2, Rf, t1, d, J, j, valid);
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            tc::mma_kloop(tmem, tc::smem_u32(A2), tc::smem_u32(img + S::B2_OFF), S::K2, id2);
+            tc::mma_commit(&mbar_mma);
+        }
+        bool ok = tc::mbar_wait(&mbar_mma, ph_mma, kWaitLimit);
+        ph_mma ^= 1;
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) atomicOr(err, 1);
+            break;
+        }
+        tc::fence_after_sync();
+        epi_layer2<S, BF>(taddr, vec, t1, t2, A3, tid);
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            tc::mma_kloop(tmem + S::N2, tc::smem_u32(A3), tc::smem_u32(img + S::B3_OFF), S::N2, id3);
+            tc::mma_commit(&mbar_mma);
+        }
+        ok = tc::mbar_wait(&mbar_mma, ph_mma, kWaitLimit);
+        ph_mma ^= 1;
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) atomicOr(err, 1);
+            break;
+        }
+        tc::fence_after_sync();
+        // layer-3 epilogue: G = skip(y2) + tanh(z3 + b3), 16 channels at a time,
+        // each block contracted at once: T[atom][m][c] += sum_rows G[row][m] R[row][c]
+        {
+            const float *b3 = vec + 2 * S::K2 + S::N2;
+            float y2[S::E1];
+#pragma unroll
+            for (int k = 0; k < S::E1; ++k) y2[k] = skip_of<S::E0, S::E1>(t1, k) + t2[k];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sR[lane * 4 + c] = Rf[c];
+            float *Ta = T + (int64_t)(ch.atom >= 0 ? ch.atom : 0) * 4 * S::E2;
+            const int mu = lane & 15, cp = (lane >> 4) * 2;
+#pragma unroll
+            for (int c0 = 0; c0 < S::N3; c0 += 16) {
+                float z[16];
+                tc::tmem_ld16(taddr + S::N2 + c0, z);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int m = c0 + u;
+                    sG[lane * 17 + u] = m < S::E2 ? skip_of<S::E1, S::E2>(y2, m) + tc::tanh_fast(z[u] + b3[m]) : 0.f;
+                }
+                __syncwarp();
+                float a0 = 0.f, a1 = 0.f;
+#pragma unroll 8
+                for (int r = 0; r < 32; ++r) {
+                    const float g = sG[r * 17 + mu];
+                    const float2 rr = *reinterpret_cast<const float2 *>(sR + r * 4 + cp);
+                    a0 = fmaf(g, rr.x, a0);
+                    a1 = fmaf(g, rr.y, a1);
+                }
+                if (ch.atom >= 0 && c0 + mu < S::E2) {
+                    atomicAdd(Ta + 4 * (c0 + mu) + cp, a0);
+                    atomicAdd(Ta + 4 * (c0 + mu) + cp + 1, a1);
+                }
+                __syncwarp();
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+template <class S, int BF>
+__global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, BoxDev bx, const Pos4 *__restrict__ pos,
+                                                            const int32_t *__restrict__ nlist,
+                                                            const int32_t *__restrict__ nnei,
+                                                            const int4 *__restrict__ chunks,
+                                                            const int *__restrict__ ntiles_ptr,
+                                                            const unsigned char *__restrict__ wimg,
+                                                            const float *__restrict__ dT, double *__restrict__ force,
+                                                            double *__restrict__ atom_virial, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar_mma, mbar_w;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char *img = smem;
+    unsigned char *A2 = smem + S::A2_OFF;
+    unsigned char *A3 = smem + S::A3_OFF;     // forward layer-3 input, then dz2
+    unsigned char *AB1 = smem + S::AB1_OFF;   // dz3
+    float *sdT = reinterpret_cast<float *>(smem + S::X_OFF) + warp * 4 * S::E2;
+    const float *vec = reinterpret_cast<const float *>(img + S::VEC_OFF);
+    if (tid == 0) {
+        tc::mbar_init(&mbar_mma, 1);
+        tc::mbar_init(&mbar_w, 1);
+        tc::mbar_init_fence();
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t id2 = tc::idesc_f16(128, S::N2, BF), id3 = tc::idesc_f16(128, S::N3, BF);
+    const uint32_t idb1 = tc::idesc_f16(128, S::N2, BF), idb2 = tc::idesc_f16(128, S::K2, BF);
+    uint32_t ph_mma = 0, ph_w = 0;
+    int cur_net = -1;
+    const int ntiles = *ntiles_ptr;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int4 c4 = load_chunk(chunks, (int64_t)tile * 4 + warp);
+        const int net = load_chunk(chunks, (int64_t)tile * 4).w;
+        TileCtx ch{c4.x, c4.y, c4.z, c4.w};
+        if (net != cur_net) {
+            if (tid == 0) {
+                tc::mbar_expect_tx(&mbar_w, S::IMG);
+                tc::bulk_g2s(img, wimg + (size_t)net * S::IMG, S::IMG, &mbar_w);
+            }
+            bool ok = tc::mbar_wait(&mbar_w, ph_w, kWaitLimit);
+            ph_w ^= 1;
+            if (!__syncthreads_and(ok)) {
+                if (tid == 0) atomicOr(err, 1);
+                break;
+            }
+            cur_net = net;
+        }
+        // dE/dT of this warp's atom (already scaled by 1/sum(sel))
+        for (int q = lane; q < 4 * S::E2; q += 32) sdT[q] = ch.atom >= 0 ? dT[(int64_t)ch.atom * 4 * S::E2 + q] : 0.f;
+        float Rf[4], t1[S::E0], t2[S::E1];
+        double d[3], J[12];
+        int j;
+        bool valid;
+        rows_layer1<S, BF>(md, bx, pos, nlist, nnei, ch, lane, tid, vec, A2, Rf, t1, d, J, j, valid);
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            tc::mma_kloop(tmem, tc::smem_u32(A2), tc::smem_u32(img + S::B2_OFF), S::K2, id2);
+            tc::mma_commit(&mbar_mma);
+        }
+        bool ok = tc::mbar_wait(&mbar_mma, ph_mma, kWaitLimit);
+        ph_mma ^= 1;
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) atomicOr(err, 1);
+            break;
+        }
+        tc::fence_after_sync();
+        epi_layer2<S, BF>(taddr, vec, t1, t2, A3, tid);
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            tc::mma_kloop(tmem + S::N2, tc::smem_u32(A3), tc::smem_u32(img + S::B3_OFF), S::N2, id3);
+            tc::mma_commit(&mbar_mma);
+        }
+        ok = tc::mbar_wait(&mbar_mma, ph_mma, kWaitLimit);
+        ph_mma ^= 1;
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) atomicOr(err, 1);
+            break;
+        }
+        tc::fence_after_sync();
+        // layer-3 epilogue fused with the start of the backward pass:
+        //   G = skip(y2) + t3,  dG = dT R,  dR += dT^T G,  dz3 = dG (1 - t3^2)
+        float dR[4] = {0.f, 0.f, 0.f, 0.f};
+        float res2[S::E1];
+#pragma unroll
+        for (int k = 0; k < S::E1; ++k) res2[k] = 0.f;
+        {
+            const float *b3 = vec + 2 * S::K2 + S::N2;
+            float y2[S::E1];
+#pragma unroll
+            for (int k = 0; k < S::E1; ++k) y2[k] = skip_of<S::E0, S::E1>(t1, k) + t2[k];
+#pragma unroll
+            for (int c0 = 0; c0 < S::N3; c0 += 16) {
+                float z[16];
+                tc::tmem_ld16(taddr + S::N2 + c0, z);
+                tc::tmem_ld_wait();
+                float buf[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int m = c0 + u;
+                    float v = 0.f;
+                    if (m < S::E2) {
+                        const float t = tc::tanh_fast(z[u] + b3[m]);
+                        const float G = skip_of<S::E1, S::E2>(y2, m) + t;
+                        const float4 dt = *reinterpret_cast<const float4 *>(sdT + 4 * m);
+                        dR[0] = fmaf(dt.x, G, dR[0]);
+                        dR[1] = fmaf(dt.y, G, dR[1]);
+                        dR[2] = fmaf(dt.z, G, dR[2]);
+                        dR[3] = fmaf(dt.w, G, dR[3]);
+                        const float dG = dt.x * Rf[0] + dt.y * Rf[1] + dt.z * Rf[2] + dt.w * Rf[3];
+                        v = dG * (1.f - t * t);
+                        if (S::E2 == S::E1) res2[m] += dG;
+                        else if (S::E2 == 2 * S::E1) res2[m % S::E1] += dG;
+                    }
+                    buf[u] = v;
+                }
+                st_row8<BF>(AB1, tid, c0, S::N3, buf);
+                st_row8<BF>(AB1, tid, c0 + 8, S::N3, buf + 8);
+            }
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            // dY2 = dz3 x W3^T: B rows are the outputs k of W3's input side (W3 [E1][E2] row-major)
+            tc::mma_kloop(tmem, tc::smem_u32(AB1), tc::smem_u32(img + S::B3B_OFF), S::N3, idb1);
+            tc::mma_commit(&mbar_mma);
+        }
+        ok = tc::mbar_wait(&mbar_mma, ph_mma, kWaitLimit);
+        ph_mma ^= 1;
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) atomicOr(err, 1);
+            break;
+        }
+        tc::fence_after_sync();
+        float res1[S::E0];
+#pragma unroll
+        for (int k = 0; k < S::E0; ++k) res1[k] = 0.f;
+#pragma unroll
+        for (int c0 = 0; c0 < S::N2; c0 += 16) {
+            float z[16];
+            tc::tmem_ld16(taddr + c0, z);
+            tc::tmem_ld_wait();
+            float buf[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int k = c0 + u;
+                float v = 0.f;
+                if (k < S::E1) {
+                    const float dy2 = z[u] + res2[k];
+                    v = dy2 * (1.f - t2[k] * t2[k]);
+                    if (S::E1 == S::E0) res1[k] += dy2;
+                    else if (S::E1 == 2 * S::E0) res1[k % S::E0] += dy2;
+                }
+                buf[u] = v;
+            }
+            st_row8<BF>(A3, tid, c0, S::N2, buf);
+            st_row8<BF>(A3, tid, c0 + 8, S::N2, buf + 8);
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            // dY1 = dz2 x W2^T
+            tc::mma_kloop(tmem + S::N2, tc::smem_u32(A3), tc::smem_u32(img + S::B2B_OFF), S::N2, idb2);
+            tc::mma_commit(&mbar_mma);
+        }
+        ok = tc::mbar_wait(&mbar_mma, ph_mma, kWaitLimit);
+        ph_mma ^= 1;
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) atomicOr(err, 1);
+            break;
+        }
+        tc::fence_after_sync();
+        float ds = 0.f;
+        {
+            const float *W1 = vec;
+#pragma unroll
+            for (int c0 = 0; c0 < S::K2; c0 += 16) {
+                float z[16];
+                tc::tmem_ld16(taddr + S::N2 + c0, z);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int k = c0 + u;
+                    if (k < S::E0) {
+                        const float dy1 = z[u] + res1[k];
+                        ds = fmaf(dy1 * (1.f - t1[k] * t1[k]), W1[k], ds);
+                        if (S::E0 == 1) ds += dy1;
+                        else if (S::E0 == 2) ds += dy1;
+                    }
+                }
+            }
+        }
+        // FP64 from here: dE/dR -> g = J^T dE/dR, forces and virial
+        double gv[3] = {0.0, 0.0, 0.0}, vir[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) vir[q] = 0.0;
+        if (valid) {
+            const double dR0 = (double)dR[0] + (double)ds, dR1 = dR[1], dR2 = dR[2], dR3 = dR[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) gv[k] = dR0 * J[k] + dR1 * J[3 + k] + dR2 * J[6 + k] + dR3 * J[9 + k];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) atomicAdd(&force[3 * (int64_t)j + k], -gv[k]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) vir[3 * a + b] = -d[a] * gv[b];
+        }
+        // the warp's rows all belong to one atom: reduce F_i and W_i over the warp
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            for (int s = 16; s > 0; s >>= 1) gv[k] += __shfl_xor_sync(0xffffffffu, gv[k], s);
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            for (int s = 16; s > 0; s >>= 1) vir[q] += __shfl_xor_sync(0xffffffffu, vir[q], s);
+        if (ch.atom >= 0) {
+            if (lane < 3) {
+                double v = lane == 0 ? gv[0] : (lane == 1 ? gv[1] : gv[2]);
+                atomicAdd(&force[3 * (int64_t)ch.atom + lane], v);
+            }
+            if (lane < 9) {
+                double v = 0.0;
+#pragma unroll
+                for (int q = 0; q < 9; ++q) v = (q == lane) ? vir[q] : v;
+                atomicAdd(&atom_virial[9 * (int64_t)ch.atom + lane], v);
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+}
+
+// Work list: for each (center type, neighbor type) group, the 32-neighbor
+// chunks of its atoms (type-sorted order), padded with empty chunks to a
+// multiple of 4 so that a tile never mixes nets.  One block; every thread
+// walks a contiguous run of atoms.  Entry = {atom, tj, first slot, net}.
+__global__ void __launch_bounds__(1024) k_chunk_build(ModelDev md, const int32_t *__restrict__ order,
+                                                     const int64_t *__restrict__ type_off,
+                                                     const int64_t *__restrict__ type_cnt,
+                                                     const int32_t *__restrict__ nnei, int4 *__restrict__ chunks,
+                                                     int *__restrict__ ntiles)
+{
+    __shared__ int part[1024];
+    const int t = threadIdx.x, nt = blockDim.x;
+    int base = 0;
+    for (int ti = 0; ti < md.ntypes; ++ti) {
+        const int64_t off = type_off[ti], cnt = type_cnt[ti];
+        const int64_t per = (cnt + nt - 1) / nt;
+        const int64_t b = off + t * per, e = min(off + cnt, b + per);
+        for (int tj = 0; tj < md.ntypes; ++tj) {
+            const int net = ti * md.ntypes + tj;
+            int s = 0;
+            for (int64_t p = b; p < e; ++p) s += (nnei[(int64_t)order[p] * md.ntypes + tj] + 31) >> 5;
+            part[t] = s;
+            __syncthreads();
+            for (int o = 1; o < nt; o <<= 1) {
+                int v = t >= o ? part[t - o] : 0;
+                __syncthreads();
+                part[t] += v;
+                __syncthreads();
+            }
+            int w = base + part[t] - s;
+            for (int64_t p = b; p < e; ++p) {
+                const int a = order[p];
+                const int nch = (nnei[(int64_t)a * md.ntypes + tj] + 31) >> 5;
+                for (int c = 0; c < nch; ++c) chunks[w++] = make_int4(a, tj, c * 32, net);
+            }
+            const int total = part[nt - 1];
+            __syncthreads();
+            if (t == 0)
+                for (int q = total; q % 4 != 0; ++q) chunks[base + q] = make_int4(-1, tj, 0, net);
+            base += (total + 3) / 4 * 4;
+            __syncthreads();
+        }
+    }
+    if (t == 0) *ntiles = base / 4;
+}
+
+// D[p] = T T<^T of atom order[p] (T scaled by 1/sum(sel)), flattened a*M2 + b.
+__global__ void k_desc_f32(ModelDev md, const int32_t *__restrict__ order, int64_t n, const float *__restrict__ T,
+                           float *__restrict__ D)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int nd = md.desc_dim;
+    if (q >= n * nd) return;
+    const int64_t p = q / nd;
+    const int r = (int)(q - p * nd), a = r / md.m2, b = r - a * md.m2;
+    const float *Ta = T + (int64_t)order[p] * 4 * md.m1;
+    const float s = (float)(md.inv_nsel * md.inv_nsel);
+    const float4 x = *reinterpret_cast<const float4 *>(Ta + 4 * a);
+    const float4 y = *reinterpret_cast<const float4 *>(Ta + 4 * b);
+    D[q] = (x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w) * s;
+}
+
+// dE/dT (times 1/sum(sel)) of atom order[p] from dE/dD: one thread per (m, c).
+__global__ void k_dT_f32(ModelDev md, const int32_t *__restrict__ order, int64_t n, const float *__restrict__ T,
+                         const float *__restrict__ dD, float *__restrict__ dT)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int nq = 4 * md.m1;
+    if (q >= n * nq) return;
+    const int64_t p = q / nq;
+    const int r = (int)(q - p * nq), m = r >> 2, c = r & 3;
+    const int a_id = order[p];
+    const float *Ta = T + (int64_t)a_id * nq;
+    const float *dDa = dD + p * md.desc_dim;
+    const float inv = (float)md.inv_nsel;
+    float acc = 0.f;
+    for (int b = 0; b < md.m2; ++b) acc = fmaf(dDa[m * md.m2 + b], Ta[4 * b + c], acc);
+    if (m < md.m2)
+        for (int a = 0; a < md.m1; ++a) acc = fmaf(dDa[a * md.m2 + m], Ta[4 * a + c], acc);
+    dT[(int64_t)a_id * nq + r] = acc * inv * inv;
+}
+
+template <class S>
+void pack_net(const double *p, const NetLayout &L, int bf16, unsigned char *out)
+{
+    memset(out, 0, S::IMG);
+    auto put = [&](uint32_t base, int r, int k, int K, float v) {
+        uint16_t h;
+        if (bf16) {
+            __nv_bfloat16 b = __float2bfloat16_rn(v);
+            memcpy(&h, &b, 2);
+        } else {
+            __half b = __float2half_rn(v);
+            memcpy(&h, &b, 2);
+        }
+        memcpy(out + base + tc::kmaj_off(r, k, K), &h, 2);
+    };
+    const double *W1 = p + L.W[0], *b1 = p + L.b[0];
+    const double *W2 = p + L.W[1], *b2 = p + L.b[1];
+    const double *W3 = p + L.W[2], *b3 = p + L.b[2];
+    for (int a = 0; a < S::E0; ++a)
+        for (int o = 0; o < S::E1; ++o) {
+            float w = (float)W2[a * S::E1 + o];
+            put(S::B2_OFF, o, a, S::K2, w);      // W2^T: row = output o, K = input a
+            put(S::B2B_OFF, a, o, S::N2, w);     // W2:   row = input a,  K = output o
+        }
+    for (int a = 0; a < S::E1; ++a)
+        for (int o = 0; o < S::E2; ++o) {
+            float w = (float)W3[a * S::E2 + o];
+            put(S::B3_OFF, o, a, S::N2, w);
+            put(S::B3B_OFF, a, o, S::N3, w);
+        }
+    float *vec = reinterpret_cast<float *>(out + S::VEC_OFF);
+    for (int k = 0; k < S::E0; ++k) {
+        vec[k] = (float)W1[k];
+        vec[S::K2 + k] = (float)b1[k];
+    }
+    for (int k = 0; k < S::E1; ++k) vec[2 * S::K2 + k] = (float)b2[k];
+    for (int k = 0; k < S::E2; ++k) vec[2 * S::K2 + S::N2 + k] = (float)b3[k];
+}
+
+template <class S>
+dp_status pack_all(dp_model *m)
+{
+    const ModelDev &md = m->dev;
+    const int nn = m->ntypes * m->ntypes;
+    std::vector<unsigned char> img((size_t)2 * nn * S::IMG);
+    for (int bf = 0; bf < 2; ++bf)
+        for (int q = 0; q < nn; ++q)
+            pack_net<S>(m->h_params.data() + md.emb_base + q * md.emb.size, md.emb, bf,
+                        img.data() + ((size_t)bf * nn + q) * S::IMG);
+    if (!m->d_tcw) DP_CUDA(cudaMalloc((void **)&m->d_tcw, img.size()));
+    DP_CUDA(cudaMemcpyAsync(m->d_tcw, img.data(), img.size(), cudaMemcpyHostToDevice, m->stream));
+    DP_CUDA(cudaStreamSynchronize(m->stream));
+    m->tc_img_bytes = S::IMG;
+    return DP_OK;
+}
+
+template <class S, int BF>
+dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
+                 double *d_virial, double *d_atom_virial, cudaStream_t st)
+{
+    const ModelDev &md = m->dev;
+    const int64_t n = nl->n;
+    const int nn = md.ntypes * md.ntypes;
+    const int64_t max_chunks = n * md.chunks_per_atom + 4 * nn + 4;
+    // workspace: T, dT [n][4 M1] f32; D, dD [n][desc] f32; chunks; counters; type tables
+    size_t need = 0;
+    auto sz = [&](size_t b) { need += (b + 255) & ~(size_t)255; };
+    sz(sizeof(float) * 4 * md.m1 * n);
+    sz(sizeof(float) * 4 * md.m1 * n);
+    sz(sizeof(float) * md.desc_dim * n);
+    sz(sizeof(float) * md.desc_dim * n);
+    sz(sizeof(int4) * max_chunks);
+    sz(sizeof(int) * 4);
+    sz(sizeof(int64_t) * 2 * kMaxTypes);
+    DP_TRY(ensure_workspace(m, need));
+    char *w = m->ws;
+    auto carve = [&](size_t bytes) {
+        char *p = w;
+        w += (bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    float *T = (float *)carve(sizeof(float) * 4 * md.m1 * n);
+    float *dT = (float *)carve(sizeof(float) * 4 * md.m1 * n);
+    float *D = (float *)carve(sizeof(float) * md.desc_dim * n);
+    float *dD = (float *)carve(sizeof(float) * md.desc_dim * n);
+    int4 *chunks = (int4 *)carve(sizeof(int4) * max_chunks);
+    int *cnt = (int *)carve(sizeof(int) * 4);
+    int64_t *ttab = (int64_t *)carve(sizeof(int64_t) * 2 * kMaxTypes);
+    int64_t htab[2 * kMaxTypes] = {0};
+    for (int t = 0; t < md.ntypes; ++t) {
+        htab[t] = nl->type_off[t];
+        htab[kMaxTypes + t] = nl->type_count[t];
+    }
+    DP_CUDA(cudaMemcpyAsync(ttab, htab, sizeof(htab), cudaMemcpyHostToDevice, st));
+    DP_CUDA(cudaMemsetAsync(T, 0, sizeof(float) * 4 * md.m1 * n, st));
+    DP_CUDA(cudaMemsetAsync(d_force, 0, sizeof(double) * 3 * n, st));
+    DP_CUDA(cudaMemsetAsync(d_atom_virial, 0, sizeof(double) * 9 * n, st));
+    const unsigned char *wimg = m->d_tcw + (size_t)BF * nn * S::IMG;
+    BoxDev bx = make_box(nl);
+    const Pos4 *pos = (const Pos4 *)nl->d_pos;
+    int nsm = 0;
+    DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
+    const unsigned grid = (unsigned)(2 * nsm);
+    {
+        ProfScope ps(m->prof, PG_CHUNKS, 1, st);
+        k_chunk_build<<<1, 1024, 0, st>>>(md, nl->d_order, ttab, ttab + kMaxTypes, nl->d_nnei, chunks, cnt);
+    }
+    DP_CUDA(cudaGetLastError());
+    DP_CUDA(cudaFuncSetAttribute(k_embed_fwd_tc<S, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::FWD_SMEM));
+    DP_CUDA(cudaFuncSetAttribute(k_embed_bwd_tc<S, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::BWD_SMEM));
+    {
+        ProfScope ps(m->prof, PG_EMBED_FWD, 1, st);
+        k_embed_fwd_tc<S, BF><<<grid, kTcThreads, S::FWD_SMEM, st>>>(md, bx, pos, nl->d_nlist, nl->d_nnei, chunks,
+                                                                     cnt, wimg, T, m->d_err);
+    }
+    DP_CUDA(cudaGetLastError());
+    const int64_t nd = (int64_t)md.desc_dim * n, nq = (int64_t)4 * md.m1 * n;
+    {
+        ProfScope ps(m->prof, PG_DESC, 1, st);
+        k_desc_f32<<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(md, nl->d_order, n, T, D);
+    }
+    DP_CUDA(cudaGetLastError());
+    DP_TRY(fit_f32(m, nl, D, dD, d_atom_energy, st));
+    {
+        ProfScope ps(m->prof, PG_DESC, 1, st);
+        k_dT_f32<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(md, nl->d_order, n, T, dD, dT);
+    }
+    DP_CUDA(cudaGetLastError());
+    {
+        ProfScope ps(m->prof, PG_EMBED_BWD, 1, st);
+        k_embed_bwd_tc<S, BF><<<grid, kTcThreads, S::BWD_SMEM, st>>>(md, bx, pos, nl->d_nlist, nl->d_nnei, chunks,
+                                                                     cnt, wimg, dT, d_force, d_atom_virial, m->d_err);
+    }
+    DP_CUDA(cudaGetLastError());
+    ProfScope ps(m->prof, PG_REDUCE, 1, st);
+    return reduce_energy_virial(d_atom_energy, d_atom_virial, n, d_energy, d_virial, st);
+}
+
+}  // namespace
+
+dp_status pack_tc_weights(dp_model *m)
+{
+    const int *e = m->dev.emb.wout;
+    if (e[0] == 25) return pack_all<TcWater>(m);
+    if (e[0] == 8) return pack_all<TcStudent>(m);
+    return pack_all<TcPaper>(m);
+}
+
+dp_status compute_mix16(dp_model *m, dp_nlist *nl, int bf16, double *d_energy, double *d_atom_energy,
+                        double *d_force, double *d_virial, double *d_atom_virial, cudaStream_t st)
+{
+    const int *e = m->dev.emb.wout;
+    if (e[0] == 25)
+        return bf16 ? run_tc<TcWater, 1>(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st)
+                    : run_tc<TcWater, 0>(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+    if (e[0] == 8)
+        return bf16 ? run_tc<TcStudent, 1>(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st)
+                    : run_tc<TcStudent, 0>(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+    return bf16 ? run_tc<TcPaper, 1>(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st)
+                : run_tc<TcPaper, 0>(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+}
+
+}  // namespace dp

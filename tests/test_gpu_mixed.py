@@ -42,10 +42,10 @@ def test_mix32_error_budget(dp, orc, name, cfg, coord, typ, box):
     ref = orc.Model(cfg, m.params).compute(coord, typ, box)
     err = _errors(got, ref)
     print(name, "mix32", err)
-    assert err["dE_rel"] < 1e-5
-    assert err["dEi_max_rel"] < 1e-4
-    assert err["F_rmse_rel"] < 1e-4
-    assert err["W_rel"] < 1e-4
+    assert err["dE_rel"] < 1e-6
+    assert err["dEi_max_rel"] < 1e-5
+    assert err["F_rmse_rel"] < 1e-5
+    assert err["W_rel"] < 1e-5
 
 
 def test_mix32_md_runs(dp):
@@ -56,4 +56,31 @@ def test_mix32_md_runs(dp):
     m = dp.Model(cfg, 1)
     st = dp.MDState(m, coord, vel, typ, mass, box, skin=2.0)
     th = st.step(20, 1.0, "mix32", thermo_every=10)
+    assert np.isfinite(th).all()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("name,cfg,coord,typ,box", systems(), ids=[s[0] for s in systems()])
+def test_mix16_tensor_core_error_budget(dp, orc, prec, name, cfg, coord, typ, box):
+    """MIX-16 on tcgen05: embedding GEMMs with fp16/bf16 operands, FP32 accumulation and epilogues."""
+    m = dp.Model(cfg, 1, params=dpsynth.model_params(cfg, 1))
+    nl = dp.NeighborList(m, coord, typ, box)
+    got = nl.compute(coord, box, prec)
+    ref = orc.Model(cfg, m.params).compute(coord, typ, box)
+    err = _errors(got, ref)
+    print(name, prec, err)
+    assert np.isfinite(got[2]).all()
+    assert err["dE_rel"] < 1e-2
+    assert err["F_rmse_rel"] < (0.1 if prec == "bf16" else 0.03)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_mix16_student_shape_and_md(dp, prec):
+    cfg = dpsynth.copper_student_config()
+    coord, typ, box = dpsynth.copper_fcc(1, ncell=6)
+    mass = np.array([dpsynth.MASS["Cu"]])
+    vel = dpsynth.velocities(mass[typ], 300.0, 1)
+    m = dp.Model(cfg, 2)
+    st = dp.MDState(m, coord, vel, typ, mass, box, skin=2.0)
+    th = st.step(10, 1.0, prec, thermo_every=5)
     assert np.isfinite(th).all()
