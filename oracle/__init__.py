@@ -71,6 +71,8 @@ def _load():
             lib.orc_md_nve.argtypes = [P, C.c_int64, P, P, P, P, P, C.c_int64, C.c_double, C.c_int32,
                                        P, C.c_int]
             lib.orc_md_nve.restype = C.c_int
+            lib.orc_jvp_grad.argtypes = [P, C.c_int64, P, P, P, P, P, C.c_double, C.c_double, P, P, P, C.c_int]
+            lib.orc_jvp_grad.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -165,6 +167,48 @@ class Model:
         _check(_load().orc_atom(self.ref, int(i), _p(row), _p(coord), _p(typ), _p(box), _p(Ei), _p(g),
                                 _p(D)), "orc_atom")
         return float(Ei[0]), g, D
+
+    # -- parameter gradient of the force-matching loss ---------------------
+    def jvp_grad(self, coord, typ, box, v, alpha: float, beta: float, nlist=None, nthreads: int = 0):
+        """(E, Edot, grad) with Edot = sum_k v_k . dE/dr_k and grad = d(alpha E + beta Edot)/dtheta."""
+        coord = np.ascontiguousarray(coord, dtype=np.float64)
+        typ = np.ascontiguousarray(typ, dtype=np.int32)
+        box = np.ascontiguousarray(box, dtype=np.float64).reshape(3, 3)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        if nlist is None:
+            nlist = self.nlist(coord, typ, box)[0]
+        nlist = np.ascontiguousarray(nlist, dtype=np.int32)
+        E, Ed = np.zeros(1), np.zeros(1)
+        grad = np.zeros(self.params.size)
+        _check(_load().orc_jvp_grad(self.ref, coord.shape[0], _p(coord), _p(typ), _p(box), _p(nlist), _p(v),
+                                    float(alpha), float(beta), _p(E), _p(Ed), _p(grad), int(nthreads)),
+               "orc_jvp_grad")
+        return float(E[0]), float(Ed[0]), grad
+
+    def force_loss(self, frames, p_e: float = 0.0, p_f: float = 1.0):
+        """L = sum over frames of p_e (dE/N)^2 + p_f/(3N) sum_k |F_k - F_ref,k|^2.
+
+        frames: list of (coord, type, box, E_ref, F_ref)."""
+        total = 0.0
+        for coord, typ, box, E_ref, F_ref in frames:
+            E, _, F, _ = self.compute(coord, typ, box)
+            n = len(typ)
+            total += p_e * ((E - E_ref) / n) ** 2 + p_f * float(((F - F_ref) ** 2).sum()) / (3 * n)
+        return total
+
+    def force_loss_grad(self, frames, p_e: float = 0.0, p_f: float = 1.0):
+        """(L, dL/dtheta): dL/dtheta = 2 p_e dE/N^2 dE/dtheta - 2 p_f/(3N) dEdot/dtheta, v = F - F_ref."""
+        total = 0.0
+        grad = np.zeros(self.params.size)
+        for coord, typ, box, E_ref, F_ref in frames:
+            E, _, F, _ = self.compute(coord, typ, box)
+            n = len(typ)
+            v = F - F_ref
+            total += p_e * ((E - E_ref) / n) ** 2 + p_f * float((v ** 2).sum()) / (3 * n)
+            _, _, g = self.jvp_grad(coord, typ, box, v, alpha=2 * p_e * (E - E_ref) / n ** 2,
+                                    beta=-2 * p_f / (3 * n))
+            grad += g
+        return total, grad
 
     # -- velocity-Verlet NVE (Sec. 5.1) ------------------------------------
     def md_nve(self, coord, vel, typ, mass_by_type, box, nsteps: int, dt: float, thermo_every: int,

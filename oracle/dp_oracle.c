@@ -737,3 +737,326 @@ int orc_md_nve(const orc_model *m, int64_t n, double *coord, double *vel, const 
     free(F);
     return st;
 }
+
+/* ------------------------- parameter gradient of alpha E + beta Edot ------- */
+/*
+ * Edot = sum_k v_k . dE/dr_k is the directional derivative of E along the
+ * displacement field v (forward-mode tangent): per atom i, with
+ * dd_ij = v_j - v_i, the tangent of the environment row is J dd_ij, and every
+ * layer carries (x, x') with z' = x' W, t' = (1 - t^2) z', y' = skip(x') + t'.
+ * The force-matching loss L = p_e (dE/N)^2 + p_f/(3N) sum |F - F_ref|^2 has
+ * dL/dtheta = 2 p_e dE/N^2 dE/dtheta - 2 p_f/(3N) dEdot/dtheta with
+ * v = F - F_ref held fixed (F = -grad E), so the gradient of alpha E +
+ * beta Edot over theta is the one primitive needed.  It is computed by
+ * reverse mode through the primal and tangent programs; per layer, with
+ * adjoints (y_bar, y'_bar):
+ *   z'_bar = y'_bar (1 - t^2);  t_bar = y_bar + y'_bar z' (-2 t);
+ *   z_bar = t_bar (1 - t^2);
+ *   W_bar += x^T z_bar + x'^T z'_bar;  b_bar += z_bar;
+ *   x_bar = z_bar W^T + skip^T(y_bar);  x'_bar = z'_bar W^T + skip^T(y'_bar).
+ */
+
+typedef struct {
+    int nin, nout;
+    const double *W, *b;
+    double *Wg, *bg;
+} orc_layer;
+
+/* primal + tangent forward of one tanh layer; stores t and z' */
+static void layer_fwd_tan(const orc_layer *L, const double *x, const double *xd, double *t, double *zd, double *y,
+                          double *yd)
+{
+    for (int o = 0; o < L->nout; ++o) {
+        double z = L->b[o], zdo = 0.0;
+        for (int k = 0; k < L->nin; ++k) {
+            z += x[k] * L->W[(int64_t)k * L->nout + o];
+            zdo += xd[k] * L->W[(int64_t)k * L->nout + o];
+        }
+        t[o] = tanh(z);
+        zd[o] = zdo;
+    }
+    for (int o = 0; o < L->nout; ++o) {
+        double td = (1.0 - t[o] * t[o]) * zd[o];
+        double sx = 0.0, sxd = 0.0;
+        if (L->nout == L->nin) { sx = x[o]; sxd = xd[o]; }
+        else if (L->nout == 2 * L->nin) { sx = x[o % L->nin]; sxd = xd[o % L->nin]; }
+        y[o] = sx + t[o];
+        yd[o] = sxd + td;
+    }
+}
+
+/* reverse of layer_fwd_tan: accumulates W_bar, b_bar; writes x_bar, x'_bar */
+static void layer_rev_tan(const orc_layer *L, const double *x, const double *xd, const double *t, const double *zd,
+                          const double *yb, const double *ydb, double *xb, double *xdb, double *zb, double *zdb)
+{
+    for (int o = 0; o < L->nout; ++o) {
+        double g = 1.0 - t[o] * t[o];
+        zdb[o] = ydb[o] * g;
+        double tb = yb[o] + ydb[o] * zd[o] * (-2.0 * t[o]);
+        zb[o] = tb * g;
+        L->bg[o] += zb[o];
+    }
+    for (int k = 0; k < L->nin; ++k)
+        for (int o = 0; o < L->nout; ++o)
+            L->Wg[(int64_t)k * L->nout + o] += x[k] * zb[o] + xd[k] * zdb[o];
+    if (!xb) return;
+    for (int k = 0; k < L->nin; ++k) {
+        double a = 0.0, ad = 0.0;
+        for (int o = 0; o < L->nout; ++o) {
+            a += zb[o] * L->W[(int64_t)k * L->nout + o];
+            ad += zdb[o] * L->W[(int64_t)k * L->nout + o];
+        }
+        if (L->nout == L->nin) { a += yb[k]; ad += ydb[k]; }
+        else if (L->nout == 2 * L->nin) { a += yb[k] + yb[k + L->nin]; ad += ydb[k] + ydb[k + L->nin]; }
+        xb[k] = a;
+        xdb[k] = ad;
+    }
+}
+
+/* formula(Xb, Y)[a][c] = sum_b Xb[a][b] Y[b][c] + [a < M2] sum_a' Xb[a'][a] Y[a'][c] */
+static void desc_adjoint(int m1, int m2, const double *Xb, const double *Y, double *out, int accumulate)
+{
+    for (int a = 0; a < m1; ++a)
+        for (int c = 0; c < 4; ++c) {
+            double acc = 0.0;
+            for (int b = 0; b < m2; ++b) acc += Xb[a * m2 + b] * Y[4 * b + c];
+            if (a < m2)
+                for (int a2 = 0; a2 < m1; ++a2) acc += Xb[a2 * m2 + a] * Y[4 * a2 + c];
+            out[4 * a + c] = accumulate ? out[4 * a + c] + acc : acc;
+        }
+}
+
+static void make_layers(const orc_model *m, const double *net, double *gnet, int nin, int nlayers, const int32_t *w,
+                        orc_layer *out)
+{
+    int win = nin;
+    int64_t off = 0;
+    for (int k = 0; k < nlayers; ++k) {
+        out[k].nin = win;
+        out[k].nout = w[k];
+        out[k].W = net + off;
+        out[k].Wg = gnet + off;
+        off += (int64_t)win * w[k];
+        out[k].b = net + off;
+        out[k].bg = gnet + off;
+        off += w[k];
+        win = w[k];
+    }
+    (void)m;
+}
+
+/* One atom: adds d(alpha E_i + beta Edot_i)/dtheta into g (flat parameter order);
+ * returns E_i and Edot_i. */
+static int atom_jvp_grad(const orc_model *m, int64_t i, const int32_t *row, const double *coord, const int32_t *type,
+                         const double *v, const double L[3], const double invL[3], double alpha, double beta,
+                         double *Ei, double *Edi, double *g)
+{
+    const int nsel = nsel_total(m), m1 = m->embed[m->n_embed - 1], m2 = m->m2, ne = m->n_embed, nf = m->n_fit;
+    const int nd = m1 * m2;
+    int na = 0, wmax = nd;
+    for (int k = 0; k < ne; ++k) { na += m->embed[k]; if (m->embed[k] > wmax) wmax = m->embed[k]; }
+    int nfa = 0;
+    for (int k = 0; k < nf; ++k) { nfa += m->fit[k]; if (m->fit[k] > wmax) wmax = m->fit[k]; }
+    const double inv = 1.0 / (double)nsel;
+    const int ti = type[i];
+    /* per-slot storage: R, Rd, then for each embedding layer t, zd, y, yd */
+    double *R = calloc((size_t)nsel * 4, sizeof(double)), *Rd = calloc((size_t)nsel * 4, sizeof(double));
+    double *et = malloc(sizeof(double) * (size_t)nsel * na), *ezd = malloc(sizeof(double) * (size_t)nsel * na);
+    double *ey = malloc(sizeof(double) * (size_t)nsel * na), *eyd = malloc(sizeof(double) * (size_t)nsel * na);
+    double *T = calloc(4 * (size_t)m1, sizeof(double)), *Td = calloc(4 * (size_t)m1, sizeof(double));
+    double *Tb = calloc(4 * (size_t)m1, sizeof(double)), *Tdb = calloc(4 * (size_t)m1, sizeof(double));
+    double *D = malloc(sizeof(double) * nd), *Dd = malloc(sizeof(double) * nd);
+    double *ft = malloc(sizeof(double) * (nfa + 1)), *fzd = malloc(sizeof(double) * (nfa + 1));
+    double *fy = malloc(sizeof(double) * (nfa + 1)), *fyd = malloc(sizeof(double) * (nfa + 1));
+    double *b1 = malloc(sizeof(double) * wmax), *b2 = malloc(sizeof(double) * wmax);
+    double *b3 = malloc(sizeof(double) * wmax), *b4 = malloc(sizeof(double) * wmax);
+    double *zb = malloc(sizeof(double) * wmax), *zdb = malloc(sizeof(double) * wmax);
+    if (!R || !Rd || !et || !ezd || !ey || !eyd || !T || !Td || !Tb || !Tdb || !D || !Dd || !ft || !fzd || !fy ||
+        !fyd || !b1 || !b2 || !b3 || !b4 || !zb || !zdb)
+        return ORC_ERR_MEM;
+    orc_layer EL[8], FL[8];
+    /* environment rows and their tangents */
+    for (int s = 0; s < nsel; ++s) {
+        int32_t j = row[s];
+        if (j < 0) continue;
+        double d[3], J[12];
+        orc_minimg(L, invL, coord + 3 * i, coord + 3 * (int64_t)j, d);
+        orc_env_row(d, m->rcut_smth, m->rcut, R + 4 * s, J);
+        double dd[3];
+        for (int k = 0; k < 3; ++k) dd[k] = v[3 * (int64_t)j + k] - v[3 * i + k];
+        for (int c = 0; c < 4; ++c) Rd[4 * s + c] = J[3 * c] * dd[0] + J[3 * c + 1] * dd[1] + J[3 * c + 2] * dd[2];
+    }
+    /* embedding forward (primal + tangent), T and T' */
+    int off = 0;
+    for (int tj = 0; tj < m->ntypes; ++tj) {
+        make_layers(m, embed_net(m, ti, tj), g + (embed_net(m, ti, tj) - m->params), 1, ne, m->embed, EL);
+        for (int s = off; s < off + m->sel[tj]; ++s) {
+            if (row[s] < 0) continue;
+            const double *x = R + 4 * s, *xd = Rd + 4 * s;   /* input s and s' */
+            int ao = 0;
+            for (int k = 0; k < ne; ++k) {
+                layer_fwd_tan(&EL[k], x, xd, et + (int64_t)s * na + ao, ezd + (int64_t)s * na + ao,
+                              ey + (int64_t)s * na + ao, eyd + (int64_t)s * na + ao);
+                x = ey + (int64_t)s * na + ao;
+                xd = eyd + (int64_t)s * na + ao;
+                ao += m->embed[k];
+            }
+            for (int a = 0; a < m1; ++a)
+                for (int c = 0; c < 4; ++c) {
+                    T[4 * a + c] += x[a] * R[4 * s + c];
+                    Td[4 * a + c] += xd[a] * R[4 * s + c] + x[a] * Rd[4 * s + c];
+                }
+        }
+        off += m->sel[tj];
+    }
+    for (int q = 0; q < 4 * m1; ++q) { T[q] *= inv; Td[q] *= inv; }
+    for (int a = 0; a < m1; ++a)
+        for (int b = 0; b < m2; ++b) {
+            double acc = 0.0, accd = 0.0;
+            for (int c = 0; c < 4; ++c) {
+                acc += T[4 * a + c] * T[4 * b + c];
+                accd += Td[4 * a + c] * T[4 * b + c] + T[4 * a + c] * Td[4 * b + c];
+            }
+            D[a * m2 + b] = acc;
+            Dd[a * m2 + b] = accd;
+        }
+    /* fitting forward (primal + tangent) */
+    const double *fnet = fit_net(m, ti);
+    double *gfnet = g + (fnet - m->params);
+    make_layers(m, fnet, gfnet, nd, nf, m->fit, FL);
+    const double *x = D, *xd = Dd;
+    int fo = 0;
+    for (int k = 0; k < nf; ++k) {
+        layer_fwd_tan(&FL[k], x, xd, ft + fo, fzd + fo, fy + fo, fyd + fo);
+        x = fy + fo;
+        xd = fyd + fo;
+        fo += m->fit[k];
+    }
+    const int wl = m->fit[nf - 1];
+    int64_t outW = 0;
+    {
+        int win = nd;
+        for (int k = 0; k < nf; ++k) { outW += (int64_t)win * m->fit[k] + m->fit[k]; win = m->fit[k]; }
+    }
+    const double *Wout = fnet + outW, *bout = Wout + wl;
+    double e = bout[0], ed = 0.0;
+    for (int k = 0; k < wl; ++k) { e += x[k] * Wout[k]; ed += xd[k] * Wout[k]; }
+    *Ei = e;
+    *Edi = ed;
+    /* reverse: output layer */
+    double *Woutg = gfnet + outW;
+    for (int k = 0; k < wl; ++k) Woutg[k] += alpha * x[k] + beta * xd[k];
+    Woutg[wl] += alpha;
+    double *yb = b1, *ydb = b2, *xb = b3, *xdb = b4;
+    for (int k = 0; k < wl; ++k) { yb[k] = alpha * Wout[k]; ydb[k] = beta * Wout[k]; }
+    double *Db = malloc(sizeof(double) * nd), *Ddb = malloc(sizeof(double) * nd);
+    if (!Db || !Ddb) return ORC_ERR_MEM;
+    for (int k = nf - 1; k >= 0; --k) {
+        fo -= m->fit[k];
+        const double *xk = k == 0 ? D : fy + fo - m->fit[k - 1];
+        const double *xdk = k == 0 ? Dd : fyd + fo - m->fit[k - 1];
+        double *oxb = k == 0 ? Db : xb, *oxdb = k == 0 ? Ddb : xdb;
+        layer_rev_tan(&FL[k], xk, xdk, ft + fo, fzd + fo, yb, ydb, oxb, oxdb, zb, zdb);
+        if (k > 0) {
+            double *t1 = yb, *t2 = ydb;
+            yb = xb; ydb = xdb; xb = t1; xdb = t2;
+        }
+    }
+    /* descriptor and contraction adjoints */
+    desc_adjoint(m1, m2, Db, T, Tb, 0);
+    desc_adjoint(m1, m2, Ddb, Td, Tb, 1);
+    desc_adjoint(m1, m2, Ddb, T, Tdb, 0);
+    /* per slot: back through the embedding net */
+    double *Gb = malloc(sizeof(double) * m1), *Gdb = malloc(sizeof(double) * m1);
+    double *eb1 = malloc(sizeof(double) * wmax), *eb2 = malloc(sizeof(double) * wmax);
+    double *eb3 = malloc(sizeof(double) * wmax), *eb4 = malloc(sizeof(double) * wmax);
+    if (!Gb || !Gdb || !eb1 || !eb2 || !eb3 || !eb4) return ORC_ERR_MEM;
+    off = 0;
+    for (int tj = 0; tj < m->ntypes; ++tj) {
+        make_layers(m, embed_net(m, ti, tj), g + (embed_net(m, ti, tj) - m->params), 1, ne, m->embed, EL);
+        for (int s = off; s < off + m->sel[tj]; ++s) {
+            if (row[s] < 0) continue;
+            for (int a = 0; a < m1; ++a) {
+                double acc = 0.0, accd = 0.0;
+                for (int c = 0; c < 4; ++c) {
+                    acc += Tb[4 * a + c] * R[4 * s + c] + Tdb[4 * a + c] * Rd[4 * s + c];
+                    accd += Tdb[4 * a + c] * R[4 * s + c];
+                }
+                Gb[a] = acc * inv;
+                Gdb[a] = accd * inv;
+            }
+            double *cyb = Gb, *cydb = Gdb, *cxb = eb1, *cxdb = eb2;
+            int ao = na - m1;
+            for (int k = ne - 1; k >= 0; --k) {
+                const double *xk = k == 0 ? R + 4 * s : ey + (int64_t)s * na + ao - m->embed[k - 1];
+                const double *xdk = k == 0 ? Rd + 4 * s : eyd + (int64_t)s * na + ao - m->embed[k - 1];
+                layer_rev_tan(&EL[k], xk, xdk, et + (int64_t)s * na + ao, ezd + (int64_t)s * na + ao, cyb, cydb,
+                              k == 0 ? NULL : cxb, k == 0 ? NULL : cxdb, eb3, eb4);
+                if (k > 0) {
+                    ao -= m->embed[k - 1];
+                    /* the input adjoints just written become the next layer's output adjoints */
+                    double *t1 = cyb, *t2 = cydb;
+                    cyb = cxb; cydb = cxdb;
+                    cxb = t1; cxdb = t2;
+                }
+            }
+        }
+        off += m->sel[tj];
+    }
+    free(R); free(Rd); free(et); free(ezd); free(ey); free(eyd); free(T); free(Td); free(Tb); free(Tdb);
+    free(D); free(Dd); free(ft); free(fzd); free(fy); free(fyd); free(b1); free(b2); free(b3); free(b4);
+    free(zb); free(zdb); free(Db); free(Ddb); free(Gb); free(Gdb); free(eb1); free(eb2); free(eb3); free(eb4);
+    return ORC_OK;
+}
+
+/* Gradient of alpha E + beta Edot over the flat parameters (added into grad),
+ * with Edot = sum_k v_k . dE/dr_k; E and Edot are returned (summed in index
+ * order).  Atoms run in parallel with a private gradient per thread; the
+ * private gradients are added in thread order. */
+int orc_jvp_grad(const orc_model *m, int64_t n, const double *coord, const int32_t *type, const double *box,
+                 const int32_t *nlist, const double *v, double alpha, double beta, double *E_out, double *Ed_out,
+                 double *grad, int nthreads)
+{
+    double L[3], invL[3];
+    if (box_lengths(box, L, invL) != ORC_OK) return ORC_ERR_BOX;
+    const int nsel = nsel_total(m);
+    const int64_t np = orc_n_params(m);
+    double *Ei = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1)), *Edi = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!Ei || !Edi) return ORC_ERR_MEM;
+    int nt = 1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    nt = omp_get_max_threads();
+#else
+    (void)nthreads;
+#endif
+    double *priv = calloc((size_t)nt * np, sizeof(double));
+    if (!priv) return ORC_ERR_MEM;
+    int err = ORC_OK;
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *gp = priv + (size_t)tid * np;
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t i = 0; i < n; ++i) {
+            int st = atom_jvp_grad(m, i, nlist + i * nsel, coord, type, v, L, invL, alpha, beta, Ei + i, Edi + i, gp);
+            if (st != ORC_OK) {
+#pragma omp atomic write
+                err = st;
+            }
+        }
+    }
+    if (err == ORC_OK) {
+        for (int t = 0; t < nt; ++t)
+            for (int64_t q = 0; q < np; ++q) grad[q] += priv[(size_t)t * np + q];
+        double e = 0.0, ed = 0.0;
+        for (int64_t i = 0; i < n; ++i) { e += Ei[i]; ed += Edi[i]; }
+        if (E_out) *E_out = e;
+        if (Ed_out) *Ed_out = ed;
+    }
+    free(priv); free(Ei); free(Edi);
+    return err;
+}
