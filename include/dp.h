@@ -160,6 +160,11 @@ dp_status dp_nlist_build(const dp_model *m, int64_t n, const double *coord, cons
  * types, rcut, skin and capacity) and format it there. */
 dp_status dp_nlist_update(dp_nlist *nl, const double *coord, const double box[9]);
 
+/* Device-pointer form of dp_nlist_update: d_coord [n][3] in device memory,
+ * enqueued on `stream`.  A capacity overflow is recorded in the list and
+ * reported (DP_ERR_CAPACITY) by the next dp_nlist_get. */
+dp_status dp_nlist_update_dev(dp_nlist *nl, const double *d_coord, void *stream);
+
 /* The formatted list of the last format (build, update or dp_compute):
  * nlist [n][sum(sel)] int32, for each atom the type-0 block then the type-1
  * block and so on; inside a block the neighbors with r < r_c ordered by
@@ -189,6 +194,51 @@ dp_status dp_compute(dp_model *m, dp_nlist *nl, const double *coord, const doubl
 dp_status dp_compute_dev(dp_model *m, dp_nlist *nl, const double *d_coord, const double box[9],
                          dp_precision prec, double *d_energy, double *d_atom_energy, double *d_force,
                          double *d_virial, void *stream);
+
+/* ------------------------------------------------------------ training */
+
+/* Gradient over the parameters of alpha E + beta Edot, where
+ * Edot = sum_k v_k . dE/dr_k is the derivative of E along the displacement
+ * field v [n][3] (a forward-mode tangent).  With v = F - F_ref this is the
+ * primitive of force matching: F = -grad E, so the force term of a loss
+ * differentiates to -dEdot/dtheta.  Embedding activations are recomputed in
+ * the reverse pass, not stored.  prec: DP_FP64 computes in FP64, any mixed
+ * scheme in FP32.  energy, edot: host scalars (may be NULL); grad
+ * [n_params] host array, ADDED to (flat order of dp_model_get_params).
+ * coord, v host arrays; box must match the list's box.  Errors: as
+ * dp_compute. */
+dp_status dp_param_grad(dp_model *m, dp_nlist *nl, const double *coord, const double box[9], const double *v,
+                        double alpha, double beta, dp_precision prec, double *energy, double *edot, double *grad);
+
+/* Force-matching loss of one configuration and its parameter gradient:
+ * L = p_e ((E - E_ref)/n)^2 + p_f/(3n) sum_k |F_k - F_ref,k|^2, using
+ * dL/dtheta = 2 p_e (E - E_ref)/n^2 dE/dtheta - 2 p_f/(3n) dEdot/dtheta
+ * with v = F - F_ref.  E and F are evaluated in `prec` first.  *loss and
+ * grad [n_params] are ADDED to (host memory). */
+dp_status dp_force_loss_grad(dp_model *m, dp_nlist *nl, const double *coord, const double box[9],
+                             const double *F_ref, double E_ref, double p_e, double p_f, dp_precision prec,
+                             double *loss, double *grad);
+
+/* Device-pointer form: d_coord [n][3], d_F_ref [n][3], d_E_ref [1], d_loss
+ * [1] and d_grad [n_params] in device memory (the last two ADDED to),
+ * enqueued on `stream` without host synchronisation. */
+dp_status dp_force_loss_grad_dev(dp_model *m, dp_nlist *nl, const double *d_coord, const double box[9],
+                                 const double *d_F_ref, const double *d_E_ref, double p_e, double p_f,
+                                 dp_precision prec, double *d_loss, double *d_grad, void *stream);
+
+/* One Adam step (Kingma and Ba 2015) on the model's device parameters with
+ * the device gradient d_grad [n_params]: m = b1 m + (1-b1) g,
+ * v = b2 v + (1-b2) g^2, theta -= lr (m/(1-b1^t)) / (sqrt(v/(1-b2^t)) + eps);
+ * step t >= 1.  The moments are owned by the model (zero at creation).
+ * The FP32 and transposed copies are refreshed on the device; call
+ * dp_model_sync_params before reading the parameters back or evaluating in
+ * a MIX-16 scheme.  Enqueued on `stream`. */
+dp_status dp_adam_step(dp_model *m, const double *d_grad, double lr, double beta1, double beta2, double eps,
+                       int64_t t, void *stream);
+
+/* Copy the device parameters back into the model's host copy and re-pack
+ * the tensor-core images (after dp_adam_step). */
+dp_status dp_model_sync_params(dp_model *m);
 
 /* ------------------------------------------------------------------- MD */
 

@@ -28,8 +28,9 @@ EXPORTS = [
     "dp_status_string", "dp_last_error", "dp_model_create", "dp_model_n_params", "dp_model_get_params",
     "dp_model_set_params", "dp_model_destroy", "dp_model_set_stream", "dp_profile_enable", "dp_profile_read",
     "dp_profile_group_name", "dp_nlist_build", "dp_nlist_update", "dp_nlist_get",
-    "dp_nlist_destroy", "dp_compute", "dp_compute_dev", "dp_md_state_create", "dp_md_step",
-    "dp_md_state_get", "dp_md_state_destroy",
+    "dp_nlist_destroy", "dp_nlist_update_dev", "dp_compute", "dp_compute_dev", "dp_md_state_create",
+    "dp_md_step", "dp_md_state_get", "dp_md_state_destroy", "dp_param_grad", "dp_force_loss_grad",
+    "dp_force_loss_grad_dev", "dp_adam_step", "dp_model_sync_params",
 ]
 
 
@@ -75,6 +76,12 @@ def load(path: str = LIB_PATH):
             "dp_nlist_update": ([P, P, P], C.c_int),
             "dp_nlist_get": ([P, P, P], C.c_int),
             "dp_nlist_destroy": ([P], None),
+            "dp_nlist_update_dev": ([P, P, P], C.c_int),
+            "dp_param_grad": ([P, P, P, P, P, D, D, C.c_int, P, P, P], C.c_int),
+            "dp_force_loss_grad": ([P, P, P, P, P, D, D, D, C.c_int, P, P], C.c_int),
+            "dp_force_loss_grad_dev": ([P, P, P, P, P, P, D, D, C.c_int, P, P, P], C.c_int),
+            "dp_adam_step": ([P, P, D, D, D, D, I64, P], C.c_int),
+            "dp_model_sync_params": ([P], C.c_int),
             "dp_compute": ([P, P, P, P, C.c_int, P, P, P, P], C.c_int),
             "dp_compute_dev": ([P, P, P, P, C.c_int, P, P, P, P, P], C.c_int),
             "dp_md_state_create": ([P, I64, P, P, P, P, P, D, I32, P], C.c_int),
@@ -211,6 +218,16 @@ def dp_nlist_get(nl, n: int, nsel: int):
     return out, ntr.value
 
 
+def _stream(stream):
+    if stream is None:
+        return None
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
+
+
+def dp_nlist_update_dev(nl, d_coord, stream=None):
+    _check(load().dp_nlist_update_dev(nl, _ptr(d_coord), _stream(stream)), "dp_nlist_update_dev")
+
+
 def dp_nlist_destroy(nl):
     if nl:
         load().dp_nlist_destroy(nl)
@@ -237,6 +254,46 @@ def dp_compute_dev(m, nl, d_coord, box, prec, d_energy, d_atom_energy, d_force, 
     sp = None if stream is None else C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
     _check(load().dp_compute_dev(m, nl, _ptr(d_coord), _ptr(box), _prec(prec), _ptr(d_energy), _ptr(d_atom_energy),
                                  _ptr(d_force), _ptr(d_virial), sp), "dp_compute_dev")
+
+
+# ---------------------------------------------------------------- training
+
+def dp_param_grad(m, nl, coord, box, v, alpha: float, beta: float, prec="fp64", grad=None):
+    """(E, Edot, grad) with grad += d(alpha E + beta Edot)/dtheta, Edot = sum_k v_k . dE/dr_k."""
+    coord, box, v = _f64(coord), _box(box), _f64(v)
+    if grad is None:
+        grad = np.zeros(dp_model_n_params(m))
+    e, ed = C.c_double(), C.c_double()
+    _check(load().dp_param_grad(m, nl, _ptr(coord), _ptr(box), _ptr(v), float(alpha), float(beta), _prec(prec),
+                                C.byref(e), C.byref(ed), _ptr(grad)), "dp_param_grad")
+    return e.value, ed.value, grad
+
+
+def dp_force_loss_grad(m, nl, coord, box, F_ref, E_ref: float, p_e: float, p_f: float, prec="fp64", grad=None):
+    """(loss, grad): loss and grad ADDED for one configuration (host arrays)."""
+    coord, box, F_ref = _f64(coord), _box(box), _f64(F_ref)
+    if grad is None:
+        grad = np.zeros(dp_model_n_params(m))
+    loss = C.c_double(0.0)
+    _check(load().dp_force_loss_grad(m, nl, _ptr(coord), _ptr(box), _ptr(F_ref), float(E_ref), float(p_e),
+                                     float(p_f), _prec(prec), C.byref(loss), _ptr(grad)), "dp_force_loss_grad")
+    return loss.value, grad
+
+
+def dp_force_loss_grad_dev(m, nl, d_coord, box, d_F_ref, d_E_ref, p_e, p_f, prec, d_loss, d_grad, stream=None):
+    _check(load().dp_force_loss_grad_dev(m, nl, _ptr(d_coord), _ptr(_box(box)), _ptr(d_F_ref), _ptr(d_E_ref),
+                                         float(p_e), float(p_f), _prec(prec), _ptr(d_loss), _ptr(d_grad),
+                                         _stream(stream)), "dp_force_loss_grad_dev")
+
+
+def dp_adam_step(m, d_grad, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, t: int = 1,
+                 stream=None):
+    _check(load().dp_adam_step(m, _ptr(d_grad), float(lr), float(beta1), float(beta2), float(eps), int(t),
+                               _stream(stream)), "dp_adam_step")
+
+
+def dp_model_sync_params(m):
+    _check(load().dp_model_sync_params(m), "dp_model_sync_params")
 
 
 # ---------------------------------------------------------------------- MD

@@ -382,6 +382,11 @@ dp_status dp_model_get_params(const dp_model *m, double *flat, int64_t n)
 {
     if (!m || !flat) { set_error("dp_model_get_params: NULL argument"); return DP_ERR_ARG; }
     if (n != m->nparams) { set_error("expected %lld parameters, got %lld", (long long)m->nparams, (long long)n); return DP_ERR_ARG; }
+    if (m->params_dirty) {
+        DP_CUDA(cudaStreamSynchronize(m->stream));
+        DP_CUDA(cudaMemcpy(flat, m->d_params, sizeof(double) * n, cudaMemcpyDeviceToHost));
+        return DP_OK;
+    }
     memcpy(flat, m->h_params.data(), sizeof(double) * n);
     return DP_OK;
 }
@@ -393,6 +398,7 @@ dp_status dp_model_set_params(dp_model *m, const double *flat, int64_t n)
     for (int64_t q = 0; q < n; ++q)
         if (!isfinite(flat[q])) { set_error("parameter %lld is not finite", (long long)q); return DP_ERR_ARG; }
     memcpy(m->h_params.data(), flat, sizeof(double) * n);
+    m->params_dirty = false;
     return upload_params(m);
 }
 
@@ -409,6 +415,8 @@ void dp_model_destroy(dp_model *m)
     cudaFree(m->d_flag);
     cudaFree(m->d_err);
     cudaFree(m->d_tcw);
+    cudaFree(m->d_train);
+    cudaFree(m->d_tscr);
     if (m->own_stream) cudaStreamDestroy(m->own_stream);
     delete m->prof;
     delete m;
@@ -614,11 +622,31 @@ dp_status dp_nlist_update(dp_nlist *nl, const double *coord, const double box[9]
     return DP_OK;
 }
 
+dp_status dp_nlist_update_dev(dp_nlist *nl, const double *d_coord, void *stream)
+{
+    if (!nl || (nl->n > 0 && !d_coord)) { set_error("dp_nlist_update_dev: NULL argument"); return DP_ERR_ARG; }
+    if (nl->n == 0) return DP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    DP_TRY(pack_positions(nl, d_coord, st));
+    DP_TRY(nlist_build_device(nl, st, false));
+    DP_TRY(nlist_format_device(nl->m, nl, nullptr, st));
+    return DP_OK;
+}
+
 dp_status dp_nlist_get(const dp_nlist *nl, int32_t *nlist, int64_t *n_truncated)
 {
     if (!nl) { set_error("dp_nlist_get: NULL list"); return DP_ERR_ARG; }
     cudaStream_t st = nl->m->stream;
     DP_CUDA(cudaStreamSynchronize(st));
+    DP_CUDA(cudaDeviceSynchronize());
+    if (nl->n > 0) {
+        int32_t flags[3];
+        DP_CUDA(cudaMemcpy(flags, nl->d_flags, sizeof(flags), cudaMemcpyDeviceToHost));
+        if (flags[0] & kErrCapacity) {
+            set_error("a candidate list exceeded its capacity of %d; build again with a larger cand_cap", nl->cap);
+            return DP_ERR_CAPACITY;
+        }
+    }
     if (nlist && nl->n > 0)
         DP_CUDA(cudaMemcpy(nlist, nl->d_nlist, sizeof(int32_t) * nl->n * nl->m->dev.nsel, cudaMemcpyDeviceToHost));
     if (n_truncated) {

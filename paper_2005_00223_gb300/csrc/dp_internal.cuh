@@ -82,6 +82,8 @@ enum ProfGroup {
     PG_CHECK,         // non-finite scans
     PG_CHUNKS,        // tensor-core work list
     PG_DESC,          // descriptor D and dE/dT between the embedding passes
+    PG_GRAD,          // parameter-gradient kernels
+    PG_OPT,           // optimizer step
     PG_COUNT
 };
 
@@ -140,6 +142,10 @@ struct dp_model {
     int32_t *d_err = nullptr;         // [4] device error word (bounded waits that gave up)
     unsigned char *d_tcw = nullptr;   // packed fp16 and bf16 embedding weights for the tensor cores
     uint32_t tc_img_bytes = 0;
+    double *d_train = nullptr;        // Adam moments m, v [n_params] each
+    double *d_tscr = nullptr;         // scratch of the training calls
+    int64_t tscr_n = -1;
+    bool params_dirty = false;        // device parameters newer than the host copy
 };
 
 struct dp_nlist {
@@ -213,6 +219,12 @@ dp_status compute_mix16(dp_model *m, dp_nlist *nl, int bf16, double *d_energy, d
                         double *d_force, double *d_virial, double *d_atom_virial, cudaStream_t st);
 // FP32 fitting net over all atoms (type-sorted positions): D, dD [n][desc], E_i FP64.
 dp_status fit_f32(dp_model *m, dp_nlist *nl, const float *D, float *dD, double *d_atom_energy, cudaStream_t st);
+dp_status param_grad_device(dp_model *m, dp_nlist *nl, const double *d_v, const double *d_ab, dp_precision prec,
+                            double *d_E_atom, double *d_Ed_atom, double *d_grad, cudaStream_t st);
+dp_status loss_terms_device(int64_t n, const double *d_F, const double *d_F_ref, const double *d_E,
+                            const double *d_E_ref, double p_e, double p_f, double *d_v, double *d_ab, double *d_loss,
+                            cudaStream_t st);
+dp_status refresh_params_device(dp_model *m, cudaStream_t st);
 // Per-atom scratch of the model: E_i [n] at d_aux, W_i [9n] right after it.
 dp_status ensure_aux(dp_model *m, int64_t n);
 dp_status nlist_create_internal(const dp_model *m, int64_t n, const int32_t *type, const double box[9], double rcut,

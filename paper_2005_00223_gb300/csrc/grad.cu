@@ -1,0 +1,793 @@
+// Parameter gradient of alpha E + beta Edot, Edot = sum_k v_k . dE/dr_k, the
+// primitive of force-matching training (the loss
+// L = p_e (dE/N)^2 + p_f/(3N) sum |F - F_ref|^2 has
+// dL/dtheta = 2 p_e dE/N^2 dE/dtheta - 2 p_f/(3N) dEdot/dtheta with
+// v = F - F_ref held fixed, since F = -grad_r E).
+//
+// Edot is the forward-mode tangent of E along v: for atom i the tangent of
+// the environment row is J (v_j - v_i), and every layer carries (x, x') with
+// z' = x' W, t' = (1 - t^2) z', y' = skip(x') + t'.  The gradient over the
+// parameters is reverse mode through the primal and tangent programs; per
+// layer with output adjoints (y_bar, y'_bar):
+//   z'_bar = y'_bar (1 - t^2),  t_bar = y_bar - 2 t z' z'_bar / (1 - t^2) * (1 - t^2)
+//          = y_bar + y'_bar z' (-2 t),  z_bar = t_bar (1 - t^2),
+//   W_bar += x^T z_bar + x'^T z'_bar,  b_bar += z_bar,
+//   x_bar = z_bar W^T + skip^T(y_bar),  x'_bar = z'_bar W^T + skip^T(y'_bar).
+// Embedding activations are recomputed in the reverse pass, not stored.
+//
+// Kernels per evaluation (SIMT, Real = double or float; geometry FP64):
+//   k_jvp_fwd     CTA per atom: env rows and tangents, embedding primal +
+//                 tangent, T, T', D, D'.
+//   k_jvp_fit     A atoms per CTA: fitting primal + tangent, E_i, Edot_i,
+//                 reverse with (alpha, beta) -> D_bar, D'_bar; keeps layer
+//                 inputs and pre-activation adjoints for k_fit_wgrad.
+//   k_fit_wgrad   thread per fitting parameter: sums over the atoms of a type.
+//   k_jvp_bwd     persistent CTAs over atoms: T_bar, T'_bar, then per chunk
+//                 recompute the embedding primal + tangent and run it in
+//                 reverse, accumulating the embedding gradient in a private
+//                 slice per CTA.
+//   k_grad_reduce the private slices, summed in a fixed order.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "dp_internal.cuh"
+#include "geom.cuh"
+
+namespace dp {
+namespace {
+
+constexpr int kGA = 4;   // atoms per CTA in the fitting kernels
+
+__device__ __forceinline__ double g_tanh(double x) { return tanh(x); }
+__device__ __forceinline__ float g_tanh(float x) { return tanhf(x); }
+
+template <typename Real>
+__device__ __forceinline__ const Real *P_of(const ModelDev &md);
+template <>
+__device__ __forceinline__ const double *P_of<double>(const ModelDev &md) { return md.p; }
+template <>
+__device__ __forceinline__ const float *P_of<float>(const ModelDev &md) { return md.p32; }
+template <typename Real>
+__device__ __forceinline__ const Real *PT_of(const ModelDev &md);
+template <>
+__device__ __forceinline__ const double *PT_of<double>(const ModelDev &md) { return md.pT; }
+template <>
+__device__ __forceinline__ const float *PT_of<float>(const ModelDev &md) { return md.pT32; }
+
+template <int G_, int E0_, int E1_, int E2_>
+struct GShape {
+    static constexpr int G = G_, E0 = E0_, E1 = E1_, E2 = E2_, NT = 32 * G_, LD = 33;
+    static constexpr int WMAX = E2_ > E1_ ? E2_ : E1_;
+    static_assert(E0_ % G_ == 0 && E1_ % G_ == 0 && E2_ % G_ == 0, "channels split evenly over warps");
+};
+
+using GWater = GShape<5, 25, 50, 100>;
+using GStudent = GShape<4, 8, 16, 32>;
+using GPaper = GShape<4, 32, 64, 128>;
+
+// Environment rows and tangents of one chunk (warp 0, lane = neighbor).
+template <typename Real>
+__device__ __forceinline__ void env_tangent(const ModelDev &md, const BoxDev &bx, const Pos4 *pos,
+                                            const int32_t *nlist, const double *v, int i, const Pos4 &pi, int tj,
+                                            int c0, int cnt, int n, Real *sR, Real *sRd)
+{
+    double R[4] = {0, 0, 0, 0}, Rd[4] = {0, 0, 0, 0};
+    if (c0 + n < cnt) {
+        const int j = nlist[(int64_t)i * md.nsel + md.sel_off[tj] + c0 + n];
+        double d[3], J[12];
+        const double r = min_image_r(pi, pos[j], bx, d);
+        env_row(d, r, md.rcs, md.rcut, R, J);
+        double dd[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) dd[k] = v[3 * (int64_t)j + k] - v[3 * (int64_t)i + k];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Rd[c] = J[3 * c] * dd[0] + J[3 * c + 1] * dd[1] + J[3 * c + 2] * dd[2];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        sR[n * 4 + c] = (Real)R[c];
+        sRd[n * 4 + c] = (Real)Rd[c];
+    }
+}
+
+// Primal + tangent of one hidden layer for the chunk; thread owns outputs
+// o = g + G u.  Inputs X/Xd [WIN][LD], outputs Y/Yd [WOUT][LD]; t and z'
+// of the owned outputs are returned in registers.
+template <class S, int WIN, int WOUT, typename Real>
+__device__ __forceinline__ void layer_ft(const Real *W, const Real *b, const Real *X, const Real *Xd, Real *Y,
+                                         Real *Yd, Real (&t)[WOUT / S::G], Real (&zd)[WOUT / S::G], int g, int n)
+{
+    constexpr int NO = WOUT / S::G;
+    Real z[NO];
+#pragma unroll
+    for (int u = 0; u < NO; ++u) {
+        z[u] = b[g + S::G * u];
+        zd[u] = Real(0);
+    }
+    for (int k = 0; k < WIN; ++k) {
+        const Real x = X[k * S::LD + n], xd = Xd[k * S::LD + n];
+        const Real *Wr = W + k * WOUT + g;
+#pragma unroll
+        for (int u = 0; u < NO; ++u) {
+            const Real w = Wr[S::G * u];
+            z[u] += x * w;
+            zd[u] += xd * w;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < NO; ++u) {
+        const int o = g + S::G * u;
+        t[u] = g_tanh(z[u]);
+        Real sx = Real(0), sxd = Real(0);
+        if (WOUT == WIN) { sx = X[o * S::LD + n]; sxd = Xd[o * S::LD + n]; }
+        else if (WOUT == 2 * WIN) { sx = X[(o % WIN) * S::LD + n]; sxd = Xd[(o % WIN) * S::LD + n]; }
+        Y[o * S::LD + n] = sx + t[u];
+        Yd[o * S::LD + n] = sxd + (Real(1) - t[u] * t[u]) * zd[u];
+    }
+}
+
+// Layer 0 (input width 1: s and s').
+template <class S, typename Real>
+__device__ __forceinline__ void layer0_ft(const Real *W, const Real *b, Real s, Real sd, Real *Y, Real *Yd,
+                                          Real (&t)[S::E0 / S::G], Real (&zd)[S::E0 / S::G], int g, int n)
+{
+    constexpr int NO = S::E0 / S::G;
+#pragma unroll
+    for (int u = 0; u < NO; ++u) {
+        const int o = g + S::G * u;
+        const Real z = b[o] + s * W[o];
+        zd[u] = sd * W[o];
+        t[u] = g_tanh(z);
+        Real sx = Real(0), sxd = Real(0);
+        if (S::E0 == 1 || S::E0 == 2) { sx = s; sxd = sd; }
+        Y[o * S::LD + n] = sx + t[u];
+        Yd[o * S::LD + n] = sxd + (Real(1) - t[u] * t[u]) * zd[u];
+    }
+}
+
+template <class S, typename Real>
+__global__ void __launch_bounds__(S::NT) k_jvp_fwd(ModelDev md, BoxDev bx, const int32_t *__restrict__ order,
+                                                  const Pos4 *__restrict__ pos, const int32_t *__restrict__ nlist,
+                                                  const int32_t *__restrict__ nnei, const double *__restrict__ v,
+                                                  Real *__restrict__ Tp, Real *__restrict__ Tdp, Real *__restrict__ Dp,
+                                                  Real *__restrict__ Ddp)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real *sm = reinterpret_cast<Real *>(smem_raw);
+    constexpr int G = S::G, NT = S::NT, LD = S::LD;
+    const int tid = threadIdx.x, n = tid & 31, g = tid >> 5;
+    Real *sW = sm;
+    Real *X1 = sW + md.emb.size, *X1d = X1 + S::E0 * LD;
+    Real *X2 = X1d + S::E0 * LD, *X2d = X2 + S::E1 * LD;
+    Real *X3 = X2d + S::E1 * LD, *X3d = X3 + S::E2 * LD;
+    Real *sR = X3d + S::E2 * LD, *sRd = sR + 128;
+    Real *sT = sRd + 128, *sTd = sT + 4 * S::E2;
+    const int64_t p = blockIdx.x;
+    const int i = order[p];
+    const Pos4 pi = pos[i];
+    const int ti = (int)pi.w;
+    const Real *P = P_of<Real>(md);
+    constexpr int KT = (4 * S::E2 + NT - 1) / NT;
+    Real ta[KT], tda[KT];
+#pragma unroll
+    for (int u = 0; u < KT; ++u) ta[u] = tda[u] = Real(0);
+    for (int tj = 0; tj < md.ntypes; ++tj) {
+        const int cnt = nnei[(int64_t)i * md.ntypes + tj];
+        if (cnt == 0) continue;
+        __syncthreads();
+        const Real *net = P + md.emb_base + (int64_t)(ti * md.ntypes + tj) * md.emb.size;
+        for (int q = tid; q < md.emb.size; q += NT) sW[q] = net[q];
+        for (int c0 = 0; c0 < cnt; c0 += 32) {
+            if (g == 0) env_tangent<Real>(md, bx, pos, nlist, v, i, pi, tj, c0, cnt, n, sR, sRd);
+            __syncthreads();
+            Real t0[S::E0 / G], z0[S::E0 / G], t1[S::E1 / G], z1[S::E1 / G], t2[S::E2 / G], z2[S::E2 / G];
+            layer0_ft<S, Real>(sW + md.emb.W[0], sW + md.emb.b[0], sR[n * 4], sRd[n * 4], X1, X1d, t0, z0, g, n);
+            __syncthreads();
+            layer_ft<S, S::E0, S::E1, Real>(sW + md.emb.W[1], sW + md.emb.b[1], X1, X1d, X2, X2d, t1, z1, g, n);
+            __syncthreads();
+            layer_ft<S, S::E1, S::E2, Real>(sW + md.emb.W[2], sW + md.emb.b[2], X2, X2d, X3, X3d, t2, z2, g, n);
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < KT; ++u) {
+                const int q = tid + u * NT;
+                if (q < 4 * S::E2) {
+                    const int m = q >> 2, c = q & 3;
+                    Real a = Real(0), ad = Real(0);
+                    for (int nn = 0; nn < 32; ++nn) {
+                        const Real G_ = X3[m * LD + nn], Gd = X3d[m * LD + nn];
+                        a += G_ * sR[nn * 4 + c];
+                        ad += Gd * sR[nn * 4 + c] + G_ * sRd[nn * 4 + c];
+                    }
+                    ta[u] += a;
+                    tda[u] += ad;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const Real inv = (Real)md.inv_nsel;
+#pragma unroll
+    for (int u = 0; u < KT; ++u) {
+        const int q = tid + u * NT;
+        if (q < 4 * S::E2) {
+            sT[q] = ta[u] * inv;
+            sTd[q] = tda[u] * inv;
+            Tp[p * 4 * S::E2 + q] = sT[q];
+            Tdp[p * 4 * S::E2 + q] = sTd[q];
+        }
+    }
+    __syncthreads();
+    const int nd = S::E2 * md.m2;
+    for (int q = tid; q < nd; q += NT) {
+        const int a = q / md.m2, b = q - a * md.m2;
+        Real dv = Real(0), ddv = Real(0);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            dv += sT[4 * a + c] * sT[4 * b + c];
+            ddv += sTd[4 * a + c] * sT[4 * b + c] + sT[4 * a + c] * sTd[4 * b + c];
+        }
+        Dp[p * nd + q] = dv;
+        Ddp[p * nd + q] = ddv;
+    }
+}
+
+// Offsets (in Real) of the per-atom fitting record: for each hidden layer k,
+// its input x and x' (layer 0 reads D and D' instead), t, z', z_bar, z'_bar;
+// then the last hidden output y and y' and two adjoint ping-pong vectors.
+struct FitRec {
+    int x[kMaxFit + 1], xd[kMaxFit + 1], t[kMaxFit + 1], zd[kMaxFit + 1], zb[kMaxFit + 1], zdb[kMaxFit + 1];
+    int yl, yld, a0, a0d, a1, a1d;
+    int size;
+};
+
+FitRec make_fit_rec(const ModelDev &md)
+{
+    FitRec r{};
+    int off = 0, wmax = 0;
+    for (int k = 0; k < md.n_fit; ++k) {
+        const int win = md.fit.win[k], wout = md.fit.wout[k];
+        wmax = wmax > wout ? wmax : wout;
+        if (k > 0) {
+            r.x[k] = off; off += win;
+            r.xd[k] = off; off += win;
+        }
+        r.t[k] = off; off += wout;
+        r.zd[k] = off; off += wout;
+        r.zb[k] = off; off += wout;
+        r.zdb[k] = off; off += wout;
+    }
+    const int wl = md.fit.wout[md.n_fit - 1];
+    r.yl = off; off += wl;
+    r.yld = off; off += wl;
+    r.a0 = off; off += wmax;
+    r.a0d = off; off += wmax;
+    r.a1 = off; off += wmax;
+    r.a1d = off; off += wmax;
+    r.size = off;
+    return r;
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256) k_jvp_fit(ModelDev md, FitRec fr, int ti, const int32_t *__restrict__ order,
+                                                int64_t pos_begin, int64_t count, const double *__restrict__ ab,
+                                                const Real *__restrict__ D, const Real *__restrict__ Dd,
+                                                Real *__restrict__ rec, double *__restrict__ E_atom,
+                                                double *__restrict__ Ed_atom, Real *__restrict__ Db,
+                                                Real *__restrict__ Ddb)
+{
+    const int tid = threadIdx.x, nthreads = blockDim.x;
+    const int nd = md.desc_dim;
+    const int64_t first = pos_begin + (int64_t)blockIdx.x * kGA;
+    const int na = (int)min((int64_t)kGA, pos_begin + count - first);
+    const Real *net = P_of<Real>(md) + md.fit_base + (int64_t)ti * md.fit.size;
+    const Real *netT = PT_of<Real>(md) + md.fit_base + (int64_t)ti * md.fit.size;
+    const Real alpha = (Real)ab[0], beta = (Real)ab[1];
+    // forward, primal + tangent
+    for (int k = 0; k < md.n_fit; ++k) {
+        const int win = md.fit.win[k], wout = md.fit.wout[k];
+        const Real *W = net + md.fit.W[k], *b = net + md.fit.b[k];
+        for (int o = tid; o < wout; o += nthreads) {
+            Real z[kGA], zd[kGA];
+            const Real bo = b[o];
+#pragma unroll
+            for (int a = 0; a < kGA; ++a) { z[a] = bo; zd[a] = Real(0); }
+            for (int kk = 0; kk < win; ++kk) {
+                const Real w = __ldg(W + (int64_t)kk * wout + o);
+#pragma unroll
+                for (int a = 0; a < kGA; ++a) {
+                    if (a < na) {
+                        const int64_t pa = first + a;
+                        const Real x = k == 0 ? D[pa * nd + kk] : rec[pa * fr.size + fr.x[k] + kk];
+                        const Real xd = k == 0 ? Dd[pa * nd + kk] : rec[pa * fr.size + fr.xd[k] + kk];
+                        z[a] += x * w;
+                        zd[a] += xd * w;
+                    }
+                }
+            }
+            for (int a = 0; a < na; ++a) {
+                const int64_t pa = first + a;
+                Real *R = rec + pa * fr.size;
+                const Real t = g_tanh(z[a]);
+                Real sx = Real(0), sxd = Real(0);
+                if (wout == win || wout == 2 * win) {
+                    const int oi = o % win;
+                    sx = k == 0 ? D[pa * nd + oi] : R[fr.x[k] + oi];
+                    sxd = k == 0 ? Dd[pa * nd + oi] : R[fr.xd[k] + oi];
+                }
+                R[fr.t[k] + o] = t;
+                R[fr.zd[k] + o] = zd[a];
+                const Real y = sx + t, yd = sxd + (Real(1) - t * t) * zd[a];
+                if (k + 1 < md.n_fit) {
+                    R[fr.x[k + 1] + o] = y;
+                    R[fr.xd[k + 1] + o] = yd;
+                } else {
+                    R[fr.yl + o] = y;
+                    R[fr.yld + o] = yd;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // output layer: E = y . w + b, Edot = y' . w
+    const int wl = md.fit.wout[md.n_fit - 1];
+    const Real *Wout = net + md.fit.W[md.n_fit];
+    const Real bout = net[md.fit.b[md.n_fit]];
+    {
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int a = warp; a < na; a += nthreads / 32) {
+            const Real *R = rec + (first + a) * fr.size;
+            Real e = Real(0), ed = Real(0);
+            for (int o = lane; o < wl; o += 32) {
+                e += R[fr.yl + o] * Wout[o];
+                ed += R[fr.yld + o] * Wout[o];
+            }
+            for (int s = 16; s > 0; s >>= 1) {
+                e += __shfl_xor_sync(0xffffffffu, e, s);
+                ed += __shfl_xor_sync(0xffffffffu, ed, s);
+            }
+            if (lane == 0) {
+                E_atom[order[first + a]] = (double)(e + bout);
+                Ed_atom[order[first + a]] = (double)ed;
+            }
+        }
+    }
+    // reverse: output adjoints of the last hidden layer
+    for (int q = tid; q < kGA * wl; q += nthreads) {
+        const int a = q / wl, o = q - a * wl;
+        if (a < na) {
+            Real *R = rec + (first + a) * fr.size;
+            R[fr.a0 + o] = alpha * Wout[o];
+            R[fr.a0d + o] = beta * Wout[o];
+        }
+    }
+    __syncthreads();
+    int cur = 0;   // adjoint buffer holding the current layer's output adjoints
+    for (int k = md.n_fit - 1; k >= 0; --k) {
+        const int win = md.fit.win[k], wout = md.fit.wout[k];
+        const int yb = cur ? fr.a1 : fr.a0, ydb = cur ? fr.a1d : fr.a0d;
+        const int xb = cur ? fr.a0 : fr.a1, xdb = cur ? fr.a0d : fr.a1d;
+        for (int q = tid; q < kGA * wout; q += nthreads) {
+            const int a = q / wout, o = q - a * wout;
+            if (a < na) {
+                Real *R = rec + (first + a) * fr.size;
+                const Real t = R[fr.t[k] + o], g1 = Real(1) - t * t;
+                const Real zdb = R[ydb + o] * g1;
+                const Real tb = R[yb + o] + R[ydb + o] * R[fr.zd[k] + o] * (Real(-2) * t);
+                R[fr.zb[k] + o] = tb * g1;
+                R[fr.zdb[k] + o] = zdb;
+            }
+        }
+        __syncthreads();
+        const Real *WT = netT + md.fit.W[k];   // [wout][win]
+        for (int kk = tid; kk < win; kk += nthreads) {
+            Real xa[kGA], xda[kGA];
+#pragma unroll
+            for (int a = 0; a < kGA; ++a) { xa[a] = Real(0); xda[a] = Real(0); }
+            for (int o = 0; o < wout; ++o) {
+                const Real w = __ldg(WT + (int64_t)o * win + kk);
+#pragma unroll
+                for (int a = 0; a < kGA; ++a) {
+                    if (a < na) {
+                        const Real *R = rec + (first + a) * fr.size;
+                        xa[a] += R[fr.zb[k] + o] * w;
+                        xda[a] += R[fr.zdb[k] + o] * w;
+                    }
+                }
+            }
+            for (int a = 0; a < na; ++a) {
+                Real *R = rec + (first + a) * fr.size;
+                Real s1 = xa[a], s2 = xda[a];
+                if (wout == win) { s1 += R[yb + kk]; s2 += R[ydb + kk]; }
+                else if (wout == 2 * win) { s1 += R[yb + kk] + R[yb + kk + win]; s2 += R[ydb + kk] + R[ydb + kk + win]; }
+                if (k == 0) {
+                    Db[(first + a) * nd + kk] = s1;
+                    Ddb[(first + a) * nd + kk] = s2;
+                } else {
+                    R[xb + kk] = s1;
+                    R[xdb + kk] = s2;
+                }
+            }
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+}
+
+// One thread per parameter of the fitting net of type ti; sums over the
+// atoms of that type and adds into grad (FP64).
+template <typename Real>
+__global__ void k_fit_wgrad(ModelDev md, FitRec fr, int ti, int64_t pos_begin, int64_t count,
+                            const double *__restrict__ ab, const Real *__restrict__ D, const Real *__restrict__ Dd,
+                            const Real *__restrict__ rec, double *__restrict__ grad)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= md.fit.size) return;
+    const int nd = md.desc_dim;
+    double acc = 0.0;
+    int layer = -1, isb = 0, in = 0, out = 0;
+    for (int k = 0; k <= md.n_fit; ++k) {
+        if (q >= md.fit.W[k] && q < md.fit.b[k]) {
+            layer = k;
+            in = (int)((q - md.fit.W[k]) / md.fit.wout[k]);
+            out = (int)((q - md.fit.W[k]) % md.fit.wout[k]);
+        } else if (q >= md.fit.b[k] && q < md.fit.b[k] + md.fit.wout[k]) {
+            layer = k;
+            isb = 1;
+            out = (int)(q - md.fit.b[k]);
+        }
+    }
+    if (layer < 0) return;
+    if (layer == md.n_fit) {
+        // output layer: w_bar = sum alpha y + beta y', b_bar = alpha * count
+        if (isb) {
+            acc = ab[0] * (double)count;
+        } else {
+            for (int64_t a = 0; a < count; ++a) {
+                const Real *R = rec + (pos_begin + a) * fr.size;
+                acc += ab[0] * (double)R[fr.yl + in] + ab[1] * (double)R[fr.yld + in];
+            }
+        }
+    } else if (isb) {
+        for (int64_t a = 0; a < count; ++a) acc += (double)rec[(pos_begin + a) * fr.size + fr.zb[layer] + out];
+    } else {
+        for (int64_t a = 0; a < count; ++a) {
+            const int64_t pa = pos_begin + a;
+            const Real *R = rec + pa * fr.size;
+            const Real x = layer == 0 ? D[pa * nd + in] : R[fr.x[layer] + in];
+            const Real xd = layer == 0 ? Dd[pa * nd + in] : R[fr.xd[layer] + in];
+            acc += (double)x * (double)R[fr.zb[layer] + out] + (double)xd * (double)R[fr.zdb[layer] + out];
+        }
+    }
+    grad[md.fit_base + (int64_t)ti * md.fit.size + q] += acc;
+}
+
+// formula(Xb, Y)[a][c] = sum_b Xb[a][b] Y[b][c] + [a < M2] sum_a' Xb[a'][a] Y[a'][c]
+template <typename Real>
+__device__ __forceinline__ Real desc_adj(const Real *Xb, const Real *Y, int m1, int m2, int a, int c)
+{
+    Real acc = Real(0);
+    for (int b = 0; b < m2; ++b) acc += Xb[a * m2 + b] * Y[4 * b + c];
+    if (a < m2)
+        for (int a2 = 0; a2 < m1; ++a2) acc += Xb[a2 * m2 + a] * Y[4 * a2 + c];
+    return acc;
+}
+
+// Reverse of one hidden layer for a chunk.  dy, dyd: owned output adjoints
+// (registers, with the skip terms of the layer above already added); t, zd:
+// owned t and z'.  Writes z_bar, z'_bar to Zb/Zdb [WOUT][LD]; after a sync
+// accumulates W_bar and b_bar into gW (private slice); returns the input
+// adjoints (owned inputs) without this layer's skip terms added.
+template <class S, int WIN, int WOUT, typename Real>
+__device__ __forceinline__ void layer_rev(const Real *W, const Real *X, const Real *Xd, Real *Zb, Real *Zdb,
+                                          const Real (&dy)[WOUT / S::G], const Real (&dyd)[WOUT / S::G],
+                                          const Real (&t)[WOUT / S::G], const Real (&zd)[WOUT / S::G], Real *gW,
+                                          Real *gb, Real (&xb)[WIN / S::G], Real (&xdb)[WIN / S::G], int tid, int g,
+                                          int n)
+{
+    constexpr int NO = WOUT / S::G, NI = WIN / S::G, LD = S::LD, NT = S::NT;
+#pragma unroll
+    for (int u = 0; u < NO; ++u) {
+        const int o = g + S::G * u;
+        const Real g1 = Real(1) - t[u] * t[u];
+        const Real zdb = dyd[u] * g1;
+        const Real tb = dy[u] + dyd[u] * zd[u] * (Real(-2) * t[u]);
+        Zb[o * LD + n] = tb * g1;
+        Zdb[o * LD + n] = zdb;
+    }
+    __syncthreads();
+    for (int e = tid; e < WIN * WOUT; e += NT) {
+        const int k = e / WOUT, o = e - k * WOUT;
+        Real acc = Real(0);
+#pragma unroll 8
+        for (int nn = 0; nn < 32; ++nn) acc += X[k * LD + nn] * Zb[o * LD + nn] + Xd[k * LD + nn] * Zdb[o * LD + nn];
+        gW[e] += acc;
+    }
+    for (int o = tid; o < WOUT; o += NT) {
+        Real acc = Real(0);
+        for (int nn = 0; nn < 32; ++nn) acc += Zb[o * LD + nn];
+        gb[o] += acc;
+    }
+#pragma unroll
+    for (int u = 0; u < NI; ++u) { xb[u] = Real(0); xdb[u] = Real(0); }
+    for (int o = 0; o < WOUT; ++o) {
+        const Real zb = Zb[o * LD + n], zdb = Zdb[o * LD + n];
+        const Real *Wc = W + g * WOUT + o;
+#pragma unroll
+        for (int u = 0; u < NI; ++u) {
+            const Real w = Wc[S::G * u * WOUT];
+            xb[u] += zb * w;
+            xdb[u] += zdb * w;
+        }
+    }
+}
+
+template <class S, typename Real>
+__global__ void __launch_bounds__(S::NT) k_jvp_bwd(ModelDev md, BoxDev bx, const int32_t *__restrict__ order, int64_t n_atoms,
+                                                  const Pos4 *__restrict__ pos, const int32_t *__restrict__ nlist,
+                                                  const int32_t *__restrict__ nnei, const double *__restrict__ v,
+                                                  const Real *__restrict__ Tp, const Real *__restrict__ Tdp,
+                                                  const Real *__restrict__ Dbp, const Real *__restrict__ Ddbp,
+                                                  Real *__restrict__ gpriv)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real *sm = reinterpret_cast<Real *>(smem_raw);
+    constexpr int G = S::G, NT = S::NT, LD = S::LD;
+    const int tid = threadIdx.x, n = tid & 31, g = tid >> 5;
+    const int nq = 4 * S::E2, nd = S::E2 * md.m2;
+    Real *sW = sm;
+    Real *X1 = sW + md.emb.size, *X1d = X1 + S::E0 * LD;
+    Real *X2 = X1d + S::E0 * LD, *X2d = X2 + S::E1 * LD;
+    Real *Zb = X2d + S::E1 * LD, *Zdb = Zb + S::WMAX * LD;       // reused by each layer
+    Real *sR = Zdb + S::WMAX * LD, *sRd = sR + 128;
+    Real *sT = sRd + 128, *sTd = sT + nq, *sTb = sTd + nq, *sTdb = sTb + nq;
+    Real *stage = Zb;                                             // D_bar / D'_bar staging at atom start
+    Real *X3 = Zb, *X3d = Zdb;                                    // layer-3 forward outputs (only t, z' kept)
+    Real *gpb = gpriv + (int64_t)blockIdx.x * md.ntypes * md.ntypes * md.emb.size;
+    const Real *P = P_of<Real>(md);
+    for (int64_t p = blockIdx.x; p < n_atoms; p += gridDim.x) {
+        const int i = order[p];
+        const Pos4 pi = pos[i];
+        const int ti = (int)pi.w;
+        __syncthreads();
+        for (int q = tid; q < nq; q += NT) {
+            sT[q] = Tp[p * nq + q];
+            sTd[q] = Tdp[p * nq + q];
+        }
+        for (int q = tid; q < nd; q += NT) {
+            stage[q] = Dbp[p * nd + q];
+            stage[nd + q] = Ddbp[p * nd + q];
+        }
+        __syncthreads();
+        // T_bar = f(D_bar, T) + f(D'_bar, T'),  T'_bar = f(D'_bar, T), both times 1/sum(sel)
+        const Real inv = (Real)md.inv_nsel;
+        for (int q = tid; q < nq; q += NT) {
+            const int a = q >> 2, c = q & 3;
+            sTb[q] = (desc_adj<Real>(stage, sT, S::E2, md.m2, a, c) + desc_adj<Real>(stage + nd, sTd, S::E2, md.m2, a, c)) * inv;
+            sTdb[q] = desc_adj<Real>(stage + nd, sT, S::E2, md.m2, a, c) * inv;
+        }
+        for (int tj = 0; tj < md.ntypes; ++tj) {
+            const int cnt = nnei[(int64_t)i * md.ntypes + tj];
+            if (cnt == 0) continue;
+            __syncthreads();
+            const int net_id = ti * md.ntypes + tj;
+            const Real *net = P + md.emb_base + (int64_t)net_id * md.emb.size;
+            for (int q = tid; q < md.emb.size; q += NT) sW[q] = net[q];
+            Real *gnet = gpb + (int64_t)net_id * md.emb.size;
+            for (int c0 = 0; c0 < cnt; c0 += 32) {
+                if (g == 0) env_tangent<Real>(md, bx, pos, nlist, v, i, pi, tj, c0, cnt, n, sR, sRd);
+                __syncthreads();
+                Real t0[S::E0 / G], z0[S::E0 / G], t1[S::E1 / G], z1[S::E1 / G], t2[S::E2 / G], z2[S::E2 / G];
+                const Real s = sR[n * 4], sd = sRd[n * 4];
+                layer0_ft<S, Real>(sW + md.emb.W[0], sW + md.emb.b[0], s, sd, X1, X1d, t0, z0, g, n);
+                __syncthreads();
+                layer_ft<S, S::E0, S::E1, Real>(sW + md.emb.W[1], sW + md.emb.b[1], X1, X1d, X2, X2d, t1, z1, g, n);
+                __syncthreads();
+                layer_ft<S, S::E1, S::E2, Real>(sW + md.emb.W[2], sW + md.emb.b[2], X2, X2d, X3, X3d, t2, z2, g, n);
+                // G_bar = (T_bar R + T'_bar R') for the owned channels, G'_bar = T'_bar R
+                Real gb2[S::E2 / G], gdb2[S::E2 / G];
+                const Real R0 = sR[n * 4], R1 = sR[n * 4 + 1], R2 = sR[n * 4 + 2], R3 = sR[n * 4 + 3];
+                const Real Q0 = sRd[n * 4], Q1 = sRd[n * 4 + 1], Q2 = sRd[n * 4 + 2], Q3 = sRd[n * 4 + 3];
+#pragma unroll
+                for (int u = 0; u < S::E2 / G; ++u) {
+                    const int m = g + G * u;
+                    const Real *tb = sTb + 4 * m, *tdb = sTdb + 4 * m;
+                    gb2[u] = tb[0] * R0 + tb[1] * R1 + tb[2] * R2 + tb[3] * R3 + tdb[0] * Q0 + tdb[1] * Q1 +
+                             tdb[2] * Q2 + tdb[3] * Q3;
+                    gdb2[u] = tdb[0] * R0 + tdb[1] * R1 + tdb[2] * R2 + tdb[3] * R3;
+                }
+                __syncthreads();   // X3/X3d (aliasing Zb/Zdb) are no longer read
+                Real xb1[S::E1 / G], xdb1[S::E1 / G];
+                layer_rev<S, S::E1, S::E2, Real>(sW + md.emb.W[2], X2, X2d, Zb, Zdb, gb2, gdb2, t2, z2,
+                                                 gnet + md.emb.W[2], gnet + md.emb.b[2], xb1, xdb1, tid, g, n);
+                // skip of layer 3 into y2: owned k and k + E1 belong to the same thread
+#pragma unroll
+                for (int u = 0; u < S::E1 / G; ++u) {
+                    if (S::E2 == S::E1) { xb1[u] += gb2[u]; xdb1[u] += gdb2[u]; }
+                    else if (S::E2 == 2 * S::E1) {
+                        xb1[u] += gb2[u] + gb2[u + S::E1 / G];
+                        xdb1[u] += gdb2[u] + gdb2[u + S::E1 / G];
+                    }
+                }
+                __syncthreads();
+                Real xb0[S::E0 / G], xdb0[S::E0 / G];
+                layer_rev<S, S::E0, S::E1, Real>(sW + md.emb.W[1], X1, X1d, Zb, Zdb, xb1, xdb1, t1, z1,
+                                                 gnet + md.emb.W[1], gnet + md.emb.b[1], xb0, xdb0, tid, g, n);
+#pragma unroll
+                for (int u = 0; u < S::E0 / G; ++u) {
+                    if (S::E1 == S::E0) { xb0[u] += xb1[u]; xdb0[u] += xdb1[u]; }
+                    else if (S::E1 == 2 * S::E0) {
+                        xb0[u] += xb1[u] + xb1[u + S::E0 / G];
+                        xdb0[u] += xdb1[u] + xdb1[u + S::E0 / G];
+                    }
+                }
+                __syncthreads();
+                // layer 0: input (s, s'); W_bar[0][k] += s z_bar + s' z'_bar, b_bar += z_bar
+#pragma unroll
+                for (int u = 0; u < S::E0 / G; ++u) {
+                    const int o = g + G * u;
+                    const Real g1 = Real(1) - t0[u] * t0[u];
+                    const Real zdb = xdb0[u] * g1;
+                    const Real tb = xb0[u] + xdb0[u] * z0[u] * (Real(-2) * t0[u]);
+                    Zb[o * LD + n] = tb * g1;
+                    Zdb[o * LD + n] = zdb;
+                }
+                __syncthreads();
+                for (int o = tid; o < S::E0; o += NT) {
+                    Real aw = Real(0), abb = Real(0);
+                    for (int nn = 0; nn < 32; ++nn) {
+                        aw += sR[nn * 4] * Zb[o * LD + nn] + sRd[nn * 4] * Zdb[o * LD + nn];
+                        abb += Zb[o * LD + nn];
+                    }
+                    gnet[md.emb.W[0] + o] += aw;
+                    gnet[md.emb.b[0] + o] += abb;
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+// grad[emb part] += sum over the private slices, in slice order.
+template <typename Real>
+__global__ void k_grad_reduce(const Real *__restrict__ gpriv, int nslices, int64_t len, double *__restrict__ grad)
+{
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= len) return;
+    double acc = 0.0;
+    for (int s = 0; s < nslices; ++s) acc += (double)gpriv[(int64_t)s * len + q];
+    grad[q] += acc;
+}
+
+// d_ab = (alpha, beta) of the force-matching loss from E and F, plus the
+// loss itself: one block.
+__global__ void k_loss_terms(int64_t n, const double *__restrict__ F, const double *__restrict__ F_ref,
+                             const double *__restrict__ E, const double *__restrict__ E_ref, double p_e, double p_f,
+                             double *__restrict__ v, double *__restrict__ ab, double *__restrict__ loss)
+{
+    __shared__ double s[256];
+    const int t = threadIdx.x;
+    double acc = 0.0;
+    for (int64_t q = t; q < 3 * n; q += blockDim.x) {
+        const double d = F[q] - F_ref[q];
+        v[q] = d;
+        acc += d * d;
+    }
+    s[t] = acc;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (t < h) s[t] += s[t + h];
+        __syncthreads();
+    }
+    if (t == 0) {
+        const double dE = E[0] - E_ref[0];
+        const double nn = (double)n;
+        ab[0] = 2.0 * p_e * dE / (nn * nn);
+        ab[1] = -2.0 * p_f / (3.0 * nn);
+        loss[0] += p_e * (dE / nn) * (dE / nn) + p_f * s[0] / (3.0 * nn);
+    }
+}
+
+template <class S, typename Real>
+size_t fwd_smem(const ModelDev &md)
+{
+    return sizeof(Real) * ((size_t)md.emb.size + 2 * (S::E0 + S::E1 + S::E2) * S::LD + 256 + 8 * S::E2);
+}
+
+template <class S, typename Real>
+size_t bwd_smem(const ModelDev &md)
+{
+    size_t zb = (size_t)2 * S::WMAX * S::LD;
+    size_t stage = (size_t)2 * S::E2 * md.m2;
+    return sizeof(Real) * ((size_t)md.emb.size + 2 * (S::E0 + S::E1) * S::LD + (zb > stage ? zb : stage) + 256 +
+                           16 * S::E2);
+}
+
+template <class S, typename Real>
+dp_status run_grad(dp_model *m, dp_nlist *nl, const double *d_v, const double *d_ab, double *d_E_atom,
+                   double *d_Ed_atom, double *d_grad, cudaStream_t st)
+{
+    const ModelDev &md = m->dev;
+    const int64_t n = nl->n;
+    const FitRec fr = make_fit_rec(md);
+    int nsm = 0;
+    DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
+    const int nslices = nsm;
+    const int64_t emb_len = (int64_t)md.ntypes * md.ntypes * md.emb.size;
+    size_t need = 0;
+    auto sz = [&](size_t b) { need += (b + 255) & ~(size_t)255; };
+    sz(sizeof(Real) * 4 * md.m1 * n * 2);
+    sz(sizeof(Real) * md.desc_dim * n * 4);
+    sz(sizeof(Real) * (size_t)fr.size * n);
+    sz(sizeof(Real) * emb_len * nslices);
+    DP_TRY(ensure_workspace(m, need));
+    char *w = m->ws;
+    auto carve = [&](size_t bytes) {
+        char *p = w;
+        w += (bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    Real *T = (Real *)carve(sizeof(Real) * 4 * md.m1 * n * 2), *Td = T + 4 * md.m1 * n;
+    Real *D = (Real *)carve(sizeof(Real) * md.desc_dim * n * 4);
+    Real *Dd = D + md.desc_dim * n, *Db = Dd + md.desc_dim * n, *Ddb = Db + md.desc_dim * n;
+    Real *rec = (Real *)carve(sizeof(Real) * (size_t)fr.size * n);
+    Real *gpriv = (Real *)carve(sizeof(Real) * emb_len * nslices);
+    DP_CUDA(cudaMemsetAsync(gpriv, 0, sizeof(Real) * emb_len * nslices, st));
+    BoxDev bx = make_box(nl);
+    const Pos4 *pos = (const Pos4 *)nl->d_pos;
+    const size_t sf = fwd_smem<S, Real>(md), sb = bwd_smem<S, Real>(md);
+    DP_CUDA(cudaFuncSetAttribute(k_jvp_fwd<S, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
+    DP_CUDA(cudaFuncSetAttribute(k_jvp_bwd<S, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
+    {
+        ProfScope ps(m->prof, PG_GRAD, 1, st);
+        k_jvp_fwd<S, Real><<<(unsigned)n, S::NT, sf, st>>>(md, bx, nl->d_order, pos, nl->d_nlist, nl->d_nnei, d_v, T,
+                                                          Td, D, Dd);
+    }
+    DP_CUDA(cudaGetLastError());
+    for (int t = 0; t < md.ntypes; ++t) {
+        const int64_t b = nl->type_off[t], cnt = nl->type_count[t];
+        if (cnt <= 0) continue;
+        ProfScope ps(m->prof, PG_GRAD, 2, st);
+        k_jvp_fit<Real><<<(unsigned)((cnt + kGA - 1) / kGA), 256, 0, st>>>(md, fr, t, nl->d_order, b, cnt, d_ab, D,
+                                                                          Dd, rec, d_E_atom, d_Ed_atom, Db, Ddb);
+        k_fit_wgrad<Real><<<(unsigned)((md.fit.size + 255) / 256), 256, 0, st>>>(md, fr, t, b, cnt, d_ab, D, Dd,
+                                                                                rec, d_grad);
+        DP_CUDA(cudaGetLastError());
+    }
+    {
+        ProfScope ps(m->prof, PG_GRAD, 2, st);
+        k_jvp_bwd<S, Real><<<(unsigned)nslices, S::NT, sb, st>>>(md, bx, nl->d_order, n, pos, nl->d_nlist,
+                                                                 nl->d_nnei, d_v, T, Td, Db, Ddb, gpriv);
+        k_grad_reduce<Real><<<(unsigned)((emb_len + 255) / 256), 256, 0, st>>>(gpriv, nslices, emb_len,
+                                                                               d_grad + md.emb_base);
+    }
+    DP_CUDA(cudaGetLastError());
+    return DP_OK;
+}
+
+}  // namespace
+
+dp_status param_grad_device(dp_model *m, dp_nlist *nl, const double *d_v, const double *d_ab, dp_precision prec,
+                            double *d_E_atom, double *d_Ed_atom, double *d_grad, cudaStream_t st)
+{
+    const int *e = m->dev.emb.wout;
+    const bool f64 = prec == DP_FP64;
+    if (e[0] == 25)
+        return f64 ? run_grad<GWater, double>(m, nl, d_v, d_ab, d_E_atom, d_Ed_atom, d_grad, st)
+                   : run_grad<GWater, float>(m, nl, d_v, d_ab, d_E_atom, d_Ed_atom, d_grad, st);
+    if (e[0] == 8)
+        return f64 ? run_grad<GStudent, double>(m, nl, d_v, d_ab, d_E_atom, d_Ed_atom, d_grad, st)
+                   : run_grad<GStudent, float>(m, nl, d_v, d_ab, d_E_atom, d_Ed_atom, d_grad, st);
+    return f64 ? run_grad<GPaper, double>(m, nl, d_v, d_ab, d_E_atom, d_Ed_atom, d_grad, st)
+               : run_grad<GPaper, float>(m, nl, d_v, d_ab, d_E_atom, d_Ed_atom, d_grad, st);
+}
+
+dp_status loss_terms_device(int64_t n, const double *d_F, const double *d_F_ref, const double *d_E,
+                            const double *d_E_ref, double p_e, double p_f, double *d_v, double *d_ab, double *d_loss,
+                            cudaStream_t st)
+{
+    k_loss_terms<<<1, 256, 0, st>>>(n, d_F, d_F_ref, d_E, d_E_ref, p_e, p_f, d_v, d_ab, d_loss);
+    DP_CUDA(cudaGetLastError());
+    return DP_OK;
+}
+
+}  // namespace dp

@@ -1,0 +1,177 @@
+"""GPU parameter gradient, force-matching loss gradient, Adam, and the autograd.Function, against the oracle."""
+import numpy as np
+import pytest
+
+import dpsynth
+from gpu_common import rms
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dp():
+    import paper_2005_00223_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+CASES = [
+    ("water192", dpsynth.water_config, lambda: dpsynth.water_box(1)),
+    ("cu500", dpsynth.copper_config, lambda: dpsynth.copper_fcc(1, ncell=5)),
+    ("student_cu500", dpsynth.copper_student_config, lambda: dpsynth.copper_fcc(2, ncell=5)),
+]
+
+
+@pytest.mark.parametrize("name,cfgf,sysf", CASES, ids=[c[0] for c in CASES])
+def test_param_grad_matches_oracle(dp, orc, name, cfgf, sysf):
+    cfg = cfgf()
+    coord, typ, box = sysf()
+    p = dpsynth.model_params(cfg, 5)
+    m = dp.Model(cfg, 0, params=p)
+    nl = dp.NeighborList(m, coord, typ, box)
+    v = np.random.default_rng(3).normal(size=coord.shape)
+    E, Ed, g = dp.dp_param_grad(m.h, nl.h, coord, box, v, 0.3, -1.7, "fp64")
+    Er, Edr, gr = orc.Model(cfg, p).jvp_grad(coord, typ, box, v, 0.3, -1.7)
+    assert E == pytest.approx(Er, rel=1e-10)
+    assert Ed == pytest.approx(Edr, rel=1e-9)
+    assert _rel(g, gr) < 1e-9, _rel(g, gr)
+    # the FP32 gradient (training precision) within FP32 rounding of the FP64 one
+    E32, Ed32, g32 = dp.dp_param_grad(m.h, nl.h, coord, box, v, 0.3, -1.7, "mix32")
+    print(name, "fp32 grad rel err", _rel(g32, gr))
+    assert _rel(g32, gr) < 1e-3
+
+
+def test_force_loss_grad_matches_oracle_and_fd(dp, orc):
+    cfg = dpsynth.water_config()
+    p = dpsynth.model_params(cfg, 6)
+    rng = np.random.default_rng(4)
+    frames = []
+    for s in range(4):
+        c, t, b = dpsynth.water_box(20 + s)
+        frames.append((c, t, b, float(rng.normal()), rng.normal(scale=1e-3, size=c.shape)))
+    m = dp.Model(cfg, 0, params=p)
+    loss, grad = 0.0, np.zeros(len(p))
+    for c, t, b, Eref, Fref in frames:
+        nl = dp.NeighborList(m, c, t, b)
+        l, _ = dp.dp_force_loss_grad(m.h, nl.h, c, b, Fref, Eref, 0.5, 100.0, "fp64", grad=grad)
+        loss += l
+    om = orc.Model(cfg, p)
+    Lr, gr = om.force_loss_grad(frames, p_e=0.5, p_f=100.0)
+    assert loss == pytest.approx(Lr, rel=1e-10)
+    assert _rel(grad, gr) < 1e-9
+    # central differences of the GPU loss along a few parameters
+    idx = rng.choice(len(p), 8, replace=False)
+
+    def gpu_loss(pp):
+        mm = dp.Model(cfg, 0, params=pp)
+        tot = 0.0
+        for c, t, b, Eref, Fref in frames:
+            nl = dp.NeighborList(mm, c, t, b)
+            E, _, F, _ = nl.compute(c, b, "fp64")
+            tot += 0.5 * ((E - Eref) / len(t)) ** 2 + 100.0 * float(((F - Fref) ** 2).sum()) / (3 * len(t))
+        return tot
+
+    h = 1e-4
+    for q in idx:
+        vals = []
+        for k in (2, 1, -1, -2):
+            pp = p.copy()
+            pp[q] += k * h
+            vals.append(gpu_loss(pp))
+        fd = (-vals[0] + 8 * vals[1] - 8 * vals[2] + vals[3]) / (12 * h)
+        assert grad[q] == pytest.approx(fd, rel=1e-5, abs=1e-10)
+
+
+@pytest.mark.slow
+def test_force_loss_grad_32_frames(dp, orc):
+    """The 32 seeded 192-atom water frames: GPU FP64 gradient against the oracle."""
+    cfg = dpsynth.water_config()
+    p = dpsynth.model_params(cfg, 7)
+    rng = np.random.default_rng(5)
+    m = dp.Model(cfg, 0, params=p)
+    frames, grad, loss = [], np.zeros(len(p)), 0.0
+    for s in range(32):
+        c, t, b = dpsynth.water_box(100 + s)
+        fr = (c, t, b, float(rng.normal()), rng.normal(scale=1e-3, size=c.shape))
+        frames.append(fr)
+        nl = dp.NeighborList(m, c, t, b)
+        l, _ = dp.dp_force_loss_grad(m.h, nl.h, c, b, fr[4], fr[3], 1.0, 100.0, "fp64", grad=grad)
+        loss += l
+    Lr, gr = orc.Model(cfg, p).force_loss_grad(frames, p_e=1.0, p_f=100.0)
+    assert loss == pytest.approx(Lr, rel=1e-10)
+    assert _rel(grad, gr) < 1e-9
+
+
+def test_adam_step_matches_definition(dp):
+    import torch
+    cfg = dpsynth.copper_student_config()
+    p = dpsynth.model_params(cfg, 8)
+    m = dp.Model(cfg, 0, params=p)
+    rng = np.random.default_rng(6)
+    mo = np.zeros_like(p)
+    ve = np.zeros_like(p)
+    ref = p.copy()
+    for t in range(1, 4):
+        g = rng.normal(size=p.shape)
+        dg = torch.tensor(g, dtype=torch.float64, device="cuda")
+        dp.dp_adam_step(m.h, dg, 1e-3, 0.9, 0.999, 1e-8, t)
+        torch.cuda.synchronize()
+        mo = 0.9 * mo + 0.1 * g
+        ve = 0.999 * ve + 0.001 * g * g
+        ref -= 1e-3 * (mo / (1 - 0.9 ** t)) / (np.sqrt(ve / (1 - 0.999 ** t)) + 1e-8)
+    np.testing.assert_allclose(m.params, ref, rtol=1e-12, atol=1e-15)
+    dp.dp_model_sync_params(m.h)
+    np.testing.assert_allclose(m.params, ref, rtol=1e-12, atol=1e-15)
+
+
+def test_autograd_function_gives_forces(dp, orc):
+    import torch
+    from paper_2005_00223_gb300.torch_ops import dp_energy
+    cfg = dpsynth.water_config()
+    coord, typ, box = dpsynth.water_box(3)
+    p = dpsynth.model_params(cfg, 9)
+    m = dp.Model(cfg, 0, params=p)
+    nl = dp.NeighborList(m, coord, typ, box, skin=1.0)
+    x = torch.tensor(coord, dtype=torch.float64, device="cuda", requires_grad=True)
+    E, Ei, F, W = dp_energy(m, nl, x, box, "fp64")
+    (gx,) = torch.autograd.grad(E, x)
+    Er, _, Fr, Wr = orc.Model(cfg, p).compute(coord, typ, box)
+    assert float(E) == pytest.approx(Er, rel=1e-10)
+    np.testing.assert_allclose(-gx.cpu().numpy(), Fr, atol=1e-10 * rms(Fr))
+    np.testing.assert_allclose(W.cpu().numpy(), Wr, atol=1e-10 * np.abs(Wr).max())
+    # mixed precision through the same Function
+    E16, _, F16, _ = dp_energy(m, nl, x.detach(), box, "bf16")
+    assert abs(float(E16) - Er) < 1e-2 * abs(Er)
+
+
+@pytest.mark.slow
+def test_water_1p57m_bf16_autograd_sampled(dp, orc):
+    """The 1,572,864-atom water box in MIX-16 through the autograd.Function; sampled E_i vs the oracle."""
+    import torch
+    from paper_2005_00223_gb300.torch_ops import dp_energy
+    cfg = dpsynth.water_config()
+    c0, t0, b0 = dpsynth.water_box(1)
+    coord, typ, box = dpsynth.replicate(c0, t0, b0, (32, 16, 16))
+    p = dpsynth.model_params(cfg, 1)
+    m = dp.Model(cfg, 0, params=p)
+    nl = dp.NeighborList(m, coord, typ, box)
+    x = torch.tensor(coord, dtype=torch.float64, device="cuda", requires_grad=True)
+    E, Ei, F, W = dp_energy(m, nl, x, box, "bf16")
+    (gx,) = torch.autograd.grad(E, x)
+    F = F.cpu().numpy()
+    Ei = Ei.cpu().numpy()
+    assert np.isfinite(F).all() and np.isfinite(Ei).all()
+    np.testing.assert_array_equal(-gx.cpu().numpy(), F)
+    om = orc.Model(cfg, p)
+    nref = nl.get()[0]
+    # periodic replicas of the 192-atom box see identical environments
+    Eb, _, Fb, _ = om.compute(c0, t0, b0)
+    for i in (0, 1, 777, 1572863):
+        Ek, _, _ = om.atom(i, nref[i], coord, typ, box)
+        assert abs(Ei[i] - Ek) < 1e-3 * abs(Ek)
+        assert abs(Ek - om.compute(c0, t0, b0)[1][i % 192]) < 1e-9 * abs(Ek)
+    assert abs(float(E) - 8192 * Eb) < 1e-3 * abs(8192 * Eb)
