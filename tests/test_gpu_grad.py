@@ -167,7 +167,8 @@ def test_water_1p57m_bf16_autograd_sampled(dp, orc):
     assert np.isfinite(F).all() and np.isfinite(Ei).all()
     np.testing.assert_array_equal(-gx.cpu().numpy(), F)
     om = orc.Model(cfg, p)
-    nref = nl.get()[0]
+    nref, _, _ = om.nlist(coord, typ, box)
+    np.testing.assert_array_equal(nl.get()[0], nref)
     # periodic replicas of the 192-atom box see identical environments
     Eb, _, Fb, _ = om.compute(c0, t0, b0)
     for i in (0, 1, 777, 1572863):
