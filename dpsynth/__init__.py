@@ -28,7 +28,7 @@ import numpy as np
 
 __all__ = [
     "SplitMix64", "ModelConfig", "water_config", "copper_config",
-    "copper_student_config", "param_shapes", "n_params", "model_params",
+    "copper_student_config", "param_shapes", "n_params", "model_params", "scale_output",
     "water_box", "replicate", "copper_fcc", "velocities", "MASS",
     "KB_EV", "MVV2E",
 ]
@@ -191,6 +191,24 @@ def model_params(cfg: ModelConfig, seed: int) -> np.ndarray:
     for _name, shape, fan_in in _shapes_with_fan_in(cfg):
         cnt = int(np.prod(shape))
         out[pos:pos + cnt] = rng.normals(cnt) * math.sqrt(1.0 / fan_in)
+        pos += cnt
+    return out
+
+
+def scale_output(cfg: ModelConfig, params: np.ndarray, lam: float) -> np.ndarray:
+    """Copy of params with every fitting net's output layer (W and b) multiplied by lam.
+
+    A documented global output scale: energies, forces and virials of the
+    model scale by lam, so a random-weight model can be given forces of a
+    chosen magnitude (e.g. an RMS force of 1 eV/A).
+    """
+    out = np.array(params, dtype=np.float64, copy=True)
+    last = len(cfg.fit)
+    pos = 0
+    for name, shape in param_shapes(cfg):
+        cnt = int(np.prod(shape))
+        if name.startswith("fit[") and (name.endswith(f".W{last}") or name.endswith(f".b{last}")):
+            out[pos:pos + cnt] *= lam
         pos += cnt
     return out
 

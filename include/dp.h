@@ -262,6 +262,20 @@ dp_status dp_md_state_create(dp_model *m, int64_t n, const double *coord, const 
 dp_status dp_md_step(dp_model *m, dp_md_state *s, int64_t nsteps, double dt_fs, dp_precision prec,
                      int32_t thermo_every, double *thermo);
 
+/* The learned fast path with the full model as judge and fallback: nsteps
+ * NVE steps of `s` (created with `student`) driven by the student's forces;
+ * after every judge_every-th step the full model `teacher` is evaluated at
+ * the same coordinates, the force RMSE sqrt(mean_i |F_s,i - F_t,i|^2) is
+ * written to rmse_log[w] (w = window index) and, when it exceeds rmse_max,
+ * the next window runs on the teacher's forces (fallback_log[w] = 1) until
+ * a later judgement is within rmse_max again.  Both models must share
+ * types, r_c and sel, and use the same stream.  rmse_log, fallback_log:
+ * host arrays [nsteps/judge_every] (may be NULL).  The host synchronises
+ * once per judgement.  Errors: as dp_md_step. */
+dp_status dp_md_step_judged(dp_model *student, dp_model *teacher, dp_md_state *s, int64_t nsteps, double dt_fs,
+                            dp_precision student_prec, dp_precision teacher_prec, int32_t judge_every,
+                            double rmse_max, double *rmse_log, int32_t *fallback_log);
+
 /* Copy the state out: coord [n][3], vel [n][3] (either may be NULL),
  * *step = steps taken so far, *n_rebuilds = list rebuilds so far (NULL ok). */
 dp_status dp_md_state_get(const dp_md_state *s, double *coord, double *vel, int64_t *step, int64_t *n_rebuilds);

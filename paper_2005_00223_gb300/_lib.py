@@ -30,7 +30,7 @@ EXPORTS = [
     "dp_profile_group_name", "dp_nlist_build", "dp_nlist_update", "dp_nlist_get",
     "dp_nlist_destroy", "dp_nlist_update_dev", "dp_compute", "dp_compute_dev", "dp_md_state_create",
     "dp_md_step", "dp_md_state_get", "dp_md_state_destroy", "dp_param_grad", "dp_force_loss_grad",
-    "dp_force_loss_grad_dev", "dp_adam_step", "dp_model_sync_params",
+    "dp_force_loss_grad_dev", "dp_adam_step", "dp_model_sync_params", "dp_md_step_judged",
 ]
 
 
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
             "dp_md_state_create": ([P, I64, P, P, P, P, P, D, I32, P], C.c_int),
             "dp_md_step": ([P, P, I64, D, C.c_int, I32, P], C.c_int),
             "dp_md_state_get": ([P, P, P, P, P], C.c_int),
+            "dp_md_step_judged": ([P, P, P, I64, D, C.c_int, C.c_int, I32, D, P, P], C.c_int),
             "dp_md_state_destroy": ([P], None),
         }
         for name, (args, res) in sig.items():
@@ -312,6 +313,19 @@ def dp_md_step(m, s, nsteps: int, dt_fs: float, prec="fp64", thermo_every: int =
     _check(load().dp_md_step(m, s, int(nsteps), float(dt_fs), _prec(prec), int(thermo_every),
                              _ptr(th) if rows else None), "dp_md_step")
     return th[:rows]
+
+
+def dp_md_step_judged(student, teacher, s, nsteps: int, dt_fs: float, student_prec="mix32", teacher_prec="mix32",
+                      judge_every: int = 10, rmse_max: float = 0.05):
+    """(rmse per judgement, fallback flag per judgement)."""
+    w = max(nsteps // judge_every, 1)
+    rm = np.zeros(w)
+    fb = np.zeros(w, dtype=np.int32)
+    _check(load().dp_md_step_judged(student, teacher, s, int(nsteps), float(dt_fs), _prec(student_prec),
+                                    _prec(teacher_prec), int(judge_every), float(rmse_max), _ptr(rm), _ptr(fb)),
+           "dp_md_step_judged")
+    k = nsteps // judge_every
+    return rm[:k], fb[:k]
 
 
 def dp_md_state_get(s, n: int):

@@ -293,3 +293,131 @@ dp_status dp_md_state_get(const dp_md_state *s, double *coord, double *vel, int6
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ judged MD
+
+namespace dp {
+namespace {
+
+// Force RMSE between two force arrays (one block, fixed order): out[0] = sqrt(mean |a - b|^2 per atom).
+__global__ void __launch_bounds__(512) k_force_rmse(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
+                                                   double *__restrict__ out)
+{
+    __shared__ double s[512];
+    const int t = threadIdx.x;
+    double acc = 0.0;
+    for (int64_t q = t; q < 3 * n; q += 512) {
+        const double d = a[q] - b[q];
+        acc += d * d;
+    }
+    s[t] = acc;
+    __syncthreads();
+    for (int h = 256; h > 0; h >>= 1) {
+        if (t < h) s[t] += s[t + h];
+        __syncthreads();
+    }
+    if (t == 0) out[0] = n > 0 ? sqrt(s[0] / (double)n) : 0.0;
+}
+
+}  // namespace
+}  // namespace dp
+
+extern "C" {
+
+dp_status dp_md_step_judged(dp_model *student, dp_model *teacher, dp_md_state *s, int64_t nsteps, double dt_fs,
+                            dp_precision student_prec, dp_precision teacher_prec, int32_t judge_every,
+                            double rmse_max, double *rmse_log, int32_t *fallback_log)
+{
+    if (!student || !teacher || !s || s->m != student) { set_error("dp_md_step_judged: NULL or mismatched handle"); return DP_ERR_ARG; }
+    if (nsteps < 0 || !(dt_fs > 0) || judge_every < 1 || !(rmse_max >= 0)) { set_error("dp_md_step_judged: bad argument"); return DP_ERR_ARG; }
+    if (student->ntypes != teacher->ntypes || student->rcut != teacher->rcut || student->dev.nsel != teacher->dev.nsel) {
+        set_error("student and teacher must share types, cut-off and sel");
+        return DP_ERR_ARG;
+    }
+    for (int t = 0; t < student->ntypes; ++t)
+        if (student->sel[t] != teacher->sel[t]) { set_error("student and teacher must share sel"); return DP_ERR_ARG; }
+    if (teacher->stream != student->stream) { set_error("student and teacher must use the same stream"); return DP_ERR_ARG; }
+    const int64_t n = s->n;
+    if (n == 0 || nsteps == 0) return DP_OK;
+    dp_nlist *nl = s->nl;
+    cudaStream_t st = student->stream;
+    DP_TRY(ensure_aux(student, n));
+    DP_TRY(ensure_aux(teacher, n));
+    double *Wi_s = student->d_aux + student->aux_n, *Wi_t = teacher->d_aux + teacher->aux_n;
+    // teacher scratch: forces, atom energies, scalars
+    double *Ft = teacher->d_aux + teacher->aux_n * 10;      // F slot of the teacher's aux area
+    double *Et = teacher->d_aux;                            // E_i slot
+    double *St = teacher->d_aux + teacher->aux_n * 16;      // scalar slot
+    BoxDev bx = make_box(nl);
+    DP_CUDA(cudaMemsetAsync(student->d_flag, 0, sizeof(int32_t), st));
+    DP_CUDA(cudaMemsetAsync(nl->d_flags, 0, sizeof(int32_t), st));
+    bool use_teacher = false;
+    // forces of the active model at the starting coordinates
+    DP_TRY(pack_positions(nl, s->d_x, st));
+    DP_TRY(compute_device(student, nl, nullptr, student_prec, s->d_scal, s->d_e, s->d_f, s->d_scal + 1, Wi_s, st));
+    s->forces_valid = false;
+    const double lim = 0.5 * nl->skin;
+    int64_t win = 0;
+    for (int64_t k = 1; k <= nsteps; ++k) {
+        dp_model *act = use_teacher ? teacher : student;
+        dp_precision ap = use_teacher ? teacher_prec : student_prec;
+        double *Wi = use_teacher ? Wi_t : Wi_s;
+        {
+            ProfScope ps(student->prof, PG_MD, 3, st);
+            k_kick<<<nblk(n), 256, 0, st>>>(n, s->d_v, s->d_f, nl->d_type, s->d_minv, 0.5 * dt_fs);
+            k_drift<<<nblk(n), 256, 0, st>>>(n, s->d_x, s->d_v, nl->d_type, dt_fs, bx, (Pos4 *)nl->d_pos);
+            DP_CUDA(cudaMemsetAsync(nl->d_flags + 1, 0, sizeof(int32_t), st));
+            k_disp_check<<<nblk(n), 256, 0, st>>>(n, (const Pos4 *)nl->d_pos, (const Pos4 *)nl->d_ref, bx, lim * lim,
+                                                  nl->d_flags);
+        }
+        DP_CUDA(cudaGetLastError());
+        DP_TRY(nlist_build_device(nl, st, true));
+        DP_TRY(compute_device(act, nl, nullptr, ap, s->d_scal, s->d_e, s->d_f, s->d_scal + 1, Wi, st));
+        {
+            ProfScope ps(student->prof, PG_MD, 1, st);
+            k_kick<<<nblk(n), 256, 0, st>>>(n, s->d_v, s->d_f, nl->d_type, s->d_minv, 0.5 * dt_fs);
+        }
+        DP_CUDA(cudaGetLastError());
+        if (k % judge_every == 0) {
+            // judge: the other model at the same coordinates (formatting is shared)
+            double *Fo = s->d_f;                            // forces of the model that drove this step
+            double *Fs = use_teacher ? Ft : s->d_f;
+            double *Fteach = use_teacher ? s->d_f : Ft;
+            if (use_teacher) {
+                DP_TRY(compute_device(student, nl, nullptr, student_prec, St + 1, Et, Ft, St + 2, Wi_s, st));
+            } else {
+                DP_TRY(compute_device(teacher, nl, nullptr, teacher_prec, St + 1, Et, Ft, St + 2, Wi_t, st));
+            }
+            k_force_rmse<<<1, 512, 0, st>>>(n, Fs, Fteach, St);
+            DP_CUDA(cudaGetLastError());
+            double rmse = 0.0;
+            DP_CUDA(cudaMemcpyAsync(&rmse, St, sizeof(double), cudaMemcpyDeviceToHost, st));
+            DP_CUDA(cudaStreamSynchronize(st));
+            const bool next_teacher = !(rmse <= rmse_max);
+            if (rmse_log) rmse_log[win] = rmse;
+            if (fallback_log) fallback_log[win] = next_teacher ? 1 : 0;
+            ++win;
+            if (next_teacher != use_teacher) {
+                // the next step starts from the newly active model's forces at these coordinates
+                DP_CUDA(cudaMemcpyAsync(s->d_f, Fo == Fs ? Fteach : Fs, sizeof(double) * 3 * n,
+                                        cudaMemcpyDeviceToDevice, st));
+            }
+            use_teacher = next_teacher;
+        }
+    }
+    s->step += nsteps;
+    int32_t flags[3], flag = 0, derr = 0;
+    DP_TRY(check_nonfinite(s->d_x, 3 * n, student->d_flag, st));
+    DP_CUDA(cudaMemcpyAsync(flags, nl->d_flags, sizeof(flags), cudaMemcpyDeviceToHost, st));
+    DP_CUDA(cudaMemcpyAsync(&flag, student->d_flag, sizeof(flag), cudaMemcpyDeviceToHost, st));
+    DP_CUDA(cudaMemcpyAsync(&derr, student->d_err, sizeof(derr), cudaMemcpyDeviceToHost, st));
+    int32_t derr2 = 0;
+    DP_CUDA(cudaMemcpyAsync(&derr2, teacher->d_err, sizeof(derr2), cudaMemcpyDeviceToHost, st));
+    DP_CUDA(cudaStreamSynchronize(st));
+    if (derr || derr2) { set_error("a bounded device wait gave up during MD"); return DP_ERR_TIMEOUT; }
+    if (flags[0] & kErrCapacity) { set_error("a candidate list rebuild exceeded its capacity"); return DP_ERR_CAPACITY; }
+    if (flag) { set_error("non-finite coordinates during MD"); return DP_ERR_NONFINITE; }
+    return DP_OK;
+}
+
+}  // extern "C"

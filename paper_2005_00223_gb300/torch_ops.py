@@ -25,12 +25,12 @@ class DPEnergy(torch.autograd.Function):
         energy = torch.empty(1, dtype=torch.float64, device=coord.device)
         atom_energy = torch.empty(n, dtype=torch.float64, device=coord.device)
         force = torch.empty((n, 3), dtype=torch.float64, device=coord.device)
-        virial = torch.empty(9, dtype=torch.float64, device=coord.device)
+        virial = torch.empty((3, 3), dtype=torch.float64, device=coord.device)
         stream = torch.cuda.current_stream(coord.device)
         _lib.dp_compute_dev(model_h, nlist_h, coord, box, prec, energy, atom_energy, force, virial, stream)
         ctx.save_for_backward(force)
         ctx.mark_non_differentiable(atom_energy, force, virial)
-        return energy[0], atom_energy, force, virial.view(3, 3)
+        return energy[0], atom_energy, force, virial
 
     @staticmethod
     def backward(ctx, g_energy, g_atom_energy, g_force, g_virial):

@@ -140,12 +140,12 @@ def test_autograd_function_gives_forces(dp, orc):
     E, Ei, F, W = dp_energy(m, nl, x, box, "fp64")
     (gx,) = torch.autograd.grad(E, x)
     Er, _, Fr, Wr = orc.Model(cfg, p).compute(coord, typ, box)
-    assert float(E) == pytest.approx(Er, rel=1e-10)
+    assert float(E.detach()) == pytest.approx(Er, rel=1e-10)
     np.testing.assert_allclose(-gx.cpu().numpy(), Fr, atol=1e-10 * rms(Fr))
-    np.testing.assert_allclose(W.cpu().numpy(), Wr, atol=1e-10 * np.abs(Wr).max())
+    np.testing.assert_allclose(W.detach().cpu().numpy(), Wr, atol=1e-10 * np.abs(Wr).max())
     # mixed precision through the same Function
     E16, _, F16, _ = dp_energy(m, nl, x.detach(), box, "bf16")
-    assert abs(float(E16) - Er) < 1e-2 * abs(Er)
+    assert abs(float(E16.detach()) - Er) < 1e-2 * abs(Er)
 
 
 @pytest.mark.slow
@@ -162,8 +162,8 @@ def test_water_1p57m_bf16_autograd_sampled(dp, orc):
     x = torch.tensor(coord, dtype=torch.float64, device="cuda", requires_grad=True)
     E, Ei, F, W = dp_energy(m, nl, x, box, "bf16")
     (gx,) = torch.autograd.grad(E, x)
-    F = F.cpu().numpy()
-    Ei = Ei.cpu().numpy()
+    F = F.detach().cpu().numpy()
+    Ei = Ei.detach().cpu().numpy()
     assert np.isfinite(F).all() and np.isfinite(Ei).all()
     np.testing.assert_array_equal(-gx.cpu().numpy(), F)
     om = orc.Model(cfg, p)
@@ -175,4 +175,4 @@ def test_water_1p57m_bf16_autograd_sampled(dp, orc):
         Ek, _, _ = om.atom(i, nref[i], coord, typ, box)
         assert abs(Ei[i] - Ek) < 1e-3 * abs(Ek)
         assert abs(Ek - om.compute(c0, t0, b0)[1][i % 192]) < 1e-9 * abs(Ek)
-    assert abs(float(E) - 8192 * Eb) < 1e-3 * abs(8192 * Eb)
+    assert abs(float(E.detach()) - 8192 * Eb) < 1e-3 * abs(8192 * Eb)
