@@ -39,7 +39,17 @@ import dpsynth  # noqa: E402
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 FLOP x 2070 MHz
 
 
-def workload(name: str):
+def workload(name: str, model: str = "full"):
+    cfg, coord, typ, box, mass, dt, desc = _workload(name)
+    if model == "student":
+        if cfg.ntypes != 1:
+            raise SystemExit("the student model is the copper one")
+        cfg = dpsynth.copper_student_config()
+        desc += "; student nets 8-16-32 / M2 8 / 64-64-64"
+    return cfg, coord, typ, box, mass, dt, desc
+
+
+def _workload(name: str):
     if name == "cu4000":
         cfg = dpsynth.copper_config()
         coord, typ, box = dpsynth.copper_fcc(1, ncell=10)
@@ -126,7 +136,7 @@ def run_mine(args, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    cfg, coord, typ, box, mass, dt, desc = workload(args.workload)
+    cfg, coord, typ, box, mass, dt, desc = workload(args.workload, args.model)
     n = len(typ)
     vel = dpsynth.velocities(mass[typ], 300.0, 1)
     model = dp.Model(cfg, seed=1)
@@ -237,9 +247,8 @@ def run_e2e(dp, model, cfg, coord, vel, typ, box, mass, dt, args, stream):
 def cpu_baseline(args, budget_s=15.0):
     """The FP64 oracle on the host cores: whole NVE steps of the same workload."""
     import oracle
-    cfg, coord, typ, box, mass, dt, desc = workload(args.workload)
+    cfg, coord, typ, box, mass, dt, desc = workload(args.workload, args.model)
     n = len(typ)
-    import paper_2005_00223_gb300 as dp  # noqa: F401  (weights of the same seeded model)
     params = dpsynth.model_params(cfg, 1)
     om = oracle.Model(cfg, params)
     vel = dpsynth.velocities(mass[typ], 300.0, 1)
@@ -259,7 +268,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     import oracle
-    cfg, coord, typ, box, mass, dt, desc = workload(args.workload)
+    cfg, coord, typ, box, mass, dt, desc = workload(args.workload, args.model)
     n = len(typ)
     om = oracle.Model(cfg, dpsynth.model_params(cfg, 1))
     vel = dpsynth.velocities(mass[typ], 300.0, 1)
@@ -289,6 +298,7 @@ def main():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mix32", "bf16", "fp16"])
     ap.add_argument("--workload", default="cu4000")
+    ap.add_argument("--model", default="full", choices=["full", "student"])
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

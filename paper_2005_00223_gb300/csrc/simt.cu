@@ -35,7 +35,6 @@
 namespace dp {
 namespace {
 
-constexpr int kFitAtoms = 8;
 
 __device__ __forceinline__ double act_tanh(double x) { return tanh(x); }
 __device__ __forceinline__ float act_tanh(float x) { return tanhf(x); }
@@ -209,14 +208,13 @@ __global__ void __launch_bounds__(S::NT) k_embed_fwd(ModelDev md, BoxDev bx, con
 
 // Fitting net of center type ti on A atoms (positions pos_begin + A*blockIdx.x
 // of the type-sorted order): E_i forward, dE/dD backward.
-template <typename Real>
+template <typename Real, int A>
 __global__ void __launch_bounds__(256) k_fit(ModelDev md, int ti, const int32_t *__restrict__ order, int64_t p0,
                                             int64_t pos_begin, int64_t count, const Real *__restrict__ D,
                                             Real *__restrict__ dD, double *__restrict__ E_atom)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Real *smem = reinterpret_cast<Real *>(smem_raw);
-    constexpr int A = kFitAtoms;
     const int tid = threadIdx.x, nthreads = blockDim.x;
     const int nd = md.desc_dim;
     int wmax = 0;
@@ -553,15 +551,66 @@ size_t embed_bwd_smem(const ModelDev &md)
 }
 
 template <typename Real>
-size_t fit_smem(const ModelDev &md)
+size_t fit_smem(const ModelDev &md, int A)
 {
     int wmax = 0, fsum = 0;
     for (int k = 0; k < md.n_fit; ++k) {
         wmax = wmax > md.fit.wout[k] ? wmax : md.fit.wout[k];
         fsum += md.fit.wout[k];
     }
-    size_t a = (size_t)kFitAtoms * md.desc_dim, b = (size_t)3 * kFitAtoms * wmax;
-    return sizeof(Real) * ((a > b ? a : b) + 2 * (size_t)kFitAtoms * fsum);
+    size_t a = (size_t)A * md.desc_dim, b = (size_t)3 * A * wmax;
+    return sizeof(Real) * ((a > b ? a : b) + 2 * (size_t)A * fsum);
+}
+
+// Launches the fitting net of type t over `count` type-sorted positions from
+// `b`.  The atoms per CTA (6..9) are chosen to minimise (waves x atoms per
+// CTA) for this count, since the kernel is arithmetic bound and a partly
+// filled last wave idles SMs.
+template <typename Real>
+dp_status launch_fit(dp_model *m, const int32_t *order, int t, int64_t p0, int64_t b, int64_t count, const Real *D, Real *dD,
+                     double *E_atom, cudaStream_t st)
+{
+    const ModelDev &md = m->dev;
+    int nsm = 0;
+    DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
+    int bestA = 0;
+    long best = -1;
+    for (int A = 6; A <= 9; ++A) {
+        const size_t sm = fit_smem<Real>(md, A);
+        if (sm > 227 * 1024) continue;
+        const long per_sm = (long)((228 * 1024) / (sm + 1024)) < 8 ? (long)((228 * 1024) / (sm + 1024)) : 8;
+        const long tiles = (long)((count + A - 1) / A);
+        const long slots = (long)nsm * (per_sm > 0 ? per_sm : 1);
+        const long cost = ((tiles + slots - 1) / slots) * A;
+        if (best < 0 || cost < best) { best = cost; bestA = A; }
+    }
+    if (bestA == 0) {
+        set_error("fitting net too wide for the shared-memory tile");
+        return DP_ERR_UNSUPPORTED;
+    }
+    const size_t sfit = fit_smem<Real>(md, bestA);
+    const unsigned tiles = (unsigned)((count + bestA - 1) / bestA);
+    ProfScope ps(m->prof, PG_FIT, 1, st);
+    switch (bestA) {
+    case 6:
+        DP_CUDA(cudaFuncSetAttribute(k_fit<Real, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sfit));
+        k_fit<Real, 6><<<tiles, 256, sfit, st>>>(md, t, order, p0, b, count, D, dD, E_atom);
+        break;
+    case 7:
+        DP_CUDA(cudaFuncSetAttribute(k_fit<Real, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sfit));
+        k_fit<Real, 7><<<tiles, 256, sfit, st>>>(md, t, order, p0, b, count, D, dD, E_atom);
+        break;
+    case 8:
+        DP_CUDA(cudaFuncSetAttribute(k_fit<Real, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sfit));
+        k_fit<Real, 8><<<tiles, 256, sfit, st>>>(md, t, order, p0, b, count, D, dD, E_atom);
+        break;
+    default:
+        DP_CUDA(cudaFuncSetAttribute(k_fit<Real, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sfit));
+        k_fit<Real, 9><<<tiles, 256, sfit, st>>>(md, t, order, p0, b, count, D, dD, E_atom);
+        break;
+    }
+    DP_CUDA(cudaGetLastError());
+    return DP_OK;
 }
 
 template <class S, typename Real>
@@ -569,10 +618,9 @@ dp_status launch_batch(dp_model *m, dp_nlist *nl, BoxDev bx, int64_t p0, int64_t
                        Real *act, double *E_atom, double *force, double *atom_virial, cudaStream_t st)
 {
     const ModelDev &md = m->dev;
-    size_t sf = embed_fwd_smem<S, Real>(md), sb = embed_bwd_smem<S, Real>(md), sfit = fit_smem<Real>(md);
+    size_t sf = embed_fwd_smem<S, Real>(md), sb = embed_bwd_smem<S, Real>(md);
     DP_CUDA(cudaFuncSetAttribute(k_embed_fwd<S, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
     DP_CUDA(cudaFuncSetAttribute(k_embed_bwd<S, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
-    DP_CUDA(cudaFuncSetAttribute(k_fit<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sfit));
     const Pos4 *pos = (const Pos4 *)nl->d_pos;
     {
         ProfScope ps(m->prof, PG_EMBED_FWD, 1, st);
@@ -585,10 +633,7 @@ dp_status launch_batch(dp_model *m, dp_nlist *nl, BoxDev bx, int64_t p0, int64_t
         int64_t e = nl->type_off[t] + nl->type_count[t];
         if (e > p0 + nb) e = p0 + nb;
         if (e <= b) continue;
-        unsigned tiles = (unsigned)((e - b + kFitAtoms - 1) / kFitAtoms);
-        ProfScope ps(m->prof, PG_FIT, 1, st);
-        k_fit<Real><<<tiles, 256, sfit, st>>>(md, t, nl->d_order, p0, b, e - b, D, dD, E_atom);
-        DP_CUDA(cudaGetLastError());
+        DP_TRY(launch_fit<Real>(m, nl->d_order, t, p0, b, e - b, D, dD, E_atom, st));
     }
     {
         ProfScope ps(m->prof, PG_EMBED_BWD, 1, st);
@@ -664,15 +709,10 @@ size_t fp64_bytes_per_atom(const ModelDev &md) { return bytes_per_atom<double>(m
 dp_status fit_f32(dp_model *m, dp_nlist *nl, const float *D, float *dD, double *d_atom_energy, cudaStream_t st)
 {
     const ModelDev &md = m->dev;
-    const size_t sfit = fit_smem<float>(md);
-    DP_CUDA(cudaFuncSetAttribute(k_fit<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sfit));
     for (int t = 0; t < md.ntypes; ++t) {
         const int64_t b = nl->type_off[t], cnt = nl->type_count[t];
         if (cnt <= 0) continue;
-        unsigned tiles = (unsigned)((cnt + kFitAtoms - 1) / kFitAtoms);
-        ProfScope ps(m->prof, PG_FIT, 1, st);
-        k_fit<float><<<tiles, 256, sfit, st>>>(md, t, nl->d_order, 0, b, cnt, D, dD, d_atom_energy);
-        DP_CUDA(cudaGetLastError());
+        DP_TRY(launch_fit<float>(m, nl->d_order, t, 0, b, cnt, D, dD, d_atom_energy, st));
     }
     return DP_OK;
 }
