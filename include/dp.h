@@ -269,7 +269,7 @@ dp_status dp_md_step(dp_model *m, dp_md_state *s, int64_t nsteps, double dt_fs, 
  * written to rmse_log[w] (w = window index) and, when it exceeds rmse_max,
  * the next window runs on the teacher's forces (fallback_log[w] = 1) until
  * a later judgement is within rmse_max again.  Both models must share
- * types, r_c and sel, and use the same stream.  rmse_log, fallback_log:
+ * types, r_c and sel; the teacher's work runs on the student's stream.  rmse_log, fallback_log:
  * host arrays [nsteps/judge_every] (may be NULL).  The host synchronises
  * once per judgement.  Errors: as dp_md_step. */
 dp_status dp_md_step_judged(dp_model *student, dp_model *teacher, dp_md_state *s, int64_t nsteps, double dt_fs,

@@ -336,9 +336,17 @@ dp_status dp_md_step_judged(dp_model *student, dp_model *teacher, dp_md_state *s
     }
     for (int t = 0; t < student->ntypes; ++t)
         if (student->sel[t] != teacher->sel[t]) { set_error("student and teacher must share sel"); return DP_ERR_ARG; }
-    if (teacher->stream != student->stream) { set_error("student and teacher must use the same stream"); return DP_ERR_ARG; }
     const int64_t n = s->n;
     if (n == 0 || nsteps == 0) return DP_OK;
+    // the teacher runs on the student's stream for the duration of the call
+    DP_CUDA(cudaStreamSynchronize(teacher->stream));
+    cudaStream_t teacher_stream = teacher->stream;
+    teacher->stream = student->stream;
+    struct Restore {
+        dp_model *t;
+        cudaStream_t s;
+        ~Restore() { t->stream = s; }
+    } restore{teacher, teacher_stream};
     dp_nlist *nl = s->nl;
     cudaStream_t st = student->stream;
     DP_TRY(ensure_aux(student, n));
