@@ -415,6 +415,7 @@ void dp_model_destroy(dp_model *m)
     cudaFree(m->d_flag);
     cudaFree(m->d_err);
     cudaFree(m->d_tcw);
+    cudaFree(m->d_tcfit);
     cudaFree(m->d_train);
     cudaFree(m->d_tscr);
     if (m->own_stream) cudaStreamDestroy(m->own_stream);

@@ -141,6 +141,7 @@ struct dp_model {
     int32_t *d_flag = nullptr;        // [4] non-finite flag and spare
     int32_t *d_err = nullptr;         // [4] device error word (bounded waits that gave up)
     unsigned char *d_tcw = nullptr;   // packed fp16 and bf16 embedding weights for the tensor cores
+    unsigned char *d_tcfit = nullptr; // packed fp16 and bf16 fitting weights for the tensor cores
     uint32_t tc_img_bytes = 0;
     double *d_train = nullptr;        // Adam moments m, v [n_params] each
     double *d_tscr = nullptr;         // scratch of the training calls

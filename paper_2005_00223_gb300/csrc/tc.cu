@@ -24,6 +24,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <vector>
@@ -647,6 +648,319 @@ __global__ void k_dT_f32(ModelDev md, const int32_t *__restrict__ order, int64_t
     dT[(int64_t)a_id * nq + r] = acc * inv * inv;
 }
 
+// Fitting net of the MIX-16 scheme on the tensor cores (tcgen05), fused with
+// the descriptor and its adjoint.  One persistent CTA per SM walks tiles of
+// 128 atoms of one center type (thread = atom row):
+//   D = T T<^T (times 1/sum(sel)^2) is built straight into the A operand,
+//     64 columns at a time, while the tensor core consumes the previous
+//     chunk (two stages; W1^T chunks arrive by bulk copies on the TMA engine);
+//   three hidden layers y_k = skip + tanh(z_k) with M = 128, N = K = F MMAs,
+//     tanh, skip and bias in FP32 epilogues; E_i = y3 . w + b in FP32;
+//   the backward: dz3 = w (1 - t3^2) -> MMA with W3 -> dz2 -> MMA with W2 ->
+//     dz1 -> MMA with W1 in N-chunks -> dE/dD, folded at once into
+//     dE/dT[a][c] = sum_b dD[a][b] T[b][c] + [a < M2] sum_a' dD[a'][a] T[a'][c].
+// D and dE/dD never reach HBM.  Operands are fp16 or bf16, accumulators FP32
+// in TMEM; the last layer and E_i stay FP32 as the paper prescribes.
+
+template <int M1_, int M2_, int F_>
+struct FitShape {
+    static constexpr int M1 = M1_, M2 = M2_, F = F_, D = M1_ * M2_;
+    static constexpr int KC = 64;                       // K chunk of layer 1
+    static constexpr int NK1 = D / KC;
+    static constexpr int NC = (D % 160 == 0) ? 160 : 128;   // N chunk of the layer-1 input gradient
+    static constexpr int NB1 = D / NC;
+    static_assert(D % KC == 0 && D % NC == 0 && NC % M2_ == 0 && KC % M2_ == 0 && 16 % M2_ == 0 && F_ % 16 == 0 &&
+                      F_ <= 256, "fitting tile shape");
+    // packed weight image per center type (bytes)
+    static constexpr uint32_t W1T_OFF = 0;                                  // NK1 x [F][KC]
+    static constexpr uint32_t W2T_OFF = W1T_OFF + NK1 * F * KC * 2;         // [F][F], (o, k) = W2[k][o]
+    static constexpr uint32_t W3T_OFF = W2T_OFF + F * F * 2;
+    static constexpr uint32_t W3B_OFF = W3T_OFF + F * F * 2;                // [F][F], (k, o) = W3[k][o]
+    static constexpr uint32_t W2B_OFF = W3B_OFF + F * F * 2;
+    static constexpr uint32_t W1B_OFF = W2B_OFF + F * F * 2;                // NB1 x [NC][F], (d, o) = W1[d][o]
+    static constexpr uint32_t VEC_OFF = W1B_OFF + NB1 * NC * F * 2;         // b1, b2, b3, w_out [F]; b_out
+    static constexpr uint32_t IMG = VEC_OFF + (4 * F + 4) * 4;
+    // shared memory
+    static constexpr uint32_t ABUF = (128 * F * 2 > 2 * 128 * KC * 2) ? 128 * F * 2 : 2 * 128 * KC * 2;
+    static constexpr uint32_t BB1 = F * F * 2, BB2 = 2 * F * KC * 2, BB3 = NC * F * 2;
+    static constexpr uint32_t BBUF = BB1 > BB2 ? (BB1 > BB3 ? BB1 : BB3) : (BB2 > BB3 ? BB2 : BB3);
+    static constexpr uint32_t A_OFF = 0, B_OFF = ABUF, V_OFF = ABUF + BBUF;
+    static constexpr uint32_t SMEM = V_OFF + (4 * F + 4) * 4;
+};
+
+
+
+template <class S, int BF>
+__global__ void __launch_bounds__(128, 1) k_fit_tc(ModelDev md, const int32_t *__restrict__ order, int64_t pos_begin,
+                                                  int64_t count, const float *__restrict__ T,
+                                                  const unsigned char *__restrict__ img, float *__restrict__ tstore,
+                                                  double *__restrict__ E_atom, float *__restrict__ dT, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_t[2], bar_m[2];
+    __shared__ uint32_t tmem_base;
+    constexpr int F = S::F, KC = S::KC, M2 = S::M2, M1 = S::M1;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    unsigned char *A = smem + S::A_OFF, *B = smem + S::B_OFF;
+    float *vec = reinterpret_cast<float *>(smem + S::V_OFF);
+    const float *b1 = vec, *b2 = vec + F, *b3 = vec + 2 * F, *wo = vec + 3 * F;
+    float *ts = tstore + (int64_t)blockIdx.x * 2 * F * 128;
+    if (tid == 0) {
+        for (int q = 0; q < 2; ++q) {
+            tc::mbar_init(&bar_t[q], 1);
+            tc::mbar_init(&bar_m[q], 1);
+        }
+        tc::mbar_init_fence();
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
+    {
+        const float *gv = reinterpret_cast<const float *>(img + S::VEC_OFF);
+        for (int q = tid; q < 4 * F + 4; q += 128) vec[q] = gv[q];
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tm = tmem_base;
+    const uint32_t trow = tm + ((uint32_t)(warp * 32) << 16);
+    const float bout = vec[4 * F];
+    const float inv2 = (float)(md.inv_nsel * md.inv_nsel);
+    const uint32_t idF = tc::idesc_f16(128, F, BF), idN = tc::idesc_f16(128, S::NC, BF);
+    uint32_t ph_t[2] = {0, 0}, ph_m[2] = {0, 0};
+    bool dead = false;
+    const int64_t ntiles = (count + 127) / 128;
+    // one wait by every thread, then a block-wide vote; false when any thread gave up
+    auto waitv = [&](uint64_t *bar, uint32_t &ph) {
+        bool ok = tc::mbar_wait(bar, ph, kWaitLimit);
+        ph ^= 1;
+        return __syncthreads_and(ok) != 0;
+    };
+    auto mma = [&](uint32_t d, const unsigned char *a, const unsigned char *b, int K, uint32_t id, bool acc0) {
+        const uint32_t sbo = (uint32_t)(K >> 3) * 128;
+        for (int ks = 0; ks < (K >> 4); ++ks) {
+            uint64_t ad = tc::smem_desc(tc::smem_u32(a) + ks * 256, 128, sbo);
+            uint64_t bd = tc::smem_desc(tc::smem_u32(b) + ks * 256, 128, sbo);
+            uint32_t acc = (acc0 || ks > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+                "l"(ad), "l"(bd), "r"(id), "r"(acc));
+        }
+    };
+    auto load_b = [&](int s, uint32_t off, uint32_t bytes, unsigned char *dst) {
+        if (tid == 0) {
+            tc::mbar_expect_tx(&bar_t[s], bytes);
+            tc::bulk_g2s(dst, img + off, bytes, &bar_t[s]);
+        }
+    };
+    // issue one GEMM over the full A tile (K = F) after the A writes of every thread
+    auto gemm_full = [&](uint32_t d, int N_id_is_F) -> bool {
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (!waitv(&bar_t[0], ph_t[0])) return false;
+        if (tid == 0) {
+            tc::fence_after_sync();
+            mma(d, A, B, F, N_id_is_F ? idF : idN, false);
+            tc::mma_commit(&bar_m[0]);
+        }
+        if (!waitv(&bar_m[0], ph_m[0])) return false;
+        tc::fence_after_sync();
+        return true;
+    };
+    for (int64_t tile = blockIdx.x; tile < ntiles && !dead; tile += gridDim.x) {
+        const int64_t r0 = tile * 128 + tid;
+        const bool valid = r0 < count;
+        const int atom = valid ? order[pos_begin + r0] : 0;
+        const float4 *Ta = reinterpret_cast<const float4 *>(T + (int64_t)atom * 4 * M1);
+        float4 tb[M2];
+#pragma unroll
+        for (int b = 0; b < M2; ++b) tb[b] = valid ? Ta[b] : make_float4(0.f, 0.f, 0.f, 0.f);
+        // ---- layer 1: D x W1, K in chunks of 64, two stages
+        for (int kc = 0; kc < S::NK1; ++kc) {
+            const int s = kc & 1;
+            if (kc >= 2 && !waitv(&bar_m[s], ph_m[s])) { dead = true; break; }
+            load_b(s, S::W1T_OFF + (uint32_t)kc * F * KC * 2, F * KC * 2, B + s * F * KC * 2);
+            unsigned char *As = A + s * 128 * KC * 2;
+            // KC is a multiple of M2, so b = (c8 + u) % M2 is known at compile time
+#pragma unroll
+            for (int c8 = 0; c8 < KC; c8 += 8) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int a = (kc * KC) / M2 + (c8 + u) / M2, b = (c8 + u) % M2;
+                    const float4 ta = valid ? Ta[a] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    v[u] = (ta.x * tb[b].x + ta.y * tb[b].y + ta.z * tb[b].z + ta.w * tb[b].w) * inv2;
+                }
+                st_row8<BF>(As, tid, c8, KC, v);
+            }
+            tc::fence_async_smem();
+            tc::fence_before_sync();
+            __syncthreads();
+            if (!waitv(&bar_t[s], ph_t[s])) { dead = true; break; }
+            if (tid == 0) {
+                tc::fence_after_sync();
+                mma(tm, As, B + s * F * KC * 2, KC, idF, kc > 0);
+                tc::mma_commit(&bar_m[s]);
+            }
+        }
+        if (dead) break;
+        for (int kc = (S::NK1 > 2 ? S::NK1 - 2 : 0); kc < S::NK1; ++kc)
+            if (!waitv(&bar_m[kc & 1], ph_m[kc & 1])) { dead = true; break; }
+        if (dead) break;
+        tc::fence_after_sync();
+        load_b(0, S::W2T_OFF, F * F * 2, B);
+        // layer-1 epilogue: t1 = tanh(z + b1) (plain layer), kept for the backward
+#pragma unroll 1
+        for (int c0 = 0; c0 < F; c0 += 16) {
+            float z[16], v[16];
+            tc::tmem_ld16(trow + c0, z);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int k = c0 + u;
+                const float t = tc::tanh_fast(z[u] + b1[k]);
+                ts[k * 128 + tid] = t;
+                v[u] = t;
+            }
+            st_row8<BF>(A, tid, c0, F, v);
+            st_row8<BF>(A, tid, c0 + 8, F, v + 8);
+        }
+        if (!gemm_full(tm, 1)) { dead = true; break; }
+        load_b(0, S::W3T_OFF, F * F * 2, B);
+        // layer-2 epilogue: y2 = t1 + t2
+#pragma unroll 1
+        for (int c0 = 0; c0 < F; c0 += 16) {
+            float z[16], v[16];
+            tc::tmem_ld16(trow + c0, z);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int k = c0 + u;
+                const float t = tc::tanh_fast(z[u] + b2[k]);
+                ts[(F + k) * 128 + tid] = t;
+                v[u] = ts[k * 128 + tid] + t;
+            }
+            st_row8<BF>(A, tid, c0, F, v);
+            st_row8<BF>(A, tid, c0 + 8, F, v + 8);
+        }
+        if (!gemm_full(tm, 1)) { dead = true; break; }
+        load_b(0, S::W3B_OFF, F * F * 2, B);
+        // layer-3 epilogue: y3 = t1 + t2 + t3, E_i = y3 . w + b (FP32), dz3 = w (1 - t3^2)
+        float e = 0.f;
+#pragma unroll 1
+        for (int c0 = 0; c0 < F; c0 += 16) {
+            float z[16], v[16];
+            tc::tmem_ld16(trow + c0, z);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int k = c0 + u;
+                const float t = tc::tanh_fast(z[u] + b3[k]);
+                const float y3 = ts[k * 128 + tid] + ts[(F + k) * 128 + tid] + t;
+                e = fmaf(y3, wo[k], e);
+                v[u] = wo[k] * (1.f - t * t);
+            }
+            st_row8<BF>(A, tid, c0, F, v);
+            st_row8<BF>(A, tid, c0 + 8, F, v + 8);
+        }
+        if (valid) E_atom[atom] = (double)(e + bout);
+        if (!gemm_full(tm, 1)) { dead = true; break; }
+        load_b(0, S::W2B_OFF, F * F * 2, B);
+        // dY2 epilogue: dy2 = dz3 W3^T + w (skip of layer 3), dz2 = dy2 (1 - t2^2); dy2 replaces t2
+#pragma unroll 1
+        for (int c0 = 0; c0 < F; c0 += 16) {
+            float z[16], v[16];
+            tc::tmem_ld16(trow + c0, z);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int k = c0 + u;
+                const float dy2 = z[u] + wo[k];
+                const float t2 = ts[(F + k) * 128 + tid];
+                ts[(F + k) * 128 + tid] = dy2;
+                v[u] = dy2 * (1.f - t2 * t2);
+            }
+            st_row8<BF>(A, tid, c0, F, v);
+            st_row8<BF>(A, tid, c0 + 8, F, v + 8);
+        }
+        if (!gemm_full(tm, 1)) { dead = true; break; }
+        load_b(0, S::W1B_OFF, S::NC * F * 2, B);
+        // dY1 epilogue: dy1 = dz2 W2^T + dy2 (skip of layer 2), dz1 = dy1 (1 - t1^2)
+#pragma unroll 1
+        for (int c0 = 0; c0 < F; c0 += 16) {
+            float z[16], v[16];
+            tc::tmem_ld16(trow + c0, z);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int k = c0 + u;
+                const float dy1 = z[u] + ts[(F + k) * 128 + tid];
+                const float t1 = ts[k * 128 + tid];
+                v[u] = dy1 * (1.f - t1 * t1);
+            }
+            st_row8<BF>(A, tid, c0, F, v);
+            st_row8<BF>(A, tid, c0 + 8, F, v + 8);
+        }
+        // dE/dD = dz1 W1^T in N chunks, folded into dE/dT
+        float4 dtb[M2];
+#pragma unroll
+        for (int b = 0; b < M2; ++b) dtb[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 *dTa = reinterpret_cast<float4 *>(dT + (int64_t)atom * 4 * M1);
+        for (int j = 0; j < S::NB1 && !dead; ++j) {
+            const uint32_t reg = (uint32_t)(j & 1) * 256;
+            if (!gemm_full(tm + reg, 0)) { dead = true; break; }
+            if (j + 1 < S::NB1) load_b(0, S::W1B_OFF + (uint32_t)(j + 1) * S::NC * F * 2, S::NC * F * 2, B);
+#pragma unroll
+            for (int c0 = 0; c0 < S::NC; c0 += 16) {
+                float z[16];
+                tc::tmem_ld16(trow + reg + c0, z);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int h = 0; h < 16; h += M2 < 16 ? M2 : 16) {
+                    const int a = (j * S::NC) / M2 + (c0 + h) / M2;
+                    const float4 ta = valid ? Ta[a] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int u = 0; u < (M2 < 16 ? M2 : 16); ++u) {
+                        const int b = (c0 + h + u) % M2;
+                        const float dd = z[h + u];
+                        acc.x = fmaf(dd, tb[b].x, acc.x);
+                        acc.y = fmaf(dd, tb[b].y, acc.y);
+                        acc.z = fmaf(dd, tb[b].z, acc.z);
+                        acc.w = fmaf(dd, tb[b].w, acc.w);
+                        dtb[b].x = fmaf(dd, ta.x, dtb[b].x);
+                        dtb[b].y = fmaf(dd, ta.y, dtb[b].y);
+                        dtb[b].z = fmaf(dd, ta.z, dtb[b].z);
+                        dtb[b].w = fmaf(dd, ta.w, dtb[b].w);
+                    }
+                    // an M2-wide block of columns completes the first term of dE/dT for row a
+                    if (valid) dTa[a] = make_float4(acc.x * inv2, acc.y * inv2, acc.z * inv2, acc.w * inv2);
+                }
+            }
+        }
+        if (dead) break;
+        if (valid) {
+#pragma unroll
+            for (int b = 0; b < M2; ++b) {
+                float4 o = dTa[b];
+                o.x += dtb[b].x * inv2;
+                o.y += dtb[b].y * inv2;
+                o.z += dtb[b].z * inv2;
+                o.w += dtb[b].w * inv2;
+                dTa[b] = o;
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    if (dead && tid == 0) atomicOr(err, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tm, 512);
+}
+
+
 template <class S>
 void pack_net(const double *p, const NetLayout &L, int bf16, unsigned char *out)
 {
@@ -703,6 +1017,110 @@ dp_status pack_all(dp_model *m)
     return DP_OK;
 }
 
+
+template <class FS>
+void pack_fit_net(const double *p, const NetLayout &L, int bf16, unsigned char *out)
+{
+    memset(out, 0, FS::IMG);
+    auto put = [&](uint32_t base, int r, int k, int K, float v) {
+        uint16_t h;
+        if (bf16) {
+            __nv_bfloat16 b = __float2bfloat16_rn(v);
+            memcpy(&h, &b, 2);
+        } else {
+            __half b = __float2half_rn(v);
+            memcpy(&h, &b, 2);
+        }
+        memcpy(out + base + tc::kmaj_off(r, k, K), &h, 2);
+    };
+    constexpr int F = FS::F, KC = FS::KC, NC = FS::NC;
+    const double *W1 = p + L.W[0], *W2 = p + L.W[1], *W3 = p + L.W[2];
+    for (int d = 0; d < FS::D; ++d)
+        for (int o = 0; o < F; ++o) {
+            const float w = (float)W1[(int64_t)d * F + o];
+            put(FS::W1T_OFF + (uint32_t)(d / KC) * F * KC * 2, o, d % KC, KC, w);   // B[n = o][k = d]
+            put(FS::W1B_OFF + (uint32_t)(d / NC) * NC * F * 2, d % NC, o, F, w);    // B[n = d][k = o]
+        }
+    for (int k = 0; k < F; ++k)
+        for (int o = 0; o < F; ++o) {
+            const float w2 = (float)W2[k * F + o], w3 = (float)W3[k * F + o];
+            put(FS::W2T_OFF, o, k, F, w2);
+            put(FS::W3T_OFF, o, k, F, w3);
+            put(FS::W2B_OFF, k, o, F, w2);
+            put(FS::W3B_OFF, k, o, F, w3);
+        }
+    float *vec = reinterpret_cast<float *>(out + FS::VEC_OFF);
+    for (int k = 0; k < F; ++k) {
+        vec[k] = (float)p[L.b[0] + k];
+        vec[F + k] = (float)p[L.b[1] + k];
+        vec[2 * F + k] = (float)p[L.b[2] + k];
+        vec[3 * F + k] = (float)p[L.W[3] + k];
+    }
+    vec[4 * F] = (float)p[L.b[3]];
+}
+
+template <class FS>
+dp_status pack_fit_all(dp_model *m)
+{
+    const ModelDev &md = m->dev;
+    std::vector<unsigned char> img((size_t)2 * md.ntypes * FS::IMG);
+    for (int bf = 0; bf < 2; ++bf)
+        for (int t = 0; t < md.ntypes; ++t)
+            pack_fit_net<FS>(m->h_params.data() + md.fit_base + t * md.fit.size, md.fit, bf,
+                             img.data() + ((size_t)bf * md.ntypes + t) * FS::IMG);
+    if (!m->d_tcfit) DP_CUDA(cudaMalloc((void **)&m->d_tcfit, img.size()));
+    DP_CUDA(cudaMemcpyAsync(m->d_tcfit, img.data(), img.size(), cudaMemcpyHostToDevice, m->stream));
+    DP_CUDA(cudaStreamSynchronize(m->stream));
+    return DP_OK;
+}
+
+using FitWater = FitShape<100, 16, 240>;
+using FitStudent = FitShape<32, 8, 64>;
+using FitPaper = FitShape<128, 16, 240>;
+
+// The fused tensor-core fitting kernel covers three equal hidden widths F
+// after a plain first layer (the configs' 240-240-240 and 64-64-64).
+int fit_tc_kind(const ModelDev &md)
+{
+    if (md.n_fit != 3 || md.fit.wout[0] != md.fit.wout[1] || md.fit.wout[1] != md.fit.wout[2]) return 0;
+    const int F = md.fit.wout[0];
+    if (md.m1 == 100 && md.m2 == 16 && F == 240) return 1;
+    if (md.m1 == 32 && md.m2 == 8 && F == 64) return 2;
+    if (md.m1 == 128 && md.m2 == 16 && F == 240) return 3;
+    return 0;
+}
+
+template <class FS, int BF>
+dp_status launch_fit_tc(dp_model *m, dp_nlist *nl, const float *T, float *tstore, int grid, double *E_atom,
+                        float *dT, cudaStream_t st)
+{
+    const ModelDev &md = m->dev;
+    DP_CUDA(cudaFuncSetAttribute(k_fit_tc<FS, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FS::SMEM));
+    for (int t = 0; t < md.ntypes; ++t) {
+        const int64_t b = nl->type_off[t], cnt = nl->type_count[t];
+        if (cnt <= 0) continue;
+        const int64_t tiles = (cnt + 127) / 128;
+        const unsigned g = (unsigned)(tiles < grid ? tiles : grid);
+        const unsigned char *img = m->d_tcfit + ((size_t)BF * md.ntypes + t) * FS::IMG;
+        ProfScope ps(m->prof, PG_FIT, 1, st);
+        k_fit_tc<FS, BF><<<g, 128, FS::SMEM, st>>>(md, nl->d_order, b, cnt, T, img, tstore, E_atom, dT, m->d_err);
+        DP_CUDA(cudaGetLastError());
+    }
+    return DP_OK;
+}
+
+template <int BF>
+dp_status fit_tc(dp_model *m, dp_nlist *nl, const float *T, float *tstore, int grid, double *E_atom, float *dT,
+                 cudaStream_t st)
+{
+    switch (fit_tc_kind(m->dev)) {
+    case 1: return launch_fit_tc<FitWater, BF>(m, nl, T, tstore, grid, E_atom, dT, st);
+    case 2: return launch_fit_tc<FitStudent, BF>(m, nl, T, tstore, grid, E_atom, dT, st);
+    case 3: return launch_fit_tc<FitPaper, BF>(m, nl, T, tstore, grid, E_atom, dT, st);
+    default: set_error("no tensor-core fitting kernel for this shape"); return DP_ERR_UNSUPPORTED;
+    }
+}
+
 template <class S, int BF>
 dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
                  double *d_virial, double *d_atom_virial, cudaStream_t st)
@@ -721,6 +1139,11 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     sz(sizeof(int4) * max_chunks);
     sz(sizeof(int) * 4);
     sz(sizeof(int64_t) * 2 * kMaxTypes);
+    int nsm = 0;
+    DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
+    const bool tcfit = fit_tc_kind(md) != 0 && getenv("DP_SIMT_FIT") == nullptr;
+    const int fgrid = nsm;
+    if (tcfit) sz(sizeof(float) * (size_t)fgrid * 2 * 256 * 128);
     DP_TRY(ensure_workspace(m, need));
     char *w = m->ws;
     auto carve = [&](size_t bytes) {
@@ -735,6 +1158,7 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     int4 *chunks = (int4 *)carve(sizeof(int4) * max_chunks);
     int *cnt = (int *)carve(sizeof(int) * 4);
     int64_t *ttab = (int64_t *)carve(sizeof(int64_t) * 2 * kMaxTypes);
+    float *tstore = tcfit ? (float *)carve(sizeof(float) * (size_t)fgrid * 2 * 256 * 128) : nullptr;
     int64_t htab[2 * kMaxTypes] = {0};
     for (int t = 0; t < md.ntypes; ++t) {
         htab[t] = nl->type_off[t];
@@ -747,8 +1171,6 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     const unsigned char *wimg = m->d_tcw + (size_t)BF * nn * S::IMG;
     BoxDev bx = make_box(nl);
     const Pos4 *pos = (const Pos4 *)nl->d_pos;
-    int nsm = 0;
-    DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
     const unsigned grid = (unsigned)(2 * nsm);
     {
         ProfScope ps(m->prof, PG_CHUNKS, 1, st);
@@ -764,17 +1186,21 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     }
     DP_CUDA(cudaGetLastError());
     const int64_t nd = (int64_t)md.desc_dim * n, nq = (int64_t)4 * md.m1 * n;
-    {
-        ProfScope ps(m->prof, PG_DESC, 1, st);
-        k_desc_f32<<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(md, nl->d_order, n, T, D);
+    if (tcfit) {
+        DP_TRY(fit_tc<BF>(m, nl, T, tstore, fgrid, d_atom_energy, dT, st));
+    } else {
+        {
+            ProfScope ps(m->prof, PG_DESC, 1, st);
+            k_desc_f32<<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(md, nl->d_order, n, T, D);
+        }
+        DP_CUDA(cudaGetLastError());
+        DP_TRY(fit_f32(m, nl, D, dD, d_atom_energy, st));
+        {
+            ProfScope ps(m->prof, PG_DESC, 1, st);
+            k_dT_f32<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(md, nl->d_order, n, T, dD, dT);
+        }
+        DP_CUDA(cudaGetLastError());
     }
-    DP_CUDA(cudaGetLastError());
-    DP_TRY(fit_f32(m, nl, D, dD, d_atom_energy, st));
-    {
-        ProfScope ps(m->prof, PG_DESC, 1, st);
-        k_dT_f32<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(md, nl->d_order, n, T, dD, dT);
-    }
-    DP_CUDA(cudaGetLastError());
     {
         ProfScope ps(m->prof, PG_EMBED_BWD, 1, st);
         k_embed_bwd_tc<S, BF><<<grid, kTcThreads, S::BWD_SMEM, st>>>(md, bx, pos, nl->d_nlist, nl->d_nnei, chunks,
@@ -790,9 +1216,15 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
 dp_status pack_tc_weights(dp_model *m)
 {
     const int *e = m->dev.emb.wout;
-    if (e[0] == 25) return pack_all<TcWater>(m);
-    if (e[0] == 8) return pack_all<TcStudent>(m);
-    return pack_all<TcPaper>(m);
+    if (e[0] == 25) DP_TRY(pack_all<TcWater>(m));
+    else if (e[0] == 8) DP_TRY(pack_all<TcStudent>(m));
+    else DP_TRY(pack_all<TcPaper>(m));
+    switch (fit_tc_kind(m->dev)) {
+    case 1: return pack_fit_all<FitWater>(m);
+    case 2: return pack_fit_all<FitStudent>(m);
+    case 3: return pack_fit_all<FitPaper>(m);
+    default: return DP_OK;
+    }
 }
 
 dp_status compute_mix16(dp_model *m, dp_nlist *nl, int bf16, double *d_energy, double *d_atom_energy,

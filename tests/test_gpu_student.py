@@ -46,12 +46,16 @@ def test_student_distillation_and_judge(dp):
     print(f"RMS F {frms:.4g} eV/A; student force RMSE untrained {r0:.4g} ({r0 / frms:.3f} of RMS F), "
           f"trained {r1:.4g} ({r1 / frms:.3f}); loss log {log[:2]} ... {log[-2:]}")
     assert np.isfinite(r1) and r1 < 0.5 * r0
-    # judged MD: the untrained student is rejected at every judgement
+    # judged MD at 300 K: threshold 10% of the teacher's RMS force at the start;
+    # the untrained student is rejected at every judgement
+    nl0 = dp.NeighborList(teacher, coord, typ, box)
+    F0 = nl0.compute(coord, box, "mix32")[2]
+    rmse_max = 0.1 * float(np.sqrt((F0 ** 2).sum(1).mean()))
     fresh = dp.Model(dpsynth.copper_student_config(), seed=2)
     for model, expect_all in ((fresh, True), (stu, False)):
         st = dp.MDState(model, coord, vels[0], typ, mass, box, skin=2.0)
         rm, fb = dp.dp_md_step_judged(model.h, teacher.h, st.h, 60, 1.0, "mix32", "mix32", judge_every=10,
-                                      rmse_max=0.5 * r0)
+                                      rmse_max=rmse_max)
         print("judged", "untrained" if expect_all else "trained", rm, fb)
         assert len(rm) == 6 and np.isfinite(rm).all()
         if expect_all:
