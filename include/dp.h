@@ -175,6 +175,30 @@ dp_status dp_nlist_get(const dp_nlist *nl, int32_t *nlist, int64_t *n_truncated)
 
 void dp_nlist_destroy(dp_nlist *nl);
 
+/* Formatted neighbor list that allocates no device memory.  The paper has
+ * no counterpart: this entry point serves callers that cannot allocate
+ * device memory, such as a host MD engine whose device memory belongs to
+ * its own pool or to a framework's caching allocator, or code that must not
+ * let cudaMalloc / cudaFree synchronise the device.  It computes the same
+ * canonical list as dp_nlist_build + dp_nlist_get (r < rcut, type blocks of
+ * sel_t slots ordered by (floor(r * 1e8), index), -1 padded), from a cell
+ * grid held in a fixed static device array of about 1.5 MB that every GPU
+ * loading the library keeps until exit.
+ *   n <= 131072 atoms, else DP_ERR_ARG; at most 1024 neighbors within rcut
+ *   per atom (more sets *d_status = 1 and the list of that atom is partial).
+ *   d_coord [n][3], d_type [n] (0..ntypes-1; other values set *d_status = 1
+ *   and are left out), d_nlist [n][sum(sel)] output, *d_ntrunc output
+ *   (neighbors dropped by full blocks), *d_status output (0 = fine): all
+ *   device memory owned by the caller; box, sel: host arrays.
+ *   Enqueued on `stream` without host synchronisation.  The first call on
+ *   a device looks up the static array's device address (a synchronous
+ *   runtime call); make that first call before any stream capture.  Every
+ *   call reuses the same static array, so calls that overlap on the GPU
+ *   (different streams, or different host threads) race: serialise them. */
+dp_status dp_nlist_format_noalloc(int64_t n, const double *d_coord, const int32_t *d_type, const double box[9],
+                                  double rcut, int32_t ntypes, const int32_t *sel, int32_t *d_nlist,
+                                  unsigned long long *d_ntrunc, int32_t *d_status, void *stream);
+
 /* -------------------------------------------------------------- compute */
 
 /* Energy, per-atom energies, forces and virial at coordinates coord [n][3]

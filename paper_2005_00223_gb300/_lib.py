@@ -31,6 +31,7 @@ EXPORTS = [
     "dp_nlist_destroy", "dp_nlist_update_dev", "dp_compute", "dp_compute_dev", "dp_md_state_create",
     "dp_md_step", "dp_md_state_get", "dp_md_state_destroy", "dp_param_grad", "dp_force_loss_grad",
     "dp_force_loss_grad_dev", "dp_adam_step", "dp_model_sync_params", "dp_md_step_judged",
+    "dp_nlist_format_noalloc",
 ]
 
 
@@ -77,6 +78,7 @@ def load(path: str = LIB_PATH):
             "dp_nlist_get": ([P, P, P], C.c_int),
             "dp_nlist_destroy": ([P], None),
             "dp_nlist_update_dev": ([P, P, P], C.c_int),
+            "dp_nlist_format_noalloc": ([I64, P, P, P, D, I32, P, P, P, P, P], C.c_int),
             "dp_param_grad": ([P, P, P, P, P, D, D, C.c_int, P, P, P], C.c_int),
             "dp_force_loss_grad": ([P, P, P, P, P, D, D, D, C.c_int, P, P], C.c_int),
             "dp_force_loss_grad_dev": ([P, P, P, P, P, P, D, D, C.c_int, P, P, P], C.c_int),
@@ -227,6 +229,14 @@ def _stream(stream):
 
 def dp_nlist_update_dev(nl, d_coord, stream=None):
     _check(load().dp_nlist_update_dev(nl, _ptr(d_coord), _stream(stream)), "dp_nlist_update_dev")
+
+
+def dp_nlist_format_noalloc(d_coord, d_type, box, rcut: float, sel, d_nlist, d_ntrunc, d_status, stream=None):
+    """Formatted list into caller-owned device buffers; the library allocates nothing."""
+    sel = _i32(sel)
+    _check(load().dp_nlist_format_noalloc(int(d_type.numel()), _ptr(d_coord), _ptr(d_type), _ptr(_box(box)),
+                                          float(rcut), int(sel.size), _ptr(sel), _ptr(d_nlist), _ptr(d_ntrunc),
+                                          _ptr(d_status), _stream(stream)), "dp_nlist_format_noalloc")
 
 
 def dp_nlist_destroy(nl):
