@@ -109,7 +109,7 @@ dp_status compute_device(dp_model *m, dp_nlist *nl, const double *d_coord, dp_pr
                          double *d_atom_energy, double *d_force, double *d_virial, double *d_atom_virial,
                          cudaStream_t st)
 {
-    DP_TRY(nlist_format_device(m, nl, d_coord, st));
+    DP_TRY(nlist_format_device(m, nl, d_coord, st, prec == DP_MIX_BF16 || prec == DP_MIX_FP16));
     if (nl->n == 0) {
         DP_CUDA(cudaMemsetAsync(d_energy, 0, sizeof(double), st));
         if (d_virial) DP_CUDA(cudaMemsetAsync(d_virial, 0, 9 * sizeof(double), st));
@@ -314,6 +314,7 @@ dp_status dp_model_create(const dp_model_config *cfg, uint64_t seed, dp_model **
     md.chunks_per_atom = coff;
     md.rcut = m->rcut;
     md.rcs = m->rcs;
+    md.inv_sw = 1.0 / (m->rcut - m->rcs);
     md.inv_nsel = 1.0 / (double)nsel;
     md.emb = make_layout(1, m->n_embed, m->embed, false);
     md.fit = make_layout(md.desc_dim, m->n_fit, m->fit, true);
@@ -440,6 +441,8 @@ static void nlist_free(dp_nlist *nl)
     cudaFree(nl->d_ntrunc);
     cudaFree(nl->d_flags);
     cudaFree(nl->d_pos);
+    cudaFree(nl->d_posf);
+    cudaFree(nl->d_env);
     cudaFree(nl->d_coord);
     cudaFree(nl->d_order);
 }
@@ -527,6 +530,7 @@ dp_status dp::nlist_create_internal(const dp_model *m, int64_t n, const int32_t 
     A((void **)&nl->d_ntrunc, sizeof(unsigned long long));
     A((void **)&nl->d_flags, sizeof(int32_t) * 4);
     A((void **)&nl->d_pos, sizeof(double) * 4 * nn);
+    A((void **)&nl->d_posf, sizeof(float) * 4 * nn);
     A((void **)&nl->d_coord, sizeof(double) * 3 * nn);
     A((void **)&nl->d_order, sizeof(int32_t) * nn);
     if (e != cudaSuccess) {

@@ -56,6 +56,7 @@ struct ModelDev {
     int chunk_off[kMaxTypes + 1];   // chunk index where each type block starts
     int chunks_per_atom;            // sum_t ceil(sel_t / 32)
     double rcut, rcs;
+    double inv_sw;                  // 1 / (rcut - rcs)
     double inv_nsel;
     NetLayout emb;                  // layout of every embedding net (all alike)
     NetLayout fit;                  // layout of every fitting net, incl. the output layer
@@ -170,6 +171,8 @@ struct dp_nlist {
     unsigned long long *d_ntrunc = nullptr;
     int32_t *d_flags = nullptr;       // [0] error bits, [1] rebuild needed, [2] rebuild count
     double *d_pos = nullptr;          // [n][4] packed current coordinates (x, y, z, type)
+    float *d_posf = nullptr;          // [n][4] FP32 copy of the coordinates (prefilter of the formatting)
+    float *d_env = nullptr;           // tensor-core geometry (lazy): [n][nsel] float4 (s, u), then [n][nsel] float2 (ds/dr, r)
     double *d_coord = nullptr;        // [n][3] staging for host-pointer calls
     int32_t *d_order = nullptr;       // [n] atom indices sorted by type (stable)
     std::vector<int64_t> type_count, type_off;
@@ -198,7 +201,8 @@ namespace dp {
 
 // Launchers (return DP_OK or an error after recording a message).
 dp_status nlist_build_device(dp_nlist *nl, cudaStream_t st, bool conditional);
-dp_status nlist_format_device(const dp_model *m, dp_nlist *nl, const double *d_coord, cudaStream_t st);
+dp_status nlist_format_device(const dp_model *m, dp_nlist *nl, const double *d_coord, cudaStream_t st,
+                              bool with_env = false);
 dp_status pack_positions(dp_nlist *nl, const double *d_coord, cudaStream_t st);
 dp_status compute_fp64(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
                        double *d_virial, double *d_atom_virial, cudaStream_t st);

@@ -47,6 +47,16 @@ __device__ __forceinline__ double min_image_r(const Pos4 a, const Pos4 b, const 
     return __dsqrt_rn(r2);
 }
 
+// FP32 copy of a position wrapped into [0, L) in FP64 (so its rounding error
+// is bounded by the box, whatever the raw coordinate), type bits in w.
+__device__ __forceinline__ float4 wrapped_f32(const double *x, int32_t type, const BoxDev &bx)
+{
+    float w[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) w[k] = (float)(x[k] - bx.L[k] * floor(x[k] * bx.invL[k]));
+    return make_float4(w[0], w[1], w[2], __int_as_float(type));
+}
+
 // Switching function of the environment matrix: s = 1/r below r_cs,
 // (1/r)(u^3(-6u^2 + 15u - 10) + 1) with u = (r - r_cs)/(r_c - r_cs) up to
 // r_c, 0 beyond; *ds = ds/dr.  The quintic is twice continuously

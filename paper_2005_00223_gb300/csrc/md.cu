@@ -33,7 +33,7 @@ __global__ void k_kick(int64_t n, double *__restrict__ v, const double *__restri
 
 // x += dt v, wrapped into [0, L); the packed position array is refreshed too.
 __global__ void k_drift(int64_t n, double *__restrict__ x, const double *__restrict__ v, const int32_t *__restrict__ type,
-                        double dt, BoxDev bx, Pos4 *__restrict__ pos)
+                        double dt, BoxDev bx, Pos4 *__restrict__ pos, float4 *__restrict__ posf)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -46,6 +46,7 @@ __global__ void k_drift(int64_t n, double *__restrict__ x, const double *__restr
         p[k] = y;
     }
     pos[i] = Pos4{p[0], p[1], p[2], (double)type[i]};
+    posf[i] = wrapped_f32(p, type[i], bx);
 }
 
 // flags[1] = 1 when some atom moved more than half the skin since the last build.
@@ -229,7 +230,8 @@ dp_status dp_md_step(dp_model *m, dp_md_state *s, int64_t nsteps, double dt_fs, 
         {
             ProfScope ps(m->prof, PG_MD, 3, st);
             k_kick<<<nblk(n), 256, 0, st>>>(n, s->d_v, s->d_f, nl->d_type, s->d_minv, 0.5 * dt_fs);
-            k_drift<<<nblk(n), 256, 0, st>>>(n, s->d_x, s->d_v, nl->d_type, dt_fs, bx, (Pos4 *)nl->d_pos);
+            k_drift<<<nblk(n), 256, 0, st>>>(n, s->d_x, s->d_v, nl->d_type, dt_fs, bx, (Pos4 *)nl->d_pos,
+                                                  (float4 *)nl->d_posf);
             DP_CUDA(cudaMemsetAsync(nl->d_flags + 1, 0, sizeof(int32_t), st));
             k_disp_check<<<nblk(n), 256, 0, st>>>(n, (const Pos4 *)nl->d_pos, (const Pos4 *)nl->d_ref, bx,
                                               lim * lim, nl->d_flags);
@@ -373,7 +375,8 @@ dp_status dp_md_step_judged(dp_model *student, dp_model *teacher, dp_md_state *s
         {
             ProfScope ps(student->prof, PG_MD, 3, st);
             k_kick<<<nblk(n), 256, 0, st>>>(n, s->d_v, s->d_f, nl->d_type, s->d_minv, 0.5 * dt_fs);
-            k_drift<<<nblk(n), 256, 0, st>>>(n, s->d_x, s->d_v, nl->d_type, dt_fs, bx, (Pos4 *)nl->d_pos);
+            k_drift<<<nblk(n), 256, 0, st>>>(n, s->d_x, s->d_v, nl->d_type, dt_fs, bx, (Pos4 *)nl->d_pos,
+                                                  (float4 *)nl->d_posf);
             DP_CUDA(cudaMemsetAsync(nl->d_flags + 1, 0, sizeof(int32_t), st));
             k_disp_check<<<nblk(n), 256, 0, st>>>(n, (const Pos4 *)nl->d_pos, (const Pos4 *)nl->d_ref, bx, lim * lim,
                                                   nl->d_flags);

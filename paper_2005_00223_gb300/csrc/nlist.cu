@@ -32,12 +32,13 @@ __device__ __forceinline__ int cell_coord(double x, double invL, int nc)
     return c >= nc ? nc - 1 : (c < 0 ? 0 : c);
 }
 
-__global__ void k_pack(int64_t n, const double *__restrict__ coord, const int32_t *__restrict__ type,
-                       Pos4 *__restrict__ pos)
+__global__ void k_pack(int64_t n, const double *__restrict__ coord, const int32_t *__restrict__ type, BoxDev bx,
+                       Pos4 *__restrict__ pos, float4 *__restrict__ posf)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     pos[i] = Pos4{coord[3 * i], coord[3 * i + 1], coord[3 * i + 2], (double)type[i]};
+    posf[i] = wrapped_f32(coord + 3 * i, type[i], bx);
 }
 
 // flags[1] gates the conditional (MD) rebuild: kernels return at once when
@@ -160,41 +161,107 @@ __global__ void k_candidates(int64_t n, const Pos4 *__restrict__ pos, BoxDev bx,
     if (i == 0 && lane == 0) atomicAdd(&flags[2], 1);
 }
 
-// One warp per atom; keys of the atom's real neighbors staged in shared
-// memory (cap per warp).  Slot of a key = number of smaller keys minus the
-// keys of lower types.
-__global__ void k_format(int64_t n, const Pos4 *__restrict__ pos, BoxDev bx, ModelDev md,
-                         const int32_t *__restrict__ cand, const int32_t *__restrict__ cand_cnt, int32_t cap,
-                         int32_t *__restrict__ nlist, int32_t *__restrict__ nnei, unsigned long long *ntrunc)
+// One warp per atom, three stages.  (A) FP32 prefilter on wrapped FP32
+// coordinates: candidates within r_c plus a margin far above its error are
+// compacted into a list of (type << 26 | j).  (B) The exact FP64
+// minimum-image distance on the compacted list (dense warps); keys of the
+// atoms within r_c are staged in shared memory.  (C) Slot of a key = number
+// of smaller keys minus the keys of lower types.  With env != NULL stage B
+// also computes the geometry of each kept neighbor for the tensor-core path
+// from the exact FP64 difference and distance, staged beside the keys: the
+// switching function s(r) and ds/dr in FP64, stored as FP32 in two planes,
+// (s, u_x, u_y, u_z) with u = d/r at env[slot] and (ds/dr, r) at
+// env + 4 n nsel.  Shared memory per warp (cap2 = cap rounded up to even):
+// keys [cap2] u64, then either the list [cap2] u32 (no env) or the records
+// recA [cap2] float4 and recB [cap2] float2 with the list in the tail of
+// recA: stage B reads entry p of its iteration before writing record q <= p,
+// and record q ends below every later entry p' (16 (q + 1) <= 4 (4 cap2 - nc + p')).
+__global__ void k_format(int64_t n, const Pos4 *__restrict__ pos, const float4 *__restrict__ posf, BoxDev bx,
+                         ModelDev md, const int32_t *__restrict__ cand, const int32_t *__restrict__ cand_cnt,
+                         int32_t cap, int32_t *__restrict__ nlist, int32_t *__restrict__ nnei,
+                         unsigned long long *ntrunc, float *__restrict__ env)
 {
     extern __shared__ unsigned long long keys_all[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
-    unsigned long long *keys = keys_all + (int64_t)warp * cap;
+    const int cap2 = (cap + 1) & ~1;
+    const int per_warp = env ? 4 * cap2 : cap2 + cap2 / 2;   // 8-byte words
+    unsigned long long *keys = keys_all + (int64_t)warp * per_warp;
+    float4 *recA = reinterpret_cast<float4 *>(keys + cap2);
+    float2 *recB = reinterpret_cast<float2 *>(keys + 3 * cap2);
     const Pos4 pi = pos[i];
+    const float4 pf = posf[i];
     const int32_t nc = cand_cnt[i];
     const int32_t *row = cand + i * (int64_t)cap;
+    uint32_t *list =
+        env ? reinterpret_cast<uint32_t *>(recA) + 4 * cap2 - nc : reinterpret_cast<uint32_t *>(keys + cap2);
+    const unsigned lt = (1u << lane) - 1u;
+    // (A) prefilter
+    int nf = 0;
+    {
+        const float Lf[3] = {(float)bx.L[0], (float)bx.L[1], (float)bx.L[2]};
+        const float iLf[3] = {(float)bx.invL[0], (float)bx.invL[1], (float)bx.invL[2]};
+        const float rpre = (float)md.rcut + 2e-3f;
+        for (int base = 0; base < nc; base += 32) {
+            const int c = base + lane;
+            bool pass = false;
+            uint32_t e = 0;
+            if (c < nc) {
+                const int32_t j = row[c];
+                const float4 qf = posf[j];
+                float df[3] = {qf.x - pf.x, qf.y - pf.y, qf.z - pf.z};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) df[k] -= Lf[k] * rintf(df[k] * iLf[k]);
+                const float r2f = df[0] * df[0] + df[1] * df[1] + df[2] * df[2];
+                pass = j != i && r2f < rpre * rpre;
+                e = ((uint32_t)__float_as_int(qf.w) << 26) | (uint32_t)j;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, pass);
+            if (pass) list[nf + __popc(m & lt)] = e;
+            nf += __popc(m);
+        }
+    }
+    __syncwarp();
+    // (B) exact distances on the dense list
     int nk = 0;
-    for (int base = 0; base < nc; base += 32) {
-        int c = base + lane;
+    for (int base = 0; base < nf; base += 32) {
+        const int p = base + lane;
+        const uint32_t e = p < nf ? list[p] : 0u;
+        __syncwarp();
+        const int32_t j = (int32_t)(e & ((1u << 26) - 1u));
         bool ok = false;
-        unsigned long long key = 0;
-        if (c < nc) {
-            int32_t j = row[c];
-            Pos4 pj = pos[j];
-            double d[3];
-            double r = min_image_r(pi, pj, bx, d);
-            if (j != i && r < md.rcut) {
-                ok = true;
-                unsigned long long q = (unsigned long long)floor(__dmul_rn(r, 1e8));
-                key = ((unsigned long long)(int)pj.w << 56) | (q << 26) | (unsigned long long)j;
+        double d[3], r = 0.0;
+        if (p < nf) {
+            r = min_image_r(pi, pos[j], bx, d);
+            ok = r < md.rcut;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            const int q = nk + __popc(m & lt);
+            // r >= 0: the conversion's truncation is the floor
+            const unsigned long long qr = (unsigned long long)__dmul_rn(r, 1e8);
+            keys[q] = ((unsigned long long)(e >> 26) << 56) | (qr << 26) | (unsigned long long)j;
+            if (env) {
+                const double ir = 1.0 / r;
+                double s, ds;
+                if (r < md.rcs) {
+                    s = ir;
+                    ds = -ir * ir;
+                } else {
+                    const double u = (r - md.rcs) * md.inv_sw;
+                    const double u2 = u * u, um = u - 1.0;
+                    const double poly = fma(u2 * u, fma(fma(-6.0, u, 15.0), u, -10.0), 1.0);
+                    const double dpoly = -30.0 * md.inv_sw * u2 * (um * um);
+                    s = poly * ir;
+                    ds = (dpoly - s) * ir;
+                }
+                const float irf = (float)ir;
+                recA[q] = make_float4((float)s, (float)d[0] * irf, (float)d[1] * irf, (float)d[2] * irf);
+                recB[q] = make_float2((float)ds, (float)r);
             }
         }
-        unsigned m = __ballot_sync(0xffffffffu, ok);
-        int off = __popc(m & ((1u << lane) - 1u));
-        if (ok) keys[nk + off] = key;
         nk += __popc(m);
     }
     __syncwarp();
@@ -215,13 +282,22 @@ __global__ void k_format(int64_t n, const Pos4 *__restrict__ pos, BoxDev bx, Mod
 #pragma unroll
     for (int t = 0; t < kMaxTypes; ++t) { tstart[t] = acc; acc += tcount[t]; }
     int32_t *out = nlist + i * (int64_t)md.nsel;
+    const int64_t plane = n * (int64_t)md.nsel;
     for (int p = lane; p < nk; p += 32) {
         unsigned long long k = keys[p];
         int rank = 0;
         for (int q = 0; q < nk; ++q) rank += keys[q] < k;
         int t = (int)(k >> 56);
         int local = rank - tstart[t];
-        if (local < md.sel[t]) out[md.sel_off[t] + local] = (int32_t)(k & ((1ull << 26) - 1));
+        if (local < md.sel[t]) {
+            const int slot = md.sel_off[t] + local;
+            out[slot] = (int32_t)(k & ((1ull << 26) - 1));
+            if (env) {
+                const int64_t q = (int64_t)i * md.nsel + slot;
+                reinterpret_cast<float4 *>(env)[q] = recA[p];
+                reinterpret_cast<float2 *>(env + 4 * plane)[q] = recB[p];
+            }
+        }
     }
     unsigned long long dropped = 0;
     for (int t = 0; t < md.ntypes; ++t) {
@@ -241,7 +317,8 @@ dp_status pack_positions(dp_nlist *nl, const double *d_coord, cudaStream_t st)
 {
     if (nl->n == 0) return DP_OK;
     ProfScope ps(nl->m->prof, PG_PACK, 1, st);
-    k_pack<<<blocks_for(nl->n, 256), 256, 0, st>>>(nl->n, d_coord, nl->d_type, (Pos4 *)nl->d_pos);
+    k_pack<<<blocks_for(nl->n, 256), 256, 0, st>>>(nl->n, d_coord, nl->d_type, make_box(nl), (Pos4 *)nl->d_pos,
+                                                   (float4 *)nl->d_posf);
     DP_CUDA(cudaGetLastError());
     return DP_OK;
 }
@@ -269,20 +346,27 @@ dp_status nlist_build_device(dp_nlist *nl, cudaStream_t st, bool conditional)
     return DP_OK;
 }
 
-dp_status nlist_format_device(const dp_model *m, dp_nlist *nl, const double *d_coord, cudaStream_t st)
+dp_status nlist_format_device(const dp_model *m, dp_nlist *nl, const double *d_coord, cudaStream_t st,
+                              bool with_env)
 {
     if (nl->n == 0) return DP_OK;
     if (d_coord) DP_TRY(pack_positions(nl, d_coord, st));
+    if (with_env && !nl->d_env) {
+        DP_CUDA(cudaStreamSynchronize(st));
+        DP_CUDA(cudaMalloc((void **)&nl->d_env, sizeof(float) * 6 * (size_t)nl->n * m->dev.nsel));
+    }
     BoxDev bx = make_box(nl);
     DP_CUDA(cudaMemsetAsync(nl->d_ntrunc, 0, sizeof(unsigned long long), st));
-    const int warps = 4;
-    size_t smem = (size_t)warps * nl->cap * sizeof(unsigned long long);
+    const size_t cap2 = (size_t)((nl->cap + 1) & ~1);
+    const size_t per_warp = (with_env ? 4 * cap2 : cap2 + cap2 / 2) * sizeof(unsigned long long);
+    const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(200 * 1024) / per_warp));
+    size_t smem = (size_t)warps * per_warp;
     if (smem > 48 * 1024)
         DP_CUDA(cudaFuncSetAttribute(k_format, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope ps(m->prof, PG_FORMAT, 1, st);
-    k_format<<<blocks_for(nl->n, warps), warps * 32, smem, st>>>(nl->n, (const Pos4 *)nl->d_pos, bx, m->dev,
-                                                                  nl->d_cand, nl->d_cand_cnt, nl->cap, nl->d_nlist,
-                                                                  nl->d_nnei, nl->d_ntrunc);
+    k_format<<<blocks_for(nl->n, warps), warps * 32, smem, st>>>(
+        nl->n, (const Pos4 *)nl->d_pos, (const float4 *)nl->d_posf, bx, m->dev, nl->d_cand, nl->d_cand_cnt, nl->cap,
+        nl->d_nlist, nl->d_nnei, nl->d_ntrunc, with_env ? nl->d_env : nullptr);
     DP_CUDA(cudaGetLastError());
     return DP_OK;
 }

@@ -109,30 +109,38 @@ struct TileCtx {
     int atom, tj, c0, net;
 };
 
-// Environment row of this thread's neighbor (FP64) plus layer 1 in FP32;
-// writes the layer-1 output row into A2.  Returns the FP32 row R.
-template <class S, int BF>
-__device__ __forceinline__ void rows_layer1(const ModelDev &md, const BoxDev &bx, const Pos4 *__restrict__ pos,
-                                            const int32_t *__restrict__ nlist, const int32_t *__restrict__ nnei,
-                                            const TileCtx &ch, int lane, int row, const float *vec,
-                                            unsigned char *A2, float Rf[4], float t1[S::E0], double d[3],
-                                            double J[12], int &j, bool &valid)
+// Geometry of this thread's neighbor from the formatted list (s, u = d/r
+// and, for the backward pass, ds/dr and r; all evaluated in FP64 by the
+// formatting kernel), plus layer 1 in FP32; writes the layer-1 output row
+// into A2.  Rf = (s, s u_x, s u_y, s u_z) is the environment row of Eq. 4.
+template <class S, int BF, bool BWD>
+__device__ __forceinline__ void rows_layer1(const ModelDev &md, const float4 *__restrict__ envA,
+                                            const float2 *__restrict__ envB, const int32_t *__restrict__ nlist,
+                                            const int32_t *__restrict__ nnei, const TileCtx &ch, int lane, int row,
+                                            const float *vec, unsigned char *A2, float Rf[4], float t1[S::E0],
+                                            float geo[6], int &j, bool &valid)
 {
-    double R[4] = {0.0, 0.0, 0.0, 0.0};
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 b = make_float2(0.f, 0.f);
     j = -1;
     valid = false;
-#pragma unroll
-    for (int q = 0; q < 12; ++q) J[q] = 0.0;
-    d[0] = d[1] = d[2] = 0.0;
     if (ch.atom >= 0 && ch.c0 + lane < nnei[(int64_t)ch.atom * md.ntypes + ch.tj]) {
-        j = nlist[(int64_t)ch.atom * md.nsel + md.sel_off[ch.tj] + ch.c0 + lane];
-        const Pos4 pi = pos[ch.atom];
-        double r = min_image_r(pi, pos[j], bx, d);
-        env_row(d, r, md.rcs, md.rcut, R, J);
+        const int64_t slot = (int64_t)ch.atom * md.nsel + md.sel_off[ch.tj] + ch.c0 + lane;
+        j = nlist[slot];
+        a = envA[slot];
+        if (BWD) b = envB[slot];
         valid = true;
     }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) Rf[c] = (float)R[c];
+    Rf[0] = a.x;
+    Rf[1] = a.x * a.y;
+    Rf[2] = a.x * a.z;
+    Rf[3] = a.x * a.w;
+    geo[0] = a.y;                          // u
+    geo[1] = a.z;
+    geo[2] = a.w;
+    geo[3] = b.x;                          // ds/dr
+    geo[4] = b.y;                          // r
+    geo[5] = valid ? a.x / b.y : 0.f;      // s/r
     const float *W1 = vec, *b1 = vec + S::K2;
     const float s = Rf[0];
     float buf[8];
@@ -184,7 +192,7 @@ __device__ __forceinline__ void epi_layer2(uint32_t taddr, const float *vec, con
 __device__ __forceinline__ int4 load_chunk(const int4 *chunks, int64_t idx) { return chunks[idx]; }
 
 template <class S, int BF>
-__global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, BoxDev bx, const Pos4 *__restrict__ pos,
+__global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const float4 *__restrict__ envA,
                                                             const int32_t *__restrict__ nlist,
                                                             const int32_t *__restrict__ nnei,
                                                             const int4 *__restrict__ chunks,
@@ -234,11 +242,10 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, BoxDev
             }
             cur_net = net;
         }
-        float Rf[4], t1[S::E0], t2[S::E1];
-        double d[3], J[12];
+        float Rf[4], t1[S::E0], t2[S::E1], geo[6];
         int j;
         bool valid;
-        rows_layer1<S, BF>(md, bx, pos, nlist, nnei, ch, lane, tid, vec, A2, Rf, t1, d, J, j, valid);
+        rows_layer1<S, BF, false>(md, envA, nullptr, nlist, nnei, ch, lane, tid, vec, A2, Rf, t1, geo, j, valid);
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
@@ -317,7 +324,8 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, BoxDev
 }
 
 template <class S, int BF>
-__global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, BoxDev bx, const Pos4 *__restrict__ pos,
+__global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, const float4 *__restrict__ envA,
+                                                            const float2 *__restrict__ envB,
                                                             const int32_t *__restrict__ nlist,
                                                             const int32_t *__restrict__ nnei,
                                                             const int4 *__restrict__ chunks,
@@ -371,11 +379,10 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, BoxDev
         }
         // dE/dT of this warp's atom (already scaled by 1/sum(sel))
         for (int q = lane; q < 4 * S::E2; q += 32) sdT[q] = ch.atom >= 0 ? dT[(int64_t)ch.atom * 4 * S::E2 + q] : 0.f;
-        float Rf[4], t1[S::E0], t2[S::E1];
-        double d[3], J[12];
+        float Rf[4], t1[S::E0], t2[S::E1], geo[6];
         int j;
         bool valid;
-        rows_layer1<S, BF>(md, bx, pos, nlist, nnei, ch, lane, tid, vec, A2, Rf, t1, d, J, j, valid);
+        rows_layer1<S, BF, true>(md, envA, envB, nlist, nnei, ch, lane, tid, vec, A2, Rf, t1, geo, j, valid);
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
@@ -523,20 +530,24 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, BoxDev
                 }
             }
         }
-        // FP64 from here: dE/dR -> g = J^T dE/dR, forces and virial
-        double gv[3] = {0.0, 0.0, 0.0}, vir[9];
+        // g = (dR/dr_ij)^T dE/dR in FP32.  With R = (s, s u), u = d/r:
+        //   g = u (dR0 s' + (s' - s/r) u.dR') + (s/r) dR',  dR' = (dR1, dR2, dR3);
+        // F_j -= g, F_i += g, W_i -= d (x) g, accumulated in FP64.
+        float gv[3] = {0.f, 0.f, 0.f}, vir[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) vir[q] = 0.0;
+        for (int q = 0; q < 9; ++q) vir[q] = 0.f;
         if (valid) {
-            const double dR0 = (double)dR[0] + (double)ds, dR1 = dR[1], dR2 = dR[2], dR3 = dR[3];
+            const float dR0 = dR[0] + ds;
+            const float ud = geo[0] * dR[1] + geo[1] * dR[2] + geo[2] * dR[3];
+            const float cu = fmaf(geo[3] - geo[5], ud, dR0 * geo[3]);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) gv[k] = dR0 * J[k] + dR1 * J[3 + k] + dR2 * J[6 + k] + dR3 * J[9 + k];
+            for (int k = 0; k < 3; ++k) gv[k] = fmaf(cu, geo[k], geo[5] * dR[1 + k]);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) atomicAdd(&force[3 * (int64_t)j + k], -gv[k]);
+            for (int k = 0; k < 3; ++k) atomicAdd(&force[3 * (int64_t)j + k], -(double)gv[k]);
 #pragma unroll
             for (int a = 0; a < 3; ++a)
 #pragma unroll
-                for (int b = 0; b < 3; ++b) vir[3 * a + b] = -d[a] * gv[b];
+                for (int b = 0; b < 3; ++b) vir[3 * a + b] = -(geo[4] * geo[a]) * gv[b];
         }
         // the warp's rows all belong to one atom: reduce F_i and W_i over the warp
 #pragma unroll
@@ -547,14 +558,14 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, BoxDev
             for (int s = 16; s > 0; s >>= 1) vir[q] += __shfl_xor_sync(0xffffffffu, vir[q], s);
         if (ch.atom >= 0) {
             if (lane < 3) {
-                double v = lane == 0 ? gv[0] : (lane == 1 ? gv[1] : gv[2]);
-                atomicAdd(&force[3 * (int64_t)ch.atom + lane], v);
+                float v = lane == 0 ? gv[0] : (lane == 1 ? gv[1] : gv[2]);
+                atomicAdd(&force[3 * (int64_t)ch.atom + lane], (double)v);
             }
             if (lane < 9) {
-                double v = 0.0;
+                float v = 0.f;
 #pragma unroll
                 for (int q = 0; q < 9; ++q) v = (q == lane) ? vir[q] : v;
-                atomicAdd(&atom_virial[9 * (int64_t)ch.atom + lane], v);
+                atomicAdd(&atom_virial[9 * (int64_t)ch.atom + lane], (double)v);
             }
         }
         tc::fence_before_sync();
@@ -1169,8 +1180,12 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     DP_CUDA(cudaMemsetAsync(d_force, 0, sizeof(double) * 3 * n, st));
     DP_CUDA(cudaMemsetAsync(d_atom_virial, 0, sizeof(double) * 9 * n, st));
     const unsigned char *wimg = m->d_tcw + (size_t)BF * nn * S::IMG;
-    BoxDev bx = make_box(nl);
-    const Pos4 *pos = (const Pos4 *)nl->d_pos;
+    if (!nl->d_env) {
+        set_error("tensor-core path needs the neighbor geometry of the formatting kernel");
+        return DP_ERR_ARG;
+    }
+    const float4 *envA = reinterpret_cast<const float4 *>(nl->d_env);
+    const float2 *envB = reinterpret_cast<const float2 *>(nl->d_env + 4 * (size_t)n * md.nsel);
     const unsigned grid = (unsigned)(2 * nsm);
     {
         ProfScope ps(m->prof, PG_CHUNKS, 1, st);
@@ -1181,7 +1196,7 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     DP_CUDA(cudaFuncSetAttribute(k_embed_bwd_tc<S, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::BWD_SMEM));
     {
         ProfScope ps(m->prof, PG_EMBED_FWD, 1, st);
-        k_embed_fwd_tc<S, BF><<<grid, kTcThreads, S::FWD_SMEM, st>>>(md, bx, pos, nl->d_nlist, nl->d_nnei, chunks,
+        k_embed_fwd_tc<S, BF><<<grid, kTcThreads, S::FWD_SMEM, st>>>(md, envA, nl->d_nlist, nl->d_nnei, chunks,
                                                                      cnt, wimg, T, m->d_err);
     }
     DP_CUDA(cudaGetLastError());
@@ -1203,7 +1218,7 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     }
     {
         ProfScope ps(m->prof, PG_EMBED_BWD, 1, st);
-        k_embed_bwd_tc<S, BF><<<grid, kTcThreads, S::BWD_SMEM, st>>>(md, bx, pos, nl->d_nlist, nl->d_nnei, chunks,
+        k_embed_bwd_tc<S, BF><<<grid, kTcThreads, S::BWD_SMEM, st>>>(md, envA, envB, nl->d_nlist, nl->d_nnei, chunks,
                                                                      cnt, wimg, dT, d_force, d_atom_virial, m->d_err);
     }
     DP_CUDA(cudaGetLastError());
