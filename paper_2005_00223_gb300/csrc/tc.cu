@@ -3,8 +3,11 @@
 // fp16 or bf16 operands in shared memory and FP32 accumulators in tensor
 // memory; the first embedding layer (K = 1, too small for the tensor cores),
 // tanh and its derivative run in FP32 on the CUDA cores, as the paper does.
-// Coordinates, minimum image, the environment row and its Jacobian, the
-// chain dE/dR -> dE/dd and the force / virial scatter stay FP64.
+// The minimum image, the distance and the switching function s(r), ds/dr are
+// evaluated in FP64 once per evaluation by the formatting kernel, which
+// stores (s, u = d/r) and (ds/dr, r) per neighbor slot as FP32; here the
+// environment row R = (s, s u) and the chain dE/dR -> g_ij run in FP32, and
+// the force / virial accumulation is FP64.
 //
 // Work unit: a tile of 128 neighbor rows = 4 chunks of 32 rows, one chunk per
 // warp; every chunk is up to 32 neighbors of one type of one atom, and the 4
@@ -13,12 +16,12 @@
 // CTA keeps the packed weights of the current net in shared memory, loaded
 // by one bulk copy on the TMA engine.
 //
-// Per tile, forward (k_embed_fwd_tc):  env rows -> layer 1 (FP32) -> A2 ->
+// Per tile, forward (k_embed_fwd_tc):  rows R -> layer 1 (FP32) -> A2 ->
 //   MMA (A2 x W2) -> tanh / skip epilogue -> A3 -> MMA (A3 x W3) -> epilogue
 //   gives G -> contraction T_i += G^T R (FP32, per warp) -> atomics into T.
 // Backward (k_embed_bwd_tc) recomputes the forward (no activation storage),
 //   then dG = dT R, dR = dT^T G, dz3 -> MMA (dz3 x W3^T) -> dz2 -> MMA
-//   (dz2 x W2^T) -> ds -> g_ij = J^T dR -> FP64 force and virial atomics.
+//   (dz2 x W2^T) -> ds -> g_ij -> FP64 force and virial atomics.
 // The descriptor D = T T<^T, the fitting net and dE/dT sit between the two.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
