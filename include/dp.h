@@ -306,6 +306,16 @@ dp_status dp_md_state_get(const dp_md_state *s, double *coord, double *vel, int6
 
 void dp_md_state_destroy(dp_md_state *s);
 
+/* ---------------------------------------------------------- diagnostics */
+
+/* The activation function of the FP64 nets (Fig. 1(e-g)): y[i] = tanh(x[i])
+ * for d_x, d_y [n] FP64 in device memory, evaluated by the same device
+ * routine the FP64 kernels use (degree-10 Taylor table on intervals of 1/16,
+ * library tanh for |x| >= 16).  Enqueued on `stream`.  Exposed so that its
+ * accuracy can be tested.  Errors: DP_ERR_ARG (n < 0, NULL with n > 0),
+ * DP_ERR_CUDA. */
+dp_status dp_tanh_f64_dev(int64_t n, const double *d_x, double *d_y, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,7 @@ EXPORTS = [
     "dp_nlist_destroy", "dp_nlist_update_dev", "dp_compute", "dp_compute_dev", "dp_md_state_create",
     "dp_md_step", "dp_md_state_get", "dp_md_state_destroy", "dp_param_grad", "dp_force_loss_grad",
     "dp_force_loss_grad_dev", "dp_adam_step", "dp_model_sync_params", "dp_md_step_judged",
-    "dp_nlist_format_noalloc",
+    "dp_nlist_format_noalloc", "dp_tanh_f64_dev",
 ]
 
 
@@ -79,6 +79,7 @@ def load(path: str = LIB_PATH):
             "dp_nlist_destroy": ([P], None),
             "dp_nlist_update_dev": ([P, P, P], C.c_int),
             "dp_nlist_format_noalloc": ([I64, P, P, P, D, I32, P, P, P, P, P], C.c_int),
+            "dp_tanh_f64_dev": ([I64, P, P, P], C.c_int),
             "dp_param_grad": ([P, P, P, P, P, D, D, C.c_int, P, P, P], C.c_int),
             "dp_force_loss_grad": ([P, P, P, P, P, D, D, D, C.c_int, P, P], C.c_int),
             "dp_force_loss_grad_dev": ([P, P, P, P, P, P, D, D, C.c_int, P, P, P], C.c_int),
@@ -237,6 +238,11 @@ def dp_nlist_format_noalloc(d_coord, d_type, box, rcut: float, sel, d_nlist, d_n
     _check(load().dp_nlist_format_noalloc(int(d_type.numel()), _ptr(d_coord), _ptr(d_type), _ptr(_box(box)),
                                           float(rcut), int(sel.size), _ptr(sel), _ptr(d_nlist), _ptr(d_ntrunc),
                                           _ptr(d_status), _stream(stream)), "dp_nlist_format_noalloc")
+
+
+def dp_tanh_f64_dev(d_x, d_y, stream=None):
+    """y = tanh(x) by the FP64 kernels' own routine (device tensors of equal size)."""
+    _check(load().dp_tanh_f64_dev(int(d_x.numel()), _ptr(d_x), _ptr(d_y), _stream(stream)), "dp_tanh_f64_dev")
 
 
 def dp_nlist_destroy(nl):

@@ -35,7 +35,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
     sources = sorted(glob.glob(os.path.join(SRC, "*.cu")))
-    headers = sorted(glob.glob(os.path.join(SRC, "*.cuh"))) + [
+    headers = sorted(glob.glob(os.path.join(SRC, "*.cuh"))) + sorted(glob.glob(os.path.join(SRC, "*.inc"))) + [
         os.path.join(os.path.dirname(HERE), "include", "dp.h")]
     objs = []
     jobs = []

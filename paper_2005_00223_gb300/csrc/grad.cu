@@ -32,13 +32,14 @@
 
 #include "dp_internal.cuh"
 #include "geom.cuh"
+#include "tanh64.cuh"
 
 namespace dp {
 namespace {
 
 constexpr int kGA = 4;   // atoms per CTA in the fitting kernels
 
-__device__ __forceinline__ double g_tanh(double x) { return tanh(x); }
+__device__ __forceinline__ double g_tanh(double x) { return tanh_f64(x); }
 __device__ __forceinline__ float g_tanh(float x) { return tanhf(x); }
 
 template <typename Real>

@@ -31,12 +31,13 @@
 
 #include "dp_internal.cuh"
 #include "geom.cuh"
+#include "tanh64.cuh"
 
 namespace dp {
 namespace {
 
 
-__device__ __forceinline__ double act_tanh(double x) { return tanh(x); }
+__device__ __forceinline__ double act_tanh(double x) { return tanh_f64(x); }
 __device__ __forceinline__ float act_tanh(float x) { return tanhf(x); }
 
 template <typename Real>
@@ -562,10 +563,25 @@ size_t fit_smem(const ModelDev &md, int A)
     return sizeof(Real) * ((a > b ? a : b) + 2 * (size_t)A * fsum);
 }
 
+template <typename Real, int A>
+dp_status launch_fit_a(dp_model *m, const int32_t *order, int t, int64_t p0, int64_t b, int64_t count,
+                       const Real *D, Real *dD, double *E_atom, cudaStream_t st)
+{
+    const size_t sfit = fit_smem<Real>(m->dev, A);
+    const unsigned tiles = (unsigned)((count + A - 1) / A);
+    DP_CUDA(cudaFuncSetAttribute(k_fit<Real, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sfit));
+    k_fit<Real, A><<<tiles, 256, sfit, st>>>(m->dev, t, order, p0, b, count, D, dD, E_atom);
+    DP_CUDA(cudaGetLastError());
+    return DP_OK;
+}
+
 // Launches the fitting net of type t over `count` type-sorted positions from
-// `b`.  The atoms per CTA (6..9) are chosen to minimise (waves x atoms per
-// CTA) for this count, since the kernel is arithmetic bound and a partly
-// filled last wave idles SMs.
+// `b`.  The kernel is bound by the arithmetic pipe of the SM it runs on, and
+// CTAs that share an SM share that pipe, so the time goes with the number of
+// atoms the busiest SM handles: ceil(ceil(count / A) / SMs) * A.  The atoms
+// per CTA A (1, 2, 4 or 6..9) minimise it; ties go to the larger A, whose
+// weight loads serve more atoms.  Small systems thus spread one atom per CTA
+// over all SMs, large ones keep 6-9 atoms per CTA.
 template <typename Real>
 dp_status launch_fit(dp_model *m, const int32_t *order, int t, int64_t p0, int64_t b, int64_t count, const Real *D, Real *dD,
                      double *E_atom, cudaStream_t st)
@@ -573,44 +589,29 @@ dp_status launch_fit(dp_model *m, const int32_t *order, int t, int64_t p0, int64
     const ModelDev &md = m->dev;
     int nsm = 0;
     DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
+    static const int choices[] = {1, 2, 4, 6, 7, 8, 9};
     int bestA = 0;
     long best = -1;
-    for (int A = 6; A <= 9; ++A) {
-        const size_t sm = fit_smem<Real>(md, A);
-        if (sm > 227 * 1024) continue;
-        const long per_sm = (long)((228 * 1024) / (sm + 1024)) < 8 ? (long)((228 * 1024) / (sm + 1024)) : 8;
+    for (int A : choices) {
+        if (fit_smem<Real>(md, A) > 227 * 1024) continue;
         const long tiles = (long)((count + A - 1) / A);
-        const long slots = (long)nsm * (per_sm > 0 ? per_sm : 1);
-        const long cost = ((tiles + slots - 1) / slots) * A;
-        if (best < 0 || cost < best) { best = cost; bestA = A; }
+        const long cost = ((tiles + nsm - 1) / nsm) * A;
+        if (best < 0 || cost <= best) { best = cost; bestA = A; }
     }
     if (bestA == 0) {
         set_error("fitting net too wide for the shared-memory tile");
         return DP_ERR_UNSUPPORTED;
     }
-    const size_t sfit = fit_smem<Real>(md, bestA);
-    const unsigned tiles = (unsigned)((count + bestA - 1) / bestA);
     ProfScope ps(m->prof, PG_FIT, 1, st);
     switch (bestA) {
-    case 6:
-        DP_CUDA(cudaFuncSetAttribute(k_fit<Real, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sfit));
-        k_fit<Real, 6><<<tiles, 256, sfit, st>>>(md, t, order, p0, b, count, D, dD, E_atom);
-        break;
-    case 7:
-        DP_CUDA(cudaFuncSetAttribute(k_fit<Real, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sfit));
-        k_fit<Real, 7><<<tiles, 256, sfit, st>>>(md, t, order, p0, b, count, D, dD, E_atom);
-        break;
-    case 8:
-        DP_CUDA(cudaFuncSetAttribute(k_fit<Real, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sfit));
-        k_fit<Real, 8><<<tiles, 256, sfit, st>>>(md, t, order, p0, b, count, D, dD, E_atom);
-        break;
-    default:
-        DP_CUDA(cudaFuncSetAttribute(k_fit<Real, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sfit));
-        k_fit<Real, 9><<<tiles, 256, sfit, st>>>(md, t, order, p0, b, count, D, dD, E_atom);
-        break;
+    case 1: return launch_fit_a<Real, 1>(m, order, t, p0, b, count, D, dD, E_atom, st);
+    case 2: return launch_fit_a<Real, 2>(m, order, t, p0, b, count, D, dD, E_atom, st);
+    case 4: return launch_fit_a<Real, 4>(m, order, t, p0, b, count, D, dD, E_atom, st);
+    case 6: return launch_fit_a<Real, 6>(m, order, t, p0, b, count, D, dD, E_atom, st);
+    case 7: return launch_fit_a<Real, 7>(m, order, t, p0, b, count, D, dD, E_atom, st);
+    case 8: return launch_fit_a<Real, 8>(m, order, t, p0, b, count, D, dD, E_atom, st);
+    default: return launch_fit_a<Real, 9>(m, order, t, p0, b, count, D, dD, E_atom, st);
     }
-    DP_CUDA(cudaGetLastError());
-    return DP_OK;
 }
 
 template <class S, typename Real>
@@ -730,3 +731,31 @@ dp_status compute_mix32(dp_model *m, dp_nlist *nl, double *d_energy, double *d_a
 }
 
 }  // namespace dp
+
+namespace dp {
+namespace {
+
+__global__ void k_tanh_f64(int64_t n, const double *__restrict__ x, double *__restrict__ y)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = tanh_f64(x[i]);
+}
+
+}  // namespace
+}  // namespace dp
+
+extern "C" dp_status dp_tanh_f64_dev(int64_t n, const double *d_x, double *d_y, void *stream)
+{
+    if (n < 0 || (n > 0 && (!d_x || !d_y))) {
+        dp::set_error("dp_tanh_f64_dev: bad argument");
+        return DP_ERR_ARG;
+    }
+    if (n == 0) return DP_OK;
+    dp::k_tanh_f64<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, d_x, d_y);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        dp::set_error("dp_tanh_f64_dev: %s", cudaGetErrorString(e));
+        return DP_ERR_CUDA;
+    }
+    return DP_OK;
+}
