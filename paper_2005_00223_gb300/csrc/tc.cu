@@ -18,7 +18,8 @@
 //
 // Per tile, forward (k_embed_fwd_tc):  rows R -> layer 1 (FP32) -> A2 ->
 //   MMA (A2 x W2) -> tanh / skip epilogue -> A3 -> MMA (A3 x W3) -> epilogue
-//   gives G -> contraction T_i += G^T R (FP32, per warp) -> atomics into T.
+//   gives G (fp16) -> contraction T_q = G^T R per chunk as MMAs with
+//   MN-major operands (FP32 accumulators) -> atomics into T.
 // Backward (k_embed_bwd_tc) recomputes the forward (no activation storage),
 //   then dG = dT R, dR = dT^T G, dz3 -> MMA (dz3 x W3^T) -> dz2 -> MMA
 //   (dz2 x W2^T) -> ds -> g_ij -> FP64 force and virial atomics.
@@ -62,13 +63,18 @@ struct TcShape {
     static constexpr uint32_t A3_OFF = A2_OFF + 128 * K2 * 2;          // [128][N2]
     static constexpr uint32_t AB1_OFF = A3_OFF + 128 * N2 * 2;         // [128][N3] (backward)
     static constexpr uint32_t X_OFF = AB1_OFF + 128 * N3 * 2;          // backward: dT per warp (FP32)
-    static constexpr uint32_t FX_OFF = AB1_OFF;                        // forward: G and R per warp (FP32)
-    static constexpr uint32_t FWD_SCRATCH = 4 * 32 * 17 * 4 + 4 * 32 * 4 * 4;
+    // forward: the contraction T = G^T R as MMAs with MN-major fp16 operands,
+    // G^T [128 m][128 rows] and R [16 c][128 rows] (c >= 4 and m >= E2 stay 0)
+    static constexpr uint32_t GT_OFF = AB1_OFF;
+    static constexpr uint32_t RT_OFF = GT_OFF + 128 * 128 * 2;
+    static constexpr uint32_t FWD_SCRATCH = 128 * 128 * 2 + 16 * 128 * 2;
     static constexpr uint32_t BWD_SCRATCH = 4 * 4 * E2 * 4;
     // at most two CTAs per SM (each holds 256 TMEM columns of the SM's 512)
-    static constexpr uint32_t FWD_SMEM = FX_OFF + FWD_SCRATCH > 80 * 1024 ? FX_OFF + FWD_SCRATCH : 80 * 1024;
+    static constexpr uint32_t FWD_SMEM = GT_OFF + FWD_SCRATCH > 80 * 1024 ? GT_OFF + FWD_SCRATCH : 80 * 1024;
     static constexpr uint32_t BWD_SMEM = X_OFF + BWD_SCRATCH > 80 * 1024 ? X_OFF + BWD_SCRATCH : 80 * 1024;
-    static_assert(N2 + N3 <= kTmemCols, "TMEM columns");
+    static constexpr uint32_t TCOL = N2 + N3;                          // TMEM columns of the 4 chunks' T
+    static_assert(N2 + N3 + 64 <= kTmemCols, "TMEM columns");
+    static_assert(N3 <= 128 && 2 * FWD_SMEM <= 227 * 1024, "forward tile");
 };
 
 using TcWater = TcShape<25, 50, 100>;
@@ -210,9 +216,11 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const 
     unsigned char *img = smem;
     unsigned char *A2 = smem + S::A2_OFF;
     unsigned char *A3 = smem + S::A3_OFF;
-    float *sG = reinterpret_cast<float *>(smem + S::FX_OFF) + warp * 32 * 17;
-    float *sR = reinterpret_cast<float *>(smem + S::FX_OFF) + 4 * 32 * 17 + warp * 32 * 4;
+    unsigned char *GT = smem + S::GT_OFF;
+    unsigned char *RT = smem + S::RT_OFF;
     const float *vec = reinterpret_cast<const float *>(img + S::VEC_OFF);
+    for (int q = tid; q < (int)(S::FWD_SCRATCH / 16); q += kTcThreads)
+        reinterpret_cast<uint4 *>(GT)[q] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
         tc::mbar_init(&mbar_mma, 1);
         tc::mbar_init(&mbar_w, 1);
@@ -225,6 +233,7 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const 
     const uint32_t tmem = tmem_base;
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
     const uint32_t id2 = tc::idesc_f16(128, S::N2, BF), id3 = tc::idesc_f16(128, S::N3, BF);
+    const uint32_t idT = tc::idesc_f16_mn(128, 16);
     uint32_t ph_mma = 0, ph_w = 0;
     int cur_net = -1;
     const int ntiles = *ntiles_ptr;
@@ -280,41 +289,65 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const 
             break;
         }
         tc::fence_after_sync();
-        // layer-3 epilogue: G = skip(y2) + tanh(z3 + b3), 16 channels at a time,
-        // each block contracted at once: T[atom][m][c] += sum_rows G[row][m] R[row][c]
+        // layer-3 epilogue: G = skip(y2) + tanh(z3 + b3) in fp16 into G^T, this
+        // thread's row R (zero on padded rows) into R^T
         {
             const float *b3 = vec + 2 * S::K2 + S::N2;
             float y2[S::E1];
 #pragma unroll
             for (int k = 0; k < S::E1; ++k) y2[k] = skip_of<S::E0, S::E1>(t1, k) + t2[k];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) sR[lane * 4 + c] = Rf[c];
-            float *Ta = T + (int64_t)(ch.atom >= 0 ? ch.atom : 0) * 4 * S::E2;
-            const int mu = lane & 15, cp = (lane >> 4) * 2;
+            *reinterpret_cast<uint4 *>(RT + tc::mnmaj_off(0, tid, 16)) =
+                make_uint4(pack2<0>(Rf[0], Rf[1]), pack2<0>(Rf[2], Rf[3]), 0u, 0u);
 #pragma unroll
             for (int c0 = 0; c0 < S::N3; c0 += 16) {
                 float z[16];
                 tc::tmem_ld16(taddr + S::N2 + c0, z);
                 tc::tmem_ld_wait();
+                float g[16];
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     const int m = c0 + u;
-                    sG[lane * 17 + u] = m < S::E2 ? skip_of<S::E1, S::E2>(y2, m) + tc::tanh_fast(z[u] + b3[m]) : 0.f;
+                    g[u] = m < S::E2 ? skip_of<S::E1, S::E2>(y2, m) + tc::tanh_fast(z[u] + b3[m]) : 0.f;
                 }
-                __syncwarp();
-                float a0 = 0.f, a1 = 0.f;
-#pragma unroll 8
-                for (int r = 0; r < 32; ++r) {
-                    const float g = sG[r * 17 + mu];
-                    const float2 rr = *reinterpret_cast<const float2 *>(sR + r * 4 + cp);
-                    a0 = fmaf(g, rr.x, a0);
-                    a1 = fmaf(g, rr.y, a1);
+                *reinterpret_cast<uint4 *>(GT + tc::mnmaj_off(c0, tid, 128)) =
+                    make_uint4(pack2<0>(g[0], g[1]), pack2<0>(g[2], g[3]), pack2<0>(g[4], g[5]), pack2<0>(g[6], g[7]));
+                *reinterpret_cast<uint4 *>(GT + tc::mnmaj_off(c0 + 8, tid, 128)) = make_uint4(
+                    pack2<0>(g[8], g[9]), pack2<0>(g[10], g[11]), pack2<0>(g[12], g[13]), pack2<0>(g[14], g[15]));
+            }
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            // chunk q: T_q[m][c] = sum over its 32 rows of G[row][m] R[row][c]
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                tc::mma_kloop_mn(tmem + S::TCOL + 16 * q, tc::smem_u32(GT), 128, tc::smem_u32(RT), 16, 32 * q, 32,
+                                 idT, false);
+            tc::mma_commit(&mbar_mma);
+        }
+        ok = tc::mbar_wait(&mbar_mma, ph_mma, kWaitLimit);
+        ph_mma ^= 1;
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) atomicOr(err, 1);
+            break;
+        }
+        tc::fence_after_sync();
+        // warp w holds channels m = 32 w + lane of every chunk's T
+        {
+            const int m = warp * 32 + lane;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float v[4];
+                tc::tmem_ld4(taddr + S::TCOL + 16 * q, v);
+                tc::tmem_ld_wait();
+                const int atom = load_chunk(chunks, (int64_t)tile * 4 + q).x;
+                if (atom >= 0 && m < S::E2) {
+                    float *Tm = T + (int64_t)atom * 4 * S::E2 + 4 * m;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) atomicAdd(Tm + c, v[c]);
                 }
-                if (ch.atom >= 0 && c0 + mu < S::E2) {
-                    atomicAdd(Ta + 4 * (c0 + mu) + cp, a0);
-                    atomicAdd(Ta + 4 * (c0 + mu) + cp + 1, a1);
-                }
-                __syncwarp();
             }
         }
         tc::fence_before_sync();

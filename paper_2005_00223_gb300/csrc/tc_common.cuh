@@ -11,9 +11,12 @@ namespace tc {
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Shared-memory matrix descriptor, K-major, no swizzle: the operand is a grid
-// of 8-row x 16-byte core matrices; lbo = byte stride between core matrices
-// along K, sbo = byte stride between 8-row groups along M (or N).
+// Shared-memory matrix descriptor, no swizzle: the operand is a grid of
+// 8 x 16-byte core matrices.  K-major: lbo = byte stride between core
+// matrices along K, sbo = byte stride between 8-row groups along M (or N).
+// MN-major (with the transpose bit of the instruction descriptor): lbo =
+// stride between groups of 8 K-rows, sbo = stride between groups of 8
+// M (or N) elements.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
 {
     uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
@@ -31,6 +34,22 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int bf16)
            ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor of kind::f16 with fp16 A and B, both MN-major
+// (transposed: bits 15 and 16), FP32 accumulator, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_f16_mn(int M, int N)
+{
+    return (1u << 4) | (1u << 15) | (1u << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of element (mn, k) of an MN-major no-swizzle tile with MN rows:
+// core matrices of 8 K-rows x 16 bytes (8 consecutive MN elements); groups of
+// 8 MN elements 128 bytes apart (the descriptor's sbo), groups of 8 K-rows
+// MN/8 * 128 bytes apart (its lbo).
+__host__ __device__ __forceinline__ uint32_t mnmaj_off(int mn, int k, int MN)
+{
+    return (uint32_t)((mn & 7) * 2 + (mn >> 3) * 128 + (k & 7) * 16 + (k >> 3) * (MN >> 3) * 128);
+}
+
 // Byte offset of element (r, k) of a K-major no-swizzle tile with K columns
 // (lbo = 128, sbo = K/8 * 128).
 __host__ __device__ __forceinline__ uint32_t kmaj_off(int r, int k, int K)
@@ -46,6 +65,24 @@ __device__ __forceinline__ void mma_kloop(uint32_t d_tmem, uint32_t a_saddr, uin
         uint64_t ad = smem_desc(a_saddr + ks * 256, 128, sbo);
         uint64_t bd = smem_desc(b_saddr + ks * 256, 128, sbo);
         uint32_t acc = ks > 0;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    }
+}
+
+// D[tmem] (+)= A B^T with both operands MN-major (mnmaj_off layouts with
+// MN extents MA and NB), K a multiple of 16 starting at K-row k0; M = 128.
+__device__ __forceinline__ void mma_kloop_mn(uint32_t d_tmem, uint32_t a_saddr, int MA, uint32_t b_saddr, int NB,
+                                             int k0, int K, uint32_t idesc, bool accumulate)
+{
+    const uint32_t lbo_a = (uint32_t)(MA >> 3) * 128, lbo_b = (uint32_t)(NB >> 3) * 128;
+    for (int ks = 0; ks < (K >> 4); ++ks) {
+        const int kg = (k0 >> 3) + 2 * ks;
+        uint64_t ad = smem_desc(a_saddr + kg * lbo_a, lbo_a, 128);
+        uint64_t bd = smem_desc(b_saddr + kg * lbo_b, lbo_b, 128);
+        uint32_t acc = (accumulate || ks > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
@@ -127,6 +164,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *out)
         : "r"(taddr));
 #pragma unroll
     for (int i = 0; i < 16; ++i) out[i] = __uint_as_float(r[i]);
+}
+
+// 4 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float *out)
+{
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) out[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
