@@ -346,6 +346,7 @@ dp_status dp_model_create(const dp_model_config *cfg, uint64_t seed, dp_model **
     if (e == cudaSuccess) e = cudaMalloc((void **)&m->d_params32, sizeof(float) * m->nparams);
     if (e == cudaSuccess) e = cudaMalloc((void **)&m->d_paramsT32, sizeof(float) * m->nparams);
     if (e == cudaSuccess) e = cudaMalloc((void **)&m->d_flag, sizeof(int32_t) * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&m->d_red, sizeof(double) * kRedParts * 10);
     if (e == cudaSuccess) e = cudaMalloc((void **)&m->d_err, sizeof(int32_t) * 4);
     if (e == cudaSuccess) e = cudaMemset(m->d_err, 0, sizeof(int32_t) * 4);
     if (e != cudaSuccess) st = cuda_fail(e, "dp_model_create");
@@ -414,6 +415,7 @@ void dp_model_destroy(dp_model *m)
     cudaFree(m->ws);
     cudaFree(m->d_aux);
     cudaFree(m->d_flag);
+    cudaFree(m->d_red);
     cudaFree(m->d_err);
     cudaFree(m->d_tcw);
     cudaFree(m->d_tcfit);

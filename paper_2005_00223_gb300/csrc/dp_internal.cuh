@@ -140,6 +140,7 @@ struct dp_model {
     double *d_aux = nullptr;
     int64_t aux_n = -1;
     int32_t *d_flag = nullptr;        // [4] non-finite flag and spare
+    double *d_red = nullptr;          // [kRedParts][10] partial sums of the energy / virial reduction
     int32_t *d_err = nullptr;         // [4] device error word (bounded waits that gave up)
     unsigned char *d_tcw = nullptr;   // packed fp16 and bf16 embedding weights for the tensor cores
     unsigned char *d_tcfit = nullptr; // packed fp16 and bf16 fitting weights for the tensor cores
@@ -206,8 +207,9 @@ dp_status nlist_format_device(const dp_model *m, dp_nlist *nl, const double *d_c
 dp_status pack_positions(dp_nlist *nl, const double *d_coord, cudaStream_t st);
 dp_status compute_fp64(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
                        double *d_virial, double *d_atom_virial, cudaStream_t st);
+constexpr int kRedParts = 256;        // blocks of the first reduction stage
 dp_status reduce_energy_virial(const double *d_atom_energy, const double *d_atom_virial, int64_t n,
-                               double *d_energy, double *d_virial, cudaStream_t st);
+                               double *d_energy, double *d_virial, double *d_scratch, cudaStream_t st);
 dp_status ensure_workspace(dp_model *m, size_t bytes);
 dp_status check_nonfinite(const double *d_x, int64_t n, int32_t *d_flag, cudaStream_t st);
 bool embed_shape_supported(int n_embed, const int *e);

@@ -1,7 +1,8 @@
 // Deterministic reductions: E = sum_i E_i and W = sum_i W_i in a fixed order
-// (one block, strided partial sums, then a fixed tree), plus a scan of the
-// forces for NaN / Inf.  E is summed in FP64 as Sec. 4.1.3 prescribes for
-// the mixed schemes too.
+// (kRedParts blocks over contiguous atom ranges, strided partial sums and a
+// fixed tree in each, then one block over the partial sums), plus a scan of
+// the forces for NaN / Inf.  E is summed in FP64 as Sec. 4.1.3 prescribes
+// for the mixed schemes too.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -10,23 +11,12 @@
 namespace dp {
 namespace {
 
-constexpr int kRedThreads = 512;
+constexpr int kRedThreads = 256;
 
-__global__ void __launch_bounds__(kRedThreads) k_reduce(const double *__restrict__ Ei, const double *__restrict__ Wi,
-                                                       int64_t n, double *__restrict__ E, double *__restrict__ W)
+// Fixed-shape tree over the block's kRedThreads values of 10 sums.
+__device__ __forceinline__ void block_tree(double (*s)[kRedThreads], double acc[10])
 {
-    __shared__ double s[10][kRedThreads];
     const int t = threadIdx.x;
-    double acc[10];
-#pragma unroll
-    for (int q = 0; q < 10; ++q) acc[q] = 0.0;
-    for (int64_t i = t; i < n; i += kRedThreads) {
-        acc[0] += Ei[i];
-        if (Wi) {
-#pragma unroll
-            for (int q = 0; q < 9; ++q) acc[1 + q] += Wi[9 * i + q];
-        }
-    }
 #pragma unroll
     for (int q = 0; q < 10; ++q) s[q][t] = acc[q];
     __syncthreads();
@@ -37,9 +27,46 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const double *__restrict
         }
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_reduce_part(const double *__restrict__ Ei,
+                                                            const double *__restrict__ Wi, int64_t n,
+                                                            double *__restrict__ part)
+{
+    __shared__ double s[10][kRedThreads];
+    const int t = threadIdx.x;
+    const int64_t per = (n + kRedParts - 1) / kRedParts;
+    const int64_t b0 = blockIdx.x * per, b1 = b0 + per < n ? b0 + per : n;
+    double acc[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) acc[q] = 0.0;
+    for (int64_t i = b0 + t; i < b1; i += kRedThreads) {
+        acc[0] += Ei[i];
+        if (Wi) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) acc[1 + q] += Wi[9 * i + q];
+        }
+    }
+    block_tree(s, acc);
+    if (t < 10) part[blockIdx.x * 10 + t] = s[t][0];
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_reduce_final(const double *__restrict__ part, bool has_w,
+                                                             double *__restrict__ E, double *__restrict__ W)
+{
+    __shared__ double s[10][kRedThreads];
+    const int t = threadIdx.x;
+    double acc[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) acc[q] = 0.0;
+    for (int b = t; b < kRedParts; b += kRedThreads) {
+#pragma unroll
+        for (int q = 0; q < 10; ++q) acc[q] += part[b * 10 + q];
+    }
+    block_tree(s, acc);
     if (t == 0) {
         E[0] = s[0][0];
-        if (W && Wi)
+        if (W && has_w)
             for (int q = 0; q < 9; ++q) W[q] = s[1 + q][0];
     }
 }
@@ -53,9 +80,10 @@ __global__ void k_nonfinite(const double *__restrict__ x, int64_t n, int32_t *fl
 }  // namespace
 
 dp_status reduce_energy_virial(const double *d_atom_energy, const double *d_atom_virial, int64_t n,
-                               double *d_energy, double *d_virial, cudaStream_t st)
+                               double *d_energy, double *d_virial, double *d_scratch, cudaStream_t st)
 {
-    k_reduce<<<1, kRedThreads, 0, st>>>(d_atom_energy, d_atom_virial, n, d_energy, d_virial);
+    k_reduce_part<<<kRedParts, kRedThreads, 0, st>>>(d_atom_energy, d_atom_virial, n, d_scratch);
+    k_reduce_final<<<1, kRedThreads, 0, st>>>(d_scratch, d_atom_virial != nullptr, d_energy, d_virial);
     DP_CUDA(cudaGetLastError());
     return DP_OK;
 }

@@ -576,12 +576,12 @@ dp_status launch_fit_a(dp_model *m, const int32_t *order, int t, int64_t p0, int
 }
 
 // Launches the fitting net of type t over `count` type-sorted positions from
-// `b`.  The kernel is bound by the arithmetic pipe of the SM it runs on, and
-// CTAs that share an SM share that pipe, so the time goes with the number of
-// atoms the busiest SM handles: ceil(ceil(count / A) / SMs) * A.  The atoms
-// per CTA A (1, 2, 4 or 6..9) minimise it; ties go to the larger A, whose
-// weight loads serve more atoms.  Small systems thus spread one atom per CTA
-// over all SMs, large ones keep 6-9 atoms per CTA.
+// `b`.  Atoms per CTA A: when 6 per CTA would leave SMs idle, each CTA gets
+// an SM of its own and the time goes with A, so A in {1, 2, 4, 6} minimises
+// ceil(ceil(count / A) / SMs) * A (ties to the larger A, whose weight loads
+// serve more atoms).  Otherwise A in 6..9 minimises (waves x A) with the
+// CTAs that fit on an SM at once, since the kernel is arithmetic bound and a
+// partly filled last wave idles SMs.
 template <typename Real>
 dp_status launch_fit(dp_model *m, const int32_t *order, int t, int64_t p0, int64_t b, int64_t count, const Real *D, Real *dD,
                      double *E_atom, cudaStream_t st)
@@ -589,14 +589,26 @@ dp_status launch_fit(dp_model *m, const int32_t *order, int t, int64_t p0, int64
     const ModelDev &md = m->dev;
     int nsm = 0;
     DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
-    static const int choices[] = {1, 2, 4, 6, 7, 8, 9};
     int bestA = 0;
     long best = -1;
-    for (int A : choices) {
-        if (fit_smem<Real>(md, A) > 227 * 1024) continue;
-        const long tiles = (long)((count + A - 1) / A);
-        const long cost = ((tiles + nsm - 1) / nsm) * A;
-        if (best < 0 || cost <= best) { best = cost; bestA = A; }
+    if (count < 6L * nsm) {
+        for (int A : {1, 2, 4, 6}) {
+            if (fit_smem<Real>(md, A) > 227 * 1024) continue;
+            const long tiles = (long)((count + A - 1) / A);
+            const long cost = ((tiles + nsm - 1) / nsm) * A;
+            if (best < 0 || cost <= best) { best = cost; bestA = A; }
+        }
+    } else {
+        for (int A = 6; A <= 9; ++A) {
+            const size_t sm = fit_smem<Real>(md, A);
+            if (sm > 227 * 1024) continue;
+            const long fit = (long)((228 * 1024) / (sm + 1024));
+            const long per_sm = fit < 1 ? 1 : (fit > 8 ? 8 : fit);
+            const long tiles = (long)((count + A - 1) / A);
+            const long slots = (long)nsm * per_sm;
+            const long cost = ((tiles + slots - 1) / slots) * A;
+            if (best < 0 || cost < best) { best = cost; bestA = A; }
+        }
     }
     if (bestA == 0) {
         set_error("fitting net too wide for the shared-memory tile");
@@ -691,8 +703,8 @@ dp_status compute_simt(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
             s = launch_batch<ShapePaper, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, st);
         if (s != DP_OK) return s;
     }
-    ProfScope ps(m->prof, PG_REDUCE, 1, st);
-    return reduce_energy_virial(d_atom_energy, d_atom_virial, n, d_energy, d_virial, st);
+    ProfScope ps(m->prof, PG_REDUCE, 2, st);
+    return reduce_energy_virial(d_atom_energy, d_atom_virial, n, d_energy, d_virial, m->d_red, st);
 }
 
 }  // namespace

@@ -12,7 +12,7 @@
 // Work unit: a tile of 128 neighbor rows = 4 chunks of 32 rows, one chunk per
 // warp; every chunk is up to 32 neighbors of one type of one atom, and the 4
 // chunks of a tile share the (center type, neighbor type) net.  Tiles are
-// listed per evaluation by k_chunk_build; persistent CTAs walk them.  Each
+// listed per evaluation (k_cb_count / k_cb_plan / k_cb_write); persistent CTAs walk them.  Each
 // CTA keeps the packed weights of the current net in shared memory, loaded
 // by one bulk copy on the TMA engine.
 //
@@ -615,48 +615,119 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, const 
 
 // Work list: for each (center type, neighbor type) group, the 32-neighbor
 // chunks of its atoms (type-sorted order), padded with empty chunks to a
-// multiple of 4 so that a tile never mixes nets.  One block; every thread
-// walks a contiguous run of atoms.  Entry = {atom, tj, first slot, net}.
-__global__ void __launch_bounds__(1024) k_chunk_build(ModelDev md, const int32_t *__restrict__ order,
-                                                     const int64_t *__restrict__ type_off,
-                                                     const int64_t *__restrict__ type_cnt,
-                                                     const int32_t *__restrict__ nnei, int4 *__restrict__ chunks,
-                                                     int *__restrict__ ntiles)
+// multiple of 4 so that a tile never mixes nets.  Entry = {atom, tj, first
+// slot, net}.  Built by three kernels: per 1024 positions, an exclusive scan
+// of the chunk counts (k_cb_count); one block scanning the block sums and
+// placing the groups (k_cb_plan); the scatter of the entries (k_cb_write).
+constexpr int kCbThreads = 1024;
+
+// Exclusive scan of v over the block (kCbThreads threads); *total = sum.
+__device__ __forceinline__ int block_excl_scan(int v, int *warp_sums, int *total)
 {
-    __shared__ int part[1024];
-    const int t = threadIdx.x, nt = blockDim.x;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = warp_sums[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const int incl = x + (w > 0 ? warp_sums[w - 1] : 0);
+    *total = warp_sums[31];
+    __syncthreads();
+    return incl - v;
+}
+
+// loc[tj][p] = chunks of positions [block start, p) for neighbor type tj;
+// bsum[tj][block] = the block's total.
+__global__ void __launch_bounds__(kCbThreads) k_cb_count(ModelDev md, int64_t n, const int32_t *__restrict__ order,
+                                                        const int32_t *__restrict__ nnei, int *__restrict__ loc,
+                                                        int *__restrict__ bsum, int nb)
+{
+    __shared__ int ws[32];
+    const int64_t p = blockIdx.x * (int64_t)kCbThreads + threadIdx.x;
+    const int a = p < n ? order[p] : 0;
+    for (int tj = 0; tj < md.ntypes; ++tj) {
+        const int c = p < n ? (nnei[(int64_t)a * md.ntypes + tj] + 31) >> 5 : 0;
+        int total;
+        const int ex = block_excl_scan(c, ws, &total);
+        if (p < n) loc[(int64_t)tj * n + p] = ex;
+        if (threadIdx.x == 0) bsum[tj * nb + blockIdx.x] = total;
+    }
+}
+
+// One block: boff[tj][b] = exclusive scan of bsum[tj][.]; per group (ti, tj)
+// its first entry gbase and the chunk prefix tstart at its first position;
+// the padding entries; the tile count.
+__global__ void __launch_bounds__(kCbThreads) k_cb_plan(ModelDev md, int64_t n, const int64_t *__restrict__ type_off,
+                                                       const int64_t *__restrict__ type_cnt,
+                                                       const int *__restrict__ loc, const int *__restrict__ bsum,
+                                                       int *__restrict__ boff, int nb, int *__restrict__ gtab,
+                                                       int4 *__restrict__ chunks, int *__restrict__ ntiles)
+{
+    __shared__ int ws[32];
+    __shared__ int tot[kMaxTypes];
+    for (int tj = 0; tj < md.ntypes; ++tj) {
+        int carry = 0;
+        for (int b0 = 0; b0 < nb; b0 += kCbThreads) {
+            const int b = b0 + threadIdx.x;
+            const int v = b < nb ? bsum[tj * nb + b] : 0;
+            int total;
+            const int ex = block_excl_scan(v, ws, &total);
+            if (b < nb) boff[tj * nb + b] = carry + ex;
+            carry += total;
+        }
+        if (threadIdx.x == 0) tot[tj] = carry;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    // prefix of neighbor type tj at position q (q <= n)
+    auto prefix = [&](int tj, int64_t q) -> int {
+        if (q >= n) return tot[tj];
+        return boff[tj * nb + (int)(q / kCbThreads)] + loc[(int64_t)tj * n + q];
+    };
     int base = 0;
     for (int ti = 0; ti < md.ntypes; ++ti) {
-        const int64_t off = type_off[ti], cnt = type_cnt[ti];
-        const int64_t per = (cnt + nt - 1) / nt;
-        const int64_t b = off + t * per, e = min(off + cnt, b + per);
         for (int tj = 0; tj < md.ntypes; ++tj) {
             const int net = ti * md.ntypes + tj;
-            int s = 0;
-            for (int64_t p = b; p < e; ++p) s += (nnei[(int64_t)order[p] * md.ntypes + tj] + 31) >> 5;
-            part[t] = s;
-            __syncthreads();
-            for (int o = 1; o < nt; o <<= 1) {
-                int v = t >= o ? part[t - o] : 0;
-                __syncthreads();
-                part[t] += v;
-                __syncthreads();
-            }
-            int w = base + part[t] - s;
-            for (int64_t p = b; p < e; ++p) {
-                const int a = order[p];
-                const int nch = (nnei[(int64_t)a * md.ntypes + tj] + 31) >> 5;
-                for (int c = 0; c < nch; ++c) chunks[w++] = make_int4(a, tj, c * 32, net);
-            }
-            const int total = part[nt - 1];
-            __syncthreads();
-            if (t == 0)
-                for (int q = total; q % 4 != 0; ++q) chunks[base + q] = make_int4(-1, tj, 0, net);
+            const int s0 = prefix(tj, type_off[ti]);
+            const int s1 = prefix(tj, type_off[ti] + type_cnt[ti]);
+            const int total = type_cnt[ti] > 0 ? s1 - s0 : 0;
+            gtab[2 * net] = base;
+            gtab[2 * net + 1] = s0;
+            for (int q = total; q % 4 != 0; ++q) chunks[base + q] = make_int4(-1, tj, 0, net);
             base += (total + 3) / 4 * 4;
-            __syncthreads();
         }
     }
-    if (t == 0) *ntiles = base / 4;
+    *ntiles = base / 4;
+}
+
+__global__ void __launch_bounds__(kCbThreads) k_cb_write(ModelDev md, int64_t n, const int32_t *__restrict__ order,
+                                                        const int32_t *__restrict__ type,
+                                                        const int32_t *__restrict__ nnei, const int *__restrict__ loc,
+                                                        const int *__restrict__ boff, int nb,
+                                                        const int *__restrict__ gtab, int4 *__restrict__ chunks)
+{
+    const int64_t p = blockIdx.x * (int64_t)kCbThreads + threadIdx.x;
+    if (p >= n) return;
+    const int a = order[p], ti = type[a];
+    for (int tj = 0; tj < md.ntypes; ++tj) {
+        const int nch = (nnei[(int64_t)a * md.ntypes + tj] + 31) >> 5;
+        const int net = ti * md.ntypes + tj;
+        const int dst = gtab[2 * net] + boff[tj * nb + blockIdx.x] + loc[(int64_t)tj * n + p] - gtab[2 * net + 1];
+        for (int c = 0; c < nch; ++c) chunks[dst + c] = make_int4(a, tj, c * 32, net);
+    }
 }
 
 // D[p] = T T<^T of atom order[p] (T scaled by 1/sum(sel)), flattened a*M2 + b.
@@ -740,18 +811,18 @@ struct FitShape {
 template <class S, int BF>
 __global__ void __launch_bounds__(128, 1) k_fit_tc(ModelDev md, const int32_t *__restrict__ order, int64_t pos_begin,
                                                   int64_t count, const float *__restrict__ T,
-                                                  const unsigned char *__restrict__ img, float *__restrict__ tstore,
-                                                  double *__restrict__ E_atom, float *__restrict__ dT, int *err)
+                                                  const unsigned char *__restrict__ img, double *__restrict__ E_atom,
+                                                  float *__restrict__ dT, int *err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar_t[2], bar_m[2];
     __shared__ uint32_t tmem_base;
     constexpr int F = S::F, KC = S::KC, M2 = S::M2, M1 = S::M1;
+    constexpr int AK = KC / M2;                 // rows a of T per K chunk of layer 1
     const int tid = threadIdx.x, warp = tid >> 5;
     unsigned char *A = smem + S::A_OFF, *B = smem + S::B_OFF;
     float *vec = reinterpret_cast<float *>(smem + S::V_OFF);
     const float *b1 = vec, *b2 = vec + F, *b3 = vec + 2 * F, *wo = vec + 3 * F;
-    float *ts = tstore + (int64_t)blockIdx.x * 2 * F * 128;
     if (tid == 0) {
         for (int q = 0; q < 2; ++q) {
             tc::mbar_init(&bar_t[q], 1);
@@ -769,6 +840,9 @@ __global__ void __launch_bounds__(128, 1) k_fit_tc(ModelDev md, const int32_t *_
     tc::fence_after_sync();
     const uint32_t tm = tmem_base;
     const uint32_t trow = tm + ((uint32_t)(warp * 32) << 16);
+    // columns 256.. of this row: t1 (FP32) after layer 1, then the packed
+    // derivative factors (1 - t1^2, 1 - t2^2) as fp16 pairs until the backward
+    const uint32_t tsc = trow + 256;
     const float bout = vec[4 * F];
     const float inv2 = (float)(md.inv_nsel * md.inv_nsel);
     const uint32_t idF = tc::idesc_f16(128, F, BF), idN = tc::idesc_f16(128, S::NC, BF);
@@ -799,15 +873,15 @@ __global__ void __launch_bounds__(128, 1) k_fit_tc(ModelDev md, const int32_t *_
             tc::bulk_g2s(dst, img + off, bytes, &bar_t[s]);
         }
     };
-    // issue one GEMM over the full A tile (K = F) after the A writes of every thread
-    auto gemm_full = [&](uint32_t d, int N_id_is_F) -> bool {
+    // one GEMM over the full A tile (K = F) after the A (and TMEM) writes of every thread
+    auto gemm_full = [&](uint32_t d, int N_id_is_F, bool acc0) -> bool {
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
         if (!waitv(&bar_t[0], ph_t[0])) return false;
         if (tid == 0) {
             tc::fence_after_sync();
-            mma(d, A, B, F, N_id_is_F ? idF : idN, false);
+            mma(d, A, B, F, N_id_is_F ? idF : idN, acc0);
             tc::mma_commit(&bar_m[0]);
         }
         if (!waitv(&bar_m[0], ph_m[0])) return false;
@@ -819,24 +893,35 @@ __global__ void __launch_bounds__(128, 1) k_fit_tc(ModelDev md, const int32_t *_
         const bool valid = r0 < count;
         const int atom = valid ? order[pos_begin + r0] : 0;
         const float4 *Ta = reinterpret_cast<const float4 *>(T + (int64_t)atom * 4 * M1);
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 tb[M2];
 #pragma unroll
-        for (int b = 0; b < M2; ++b) tb[b] = valid ? Ta[b] : make_float4(0.f, 0.f, 0.f, 0.f);
-        // ---- layer 1: D x W1, K in chunks of 64, two stages
+        for (int b = 0; b < M2; ++b) tb[b] = valid ? Ta[b] : zero4;
+        // ---- layer 1: D x W1, K in chunks of KC, two stages; the T rows of
+        // the next chunk are loaded while this one is built
+        float4 nxt[AK];
+#pragma unroll
+        for (int q = 0; q < AK; ++q) nxt[q] = valid ? Ta[q] : zero4;
         for (int kc = 0; kc < S::NK1; ++kc) {
             const int s = kc & 1;
             if (kc >= 2 && !waitv(&bar_m[s], ph_m[s])) { dead = true; break; }
             load_b(s, S::W1T_OFF + (uint32_t)kc * F * KC * 2, F * KC * 2, B + s * F * KC * 2);
+            float4 cur[AK];
+#pragma unroll
+            for (int q = 0; q < AK; ++q) cur[q] = nxt[q];
+            if (kc + 1 < S::NK1) {
+#pragma unroll
+                for (int q = 0; q < AK; ++q) nxt[q] = valid ? Ta[(kc + 1) * AK + q] : zero4;
+            }
             unsigned char *As = A + s * 128 * KC * 2;
-            // KC is a multiple of M2, so b = (c8 + u) % M2 is known at compile time
 #pragma unroll
             for (int c8 = 0; c8 < KC; c8 += 8) {
                 float v[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const int a = (kc * KC) / M2 + (c8 + u) / M2, b = (c8 + u) % M2;
-                    const float4 ta = valid ? Ta[a] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    v[u] = (ta.x * tb[b].x + ta.y * tb[b].y + ta.z * tb[b].z + ta.w * tb[b].w) * inv2;
+                    const float4 ta = cur[(c8 + u) / M2];
+                    const float4 t2 = tb[(c8 + u) % M2];
+                    v[u] = (ta.x * t2.x + ta.y * t2.y + ta.z * t2.z + ta.w * t2.w) * inv2;
                 }
                 st_row8<BF>(As, tid, c8, KC, v);
             }
@@ -856,44 +941,52 @@ __global__ void __launch_bounds__(128, 1) k_fit_tc(ModelDev md, const int32_t *_
         if (dead) break;
         tc::fence_after_sync();
         load_b(0, S::W2T_OFF, F * F * 2, B);
-        // layer-1 epilogue: t1 = tanh(z + b1) (plain layer), kept for the backward
+        // layer-1 epilogue: t1 = tanh(z + b1) (plain layer), kept in TMEM for layer 2
 #pragma unroll 1
         for (int c0 = 0; c0 < F; c0 += 16) {
             float z[16], v[16];
+            uint32_t w[16];
             tc::tmem_ld16(trow + c0, z);
             tc::tmem_ld_wait();
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
-                const int k = c0 + u;
-                const float t = tc::tanh_fast(z[u] + b1[k]);
-                ts[k * 128 + tid] = t;
-                v[u] = t;
+                v[u] = tc::tanh_fast(z[u] + b1[c0 + u]);
+                w[u] = __float_as_uint(v[u]);
             }
+            tc::tmem_st16(tsc + c0, w);
             st_row8<BF>(A, tid, c0, F, v);
             st_row8<BF>(A, tid, c0 + 8, F, v + 8);
         }
-        if (!gemm_full(tm, 1)) { dead = true; break; }
+        tc::tmem_st_wait();
+        if (!gemm_full(tm, 1, false)) { dead = true; break; }
         load_b(0, S::W3T_OFF, F * F * 2, B);
-        // layer-2 epilogue: y2 = t1 + t2
+        // layer-2 epilogue: y2 = t1 + t2; E gets y2 . w now (y3 = y2 + t3);
+        // the derivative factors of layers 1 and 2 replace t1
+        float e = 0.f;
 #pragma unroll 1
         for (int c0 = 0; c0 < F; c0 += 16) {
-            float z[16], v[16];
+            float z[16], t1[16], v[16];
+            uint32_t w[16];
             tc::tmem_ld16(trow + c0, z);
+            tc::tmem_ld16(tsc + c0, t1);
             tc::tmem_ld_wait();
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
                 const int k = c0 + u;
                 const float t = tc::tanh_fast(z[u] + b2[k]);
-                ts[(F + k) * 128 + tid] = t;
-                v[u] = ts[k * 128 + tid] + t;
+                v[u] = t1[u] + t;
+                e = fmaf(v[u], wo[k], e);
+                __half2 h = __floats2half2_rn(1.f - t1[u] * t1[u], 1.f - t * t);
+                w[u] = *reinterpret_cast<uint32_t *>(&h);
             }
+            tc::tmem_st16(tsc + c0, w);
             st_row8<BF>(A, tid, c0, F, v);
             st_row8<BF>(A, tid, c0 + 8, F, v + 8);
         }
-        if (!gemm_full(tm, 1)) { dead = true; break; }
+        tc::tmem_st_wait();
+        if (!gemm_full(tm, 1, false)) { dead = true; break; }
         load_b(0, S::W3B_OFF, F * F * 2, B);
-        // layer-3 epilogue: y3 = t1 + t2 + t3, E_i = y3 . w + b (FP32), dz3 = w (1 - t3^2)
-        float e = 0.f;
+        // layer-3 epilogue: E_i = (y2 + t3) . w + b (FP32), dz3 = w (1 - t3^2)
 #pragma unroll 1
         for (int c0 = 0; c0 < F; c0 += 16) {
             float z[16], v[16];
@@ -903,47 +996,52 @@ __global__ void __launch_bounds__(128, 1) k_fit_tc(ModelDev md, const int32_t *_
             for (int u = 0; u < 16; ++u) {
                 const int k = c0 + u;
                 const float t = tc::tanh_fast(z[u] + b3[k]);
-                const float y3 = ts[k * 128 + tid] + ts[(F + k) * 128 + tid] + t;
-                e = fmaf(y3, wo[k], e);
+                e = fmaf(t, wo[k], e);
                 v[u] = wo[k] * (1.f - t * t);
             }
             st_row8<BF>(A, tid, c0, F, v);
             st_row8<BF>(A, tid, c0 + 8, F, v + 8);
         }
         if (valid) E_atom[atom] = (double)(e + bout);
-        if (!gemm_full(tm, 1)) { dead = true; break; }
+        if (!gemm_full(tm, 1, false)) { dead = true; break; }
         load_b(0, S::W2B_OFF, F * F * 2, B);
-        // dY2 epilogue: dy2 = dz3 W3^T + w (skip of layer 3), dz2 = dy2 (1 - t2^2); dy2 replaces t2
+        // dY2 epilogue: dy2 = dz3 W3^T + w (skip of layer 3), dz2 = dy2 (1 - t2^2);
+        // dy2 goes back into the accumulator, so that the next MMA adds dz2 W2^T
+        // to it (the skip of layer 2)
 #pragma unroll 1
         for (int c0 = 0; c0 < F; c0 += 16) {
-            float z[16], v[16];
+            float z[16], pk[16], v[16];
+            uint32_t w[16];
             tc::tmem_ld16(trow + c0, z);
+            tc::tmem_ld16(tsc + c0, pk);
             tc::tmem_ld_wait();
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
-                const int k = c0 + u;
-                const float dy2 = z[u] + wo[k];
-                const float t2 = ts[(F + k) * 128 + tid];
-                ts[(F + k) * 128 + tid] = dy2;
-                v[u] = dy2 * (1.f - t2 * t2);
+                const float dy2 = z[u] + wo[c0 + u];
+                uint32_t bits = __float_as_uint(pk[u]);
+                const float2 g = __half22float2(*reinterpret_cast<__half2 *>(&bits));
+                v[u] = dy2 * g.y;
+                w[u] = __float_as_uint(dy2);
             }
+            tc::tmem_st16(trow + c0, w);
             st_row8<BF>(A, tid, c0, F, v);
             st_row8<BF>(A, tid, c0 + 8, F, v + 8);
         }
-        if (!gemm_full(tm, 1)) { dead = true; break; }
+        tc::tmem_st_wait();
+        if (!gemm_full(tm, 1, true)) { dead = true; break; }
         load_b(0, S::W1B_OFF, S::NC * F * 2, B);
-        // dY1 epilogue: dy1 = dz2 W2^T + dy2 (skip of layer 2), dz1 = dy1 (1 - t1^2)
+        // dY1 epilogue: dy1 = dy2 + dz2 W2^T (from the accumulator), dz1 = dy1 (1 - t1^2)
 #pragma unroll 1
         for (int c0 = 0; c0 < F; c0 += 16) {
-            float z[16], v[16];
+            float z[16], pk[16], v[16];
             tc::tmem_ld16(trow + c0, z);
+            tc::tmem_ld16(tsc + c0, pk);
             tc::tmem_ld_wait();
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
-                const int k = c0 + u;
-                const float dy1 = z[u] + ts[(F + k) * 128 + tid];
-                const float t1 = ts[k * 128 + tid];
-                v[u] = dy1 * (1.f - t1 * t1);
+                uint32_t bits = __float_as_uint(pk[u]);
+                const float2 g = __half22float2(*reinterpret_cast<__half2 *>(&bits));
+                v[u] = z[u] * g.x;
             }
             st_row8<BF>(A, tid, c0, F, v);
             st_row8<BF>(A, tid, c0 + 8, F, v + 8);
@@ -951,24 +1049,30 @@ __global__ void __launch_bounds__(128, 1) k_fit_tc(ModelDev md, const int32_t *_
         // dE/dD = dz1 W1^T in N chunks, folded into dE/dT
         float4 dtb[M2];
 #pragma unroll
-        for (int b = 0; b < M2; ++b) dtb[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int b = 0; b < M2; ++b) dtb[b] = zero4;
         float4 *dTa = reinterpret_cast<float4 *>(dT + (int64_t)atom * 4 * M1);
         for (int j = 0; j < S::NB1 && !dead; ++j) {
             const uint32_t reg = (uint32_t)(j & 1) * 256;
-            if (!gemm_full(tm + reg, 0)) { dead = true; break; }
+            if (!gemm_full(tm + reg, 0, false)) { dead = true; break; }
             if (j + 1 < S::NB1) load_b(0, S::W1B_OFF + (uint32_t)(j + 1) * S::NC * F * 2, S::NC * F * 2, B);
+            // column block [c0 + h, c0 + h + HS) of this chunk is row a = a0 + (c0 + h) / M2 of T;
+            // the next block's row is loaded ahead of its use
+            constexpr int HS = M2 < 16 ? M2 : 16;
+            const int a0 = (j * S::NC) / M2;
+            float4 tan = valid ? Ta[a0] : zero4;
 #pragma unroll
             for (int c0 = 0; c0 < S::NC; c0 += 16) {
                 float z[16];
                 tc::tmem_ld16(trow + reg + c0, z);
                 tc::tmem_ld_wait();
 #pragma unroll
-                for (int h = 0; h < 16; h += M2 < 16 ? M2 : 16) {
-                    const int a = (j * S::NC) / M2 + (c0 + h) / M2;
-                    const float4 ta = valid ? Ta[a] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int h = 0; h < 16; h += HS) {
+                    const int a = a0 + (c0 + h) / M2;
+                    const float4 ta = tan;
+                    if ((c0 + h) / M2 + 1 < S::NC / M2) tan = valid ? Ta[a + 1] : zero4;
+                    float4 acc = zero4;
 #pragma unroll
-                    for (int u = 0; u < (M2 < 16 ? M2 : 16); ++u) {
+                    for (int u = 0; u < HS; ++u) {
                         const int b = (c0 + h + u) % M2;
                         const float dd = z[h + u];
                         acc.x = fmaf(dd, tb[b].x, acc.x);
@@ -1138,8 +1242,8 @@ int fit_tc_kind(const ModelDev &md)
 }
 
 template <class FS, int BF>
-dp_status launch_fit_tc(dp_model *m, dp_nlist *nl, const float *T, float *tstore, int grid, double *E_atom,
-                        float *dT, cudaStream_t st)
+dp_status launch_fit_tc(dp_model *m, dp_nlist *nl, const float *T, int grid, double *E_atom, float *dT,
+                        cudaStream_t st)
 {
     const ModelDev &md = m->dev;
     DP_CUDA(cudaFuncSetAttribute(k_fit_tc<FS, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FS::SMEM));
@@ -1150,20 +1254,20 @@ dp_status launch_fit_tc(dp_model *m, dp_nlist *nl, const float *T, float *tstore
         const unsigned g = (unsigned)(tiles < grid ? tiles : grid);
         const unsigned char *img = m->d_tcfit + ((size_t)BF * md.ntypes + t) * FS::IMG;
         ProfScope ps(m->prof, PG_FIT, 1, st);
-        k_fit_tc<FS, BF><<<g, 128, FS::SMEM, st>>>(md, nl->d_order, b, cnt, T, img, tstore, E_atom, dT, m->d_err);
+        k_fit_tc<FS, BF><<<g, 128, FS::SMEM, st>>>(md, nl->d_order, b, cnt, T, img, E_atom, dT, m->d_err);
         DP_CUDA(cudaGetLastError());
     }
     return DP_OK;
 }
 
 template <int BF>
-dp_status fit_tc(dp_model *m, dp_nlist *nl, const float *T, float *tstore, int grid, double *E_atom, float *dT,
+dp_status fit_tc(dp_model *m, dp_nlist *nl, const float *T, int grid, double *E_atom, float *dT,
                  cudaStream_t st)
 {
     switch (fit_tc_kind(m->dev)) {
-    case 1: return launch_fit_tc<FitWater, BF>(m, nl, T, tstore, grid, E_atom, dT, st);
-    case 2: return launch_fit_tc<FitStudent, BF>(m, nl, T, tstore, grid, E_atom, dT, st);
-    case 3: return launch_fit_tc<FitPaper, BF>(m, nl, T, tstore, grid, E_atom, dT, st);
+    case 1: return launch_fit_tc<FitWater, BF>(m, nl, T, grid, E_atom, dT, st);
+    case 2: return launch_fit_tc<FitStudent, BF>(m, nl, T, grid, E_atom, dT, st);
+    case 3: return launch_fit_tc<FitPaper, BF>(m, nl, T, grid, E_atom, dT, st);
     default: set_error("no tensor-core fitting kernel for this shape"); return DP_ERR_UNSUPPORTED;
     }
 }
@@ -1185,12 +1289,15 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     sz(sizeof(float) * md.desc_dim * n);
     sz(sizeof(int4) * max_chunks);
     sz(sizeof(int) * 4);
+    const int nb = (int)((n + kCbThreads - 1) / kCbThreads);
+    sz(sizeof(int) * (size_t)md.ntypes * n);             // chunk-count scans
+    sz(sizeof(int) * (size_t)2 * md.ntypes * nb);        // block sums and offsets
+    sz(sizeof(int) * 2 * kMaxTypes * kMaxTypes);          // group placement
     sz(sizeof(int64_t) * 2 * kMaxTypes);
     int nsm = 0;
     DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
     const bool tcfit = fit_tc_kind(md) != 0 && getenv("DP_SIMT_FIT") == nullptr;
     const int fgrid = nsm;
-    if (tcfit) sz(sizeof(float) * (size_t)fgrid * 2 * 256 * 128);
     DP_TRY(ensure_workspace(m, need));
     char *w = m->ws;
     auto carve = [&](size_t bytes) {
@@ -1204,8 +1311,11 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     float *dD = (float *)carve(sizeof(float) * md.desc_dim * n);
     int4 *chunks = (int4 *)carve(sizeof(int4) * max_chunks);
     int *cnt = (int *)carve(sizeof(int) * 4);
+    int *cb_loc = (int *)carve(sizeof(int) * (size_t)md.ntypes * n);
+    int *cb_bsum = (int *)carve(sizeof(int) * (size_t)2 * md.ntypes * nb);
+    int *cb_boff = cb_bsum + (size_t)md.ntypes * nb;
+    int *cb_gtab = (int *)carve(sizeof(int) * 2 * kMaxTypes * kMaxTypes);
     int64_t *ttab = (int64_t *)carve(sizeof(int64_t) * 2 * kMaxTypes);
-    float *tstore = tcfit ? (float *)carve(sizeof(float) * (size_t)fgrid * 2 * 256 * 128) : nullptr;
     int64_t htab[2 * kMaxTypes] = {0};
     for (int t = 0; t < md.ntypes; ++t) {
         htab[t] = nl->type_off[t];
@@ -1224,8 +1334,12 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     const float2 *envB = reinterpret_cast<const float2 *>(nl->d_env + 4 * (size_t)n * md.nsel);
     const unsigned grid = (unsigned)(2 * nsm);
     {
-        ProfScope ps(m->prof, PG_CHUNKS, 1, st);
-        k_chunk_build<<<1, 1024, 0, st>>>(md, nl->d_order, ttab, ttab + kMaxTypes, nl->d_nnei, chunks, cnt);
+        ProfScope ps(m->prof, PG_CHUNKS, 3, st);
+        k_cb_count<<<nb, kCbThreads, 0, st>>>(md, n, nl->d_order, nl->d_nnei, cb_loc, cb_bsum, nb);
+        k_cb_plan<<<1, kCbThreads, 0, st>>>(md, n, ttab, ttab + kMaxTypes, cb_loc, cb_bsum, cb_boff, nb, cb_gtab,
+                                            chunks, cnt);
+        k_cb_write<<<nb, kCbThreads, 0, st>>>(md, n, nl->d_order, nl->d_type, nl->d_nnei, cb_loc, cb_boff, nb,
+                                              cb_gtab, chunks);
     }
     DP_CUDA(cudaGetLastError());
     DP_CUDA(cudaFuncSetAttribute(k_embed_fwd_tc<S, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::FWD_SMEM));
@@ -1238,7 +1352,7 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     DP_CUDA(cudaGetLastError());
     const int64_t nd = (int64_t)md.desc_dim * n, nq = (int64_t)4 * md.m1 * n;
     if (tcfit) {
-        DP_TRY(fit_tc<BF>(m, nl, T, tstore, fgrid, d_atom_energy, dT, st));
+        DP_TRY(fit_tc<BF>(m, nl, T, fgrid, d_atom_energy, dT, st));
     } else {
         {
             ProfScope ps(m->prof, PG_DESC, 1, st);
@@ -1258,8 +1372,8 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
                                                                      cnt, wimg, dT, d_force, d_atom_virial, m->d_err);
     }
     DP_CUDA(cudaGetLastError());
-    ProfScope ps(m->prof, PG_REDUCE, 1, st);
-    return reduce_energy_virial(d_atom_energy, d_atom_virial, n, d_energy, d_virial, st);
+    ProfScope ps(m->prof, PG_REDUCE, 2, st);
+    return reduce_energy_virial(d_atom_energy, d_atom_virial, n, d_energy, d_virial, m->d_red, st);
 }
 
 }  // namespace

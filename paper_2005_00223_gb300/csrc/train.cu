@@ -148,8 +148,8 @@ dp_status dp_param_grad(dp_model *m, dp_nlist *nl, const double *coord, const do
     DP_TRY(nlist_format_device(m, nl, t.coord, st));
     if (n > 0) {
         DP_TRY(param_grad_device(m, nl, t.v, t.scal + 8, prec, t.Ei, t.Edi, t.grad, st));
-        DP_TRY(reduce_energy_virial(t.Ei, nullptr, n, t.scal, nullptr, st));
-        DP_TRY(reduce_energy_virial(t.Edi, nullptr, n, t.scal + 1, nullptr, st));
+        DP_TRY(reduce_energy_virial(t.Ei, nullptr, n, t.scal, nullptr, m->d_red, st));
+        DP_TRY(reduce_energy_virial(t.Edi, nullptr, n, t.scal + 1, nullptr, m->d_red, st));
     } else {
         DP_CUDA(cudaMemsetAsync(t.scal, 0, 2 * sizeof(double), st));
     }
