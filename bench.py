@@ -231,6 +231,219 @@ def run_mine(args, rank, world):
     return out
 
 
+def grad_frames():
+    """Config 3's training batch: 32 seeded 192-atom water frames with seeded reference labels."""
+    cfg = dpsynth.water_config()
+    params = dpsynth.model_params(cfg, 7)
+    rng = np.random.default_rng(5)
+    frames = []
+    for s in range(32):
+        c, t, b = dpsynth.water_box(100 + s)
+        frames.append((c, t, b, float(rng.normal()), rng.normal(scale=1e-3, size=c.shape)))
+    return cfg, params, frames
+
+
+def grad_flops(cfg, nnei_total: int, n: int):
+    """Algorithmic FLOP of one force-loss gradient of a frame: 3x an evaluation.
+
+    Per layer with C multiply-adds per row, the evaluation does 2C (forward and
+    input gradient); the gradient does the primal and the tangent forward (2C)
+    and the reverse of both, input adjoints and weight gradients (4C).
+    """
+    f = flops_per_group(cfg, nnei_total, n)
+    return 3 * sum(f.values())
+
+
+def run_grad(args, rank, world):
+    """Parameter gradient of the force-matching loss over the 32 water frames (rows a11 / config 3)."""
+    import torch
+
+    import paper_2005_00223_gb300 as dp
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    prec = args.precision if args.precision in ("fp64", "mix32") else "fp64"
+    cfg, params, frames = grad_frames()
+    typ, box = frames[0][1], frames[0][2]
+    n = len(typ)
+    model = dp.Model(cfg, 0, params=params)
+    stream = torch.cuda.Stream(device=dev)
+    dp.dp_model_set_stream(model.h, stream)
+    X = torch.tensor(np.array([f[0] for f in frames]), dtype=torch.float64, device=dev)
+    Fr = torch.tensor(np.array([f[4] for f in frames]), dtype=torch.float64, device=dev)
+    Er = torch.tensor([f[3] for f in frames], dtype=torch.float64, device=dev)
+    grad = torch.zeros(dp.dp_model_n_params(model.h), dtype=torch.float64, device=dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    nl = dp.NeighborList(model, frames[0][0], typ, box, skin=0.0)
+    nnei_total = 0
+    for f in frames:
+        nl.update(f[0], box)
+        nnei_total += int((nl.get()[0] >= 0).sum())
+
+    torch.cuda.synchronize()
+
+    def one_gradient():
+        grad.zero_()
+        loss.zero_()
+        for k in range(len(frames)):
+            dp.dp_nlist_update_dev(nl.h, X[k], stream)
+            dp.dp_force_loss_grad_dev(model.h, nl.h, X[k], box, Fr[k], Er[k:k + 1], 1.0, 100.0, prec, loss, grad,
+                                      stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_gradient()
+    sampler = ClockSampler()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    dp.dp_profile_enable(model.h, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            one_gradient()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop()
+    prof = dp.dp_profile_read(model.h)
+    dp.dp_profile_enable(model.h, False)
+    groups = {g: {"launches": v[0], "ms_total": round(v[1], 4), "share": round(v[1] / ms, 4)}
+              for g, v in prof.items() if v[0] > 0}
+    per_grad_s = ms * 1e-3 / args.steps
+    flop = grad_flops(cfg, nnei_total, n * len(frames))
+    kg = prof.get("param_grad", (0, 0.0))
+    peak = FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS
+    roofline = None
+    if kg[0] > 0:
+        achieved = flop * args.steps / (kg[1] * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": "param_grad", "achieved": round(achieved, 4), "peak": round(peak, 4),
+                    "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                    "peak_source": "derived: 152 SMs x %s FMA/clk x 2 FLOP x 2070 MHz" % (
+                        "2 FP64" if prec == "fp64" else "128 FP32"),
+                    "flop_model": "3 x the evaluation's algorithmic FLOP per frame"}
+    # end to end: the host-pointer call, one frame after another
+    e2e = None
+    if args.e2e_steps > 0:
+        g = np.zeros(dp.dp_model_n_params(model.h))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for f in frames:
+            nl.update(f[0], box)
+            dp.dp_force_loss_grad(model.h, nl.h, f[0], box, f[4], f[3], 1.0, 100.0, prec, grad=g)
+        t1 = time.perf_counter()
+        e2e = {"value": t1 - t0, "unit": "s/gradient", "h2d_bytes_per_step": len(frames) * n * 3 * 8 * 3,
+               "d2h_bytes_per_step": len(frames) * (g.size * 8 + 8),
+               "path": "dp_nlist_update + dp_force_loss_grad (host arrays) per frame"}
+    nl.close()
+    out = {"metric": "s/gradient (32 water frames of 192 atoms)", "value": per_grad_s, "unit": "s/gradient",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if prec == "fp64" else "f32", "precision": prec,
+           "data": "synthetic (seeded water frames and labels, seeded random-init weights)",
+           "config": {"workload": "force-loss parameter gradient, 32 x 64 H2O (192 atoms), rcut 6, sel 46/92",
+                      "frames": len(frames), "atoms_per_frame": n, "real_neighbors": nnei_total,
+                      "parameters": int(grad.numel()), "l2": "working set below L2; frames differ each call",
+                      "parallelism": "1 GPU"},
+           "gflop_per_step": flop / 1e9, "roofline": roofline, "kernel_groups": groups,
+           "gpu_launches": int(sum(v[0] for v in prof.values())), "clocks": clocks, "e2e": e2e}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        om = oracle.Model(cfg, params)
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        om.force_loss_grad(frames[:4], p_e=1.0, p_f=100.0)
+        el = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": el * len(frames) / 4, "unit": "s/gradient", "cores": cores,
+                               "kind": "oracle", "sample": "the FP64 oracle gradient of 4 of the 32 frames, x 8"}
+    return out
+
+
+def run_judged(args, rank, world):
+    """Distilled student MD judged by the full model every 10 steps (rows a12 / config 4).
+
+    Untimed: teacher frames from its own NVE at 300 K and 1,200 K on 4,000
+    atoms and 800 Adam steps of the student on them (the recipe of the
+    distillation test).  Timed: judged MD of the trained student on the
+    workload, the teacher evaluated at every judgement and taking over while
+    the student's force RMSE exceeds 0.1 x the teacher's RMS force.
+    """
+    import torch
+
+    import paper_2005_00223_gb300 as dp
+    from paper_2005_00223_gb300 import student as S
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    cfg = dpsynth.copper_config()
+    teacher = dp.Model(cfg, 0, params=dpsynth.model_params(cfg, 1))
+    c4, t4, b4 = dpsynth.copper_fcc(1, ncell=10)
+    mass = np.array([dpsynth.MASS["Cu"]])
+    vels = [dpsynth.velocities(mass[t4], T, 10 + k) for k, T in enumerate((300.0, 1200.0))]
+    X, E, F = S.teacher_frames(teacher, c4, t4, b4, mass, vels, nframes=24, stride=5, dt_fs=1.0)
+    frms = float(np.sqrt((F ** 2).sum(-1).mean()))
+    stu = dp.Model(dpsynth.copper_student_config(), seed=2)
+    S.train(stu, t4, b4, X, E, F, steps=800, lr0=3e-3, lr1=1e-4, p_e=1.0, p_f=100.0 / frms ** 2)
+    _, coord, typ, box, mass, dt, desc = workload(args.workload)
+    n = len(typ)
+    vel = dpsynth.velocities(mass[typ], 300.0, 1)
+    stream = torch.cuda.Stream(device=dev)
+    dp.dp_model_set_stream(stu.h, stream)
+    dp.dp_model_set_stream(teacher.h, stream)
+    nl0 = dp.NeighborList(teacher, coord, typ, box)
+    F0 = nl0.compute(coord, box, args.precision)[2]
+    nnei_total = int((nl0.get()[0] >= 0).sum())
+    nl0.close()
+    rmse_max = 0.1 * float(np.sqrt((F0 ** 2).sum(1).mean()))
+    state = dp.MDState(stu, coord, vel, typ, mass, box, skin=2.0)
+    every = 10
+    steps = max(every, (args.steps // every) * every)
+    dp.dp_md_step_judged(stu.h, teacher.h, state.h, every * max(1, args.warmup // every), dt, args.precision,
+                         args.precision, judge_every=every, rmse_max=rmse_max)
+    sampler = ClockSampler()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    dp.dp_profile_enable(stu.h, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    rm, fb = dp.dp_md_step_judged(stu.h, teacher.h, state.h, steps, dt, args.precision, args.precision,
+                                  judge_every=every, rmse_max=rmse_max)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop()
+    prof = dp.dp_profile_read(stu.h)
+    dp.dp_profile_enable(stu.h, False)
+    state.close()
+    step_s = ms * 1e-3 / steps
+    scfg = dpsynth.copper_student_config()
+    flops = flops_per_group(scfg, nnei_total, n)
+    top = max((g for g in flops if prof.get(g, (0, 0.0))[0] > 0), key=lambda g: prof[g][1], default=None)
+    roofline = None
+    if top is not None:
+        peak, src = tensor_peak()
+        # one launch per student evaluation (the teacher keeps its own counters)
+        achieved = flops[top] * prof[top][0] / (prof[top][1] * 1e-3) / 1e12
+        roofline = {"bound": "tensor", "kernel": "student " + top, "achieved": round(achieved, 4),
+                    "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(achieved / peak, 6), "traffic": None,
+                    "peak_source": src}
+    return {"metric": "s/step/atom (judged student MD)", "value": step_s / (n * world), "unit": "s/step/atom",
+            "n_gpus": world, "steps": steps, "warmup": every * max(1, args.warmup // every),
+            "ms_per_step": ms / steps, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "ns_per_day": 86400.0 * dt * 1e-6 / step_s, "dtype": args.precision, "precision": args.precision,
+            "data": "synthetic (seeded FCC copper; student distilled from the seeded teacher's own MD)",
+            "config": {"workload": desc, "atoms": n, "judge_every": every, "rmse_max_eV_per_A": rmse_max,
+                       "teacher_rms_force_eV_per_A": rmse_max / 0.1, "judgements": int(len(rm)),
+                       "fallback_windows": int(fb.sum()), "student_rmse_max": float(rm.max()),
+                       "student_rmse_mean": float(rm.mean()), "parallelism": "1 GPU",
+                       "l2": "working set per step > L2"},
+            "roofline": roofline, "kernel_groups": {g: {"launches": v[0], "ms_total": round(v[1], 4)}
+                                                 for g, v in prof.items() if v[0] > 0},
+            "gpu_launches": int(sum(v[0] for v in prof.values())), "clocks": clocks, "e2e": None}
+
+
 def run_e2e(dp, model, cfg, coord, vel, typ, box, mass, dt, args, stream):
     """dp_compute with host buffers every step; velocity Verlet on the host."""
     import torch
@@ -322,6 +535,9 @@ def main():
     ap.add_argument("--model", default="full", choices=["full", "student"])
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--task", default="md", choices=["md", "grad", "judged"],
+                    help="md: NVE steps (default); grad: force-loss parameter gradient over 32 water frames; "
+                         "judged: distilled student MD judged by the full model")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "mine":
         args.warmup = 3
@@ -332,6 +548,10 @@ def main():
         torch.distributed.init_process_group("nccl" if args.impl == "mine" else "gloo")
     if args.impl == "reference":
         out = run_reference(args, rank, world)
+    elif args.task == "grad":
+        out = run_grad(args, rank, world)
+    elif args.task == "judged":
+        out = run_judged(args, rank, world)
     else:
         out = run_mine(args, rank, world)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -118,28 +118,62 @@ struct TileCtx {
     int atom, tj, c0, net;
 };
 
-// Geometry of this thread's neighbor from the formatted list (s, u = d/r
-// and, for the backward pass, ds/dr and r; all evaluated in FP64 by the
-// formatting kernel), plus layer 1 in FP32; writes the layer-1 output row
-// into A2.  Rf = (s, s u_x, s u_y, s u_z) is the environment row of Eq. 4.
-template <class S, int BF, bool BWD>
-__device__ __forceinline__ void rows_layer1(const ModelDev &md, const float4 *__restrict__ envA,
-                                            const float2 *__restrict__ envB, const int32_t *__restrict__ nlist,
-                                            const int32_t *__restrict__ nnei, const TileCtx &ch, int lane, int row,
-                                            const float *vec, unsigned char *A2, float Rf[4], float t1[S::E0],
-                                            float geo[6], int &j, bool &valid)
+// One thread's row of a tile as read from global memory: the chunk entry,
+// the neighbor count of its (atom, type) block and the slot's neighbor
+// geometry (s, u = d/r and, for the backward pass, ds/dr, r and j; all
+// evaluated in FP64 by the formatting kernel).  Fetched one tile ahead: the
+// slot loads do not wait for the count (they stay inside the type block's
+// sel slots), and the row's validity is applied when it is used.
+struct RowIn {
+    TileCtx ch;
+    int net, cnt, j;
+    float4 a;
+    float2 b;
+};
+
+template <bool BWD>
+__device__ __forceinline__ RowIn fetch_row(const ModelDev &md, const int4 *__restrict__ chunks, int tile, int ntiles,
+                                           int warp, int lane, const int32_t *__restrict__ nnei,
+                                           const int32_t *__restrict__ nlist, const float4 *__restrict__ envA,
+                                           const float2 *__restrict__ envB)
 {
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-    float2 b = make_float2(0.f, 0.f);
-    j = -1;
-    valid = false;
-    if (ch.atom >= 0 && ch.c0 + lane < nnei[(int64_t)ch.atom * md.ntypes + ch.tj]) {
-        const int64_t slot = (int64_t)ch.atom * md.nsel + md.sel_off[ch.tj] + ch.c0 + lane;
-        j = nlist[slot];
-        a = envA[slot];
-        if (BWD) b = envB[slot];
-        valid = true;
+    RowIn r;
+    r.ch = TileCtx{-1, 0, 0, 0};
+    r.net = -1;
+    r.cnt = 0;
+    r.j = -1;
+    r.a = make_float4(0.f, 0.f, 0.f, 0.f);
+    r.b = make_float2(0.f, 0.f);
+    if (tile >= ntiles) return r;
+    const int4 c4 = chunks[(int64_t)tile * 4 + warp];
+    r.net = chunks[(int64_t)tile * 4].w;
+    r.ch = TileCtx{c4.x, c4.y, c4.z, c4.w};
+    if (c4.x >= 0) {
+        const int k = c4.z + lane;
+        r.cnt = nnei[(int64_t)c4.x * md.ntypes + c4.y];
+        if (k < md.sel[c4.y]) {
+            const int64_t slot = (int64_t)c4.x * md.nsel + md.sel_off[c4.y] + k;
+            r.a = envA[slot];
+            if (BWD) {
+                r.b = envB[slot];
+                r.j = nlist[slot];
+            }
+        }
     }
+    return r;
+}
+
+// The environment row Rf = (s, s u_x, s u_y, s u_z) of Eq. 4 and the
+// geometry of this thread's row (zero on padded rows), plus layer 1 in
+// FP32; writes the layer-1 output row into A2.
+template <class S, int BF, bool BWD>
+__device__ __forceinline__ void rows_layer1(const RowIn &in, int lane, int row, const float *vec, unsigned char *A2,
+                                            float Rf[4], float t1[S::E0], float geo[6], int &j, bool &valid)
+{
+    valid = in.ch.atom >= 0 && in.ch.c0 + lane < in.cnt;
+    const float4 a = valid ? in.a : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float2 b = valid ? in.b : make_float2(0.f, 0.f);
+    j = valid ? in.j : -1;
     Rf[0] = a.x;
     Rf[1] = a.x * a.y;
     Rf[2] = a.x * a.z;
@@ -149,7 +183,7 @@ __device__ __forceinline__ void rows_layer1(const ModelDev &md, const float4 *__
     geo[2] = a.w;
     geo[3] = b.x;                          // ds/dr
     geo[4] = b.y;                          // r
-    geo[5] = valid ? a.x / b.y : 0.f;      // s/r
+    geo[5] = (BWD && valid) ? a.x / b.y : 0.f;      // s/r
     const float *W1 = vec, *b1 = vec + S::K2;
     const float s = Rf[0];
     float buf[8];
@@ -237,10 +271,12 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const 
     uint32_t ph_mma = 0, ph_w = 0;
     int cur_net = -1;
     const int ntiles = *ntiles_ptr;
+    RowIn nxt = fetch_row<false>(md, chunks, blockIdx.x, ntiles, warp, lane, nnei, nlist, envA, nullptr);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int4 c4 = load_chunk(chunks, (int64_t)tile * 4 + warp);
-        const int net = load_chunk(chunks, (int64_t)tile * 4).w;
-        TileCtx ch{c4.x, c4.y, c4.z, c4.w};
+        const RowIn in = nxt;
+        nxt = fetch_row<false>(md, chunks, tile + gridDim.x, ntiles, warp, lane, nnei, nlist, envA, nullptr);
+        const int net = in.net;
+        const TileCtx ch = in.ch;
         if (net != cur_net) {
             if (tid == 0) {
                 tc::mbar_expect_tx(&mbar_w, S::IMG);
@@ -257,7 +293,7 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const 
         float Rf[4], t1[S::E0], t2[S::E1], geo[6];
         int j;
         bool valid;
-        rows_layer1<S, BF, false>(md, envA, nullptr, nlist, nnei, ch, lane, tid, vec, A2, Rf, t1, geo, j, valid);
+        rows_layer1<S, BF, false>(in, lane, tid, vec, A2, Rf, t1, geo, j, valid);
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
@@ -396,10 +432,12 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, const 
     uint32_t ph_mma = 0, ph_w = 0;
     int cur_net = -1;
     const int ntiles = *ntiles_ptr;
+    RowIn nxt = fetch_row<true>(md, chunks, blockIdx.x, ntiles, warp, lane, nnei, nlist, envA, envB);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int4 c4 = load_chunk(chunks, (int64_t)tile * 4 + warp);
-        const int net = load_chunk(chunks, (int64_t)tile * 4).w;
-        TileCtx ch{c4.x, c4.y, c4.z, c4.w};
+        const RowIn in = nxt;
+        nxt = fetch_row<true>(md, chunks, tile + gridDim.x, ntiles, warp, lane, nnei, nlist, envA, envB);
+        const int net = in.net;
+        const TileCtx ch = in.ch;
         if (net != cur_net) {
             if (tid == 0) {
                 tc::mbar_expect_tx(&mbar_w, S::IMG);
@@ -418,7 +456,7 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, const 
         float Rf[4], t1[S::E0], t2[S::E1], geo[6];
         int j;
         bool valid;
-        rows_layer1<S, BF, true>(md, envA, envB, nlist, nnei, ch, lane, tid, vec, A2, Rf, t1, geo, j, valid);
+        rows_layer1<S, BF, true>(in, lane, tid, vec, A2, Rf, t1, geo, j, valid);
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
