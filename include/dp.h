@@ -156,6 +156,20 @@ const char *dp_profile_group_name(int32_t group);
 dp_status dp_nlist_build(const dp_model *m, int64_t n, const double *coord, const int32_t *type,
                          const double box[9], double rcut, double skin, int32_t cand_cap, dp_nlist **out);
 
+/* Several independent configurations ("frames") of the same n atoms (same
+ * types, same box) as one list over nframes * n atoms: frame f holds atoms
+ * [f n, (f+1) n) and each frame has its own cell grid, so no neighbor
+ * crosses frames.  A training batch is evaluated by one call over it (all
+ * frames fill the GPU together).  coord [nframes][n][3], type [n] (shared
+ * by every frame), box as for dp_nlist_build; dp_nlist_update /
+ * dp_nlist_update_dev then take [nframes][n][3].  dp_compute over such a
+ * list returns the sums over the frames of E and W (E_i and F per atom);
+ * dp_force_loss_grad_dev sums the per-frame losses and gradients.  MD
+ * states build their own single-frame lists.  Errors: as dp_nlist_build. */
+dp_status dp_nlist_build_frames(const dp_model *m, int32_t nframes, int64_t n, const double *coord,
+                                const int32_t *type, const double box[9], double rcut, double skin,
+                                int32_t cand_cap, dp_nlist **out);
+
 /* Rebuild the candidates of an existing list at new coordinates (same n,
  * types, rcut, skin and capacity) and format it there. */
 dp_status dp_nlist_update(dp_nlist *nl, const double *coord, const double box[9]);
@@ -238,14 +252,17 @@ dp_status dp_param_grad(dp_model *m, dp_nlist *nl, const double *coord, const do
  * L = p_e ((E - E_ref)/n)^2 + p_f/(3n) sum_k |F_k - F_ref,k|^2, using
  * dL/dtheta = 2 p_e (E - E_ref)/n^2 dE/dtheta - 2 p_f/(3n) dEdot/dtheta
  * with v = F - F_ref.  E and F are evaluated in `prec` first.  *loss and
- * grad [n_params] are ADDED to (host memory). */
+ * grad [n_params] are ADDED to (host memory).  The list must hold one
+ * frame (DP_ERR_ARG otherwise). */
 dp_status dp_force_loss_grad(dp_model *m, dp_nlist *nl, const double *coord, const double box[9],
                              const double *F_ref, double E_ref, double p_e, double p_f, dp_precision prec,
                              double *loss, double *grad);
 
-/* Device-pointer form: d_coord [n][3], d_F_ref [n][3], d_E_ref [1], d_loss
- * [1] and d_grad [n_params] in device memory (the last two ADDED to),
- * enqueued on `stream` without host synchronisation. */
+/* Device-pointer form: d_coord [n][3], d_F_ref [n][3], d_E_ref [nframes]
+ * (one per frame of the list, see dp_nlist_build_frames), d_loss [1] and
+ * d_grad [n_params] in device memory (the last two ADDED to), enqueued on
+ * `stream` without host synchronisation.  Over frames, the loss and the
+ * gradient are the sums of the single-frame ones (n = atoms per frame). */
 dp_status dp_force_loss_grad_dev(dp_model *m, dp_nlist *nl, const double *d_coord, const double box[9],
                                  const double *d_F_ref, const double *d_E_ref, double p_e, double p_f,
                                  dp_precision prec, double *d_loss, double *d_grad, void *stream);

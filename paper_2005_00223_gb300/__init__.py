@@ -6,6 +6,8 @@ binding with the same entry-point names, plus small owning wrappers.
 """
 from __future__ import annotations
 
+import numpy as np
+
 from . import _lib
 from ._lib import (DP_FP64, DP_MIX32, DP_MIX_BF16, DP_MIX_FP16, DPError, EXPORTS, load,  # noqa: F401
                    dp_compute, dp_compute_dev, dp_md_state_create, dp_md_state_destroy, dp_md_state_get,
@@ -13,7 +15,8 @@ from ._lib import (DP_FP64, DP_MIX32, DP_MIX_BF16, DP_MIX_FP16, DPError, EXPORTS
                    dp_model_set_params, dp_model_set_stream, dp_nlist_build, dp_nlist_destroy, dp_nlist_get,
                    dp_nlist_update, dp_profile_enable, dp_profile_group_name, dp_profile_read,
                    dp_nlist_update_dev, dp_param_grad, dp_force_loss_grad, dp_force_loss_grad_dev, dp_adam_step,
-                   dp_model_sync_params, dp_md_step_judged, dp_nlist_format_noalloc, dp_tanh_f64_dev)
+                   dp_model_sync_params, dp_md_step_judged, dp_nlist_format_noalloc, dp_tanh_f64_dev,
+                   dp_nlist_build_frames)
 
 
 def build(force: bool = False) -> str:
@@ -57,6 +60,17 @@ class NeighborList:
         self.model = model
         self.n = len(typ)
         self.h = dp_nlist_build(model.h, coord, typ, box, model.cfg.rcut if rcut is None else rcut, skin, cand_cap)
+
+    @classmethod
+    def frames(cls, model: Model, coords, typ, box, skin: float = 0.0, cand_cap: int = 0, rcut=None):
+        """One list over independent frames coords [F][n][3] of the same atoms (see dp_nlist_build_frames)."""
+        self = cls.__new__(cls)
+        self.model = model
+        coords = np.asarray(coords, dtype=np.float64)
+        self.n = coords.shape[0] * len(typ)
+        self.h = dp_nlist_build_frames(model.h, coords, typ, box, model.cfg.rcut if rcut is None else rcut, skin,
+                                       cand_cap)
+        return self
 
     def update(self, coord, box):
         dp_nlist_update(self.h, coord, box)

@@ -31,7 +31,7 @@ EXPORTS = [
     "dp_nlist_destroy", "dp_nlist_update_dev", "dp_compute", "dp_compute_dev", "dp_md_state_create",
     "dp_md_step", "dp_md_state_get", "dp_md_state_destroy", "dp_param_grad", "dp_force_loss_grad",
     "dp_force_loss_grad_dev", "dp_adam_step", "dp_model_sync_params", "dp_md_step_judged",
-    "dp_nlist_format_noalloc", "dp_tanh_f64_dev",
+    "dp_nlist_format_noalloc", "dp_tanh_f64_dev", "dp_nlist_build_frames",
 ]
 
 
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
             "dp_nlist_update_dev": ([P, P, P], C.c_int),
             "dp_nlist_format_noalloc": ([I64, P, P, P, D, I32, P, P, P, P, P], C.c_int),
             "dp_tanh_f64_dev": ([I64, P, P, P], C.c_int),
+            "dp_nlist_build_frames": ([P, I32, I64, P, P, P, D, D, I32, P], C.c_int),
             "dp_param_grad": ([P, P, P, P, P, D, D, C.c_int, P, P, P], C.c_int),
             "dp_force_loss_grad": ([P, P, P, P, P, D, D, D, C.c_int, P, P], C.c_int),
             "dp_force_loss_grad_dev": ([P, P, P, P, P, P, D, D, C.c_int, P, P, P], C.c_int),
@@ -207,6 +208,16 @@ def dp_nlist_build(m, coord, typ, box, rcut: float, skin: float = 0.0, cand_cap:
     h = C.c_void_p()
     _check(load().dp_nlist_build(m, typ.size, _ptr(coord), _ptr(typ), _ptr(box), float(rcut), float(skin),
                                  int(cand_cap), C.byref(h)), "dp_nlist_build")
+    return h.value
+
+
+def dp_nlist_build_frames(m, coords, typ, box, rcut: float, skin: float = 0.0, cand_cap: int = 0):
+    """One list over nframes configurations coords [F][n][3] of the same atoms typ [n] in the same box."""
+    coords, typ, box = _f64(coords), _i32(typ), _box(box)
+    nframes = coords.shape[0]
+    h = C.c_void_p()
+    _check(load().dp_nlist_build_frames(m, int(nframes), typ.size, _ptr(coords), _ptr(typ), _ptr(box), float(rcut),
+                                        float(skin), int(cand_cap), C.byref(h)), "dp_nlist_build_frames")
     return h.value
 
 

@@ -473,11 +473,12 @@ static dp_status check_build_flags(dp_nlist *nl, cudaStream_t st)
 }  // extern "C"
 
 dp_status dp::nlist_create_internal(const dp_model *m, int64_t n, const int32_t *type, const double box[9],
-                                    double rcut, double skin, int32_t cand_cap, dp_nlist **out)
+                                    double rcut, double skin, int32_t cand_cap, dp_nlist **out, int32_t nframes)
 {
     if (!m || !out || (n > 0 && !type)) { set_error("dp_nlist_build: NULL argument"); return DP_ERR_ARG; }
     *out = nullptr;
     if (n < 0 || n >= (int64_t)1 << 26) { set_error("atom count %lld outside 0..2^26-1", (long long)n); return DP_ERR_ARG; }
+    if (nframes < 1 || n % nframes != 0) { set_error("%lld atoms do not split into %d frames", (long long)n, nframes); return DP_ERR_ARG; }
     if (!(rcut >= m->rcut) || !(skin >= 0) || !isfinite(rcut + skin)) {
         set_error("need rcut >= model rcut (%g) and skin >= 0 (got %g, %g)", m->rcut, rcut, skin);
         return DP_ERR_ARG;
@@ -500,11 +501,14 @@ dp_status dp::nlist_create_internal(const dp_model *m, int64_t n, const int32_t 
         int c = (int)floor(L[k] / nl->rlist);
         nl->nc[k] = c < 1 ? 1 : c;
     }
-    nl->ncell = (int64_t)nl->nc[0] * nl->nc[1] * nl->nc[2];
+    nl->nframes = nframes;
+    nl->frame_n = n / nframes;
+    nl->ncell_frame = (int64_t)nl->nc[0] * nl->nc[1] * nl->nc[2];
+    nl->ncell = nl->ncell_frame * nframes;
     if (cand_cap <= 0) {
-        double expect = (double)n / vol * 4.0 / 3.0 * M_PI * nl->rlist * nl->rlist * nl->rlist;
+        double expect = (double)nl->frame_n / vol * 4.0 / 3.0 * M_PI * nl->rlist * nl->rlist * nl->rlist;
         int64_t c = (int64_t)(expect * 1.3) + 64;
-        if (c > n) c = n;
+        if (c > nl->frame_n) c = nl->frame_n;
         c = (c + 31) / 32 * 32;
         nl->cap = (int32_t)(c < 32 ? 32 : c);
     } else {
@@ -607,6 +611,41 @@ dp_status dp_nlist_build(const dp_model *m, int64_t n, const double *coord, cons
         if (s == DP_OK) {
             cudaError_t e2 = cudaStreamSynchronize(m->stream);
             if (e2 != cudaSuccess) s = cuda_fail(e2, "dp_nlist_build");
+        }
+        if (s != DP_OK) {
+            dp_nlist_destroy(nl);
+            return s;
+        }
+    }
+    *out = nl;
+    return DP_OK;
+}
+
+dp_status dp_nlist_build_frames(const dp_model *m, int32_t nframes, int64_t n, const double *coord,
+                                const int32_t *type, const double box[9], double rcut, double skin,
+                                int32_t cand_cap, dp_nlist **out)
+{
+    if (!out || nframes < 1 || n < 0 || (n > 0 && (!coord || !type))) {
+        set_error("dp_nlist_build_frames: NULL or bad argument");
+        return DP_ERR_ARG;
+    }
+    if ((int64_t)nframes * n >= (int64_t)1 << 26) { set_error("dp_nlist_build_frames: too many atoms"); return DP_ERR_ARG; }
+    std::vector<int32_t> all((size_t)nframes * n);
+    for (int32_t f = 0; f < nframes; ++f)
+        for (int64_t i = 0; i < n; ++i) all[(size_t)f * n + i] = type[i];
+    dp_nlist *nl = nullptr;
+    const int64_t nt = (int64_t)nframes * n;
+    DP_TRY(nlist_create_internal(m, nt, all.data(), box, rcut, skin, cand_cap, &nl, nframes));
+    if (nt > 0) {
+        cudaError_t e = cudaMemcpyAsync(nl->d_coord, coord, sizeof(double) * 3 * nt, cudaMemcpyHostToDevice, m->stream);
+        if (e != cudaSuccess) {
+            dp_nlist_destroy(nl);
+            return cuda_fail(e, "dp_nlist_build_frames (coordinates)");
+        }
+        dp_status s = nlist_rebuild_device(nl, nl->d_coord, m->stream);
+        if (s == DP_OK) {
+            cudaError_t e2 = cudaStreamSynchronize(m->stream);
+            if (e2 != cudaSuccess) s = cuda_fail(e2, "dp_nlist_build_frames");
         }
         if (s != DP_OK) {
             dp_nlist_destroy(nl);

@@ -158,7 +158,10 @@ struct dp_nlist {
     int32_t cap = 0;
     double L[3] = {0, 0, 0};
     int nc[3] = {1, 1, 1};
-    int64_t ncell = 0;
+    int64_t ncell = 0;                // cells of all frames: nframes x ncell_frame
+    int64_t ncell_frame = 0;          // nc[0] nc[1] nc[2]
+    int32_t nframes = 1;              // independent configurations of frame_n atoms each (atoms f*frame_n..)
+    int64_t frame_n = 0;
     int32_t *d_type = nullptr;
     int32_t *d_cand = nullptr;        // [n][cap]
     int32_t *d_cand_cnt = nullptr;    // [n]
@@ -228,13 +231,16 @@ dp_status compute_mix16(dp_model *m, dp_nlist *nl, int bf16, double *d_energy, d
 dp_status fit_f32(dp_model *m, dp_nlist *nl, const float *D, float *dD, double *d_atom_energy, cudaStream_t st);
 dp_status param_grad_device(dp_model *m, dp_nlist *nl, const double *d_v, const double *d_ab, dp_precision prec,
                             double *d_E_atom, double *d_Ed_atom, double *d_grad, cudaStream_t st);
-dp_status loss_terms_device(int64_t n, const double *d_F, const double *d_F_ref, const double *d_E,
-                            const double *d_E_ref, double p_e, double p_f, double *d_v, double *d_ab, double *d_loss,
-                            cudaStream_t st);
+// Per frame f of a list (frames of frame_n atoms): v = F - F_ref, the frame's
+// energy from the per-atom energies d_Ei, d_ab = [beta, alpha_0 .. alpha_{F-1}],
+// d_lf [F] scratch; d_loss += the loss summed over the frames in frame order.
+dp_status loss_terms_device(int64_t n, int64_t frame_n, const double *d_F, const double *d_F_ref,
+                            const double *d_Ei, const double *d_E_ref, double p_e, double p_f, double *d_v,
+                            double *d_ab, double *d_lf, double *d_loss, cudaStream_t st);
 dp_status refresh_params_device(dp_model *m, cudaStream_t st);
 // Per-atom scratch of the model: E_i [n] at d_aux, W_i [9n] right after it.
 dp_status ensure_aux(dp_model *m, int64_t n);
 dp_status nlist_create_internal(const dp_model *m, int64_t n, const int32_t *type, const double box[9], double rcut,
-                                double skin, int32_t cand_cap, dp_nlist **out);
+                                double skin, int32_t cand_cap, dp_nlist **out, int32_t nframes = 1);
 
 }  // namespace dp

@@ -16,6 +16,8 @@ struct __align__(32) Pos4 {
 struct BoxDev {
     double L[3], invL[3];
     int nc[3];
+    int ncell_f;          // cells of one frame
+    int64_t frame_n;      // atoms per frame (frame of atom i = i / frame_n)
 };
 
 inline BoxDev make_box(const dp_nlist *nl)
@@ -26,6 +28,8 @@ inline BoxDev make_box(const dp_nlist *nl)
         b.invL[k] = 1.0 / nl->L[k];
         b.nc[k] = nl->nc[k];
     }
+    b.ncell_f = (int)nl->ncell_frame;
+    b.frame_n = nl->frame_n > 0 ? nl->frame_n : 1;
     return b;
 }
 

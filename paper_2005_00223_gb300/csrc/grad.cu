@@ -37,7 +37,7 @@
 namespace dp {
 namespace {
 
-constexpr int kGA = 4;   // atoms per CTA in the fitting kernels
+// Atoms per CTA of the fitting tangent kernel: 4, or 1 when 4 would leave SMs idle.
 
 __device__ __forceinline__ double g_tanh(double x) { return tanh_f64(x); }
 __device__ __forceinline__ float g_tanh(float x) { return tanhf(x); }
@@ -268,10 +268,10 @@ FitRec make_fit_rec(const ModelDev &md)
     return r;
 }
 
-template <typename Real>
+template <typename Real, int kGA>
 __global__ void __launch_bounds__(256) k_jvp_fit(ModelDev md, FitRec fr, int ti, const int32_t *__restrict__ order,
                                                 int64_t pos_begin, int64_t count, const double *__restrict__ ab,
-                                                const Real *__restrict__ D, const Real *__restrict__ Dd,
+                                                int64_t frame_n, const Real *__restrict__ D, const Real *__restrict__ Dd,
                                                 Real *__restrict__ rec, double *__restrict__ E_atom,
                                                 double *__restrict__ Ed_atom, Real *__restrict__ Db,
                                                 Real *__restrict__ Ddb)
@@ -282,7 +282,8 @@ __global__ void __launch_bounds__(256) k_jvp_fit(ModelDev md, FitRec fr, int ti,
     const int na = (int)min((int64_t)kGA, pos_begin + count - first);
     const Real *net = P_of<Real>(md) + md.fit_base + (int64_t)ti * md.fit.size;
     const Real *netT = PT_of<Real>(md) + md.fit_base + (int64_t)ti * md.fit.size;
-    const Real alpha = (Real)ab[0], beta = (Real)ab[1];
+    // ab = [beta, alpha of frame 0, 1, ...]: the loss weights of Edot and of each frame's E
+    const Real beta = (Real)ab[0];
     // forward, primal + tangent
     for (int k = 0; k < md.n_fit; ++k) {
         const int win = md.fit.win[k], wout = md.fit.wout[k];
@@ -357,6 +358,7 @@ __global__ void __launch_bounds__(256) k_jvp_fit(ModelDev md, FitRec fr, int ti,
         const int a = q / wl, o = q - a * wl;
         if (a < na) {
             Real *R = rec + (first + a) * fr.size;
+            const Real alpha = (Real)ab[1 + order[first + a] / frame_n];
             R[fr.a0 + o] = alpha * Wout[o];
             R[fr.a0d + o] = beta * Wout[o];
         }
@@ -417,9 +419,10 @@ __global__ void __launch_bounds__(256) k_jvp_fit(ModelDev md, FitRec fr, int ti,
 // One thread per parameter of the fitting net of type ti; sums over the
 // atoms of that type and adds into grad (FP64).
 template <typename Real>
-__global__ void k_fit_wgrad(ModelDev md, FitRec fr, int ti, int64_t pos_begin, int64_t count,
-                            const double *__restrict__ ab, const Real *__restrict__ D, const Real *__restrict__ Dd,
-                            const Real *__restrict__ rec, double *__restrict__ grad)
+__global__ void k_fit_wgrad(ModelDev md, FitRec fr, int ti, const int32_t *__restrict__ order, int64_t pos_begin,
+                            int64_t count, const double *__restrict__ ab, int64_t frame_n,
+                            const Real *__restrict__ D, const Real *__restrict__ Dd, const Real *__restrict__ rec,
+                            double *__restrict__ grad)
 {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= md.fit.size) return;
@@ -441,11 +444,11 @@ __global__ void k_fit_wgrad(ModelDev md, FitRec fr, int ti, int64_t pos_begin, i
     if (layer == md.n_fit) {
         // output layer: w_bar = sum alpha y + beta y', b_bar = alpha * count
         if (isb) {
-            acc = ab[0] * (double)count;
+            for (int64_t a = 0; a < count; ++a) acc += ab[1 + order[pos_begin + a] / frame_n];
         } else {
             for (int64_t a = 0; a < count; ++a) {
                 const Real *R = rec + (pos_begin + a) * fr.size;
-                acc += ab[0] * (double)R[fr.yl + in] + ab[1] * (double)R[fr.yld + in];
+                acc += ab[1 + order[pos_begin + a] / frame_n] * (double)R[fr.yl + in] + ab[0] * (double)R[fr.yld + in];
             }
         }
     } else if (isb) {
@@ -659,33 +662,57 @@ __global__ void k_grad_reduce(const Real *__restrict__ gpriv, int nslices, int64
     grad[q] += acc;
 }
 
-// d_ab = (alpha, beta) of the force-matching loss from E and F, plus the
-// loss itself: one block.
-__global__ void k_loss_terms(int64_t n, const double *__restrict__ F, const double *__restrict__ F_ref,
-                             const double *__restrict__ E, const double *__restrict__ E_ref, double p_e, double p_f,
-                             double *__restrict__ v, double *__restrict__ ab, double *__restrict__ loss)
+// Per frame (one block each, fixed-order sums): v = F - F_ref, the frame's
+// energy E_f = sum of its E_i, the loss weight alpha_f = 2 p_e (E_f - E_ref,f) / n_f^2
+// of dE_f/dtheta, and the frame's loss p_e (dE_f / n_f)^2 + p_f / (3 n_f) sum |F - F_ref|^2;
+// beta = -2 p_f / (3 n_f) weighs dEdot/dtheta (Edot along v, since F = -grad E).
+__global__ void __launch_bounds__(256) k_loss_frames(int64_t frame_n, const double *__restrict__ F,
+                                                    const double *__restrict__ F_ref, const double *__restrict__ Ei,
+                                                    const double *__restrict__ E_ref, double p_e, double p_f,
+                                                    double *__restrict__ v, double *__restrict__ ab,
+                                                    double *__restrict__ lf)
+{
+    __shared__ double s[2][256];
+    const int t = threadIdx.x, f = blockIdx.x;
+    const int64_t a0 = (int64_t)f * frame_n;
+    double acc = 0.0, e = 0.0;
+    for (int64_t q = t; q < 3 * frame_n; q += 256) {
+        const double d = F[3 * a0 + q] - F_ref[3 * a0 + q];
+        v[3 * a0 + q] = d;
+        acc += d * d;
+    }
+    for (int64_t i = t; i < frame_n; i += 256) e += Ei[a0 + i];
+    s[0][t] = acc;
+    s[1][t] = e;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (t < h) {
+            s[0][t] += s[0][t + h];
+            s[1][t] += s[1][t + h];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const double nn = (double)frame_n, dE = s[1][0] - E_ref[f];
+        ab[1 + f] = 2.0 * p_e * dE / (nn * nn);
+        lf[f] = p_e * (dE / nn) * (dE / nn) + p_f * s[0][0] / (3.0 * nn);
+        if (f == 0) ab[0] = -2.0 * p_f / (3.0 * nn);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_loss_sum(int nframes, const double *__restrict__ lf, double *__restrict__ loss)
 {
     __shared__ double s[256];
     const int t = threadIdx.x;
     double acc = 0.0;
-    for (int64_t q = t; q < 3 * n; q += blockDim.x) {
-        const double d = F[q] - F_ref[q];
-        v[q] = d;
-        acc += d * d;
-    }
+    for (int f = t; f < nframes; f += 256) acc += lf[f];
     s[t] = acc;
     __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    for (int h = 128; h > 0; h >>= 1) {
         if (t < h) s[t] += s[t + h];
         __syncthreads();
     }
-    if (t == 0) {
-        const double dE = E[0] - E_ref[0];
-        const double nn = (double)n;
-        ab[0] = 2.0 * p_e * dE / (nn * nn);
-        ab[1] = -2.0 * p_f / (3.0 * nn);
-        loss[0] += p_e * (dE / nn) * (dE / nn) + p_f * s[0] / (3.0 * nn);
-    }
+    if (t == 0) loss[0] += s[0];
 }
 
 template <class S, typename Real>
@@ -748,10 +775,15 @@ dp_status run_grad(dp_model *m, dp_nlist *nl, const double *d_v, const double *d
         const int64_t b = nl->type_off[t], cnt = nl->type_count[t];
         if (cnt <= 0) continue;
         ProfScope ps(m->prof, PG_GRAD, 2, st);
-        k_jvp_fit<Real><<<(unsigned)((cnt + kGA - 1) / kGA), 256, 0, st>>>(md, fr, t, nl->d_order, b, cnt, d_ab, D,
-                                                                          Dd, rec, d_E_atom, d_Ed_atom, Db, Ddb);
-        k_fit_wgrad<Real><<<(unsigned)((md.fit.size + 255) / 256), 256, 0, st>>>(md, fr, t, b, cnt, d_ab, D, Dd,
-                                                                                rec, d_grad);
+        const int64_t fn = nl->frame_n > 0 ? nl->frame_n : n;
+        if ((cnt + 3) / 4 < nsm)
+            k_jvp_fit<Real, 1><<<(unsigned)cnt, 256, 0, st>>>(md, fr, t, nl->d_order, b, cnt, d_ab, fn, D, Dd, rec,
+                                                               d_E_atom, d_Ed_atom, Db, Ddb);
+        else
+            k_jvp_fit<Real, 4><<<(unsigned)((cnt + 3) / 4), 256, 0, st>>>(md, fr, t, nl->d_order, b, cnt, d_ab, fn, D,
+                                                                         Dd, rec, d_E_atom, d_Ed_atom, Db, Ddb);
+        k_fit_wgrad<Real><<<(unsigned)((md.fit.size + 255) / 256), 256, 0, st>>>(md, fr, t, nl->d_order, b, cnt,
+                                                                                d_ab, fn, D, Dd, rec, d_grad);
         DP_CUDA(cudaGetLastError());
     }
     {
@@ -782,11 +814,13 @@ dp_status param_grad_device(dp_model *m, dp_nlist *nl, const double *d_v, const 
                : run_grad<GPaper, float>(m, nl, d_v, d_ab, d_E_atom, d_Ed_atom, d_grad, st);
 }
 
-dp_status loss_terms_device(int64_t n, const double *d_F, const double *d_F_ref, const double *d_E,
-                            const double *d_E_ref, double p_e, double p_f, double *d_v, double *d_ab, double *d_loss,
-                            cudaStream_t st)
+dp_status loss_terms_device(int64_t n, int64_t frame_n, const double *d_F, const double *d_F_ref,
+                            const double *d_Ei, const double *d_E_ref, double p_e, double p_f, double *d_v,
+                            double *d_ab, double *d_lf, double *d_loss, cudaStream_t st)
 {
-    k_loss_terms<<<1, 256, 0, st>>>(n, d_F, d_F_ref, d_E, d_E_ref, p_e, p_f, d_v, d_ab, d_loss);
+    const int nframes = (int)(n / frame_n);
+    k_loss_frames<<<nframes, 256, 0, st>>>(frame_n, d_F, d_F_ref, d_Ei, d_E_ref, p_e, p_f, d_v, d_ab, d_lf);
+    k_loss_sum<<<1, 256, 0, st>>>(nframes, d_lf, d_loss);
     DP_CUDA(cudaGetLastError());
     return DP_OK;
 }

@@ -62,7 +62,8 @@ __global__ void k_cell_assign(int64_t n, const Pos4 *__restrict__ pos, BoxDev bx
     int cx = cell_coord(p.x, bx.invL[0], bx.nc[0]);
     int cy = cell_coord(p.y, bx.invL[1], bx.nc[1]);
     int cz = cell_coord(p.z, bx.invL[2], bx.nc[2]);
-    int c = (cx * bx.nc[1] + cy) * bx.nc[2] + cz;
+    // each frame has its own block of cells, so no candidate crosses frames
+    int c = (int)(i / bx.frame_n) * bx.ncell_f + (cx * bx.nc[1] + cy) * bx.nc[2] + cz;
     cell_of[i] = c;
     atomicAdd(&cnt[c], 1);
 }
@@ -118,7 +119,9 @@ __global__ void k_candidates(int64_t n, const Pos4 *__restrict__ pos, BoxDev bx,
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
     const Pos4 pi = pos[i];
-    const int c = cell_of[i];
+    const int cf = cell_of[i];
+    const int fbase = (cf / bx.ncell_f) * bx.ncell_f;      // first cell of this atom's frame
+    const int c = cf - fbase;
     const int c3[3] = {c / (bx.nc[1] * bx.nc[2]), (c / bx.nc[2]) % bx.nc[1], c % bx.nc[2]};
     int lo[3], hi[3];
 #pragma unroll
@@ -134,7 +137,7 @@ __global__ void k_candidates(int64_t n, const Pos4 *__restrict__ pos, BoxDev bx,
                 int x = (c3[0] + a + bx.nc[0]) % bx.nc[0];
                 int y = (c3[1] + b + bx.nc[1]) % bx.nc[1];
                 int z = (c3[2] + e + bx.nc[2]) % bx.nc[2];
-                int cell = (x * bx.nc[1] + y) * bx.nc[2] + z;
+                int cell = fbase + (x * bx.nc[1] + y) * bx.nc[2] + z;
                 int s0 = start[cell], s1 = start[cell + 1];
                 for (int base = s0; base < s1; base += 32) {
                     int p = base + lane;

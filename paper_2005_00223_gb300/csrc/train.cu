@@ -57,15 +57,16 @@ __global__ void k_adam(int64_t np, double *__restrict__ p, const double *__restr
 }
 
 // Scratch of the training calls: coord, F_ref, F, v [3n] each; E_i, Edot_i,
-// W_i (9n); scalars.
+// W_i (9n); scalars; the loss weights [beta, alpha per frame] and the
+// per-frame losses (at most n frames).
 struct TScr {
-    double *coord, *Fref, *F, *v, *Ei, *Edi, *Wi, *scal, *grad;
+    double *coord, *Fref, *F, *v, *Ei, *Edi, *Wi, *scal, *ab, *lf, *grad;
 };
 
 dp_status ensure_tscr(dp_model *m, int64_t n, TScr *t)
 {
     int64_t nn = n > 0 ? n : 1;
-    size_t need = (size_t)nn * (3 * 4 + 2 + 9) + 32 + (size_t)m->nparams;
+    size_t need = (size_t)nn * (3 * 4 + 2 + 9 + 2) + 32 + 1 + (size_t)m->nparams;
     if (nn > m->tscr_n) {
         if (m->d_tscr) {
             DP_CUDA(cudaStreamSynchronize(m->stream));
@@ -85,6 +86,8 @@ dp_status ensure_tscr(dp_model *m, int64_t n, TScr *t)
     t->Edi = b; b += nn;
     t->Wi = b; b += 9 * nn;
     t->scal = b; b += 32;
+    t->ab = b; b += nn + 1;
+    t->lf = b; b += nn;
     t->grad = b;
     return DP_OK;
 }
@@ -142,12 +145,14 @@ dp_status dp_param_grad(dp_model *m, dp_nlist *nl, const double *coord, const do
         DP_CUDA(cudaMemcpyAsync(t.coord, coord, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
         DP_CUDA(cudaMemcpyAsync(t.v, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
     }
-    double ab[2] = {alpha, beta};
-    DP_CUDA(cudaMemcpyAsync(t.scal + 8, ab, sizeof(ab), cudaMemcpyHostToDevice, st));
+    // weights [beta, alpha of every frame]
+    std::vector<double> ab(1 + (size_t)nl->nframes, alpha);
+    ab[0] = beta;
+    DP_CUDA(cudaMemcpyAsync(t.ab, ab.data(), sizeof(double) * ab.size(), cudaMemcpyHostToDevice, st));
     DP_CUDA(cudaMemsetAsync(t.grad, 0, sizeof(double) * m->nparams, st));
     DP_TRY(nlist_format_device(m, nl, t.coord, st));
     if (n > 0) {
-        DP_TRY(param_grad_device(m, nl, t.v, t.scal + 8, prec, t.Ei, t.Edi, t.grad, st));
+        DP_TRY(param_grad_device(m, nl, t.v, t.ab, prec, t.Ei, t.Edi, t.grad, st));
         DP_TRY(reduce_energy_virial(t.Ei, nullptr, n, t.scal, nullptr, m->d_red, st));
         DP_TRY(reduce_energy_virial(t.Edi, nullptr, n, t.scal + 1, nullptr, m->d_red, st));
     } else {
@@ -173,8 +178,8 @@ static dp_status loss_grad_enqueue(dp_model *m, dp_nlist *nl, const double *d_co
     DP_TRY(ensure_tscr(m, n, &t));
     if (n == 0) return DP_OK;
     DP_TRY(compute_device(m, nl, d_coord, prec, t.scal, t.Ei, t.F, t.scal + 1, t.Wi, st));
-    DP_TRY(loss_terms_device(n, t.F, d_F_ref, t.scal, d_E_ref, p_e, p_f, t.v, t.scal + 12, d_loss, st));
-    return param_grad_device(m, nl, t.v, t.scal + 12, prec, t.Ei, t.Edi, d_grad, st);
+    DP_TRY(loss_terms_device(n, nl->frame_n, t.F, d_F_ref, t.Ei, d_E_ref, p_e, p_f, t.v, t.ab, t.lf, d_loss, st));
+    return param_grad_device(m, nl, t.v, t.ab, prec, t.Ei, t.Edi, d_grad, st);
 }
 
 dp_status dp_force_loss_grad(dp_model *m, dp_nlist *nl, const double *coord, const double box[9],
@@ -184,6 +189,7 @@ dp_status dp_force_loss_grad(dp_model *m, dp_nlist *nl, const double *coord, con
     DP_TRY(check_args(m, nl, box));
     const int64_t n = nl->n;
     if ((n > 0 && (!coord || !F_ref)) || !grad || !loss) { set_error("dp_force_loss_grad: NULL argument"); return DP_ERR_ARG; }
+    if (nl->nframes != 1) { set_error("dp_force_loss_grad takes one configuration; use dp_force_loss_grad_dev for frames"); return DP_ERR_ARG; }
     cudaStream_t st = m->stream;
     TScr t;
     DP_TRY(ensure_tscr(m, n, &t));

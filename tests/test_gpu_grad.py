@@ -179,3 +179,53 @@ def test_water_1p57m_bf16_autograd_sampled(dp, orc):
         assert abs(Ei[i] - Ek) < 4 * u * scale
         assert abs(Ek - Eib[i % 192]) < 1e-9 * abs(Ek)
     assert abs(float(E.detach()) - 8192 * Eb) < 2 * u * 8192 * float(np.abs(Eib).sum())
+
+
+def test_frames_list_and_batched_loss_gradient(dp, orc):
+    """32 water frames in one list: the list is the per-frame lists with offset indices (bit-exact), and one
+    batched loss / gradient call equals the sum of the per-frame calls (FP64) and the oracle's."""
+    import torch
+    cfg = dpsynth.water_config()
+    p = dpsynth.model_params(cfg, 7)
+    rng = np.random.default_rng(5)
+    m = dp.Model(cfg, 0, params=p)
+    frames = []
+    for s in range(32):
+        c, t, b = dpsynth.water_box(100 + s)
+        frames.append((c, t, b, float(rng.normal()), rng.normal(scale=1e-3, size=c.shape)))
+    typ, box, n = frames[0][1], frames[0][2], len(frames[0][1])
+    X = np.array([f[0] for f in frames])
+    nlf = dp.NeighborList.frames(m, X, typ, box)
+    big, ntr = nlf.get()
+    assert ntr == 0
+    nsel = sum(cfg.sel)
+    for f in range(32):
+        nl1 = dp.NeighborList(m, X[f], typ, box)
+        one, _ = nl1.get()
+        nl1.close()
+        exp = np.where(one >= 0, one + f * n, -1)
+        np.testing.assert_array_equal(big[f * n:(f + 1) * n].reshape(n, nsel), exp.reshape(n, nsel))
+    # batched loss and gradient vs the per-frame host calls
+    dev = torch.device("cuda")
+    Xd = torch.tensor(X.reshape(-1, 3), device=dev)
+    Fd = torch.tensor(np.array([f[4] for f in frames]).reshape(-1, 3), device=dev)
+    Ed = torch.tensor([f[3] for f in frames], dtype=torch.float64, device=dev)
+    grad = torch.zeros(len(p), dtype=torch.float64, device=dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    dp.dp_model_set_stream(m.h, stream)
+    dp.dp_force_loss_grad_dev(m.h, nlf.h, Xd, box, Fd, Ed, 1.0, 100.0, "fp64", loss, grad, stream)
+    torch.cuda.synchronize()
+    dp.dp_model_set_stream(m.h, None)
+    gsum, lsum = np.zeros(len(p)), 0.0
+    for f in frames:
+        nl1 = dp.NeighborList(m, f[0], typ, box)
+        l1, _ = dp.dp_force_loss_grad(m.h, nl1.h, f[0], box, f[4], f[3], 1.0, 100.0, "fp64", grad=gsum)
+        lsum += l1
+        nl1.close()
+    nlf.close()
+    assert float(loss.item()) == pytest.approx(lsum, rel=1e-12)
+    assert _rel(grad.cpu().numpy(), gsum) < 1e-12
+    Lr, gr = orc.Model(cfg, p).force_loss_grad(frames, p_e=1.0, p_f=100.0)
+    assert float(loss.item()) == pytest.approx(Lr, rel=1e-10)
+    assert _rel(grad.cpu().numpy(), gr) < 1e-9
