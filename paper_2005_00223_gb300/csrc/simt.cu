@@ -335,18 +335,19 @@ __global__ void __launch_bounds__(256) k_fit(ModelDev md, int ti, const int32_t 
 // returns dx of the layer inputs in the same ownership pattern.
 template <int G, int WIN, int WOUT, typename Real>
 __device__ __forceinline__ void emb_layer_bwd(const Real *__restrict__ sWl, const Real *__restrict__ act_t,
-                                              Real *__restrict__ sdz, Real *__restrict__ sdy,
-                                              const Real (&dy)[(WOUT + G - 1) / G], Real (&dx)[(WIN + G - 1) / G],
-                                              int g, int n)
+                                              Real *__restrict__ sdz, const Real (&dy)[(WOUT + G - 1) / G],
+                                              Real (&dx)[(WIN + G - 1) / G], int g, int n)
 {
     constexpr int NO = (WOUT + G - 1) / G, NI = (WIN + G - 1) / G;
+    // the skip sources of input kk (outputs kk and kk + WIN) belong to this
+    // thread too, since channel o is owned by warp o % G and G divides WIN
+    static_assert(WIN % G == 0 || (WOUT != WIN && WOUT != 2 * WIN), "skip sources on another warp");
 #pragma unroll
     for (int u = 0; u < NO; ++u) {
         const int o = g + G * u;
         if (WOUT % G == 0 || o < WOUT) {
             const Real t = act_t[o * 32 + n];
             sdz[o * 32 + n] = dy[u] * (Real(1) - t * t);
-            sdy[o * 32 + n] = dy[u];
         }
     }
     __syncthreads();
@@ -362,11 +363,8 @@ __device__ __forceinline__ void emb_layer_bwd(const Real *__restrict__ sWl, cons
     }
 #pragma unroll
     for (int u = 0; u < NI; ++u) {
-        const int kk = g + G * u;
-        if (WIN % G == 0 || kk < WIN) {
-            if (WOUT == WIN) dx[u] += sdy[kk * 32 + n];
-            else if (WOUT == 2 * WIN) dx[u] += sdy[kk * 32 + n] + sdy[(kk + WIN) * 32 + n];
-        }
+        if (WOUT == WIN) dx[u] += dy[u];
+        else if (WOUT == 2 * WIN) dx[u] += dy[u] + dy[u + WIN / G];
     }
     __syncthreads();
 }
@@ -387,13 +385,13 @@ __global__ void __launch_bounds__(S::NT) k_embed_bwd(ModelDev md, BoxDev bx, con
     double *sJ = reinterpret_cast<double *>(smem_raw);   // [32][12]
     double *sd = sJ + 32 * 12;                           // [32][3]
     Real *sW = reinterpret_cast<Real *>(sd + 32 * 3);
-    Real *sdz = sW + md.emb.size;          // [WMAX][32]
-    Real *sdy = sdz + S::WMAX * 32;        // [WMAX][32]
-    Real *sR = sdy + S::WMAX * 32;         // [32][4]
+    Real *sdz = sW + md.emb.size;          // [WMAX][32] pre-activation adjoints of one layer
+    Real *sdy = sdz + S::WMAX * 32;        // [2][32] layer-1 skip adjoints (first layer of width 1 or 2)
+    Real *sR = sdy + 2 * 32;               // [32][4]
     Real *sdR = sR + 32 * 4;               // [G][32][4]
     Real *sT = sdR + G * 32 * 4;           // [M1][4]
     Real *sdT = sT + nq;                   // [M1][4]
-    Real *sdD = sdT + nq;                  // [M1*M2]
+    const Real *gdD = dD_in + (int64_t)blockIdx.x * nd;   // dE/dD of this atom (read through L1)
     const int64_t p = p0 + blockIdx.x;
     const int i = order[p];
     const Pos4 pi = pos[i];
@@ -401,15 +399,14 @@ __global__ void __launch_bounds__(S::NT) k_embed_bwd(ModelDev md, BoxDev bx, con
     const Real *P = params_of<Real>(md);
 
     for (int q = tid; q < nq; q += NT) sT[q] = T_in[(int64_t)blockIdx.x * nq + q];
-    for (int q = tid; q < nd; q += NT) sdD[q] = dD_in[(int64_t)blockIdx.x * nd + q];
     __syncthreads();
     // dE/dT[m][c] = sum_b dD[m][b] T[b][c] + [m < M2] sum_a dD[a][m] T[a][c], times 1/sum(sel)
     for (int q = tid; q < nq; q += NT) {
         const int m = q >> 2, c = q & 3;
         Real acc = Real(0);
-        for (int b = 0; b < md.m2; ++b) acc += sdD[m * md.m2 + b] * sT[b * 4 + c];
+        for (int b = 0; b < md.m2; ++b) acc += __ldg(gdD + m * md.m2 + b) * sT[b * 4 + c];
         if (m < md.m2)
-            for (int a = 0; a < S::E2; ++a) acc += sdD[a * md.m2 + m] * sT[a * 4 + c];
+            for (int a = 0; a < S::E2; ++a) acc += __ldg(gdD + a * md.m2 + m) * sT[a * 4 + c];
         sdT[q] = acc * (Real)md.inv_nsel;
     }
     constexpr int act_chunk = S::ACT * 32;
@@ -469,9 +466,8 @@ __global__ void __launch_bounds__(S::NT) k_embed_bwd(ModelDev md, BoxDev bx, con
 #pragma unroll
             for (int c = 0; c < 4; ++c) sdR[(g * 32 + n) * 4 + c] = dRp[c];
             Real dy1[N1], dy0[N0];
-            emb_layer_bwd<G, S::E1, S::E2, Real>(sW + md.emb.W[2], ca + (S::E0 + S::E1) * 32, sdz, sdy, dy2, dy1, g,
-                                                 n);
-            emb_layer_bwd<G, S::E0, S::E1, Real>(sW + md.emb.W[1], ca + S::E0 * 32, sdz, sdy, dy1, dy0, g, n);
+            emb_layer_bwd<G, S::E1, S::E2, Real>(sW + md.emb.W[2], ca + (S::E0 + S::E1) * 32, sdz, dy2, dy1, g, n);
+            emb_layer_bwd<G, S::E0, S::E1, Real>(sW + md.emb.W[1], ca + S::E0 * 32, sdz, dy1, dy0, g, n);
             // layer 0 (input width 1): ds = sum_o dz_o W0[o] (+ skip when E0 is 1 or 2)
 #pragma unroll
             for (int u = 0; u < N0; ++u) {
@@ -479,7 +475,7 @@ __global__ void __launch_bounds__(S::NT) k_embed_bwd(ModelDev md, BoxDev bx, con
                 if (S::E0 % G == 0 || o < S::E0) {
                     const Real t = ca[o * 32 + n];
                     sdz[o * 32 + n] = dy0[u] * (Real(1) - t * t);
-                    sdy[o * 32 + n] = dy0[u];
+                    if (S::E0 <= 2) sdy[o * 32 + n] = dy0[u];
                 }
             }
             __syncthreads();
@@ -547,8 +543,7 @@ template <class S, typename Real>
 size_t embed_bwd_smem(const ModelDev &md)
 {
     return sizeof(double) * 32 * (12 + 3) +
-           sizeof(Real) * ((size_t)md.emb.size + 2 * S::WMAX * 32 + 32 * 4 + S::G * 32 * 4 + 8 * S::E2 +
-                           (size_t)S::E2 * md.m2);
+           sizeof(Real) * ((size_t)md.emb.size + S::WMAX * 32 + 2 * 32 + 32 * 4 + S::G * 32 * 4 + 8 * S::E2);
 }
 
 template <typename Real>
