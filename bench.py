@@ -232,7 +232,7 @@ def run_mine(args, rank, world):
 
 
 def grad_frames():
-    """Config 3's training batch: 32 seeded 192-atom water frames with seeded reference labels."""
+    """The training batch: 32 seeded 192-atom water frames with seeded reference labels."""
     cfg = dpsynth.water_config()
     params = dpsynth.model_params(cfg, 7)
     rng = np.random.default_rng(5)
@@ -255,7 +255,7 @@ def grad_flops(cfg, nnei_total: int, n: int):
 
 
 def run_grad(args, rank, world):
-    """Parameter gradient of the force-matching loss over the 32 water frames (rows a11 / config 3)."""
+    """Parameter gradient of the force-matching loss over 32 water frames of 192 atoms, one batched call."""
     import torch
 
     import paper_2005_00223_gb300 as dp
@@ -368,7 +368,7 @@ def run_grad(args, rank, world):
 
 
 def run_judged(args, rank, world):
-    """Distilled student MD judged by the full model every 10 steps (rows a12 / config 4).
+    """Distilled student MD judged by the full model every 10 steps.
 
     Untimed: teacher frames from its own NVE at 300 K and 1,200 K on 4,000
     atoms and 800 Adam steps of the student on them (the recipe of the

@@ -31,3 +31,13 @@ def assert_close_fp64(gpu, ref, rtol=1e-10):
     err = np.sqrt(((F - Fr) ** 2).sum(1)).max()
     assert err <= rtol * fs, err / fs
     assert np.abs(W - Wr).max() <= rtol * np.abs(Wr).max(), np.abs(W - Wr).max() / np.abs(Wr).max()
+
+
+def sampled_oracle_force(om, coord, typ, box, nl_ref, k):
+    """E_k and F_k = sum_s g_k,s - sum over atoms i with k in their list of g_i,slot(k), from the oracle."""
+    Ek, gk, _ = om.atom(k, nl_ref[k], coord, typ, box)
+    F = gk[nl_ref[k] >= 0].sum(0)
+    for i in np.unique(np.where(nl_ref == k)[0]):
+        _, gi, _ = om.atom(i, nl_ref[i], coord, typ, box)
+        F -= gi[nl_ref[i] == k].sum(0)
+    return Ek, F

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import dpsynth
-from gpu_common import assert_close_fp64, rms, systems
+from gpu_common import assert_close_fp64, rms, sampled_oracle_force, systems
 
 pytestmark = pytest.mark.gpu
 
@@ -157,16 +157,6 @@ def test_bad_arguments_are_rejected(dp):
         dp.dp_model_set_params(m.h, np.zeros(5))
 
 
-def _sampled_oracle_force(om, coord, typ, box, nl_ref, k):
-    """F_k = sum_s g_k,s - sum over atoms i with k in their list of g_i,slot(k)."""
-    Ek, gk, _ = om.atom(k, nl_ref[k], coord, typ, box)
-    F = gk[nl_ref[k] >= 0].sum(0)
-    for i in np.unique(np.where(nl_ref == k)[0]):
-        _, gi, _ = om.atom(i, nl_ref[i], coord, typ, box)
-        F -= gi[nl_ref[i] == k].sum(0)
-    return Ek, F
-
-
 def test_fp64_copper_4000_full_oracle(dp, orc):
     """The 4,000-atom copper workload: whole-system parity against the oracle."""
     cfg = dpsynth.copper_config()
@@ -194,7 +184,7 @@ def test_fp64_copper_108k_sampled(dp, orc):
     np.testing.assert_array_equal(nl.get()[0], nref)
     fs = rms(F)
     for k in (0, 4321, 107999):
-        Ek, Fk = _sampled_oracle_force(om, coord, typ, box, nref, k)
+        Ek, Fk = sampled_oracle_force(om, coord, typ, box, nref, k)
         assert abs(Ei[k] - Ek) <= 1e-10 * abs(Ek)
         assert np.linalg.norm(F[k] - Fk) <= 1e-10 * fs
     assert abs(E - Ei.sum()) <= 1e-12 * abs(E)

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import dpsynth
-from gpu_common import rms, systems
+from gpu_common import rms, sampled_oracle_force, systems
 
 pytestmark = pytest.mark.gpu
 
@@ -91,3 +91,57 @@ def test_mix16_student_shape_and_md(dp, prec):
     st = dp.MDState(m, coord, vel, typ, mass, box, skin=2.0)
     th = st.step(10, 1.0, prec, thermo_every=5)
     assert np.isfinite(th).all()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp64"])
+def test_far_unwrapped_coordinates(dp, prec):
+    """Atoms shifted by random whole box vectors (up to 40 boxes away) give the same neighbor list and,
+    up to the rounding of the larger coordinates, the same energy and forces: the minimum image works
+    on raw coordinates, and the FP32 prefilter of the formatting uses coordinates wrapped in FP64."""
+    cfg = dpsynth.water_config()
+    coord, typ, box = dpsynth.water_box(3)
+    L = np.diag(box)
+    rng = np.random.default_rng(11)
+    shifted = coord + rng.integers(-40, 41, size=coord.shape) * L
+    m = dp.Model(cfg, 1)
+    nl0 = dp.NeighborList(m, coord, typ, box)
+    nl1 = dp.NeighborList(m, shifted, typ, box)
+    E0, _, F0, W0 = nl0.compute(coord, box, prec)
+    E1, _, F1, W1 = nl1.compute(shifted, box, prec)
+    a, _ = nl0.get()
+    b, _ = nl1.get()
+    # the same neighbor set per atom (a key can move by one unit in its last place with the shifted rounding)
+    nsel = sum(cfg.sel)
+    for i in range(len(typ)):
+        assert set(a.reshape(-1, nsel)[i]) == set(b.reshape(-1, nsel)[i])
+    tol = 1e-9 if prec == "fp64" else 1e-5
+    assert abs(E1 - E0) <= tol * np.abs(E0)
+    assert rms(F1 - F0) <= tol * rms(F0)
+    assert np.abs(W1 - W0).max() <= tol * np.abs(W0).max()
+    nl0.close()
+    nl1.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec,u", [("bf16", 2.0 ** -9), ("fp16", 2.0 ** -11)])
+def test_mix16_copper_108k_sampled(dp, orc, prec, u):
+    """The 108,000-atom copper workload on the tensor-core path: the neighbor list equals the oracle's, and
+    sampled E_i and F_k are within the 16-bit error budget of the FP64 oracle (4u of E_k; 30u of the RMS
+    force per atom, three times the 10u RMSE budget)."""
+    cfg = dpsynth.copper_config()
+    coord, typ, box = dpsynth.copper_fcc(1, ncell=30)
+    m = dp.Model(cfg, 1)
+    nl = dp.NeighborList(m, coord, typ, box, skin=2.0)
+    E, Ei, F, W = nl.compute(coord, box, prec)
+    om = orc.Model(cfg, m.params)
+    nref, _, _ = om.nlist(coord, typ, box)
+    np.testing.assert_array_equal(nl.get()[0], nref)
+    fs = rms(F)
+    samples = [sampled_oracle_force(om, coord, typ, box, nref, k) for k in (0, 4321, 107999)]
+    escale = max(abs(s[0]) for s in samples)
+    for k, (Ek, Fk) in zip((0, 4321, 107999), samples):
+        assert abs(Ei[k] - Ek) <= 4 * u * escale
+        assert np.linalg.norm(F[k] - Fk) <= 30 * u * fs
+    assert abs(E - Ei.sum()) <= 1e-12 * np.abs(Ei).sum()
+    np.testing.assert_allclose(F.sum(0), 0.0, atol=1e-6 * fs * np.sqrt(len(F)))
+    nl.close()
