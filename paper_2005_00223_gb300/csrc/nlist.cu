@@ -164,21 +164,46 @@ __global__ void k_candidates(int64_t n, const Pos4 *__restrict__ pos, BoxDev bx,
     if (i == 0 && lane == 0) atomicAdd(&flags[2], 1);
 }
 
+// Geometry record of a kept neighbor for the tensor-core path, from the
+// exact FP64 difference d and distance r: the switching function s(r) and
+// ds/dr in FP64, stored as FP32 (s, d/r) and (ds/dr, r).
+__device__ __forceinline__ void env_record(const double d[3], double r, const ModelDev &md, float4 &ra, float2 &rb)
+{
+    const double ir = 1.0 / r;
+    double s, ds;
+    if (r < md.rcs) {
+        s = ir;
+        ds = -ir * ir;
+    } else {
+        const double u = (r - md.rcs) * md.inv_sw;
+        const double u2 = u * u, um = u - 1.0;
+        const double poly = fma(u2 * u, fma(fma(-6.0, u, 15.0), u, -10.0), 1.0);
+        const double dpoly = -30.0 * md.inv_sw * u2 * (um * um);
+        s = poly * ir;
+        ds = (dpoly - s) * ir;
+    }
+    const float irf = (float)ir;
+    ra = make_float4((float)s, (float)d[0] * irf, (float)d[1] * irf, (float)d[2] * irf);
+    rb = make_float2((float)ds, (float)r);
+}
+
+constexpr int kRecStage = 256;   // kept neighbors per atom whose records are staged in shared memory
+
 // One warp per atom, three stages.  (A) FP32 prefilter on wrapped FP32
 // coordinates: candidates within r_c plus a margin far above its error are
 // compacted into a list of (type << 26 | j).  (B) The exact FP64
 // minimum-image distance on the compacted list (dense warps); keys of the
 // atoms within r_c are staged in shared memory.  (C) Slot of a key = number
 // of smaller keys minus the keys of lower types.  With env != NULL stage B
-// also computes the geometry of each kept neighbor for the tensor-core path
-// from the exact FP64 difference and distance, staged beside the keys: the
-// switching function s(r) and ds/dr in FP64, stored as FP32 in two planes,
-// (s, u_x, u_y, u_z) with u = d/r at env[slot] and (ds/dr, r) at
-// env + 4 n nsel.  Shared memory per warp (cap2 = cap rounded up to even):
-// keys [cap2] u64, then either the list [cap2] u32 (no env) or the records
-// recA [cap2] float4 and recB [cap2] float2 with the list in the tail of
-// recA: stage B reads entry p of its iteration before writing record q <= p,
-// and record q ends below every later entry p' (16 (q + 1) <= 4 (4 cap2 - nc + p')).
+// also computes the geometry record of each kept neighbor for the
+// tensor-core path (env_record; planes (s, d/r) at env[slot] and
+// (ds/dr, r) at env + 4 n nsel); the first kRecStage are staged beside the
+// keys, any later one is computed again in stage C by the same function.
+// Shared memory per warp (cap2 = cap rounded up to even): keys [cap2] u64
+// with the list [nc] u32 in its tail (stage B reads entry p of its
+// iteration before writing key q <= p, and key q ends below every later
+// entry p': 8 (q + 1) <= 4 (2 cap2 - nc + p')), then the records recA
+// [kRecStage] float4 and recB [kRecStage] float2.
 __global__ void k_format(int64_t n, const Pos4 *__restrict__ pos, const float4 *__restrict__ posf, BoxDev bx,
                          ModelDev md, const int32_t *__restrict__ cand, const int32_t *__restrict__ cand_cnt,
                          int32_t cap, int32_t *__restrict__ nlist, int32_t *__restrict__ nnei,
@@ -190,16 +215,15 @@ __global__ void k_format(int64_t n, const Pos4 *__restrict__ pos, const float4 *
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
     const int cap2 = (cap + 1) & ~1;
-    const int per_warp = env ? 4 * cap2 : cap2 + cap2 / 2;   // 8-byte words
+    const int per_warp = cap2 + (env ? 3 * kRecStage : 0);   // 8-byte words
     unsigned long long *keys = keys_all + (int64_t)warp * per_warp;
     float4 *recA = reinterpret_cast<float4 *>(keys + cap2);
-    float2 *recB = reinterpret_cast<float2 *>(keys + 3 * cap2);
+    float2 *recB = reinterpret_cast<float2 *>(keys + cap2 + 2 * kRecStage);
     const Pos4 pi = pos[i];
     const float4 pf = posf[i];
     const int32_t nc = cand_cnt[i];
     const int32_t *row = cand + i * (int64_t)cap;
-    uint32_t *list =
-        env ? reinterpret_cast<uint32_t *>(recA) + 4 * cap2 - nc : reinterpret_cast<uint32_t *>(keys + cap2);
+    uint32_t *list = reinterpret_cast<uint32_t *>(keys) + 2 * cap2 - nc;
     const unsigned lt = (1u << lane) - 1u;
     // (A) prefilter
     int nf = 0;
@@ -246,24 +270,7 @@ __global__ void k_format(int64_t n, const Pos4 *__restrict__ pos, const float4 *
             // r >= 0: the conversion's truncation is the floor
             const unsigned long long qr = (unsigned long long)__dmul_rn(r, 1e8);
             keys[q] = ((unsigned long long)(e >> 26) << 56) | (qr << 26) | (unsigned long long)j;
-            if (env) {
-                const double ir = 1.0 / r;
-                double s, ds;
-                if (r < md.rcs) {
-                    s = ir;
-                    ds = -ir * ir;
-                } else {
-                    const double u = (r - md.rcs) * md.inv_sw;
-                    const double u2 = u * u, um = u - 1.0;
-                    const double poly = fma(u2 * u, fma(fma(-6.0, u, 15.0), u, -10.0), 1.0);
-                    const double dpoly = -30.0 * md.inv_sw * u2 * (um * um);
-                    s = poly * ir;
-                    ds = (dpoly - s) * ir;
-                }
-                const float irf = (float)ir;
-                recA[q] = make_float4((float)s, (float)d[0] * irf, (float)d[1] * irf, (float)d[2] * irf);
-                recB[q] = make_float2((float)ds, (float)r);
-            }
+            if (env && q < kRecStage) env_record(d, r, md, recA[q], recB[q]);
         }
         nk += __popc(m);
     }
@@ -297,8 +304,18 @@ __global__ void k_format(int64_t n, const Pos4 *__restrict__ pos, const float4 *
             out[slot] = (int32_t)(k & ((1ull << 26) - 1));
             if (env) {
                 const int64_t q = (int64_t)i * md.nsel + slot;
-                reinterpret_cast<float4 *>(env)[q] = recA[p];
-                reinterpret_cast<float2 *>(env + 4 * plane)[q] = recB[p];
+                float4 ra;
+                float2 rb;
+                if (p < kRecStage) {
+                    ra = recA[p];
+                    rb = recB[p];
+                } else {
+                    double d[3];
+                    const int32_t j = (int32_t)(k & ((1ull << 26) - 1));
+                    env_record(d, min_image_r(pi, pos[j], bx, d), md, ra, rb);
+                }
+                reinterpret_cast<float4 *>(env)[q] = ra;
+                reinterpret_cast<float2 *>(env + 4 * plane)[q] = rb;
             }
         }
     }
@@ -361,7 +378,7 @@ dp_status nlist_format_device(const dp_model *m, dp_nlist *nl, const double *d_c
     BoxDev bx = make_box(nl);
     DP_CUDA(cudaMemsetAsync(nl->d_ntrunc, 0, sizeof(unsigned long long), st));
     const size_t cap2 = (size_t)((nl->cap + 1) & ~1);
-    const size_t per_warp = (with_env ? 4 * cap2 : cap2 + cap2 / 2) * sizeof(unsigned long long);
+    const size_t per_warp = (cap2 + (with_env ? 3 * kRecStage : 0)) * sizeof(unsigned long long);
     const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(200 * 1024) / per_warp));
     size_t smem = (size_t)warps * per_warp;
     if (smem > 48 * 1024)
