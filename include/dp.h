@@ -333,6 +333,19 @@ void dp_md_state_destroy(dp_md_state *s);
  * DP_ERR_CUDA. */
 dp_status dp_tanh_f64_dev(int64_t n, const double *d_x, double *d_y, void *stream);
 
+/* The FP64 product the double-precision fitting net runs on the tensor
+ * cores: C = A B^T with A [M][K], Bt = B^T stored as [N][K], C [M][N],
+ * row-major FP64 in device memory, by error-free splitting into fp16
+ * digits (the scheme of Ozaki, Ogita, Oishi and Rump): per entry an error
+ * of the order of K 2^-54 max|A_row| max|B_row|, the size of FP64
+ * rounding.  Shapes: K % 16 == 0 and K <= 1808; N % 64 == 0 when
+ * K <= 256 (8 digits of 7 bits), else N % 48 == 0 (9 digits of 6 bits).
+ * Allocates its digit buffers, runs on `stream` and synchronises it.
+ * Exposed so that its accuracy can be tested.  Errors: DP_ERR_ARG (shape), DP_ERR_OOM,
+ * DP_ERR_CUDA, DP_ERR_TIMEOUT. */
+dp_status dp_ozaki_dgemm_dev(dp_model *m, int64_t M, int32_t N, int32_t K, const double *d_A, const double *d_Bt,
+                             double *d_C, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

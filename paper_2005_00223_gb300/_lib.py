@@ -31,7 +31,7 @@ EXPORTS = [
     "dp_nlist_destroy", "dp_nlist_update_dev", "dp_compute", "dp_compute_dev", "dp_md_state_create",
     "dp_md_step", "dp_md_state_get", "dp_md_state_destroy", "dp_param_grad", "dp_force_loss_grad",
     "dp_force_loss_grad_dev", "dp_adam_step", "dp_model_sync_params", "dp_md_step_judged",
-    "dp_nlist_format_noalloc", "dp_tanh_f64_dev", "dp_nlist_build_frames",
+    "dp_nlist_format_noalloc", "dp_tanh_f64_dev", "dp_nlist_build_frames", "dp_ozaki_dgemm_dev",
 ]
 
 
@@ -81,6 +81,7 @@ def load(path: str = LIB_PATH):
             "dp_nlist_format_noalloc": ([I64, P, P, P, D, I32, P, P, P, P, P], C.c_int),
             "dp_tanh_f64_dev": ([I64, P, P, P], C.c_int),
             "dp_nlist_build_frames": ([P, I32, I64, P, P, P, D, D, I32, P], C.c_int),
+            "dp_ozaki_dgemm_dev": ([P, I64, I32, I32, P, P, P, P], C.c_int),
             "dp_param_grad": ([P, P, P, P, P, D, D, C.c_int, P, P, P], C.c_int),
             "dp_force_loss_grad": ([P, P, P, P, P, D, D, D, C.c_int, P, P], C.c_int),
             "dp_force_loss_grad_dev": ([P, P, P, P, P, P, D, D, C.c_int, P, P, P], C.c_int),
@@ -254,6 +255,14 @@ def dp_nlist_format_noalloc(d_coord, d_type, box, rcut: float, sel, d_nlist, d_n
 def dp_tanh_f64_dev(d_x, d_y, stream=None):
     """y = tanh(x) by the FP64 kernels' own routine (device tensors of equal size)."""
     _check(load().dp_tanh_f64_dev(int(d_x.numel()), _ptr(d_x), _ptr(d_y), _stream(stream)), "dp_tanh_f64_dev")
+
+
+def dp_ozaki_dgemm_dev(m, d_A, d_Bt, d_C, stream=None):
+    """C = A Bt^T in FP64 on the tensor cores (device tensors A [M][K], Bt [N][K], C [M][N])."""
+    M, K = d_A.shape
+    N = d_Bt.shape[0]
+    _check(load().dp_ozaki_dgemm_dev(m, int(M), int(N), int(K), _ptr(d_A), _ptr(d_Bt), _ptr(d_C), _stream(stream)),
+           "dp_ozaki_dgemm_dev")
 
 
 def dp_nlist_destroy(nl):

@@ -2,6 +2,7 @@
 // kernel launchers.  Not part of the public C-ABI (include/dp.h).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -144,6 +145,9 @@ struct dp_model {
     int32_t *d_err = nullptr;         // [4] device error word (bounded waits that gave up)
     unsigned char *d_tcw = nullptr;   // packed fp16 and bf16 embedding weights for the tensor cores
     unsigned char *d_tcfit = nullptr; // packed fp16 and bf16 fitting weights for the tensor cores
+    void *d_ozw = nullptr;            // fp16 digits of the first fitting layer's weights (FP64 products on the tensor cores)
+    int *d_oze = nullptr;             // their row scales
+    bool oz_stale = true;             // digits older than the parameters
     uint32_t tc_img_bytes = 0;
     double *d_train = nullptr;        // Adam moments m, v [n_params] each
     double *d_tscr = nullptr;         // scratch of the training calls
@@ -238,6 +242,14 @@ dp_status loss_terms_device(int64_t n, int64_t frame_n, const double *d_F, const
                             const double *d_Ei, const double *d_E_ref, double p_e, double p_f, double *d_v,
                             double *d_ab, double *d_lf, double *d_loss, cudaStream_t st);
 dp_status refresh_params_device(dp_model *m, cudaStream_t st);
+// FP64 products on the tensor cores (ozaki.cu): digits of the rows of an
+// FP64 matrix, and C = A B^T (+ bias) from the digits of A and of B.
+template <int S, int BETA>
+dp_status oz_split(const double *X, int64_t ldx, int64_t rows, int64_t rows_pad, int K, int TR, int KC, __half *dig,
+                   int *ex, cudaStream_t st);
+template <int S, int BETA, int NC, int KC>
+dp_status oz_gemm(const dp_model *m, int64_t M, int N, int K, const __half *dA, const int *eA, int64_t M_pad,
+                  const __half *dB, const int *eB, const double *bias, double *C, int64_t ldc, cudaStream_t st);
 // Per-atom scratch of the model: E_i [n] at d_aux, W_i [9n] right after it.
 dp_status ensure_aux(dp_model *m, int64_t n);
 dp_status nlist_create_internal(const dp_model *m, int64_t n, const int32_t *type, const double box[9], double rcut,

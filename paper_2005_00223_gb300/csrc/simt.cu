@@ -209,10 +209,15 @@ __global__ void __launch_bounds__(S::NT) k_embed_fwd(ModelDev md, BoxDev bx, con
 
 // Fitting net of center type ti on A atoms (positions pos_begin + A*blockIdx.x
 // of the type-sorted order): E_i forward, dE/dD backward.
-template <typename Real, int A>
+// OZ: the first layer's products are done elsewhere (FP64 on the tensor
+// cores): its pre-activations z1 [count][f0] (bias included) are read, and
+// its pre-activation adjoints are written to dz1 [count][f0] instead of
+// forming dE/dD here.
+template <typename Real, int A, bool OZ>
 __global__ void __launch_bounds__(256) k_fit(ModelDev md, int ti, const int32_t *__restrict__ order, int64_t p0,
                                             int64_t pos_begin, int64_t count, const Real *__restrict__ D,
-                                            Real *__restrict__ dD, double *__restrict__ E_atom)
+                                            Real *__restrict__ dD, double *__restrict__ E_atom,
+                                            const double *__restrict__ z1, double *__restrict__ dz1)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Real *smem = reinterpret_cast<Real *>(smem_raw);
@@ -222,18 +227,19 @@ __global__ void __launch_bounds__(256) k_fit(ModelDev md, int ti, const int32_t 
     for (int k = 0; k < md.n_fit; ++k) wmax = max(wmax, md.fit.wout[k]);
     int fsum = 0;
     for (int k = 0; k < md.n_fit; ++k) fsum += md.fit.wout[k];
-    Real *sX = smem;                                     // [A][nd], later dy/dz buffers
-    Real *sT = sX + max(A * nd, 3 * A * wmax);           // [A][fsum] tanh values
+    Real *sX = smem;                                     // [A][nd] (not with OZ), later dy/dz buffers
+    Real *sT = sX + max(OZ ? 0 : A * nd, 3 * A * wmax);  // [A][fsum] tanh values
     Real *sY = sT + A * fsum;                            // [A][fsum] layer outputs
     const int64_t first = pos_begin + (int64_t)blockIdx.x * A;
     const int na = (int)min((int64_t)A, pos_begin + count - first);
     const Real *net = params_of<Real>(md) + md.fit_base + (int64_t)ti * md.fit.size;
     const Real *netT = paramsT_of<Real>(md) + md.fit_base + (int64_t)ti * md.fit.size;
 
-    for (int q = tid; q < A * nd; q += nthreads) {
-        int a = q / nd;
-        sX[q] = a < na ? D[(first + a - p0) * nd + (q - a * nd)] : Real(0);
-    }
+    if (!OZ)
+        for (int q = tid; q < A * nd; q += nthreads) {
+            int a = q / nd;
+            sX[q] = a < na ? D[(first + a - p0) * nd + (q - a * nd)] : Real(0);
+        }
     __syncthreads();
     // forward
     const Real *xin = sX;
@@ -244,14 +250,19 @@ __global__ void __launch_bounds__(256) k_fit(ModelDev md, int ti, const int32_t 
         const Real *b = net + md.fit.b[k];
         for (int o = tid; o < wout; o += nthreads) {
             Real acc[A];
-            const Real bo = __ldg(b + o);
+            if (OZ && k == 0) {
 #pragma unroll
-            for (int a = 0; a < A; ++a) acc[a] = bo;
+                for (int a = 0; a < A; ++a) acc[a] = a < na ? (Real)z1[(first + a - pos_begin) * wout + o] : Real(0);
+            } else {
+                const Real bo = __ldg(b + o);
+#pragma unroll
+                for (int a = 0; a < A; ++a) acc[a] = bo;
 #pragma unroll 4
-            for (int kk = 0; kk < win; ++kk) {
-                const Real w = __ldg(W + (int64_t)kk * wout + o);
+                for (int kk = 0; kk < win; ++kk) {
+                    const Real w = __ldg(W + (int64_t)kk * wout + o);
 #pragma unroll
-                for (int a = 0; a < A; ++a) acc[a] += xin[a * win + kk] * w;
+                    for (int a = 0; a < A; ++a) acc[a] += xin[a * win + kk] * w;
+                }
             }
 #pragma unroll
             for (int a = 0; a < A; ++a) {
@@ -302,6 +313,13 @@ __global__ void __launch_bounds__(256) k_fit(ModelDev md, int ti, const int32_t 
             dz[q] = dy[q] * (Real(1) - t * t);
         }
         __syncthreads();
+        if (OZ && k == 0) {
+            for (int q = tid; q < A * wout; q += nthreads) {
+                const int a = q / wout, o = q - a * wout;
+                if (a < na) dz1[(first + a - pos_begin) * wout + o] = (double)dz[q];
+            }
+            break;
+        }
         const Real *WT = netT + md.fit.W[k];             // [wout][kin]
         for (int kk = tid; kk < kin; kk += nthreads) {
             Real acc[A];
@@ -547,25 +565,25 @@ size_t embed_bwd_smem(const ModelDev &md)
 }
 
 template <typename Real>
-size_t fit_smem(const ModelDev &md, int A)
+size_t fit_smem(const ModelDev &md, int A, bool oz = false)
 {
     int wmax = 0, fsum = 0;
     for (int k = 0; k < md.n_fit; ++k) {
         wmax = wmax > md.fit.wout[k] ? wmax : md.fit.wout[k];
         fsum += md.fit.wout[k];
     }
-    size_t a = (size_t)A * md.desc_dim, b = (size_t)3 * A * wmax;
+    size_t a = oz ? 0 : (size_t)A * md.desc_dim, b = (size_t)3 * A * wmax;
     return sizeof(Real) * ((a > b ? a : b) + 2 * (size_t)A * fsum);
 }
 
-template <typename Real, int A>
+template <typename Real, int A, bool OZ>
 dp_status launch_fit_a(dp_model *m, const int32_t *order, int t, int64_t p0, int64_t b, int64_t count,
-                       const Real *D, Real *dD, double *E_atom, cudaStream_t st)
+                       const Real *D, Real *dD, double *E_atom, const double *z1, double *dz1, cudaStream_t st)
 {
-    const size_t sfit = fit_smem<Real>(m->dev, A);
+    const size_t sfit = fit_smem<Real>(m->dev, A, OZ);
     const unsigned tiles = (unsigned)((count + A - 1) / A);
-    DP_CUDA(cudaFuncSetAttribute(k_fit<Real, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sfit));
-    k_fit<Real, A><<<tiles, 256, sfit, st>>>(m->dev, t, order, p0, b, count, D, dD, E_atom);
+    DP_CUDA(cudaFuncSetAttribute(k_fit<Real, A, OZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sfit));
+    k_fit<Real, A, OZ><<<tiles, 256, sfit, st>>>(m->dev, t, order, p0, b, count, D, dD, E_atom, z1, dz1);
     DP_CUDA(cudaGetLastError());
     return DP_OK;
 }
@@ -577,9 +595,9 @@ dp_status launch_fit_a(dp_model *m, const int32_t *order, int t, int64_t p0, int
 // serve more atoms).  Otherwise A in 6..9 minimises (waves x A) with the
 // CTAs that fit on an SM at once, since the kernel is arithmetic bound and a
 // partly filled last wave idles SMs.
-template <typename Real>
-dp_status launch_fit(dp_model *m, const int32_t *order, int t, int64_t p0, int64_t b, int64_t count, const Real *D, Real *dD,
-                     double *E_atom, cudaStream_t st)
+template <typename Real, bool OZ>
+dp_status launch_fit_oz(dp_model *m, const int32_t *order, int t, int64_t p0, int64_t b, int64_t count,
+                        const Real *D, Real *dD, double *E_atom, const double *z1, double *dz1, cudaStream_t st)
 {
     const ModelDev &md = m->dev;
     int nsm = 0;
@@ -588,14 +606,14 @@ dp_status launch_fit(dp_model *m, const int32_t *order, int t, int64_t p0, int64
     long best = -1;
     if (count < 6L * nsm) {
         for (int A : {1, 2, 4, 6}) {
-            if (fit_smem<Real>(md, A) > 227 * 1024) continue;
+            if (fit_smem<Real>(md, A, OZ) > 227 * 1024) continue;
             const long tiles = (long)((count + A - 1) / A);
             const long cost = ((tiles + nsm - 1) / nsm) * A;
             if (best < 0 || cost <= best) { best = cost; bestA = A; }
         }
     } else {
         for (int A = 6; A <= 9; ++A) {
-            const size_t sm = fit_smem<Real>(md, A);
+            const size_t sm = fit_smem<Real>(md, A, OZ);
             if (sm > 227 * 1024) continue;
             const long fit = (long)((228 * 1024) / (sm + 1024));
             const long per_sm = fit < 1 ? 1 : (fit > 8 ? 8 : fit);
@@ -609,21 +627,112 @@ dp_status launch_fit(dp_model *m, const int32_t *order, int t, int64_t p0, int64
         set_error("fitting net too wide for the shared-memory tile");
         return DP_ERR_UNSUPPORTED;
     }
-    ProfScope ps(m->prof, PG_FIT, 1, st);
     switch (bestA) {
-    case 1: return launch_fit_a<Real, 1>(m, order, t, p0, b, count, D, dD, E_atom, st);
-    case 2: return launch_fit_a<Real, 2>(m, order, t, p0, b, count, D, dD, E_atom, st);
-    case 4: return launch_fit_a<Real, 4>(m, order, t, p0, b, count, D, dD, E_atom, st);
-    case 6: return launch_fit_a<Real, 6>(m, order, t, p0, b, count, D, dD, E_atom, st);
-    case 7: return launch_fit_a<Real, 7>(m, order, t, p0, b, count, D, dD, E_atom, st);
-    case 8: return launch_fit_a<Real, 8>(m, order, t, p0, b, count, D, dD, E_atom, st);
-    default: return launch_fit_a<Real, 9>(m, order, t, p0, b, count, D, dD, E_atom, st);
+    case 1: return launch_fit_a<Real, 1, OZ>(m, order, t, p0, b, count, D, dD, E_atom, z1, dz1, st);
+    case 2: return launch_fit_a<Real, 2, OZ>(m, order, t, p0, b, count, D, dD, E_atom, z1, dz1, st);
+    case 4: return launch_fit_a<Real, 4, OZ>(m, order, t, p0, b, count, D, dD, E_atom, z1, dz1, st);
+    case 6: return launch_fit_a<Real, 6, OZ>(m, order, t, p0, b, count, D, dD, E_atom, z1, dz1, st);
+    case 7: return launch_fit_a<Real, 7, OZ>(m, order, t, p0, b, count, D, dD, E_atom, z1, dz1, st);
+    case 8: return launch_fit_a<Real, 8, OZ>(m, order, t, p0, b, count, D, dD, E_atom, z1, dz1, st);
+    default: return launch_fit_a<Real, 9, OZ>(m, order, t, p0, b, count, D, dD, E_atom, z1, dz1, st);
     }
+}
+
+// Launches the fitting net of type t over `count` type-sorted positions from
+// `b`.  Atoms per CTA A: when 6 per CTA would leave SMs idle, each CTA gets
+// an SM of its own and the time goes with A, so A in {1, 2, 4, 6} minimises
+// ceil(ceil(count / A) / SMs) * A (ties to the larger A, whose weight loads
+// serve more atoms).  Otherwise A in 6..9 minimises (waves x A) with the
+// CTAs that fit on an SM at once, since the kernel is arithmetic bound and a
+// partly filled last wave idles SMs.
+template <typename Real>
+dp_status launch_fit(dp_model *m, const int32_t *order, int t, int64_t p0, int64_t b, int64_t count, const Real *D, Real *dD,
+                     double *E_atom, cudaStream_t st)
+{
+    ProfScope ps(m->prof, PG_FIT, 1, st);
+    return launch_fit_oz<Real, false>(m, order, t, p0, b, count, D, dD, E_atom, nullptr, nullptr, st);
+}
+
+// The first fitting layer of the FP64 scheme as FP64 products on the tensor
+// cores (ozaki.cu): digits of W1 (6-bit, rows of W1^T, for z1 = D W1) and of
+// W1^T (7-bit, rows of W1, for dE/dD = dz1 W1^T) per center type.
+constexpr int kOzSF = 9, kOzBF = 6, kOzSB = 8, kOzBB = 7;
+// Below this many atoms of a type the GEMMs cannot fill the GPU (a work unit
+// is 128 atoms) and the SIMT net is faster.
+constexpr int64_t kOzMinAtoms = 1024;
+
+bool oz_fit_ok(const ModelDev &md)
+{
+    const int f0 = md.fit.wout[0], nd = md.desc_dim;
+    return f0 % 48 == 0 && f0 <= 256 && nd % 64 == 0 && nd <= 1808 && getenv("DP_NO_OZAKI") == nullptr;
+}
+
+size_t oz_weight_halves(const ModelDev &md)
+{
+    return (size_t)(kOzSF + kOzSB) * md.fit.wout[0] * md.desc_dim;
+}
+
+dp_status oz_refresh_weights(dp_model *m, cudaStream_t st)
+{
+    const ModelDev &md = m->dev;
+    const int f0 = md.fit.wout[0], nd = md.desc_dim;
+    if (!m->d_ozw) {
+        DP_CUDA(cudaMalloc(&m->d_ozw, sizeof(__half) * oz_weight_halves(md) * md.ntypes));
+        DP_CUDA(cudaMalloc((void **)&m->d_oze, sizeof(int) * (size_t)(f0 + nd) * md.ntypes));
+        m->oz_stale = true;
+    }
+    if (!m->oz_stale) return DP_OK;
+    for (int t = 0; t < md.ntypes; ++t) {
+        __half *wf = (__half *)m->d_ozw + oz_weight_halves(md) * t, *wb = wf + (size_t)kOzSF * f0 * nd;
+        int *ef = m->d_oze + (size_t)(f0 + nd) * t, *eb = ef + f0;
+        const int64_t W0 = md.fit_base + (int64_t)t * md.fit.size + md.fit.W[0];
+        DP_TRY((oz_split<kOzSF, kOzBF>(md.pT + W0, nd, f0, f0, nd, 48, 16, wf, ef, st)));   // rows of W1^T
+        DP_TRY((oz_split<kOzSB, kOzBB>(md.p + W0, f0, nd, nd, f0, 64, 16, wb, eb, st)));    // rows of W1
+    }
+    m->oz_stale = false;
+    return DP_OK;
+}
+
+// Scratch of the first fitting layer for nb atoms (rows padded per type).
+size_t oz_bytes(const ModelDev &md, int64_t nb)
+{
+    const int64_t rows = nb + 128 * md.ntypes;
+    const int f0 = md.fit.wout[0], nd = md.desc_dim;
+    return sizeof(__half) * rows * (size_t)(kOzSF * nd + kOzSB * f0) + sizeof(int) * rows * 2 +
+           sizeof(double) * rows * 2 * f0 + 6 * 256;
+}
+
+dp_status fit_fp64_oz(dp_model *m, dp_nlist *nl, int t, int64_t p0, int64_t b, int64_t count, const double *D,
+                      double *dD, double *E_atom, char *scratch, cudaStream_t st)
+{
+    const ModelDev &md = m->dev;
+    const int f0 = md.fit.wout[0], nd = md.desc_dim;
+    const int64_t rows_pad = (count + 127) / 128 * 128;
+    auto carve = [&](size_t bytes) {
+        char *p = scratch;
+        scratch += (bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    __half *da = (__half *)carve(sizeof(__half) * rows_pad * kOzSF * nd);
+    __half *db = (__half *)carve(sizeof(__half) * rows_pad * kOzSB * f0);
+    int *ea = (int *)carve(sizeof(int) * rows_pad), *eb = (int *)carve(sizeof(int) * rows_pad);
+    double *z1 = (double *)carve(sizeof(double) * count * f0), *dz1 = (double *)carve(sizeof(double) * count * f0);
+    const __half *wf = (const __half *)m->d_ozw + oz_weight_halves(md) * t, *wb = wf + (size_t)kOzSF * f0 * nd;
+    const int *ef = m->d_oze + (size_t)(f0 + nd) * t, *eb2 = ef + f0;
+    const double *b1 = md.p + md.fit_base + (int64_t)t * md.fit.size + md.fit.b[0];
+    ProfScope ps(m->prof, PG_FIT, 5, st);
+    DP_TRY((oz_split<kOzSF, kOzBF>(D + (b - p0) * nd, nd, count, rows_pad, nd, 128, 16, da, ea, st)));
+    DP_TRY((oz_gemm<kOzSF, kOzBF, 48, 16>(m, count, f0, nd, da, ea, rows_pad, wf, ef, b1, z1, f0, st)));
+    DP_TRY((launch_fit_oz<double, true>(m, nl->d_order, t, p0, b, count, D, dD, E_atom, z1, dz1, st)));
+    DP_TRY((oz_split<kOzSB, kOzBB>(dz1, f0, count, rows_pad, f0, 128, 16, db, eb, st)));
+    return oz_gemm<kOzSB, kOzBB, 64, 16>(m, count, nd, f0, db, eb, rows_pad, wb, eb2, nullptr, dD + (b - p0) * nd, nd,
+                                        st);
 }
 
 template <class S, typename Real>
 dp_status launch_batch(dp_model *m, dp_nlist *nl, BoxDev bx, int64_t p0, int64_t nb, Real *T, Real *D, Real *dD,
-                       Real *act, double *E_atom, double *force, double *atom_virial, cudaStream_t st)
+                       Real *act, double *E_atom, double *force, double *atom_virial, char *oz_scratch,
+                       cudaStream_t st)
 {
     const ModelDev &md = m->dev;
     size_t sf = embed_fwd_smem<S, Real>(md), sb = embed_bwd_smem<S, Real>(md);
@@ -641,7 +750,10 @@ dp_status launch_batch(dp_model *m, dp_nlist *nl, BoxDev bx, int64_t p0, int64_t
         int64_t e = nl->type_off[t] + nl->type_count[t];
         if (e > p0 + nb) e = p0 + nb;
         if (e <= b) continue;
-        DP_TRY(launch_fit<Real>(m, nl->d_order, t, p0, b, e - b, D, dD, E_atom, st));
+        if (oz_scratch && e - b >= kOzMinAtoms)
+            DP_TRY(fit_fp64_oz(m, nl, t, p0, b, e - b, (const double *)D, (double *)dD, E_atom, oz_scratch, st));
+        else
+            DP_TRY(launch_fit<Real>(m, nl->d_order, t, p0, b, e - b, D, dD, E_atom, st));
     }
     {
         ProfScope ps(m->prof, PG_EMBED_BWD, 1, st);
@@ -673,7 +785,9 @@ dp_status compute_simt(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
     int64_t B = m->batch_atoms > 0 ? m->batch_atoms : n;
     if (B > n) B = n;
     if (B < 1) B = 1;
-    DP_TRY(ensure_workspace(m, per_atom * (size_t)B + 256 * 4));
+    const bool oz = sizeof(Real) == sizeof(double) && oz_fit_ok(md);
+    if (oz) DP_TRY(oz_refresh_weights(m, st));
+    DP_TRY(ensure_workspace(m, per_atom * (size_t)B + 256 * 4 + (oz ? oz_bytes(md, B) : 0)));
     char *w = m->ws;
     auto carve = [&](size_t bytes) {
         char *p = w;
@@ -684,6 +798,7 @@ dp_status compute_simt(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
     Real *D = (Real *)carve(sizeof(Real) * md.desc_dim * B);
     Real *dD = (Real *)carve(sizeof(Real) * md.desc_dim * B);
     Real *act = (Real *)carve(sizeof(Real) * (size_t)md.chunks_per_atom * md.act_stride * 32 * B);
+    char *ozs = oz ? carve(oz_bytes(md, B)) : nullptr;
     DP_CUDA(cudaMemsetAsync(d_force, 0, sizeof(double) * 3 * n, st));
     BoxDev bx = make_box(nl);
     const int *e = md.emb.wout;
@@ -691,11 +806,11 @@ dp_status compute_simt(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
         int64_t nb = n - p0 < B ? n - p0 : B;
         dp_status s;
         if (e[0] == 25)
-            s = launch_batch<ShapeWater, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, st);
+            s = launch_batch<ShapeWater, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, ozs, st);
         else if (e[0] == 8)
-            s = launch_batch<ShapeStudent, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, st);
+            s = launch_batch<ShapeStudent, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, ozs, st);
         else
-            s = launch_batch<ShapePaper, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, st);
+            s = launch_batch<ShapePaper, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, ozs, st);
         if (s != DP_OK) return s;
     }
     ProfScope ps(m->prof, PG_REDUCE, 2, st);
@@ -712,7 +827,14 @@ bool embed_shape_supported(int n_embed, const int *e)
            (e[0] == 32 && e[1] == 64 && e[2] == 128);
 }
 
-size_t fp64_bytes_per_atom(const ModelDev &md) { return bytes_per_atom<double>(md); }
+size_t fp64_bytes_per_atom(const ModelDev &md)
+{
+    // plus the first fitting layer's digits and pre-activations on the tensor-core route
+    const size_t oz = oz_fit_ok(md) ? sizeof(__half) * (size_t)(kOzSF * md.desc_dim + kOzSB * md.fit.wout[0]) +
+                                          2 * sizeof(int) + 2 * sizeof(double) * md.fit.wout[0]
+                                    : 0;
+    return bytes_per_atom<double>(md) + oz;
+}
 
 dp_status fit_f32(dp_model *m, dp_nlist *nl, const float *D, float *dD, double *d_atom_energy, cudaStream_t st)
 {
