@@ -148,6 +148,9 @@ struct dp_model {
     void *d_ozw = nullptr;            // fp16 digits of the first fitting layer's weights (FP64 products on the tensor cores)
     int *d_oze = nullptr;             // their row scales
     bool oz_stale = true;             // digits older than the parameters
+    void *d_ozw_emb = nullptr;        // fp16 digits of the widest embedding layer's weights, per net
+    int *d_oze_emb = nullptr;         // their row scales
+    bool oz_emb_stale = true;
     uint32_t tc_img_bytes = 0;
     double *d_train = nullptr;        // Adam moments m, v [n_params] each
     double *d_tscr = nullptr;         // scratch of the training calls
@@ -245,11 +248,30 @@ dp_status refresh_params_device(dp_model *m, cudaStream_t st);
 // FP64 products on the tensor cores (ozaki.cu): digits of the rows of an
 // FP64 matrix, and C = A B^T (+ bias) from the digits of A and of B.
 template <int S, int BETA>
-dp_status oz_split(const double *X, int64_t ldx, int64_t rows, int64_t rows_pad, int K, int TR, int KC, __half *dig,
-                   int *ex, cudaStream_t st);
+dp_status oz_split(const double *X, int64_t ldx, int64_t rows, int64_t rows_pad, int K, int K_pad, int TR, int KC,
+                   __half *dig, int *ex, cudaStream_t st);
 template <int S, int BETA, int NC, int KC>
 dp_status oz_gemm(const dp_model *m, int64_t M, int N, int K, const __half *dA, const int *eA, int64_t M_pad,
                   const __half *dB, const int *eB, const double *bias, double *C, int64_t ldc, cudaStream_t st);
+// Work list of the 32-neighbor chunks of positions [p0, p0 + nb) in tiles of
+// 4 chunks of one net (tc.cu): entry {atom, batch position, first slot,
+// net}, firstc [nb][ntypes], the tile count on the device.
+size_t chunks_batch_scratch(const ModelDev &md, int64_t nb);
+dp_status build_chunks_batch(dp_model *m, dp_nlist *nl, int64_t p0, int64_t nb, int4 *chunks, int *firstc,
+                             int *ntiles, char *scratch, cudaStream_t st);
+// FP64 embedding forward with its widest layer as a split product on the
+// tensor cores (oz_embed.cu): shapes, scratch per batch, weight digits, and
+// the forward of a batch (T, D, the stored activations).
+struct BoxDev;
+bool oz_emb_ok(const ModelDev &md);
+size_t oz_emb_bytes(const ModelDev &md, int64_t nb);
+dp_status oz_emb_refresh(dp_model *m, cudaStream_t st);
+dp_status oz_emb_fwd(dp_model *m, dp_nlist *nl, const BoxDev &bx, int64_t p0, int64_t nb, double *T, double *D,
+                     double *act, char *scratch, cudaStream_t st);
+// The backward of the batch whose forward ran last on the same scratch:
+// forces (added) and per-atom virials (added; zeroed by the caller).
+dp_status oz_emb_bwd(dp_model *m, dp_nlist *nl, const BoxDev &bx, int64_t nb, const double *T, const double *dD,
+                     const double *act, double *force, double *atom_virial, char *scratch, cudaStream_t st);
 // Per-atom scratch of the model: E_i [n] at d_aux, W_i [9n] right after it.
 dp_status ensure_aux(dp_model *m, int64_t n);
 dp_status nlist_create_internal(const dp_model *m, int64_t n, const int32_t *type, const double box[9], double rcut,

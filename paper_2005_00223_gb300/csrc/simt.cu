@@ -686,8 +686,8 @@ dp_status oz_refresh_weights(dp_model *m, cudaStream_t st)
         __half *wf = (__half *)m->d_ozw + oz_weight_halves(md) * t, *wb = wf + (size_t)kOzSF * f0 * nd;
         int *ef = m->d_oze + (size_t)(f0 + nd) * t, *eb = ef + f0;
         const int64_t W0 = md.fit_base + (int64_t)t * md.fit.size + md.fit.W[0];
-        DP_TRY((oz_split<kOzSF, kOzBF>(md.pT + W0, nd, f0, f0, nd, 48, 16, wf, ef, st)));   // rows of W1^T
-        DP_TRY((oz_split<kOzSB, kOzBB>(md.p + W0, f0, nd, nd, f0, 64, 16, wb, eb, st)));    // rows of W1
+        DP_TRY((oz_split<kOzSF, kOzBF>(md.pT + W0, nd, f0, f0, nd, nd, 48, 16, wf, ef, st)));   // rows of W1^T
+        DP_TRY((oz_split<kOzSB, kOzBB>(md.p + W0, f0, nd, nd, f0, f0, 64, 16, wb, eb, st)));    // rows of W1
     }
     m->oz_stale = false;
     return DP_OK;
@@ -721,10 +721,10 @@ dp_status fit_fp64_oz(dp_model *m, dp_nlist *nl, int t, int64_t p0, int64_t b, i
     const int *ef = m->d_oze + (size_t)(f0 + nd) * t, *eb2 = ef + f0;
     const double *b1 = md.p + md.fit_base + (int64_t)t * md.fit.size + md.fit.b[0];
     ProfScope ps(m->prof, PG_FIT, 5, st);
-    DP_TRY((oz_split<kOzSF, kOzBF>(D + (b - p0) * nd, nd, count, rows_pad, nd, 128, 16, da, ea, st)));
+    DP_TRY((oz_split<kOzSF, kOzBF>(D + (b - p0) * nd, nd, count, rows_pad, nd, nd, 128, 16, da, ea, st)));
     DP_TRY((oz_gemm<kOzSF, kOzBF, 48, 16>(m, count, f0, nd, da, ea, rows_pad, wf, ef, b1, z1, f0, st)));
     DP_TRY((launch_fit_oz<double, true>(m, nl->d_order, t, p0, b, count, D, dD, E_atom, z1, dz1, st)));
-    DP_TRY((oz_split<kOzSB, kOzBB>(dz1, f0, count, rows_pad, f0, 128, 16, db, eb, st)));
+    DP_TRY((oz_split<kOzSB, kOzBB>(dz1, f0, count, rows_pad, f0, f0, 128, 16, db, eb, st)));
     return oz_gemm<kOzSB, kOzBB, 64, 16>(m, count, nd, f0, db, eb, rows_pad, wb, eb2, nullptr, dD + (b - p0) * nd, nd,
                                         st);
 }
@@ -732,14 +732,17 @@ dp_status fit_fp64_oz(dp_model *m, dp_nlist *nl, int t, int64_t p0, int64_t b, i
 template <class S, typename Real>
 dp_status launch_batch(dp_model *m, dp_nlist *nl, BoxDev bx, int64_t p0, int64_t nb, Real *T, Real *D, Real *dD,
                        Real *act, double *E_atom, double *force, double *atom_virial, char *oz_scratch,
-                       cudaStream_t st)
+                       char *ozemb_scratch, cudaStream_t st)
 {
     const ModelDev &md = m->dev;
     size_t sf = embed_fwd_smem<S, Real>(md), sb = embed_bwd_smem<S, Real>(md);
     DP_CUDA(cudaFuncSetAttribute(k_embed_fwd<S, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
     DP_CUDA(cudaFuncSetAttribute(k_embed_bwd<S, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
     const Pos4 *pos = (const Pos4 *)nl->d_pos;
-    {
+    if (ozemb_scratch) {
+        ProfScope ps(m->prof, PG_EMBED_FWD, 4, st);
+        DP_TRY(oz_emb_fwd(m, nl, bx, p0, nb, (double *)T, (double *)D, (double *)act, ozemb_scratch, st));
+    } else {
         ProfScope ps(m->prof, PG_EMBED_FWD, 1, st);
         k_embed_fwd<S, Real><<<(unsigned)nb, S::NT, sf, st>>>(md, bx, nl->d_order, p0, pos, nl->d_nlist, nl->d_nnei,
                                                               T, D, act);
@@ -755,7 +758,11 @@ dp_status launch_batch(dp_model *m, dp_nlist *nl, BoxDev bx, int64_t p0, int64_t
         else
             DP_TRY(launch_fit<Real>(m, nl->d_order, t, p0, b, e - b, D, dD, E_atom, st));
     }
-    {
+    if (ozemb_scratch) {
+        ProfScope ps(m->prof, PG_EMBED_BWD, 3, st);
+        DP_TRY(oz_emb_bwd(m, nl, bx, nb, (const double *)T, (const double *)dD, (const double *)act, force,
+                          atom_virial, ozemb_scratch, st));
+    } else {
         ProfScope ps(m->prof, PG_EMBED_BWD, 1, st);
         k_embed_bwd<S, Real><<<(unsigned)nb, S::NT, sb, st>>>(md, bx, nl->d_order, p0, pos, nl->d_nlist, nl->d_nnei,
                                                               T, dD, act, force, atom_virial);
@@ -786,8 +793,11 @@ dp_status compute_simt(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
     if (B > n) B = n;
     if (B < 1) B = 1;
     const bool oz = sizeof(Real) == sizeof(double) && oz_fit_ok(md);
+    const bool ozemb = sizeof(Real) == sizeof(double) && oz_emb_ok(md);
     if (oz) DP_TRY(oz_refresh_weights(m, st));
-    DP_TRY(ensure_workspace(m, per_atom * (size_t)B + 256 * 4 + (oz ? oz_bytes(md, B) : 0)));
+    if (ozemb) DP_TRY(oz_emb_refresh(m, st));
+    DP_TRY(ensure_workspace(m, per_atom * (size_t)B + 256 * 5 + (oz ? oz_bytes(md, B) : 0) +
+                                   (ozemb ? oz_emb_bytes(md, B) : 0)));
     char *w = m->ws;
     auto carve = [&](size_t bytes) {
         char *p = w;
@@ -799,18 +809,20 @@ dp_status compute_simt(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
     Real *dD = (Real *)carve(sizeof(Real) * md.desc_dim * B);
     Real *act = (Real *)carve(sizeof(Real) * (size_t)md.chunks_per_atom * md.act_stride * 32 * B);
     char *ozs = oz ? carve(oz_bytes(md, B)) : nullptr;
+    char *ozes = ozemb ? carve(oz_emb_bytes(md, B)) : nullptr;
     DP_CUDA(cudaMemsetAsync(d_force, 0, sizeof(double) * 3 * n, st));
+    if (ozemb) DP_CUDA(cudaMemsetAsync(d_atom_virial, 0, sizeof(double) * 9 * n, st));   // accumulated per chunk
     BoxDev bx = make_box(nl);
     const int *e = md.emb.wout;
     for (int64_t p0 = 0; p0 < n; p0 += B) {
         int64_t nb = n - p0 < B ? n - p0 : B;
         dp_status s;
         if (e[0] == 25)
-            s = launch_batch<ShapeWater, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, ozs, st);
+            s = launch_batch<ShapeWater, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, ozs, ozes, st);
         else if (e[0] == 8)
-            s = launch_batch<ShapeStudent, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, ozs, st);
+            s = launch_batch<ShapeStudent, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, ozs, ozes, st);
         else
-            s = launch_batch<ShapePaper, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, ozs, st);
+            s = launch_batch<ShapePaper, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, ozs, ozes, st);
         if (s != DP_OK) return s;
     }
     ProfScope ps(m->prof, PG_REDUCE, 2, st);
@@ -833,7 +845,9 @@ size_t fp64_bytes_per_atom(const ModelDev &md)
     const size_t oz = oz_fit_ok(md) ? sizeof(__half) * (size_t)(kOzSF * md.desc_dim + kOzSB * md.fit.wout[0]) +
                                           2 * sizeof(int) + 2 * sizeof(double) * md.fit.wout[0]
                                     : 0;
-    return bytes_per_atom<double>(md) + oz;
+    // and the split-product embedding's buffers (affine in the batch size)
+    const size_t ozemb = oz_emb_ok(md) ? (oz_emb_bytes(md, 2048) - oz_emb_bytes(md, 1024)) / 1024 + 1 : 0;
+    return bytes_per_atom<double>(md) + oz + ozemb;
 }
 
 dp_status fit_f32(dp_model *m, dp_nlist *nl, const float *D, float *dD, double *d_atom_energy, cudaStream_t st)

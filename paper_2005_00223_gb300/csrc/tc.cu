@@ -751,11 +751,15 @@ __global__ void __launch_bounds__(kCbThreads) k_cb_plan(ModelDev md, int64_t n, 
     *ntiles = base / 4;
 }
 
+// Entry {atom, tj, first slot, net}; with firstc (the FP64 work list of a
+// batch) {atom, position in the batch, first slot, net} instead, and
+// firstc[p * ntypes + tj] = the index of the first chunk of (p, tj).
 __global__ void __launch_bounds__(kCbThreads) k_cb_write(ModelDev md, int64_t n, const int32_t *__restrict__ order,
                                                         const int32_t *__restrict__ type,
                                                         const int32_t *__restrict__ nnei, const int *__restrict__ loc,
                                                         const int *__restrict__ boff, int nb,
-                                                        const int *__restrict__ gtab, int4 *__restrict__ chunks)
+                                                        const int *__restrict__ gtab, int4 *__restrict__ chunks,
+                                                        int *__restrict__ firstc)
 {
     const int64_t p = blockIdx.x * (int64_t)kCbThreads + threadIdx.x;
     if (p >= n) return;
@@ -764,7 +768,8 @@ __global__ void __launch_bounds__(kCbThreads) k_cb_write(ModelDev md, int64_t n,
         const int nch = (nnei[(int64_t)a * md.ntypes + tj] + 31) >> 5;
         const int net = ti * md.ntypes + tj;
         const int dst = gtab[2 * net] + boff[tj * nb + blockIdx.x] + loc[(int64_t)tj * n + p] - gtab[2 * net + 1];
-        for (int c = 0; c < nch; ++c) chunks[dst + c] = make_int4(a, tj, c * 32, net);
+        if (firstc) firstc[p * md.ntypes + tj] = dst;
+        for (int c = 0; c < nch; ++c) chunks[dst + c] = make_int4(a, firstc ? (int)p : tj, c * 32, net);
     }
 }
 
@@ -1377,7 +1382,7 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
         k_cb_plan<<<1, kCbThreads, 0, st>>>(md, n, ttab, ttab + kMaxTypes, cb_loc, cb_bsum, cb_boff, nb, cb_gtab,
                                             chunks, cnt);
         k_cb_write<<<nb, kCbThreads, 0, st>>>(md, n, nl->d_order, nl->d_type, nl->d_nnei, cb_loc, cb_boff, nb,
-                                              cb_gtab, chunks);
+                                              cb_gtab, chunks, nullptr);
     }
     DP_CUDA(cudaGetLastError());
     DP_CUDA(cudaFuncSetAttribute(k_embed_fwd_tc<S, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::FWD_SMEM));
@@ -1415,6 +1420,53 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
 }
 
 }  // namespace
+
+// Scratch of build_chunks_batch for nb positions.
+size_t chunks_batch_scratch(const ModelDev &md, int64_t nb)
+{
+    const int64_t blocks = (nb + kCbThreads - 1) / kCbThreads;
+    return 256 * 4 + sizeof(int) * (size_t)md.ntypes * nb + sizeof(int) * (size_t)2 * md.ntypes * blocks +
+           sizeof(int) * 2 * kMaxTypes * kMaxTypes + sizeof(int64_t) * 2 * kMaxTypes;
+}
+
+// Work list of the 32-neighbor chunks of positions [p0, p0 + nb) of the
+// type-sorted order, grouped by net and padded to tiles of 4 chunks of one
+// net: entry {atom, batch position, first slot, net} (atom -1: padding),
+// firstc[q * ntypes + tj] = first chunk of (p0 + q, tj), *ntiles on the
+// device.  At most nb * chunks_per_atom + 3 ntypes^2 entries.
+dp_status build_chunks_batch(dp_model *m, dp_nlist *nl, int64_t p0, int64_t nb, int4 *chunks, int *firstc,
+                             int *ntiles, char *scratch, cudaStream_t st)
+{
+    const ModelDev &md = m->dev;
+    const int blocks = (int)((nb + kCbThreads - 1) / kCbThreads);
+    auto carve = [&](size_t bytes) {
+        char *p = scratch;
+        scratch += (bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    int *loc = (int *)carve(sizeof(int) * (size_t)md.ntypes * nb);
+    int *bsum = (int *)carve(sizeof(int) * (size_t)2 * md.ntypes * blocks);
+    int *boff = bsum + (size_t)md.ntypes * blocks;
+    int *gtab = (int *)carve(sizeof(int) * 2 * kMaxTypes * kMaxTypes);
+    int64_t *ttab = (int64_t *)carve(sizeof(int64_t) * 2 * kMaxTypes);
+    int64_t htab[2 * kMaxTypes] = {0};
+    for (int t = 0; t < md.ntypes; ++t) {
+        int64_t b = nl->type_off[t] - p0, e = nl->type_off[t] + nl->type_count[t] - p0;
+        b = b < 0 ? 0 : (b > nb ? nb : b);
+        e = e < 0 ? 0 : (e > nb ? nb : e);
+        htab[t] = b;
+        htab[kMaxTypes + t] = e - b;
+    }
+    DP_CUDA(cudaMemcpyAsync(ttab, htab, sizeof(htab), cudaMemcpyHostToDevice, st));
+    const int32_t *order = nl->d_order + p0;
+    k_cb_count<<<blocks, kCbThreads, 0, st>>>(md, nb, order, nl->d_nnei, loc, bsum, blocks);
+    k_cb_plan<<<1, kCbThreads, 0, st>>>(md, nb, ttab, ttab + kMaxTypes, loc, bsum, boff, blocks, gtab, chunks,
+                                        ntiles);
+    k_cb_write<<<blocks, kCbThreads, 0, st>>>(md, nb, order, nl->d_type, nl->d_nnei, loc, boff, blocks, gtab, chunks,
+                                              firstc);
+    DP_CUDA(cudaGetLastError());
+    return DP_OK;
+}
 
 dp_status pack_tc_weights(dp_model *m)
 {

@@ -179,6 +179,14 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *v)
 
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
+// 8 consecutive 32-bit columns of this thread's TMEM lane (raw bits).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t *r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
 // 4 consecutive FP32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float *out)
 {

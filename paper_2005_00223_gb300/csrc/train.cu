@@ -246,6 +246,7 @@ dp_status dp_adam_step(dp_model *m, const double *d_grad, double lr, double beta
     DP_TRY(refresh_params_device(m, st));
     m->params_dirty = true;
     m->oz_stale = true;
+    m->oz_emb_stale = true;
     return DP_OK;
 }
 
