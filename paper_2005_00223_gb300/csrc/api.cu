@@ -366,9 +366,13 @@ dp_status dp_model_create(const dp_model_config *cfg, uint64_t seed, dp_model **
     const char *env = getenv("DP_BATCH_ATOMS");
     m->batch_atoms = env ? atoll(env) : 0;
     if (m->batch_atoms <= 0) {
-        // workspace budget of the FP64 path: 12 GiB of per-atom scratch
+        // workspace budget of the FP64 path: a quarter of the device memory (at least 12 GiB) of
+        // per-atom scratch
+        size_t fr = 0, tot = 0;
+        size_t budget = (size_t)12 * 1024 * 1024 * 1024;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && tot / 4 > budget) budget = tot / 4;
         size_t per = fp64_bytes_per_atom(md);
-        m->batch_atoms = (int64_t)((size_t)12 * 1024 * 1024 * 1024 / per);
+        m->batch_atoms = (int64_t)(budget / per);
         if (m->batch_atoms < 256) m->batch_atoms = 256;
     }
     *out = m;

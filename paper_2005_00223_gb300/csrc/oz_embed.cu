@@ -1,24 +1,38 @@
-// Embedding net forward of the double-precision scheme (Sec. 2, Fig. 1(c,e,f))
-// with its widest layer (E1 -> E2 channels, the bulk of the multiply-adds)
-// as FP64 products on the tensor cores by error-free splitting (ozaki.cuh).
+// Embedding net of the double-precision scheme (Sec. 2, Fig. 1(c,e,f)),
+// forward and backward, with the products of its two hidden layers as FP64
+// products on the tensor cores by error-free splitting (ozaki.cuh); the
+// tanh, skip, contraction and force arithmetic around them stays FP64 on
+// the CUDA cores.
 //
 // Per batch of atoms (type-sorted positions [p0, p0 + nb)), over a work list
 // of 32-neighbor chunks grouped into tiles of 128 rows (one neighbor per
-// row) that never mix nets:
-//   k_ozf_front  one thread per row: environment row R (FP64), layer 0 and
-//                layer 1 (E0 -> E1, FP64 with the library's tanh), the tanh
-//                values stored for the backward pass, x2 (the layer-1
-//                output), R, and the fp16 digits of x2 with their row scale;
-//   oz::k_gemm   z3 = x2 W2 from the digits of x2 and of W2^T (per net), and
-//                in its epilogue (8 warps, two per row quarter, alternate
-//                groups of 8 channels) t3 = tanh(z3 + b2), the
-//                embedding output G = skip(x2) + t3, both stored for the
-//                backward pass, and the chunk's part of the contraction
-//                sum_j G_j^T R_j (a 32-row sum per chunk, in row order);
+// row, one chunk per row quarter) that never mix nets.  Forward:
+//   k_ozf_front  one thread per row: environment row R, layer 0 (t1 stored
+//                for the backward pass, x1) and the digits of x1;
+//   GEMM 1       z2 = x1 W1; epilogue: t2 = tanh(z2 + b1) (stored),
+//                x2 = skip(x1) + t2 and the digits of x2;
+//   GEMM 2       z3 = x2 W2; epilogue: t3 = tanh(z3 + b2), the embedding
+//                output G = skip(x2) + t3 (both stored) and the chunk's part
+//                of the contraction sum_j G_j^T R_j (a 32-row sum in row
+//                order);
 //   k_ozf_T      per atom: T = (1/sum sel) sum over its chunks (type, then
 //                chunk order) and D = T T<^T.
-// Results agree with the FP64 SIMT kernel to the rounding of the split
-// product (about K 2^-52 of |x2|_max |W2|_max per entry).
+// Backward:
+//   k_ozb_dT     per atom: dE/dT from dE/dD;
+//   k_ozb_front  one thread per row: dE/dG_j = dE/dT R_j, the direct part
+//                sum_m G_j[m] dE/dT[m] of dE/dR_j, dz3 = dE/dG_j (1 - t3^2)
+//                and its digits, the skip part of dE/dx2;
+//   GEMM 3       dE/dx2 = dz3 W2^T + skip; epilogue: dz2 = dE/dx2 (1 - t2^2)
+//                and its digits;
+//   GEMM 4       dE/dx1 = dz2 W1^T + skip; epilogue: layer 0, dE/ds, the
+//                chain through the environment row's Jacobian to g_ij and
+//                the scatter F_i += g_ij, F_j -= g_ij with the virial
+//                -d_ij (x) g_ij (reduced over the chunk's rows, added to the
+//                center atom).
+// The GEMM epilogues run on 8 warps, the two warps of a row quarter taking
+// alternate groups of 8 channels.  Results agree with the FP64 SIMT kernels
+// to the rounding of the split products (about K 2^-52 of |x|_max |W|_max
+// per entry).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -35,35 +49,62 @@ template <int E0_, int E1_, int E2_>
 struct OzEmb {
     static constexpr int E0 = E0_, E1 = E1_, E2 = E2_;
     static constexpr int S = 8, BETA = 7, NC = 64, KC = 16;
-    static constexpr int KP = (E1 + 15) / 16 * 16;   // padded K of z3 = x2 W2
-    static constexpr int NN = (E2 + NC - 1) / NC;    // units of 64 output channels
+    static constexpr int KP1 = (E0 + 15) / 16 * 16;  // padded K of z2 = x1 W1
+    static constexpr int KP = (E1 + 15) / 16 * 16;   // padded K of z3 = x2 W2 and of dE/dx1 = dz2 W1^T
+    static constexpr int KP2 = (E2 + 15) / 16 * 16;  // padded K of dE/dx2 = dz3 W2^T
+    static constexpr int NN = (E2 + NC - 1) / NC;    // units of 64 output channels of GEMM 2
     static constexpr int ACT = E0 + E1 + E2 + E2;    // stored per neighbor: t of each layer, then G
-    static constexpr int WSM = 2 * E0 + E0 * E1 + E1;
-    static constexpr int EPI = 26624;                // epilogue: G [8][8][33] and R [8][4][33] doubles
-    using Sh = oz::Shape<S, BETA, NC, KC, EPI>;
+    static constexpr int EPI = 26624;                // GEMM 2 epilogue: G [8][8][33] and R [8][4][33] doubles
+    static constexpr int EPIX = 3072;                // the other epilogues: [4][2][32] doubles
+    using Sh = oz::Shape<S, BETA, NC, KC, EPI>;      // GEMM 2
+    using Sh1 = oz::Shape<S, BETA, NC, KC, EPIX>;    // GEMM 1, 3, 4
+    // digits of the weights per net (halves): W1^T (GEMM 1), W2^T (GEMM 2), W2 (GEMM 3), W1 (GEMM 4)
+    static constexpr int64_t WF1 = (int64_t)NC * S * KP1, WF2 = (int64_t)NN * NC * S * KP, WB2 = (int64_t)NC * S * KP2,
+                             WB1 = (int64_t)NC * S * KP, WNET = WF1 + WF2 + WB2 + WB1;
+    static constexpr int ENET = 3 * NC + NN * NC;    // their row scales per net: f1, f2, b2, b1
     static_assert(8 * (8 + 4) * 33 * 8 <= EPI, "epilogue shared memory");
-    // backward: dE/dx2 = dz3 W2^T, K = E2 padded, one unit of 64 >= E1 channels
-    static constexpr int KP2 = (E2 + 15) / 16 * 16;
-    static constexpr int WSM2 = E0 + E0 * E1;        // W0, W1 of the backward epilogue
-    static constexpr int EPI2 = ((WSM2 + 4 * E0 * 32) * 8 + 16 + 1023) / 1024 * 1024;
-    using Sh2 = oz::Shape<S, BETA, NC, KC, EPI2>;
-    static_assert(E1 <= NC, "one unit of dE/dx2 channels");
+    static_assert(E1 <= NC && E0 <= NC, "one unit of 64 channels for GEMM 1, 3 and 4");
     static_assert((long long)S * KP2 * (1LL << (2 * BETA - 2)) <= (1LL << 24), "exact FP32 digit sums");
     static_assert((long long)S * KP * (1LL << (2 * BETA - 2)) <= (1LL << 24), "exact FP32 digit sums");
 };
 
-template <class O>
-__global__ void __launch_bounds__(128, 2) k_ozf_front(ModelDev md, BoxDev bx, const Pos4 *__restrict__ pos,
-                                                      const int32_t *__restrict__ nlist,
-                                                      const int32_t *__restrict__ nnei,
-                                                      const int4 *__restrict__ chunks, const int *__restrict__ ntiles_dev,
-                                                      double *__restrict__ act, __half *__restrict__ dig,
-                                                      int *__restrict__ eA, double *__restrict__ x2buf,
-                                                      double *__restrict__ Rbuf)
+// Digits of 8 consecutive columns k0 .. k0+7 of a row for row scale e (one 16-byte store per plane).
+template <class O, int KPAD>
+__device__ __forceinline__ void put_digits8(__half *dig, int64_t row, int k0, const double (&x)[8], int e)
 {
-    constexpr int E0 = O::E0, E1 = O::E1;
-    __shared__ double sW[O::WSM];   // W0 [E0], b0 [E0], W1 [E0][E1], b1 [E1]
-    const double *W0 = sW, *b0 = sW + E0, *W1 = sW + 2 * E0, *b1 = sW + 2 * E0 + E0 * E1;
+    int d[8][O::S];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) oz::digits<O::S, O::BETA>(x[c], e, d[c]);
+#pragma unroll
+    for (int i = 0; i < O::S; ++i) {
+        int v[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] = d[c][i];
+        *reinterpret_cast<uint4 *>(dig + oz::tiled(row, k0, i, O::S, 128, O::KC, KPAD)) = oz::pack8(v);
+    }
+}
+
+__device__ __forceinline__ void bar_pair(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+
+// The largest of v over the row's two warps (the two halves of a row quarter).
+__device__ __forceinline__ double pair_max(double v, unsigned char *esm, int quarter, int half, int lane)
+{
+    double *sm = reinterpret_cast<double *>(esm + 16);   // [4][2][32]
+    sm[(quarter * 2 + half) * 32 + lane] = v;
+    bar_pair(1 + quarter);
+    return fmax(v, sm[(quarter * 2 + (half ^ 1)) * 32 + lane]);
+}
+
+template <class O>
+__global__ void __launch_bounds__(128) k_ozf_front(ModelDev md, BoxDev bx, const Pos4 *__restrict__ pos,
+                                                   const int32_t *__restrict__ nlist, const int32_t *__restrict__ nnei,
+                                                   const int4 *__restrict__ chunks, const int *__restrict__ ntiles_dev,
+                                                   double *__restrict__ act, __half *__restrict__ dig1,
+                                                   int *__restrict__ eA1, double *__restrict__ x1buf,
+                                                   double *__restrict__ Rbuf)
+{
+    constexpr int E0 = O::E0;
+    __shared__ double sW[2 * E0];   // W0 [E0], b0 [E0]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ntiles = *ntiles_dev;
     int cur = -1;
@@ -76,8 +117,6 @@ __global__ void __launch_bounds__(128, 2) k_ozf_front(ModelDev md, BoxDev bx, co
                 sW[q] = P[md.emb.W[0] + q];
                 sW[E0 + q] = P[md.emb.b[0] + q];
             }
-            for (int q = tid; q < E0 * E1; q += 128) sW[2 * E0 + q] = P[md.emb.W[1] + q];
-            for (int q = tid; q < E1; q += 128) sW[2 * E0 + E0 * E1 + q] = P[md.emb.b[1] + q];
             __syncthreads();
             cur = net;
         }
@@ -99,67 +138,120 @@ __global__ void __launch_bounds__(128, 2) k_ozf_front(ModelDev md, BoxDev bx, co
                                         (O::ACT * 32)
                             : nullptr;
         // layer 0: the input is the scalar s = R[0]
-        double x1[E0];
-#pragma unroll
-        for (int o = 0; o < E0; ++o) {
-            const double t1 = tanh_f64(b0[o] + R[0] * W0[o]);
-            x1[o] = ((E0 == 1 || E0 == 2) ? R[0] : 0.0) + t1;
-            if (ca) ca[o * 32 + lane] = t1;
-        }
-        // layer 1
-        double *x2t = x2buf + (int64_t)t * E1 * 128 + tid;   // x2 of this row, channel stride 128
+        double x1[O::KP1];
         double mx = 0.0;
-        // channels o = h OW + o0: the skip source x1[o0] has a compile-time index
-        constexpr int NH = (E1 == 2 * E0) ? 2 : 1, OW = E1 / NH;
-#pragma unroll 1
-        for (int h = 0; h < NH; ++h) {
 #pragma unroll
-            for (int o0 = 0; o0 < OW; ++o0) {
-                const int o = h * OW + o0;
-                double z = b1[o];
-#pragma unroll
-                for (int k = 0; k < E0; ++k) z += x1[k] * W1[k * E1 + o];
-                const double t2 = tanh_f64(z);
-                const double x2 = ((E1 == E0 || E1 == 2 * E0) ? x1[o0] : 0.0) + t2;
-                if (ca) ca[(E0 + o) * 32 + lane] = t2;
-                x2t[o * 128] = x2;
-                mx = fmax(mx, fabs(x2));
+        for (int o = 0; o < O::KP1; ++o) {
+            x1[o] = 0.0;
+            if (o < E0) {
+                const double t1 = tanh_f64(sW[E0 + o] + R[0] * sW[o]);
+                x1[o] = ((E0 == 1 || E0 == 2) ? R[0] : 0.0) + t1;
+                if (ca) ca[o * 32 + lane] = t1;
+                x1buf[((int64_t)t * E0 + o) * 128 + tid] = x1[o];
+                mx = fmax(mx, fabs(x1[o]));
             }
         }
-        // digits of x2 (zero for rows without a neighbor), x2 read back by the thread that wrote it
-        const int e = valid ? oz::row_exp(mx) : 0;
-        eA[row] = e;
-#pragma unroll 1
-        for (int k0 = 0; k0 < O::KP; k0 += 8) {
-            int d[8][O::S];
+        const int e = oz::row_exp(mx);
+        eA1[row] = e;
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-                oz::digits<O::S, O::BETA>((valid && k0 + c < E1) ? x2t[(k0 + c) * 128] : 0.0, e, d[c]);
+        for (int k0 = 0; k0 < O::KP1; k0 += 8) {
+            double v[8];
 #pragma unroll
-            for (int i = 0; i < O::S; ++i) {
-                int v[8];
-#pragma unroll
-                for (int c = 0; c < 8; ++c) v[c] = d[c][i];
-                *reinterpret_cast<uint4 *>(dig + oz::tiled(row, k0, i, O::S, 128, O::KC, O::KP)) = oz::pack8(v);
-            }
+            for (int c = 0; c < 8; ++c) v[c] = x1[k0 + c];
+            put_digits8<O, O::KP1>(dig1, row, k0, v, e);
         }
     }
 }
+
+// GEMM 1 epilogue: z2 = x1 W1 (+ b1), t2 = tanh(z2) stored, x2 = skip(x1) + t2 stored, the digits of x2.
+template <class O>
+struct Fwd1Epi {
+    using Sh = typename O::Sh1;
+    ModelDev md;
+    const int4 *chunks;
+    const __half *wdig;   // digits of W1^T of net 0; net n at + n WNET
+    const int *weB;       // their row scales; net n at + n ENET
+    const int *eA1;
+    const double *x1buf;
+    double *act, *x2buf;
+    __half *dig2;
+    int *eA2;
+    __device__ const __half *b_unit(int64_t tile, int) const { return wdig + chunks[tile * 4].w * O::WNET; }
+    template <int HF>
+    __device__ __forceinline__ void body(int64_t tile, uint32_t trow, int rt, int lane, int quarter,
+                                         const int4 &c4, unsigned char *esm) const
+    {
+        constexpr int E0 = O::E0, E1 = O::E1, NG = (O::KP / 8 - HF + 1) / 2;   // this half's column groups
+        const int net = c4.w, tj = net % md.ntypes;
+        const int64_t row = tile * 128 + rt;
+        const int er = eA1[row];
+        const double *b1 = md.p + md.emb_base + (int64_t)net * md.emb.size + md.emb.b[1];
+        const int *eB = weB + (int64_t)net * O::ENET;
+        double *ca = act + ((int64_t)c4.y * md.chunks_per_atom + md.chunk_off[tj] + c4.z / 32) * (O::ACT * 32);
+        double xv[NG][8];
+        double mx = 0.0;
+#pragma unroll
+        for (int gi = 0; gi < NG; ++gi) {
+            const int k0 = 8 * HF + 16 * gi;
+            double xs[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int o = k0 + c;
+                xs[c] = 0.0;
+                if (o < E1 && (E1 == E0 || E1 == 2 * E0)) xs[c] = x1buf[(tile * E0 + o % E0) * 128 + rt];
+            }
+            long long H[8], L[8];
+            oz::acc_load8<Sh>(trow, k0, H, L);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int o = k0 + c;
+                xv[gi][c] = 0.0;
+                if (o < E1) {
+                    const double t2 = tanh_f64(oz::acc_value<Sh>(H[c], L[c], er + eB[o]) + b1[o]);
+                    const double x2 = xs[c] + t2;
+                    ca[(E0 + o) * 32 + lane] = t2;
+                    x2buf[(tile * E1 + o) * 128 + rt] = x2;
+                    xv[gi][c] = x2;
+                    mx = fmax(mx, fabs(x2));
+                }
+            }
+        }
+        mx = pair_max(mx, esm, quarter, HF, lane);
+        const int e = oz::row_exp(mx);
+        if (HF == 0) eA2[row] = e;
+#pragma unroll
+        for (int gi = 0; gi < NG; ++gi) put_digits8<O, O::KP>(dig2, row, 8 * HF + 16 * gi, xv[gi], e);
+    }
+    __device__ void operator()(int64_t tile, int, uint32_t trow, int tid, unsigned char *esm) const
+    {
+        const int warp = tid >> 5, lane = tid & 31, quarter = warp & 3, half = warp >> 2;
+        const int4 c4 = chunks[tile * 4 + quarter];
+        const int rt = quarter * 32 + lane;
+        if (c4.x < 0) {   // a padding chunk: zero digits
+            const double z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int k0 = 8 * half; k0 < O::KP; k0 += 16) put_digits8<O, O::KP>(dig2, tile * 128 + rt, k0, z, 0);
+            if (half == 0) eA2[tile * 128 + rt] = 0;
+            return;
+        }
+        if (half == 0) body<0>(tile, trow, rt, lane, quarter, c4, esm);
+        else body<1>(tile, trow, rt, lane, quarter, c4, esm);
+    }
+};
 
 template <class O>
 struct FwdEpi {
     using Sh = typename O::Sh;
     ModelDev md;
     const int4 *chunks;
-    const __half *wdig;   // digits of W2^T per net: [net][NN][KP / 16][S][64 x 16]
-    const int *weB;       // their row scales [net][NN * 64]
+    const __half *wdig;   // digits of W2^T of net 0 ([NN][KP / 16][S][64 x 16]); net n at + n WNET
+    const int *weB;       // their row scales; net n at + n ENET
     const int *eA;
     const double *x2buf, *Rbuf;
     double *act, *Tpart;
     __device__ const __half *b_unit(int64_t tile, int nchunk) const
     {
         const int net = chunks[tile * 4].w;
-        return wdig + ((int64_t)net * O::NN + nchunk) * (O::KP / O::KC) * O::S * O::NC * O::KC;
+        return wdig + net * O::WNET + (int64_t)nchunk * (O::KP / O::KC) * O::S * O::NC * O::KC;
     }
     // 8 warps: the two warps of a row quarter (one chunk) take alternate groups of 8 output channels
     __device__ void operator()(int64_t tile, int nchunk, uint32_t trow, int tid, unsigned char *esm) const
@@ -177,7 +269,7 @@ struct FwdEpi {
         for (int c = 0; c < 4; ++c) sR[c * 33 + lane] = Rbuf[(tile * 4 + c) * 128 + rt];
         const int er = eA[row];
         const double *b2 = md.p + md.emb_base + (int64_t)net * md.emb.size + md.emb.b[2];
-        const int *eB = weB + (int64_t)net * O::NN * O::NC;
+        const int *eB = weB + (int64_t)net * O::ENET;
         double *ca = act + ((int64_t)c4.y * md.chunks_per_atom + md.chunk_off[tj] + c4.z / 32) * (O::ACT * 32);
         double *Tp = Tpart + (tile * 4 + quarter) * 4 * E2;
         __syncwarp();
@@ -352,41 +444,35 @@ __global__ void __launch_bounds__(128) k_ozb_front(ModelDev md, const int4 *__re
     }
 }
 
-__device__ __forceinline__ void bar_pair(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
-
-// Epilogue of dx2 = dz3 W2^T (8 warps; the two warps of a row quarter take
-// alternate groups of 8 of the E1 channels): dE/dx2 = dx2 + skip, dz2, the
-// layer-1 input gradient (partial sums of the two warps combined through
-// shared memory), then one warp per quarter: layer 0, dE/ds, the chain
-// through the environment row's Jacobian to g_ij, the force scatter
-// F_i += g_ij, F_j -= g_ij and the virial -d_ij (x) g_ij (both reduced over
-// the chunk's 32 rows and added to the center atom).
+// GEMM 3 epilogue: dE/dx2 = dz3 W2^T + skip (stored), dz2 = dE/dx2 (1 - t2^2) and its digits.
 template <class O>
-struct BwdEpi {
-    using Sh = typename O::Sh2;
+struct Bwd3Epi {
+    using Sh = typename O::Sh1;
     ModelDev md;
-    BoxDev bx;
-    const Pos4 *pos;
-    const int32_t *nlist, *nnei;
     const int4 *chunks;
-    const __half *wdig;   // digits of W2 (rows k, K = E2) per net: [net][KP2 / 16][S][64 x 16]
-    const int *weB;       // their row scales [net][64]
+    const __half *wdig;   // digits of W2 of net 0; net n at + n WNET
+    const int *weB;
     const int *eA;
-    const double *act, *dskip, *dRbuf;
-    double *force, *atom_virial;
-    __device__ const __half *b_unit(int64_t tile, int) const
-    {
-        const int net = chunks[tile * 4].w;
-        return wdig + (int64_t)net * (O::KP2 / O::KC) * O::S * O::NC * O::KC;
-    }
-    // dE/dx2 for the channel groups k0 = 8 HF + 16 i, dz2, and their part of dE/dx1 (with the skip)
+    const double *act, *dskip;
+    double *dybuf;
+    __half *dig1;
+    int *eA1;
+    __device__ const __half *b_unit(int64_t tile, int) const { return wdig + chunks[tile * 4].w * O::WNET; }
     template <int HF>
-    __device__ __forceinline__ void layer1(int64_t tile, uint32_t trow, int rt, int lane, int er, const int *eB,
-                                           const double *ca, const double *W1, double (&dx1)[O::E0]) const
+    __device__ __forceinline__ void body(int64_t tile, uint32_t trow, int rt, int lane, int quarter,
+                                         const int4 &c4, unsigned char *esm) const
     {
-        constexpr int E0 = O::E0, E1 = O::E1;
+        constexpr int E0 = O::E0, E1 = O::E1, NG = (O::KP / 8 - HF + 1) / 2;
+        const int net = c4.w, tj = net % md.ntypes;
+        const int64_t row = tile * 128 + rt;
+        const int er = eA[row];
+        const int *eB = weB + (int64_t)net * O::ENET + O::NC + O::NN * O::NC;
+        const double *ca = act + ((int64_t)c4.y * md.chunks_per_atom + md.chunk_off[tj] + c4.z / 32) * (O::ACT * 32);
+        double dzv[NG][8];
+        double mx = 0.0;
 #pragma unroll
-        for (int k0 = 8 * HF; k0 < E1; k0 += 16) {
+        for (int gi = 0; gi < NG; ++gi) {
+            const int k0 = 8 * HF + 16 * gi;
             double ds8[8], t2v[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
@@ -399,69 +485,116 @@ struct BwdEpi {
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int k = k0 + c;
+                dzv[gi][c] = 0.0;
                 if (k < E1) {
                     const double dy = oz::acc_value<Sh>(H[c], L[c], er + eB[k]) + ds8[c];   // dE/dx2[k]
-                    const double dz = dy * (1.0 - t2v[c] * t2v[c]);
-#pragma unroll
-                    for (int j = 0; j < E0; ++j) dx1[j] += dz * W1[j * E1 + k];
-                    if (E1 == E0 || E1 == 2 * E0) dx1[k % E0] += dy;
+                    dybuf[(tile * E1 + k) * 128 + rt] = dy;
+                    dzv[gi][c] = dy * (1.0 - t2v[c] * t2v[c]);
+                    mx = fmax(mx, fabs(dzv[gi][c]));
                 }
             }
         }
+        mx = pair_max(mx, esm, quarter, HF, lane);
+        const int e = oz::row_exp(mx);
+        if (HF == 0) eA1[row] = e;
+#pragma unroll
+        for (int gi = 0; gi < NG; ++gi) put_digits8<O, O::KP>(dig1, row, 8 * HF + 16 * gi, dzv[gi], e);
     }
     __device__ void operator()(int64_t tile, int, uint32_t trow, int tid, unsigned char *esm) const
     {
-        constexpr int E0 = O::E0, E1 = O::E1;
-        int *s_net = reinterpret_cast<int *>(esm);                // net + 1 of the weights held (0: none yet)
-        double *sW = reinterpret_cast<double *>(esm + 16);        // W0 [E0], W1 [E0][E1]
-        double *sx = sW + O::WSM2;                                // [4][E0][32] partial dE/dx1
-        const int net = chunks[tile * 4].w;
-        if (*s_net != net + 1) {   // uniform over the CTA
-            __syncthreads();
-            const double *P = md.p + md.emb_base + (int64_t)net * md.emb.size;
-            for (int q = tid; q < E0; q += 256) sW[q] = P[md.emb.W[0] + q];
-            for (int q = tid; q < E0 * E1; q += 256) sW[E0 + q] = P[md.emb.W[1] + q];
-            __syncthreads();
-            if (tid == 0) *s_net = net + 1;
+        const int warp = tid >> 5, lane = tid & 31, quarter = warp & 3, half = warp >> 2;
+        const int4 c4 = chunks[tile * 4 + quarter];
+        const int rt = quarter * 32 + lane;
+        if (c4.x < 0) {
+            const double z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int k0 = 8 * half; k0 < O::KP; k0 += 16) put_digits8<O, O::KP>(dig1, tile * 128 + rt, k0, z, 0);
+            if (half == 0) eA1[tile * 128 + rt] = 0;
+            return;
         }
-        const double *W0 = sW, *W1 = sW + E0;
+        if (half == 0) body<0>(tile, trow, rt, lane, quarter, c4, esm);
+        else body<1>(tile, trow, rt, lane, quarter, c4, esm);
+    }
+};
+
+// GEMM 4 epilogue: dE/dx1 = dz2 W1^T + skip(dE/dx2), layer 0 (dz1, dE/ds; the two halves' parts
+// of dE/ds added through shared memory), then one warp per quarter: dE/dR_j, the Jacobian chain to
+// g_ij, the force scatter and the virial, reduced over the chunk's rows for the center atom.
+template <class O>
+struct Bwd4Epi {
+    using Sh = typename O::Sh1;
+    ModelDev md;
+    BoxDev bx;
+    const Pos4 *pos;
+    const int32_t *nlist, *nnei;
+    const int4 *chunks;
+    const __half *wdig;   // digits of W1 of net 0; net n at + n WNET
+    const int *weB;
+    const int *eA1;
+    const double *act, *dybuf, *dRbuf;
+    double *force, *atom_virial;
+    __device__ const __half *b_unit(int64_t tile, int) const { return wdig + chunks[tile * 4].w * O::WNET; }
+    template <int HF>
+    __device__ __forceinline__ double layer0(int64_t tile, uint32_t trow, int rt, int lane, int er, const int *eB,
+                                             const double *ca, const double *W0) const
+    {
+        constexpr int E0 = O::E0, E1 = O::E1, NG = (O::KP1 / 8 - HF + 1) / 2;
+        double ds = 0.0;
+#pragma unroll
+        for (int gi = 0; gi < NG; ++gi) {
+            const int j0 = 8 * HF + 16 * gi;
+            double sk[8], t1v[8], w0[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int j = j0 + c;
+                sk[c] = t1v[c] = w0[c] = 0.0;
+                if (j < E0) {
+                    if (E1 == E0) sk[c] = dybuf[(tile * E1 + j) * 128 + rt];
+                    else if (E1 == 2 * E0)
+                        sk[c] = dybuf[(tile * E1 + j) * 128 + rt] + dybuf[(tile * E1 + j + E0) * 128 + rt];
+                    t1v[c] = ca[j * 32 + lane];
+                    w0[c] = W0[j];
+                }
+            }
+            long long H[8], L[8];
+            oz::acc_load8<Sh>(trow, j0, H, L);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int j = j0 + c;
+                if (j < E0) {
+                    const double dx1 = oz::acc_value<Sh>(H[c], L[c], er + eB[j]) + sk[c];   // dE/dx1[j]
+                    ds += dx1 * (1.0 - t1v[c] * t1v[c]) * w0[c];
+                    if (E0 <= 2) ds += dx1;   // the skip of a first layer of width 1 or 2
+                }
+            }
+        }
+        return ds;
+    }
+    __device__ void operator()(int64_t tile, int, uint32_t trow, int tid, unsigned char *esm) const
+    {
+        constexpr int E0 = O::E0;
         const int warp = tid >> 5, lane = tid & 31, quarter = warp & 3, half = warp >> 2;
         const int4 c4 = chunks[tile * 4 + quarter];
         if (c4.x < 0) return;   // a padding chunk: both warps of the quarter skip
-        const int a = c4.x, tj = net % md.ntypes;
+        const int a = c4.x, net = c4.w, tj = net % md.ntypes;
         const int rt = quarter * 32 + lane;
         const int64_t row = tile * 128 + rt;
-        const int er = eA[row];
-        const int *eB = weB + (int64_t)net * O::NC;
+        const int er = eA1[row];
+        const int *eB = weB + (int64_t)net * O::ENET + 2 * O::NC + O::NN * O::NC;
         const double *ca = act + ((int64_t)c4.y * md.chunks_per_atom + md.chunk_off[tj] + c4.z / 32) * (O::ACT * 32);
-        double dx1[E0];
-#pragma unroll
-        for (int j = 0; j < E0; ++j) dx1[j] = 0.0;
-        if (half == 0) layer1<0>(tile, trow, rt, lane, er, eB, ca, W1, dx1);
-        else layer1<1>(tile, trow, rt, lane, er, eB, ca, W1, dx1);
-        double *sxq = sx + quarter * E0 * 32;
-        if (half == 1) {
-#pragma unroll
-            for (int j = 0; j < E0; ++j) sxq[j * 32 + lane] = dx1[j];
-        }
+        const double *W0 = md.p + md.emb_base + (int64_t)net * md.emb.size + md.emb.W[0];
+        double ds = half == 0 ? layer0<0>(tile, trow, rt, lane, er, eB, ca, W0)
+                              : layer0<1>(tile, trow, rt, lane, er, eB, ca, W0);
+        double *sm = reinterpret_cast<double *>(esm + 16);   // [4][32]
+        if (half == 1) sm[quarter * 32 + lane] = ds;
         bar_pair(1 + quarter);
         if (half == 1) return;
-#pragma unroll
-        for (int j = 0; j < E0; ++j) dx1[j] += sxq[j * 32 + lane];
+        ds += sm[quarter * 32 + lane];
         const int cnt = nnei[(int64_t)a * md.ntypes + tj];
         const bool valid = c4.z + lane < cnt;
         double fi[3] = {0.0, 0.0, 0.0}, vir[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) vir[q] = 0.0;
         if (valid) {
-            // layer 0 (input width 1): ds = sum_o dz_o W0[o] (+ the skip when E0 is 1 or 2)
-            double ds = 0.0;
-#pragma unroll
-            for (int j = 0; j < E0; ++j) {
-                const double t1 = ca[j * 32 + lane];
-                ds += dx1[j] * (1.0 - t1 * t1) * W0[j];
-                if (E0 <= 2) ds += dx1[j];
-            }
             double dR[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) dR[c] = dRbuf[(tile * 4 + c) * 128 + rt];
@@ -495,17 +628,19 @@ struct BwdEpi {
 #pragma unroll
             for (int q = 0; q < 9; ++q) atomicAdd(&atom_virial[9 * (int64_t)a + q], vir[q]);
         }
+        (void)E0;
     }
 };
 
 // Scratch of one batch: the work list, the digit and activation buffers of
-// both passes (the backward reuses the forward's digit, scale and x2
-// buffers), per-chunk contraction parts, dE/dT and the direct dE/dR.
+// both passes (the backward reuses the forward's buffers where their
+// contents are dead), per-chunk contraction parts, dE/dT and the direct
+// dE/dR.
 struct Bufs {
     int4 *chunks;
-    int *firstc, *ntiles, *eA;
-    __half *dig;
-    double *x2buf, *Rbuf, *Tpart, *dTbuf, *dRbuf, *dzbuf;
+    int *firstc, *ntiles, *eA, *eA1;
+    __half *dig, *dig1;
+    double *x1buf, *x2buf, *Rbuf, *Tpart, *dTbuf, *dRbuf, *dzbuf;
     char *cbs;
     size_t bytes;
 };
@@ -519,7 +654,7 @@ template <class O>
 Bufs layout(const ModelDev &md, int64_t nb, char *base)
 {
     const int64_t tiles = max_tiles_of(md, nb), rows = tiles * 128;
-    const int kmax = O::KP > O::KP2 ? O::KP : O::KP2;
+    const int kmax = O::KP > O::KP2 ? O::KP : O::KP2, kmax1 = O::KP > O::KP1 ? O::KP : O::KP1;
     Bufs b;
     size_t off = 0;
     auto carve = [&](size_t bytes) {
@@ -530,14 +665,17 @@ Bufs layout(const ModelDev &md, int64_t nb, char *base)
     b.chunks = (int4 *)carve(sizeof(int4) * tiles * 4);
     b.firstc = (int *)carve(sizeof(int) * (size_t)nb * md.ntypes);
     b.ntiles = (int *)carve(sizeof(int) * 4);
-    b.dig = (__half *)carve(sizeof(__half) * rows * O::S * kmax);
+    b.dig = (__half *)carve(sizeof(__half) * rows * O::S * kmax);     // x2 digits; then dz3
+    b.dig1 = (__half *)carve(sizeof(__half) * rows * O::S * kmax1);   // x1 digits; then dz2
     b.eA = (int *)carve(sizeof(int) * rows);
-    b.x2buf = (double *)carve(sizeof(double) * rows * O::E1);
+    b.eA1 = (int *)carve(sizeof(int) * rows);
+    b.x1buf = (double *)carve(sizeof(double) * rows * O::E0);
+    b.x2buf = (double *)carve(sizeof(double) * rows * O::E1);          // x2; then the skip part of dE/dx2
     b.Rbuf = (double *)carve(sizeof(double) * rows * 4);
     b.Tpart = (double *)carve(sizeof(double) * tiles * 4 * 4 * O::E2);
     b.dTbuf = (double *)carve(sizeof(double) * (size_t)nb * 4 * O::E2);
     b.dRbuf = (double *)carve(sizeof(double) * rows * 4);
-    b.dzbuf = (double *)carve(sizeof(double) * rows * O::KP2);
+    b.dzbuf = (double *)carve(sizeof(double) * rows * O::KP2);        // dz3 staging; then dE/dx2
     b.cbs = carve(chunks_batch_scratch(md, nb));
     b.bytes = off;
     return b;
@@ -554,27 +692,43 @@ dp_status refresh(dp_model *m, cudaStream_t st)
 {
     const ModelDev &md = m->dev;
     const int nnet = md.ntypes * md.ntypes;
-    const size_t per = (size_t)O::NN * O::NC * O::S * O::KP, per2 = (size_t)O::NC * O::S * O::KP2;
-    const size_t eper = (size_t)O::NN * O::NC + O::NC;
     if (!m->d_ozw_emb) {
-        DP_CUDA(cudaMalloc(&m->d_ozw_emb, sizeof(__half) * (per + per2) * nnet));
-        DP_CUDA(cudaMalloc((void **)&m->d_oze_emb, sizeof(int) * eper * nnet));
+        DP_CUDA(cudaMalloc(&m->d_ozw_emb, sizeof(__half) * O::WNET * nnet));
+        DP_CUDA(cudaMalloc((void **)&m->d_oze_emb, sizeof(int) * O::ENET * nnet));
         m->oz_emb_stale = true;
     }
     if (!m->oz_emb_stale) return DP_OK;
-    __half *wf = (__half *)m->d_ozw_emb, *wb = wf + per * nnet;
-    int *ef = m->d_oze_emb, *eb = ef + (size_t)O::NN * O::NC * nnet;
+    constexpr int S = O::S, B = O::BETA, NC = O::NC, KC = O::KC;
     for (int net = 0; net < nnet; ++net) {
-        // rows of W2^T (output channel m, input k) from the transposed parameter copy, for z3 = x2 W2
-        const double *W2T = md.pT + md.emb_base + (int64_t)net * md.emb.size + md.emb.W[2];
-        DP_TRY((oz_split<O::S, O::BETA>(W2T, O::E1, O::E2, (int64_t)O::NN * O::NC, O::E1, O::KP, O::NC, O::KC,
-                                        wf + per * net, ef + (size_t)O::NN * O::NC * net, st)));
-        // rows of W2 (input k, output channel m), for dE/dx2 = dz3 W2^T
-        const double *W2 = md.p + md.emb_base + (int64_t)net * md.emb.size + md.emb.W[2];
-        DP_TRY((oz_split<O::S, O::BETA>(W2, O::E2, O::E1, (int64_t)O::NC, O::E2, O::KP2, O::NC, O::KC,
-                                        wb + per2 * net, eb + (size_t)O::NC * net, st)));
+        __half *w = (__half *)m->d_ozw_emb + net * O::WNET;
+        int *e = m->d_oze_emb + (size_t)net * O::ENET;
+        const int64_t base = md.emb_base + (int64_t)net * md.emb.size;
+        // rows of W1^T (channel o, input k) and of W2^T from the transposed parameter copy, for
+        // z2 = x1 W1 and z3 = x2 W2; rows of W2 (input k, channel m) and of W1, for the input gradients
+        DP_TRY((oz_split<S, B>(md.pT + base + md.emb.W[1], O::E0, O::E1, NC, O::E0, O::KP1, NC, KC, w, e, st)));
+        DP_TRY((oz_split<S, B>(md.pT + base + md.emb.W[2], O::E1, O::E2, (int64_t)O::NN * NC, O::E1, O::KP, NC, KC,
+                               w + O::WF1, e + NC, st)));
+        DP_TRY((oz_split<S, B>(md.p + base + md.emb.W[2], O::E2, O::E1, NC, O::E2, O::KP2, NC, KC,
+                               w + O::WF1 + O::WF2, e + NC + O::NN * NC, st)));
+        DP_TRY((oz_split<S, B>(md.p + base + md.emb.W[1], O::E1, O::E0, NC, O::E1, O::KP, NC, KC,
+                               w + O::WF1 + O::WF2 + O::WB2, e + 2 * NC + O::NN * NC, st)));
     }
     m->oz_emb_stale = false;
+    return DP_OK;
+}
+
+template <class Sh, class Epi>
+dp_status run_gemm(dp_model *m, int64_t tiles, const int *ntiles, int nn, int K, const __half *dA, const Epi &epi,
+                   cudaStream_t st)
+{
+    int nsm = 0;
+    DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
+    auto kern = oz::k_gemm<Sh, Epi, 256>;
+    DP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM));
+    const int64_t units = tiles * nn;
+    const unsigned g = (unsigned)(units < nsm ? units : nsm);
+    kern<<<g, 256, Sh::SMEM, st>>>(tiles * 128, ntiles, nn * Sh::NC, K, dA, epi, m->d_err);
+    DP_CUDA(cudaGetLastError());
     return DP_OK;
 }
 
@@ -583,28 +737,24 @@ dp_status fwd(dp_model *m, dp_nlist *nl, const BoxDev &bx, int64_t p0, int64_t n
               char *scratch, cudaStream_t st)
 {
     const ModelDev &md = m->dev;
-    using Sh = typename O::Sh;
-    const int64_t tiles = max_tiles_of(md, nb), rows = tiles * 128;
+    const int64_t tiles = max_tiles_of(md, nb);
     const Bufs b = layout<O>(md, nb, scratch);
     DP_TRY(build_chunks_batch(m, nl, p0, nb, b.chunks, b.firstc, b.ntiles, b.cbs, st));
     int nsm = 0;
     DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
     const Pos4 *pos = (const Pos4 *)nl->d_pos;
+    const __half *w = (const __half *)m->d_ozw_emb;
+    const int *e = m->d_oze_emb;
     {
-        const int64_t g = tiles < 4 * (int64_t)nsm ? tiles : 4 * (int64_t)nsm;
+        const int64_t g = tiles < 8 * (int64_t)nsm ? tiles : 8 * (int64_t)nsm;
         k_ozf_front<O><<<(unsigned)g, 128, 0, st>>>(md, bx, pos, nl->d_nlist, nl->d_nnei, b.chunks, b.ntiles, act,
-                                                    b.dig, b.eA, b.x2buf, b.Rbuf);
+                                                    b.dig1, b.eA1, b.x1buf, b.Rbuf);
         DP_CUDA(cudaGetLastError());
     }
-    {
-        FwdEpi<O> epi{md, b.chunks, (const __half *)m->d_ozw_emb, m->d_oze_emb, b.eA, b.x2buf, b.Rbuf, act, b.Tpart};
-        auto kern = oz::k_gemm<Sh, FwdEpi<O>, 256>;
-        DP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM));
-        const int64_t units = tiles * O::NN;
-        const unsigned g = (unsigned)(units < nsm ? units : nsm);
-        kern<<<g, 256, Sh::SMEM, st>>>(rows, b.ntiles, O::NN * O::NC, O::KP, b.dig, epi, m->d_err);
-        DP_CUDA(cudaGetLastError());
-    }
+    Fwd1Epi<O> e1{md, b.chunks, w, e, b.eA1, b.x1buf, act, b.x2buf, b.dig, b.eA};
+    DP_TRY((run_gemm<typename O::Sh1>(m, tiles, b.ntiles, 1, O::KP1, b.dig1, e1, st)));
+    FwdEpi<O> e2{md, b.chunks, w + O::WF1, e + O::NC, b.eA, b.x2buf, b.Rbuf, act, b.Tpart};
+    DP_TRY((run_gemm<typename O::Sh>(m, tiles, b.ntiles, O::NN, O::KP, b.dig, e2, st)));
     k_ozf_T<O><<<(unsigned)nb, 128, 0, st>>>(md, nl->d_order, p0, nl->d_nnei, b.firstc, b.Tpart, T, D);
     DP_CUDA(cudaGetLastError());
     return DP_OK;
@@ -616,11 +766,12 @@ dp_status bwd(dp_model *m, dp_nlist *nl, const BoxDev &bx, int64_t nb, const dou
               const double *act, double *force, double *atom_virial, char *scratch, cudaStream_t st)
 {
     const ModelDev &md = m->dev;
-    using Sh = typename O::Sh2;
-    const int64_t tiles = max_tiles_of(md, nb), rows = tiles * 128;
+    const int64_t tiles = max_tiles_of(md, nb);
     const Bufs b = layout<O>(md, nb, scratch);
     int nsm = 0;
     DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
+    const __half *w = (const __half *)m->d_ozw_emb;
+    const int *e = m->d_oze_emb;
     k_ozb_dT<O><<<(unsigned)nb, 128, 0, st>>>(md, T, dD, b.dTbuf);
     DP_CUDA(cudaGetLastError());
     {
@@ -629,17 +780,11 @@ dp_status bwd(dp_model *m, dp_nlist *nl, const BoxDev &bx, int64_t nb, const dou
                                                     b.x2buf, b.dRbuf, b.dzbuf);
         DP_CUDA(cudaGetLastError());
     }
-    {
-        const __half *wb = (const __half *)m->d_ozw_emb + (size_t)O::NN * O::NC * O::S * O::KP * md.ntypes * md.ntypes;
-        const int *eb = m->d_oze_emb + (size_t)O::NN * O::NC * md.ntypes * md.ntypes;
-        BwdEpi<O> epi{md, bx, (const Pos4 *)nl->d_pos, nl->d_nlist, nl->d_nnei, b.chunks, wb, eb, b.eA, act,
-                      b.x2buf, b.dRbuf, force, atom_virial};
-        auto kern = oz::k_gemm<Sh, BwdEpi<O>, 256>;
-        DP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM));
-        const unsigned g = (unsigned)(tiles < nsm ? tiles : nsm);
-        kern<<<g, 256, Sh::SMEM, st>>>(rows, b.ntiles, O::NC, O::KP2, b.dig, epi, m->d_err);
-        DP_CUDA(cudaGetLastError());
-    }
+    Bwd3Epi<O> e3{md, b.chunks, w + O::WF1 + O::WF2, e, b.eA, act, b.x2buf, b.dzbuf, b.dig1, b.eA1};
+    DP_TRY((run_gemm<typename O::Sh1>(m, tiles, b.ntiles, 1, O::KP2, b.dig, e3, st)));
+    Bwd4Epi<O> e4{md, bx, (const Pos4 *)nl->d_pos, nl->d_nlist, nl->d_nnei, b.chunks,
+                  w + O::WF1 + O::WF2 + O::WB2, e, b.eA1, act, b.dzbuf, b.dRbuf, force, atom_virial};
+    DP_TRY((run_gemm<typename O::Sh1>(m, tiles, b.ntiles, 1, O::KP, b.dig1, e4, st)));
     return DP_OK;
 }
 

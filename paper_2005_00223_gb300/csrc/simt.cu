@@ -792,6 +792,7 @@ dp_status compute_simt(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
     int64_t B = m->batch_atoms > 0 ? m->batch_atoms : n;
     if (B > n) B = n;
     if (B < 1) B = 1;
+    B = (n + (n + B - 1) / B - 1) / ((n + B - 1) / B);   // equal batches: no small tail batch
     const bool oz = sizeof(Real) == sizeof(double) && oz_fit_ok(md);
     const bool ozemb = sizeof(Real) == sizeof(double) && oz_emb_ok(md);
     if (oz) DP_TRY(oz_refresh_weights(m, st));

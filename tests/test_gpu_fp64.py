@@ -89,6 +89,19 @@ def test_fp64_matches_oracle(dp, orc, name, cfg, coord, typ, box):
     assert rms(ref[2]) > 0
 
 
+@pytest.mark.parametrize("name,cfg,coord,typ,box", systems()[:2], ids=[s[0] for s in systems()[:2]])
+def test_fp64_cuda_core_route_matches_oracle(dp, orc, name, cfg, coord, typ, box):
+    """The all-CUDA-core FP64 kernels (used for net shapes without a split-product route) still agree."""
+    m = _model(dp, cfg)
+    nl = dp.NeighborList(m, coord, typ, box)
+    os.environ["DP_NO_OZAKI"] = "1"
+    try:
+        got = nl.compute(coord, box, "fp64")
+    finally:
+        os.environ.pop("DP_NO_OZAKI", None)
+    assert_close_fp64(got, orc.Model(cfg, m.params).compute(coord, typ, box))
+
+
 def test_fp64_student_shape_and_batches(dp, orc):
     """Student-size nets (8, 16, 32), and the multi-batch path (batch of 97 atoms)."""
     cfg = dpsynth.copper_student_config()
