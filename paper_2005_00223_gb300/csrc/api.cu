@@ -210,6 +210,7 @@ static dp_status upload_params(dp_model *m)
 {
     m->oz_stale = true;
     m->oz_emb_stale = true;
+    m->oz_fit_stale = true;
     const ModelDev &md = m->dev;
     std::vector<double> pT(m->h_params);
     auto transpose_net = [&](int64_t base, const NetLayout &L) {
@@ -428,6 +429,8 @@ void dp_model_destroy(dp_model *m)
     cudaFree(m->d_oze);
     cudaFree(m->d_ozw_emb);
     cudaFree(m->d_oze_emb);
+    cudaFree(m->d_ozw_fit);
+    cudaFree(m->d_oze_fit);
     cudaFree(m->d_tcfit);
     cudaFree(m->d_train);
     cudaFree(m->d_tscr);

@@ -86,6 +86,8 @@ enum ProfGroup {
     PG_DESC,          // descriptor D and dE/dT between the embedding passes
     PG_GRAD,          // parameter-gradient kernels
     PG_OPT,           // optimizer step
+    PG_EMBED_FWD_L2,  // FP64 split-product route: the widest embedding layer (forward, with its epilogue)
+    PG_EMBED_BWD_L2,  // FP64 split-product route: its input gradient (with its epilogue)
     PG_COUNT
 };
 
@@ -148,7 +150,10 @@ struct dp_model {
     void *d_ozw = nullptr;            // fp16 digits of the first fitting layer's weights (FP64 products on the tensor cores)
     int *d_oze = nullptr;             // their row scales
     bool oz_stale = true;             // digits older than the parameters
-    void *d_ozw_emb = nullptr;        // fp16 digits of the widest embedding layer's weights, per net
+    void *d_ozw_fit = nullptr;        // fp16 digits of the other fitting layers' weights, per type
+    int *d_oze_fit = nullptr;         // their row scales
+    bool oz_fit_stale = true;
+    void *d_ozw_emb = nullptr;        // fp16 digits of the hidden embedding layers' weights, per net
     int *d_oze_emb = nullptr;         // their row scales
     bool oz_emb_stale = true;
     uint32_t tc_img_bytes = 0;
@@ -272,6 +277,14 @@ dp_status oz_emb_fwd(dp_model *m, dp_nlist *nl, const BoxDev &bx, int64_t p0, in
 // forces (added) and per-atom virials (added; zeroed by the caller).
 dp_status oz_emb_bwd(dp_model *m, dp_nlist *nl, const BoxDev &bx, int64_t nb, const double *T, const double *dD,
                      const double *act, double *force, double *atom_virial, char *scratch, cudaStream_t st);
+// The fitting net's hidden layers after the first as split products
+// (oz_fit.cu): shape check, weight digits, scratch for `count` atoms, and the
+// chain from z1 to E_i and dz1.
+bool oz_fit_chain_ok(const ModelDev &md);
+dp_status oz_fit_chain_refresh(dp_model *m, cudaStream_t st);
+size_t oz_fit_chain_bytes(const ModelDev &md, int64_t count);
+dp_status oz_fit_chain(dp_model *m, int ti, const int32_t *order, int64_t pos_begin, int64_t count,
+                       const double *z1, double *dz1, double *E_atom, char *scratch, cudaStream_t st);
 // Per-atom scratch of the model: E_i [n] at d_aux, W_i [9n] right after it.
 dp_status ensure_aux(dp_model *m, int64_t n);
 dp_status nlist_create_internal(const dp_model *m, int64_t n, const int32_t *type, const double box[9], double rcut,

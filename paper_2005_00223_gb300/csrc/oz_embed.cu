@@ -739,22 +739,30 @@ dp_status fwd(dp_model *m, dp_nlist *nl, const BoxDev &bx, int64_t p0, int64_t n
     const ModelDev &md = m->dev;
     const int64_t tiles = max_tiles_of(md, nb);
     const Bufs b = layout<O>(md, nb, scratch);
-    DP_TRY(build_chunks_batch(m, nl, p0, nb, b.chunks, b.firstc, b.ntiles, b.cbs, st));
     int nsm = 0;
     DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
     const Pos4 *pos = (const Pos4 *)nl->d_pos;
     const __half *w = (const __half *)m->d_ozw_emb;
     const int *e = m->d_oze_emb;
     {
+        ProfScope ps(m->prof, PG_CHUNKS, 3, st);
+        DP_TRY(build_chunks_batch(m, nl, p0, nb, b.chunks, b.firstc, b.ntiles, b.cbs, st));
+    }
+    {
+        ProfScope ps(m->prof, PG_EMBED_FWD, 2, st);
         const int64_t g = tiles < 8 * (int64_t)nsm ? tiles : 8 * (int64_t)nsm;
         k_ozf_front<O><<<(unsigned)g, 128, 0, st>>>(md, bx, pos, nl->d_nlist, nl->d_nnei, b.chunks, b.ntiles, act,
                                                     b.dig1, b.eA1, b.x1buf, b.Rbuf);
         DP_CUDA(cudaGetLastError());
+        Fwd1Epi<O> e1{md, b.chunks, w, e, b.eA1, b.x1buf, act, b.x2buf, b.dig, b.eA};
+        DP_TRY((run_gemm<typename O::Sh1>(m, tiles, b.ntiles, 1, O::KP1, b.dig1, e1, st)));
     }
-    Fwd1Epi<O> e1{md, b.chunks, w, e, b.eA1, b.x1buf, act, b.x2buf, b.dig, b.eA};
-    DP_TRY((run_gemm<typename O::Sh1>(m, tiles, b.ntiles, 1, O::KP1, b.dig1, e1, st)));
-    FwdEpi<O> e2{md, b.chunks, w + O::WF1, e + O::NC, b.eA, b.x2buf, b.Rbuf, act, b.Tpart};
-    DP_TRY((run_gemm<typename O::Sh>(m, tiles, b.ntiles, O::NN, O::KP, b.dig, e2, st)));
+    {
+        ProfScope ps(m->prof, PG_EMBED_FWD_L2, 1, st);
+        FwdEpi<O> e2{md, b.chunks, w + O::WF1, e + O::NC, b.eA, b.x2buf, b.Rbuf, act, b.Tpart};
+        DP_TRY((run_gemm<typename O::Sh>(m, tiles, b.ntiles, O::NN, O::KP, b.dig, e2, st)));
+    }
+    ProfScope ps(m->prof, PG_DESC, 1, st);
     k_ozf_T<O><<<(unsigned)nb, 128, 0, st>>>(md, nl->d_order, p0, nl->d_nnei, b.firstc, b.Tpart, T, D);
     DP_CUDA(cudaGetLastError());
     return DP_OK;
@@ -772,16 +780,24 @@ dp_status bwd(dp_model *m, dp_nlist *nl, const BoxDev &bx, int64_t nb, const dou
     DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
     const __half *w = (const __half *)m->d_ozw_emb;
     const int *e = m->d_oze_emb;
-    k_ozb_dT<O><<<(unsigned)nb, 128, 0, st>>>(md, T, dD, b.dTbuf);
-    DP_CUDA(cudaGetLastError());
     {
+        ProfScope ps(m->prof, PG_DESC, 1, st);
+        k_ozb_dT<O><<<(unsigned)nb, 128, 0, st>>>(md, T, dD, b.dTbuf);
+        DP_CUDA(cudaGetLastError());
+    }
+    {
+        ProfScope ps(m->prof, PG_EMBED_BWD, 1, st);
         const int64_t g = tiles < 8 * (int64_t)nsm ? tiles : 8 * (int64_t)nsm;
         k_ozb_front<O><<<(unsigned)g, 128, 0, st>>>(md, b.chunks, b.ntiles, act, b.Rbuf, b.dTbuf, b.dig, b.eA,
                                                     b.x2buf, b.dRbuf, b.dzbuf);
         DP_CUDA(cudaGetLastError());
     }
-    Bwd3Epi<O> e3{md, b.chunks, w + O::WF1 + O::WF2, e, b.eA, act, b.x2buf, b.dzbuf, b.dig1, b.eA1};
-    DP_TRY((run_gemm<typename O::Sh1>(m, tiles, b.ntiles, 1, O::KP2, b.dig, e3, st)));
+    {
+        ProfScope ps(m->prof, PG_EMBED_BWD_L2, 1, st);
+        Bwd3Epi<O> e3{md, b.chunks, w + O::WF1 + O::WF2, e, b.eA, act, b.x2buf, b.dzbuf, b.dig1, b.eA1};
+        DP_TRY((run_gemm<typename O::Sh1>(m, tiles, b.ntiles, 1, O::KP2, b.dig, e3, st)));
+    }
+    ProfScope ps(m->prof, PG_EMBED_BWD, 1, st);
     Bwd4Epi<O> e4{md, bx, (const Pos4 *)nl->d_pos, nl->d_nlist, nl->d_nnei, b.chunks,
                   w + O::WF1 + O::WF2 + O::WB2, e, b.eA1, act, b.dzbuf, b.dRbuf, force, atom_virial};
     DP_TRY((run_gemm<typename O::Sh1>(m, tiles, b.ntiles, 1, O::KP, b.dig1, e4, st)));

@@ -72,7 +72,8 @@ using namespace dp;
 
 static const char *kGroupNames[PG_COUNT] = {"nlist_build", "nlist_format", "pack", "embed_fwd", "fitting",
                                              "embed_bwd", "reduce", "md_update", "thermo", "nonfinite_check",
-                                             "tc_worklist", "descriptor", "param_grad", "optimizer"};
+                                             "tc_worklist", "descriptor", "param_grad", "optimizer",
+                                             "embed_fwd_l2", "embed_bwd_l2"};
 
 extern "C" {
 

@@ -657,9 +657,15 @@ dp_status launch_fit(dp_model *m, const int32_t *order, int t, int64_t p0, int64
 // cores (ozaki.cu): digits of W1 (6-bit, rows of W1^T, for z1 = D W1) and of
 // W1^T (7-bit, rows of W1, for dE/dD = dz1 W1^T) per center type.
 constexpr int kOzSF = 9, kOzBF = 6, kOzSB = 8, kOzBB = 7;
-// Below this many atoms of a type the GEMMs cannot fill the GPU (a work unit
-// is 128 atoms) and the SIMT net is faster.
-constexpr int64_t kOzMinAtoms = 1024;
+// Below this many atoms (of a type, for the fitting net; in all, for the
+// embedding net) the split products cannot fill the GPU and the CUDA-core
+// kernels are faster (1024; DP_OZ_MIN_ATOMS overrides it, e.g. for tests of
+// the split route on small systems).
+int64_t oz_min_atoms()
+{
+    const char *v = getenv("DP_OZ_MIN_ATOMS");
+    return v ? atoll(v) : 1024;
+}
 
 bool oz_fit_ok(const ModelDev &md)
 {
@@ -693,13 +699,13 @@ dp_status oz_refresh_weights(dp_model *m, cudaStream_t st)
     return DP_OK;
 }
 
-// Scratch of the first fitting layer for nb atoms (rows padded per type).
+// Scratch of the split-product fitting net for nb atoms (rows padded per type).
 size_t oz_bytes(const ModelDev &md, int64_t nb)
 {
     const int64_t rows = nb + 128 * md.ntypes;
     const int f0 = md.fit.wout[0], nd = md.desc_dim;
     return sizeof(__half) * rows * (size_t)(kOzSF * nd + kOzSB * f0) + sizeof(int) * rows * 2 +
-           sizeof(double) * rows * 2 * f0 + 6 * 256;
+           sizeof(double) * rows * 2 * f0 + 6 * 256 + (oz_fit_chain_ok(md) ? oz_fit_chain_bytes(md, rows) : 0);
 }
 
 dp_status fit_fp64_oz(dp_model *m, dp_nlist *nl, int t, int64_t p0, int64_t b, int64_t count, const double *D,
@@ -720,10 +726,14 @@ dp_status fit_fp64_oz(dp_model *m, dp_nlist *nl, int t, int64_t p0, int64_t b, i
     const __half *wf = (const __half *)m->d_ozw + oz_weight_halves(md) * t, *wb = wf + (size_t)kOzSF * f0 * nd;
     const int *ef = m->d_oze + (size_t)(f0 + nd) * t, *eb2 = ef + f0;
     const double *b1 = md.p + md.fit_base + (int64_t)t * md.fit.size + md.fit.b[0];
-    ProfScope ps(m->prof, PG_FIT, 5, st);
+    const bool chain = oz_fit_chain_ok(md);
+    ProfScope ps(m->prof, PG_FIT, chain ? 13 : 5, st);
     DP_TRY((oz_split<kOzSF, kOzBF>(D + (b - p0) * nd, nd, count, rows_pad, nd, nd, 128, 16, da, ea, st)));
     DP_TRY((oz_gemm<kOzSF, kOzBF, 48, 16>(m, count, f0, nd, da, ea, rows_pad, wf, ef, b1, z1, f0, st)));
-    DP_TRY((launch_fit_oz<double, true>(m, nl->d_order, t, p0, b, count, D, dD, E_atom, z1, dz1, st)));
+    if (chain)   // the hidden layers after the first as split products too
+        DP_TRY(oz_fit_chain(m, t, nl->d_order, b, count, z1, dz1, E_atom, scratch, st));
+    else
+        DP_TRY((launch_fit_oz<double, true>(m, nl->d_order, t, p0, b, count, D, dD, E_atom, z1, dz1, st)));
     DP_TRY((oz_split<kOzSB, kOzBB>(dz1, f0, count, rows_pad, f0, f0, 128, 16, db, eb, st)));
     return oz_gemm<kOzSB, kOzBB, 64, 16>(m, count, nd, f0, db, eb, rows_pad, wb, eb2, nullptr, dD + (b - p0) * nd, nd,
                                         st);
@@ -740,7 +750,6 @@ dp_status launch_batch(dp_model *m, dp_nlist *nl, BoxDev bx, int64_t p0, int64_t
     DP_CUDA(cudaFuncSetAttribute(k_embed_bwd<S, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
     const Pos4 *pos = (const Pos4 *)nl->d_pos;
     if (ozemb_scratch) {
-        ProfScope ps(m->prof, PG_EMBED_FWD, 4, st);
         DP_TRY(oz_emb_fwd(m, nl, bx, p0, nb, (double *)T, (double *)D, (double *)act, ozemb_scratch, st));
     } else {
         ProfScope ps(m->prof, PG_EMBED_FWD, 1, st);
@@ -753,13 +762,12 @@ dp_status launch_batch(dp_model *m, dp_nlist *nl, BoxDev bx, int64_t p0, int64_t
         int64_t e = nl->type_off[t] + nl->type_count[t];
         if (e > p0 + nb) e = p0 + nb;
         if (e <= b) continue;
-        if (oz_scratch && e - b >= kOzMinAtoms)
+        if (oz_scratch && e - b >= oz_min_atoms())
             DP_TRY(fit_fp64_oz(m, nl, t, p0, b, e - b, (const double *)D, (double *)dD, E_atom, oz_scratch, st));
         else
             DP_TRY(launch_fit<Real>(m, nl->d_order, t, p0, b, e - b, D, dD, E_atom, st));
     }
     if (ozemb_scratch) {
-        ProfScope ps(m->prof, PG_EMBED_BWD, 3, st);
         DP_TRY(oz_emb_bwd(m, nl, bx, nb, (const double *)T, (const double *)dD, (const double *)act, force,
                           atom_virial, ozemb_scratch, st));
     } else {
@@ -794,8 +802,11 @@ dp_status compute_simt(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
     if (B < 1) B = 1;
     B = (n + (n + B - 1) / B - 1) / ((n + B - 1) / B);   // equal batches: no small tail batch
     const bool oz = sizeof(Real) == sizeof(double) && oz_fit_ok(md);
-    const bool ozemb = sizeof(Real) == sizeof(double) && oz_emb_ok(md);
+    // the split-product embedding pays off once the tiles fill the GPU; small systems keep the
+    // one-CTA-per-atom kernels
+    const bool ozemb = sizeof(Real) == sizeof(double) && oz_emb_ok(md) && n >= oz_min_atoms();
     if (oz) DP_TRY(oz_refresh_weights(m, st));
+    if (oz && oz_fit_chain_ok(md)) DP_TRY(oz_fit_chain_refresh(m, st));
     if (ozemb) DP_TRY(oz_emb_refresh(m, st));
     DP_TRY(ensure_workspace(m, per_atom * (size_t)B + 256 * 5 + (oz ? oz_bytes(md, B) : 0) +
                                    (ozemb ? oz_emb_bytes(md, B) : 0)));
@@ -843,9 +854,10 @@ bool embed_shape_supported(int n_embed, const int *e)
 size_t fp64_bytes_per_atom(const ModelDev &md)
 {
     // plus the first fitting layer's digits and pre-activations on the tensor-core route
-    const size_t oz = oz_fit_ok(md) ? sizeof(__half) * (size_t)(kOzSF * md.desc_dim + kOzSB * md.fit.wout[0]) +
-                                          2 * sizeof(int) + 2 * sizeof(double) * md.fit.wout[0]
-                                    : 0;
+    size_t oz = oz_fit_ok(md) ? sizeof(__half) * (size_t)(kOzSF * md.desc_dim + kOzSB * md.fit.wout[0]) +
+                                    2 * sizeof(int) + 2 * sizeof(double) * md.fit.wout[0]
+                              : 0;
+    if (oz && oz_fit_chain_ok(md)) oz += (oz_fit_chain_bytes(md, 2048) - oz_fit_chain_bytes(md, 1024)) / 1024 + 1;
     // and the split-product embedding's buffers (affine in the batch size)
     const size_t ozemb = oz_emb_ok(md) ? (oz_emb_bytes(md, 2048) - oz_emb_bytes(md, 1024)) / 1024 + 1 : 0;
     return bytes_per_atom<double>(md) + oz + ozemb;

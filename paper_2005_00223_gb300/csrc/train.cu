@@ -247,6 +247,7 @@ dp_status dp_adam_step(dp_model *m, const double *d_grad, double lr, double beta
     m->params_dirty = true;
     m->oz_stale = true;
     m->oz_emb_stale = true;
+    m->oz_fit_stale = true;
     return DP_OK;
 }
 

@@ -79,11 +79,18 @@ def test_nlist_exact_ties_and_cutoff(dp, orc):
     np.testing.assert_array_equal(got, ref)
 
 
+@pytest.mark.parametrize("route", ["auto", "split"])
 @pytest.mark.parametrize("name,cfg,coord,typ,box", systems(), ids=[s[0] for s in systems()])
-def test_fp64_matches_oracle(dp, orc, name, cfg, coord, typ, box):
+def test_fp64_matches_oracle(dp, orc, name, cfg, coord, typ, box, route):
+    """route split: the tensor-core split products forced on (they are used from 1,024 atoms on)."""
     m = _model(dp, cfg)
     nl = dp.NeighborList(m, coord, typ, box)
-    got = nl.compute(coord, box, "fp64")
+    if route == "split":
+        os.environ["DP_OZ_MIN_ATOMS"] = "0"
+    try:
+        got = nl.compute(coord, box, "fp64")
+    finally:
+        os.environ.pop("DP_OZ_MIN_ATOMS", None)
     ref = orc.Model(cfg, m.params).compute(coord, typ, box)
     assert_close_fp64(got, ref)
     assert rms(ref[2]) > 0
@@ -103,18 +110,23 @@ def test_fp64_cuda_core_route_matches_oracle(dp, orc, name, cfg, coord, typ, box
 
 
 def test_fp64_student_shape_and_batches(dp, orc):
-    """Student-size nets (8, 16, 32), and the multi-batch path (batch of 97 atoms)."""
+    """Student-size nets (8, 16, 32), and the multi-batch path (batch of 97 atoms), on both routes."""
     cfg = dpsynth.copper_student_config()
     coord, typ, box = dpsynth.copper_fcc(2, ncell=5)
     ref = None
-    for batch in ("0", "97"):
+    for batch, route in (("0", "auto"), ("97", "auto"), ("0", "split"), ("97", "split")):
         os.environ["DP_BATCH_ATOMS"] = batch
         try:
             m = _model(dp, cfg, seed=3)
         finally:
             os.environ.pop("DP_BATCH_ATOMS", None)
         nl = dp.NeighborList(m, coord, typ, box, skin=1.0)
-        got = nl.compute(coord, box, "fp64")
+        if route == "split":
+            os.environ["DP_OZ_MIN_ATOMS"] = "0"
+        try:
+            got = nl.compute(coord, box, "fp64")
+        finally:
+            os.environ.pop("DP_OZ_MIN_ATOMS", None)
         if ref is None:
             ref = orc.Model(cfg, m.params).compute(coord, typ, box)
         assert_close_fp64(got, ref)

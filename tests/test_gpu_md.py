@@ -27,15 +27,22 @@ def _scaled_water_model(seed):
     return cfg, p
 
 
-@pytest.mark.parametrize("skin", [2.0, 0.05])
-def test_nve_matches_oracle(dp, orc, skin):
+@pytest.mark.parametrize("skin,route", [(2.0, "auto"), (0.05, "auto"), (2.0, "split")])
+def test_nve_matches_oracle(dp, orc, skin, route):
+    """route split: the FP64 tensor-core split products forced on for this 192-atom box."""
+    import os
     cfg, p = _scaled_water_model(5)
     coord, typ, box = dpsynth.water_box(5)
     mass = np.array([dpsynth.MASS["O"], dpsynth.MASS["H"]])
     vel = dpsynth.velocities(mass[typ], 600.0, 5)
     m = dp.Model(cfg, 0, params=p)
     st = dp.MDState(m, coord, vel, typ, mass, box, skin=skin)
-    th = st.step(20, 0.5, "fp64", thermo_every=5)
+    if route == "split":
+        os.environ["DP_OZ_MIN_ATOMS"] = "0"
+    try:
+        th = st.step(20, 0.5, "fp64", thermo_every=5)
+    finally:
+        os.environ.pop("DP_OZ_MIN_ATOMS", None)
     x, v, step, nreb = st.get()
     xr, vr, thr = orc.Model(cfg, p).md_nve(coord, vel, typ, mass, box, nsteps=20, dt=0.5, thermo_every=5)
     assert step == 20
