@@ -56,7 +56,7 @@ struct OzEmb {
     static constexpr int ACT = E0 + E1 + E2 + E2;    // stored per neighbor: t of each layer, then G
     static constexpr int EPI = 26624;                // GEMM 2 epilogue: G [8][8][33] and R [8][4][33] doubles
     static constexpr int EPIX = 3072;                // the other epilogues: [4][2][32] doubles
-    using Sh = oz::Shape<S, BETA, NC, KC, EPI>;      // GEMM 2
+    using Sh = oz::Shape<S, BETA, NC, KC, EPI, 3>;   // GEMM 2 (3 stages: L1 keeps the tanh table)
     using Sh1 = oz::Shape<S, BETA, NC, KC, EPIX>;    // GEMM 1, 3, 4
     // digits of the weights per net (halves): W1^T (GEMM 1), W2^T (GEMM 2), W2 (GEMM 3), W1 (GEMM 4)
     static constexpr int64_t WF1 = (int64_t)NC * S * KP1, WF2 = (int64_t)NN * NC * S * KP, WB2 = (int64_t)NC * S * KP2,
@@ -177,22 +177,30 @@ struct Fwd1Epi {
     __half *dig2;
     int *eA2;
     __device__ const __half *b_unit(int64_t tile, int) const { return wdig + chunks[tile * 4].w * O::WNET; }
-    template <int HF>
-    __device__ __forceinline__ void body(int64_t tile, uint32_t trow, int rt, int lane, int quarter,
-                                         const int4 &c4, unsigned char *esm) const
+    // Column groups k0 = 8 half + 16 i: values first (t2, x2 stored; the row maximum kept), then,
+    // with the maximum of both warps of the quarter, the digits of x2 read back from x2buf.
+    __device__ void operator()(int64_t tile, int, uint32_t trow, int tid, unsigned char *esm) const
     {
-        constexpr int E0 = O::E0, E1 = O::E1, NG = (O::KP / 8 - HF + 1) / 2;   // this half's column groups
-        const int net = c4.w, tj = net % md.ntypes;
+        constexpr int E0 = O::E0, E1 = O::E1;
+        const int warp = tid >> 5, lane = tid & 31, quarter = warp & 3, half = warp >> 2;
+        const int4 c4 = chunks[tile * 4 + quarter];
+        const int rt = quarter * 32 + lane;
         const int64_t row = tile * 128 + rt;
+        double *x2t = x2buf + tile * E1 * 128 + rt;   // x2 of this row, channel stride 128
+        if (c4.x < 0) {   // a padding chunk: zero digits
+            const double z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int k0 = 8 * half; k0 < O::KP; k0 += 16) put_digits8<O, O::KP>(dig2, row, k0, z, 0);
+            if (half == 0) eA2[row] = 0;
+            return;
+        }
+        const int net = c4.w, tj = net % md.ntypes;
         const int er = eA1[row];
         const double *b1 = md.p + md.emb_base + (int64_t)net * md.emb.size + md.emb.b[1];
         const int *eB = weB + (int64_t)net * O::ENET;
         double *ca = act + ((int64_t)c4.y * md.chunks_per_atom + md.chunk_off[tj] + c4.z / 32) * (O::ACT * 32);
-        double xv[NG][8];
         double mx = 0.0;
-#pragma unroll
-        for (int gi = 0; gi < NG; ++gi) {
-            const int k0 = 8 * HF + 16 * gi;
+#pragma unroll 1
+        for (int k0 = 8 * half; k0 < O::KP; k0 += 16) {
             double xs[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
@@ -205,36 +213,25 @@ struct Fwd1Epi {
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int o = k0 + c;
-                xv[gi][c] = 0.0;
                 if (o < E1) {
                     const double t2 = tanh_f64(oz::acc_value<Sh>(H[c], L[c], er + eB[o]) + b1[o]);
                     const double x2 = xs[c] + t2;
                     ca[(E0 + o) * 32 + lane] = t2;
-                    x2buf[(tile * E1 + o) * 128 + rt] = x2;
-                    xv[gi][c] = x2;
+                    x2t[o * 128] = x2;
                     mx = fmax(mx, fabs(x2));
                 }
             }
         }
-        mx = pair_max(mx, esm, quarter, HF, lane);
+        mx = pair_max(mx, esm, quarter, half, lane);
         const int e = oz::row_exp(mx);
-        if (HF == 0) eA2[row] = e;
+        if (half == 0) eA2[row] = e;
+#pragma unroll 1
+        for (int k0 = 8 * half; k0 < O::KP; k0 += 16) {
+            double v[8];
 #pragma unroll
-        for (int gi = 0; gi < NG; ++gi) put_digits8<O, O::KP>(dig2, row, 8 * HF + 16 * gi, xv[gi], e);
-    }
-    __device__ void operator()(int64_t tile, int, uint32_t trow, int tid, unsigned char *esm) const
-    {
-        const int warp = tid >> 5, lane = tid & 31, quarter = warp & 3, half = warp >> 2;
-        const int4 c4 = chunks[tile * 4 + quarter];
-        const int rt = quarter * 32 + lane;
-        if (c4.x < 0) {   // a padding chunk: zero digits
-            const double z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int k0 = 8 * half; k0 < O::KP; k0 += 16) put_digits8<O, O::KP>(dig2, tile * 128 + rt, k0, z, 0);
-            if (half == 0) eA2[tile * 128 + rt] = 0;
-            return;
+            for (int c = 0; c < 8; ++c) v[c] = k0 + c < E1 ? x2t[(k0 + c) * 128] : 0.0;
+            put_digits8<O, O::KP>(dig2, row, k0, v, e);
         }
-        if (half == 0) body<0>(tile, trow, rt, lane, quarter, c4, esm);
-        else body<1>(tile, trow, rt, lane, quarter, c4, esm);
     }
 };
 
@@ -453,31 +450,40 @@ struct Bwd3Epi {
     const __half *wdig;   // digits of W2 of net 0; net n at + n WNET
     const int *weB;
     const int *eA;
-    const double *act, *dskip;
-    double *dybuf;
+    const double *act;
+    double *dskip, *dybuf;
     __half *dig1;
     int *eA1;
     __device__ const __half *b_unit(int64_t tile, int) const { return wdig + chunks[tile * 4].w * O::WNET; }
-    template <int HF>
-    __device__ __forceinline__ void body(int64_t tile, uint32_t trow, int rt, int lane, int quarter,
-                                         const int4 &c4, unsigned char *esm) const
+    // Values first (dE/dx2 to dybuf, dz2 in place of the skip part in dskip; the row maximum kept),
+    // then the digits of dz2 read back.
+    __device__ void operator()(int64_t tile, int, uint32_t trow, int tid, unsigned char *esm) const
     {
-        constexpr int E0 = O::E0, E1 = O::E1, NG = (O::KP / 8 - HF + 1) / 2;
-        const int net = c4.w, tj = net % md.ntypes;
+        constexpr int E0 = O::E0, E1 = O::E1;
+        const int warp = tid >> 5, lane = tid & 31, quarter = warp & 3, half = warp >> 2;
+        const int4 c4 = chunks[tile * 4 + quarter];
+        const int rt = quarter * 32 + lane;
         const int64_t row = tile * 128 + rt;
+        if (c4.x < 0) {
+            const double z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int k0 = 8 * half; k0 < O::KP; k0 += 16) put_digits8<O, O::KP>(dig1, row, k0, z, 0);
+            if (half == 0) eA1[row] = 0;
+            return;
+        }
+        const int net = c4.w, tj = net % md.ntypes;
         const int er = eA[row];
         const int *eB = weB + (int64_t)net * O::ENET + O::NC + O::NN * O::NC;
         const double *ca = act + ((int64_t)c4.y * md.chunks_per_atom + md.chunk_off[tj] + c4.z / 32) * (O::ACT * 32);
-        double dzv[NG][8];
+        double *dzt = dskip + tile * E1 * 128 + rt;   // the skip part of dE/dx2 in, dz2 out
+        double *dyt = dybuf + tile * E1 * 128 + rt;
         double mx = 0.0;
-#pragma unroll
-        for (int gi = 0; gi < NG; ++gi) {
-            const int k0 = 8 * HF + 16 * gi;
+#pragma unroll 1
+        for (int k0 = 8 * half; k0 < O::KP; k0 += 16) {
             double ds8[8], t2v[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int k = k0 + c;
-                ds8[c] = k < E1 ? dskip[(tile * E1 + k) * 128 + rt] : 0.0;
+                ds8[c] = k < E1 ? dzt[k * 128] : 0.0;
                 t2v[c] = k < E1 ? ca[(E0 + k) * 32 + lane] : 0.0;
             }
             long long H[8], L[8];
@@ -485,34 +491,25 @@ struct Bwd3Epi {
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int k = k0 + c;
-                dzv[gi][c] = 0.0;
                 if (k < E1) {
                     const double dy = oz::acc_value<Sh>(H[c], L[c], er + eB[k]) + ds8[c];   // dE/dx2[k]
-                    dybuf[(tile * E1 + k) * 128 + rt] = dy;
-                    dzv[gi][c] = dy * (1.0 - t2v[c] * t2v[c]);
-                    mx = fmax(mx, fabs(dzv[gi][c]));
+                    const double dz = dy * (1.0 - t2v[c] * t2v[c]);
+                    dyt[k * 128] = dy;
+                    dzt[k * 128] = dz;
+                    mx = fmax(mx, fabs(dz));
                 }
             }
         }
-        mx = pair_max(mx, esm, quarter, HF, lane);
+        mx = pair_max(mx, esm, quarter, half, lane);
         const int e = oz::row_exp(mx);
-        if (HF == 0) eA1[row] = e;
+        if (half == 0) eA1[row] = e;
+#pragma unroll 1
+        for (int k0 = 8 * half; k0 < O::KP; k0 += 16) {
+            double v[8];
 #pragma unroll
-        for (int gi = 0; gi < NG; ++gi) put_digits8<O, O::KP>(dig1, row, 8 * HF + 16 * gi, dzv[gi], e);
-    }
-    __device__ void operator()(int64_t tile, int, uint32_t trow, int tid, unsigned char *esm) const
-    {
-        const int warp = tid >> 5, lane = tid & 31, quarter = warp & 3, half = warp >> 2;
-        const int4 c4 = chunks[tile * 4 + quarter];
-        const int rt = quarter * 32 + lane;
-        if (c4.x < 0) {
-            const double z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int k0 = 8 * half; k0 < O::KP; k0 += 16) put_digits8<O, O::KP>(dig1, tile * 128 + rt, k0, z, 0);
-            if (half == 0) eA1[tile * 128 + rt] = 0;
-            return;
+            for (int c = 0; c < 8; ++c) v[c] = k0 + c < E1 ? dzt[(k0 + c) * 128] : 0.0;
+            put_digits8<O, O::KP>(dig1, row, k0, v, e);
         }
-        if (half == 0) body<0>(tile, trow, rt, lane, quarter, c4, esm);
-        else body<1>(tile, trow, rt, lane, quarter, c4, esm);
     }
 };
 
@@ -533,15 +530,14 @@ struct Bwd4Epi {
     const double *act, *dybuf, *dRbuf;
     double *force, *atom_virial;
     __device__ const __half *b_unit(int64_t tile, int) const { return wdig + chunks[tile * 4].w * O::WNET; }
-    template <int HF>
-    __device__ __forceinline__ double layer0(int64_t tile, uint32_t trow, int rt, int lane, int er, const int *eB,
-                                             const double *ca, const double *W0) const
+    // This warp's part of dE/ds: channel groups j0 = 8 half + 16 i of layer 0.
+    __device__ __forceinline__ double layer0(int64_t tile, uint32_t trow, int half, int rt, int lane, int er,
+                                             const int *eB, const double *ca, const double *W0) const
     {
-        constexpr int E0 = O::E0, E1 = O::E1, NG = (O::KP1 / 8 - HF + 1) / 2;
+        constexpr int E0 = O::E0, E1 = O::E1;
         double ds = 0.0;
-#pragma unroll
-        for (int gi = 0; gi < NG; ++gi) {
-            const int j0 = 8 * HF + 16 * gi;
+#pragma unroll 1
+        for (int j0 = 8 * half; j0 < O::KP1; j0 += 16) {
             double sk[8], t1v[8], w0[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
@@ -582,8 +578,7 @@ struct Bwd4Epi {
         const int *eB = weB + (int64_t)net * O::ENET + 2 * O::NC + O::NN * O::NC;
         const double *ca = act + ((int64_t)c4.y * md.chunks_per_atom + md.chunk_off[tj] + c4.z / 32) * (O::ACT * 32);
         const double *W0 = md.p + md.emb_base + (int64_t)net * md.emb.size + md.emb.W[0];
-        double ds = half == 0 ? layer0<0>(tile, trow, rt, lane, er, eB, ca, W0)
-                              : layer0<1>(tile, trow, rt, lane, er, eB, ca, W0);
+        double ds = layer0(tile, trow, half, rt, lane, er, eB, ca, W0);
         double *sm = reinterpret_cast<double *>(esm + 16);   // [4][32]
         if (half == 1) sm[quarter * 32 + lane] = ds;
         bar_pair(1 + quarter);
@@ -725,6 +720,9 @@ dp_status run_gemm(dp_model *m, int64_t tiles, const int *ntiles, int nn, int K,
     DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
     auto kern = oz::k_gemm<Sh, Epi, 256>;
     DP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM));
+    // the smallest shared-memory carveout that holds the stages: the rest of the SM's 256 KB stays L1
+    DP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)((Sh::SMEM + 2048) * 100 / (228 * 1024)) + 1));
     const int64_t units = tiles * nn;
     const unsigned g = (unsigned)(units < nsm ? units : nsm);
     kern<<<g, 256, Sh::SMEM, st>>>(tiles * 128, ntiles, nn * Sh::NC, K, dA, epi, m->d_err);

@@ -84,15 +84,15 @@ __device__ __forceinline__ uint4 pack8(const int *v)
 // g = 2 .. S+1 at column (g - 2) NC, so the products of A plane i with B
 // planes 1 .. S+1-i land on contiguous columns from (i - 1) NC: one MMA
 // (split at 256 columns) per A plane and K step.  EPI bytes of shared memory
-// after the stages belong to the epilogue.
-template <int S_, int BETA_, int NC_, int KC_, int EPI_ = 0>
+// after the stages belong to the epilogue; at most MAXST stages.
+template <int S_, int BETA_, int NC_, int KC_, int EPI_ = 0, int MAXST_ = 8>
 struct Shape {
     static constexpr int S = S_, BETA = BETA_, NC = NC_, KC = KC_, EPI = EPI_;
     static constexpr uint32_t A_PLANE = 128 * KC * 2, B_PLANE = NC * KC * 2;
     static constexpr uint32_t A_BYTES = S * A_PLANE, B_BYTES = S * B_PLANE;
     static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
     static constexpr int NST0 = (int)((220u * 1024u - (uint32_t)EPI) / STAGE);
-    static constexpr int NST = NST0 < 8 ? NST0 : 8;
+    static constexpr int NST = NST0 < MAXST_ ? NST0 : MAXST_;   // fewer stages leave more L1 to the epilogue
     static constexpr uint32_t SMEM = NST * STAGE + EPI;
     static constexpr uint32_t SBO = (KC / 8) * 128;   // 8-row groups of a K-major tile
     // diagonals 2 .. GH+1 are combined in one int64 (shifts <= 27 bits), the rest in another
