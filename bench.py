@@ -40,6 +40,15 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 FLOP
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FFMA/clk x 2 FLOP x 2070 MHz
 
 
+# DRAM bytes per launch of the dominant kernel from one ncu capture of the same command
+# (dram__bytes_read.sum + dram__bytes_write.sum), and the capture's summary file; valid while the
+# kernel is unchanged since the capture.
+NCU_TRAFFIC = {
+    ("fp64", "cu4000", "embed_fwd_l2"): (2.0806e9 + 1.2659e9, "profiles/fp64_cu4000_nve_step.md"),
+    ("bf16", "cu4000", "embed_bwd"): (28.8e6, "profiles/bf16_cu4000_nve_step.md"),
+}
+
+
 def tensor_peak():
     """Measured sustained dense bf16 TFLOP/s (fp16 runs at the same rate), else the recipe's fallback."""
     try:
@@ -217,6 +226,10 @@ def run_mine(args, rank, world):
             peak, src = tensor_peak()
         roofline = {"bound": bound, "kernel": top, "achieved": round(achieved, 4), "peak": round(peak, 4),
                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None, "peak_source": src}
+        tr = NCU_TRAFFIC.get((args.precision, args.workload, top))
+        if tr is not None and args.model == "full":
+            roofline["traffic"] = tr[0]
+            roofline["traffic_source"] = "ncu, " + tr[1]
         if split_route and args.precision == "fp64":
             roofline["note"] = ("FP64-accurate algorithmic FLOP/s against the FP64 pipe; the multiply-adds of the "
                                 "embedding and first fitting layers run as exact split products on the tensor cores, "
