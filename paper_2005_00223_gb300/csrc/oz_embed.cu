@@ -719,10 +719,14 @@ dp_status run_gemm(dp_model *m, int64_t tiles, const int *ntiles, int nn, int K,
     int nsm = 0;
     DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
     auto kern = oz::k_gemm<Sh, Epi, 256>;
-    DP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM));
-    // the smallest shared-memory carveout that holds the stages: the rest of the SM's 256 KB stays L1
-    DP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)((Sh::SMEM + 2048) * 100 / (228 * 1024)) + 1));
+    static bool attrs_set = false;   // per instantiation: once per process
+    if (!attrs_set) {
+        DP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM));
+        // the smallest shared-memory carveout that holds the stages: the rest of the SM's 256 KB stays L1
+        DP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)((Sh::SMEM + 2048) * 100 / (228 * 1024)) + 1));
+        attrs_set = true;
+    }
     const int64_t units = tiles * nn;
     const unsigned g = (unsigned)(units < nsm ? units : nsm);
     kern<<<g, 256, Sh::SMEM, st>>>(tiles * 128, ntiles, nn * Sh::NC, K, dA, epi, m->d_err);

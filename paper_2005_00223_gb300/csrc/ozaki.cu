@@ -120,10 +120,14 @@ dp_status oz_gemm(const dp_model *m, int64_t M, int N, int K, const __half *dA, 
     const unsigned grid = (unsigned)(units < nsm ? units : nsm);
     PlainEpi<Sh> epi{dB, K / KC, eA, eB, bias, C, ldc, M};
     auto kern = oz::k_gemm<Sh, PlainEpi<Sh>>;
-    DP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM));
-    // the smallest shared-memory carveout that holds the stages: the rest of the SM's 256 KB stays L1
-    DP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)((Sh::SMEM + 2048) * 100 / (228 * 1024)) + 1));
+    static bool attrs_set = false;   // per instantiation: once per process
+    if (!attrs_set) {
+        DP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM));
+        // the smallest shared-memory carveout that holds the stages: the rest of the SM's 256 KB stays L1
+        DP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)((Sh::SMEM + 2048) * 100 / (228 * 1024)) + 1));
+        attrs_set = true;
+    }
     kern<<<grid, 128, Sh::SMEM, st>>>(M_pad, nullptr, N, K, dA, epi, m->d_err);
     DP_CUDA(cudaGetLastError());
     return DP_OK;

@@ -45,10 +45,16 @@ __host__ __device__ inline int64_t tiled(int64_t r, int k, int i, int S, int TR,
 // Row scale e of a row whose largest magnitude is mx (0 for a zero row).
 __device__ __forceinline__ int row_exp(double mx) { return mx > 0.0 ? ilogb(mx) + 3 : 0; }
 
-// 2^e as a double (built from its bits in the normal range).
+// 2^e as a double, built from its bits with integer instructions only (subnormal for
+// -1074 <= e < -1022, 0 below, infinity above 1023): no FP64-pipe work.
 __device__ __forceinline__ double pow2i(int e)
 {
-    return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : scalbn(1.0, e);
+    long long bits;
+    if (e > 1023) bits = 0x7ffLL << 52;
+    else if (e >= -1022) bits = (long long)(e + 1023) << 52;
+    else if (e >= -1074) bits = 1LL << (e + 1074);
+    else bits = 0;
+    return __longlong_as_double(bits);
 }
 
 // The S balanced digits of x for row scale e, most significant first.

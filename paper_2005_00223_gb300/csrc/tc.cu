@@ -708,8 +708,13 @@ __global__ void __launch_bounds__(kCbThreads) k_cb_count(ModelDev md, int64_t n,
 // One block: boff[tj][b] = exclusive scan of bsum[tj][.]; per group (ti, tj)
 // its first entry gbase and the chunk prefix tstart at its first position;
 // the padding entries; the tile count.
-__global__ void __launch_bounds__(kCbThreads) k_cb_plan(ModelDev md, int64_t n, const int64_t *__restrict__ type_off,
-                                                       const int64_t *__restrict__ type_cnt,
+// The type ranges of the positions, passed by value (no host-to-device copy, which from pageable
+// memory would wait for the stream).
+struct TypeTab {
+    int64_t off[kMaxTypes], cnt[kMaxTypes];
+};
+
+__global__ void __launch_bounds__(kCbThreads) k_cb_plan(ModelDev md, int64_t n, TypeTab tt,
                                                        const int *__restrict__ loc, const int *__restrict__ bsum,
                                                        int *__restrict__ boff, int nb, int *__restrict__ gtab,
                                                        int4 *__restrict__ chunks, int *__restrict__ ntiles)
@@ -739,9 +744,9 @@ __global__ void __launch_bounds__(kCbThreads) k_cb_plan(ModelDev md, int64_t n, 
     for (int ti = 0; ti < md.ntypes; ++ti) {
         for (int tj = 0; tj < md.ntypes; ++tj) {
             const int net = ti * md.ntypes + tj;
-            const int s0 = prefix(tj, type_off[ti]);
-            const int s1 = prefix(tj, type_off[ti] + type_cnt[ti]);
-            const int total = type_cnt[ti] > 0 ? s1 - s0 : 0;
+            const int s0 = prefix(tj, tt.off[ti]);
+            const int s1 = prefix(tj, tt.off[ti] + tt.cnt[ti]);
+            const int total = tt.cnt[ti] > 0 ? s1 - s0 : 0;
             gtab[2 * net] = base;
             gtab[2 * net + 1] = s0;
             for (int q = total; q % 4 != 0; ++q) chunks[base + q] = make_int4(-1, tj, 0, net);
@@ -1358,13 +1363,11 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     int *cb_bsum = (int *)carve(sizeof(int) * (size_t)2 * md.ntypes * nb);
     int *cb_boff = cb_bsum + (size_t)md.ntypes * nb;
     int *cb_gtab = (int *)carve(sizeof(int) * 2 * kMaxTypes * kMaxTypes);
-    int64_t *ttab = (int64_t *)carve(sizeof(int64_t) * 2 * kMaxTypes);
-    int64_t htab[2 * kMaxTypes] = {0};
+    TypeTab tt = {};
     for (int t = 0; t < md.ntypes; ++t) {
-        htab[t] = nl->type_off[t];
-        htab[kMaxTypes + t] = nl->type_count[t];
+        tt.off[t] = nl->type_off[t];
+        tt.cnt[t] = nl->type_count[t];
     }
-    DP_CUDA(cudaMemcpyAsync(ttab, htab, sizeof(htab), cudaMemcpyHostToDevice, st));
     DP_CUDA(cudaMemsetAsync(T, 0, sizeof(float) * 4 * md.m1 * n, st));
     DP_CUDA(cudaMemsetAsync(d_force, 0, sizeof(double) * 3 * n, st));
     DP_CUDA(cudaMemsetAsync(d_atom_virial, 0, sizeof(double) * 9 * n, st));
@@ -1379,7 +1382,7 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     {
         ProfScope ps(m->prof, PG_CHUNKS, 3, st);
         k_cb_count<<<nb, kCbThreads, 0, st>>>(md, n, nl->d_order, nl->d_nnei, cb_loc, cb_bsum, nb);
-        k_cb_plan<<<1, kCbThreads, 0, st>>>(md, n, ttab, ttab + kMaxTypes, cb_loc, cb_bsum, cb_boff, nb, cb_gtab,
+        k_cb_plan<<<1, kCbThreads, 0, st>>>(md, n, tt, cb_loc, cb_bsum, cb_boff, nb, cb_gtab,
                                             chunks, cnt);
         k_cb_write<<<nb, kCbThreads, 0, st>>>(md, n, nl->d_order, nl->d_type, nl->d_nnei, cb_loc, cb_boff, nb,
                                               cb_gtab, chunks, nullptr);
@@ -1448,19 +1451,17 @@ dp_status build_chunks_batch(dp_model *m, dp_nlist *nl, int64_t p0, int64_t nb, 
     int *bsum = (int *)carve(sizeof(int) * (size_t)2 * md.ntypes * blocks);
     int *boff = bsum + (size_t)md.ntypes * blocks;
     int *gtab = (int *)carve(sizeof(int) * 2 * kMaxTypes * kMaxTypes);
-    int64_t *ttab = (int64_t *)carve(sizeof(int64_t) * 2 * kMaxTypes);
-    int64_t htab[2 * kMaxTypes] = {0};
+    TypeTab tt = {};
     for (int t = 0; t < md.ntypes; ++t) {
         int64_t b = nl->type_off[t] - p0, e = nl->type_off[t] + nl->type_count[t] - p0;
         b = b < 0 ? 0 : (b > nb ? nb : b);
         e = e < 0 ? 0 : (e > nb ? nb : e);
-        htab[t] = b;
-        htab[kMaxTypes + t] = e - b;
+        tt.off[t] = b;
+        tt.cnt[t] = e - b;
     }
-    DP_CUDA(cudaMemcpyAsync(ttab, htab, sizeof(htab), cudaMemcpyHostToDevice, st));
     const int32_t *order = nl->d_order + p0;
     k_cb_count<<<blocks, kCbThreads, 0, st>>>(md, nb, order, nl->d_nnei, loc, bsum, blocks);
-    k_cb_plan<<<1, kCbThreads, 0, st>>>(md, nb, ttab, ttab + kMaxTypes, loc, bsum, boff, blocks, gtab, chunks,
+    k_cb_plan<<<1, kCbThreads, 0, st>>>(md, nb, tt, loc, bsum, boff, blocks, gtab, chunks,
                                         ntiles);
     k_cb_write<<<blocks, kCbThreads, 0, st>>>(md, nb, order, nl->d_type, nl->d_nnei, loc, boff, blocks, gtab, chunks,
                                               firstc);

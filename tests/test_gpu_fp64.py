@@ -109,6 +109,23 @@ def test_fp64_cuda_core_route_matches_oracle(dp, orc, name, cfg, coord, typ, box
     assert_close_fp64(got, orc.Model(cfg, m.params).compute(coord, typ, box))
 
 
+@pytest.mark.parametrize("route", ["cuda_cores", "split"])
+def test_fp64_paper_net_shape(dp, orc, route):
+    """The nets of the paper's production models (embedding 32-64-128, Sec. 5.1) on two neighbor types."""
+    cfg = dpsynth.ModelConfig(ntypes=2, rcut=6.0, rcut_smth=0.5, sel=(46, 92), embed=(32, 64, 128), m2=16,
+                              fit=(240, 240, 240))
+    coord, typ, box = dpsynth.water_box(2)
+    m = _model(dp, cfg, seed=4)
+    nl = dp.NeighborList(m, coord, typ, box)
+    os.environ["DP_OZ_MIN_ATOMS" if route == "split" else "DP_NO_OZAKI"] = "0" if route == "split" else "1"
+    try:
+        got = nl.compute(coord, box, "fp64")
+    finally:
+        os.environ.pop("DP_OZ_MIN_ATOMS", None)
+        os.environ.pop("DP_NO_OZAKI", None)
+    assert_close_fp64(got, orc.Model(cfg, m.params).compute(coord, typ, box))
+
+
 def test_fp64_student_shape_and_batches(dp, orc):
     """Student-size nets (8, 16, 32), and the multi-batch path (batch of 97 atoms), on both routes."""
     cfg = dpsynth.copper_student_config()
