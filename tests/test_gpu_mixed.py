@@ -130,10 +130,11 @@ def test_mix16_copper_108k_sampled(dp, orc, prec, u):
     force per atom, three times the 10u RMSE budget)."""
     cfg = dpsynth.copper_config()
     coord, typ, box = dpsynth.copper_fcc(1, ncell=30)
-    m = dp.Model(cfg, 1)
+    p = dpsynth.model_params(cfg, 1)
+    m = dp.Model(cfg, 0, params=p)
     nl = dp.NeighborList(m, coord, typ, box, skin=2.0)
     E, Ei, F, W = nl.compute(coord, box, prec)
-    om = orc.Model(cfg, m.params)
+    om = orc.Model(cfg, p)
     nref, _, _ = om.nlist(coord, typ, box)
     np.testing.assert_array_equal(nl.get()[0], nref)
     fs = rms(F)
