@@ -66,6 +66,8 @@ struct OzEmb {
     static_assert(E1 <= NC && E0 <= NC, "one unit of 64 channels for GEMM 1, 3 and 4");
     static_assert((long long)S * KP2 * (1LL << (2 * BETA - 2)) <= (1LL << 24), "exact FP32 digit sums");
     static_assert((long long)S * KP * (1LL << (2 * BETA - 2)) <= (1LL << 24), "exact FP32 digit sums");
+    // every accumulator below 2^22 in magnitude: read back without conversions
+    static constexpr bool SMALL = (long long)S * (KP2 > KP ? KP2 : KP) * (1LL << (2 * BETA - 2)) <= (1LL << 22);
 };
 
 // Digits of 8 consecutive columns k0 .. k0+7 of a row for row scale e (one 16-byte store per plane).
@@ -209,7 +211,7 @@ struct Fwd1Epi {
                 if (o < E1 && (E1 == E0 || E1 == 2 * E0)) xs[c] = x1buf[(tile * E0 + o % E0) * 128 + rt];
             }
             long long H[8], L[8];
-            oz::acc_load8<Sh>(trow, k0, H, L);
+            oz::acc_load8<Sh, O::SMALL>(trow, k0, H, L);
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int o = k0 + c;
@@ -285,7 +287,7 @@ struct FwdEpi {
                 }
             }
             long long H[8], L[8];
-            oz::acc_load8<Sh>(trow, c0, H, L);
+            oz::acc_load8<Sh, O::SMALL>(trow, c0, H, L);
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int m = m0 + c;
@@ -487,7 +489,7 @@ struct Bwd3Epi {
                 t2v[c] = k < E1 ? ca[(E0 + k) * 32 + lane] : 0.0;
             }
             long long H[8], L[8];
-            oz::acc_load8<Sh>(trow, k0, H, L);
+            oz::acc_load8<Sh, O::SMALL>(trow, k0, H, L);
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int k = k0 + c;
@@ -552,7 +554,7 @@ struct Bwd4Epi {
                 }
             }
             long long H[8], L[8];
-            oz::acc_load8<Sh>(trow, j0, H, L);
+            oz::acc_load8<Sh, O::SMALL>(trow, j0, H, L);
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int j = j0 + c;

@@ -149,8 +149,19 @@ __device__ __forceinline__ void acc_load16(uint32_t trow, int c0, long long (&H)
     }
 }
 
+// The accumulator bits as an integer: F2I in general; with SMALL (every
+// |acc| < 2^22, i.e. S K 2^(2 BETA - 2) <= 2^22) by adding 1.5 2^23, which
+// puts the integer in the low mantissa bits (an FP32 add instead of a
+// conversion).
+template <bool SMALL>
+__device__ __forceinline__ long long acc_int(uint32_t bits)
+{
+    if (SMALL) return (long long)(__float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000);
+    return (long long)__float2int_rn(__uint_as_float(bits));
+}
+
 // The same for 8 columns, the loads of all diagonals issued before one wait.
-template <class Sh>
+template <class Sh, bool SMALL = false>
 __device__ __forceinline__ void acc_load8(uint32_t trow, int c0, long long (&H)[8], long long (&L)[8])
 {
     uint32_t v[Sh::S][8];
@@ -163,7 +174,7 @@ __device__ __forceinline__ void acc_load8(uint32_t trow, int c0, long long (&H)[
     for (int g = 2; g <= Sh::S + 1; ++g)
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            const long long iv = (long long)__float2int_rn(__uint_as_float(v[g - 2][c]));
+            const long long iv = acc_int<SMALL>(v[g - 2][c]);
             if (g <= Sh::GH + 1)
                 H[c] += iv << (Sh::BETA * (Sh::GH + 1 - g));
             else
@@ -171,11 +182,30 @@ __device__ __forceinline__ void acc_load8(uint32_t trow, int c0, long long (&H)[
         }
 }
 
+static __device__ __noinline__ double i2d_scaled_slow(long long v, int a) { return scalbn((double)v, a); }
+
+// v 2^a as a double, exactly, for |v| < 2^53, built with integer instructions
+// only (the FP64 pipe is the scarce unit); results outside the normal range
+// take a library path.
+__device__ __forceinline__ double i2d_scaled(long long v, int a)
+{
+    if (v == 0) return 0.0;
+    const unsigned long long sign = v < 0 ? (1ULL << 63) : 0ULL;
+    const unsigned long long u = v < 0 ? 0ULL - (unsigned long long)v : (unsigned long long)v;
+    const int lz = __clzll((long long)u);
+    const int be = 63 - lz + a + 1023;                       // biased exponent of u 2^a
+    if (be <= 0 || be >= 2047) return i2d_scaled_slow(v, a);
+    const unsigned long long mant = ((u << lz) << 1) >> 12;  // the 52 bits after the leading one
+    return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | mant));
+}
+
+// The read-back value: H 2^(E - BETA (GH+1)) + L 2^(E - BETA (S+1)); both
+// terms are exact doubles, so the one FP64 add is the only rounding (as for
+// a fused multiply-add of the two).
 template <class Sh>
 __device__ __forceinline__ double acc_value(long long H, long long L, int E)
 {
-    const double lo = (double)L * pow2i(E - Sh::BETA * (Sh::S + 1));
-    return fma((double)H, pow2i(E - Sh::BETA * (Sh::GH + 1)), lo);
+    return i2d_scaled(H, E - Sh::BETA * (Sh::GH + 1)) + i2d_scaled(L, E - Sh::BETA * (Sh::S + 1));
 }
 
 // C-unit pipeline.  Units u = tile * nn + nchunk (tile of 128 rows of A,
