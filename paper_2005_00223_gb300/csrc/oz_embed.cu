@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(128) k_ozf_front(ModelDev md, BoxDev bx, const
                 x1[o] = ((E0 == 1 || E0 == 2) ? R[0] : 0.0) + t1;
                 if (ca) ca[o * 32 + lane] = t1;
                 x1buf[((int64_t)t * E0 + o) * 128 + tid] = x1[o];
-                mx = fmax(mx, fabs(x1[o]));
+                mx = oz::amax(mx, x1[o]);
             }
         }
         const int e = oz::row_exp(mx);
@@ -220,7 +220,7 @@ struct Fwd1Epi {
                     const double x2 = xs[c] + t2;
                     ca[(E0 + o) * 32 + lane] = t2;
                     x2t[o * 128] = x2;
-                    mx = fmax(mx, fabs(x2));
+                    mx = oz::amax(mx, x2);
                 }
             }
         }
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(128) k_ozb_front(ModelDev md, const int4 *__re
                 const double t3 = ca[(E0 + E1 + m) * 32 + lane];
                 const double dz = dg * (1.0 - t3 * t3);
                 sdz[m * 128 + tid] = dz;
-                mx = fmax(mx, fabs(dz));
+                mx = oz::amax(mx, dz);
                 if (E2 == E1) sdk[m * 128 + tid] = dg;
                 else if (E2 == 2 * E1) {
                     if (m < E1) sdk[m * 128 + tid] = dg;
@@ -498,7 +498,7 @@ struct Bwd3Epi {
                     const double dz = dy * (1.0 - t2v[c] * t2v[c]);
                     dyt[k * 128] = dy;
                     dzt[k * 128] = dz;
-                    mx = fmax(mx, fabs(dz));
+                    mx = oz::amax(mx, dz);
                 }
             }
         }

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) k_fit_stage(int stage, ModelDev md, int t
             const double t = T1[q];
             dz1[q] = dy * (1.0 - t * t);
         }
-        mx = fmax(mx, fabs(v[j]));
+        mx = oz::amax(mx, v[j]);
     }
     if (stage == 2) {
         // E_i = x3 . w_out + b_out

@@ -32,7 +32,7 @@ __global__ void k_oz_split(const double *__restrict__ X, int64_t ldx, int64_t ro
     const double *x = X + r * ldx;
     double mx = 0.0;
     if (live)
-        for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(x[k]));
+        for (int k = lane; k < K; k += 32) mx = oz::amax(mx, x[k]);
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const int e = oz::row_exp(mx);
     if (lane == 0) ex[r] = e;

@@ -57,18 +57,38 @@ __device__ __forceinline__ double pow2i(int e)
     return __longlong_as_double(bits);
 }
 
-// The S balanced digits of x for row scale e, most significant first.
+// The S balanced digits of x for row scale e, most significant first.  The
+// scaled significand m = round(x 2^(BETA S - e)) (ties away from zero) is
+// formed from the bits of x with integer instructions: x = mant 2^(ex - 1075)
+// and |x| < 2^(e-2) give a shift of at most BETA S - 55 bits to the left.
 template <int S, int BETA>
 __device__ __forceinline__ void digits(double x, int e, int (&d)[S])
 {
     constexpr long long H = 1LL << (BETA - 1), MASK = (1LL << BETA) - 1;
-    long long m = llrint(x * pow2i(BETA * S - e));   // |m| <= 2^(BETA S - 2); exact power-of-two scaling
+    const long long bits = __double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    unsigned long long mant = (unsigned long long)bits & ((1ULL << 52) - 1);
+    if (ex) mant |= 1ULL << 52;
+    const int sh = (ex ? ex : 1) - 1075 + BETA * S - e;
+    long long m;
+    if (sh >= 0) m = (long long)(mant << sh);
+    else if (sh > -64) m = (long long)((mant + (1ULL << (-sh - 1))) >> (-sh));
+    else m = 0;
+    if (bits < 0) m = -m;                           // |m| <= 2^(BETA S - 2)
 #pragma unroll
     for (int i = S - 1; i >= 0; --i) {
         const long long v = ((m + H) & MASK) - H;
         m = (m - v) >> BETA;                           // exact: m - v is a multiple of 2^BETA
         d[i] = (int)v;
     }
+}
+
+// max(m, |v|) for m >= 0 by an integer comparison of the bit patterns (monotone for non-negative doubles).
+__device__ __forceinline__ double amax(double m, double v)
+{
+    const unsigned long long a = (unsigned long long)__double_as_longlong(m);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+    return __longlong_as_double((long long)(a > b ? a : b));
 }
 
 // Packs 8 digits (small integers) as 8 fp16 values.
