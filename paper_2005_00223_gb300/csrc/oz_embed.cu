@@ -49,7 +49,9 @@ template <int E0_, int E1_, int E2_>
 struct OzEmb {
     static constexpr int E0 = E0_, E1 = E1_, E2 = E2_;
     static constexpr int S = 8, BETA = 7, NC = 64, KC = 16;
-    static constexpr int KP1 = (E0 + 15) / 16 * 16;  // padded K of z2 = x1 W1
+    static constexpr int KP1 = (E0 + 15) / 16 * 16;  // E0 padded: channel groups of dE/dx1
+    static constexpr int KA1 = (E0 + 16) / 16 * 16;  // padded K of z2 = [x1, 1] [W1; b1] (the bias as a column)
+    static constexpr int KA2 = (E1 + 16) / 16 * 16;  // padded K of z3 = [x2, 1] [W2; b2]
     static constexpr int KP = (E1 + 15) / 16 * 16;   // padded K of z3 = x2 W2 and of dE/dx1 = dz2 W1^T
     static constexpr int KP2 = (E2 + 15) / 16 * 16;  // padded K of dE/dx2 = dz3 W2^T
     static constexpr int NN = (E2 + NC - 1) / NC;    // units of 64 output channels of GEMM 2
@@ -59,7 +61,7 @@ struct OzEmb {
     using Sh = oz::Shape<S, BETA, NC, KC, EPI, 3>;   // GEMM 2 (3 stages: L1 keeps the tanh table)
     using Sh1 = oz::Shape<S, BETA, NC, KC, EPIX>;    // GEMM 1, 3, 4
     // digits of the weights per net (halves): W1^T (GEMM 1), W2^T (GEMM 2), W2 (GEMM 3), W1 (GEMM 4)
-    static constexpr int64_t WF1 = (int64_t)NC * S * KP1, WF2 = (int64_t)NN * NC * S * KP, WB2 = (int64_t)NC * S * KP2,
+    static constexpr int64_t WF1 = (int64_t)NC * S * KA1, WF2 = (int64_t)NN * NC * S * KA2, WB2 = (int64_t)NC * S * KP2,
                              WB1 = (int64_t)NC * S * KP, WNET = WF1 + WF2 + WB2 + WB1;
     static constexpr int ENET = 3 * NC + NN * NC;    // their row scales per net: f1, f2, b2, b1
     static_assert(8 * (8 + 4) * 33 * 8 <= EPI, "epilogue shared memory");
@@ -67,7 +69,10 @@ struct OzEmb {
     static_assert((long long)S * KP2 * (1LL << (2 * BETA - 2)) <= (1LL << 24), "exact FP32 digit sums");
     static_assert((long long)S * KP * (1LL << (2 * BETA - 2)) <= (1LL << 24), "exact FP32 digit sums");
     // every accumulator below 2^22 in magnitude: read back without conversions
-    static constexpr bool SMALL = (long long)S * (KP2 > KP ? KP2 : KP) * (1LL << (2 * BETA - 2)) <= (1LL << 22);
+    static constexpr int KMAX = KP2 > KA2 ? KP2 : KA2;
+    static constexpr bool SMALL = (long long)S * KMAX * (1LL << (2 * BETA - 2)) <= (1LL << 22);
+    // the weights augmented with the bias column, FP64, per net: [W1^T | b1] and [W2^T | b2]
+    static constexpr int64_t AUG = (int64_t)E1 * (E0 + 1) + (int64_t)E2 * (E1 + 1);
 };
 
 // Digits of 8 consecutive columns k0 .. k0+7 of a row for row scale e (one 16-byte store per plane).
@@ -140,11 +145,11 @@ __global__ void __launch_bounds__(128) k_ozf_front(ModelDev md, BoxDev bx, const
                                         (O::ACT * 32)
                             : nullptr;
         // layer 0: the input is the scalar s = R[0]
-        double x1[O::KP1];
-        double mx = 0.0;
+        double x1[O::KA1];
+        double mx = 1.0;   // the constant input of the bias column
 #pragma unroll
-        for (int o = 0; o < O::KP1; ++o) {
-            x1[o] = 0.0;
+        for (int o = 0; o < O::KA1; ++o) {
+            x1[o] = o == E0 ? 1.0 : 0.0;
             if (o < E0) {
                 const double t1 = tanh_f64(sW[E0 + o] + R[0] * sW[o]);
                 x1[o] = ((E0 == 1 || E0 == 2) ? R[0] : 0.0) + t1;
@@ -156,16 +161,17 @@ __global__ void __launch_bounds__(128) k_ozf_front(ModelDev md, BoxDev bx, const
         const int e = oz::row_exp(mx);
         eA1[row] = e;
 #pragma unroll
-        for (int k0 = 0; k0 < O::KP1; k0 += 8) {
+        for (int k0 = 0; k0 < O::KA1; k0 += 8) {
             double v[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) v[c] = x1[k0 + c];
-            put_digits8<O, O::KP1>(dig1, row, k0, v, e);
+            put_digits8<O, O::KA1>(dig1, row, k0, v, e);
         }
     }
 }
 
-// GEMM 1 epilogue: z2 = x1 W1 (+ b1), t2 = tanh(z2) stored, x2 = skip(x1) + t2 stored, the digits of x2.
+// GEMM 1 epilogue: z2 = [x1, 1] [W1; b1], t2 = tanh(z2) stored, x2 = skip(x1) + t2 stored, the digits
+// of [x2, 1].
 template <class O>
 struct Fwd1Epi {
     using Sh = typename O::Sh1;
@@ -191,16 +197,15 @@ struct Fwd1Epi {
         double *x2t = x2buf + tile * E1 * 128 + rt;   // x2 of this row, channel stride 128
         if (c4.x < 0) {   // a padding chunk: zero digits
             const double z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int k0 = 8 * half; k0 < O::KP; k0 += 16) put_digits8<O, O::KP>(dig2, row, k0, z, 0);
+            for (int k0 = 8 * half; k0 < O::KA2; k0 += 16) put_digits8<O, O::KA2>(dig2, row, k0, z, 0);
             if (half == 0) eA2[row] = 0;
             return;
         }
         const int net = c4.w, tj = net % md.ntypes;
         const int er = eA1[row];
-        const double *b1 = md.p + md.emb_base + (int64_t)net * md.emb.size + md.emb.b[1];
         const int *eB = weB + (int64_t)net * O::ENET;
         double *ca = act + ((int64_t)c4.y * md.chunks_per_atom + md.chunk_off[tj] + c4.z / 32) * (O::ACT * 32);
-        double mx = 0.0;
+        double mx = 1.0;   // the constant input of the next product's bias column
 #pragma unroll 1
         for (int k0 = 8 * half; k0 < O::KP; k0 += 16) {
             double xs[8];
@@ -216,7 +221,7 @@ struct Fwd1Epi {
             for (int c = 0; c < 8; ++c) {
                 const int o = k0 + c;
                 if (o < E1) {
-                    const double t2 = tanh_f64(oz::acc_value<Sh>(H[c], L[c], er + eB[o]) + b1[o]);
+                    const double t2 = tanh_f64(oz::acc_value<Sh>(H[c], L[c], er + eB[o]));   // the bias is in the product
                     const double x2 = xs[c] + t2;
                     ca[(E0 + o) * 32 + lane] = t2;
                     x2t[o * 128] = x2;
@@ -228,11 +233,11 @@ struct Fwd1Epi {
         const int e = oz::row_exp(mx);
         if (half == 0) eA2[row] = e;
 #pragma unroll 1
-        for (int k0 = 8 * half; k0 < O::KP; k0 += 16) {
+        for (int k0 = 8 * half; k0 < O::KA2; k0 += 16) {
             double v[8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) v[c] = k0 + c < E1 ? x2t[(k0 + c) * 128] : 0.0;
-            put_digits8<O, O::KP>(dig2, row, k0, v, e);
+            for (int c = 0; c < 8; ++c) v[c] = k0 + c < E1 ? x2t[(k0 + c) * 128] : (k0 + c == E1 ? 1.0 : 0.0);
+            put_digits8<O, O::KA2>(dig2, row, k0, v, e);
         }
     }
 };
@@ -250,7 +255,7 @@ struct FwdEpi {
     __device__ const __half *b_unit(int64_t tile, int nchunk) const
     {
         const int net = chunks[tile * 4].w;
-        return wdig + net * O::WNET + (int64_t)nchunk * (O::KP / O::KC) * O::S * O::NC * O::KC;
+        return wdig + net * O::WNET + (int64_t)nchunk * (O::KA2 / O::KC) * O::S * O::NC * O::KC;
     }
     // 8 warps: the two warps of a row quarter (one chunk) take alternate groups of 8 output channels
     __device__ void operator()(int64_t tile, int nchunk, uint32_t trow, int tid, unsigned char *esm) const
@@ -267,7 +272,6 @@ struct FwdEpi {
 #pragma unroll
         for (int c = 0; c < 4; ++c) sR[c * 33 + lane] = Rbuf[(tile * 4 + c) * 128 + rt];
         const int er = eA[row];
-        const double *b2 = md.p + md.emb_base + (int64_t)net * md.emb.size + md.emb.b[2];
         const int *eB = weB + (int64_t)net * O::ENET;
         double *ca = act + ((int64_t)c4.y * md.chunks_per_atom + md.chunk_off[tj] + c4.z / 32) * (O::ACT * 32);
         double *Tp = Tpart + (tile * 4 + quarter) * 4 * E2;
@@ -293,7 +297,7 @@ struct FwdEpi {
                 const int m = m0 + c;
                 double g = 0.0;
                 if (m < E2) {
-                    const double z = oz::acc_value<Sh>(H[c], L[c], er + eB[m]) + b2[m];
+                    const double z = oz::acc_value<Sh>(H[c], L[c], er + eB[m]);   // the bias is in the product
                     const double t3 = tanh_f64(z);
                     g = xs[c] + t3;
                     ca[(E0 + E1 + m) * 32 + lane] = t3;
@@ -651,7 +655,7 @@ template <class O>
 Bufs layout(const ModelDev &md, int64_t nb, char *base)
 {
     const int64_t tiles = max_tiles_of(md, nb), rows = tiles * 128;
-    const int kmax = O::KP > O::KP2 ? O::KP : O::KP2, kmax1 = O::KP > O::KP1 ? O::KP : O::KP1;
+    const int kmax = O::KA2 > O::KP2 ? O::KA2 : O::KP2, kmax1 = O::KP > O::KA1 ? O::KP : O::KA1;
     Bufs b;
     size_t off = 0;
     auto carve = [&](size_t bytes) {
@@ -684,27 +688,48 @@ size_t scratch_bytes(const ModelDev &md, int64_t nb)
     return layout<O>(md, nb, nullptr).bytes;
 }
 
+// out [rows][cols + 1] = [WT | bias]: a weight matrix (rows = output channels) with its bias as the
+// last column, the B operand of a product whose A rows end in a constant 1.
+__global__ void k_aug_bias(const double *__restrict__ WT, const double *__restrict__ bias, int rows, int cols,
+                           double *__restrict__ out)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= rows * (cols + 1)) return;
+    const int r = q / (cols + 1), c = q - r * (cols + 1);
+    out[q] = c < cols ? WT[(int64_t)r * cols + c] : bias[r];
+}
+
 template <class O>
 dp_status refresh(dp_model *m, cudaStream_t st)
 {
     const ModelDev &md = m->dev;
     const int nnet = md.ntypes * md.ntypes;
     if (!m->d_ozw_emb) {
-        DP_CUDA(cudaMalloc(&m->d_ozw_emb, sizeof(__half) * O::WNET * nnet));
+        // the digits, then (8-byte aligned) the FP64 augmented weights they are split from
+        const size_t dig_bytes = (sizeof(__half) * O::WNET * nnet + 255) & ~(size_t)255;
+        DP_CUDA(cudaMalloc(&m->d_ozw_emb, dig_bytes + sizeof(double) * O::AUG));
         DP_CUDA(cudaMalloc((void **)&m->d_oze_emb, sizeof(int) * O::ENET * nnet));
         m->oz_emb_stale = true;
     }
     if (!m->oz_emb_stale) return DP_OK;
     constexpr int S = O::S, B = O::BETA, NC = O::NC, KC = O::KC;
+    double *aug1 = (double *)((char *)m->d_ozw_emb + ((sizeof(__half) * O::WNET * nnet + 255) & ~(size_t)255));
+    double *aug2 = aug1 + (int64_t)O::E1 * (O::E0 + 1);
     for (int net = 0; net < nnet; ++net) {
         __half *w = (__half *)m->d_ozw_emb + net * O::WNET;
         int *e = m->d_oze_emb + (size_t)net * O::ENET;
         const int64_t base = md.emb_base + (int64_t)net * md.emb.size;
-        // rows of W1^T (channel o, input k) and of W2^T from the transposed parameter copy, for
-        // z2 = x1 W1 and z3 = x2 W2; rows of W2 (input k, channel m) and of W1, for the input gradients
-        DP_TRY((oz_split<S, B>(md.pT + base + md.emb.W[1], O::E0, O::E1, NC, O::E0, O::KP1, NC, KC, w, e, st)));
-        DP_TRY((oz_split<S, B>(md.pT + base + md.emb.W[2], O::E1, O::E2, (int64_t)O::NN * NC, O::E1, O::KP, NC, KC,
-                               w + O::WF1, e + NC, st)));
+        // rows of [W1^T | b1] (channel o: input k, then the bias) and of [W2^T | b2] from the transposed
+        // parameter copy, for z2 = [x1, 1] [W1; b1] and z3 = [x2, 1] [W2; b2]; rows of W2 (input k,
+        // channel m) and of W1, for the input gradients
+        k_aug_bias<<<(O::E1 * (O::E0 + 1) + 255) / 256, 256, 0, st>>>(md.pT + base + md.emb.W[1], md.p + base + md.emb.b[1],
+                                                                    O::E1, O::E0, aug1);
+        k_aug_bias<<<(O::E2 * (O::E1 + 1) + 255) / 256, 256, 0, st>>>(md.pT + base + md.emb.W[2], md.p + base + md.emb.b[2],
+                                                                    O::E2, O::E1, aug2);
+        DP_CUDA(cudaGetLastError());
+        DP_TRY((oz_split<S, B>(aug1, O::E0 + 1, O::E1, NC, O::E0 + 1, O::KA1, NC, KC, w, e, st)));
+        DP_TRY((oz_split<S, B>(aug2, O::E1 + 1, O::E2, (int64_t)O::NN * NC, O::E1 + 1, O::KA2, NC, KC, w + O::WF1,
+                               e + NC, st)));
         DP_TRY((oz_split<S, B>(md.p + base + md.emb.W[2], O::E2, O::E1, NC, O::E2, O::KP2, NC, KC,
                                w + O::WF1 + O::WF2, e + NC + O::NN * NC, st)));
         DP_TRY((oz_split<S, B>(md.p + base + md.emb.W[1], O::E1, O::E0, NC, O::E1, O::KP, NC, KC,
@@ -759,12 +784,12 @@ dp_status fwd(dp_model *m, dp_nlist *nl, const BoxDev &bx, int64_t p0, int64_t n
                                                     b.dig1, b.eA1, b.x1buf, b.Rbuf);
         DP_CUDA(cudaGetLastError());
         Fwd1Epi<O> e1{md, b.chunks, w, e, b.eA1, b.x1buf, act, b.x2buf, b.dig, b.eA};
-        DP_TRY((run_gemm<typename O::Sh1>(m, tiles, b.ntiles, 1, O::KP1, b.dig1, e1, st)));
+        DP_TRY((run_gemm<typename O::Sh1>(m, tiles, b.ntiles, 1, O::KA1, b.dig1, e1, st)));
     }
     {
         ProfScope ps(m->prof, PG_EMBED_FWD_L2, 1, st);
         FwdEpi<O> e2{md, b.chunks, w + O::WF1, e + O::NC, b.eA, b.x2buf, b.Rbuf, act, b.Tpart};
-        DP_TRY((run_gemm<typename O::Sh>(m, tiles, b.ntiles, O::NN, O::KP, b.dig, e2, st)));
+        DP_TRY((run_gemm<typename O::Sh>(m, tiles, b.ntiles, O::NN, O::KA2, b.dig, e2, st)));
     }
     ProfScope ps(m->prof, PG_DESC, 1, st);
     k_ozf_T<O><<<(unsigned)nb, 128, 0, st>>>(md, nl->d_order, p0, nl->d_nnei, b.firstc, b.Tpart, T, D);
