@@ -56,15 +56,17 @@ struct OzEmb {
     static constexpr int KP2 = (E2 + 15) / 16 * 16;  // padded K of dE/dx2 = dz3 W2^T
     static constexpr int NN = (E2 + NC - 1) / NC;    // units of 64 output channels of GEMM 2
     static constexpr int ACT = E0 + E1 + E2 + E2;    // stored per neighbor: t of each layer, then G
-    static constexpr int EPI = 26624;                // GEMM 2 epilogue: G [8][8][33] and R [8][4][33] doubles
-    static constexpr int EPIX = 3072;                // the other epilogues: [4][2][32] doubles
+    static constexpr int NT2 = 384;                  // GEMM 2 epilogue: 12 warps, three per row quarter
+    static constexpr int EPI = 38912;                // its G [12][8][33] and R [12][4][33] doubles
+    static constexpr int NT1 = 384;                  // the other epilogues: 12 warps too
+    static constexpr int EPIX = 4096;                // their [4][3][32] doubles after a 16-byte header
     using Sh = oz::Shape<S, BETA, NC, KC, EPI, 3>;   // GEMM 2 (3 stages: L1 keeps the tanh table)
     using Sh1 = oz::Shape<S, BETA, NC, KC, EPIX>;    // GEMM 1, 3, 4
     // digits of the weights per net (halves): W1^T (GEMM 1), W2^T (GEMM 2), W2 (GEMM 3), W1 (GEMM 4)
     static constexpr int64_t WF1 = (int64_t)NC * S * KA1, WF2 = (int64_t)NN * NC * S * KA2, WB2 = (int64_t)NC * S * KP2,
                              WB1 = (int64_t)NC * S * KP, WNET = WF1 + WF2 + WB2 + WB1;
     static constexpr int ENET = 3 * NC + NN * NC;    // their row scales per net: f1, f2, b2, b1
-    static_assert(8 * (8 + 4) * 33 * 8 <= EPI, "epilogue shared memory");
+    static_assert(NT2 / 32 * (8 + 4) * 33 * 8 <= EPI, "epilogue shared memory");
     static_assert(E1 <= NC && E0 <= NC, "one unit of 64 channels for GEMM 1, 3 and 4");
     static_assert((long long)S * KP2 * (1LL << (2 * BETA - 2)) <= (1LL << 24), "exact FP32 digit sums");
     static_assert((long long)S * KP * (1LL << (2 * BETA - 2)) <= (1LL << 24), "exact FP32 digit sums");
@@ -91,15 +93,22 @@ __device__ __forceinline__ void put_digits8(__half *dig, int64_t row, int k0, co
     }
 }
 
-__device__ __forceinline__ void bar_pair(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
-
-// The largest of v over the row's two warps (the two halves of a row quarter).
-__device__ __forceinline__ double pair_max(double v, unsigned char *esm, int quarter, int half, int lane)
+// Barrier of the NPART warps of a row quarter (named barrier 1 + quarter).
+__device__ __forceinline__ void bar_quarter(int id, int nthreads)
 {
-    double *sm = reinterpret_cast<double *>(esm + 16);   // [4][2][32]
-    sm[(quarter * 2 + half) * 32 + lane] = v;
-    bar_pair(1 + quarter);
-    return fmax(v, sm[(quarter * 2 + (half ^ 1)) * 32 + lane]);
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// The largest of v over the NPART warps of the row's quarter.
+template <int NPART>
+__device__ __forceinline__ double quarter_max(double v, unsigned char *esm, int quarter, int part, int lane)
+{
+    double *sm = reinterpret_cast<double *>(esm + 16);   // [4][NPART][32]
+    sm[(quarter * NPART + part) * 32 + lane] = v;
+    bar_quarter(1 + quarter, 32 * NPART);
+#pragma unroll
+    for (int q = 0; q < NPART; ++q) v = oz::amax(v, sm[(quarter * NPART + q) * 32 + lane]);
+    return v;
 }
 
 template <class O>
@@ -185,20 +194,21 @@ struct Fwd1Epi {
     __half *dig2;
     int *eA2;
     __device__ const __half *b_unit(int64_t tile, int) const { return wdig + chunks[tile * 4].w * O::WNET; }
-    // Column groups k0 = 8 half + 16 i: values first (t2, x2 stored; the row maximum kept), then,
-    // with the maximum of both warps of the quarter, the digits of x2 read back from x2buf.
+    // Column groups k0 = 8 part + 8 NPART i: values first (t2, x2 stored; the row maximum kept), then,
+    // with the maximum over the quarter's warps, the digits of [x2, 1] read back from x2buf.
     __device__ void operator()(int64_t tile, int, uint32_t trow, int tid, unsigned char *esm) const
     {
         constexpr int E0 = O::E0, E1 = O::E1;
-        const int warp = tid >> 5, lane = tid & 31, quarter = warp & 3, half = warp >> 2;
+        constexpr int NPART = O::NT1 / 128;
+        const int warp = tid >> 5, lane = tid & 31, quarter = warp & 3, part = warp >> 2;
         const int4 c4 = chunks[tile * 4 + quarter];
         const int rt = quarter * 32 + lane;
         const int64_t row = tile * 128 + rt;
         double *x2t = x2buf + tile * E1 * 128 + rt;   // x2 of this row, channel stride 128
         if (c4.x < 0) {   // a padding chunk: zero digits
             const double z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int k0 = 8 * half; k0 < O::KA2; k0 += 16) put_digits8<O, O::KA2>(dig2, row, k0, z, 0);
-            if (half == 0) eA2[row] = 0;
+            for (int k0 = 8 * part; k0 < O::KA2; k0 += 8 * NPART) put_digits8<O, O::KA2>(dig2, row, k0, z, 0);
+            if (part == 0) eA2[row] = 0;
             return;
         }
         const int net = c4.w, tj = net % md.ntypes;
@@ -207,7 +217,7 @@ struct Fwd1Epi {
         double *ca = act + ((int64_t)c4.y * md.chunks_per_atom + md.chunk_off[tj] + c4.z / 32) * (O::ACT * 32);
         double mx = 1.0;   // the constant input of the next product's bias column
 #pragma unroll 1
-        for (int k0 = 8 * half; k0 < O::KP; k0 += 16) {
+        for (int k0 = 8 * part; k0 < O::KP; k0 += 8 * NPART) {
             double xs[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
@@ -229,11 +239,11 @@ struct Fwd1Epi {
                 }
             }
         }
-        mx = pair_max(mx, esm, quarter, half, lane);
+        mx = quarter_max<NPART>(mx, esm, quarter, part, lane);
         const int e = oz::row_exp(mx);
-        if (half == 0) eA2[row] = e;
+        if (part == 0) eA2[row] = e;
 #pragma unroll 1
-        for (int k0 = 8 * half; k0 < O::KA2; k0 += 16) {
+        for (int k0 = 8 * part; k0 < O::KA2; k0 += 8 * NPART) {
             double v[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) v[c] = k0 + c < E1 ? x2t[(k0 + c) * 128] : (k0 + c == E1 ? 1.0 : 0.0);
@@ -257,15 +267,15 @@ struct FwdEpi {
         const int net = chunks[tile * 4].w;
         return wdig + net * O::WNET + (int64_t)nchunk * (O::KA2 / O::KC) * O::S * O::NC * O::KC;
     }
-    // 8 warps: the two warps of a row quarter (one chunk) take alternate groups of 8 output channels
+    // NT2 / 32 warps: the warps of a row quarter (one chunk) take groups of 8 output channels in turn
     __device__ void operator()(int64_t tile, int nchunk, uint32_t trow, int tid, unsigned char *esm) const
     {
-        constexpr int E0 = O::E0, E1 = O::E1, E2 = O::E2;
-        const int warp = tid >> 5, lane = tid & 31, quarter = warp & 3, half = warp >> 2;
+        constexpr int E0 = O::E0, E1 = O::E1, E2 = O::E2, NPART = O::NT2 / 128;
+        const int warp = tid >> 5, lane = tid & 31, quarter = warp & 3, part = warp >> 2;
         const int4 c4 = chunks[tile * 4 + quarter];
-        if (c4.x < 0) return;   // a padding chunk: both warps of the quarter skip
-        double *sG = reinterpret_cast<double *>(esm) + warp * 8 * 33;              // [8][33]
-        double *sR = reinterpret_cast<double *>(esm) + 8 * 8 * 33 + warp * 4 * 33;   // [4][33]
+        if (c4.x < 0) return;   // a padding chunk: the quarter's warps skip
+        double *sG = reinterpret_cast<double *>(esm) + warp * 8 * 33;                          // [8][33]
+        double *sR = reinterpret_cast<double *>(esm) + (O::NT2 / 32) * 8 * 33 + warp * 4 * 33;   // [4][33]
         const int net = c4.w, tj = net % md.ntypes;
         const int rt = quarter * 32 + lane;   // row in the tile
         const int64_t row = tile * 128 + rt;
@@ -277,7 +287,7 @@ struct FwdEpi {
         double *Tp = Tpart + (tile * 4 + quarter) * 4 * E2;
         __syncwarp();
 #pragma unroll 1
-        for (int c0 = 8 * half; c0 < O::NC; c0 += 16) {
+        for (int c0 = 8 * part; c0 < O::NC; c0 += 8 * NPART) {
             const int m0 = nchunk * O::NC + c0;
             if (m0 >= E2) break;
             double xs[8];
@@ -466,14 +476,15 @@ struct Bwd3Epi {
     __device__ void operator()(int64_t tile, int, uint32_t trow, int tid, unsigned char *esm) const
     {
         constexpr int E0 = O::E0, E1 = O::E1;
-        const int warp = tid >> 5, lane = tid & 31, quarter = warp & 3, half = warp >> 2;
+        constexpr int NPART = O::NT1 / 128;
+        const int warp = tid >> 5, lane = tid & 31, quarter = warp & 3, part = warp >> 2;
         const int4 c4 = chunks[tile * 4 + quarter];
         const int rt = quarter * 32 + lane;
         const int64_t row = tile * 128 + rt;
         if (c4.x < 0) {
             const double z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int k0 = 8 * half; k0 < O::KP; k0 += 16) put_digits8<O, O::KP>(dig1, row, k0, z, 0);
-            if (half == 0) eA1[row] = 0;
+            for (int k0 = 8 * part; k0 < O::KP; k0 += 8 * NPART) put_digits8<O, O::KP>(dig1, row, k0, z, 0);
+            if (part == 0) eA1[row] = 0;
             return;
         }
         const int net = c4.w, tj = net % md.ntypes;
@@ -484,7 +495,7 @@ struct Bwd3Epi {
         double *dyt = dybuf + tile * E1 * 128 + rt;
         double mx = 0.0;
 #pragma unroll 1
-        for (int k0 = 8 * half; k0 < O::KP; k0 += 16) {
+        for (int k0 = 8 * part; k0 < O::KP; k0 += 8 * NPART) {
             double ds8[8], t2v[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
@@ -506,11 +517,11 @@ struct Bwd3Epi {
                 }
             }
         }
-        mx = pair_max(mx, esm, quarter, half, lane);
+        mx = quarter_max<NPART>(mx, esm, quarter, part, lane);
         const int e = oz::row_exp(mx);
-        if (half == 0) eA1[row] = e;
+        if (part == 0) eA1[row] = e;
 #pragma unroll 1
-        for (int k0 = 8 * half; k0 < O::KP; k0 += 16) {
+        for (int k0 = 8 * part; k0 < O::KP; k0 += 8 * NPART) {
             double v[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) v[c] = k0 + c < E1 ? dzt[(k0 + c) * 128] : 0.0;
@@ -536,14 +547,14 @@ struct Bwd4Epi {
     const double *act, *dybuf, *dRbuf;
     double *force, *atom_virial;
     __device__ const __half *b_unit(int64_t tile, int) const { return wdig + chunks[tile * 4].w * O::WNET; }
-    // This warp's part of dE/ds: channel groups j0 = 8 half + 16 i of layer 0.
-    __device__ __forceinline__ double layer0(int64_t tile, uint32_t trow, int half, int rt, int lane, int er,
+    // This warp's part of dE/ds: channel groups j0 = 8 part + 8 NPART i of layer 0.
+    __device__ __forceinline__ double layer0(int64_t tile, uint32_t trow, int part, int rt, int lane, int er,
                                              const int *eB, const double *ca, const double *W0) const
     {
         constexpr int E0 = O::E0, E1 = O::E1;
         double ds = 0.0;
 #pragma unroll 1
-        for (int j0 = 8 * half; j0 < O::KP1; j0 += 16) {
+        for (int j0 = 8 * part; j0 < O::KP1; j0 += 8 * (O::NT1 / 128)) {
             double sk[8], t1v[8], w0[8];
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
@@ -574,9 +585,10 @@ struct Bwd4Epi {
     __device__ void operator()(int64_t tile, int, uint32_t trow, int tid, unsigned char *esm) const
     {
         constexpr int E0 = O::E0;
-        const int warp = tid >> 5, lane = tid & 31, quarter = warp & 3, half = warp >> 2;
+        constexpr int NPART = O::NT1 / 128;
+        const int warp = tid >> 5, lane = tid & 31, quarter = warp & 3, part = warp >> 2;
         const int4 c4 = chunks[tile * 4 + quarter];
-        if (c4.x < 0) return;   // a padding chunk: both warps of the quarter skip
+        if (c4.x < 0) return;   // a padding chunk: the quarter's warps skip
         const int a = c4.x, net = c4.w, tj = net % md.ntypes;
         const int rt = quarter * 32 + lane;
         const int64_t row = tile * 128 + rt;
@@ -584,12 +596,13 @@ struct Bwd4Epi {
         const int *eB = weB + (int64_t)net * O::ENET + 2 * O::NC + O::NN * O::NC;
         const double *ca = act + ((int64_t)c4.y * md.chunks_per_atom + md.chunk_off[tj] + c4.z / 32) * (O::ACT * 32);
         const double *W0 = md.p + md.emb_base + (int64_t)net * md.emb.size + md.emb.W[0];
-        double ds = layer0(tile, trow, half, rt, lane, er, eB, ca, W0);
-        double *sm = reinterpret_cast<double *>(esm + 16);   // [4][32]
-        if (half == 1) sm[quarter * 32 + lane] = ds;
-        bar_pair(1 + quarter);
-        if (half == 1) return;
-        ds += sm[quarter * 32 + lane];
+        double ds = layer0(tile, trow, part, rt, lane, er, eB, ca, W0);
+        double *sm = reinterpret_cast<double *>(esm + 16);   // [4][NPART][32]
+        if (part > 0) sm[(quarter * NPART + part) * 32 + lane] = ds;
+        bar_quarter(1 + quarter, 32 * NPART);
+        if (part > 0) return;
+#pragma unroll
+        for (int q = 1; q < NPART; ++q) ds += sm[(quarter * NPART + q) * 32 + lane];
         const int cnt = nnei[(int64_t)a * md.ntypes + tj];
         const bool valid = c4.z + lane < cnt;
         double fi[3] = {0.0, 0.0, 0.0}, vir[9];
@@ -739,13 +752,13 @@ dp_status refresh(dp_model *m, cudaStream_t st)
     return DP_OK;
 }
 
-template <class Sh, class Epi>
+template <class Sh, class Epi, int NT = 256>
 dp_status run_gemm(dp_model *m, int64_t tiles, const int *ntiles, int nn, int K, const __half *dA, const Epi &epi,
                    cudaStream_t st)
 {
     int nsm = 0;
     DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
-    auto kern = oz::k_gemm<Sh, Epi, 256>;
+    auto kern = oz::k_gemm<Sh, Epi, NT>;
     static bool attrs_set = false;   // per instantiation: once per process
     if (!attrs_set) {
         DP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM));
@@ -756,7 +769,7 @@ dp_status run_gemm(dp_model *m, int64_t tiles, const int *ntiles, int nn, int K,
     }
     const int64_t units = tiles * nn;
     const unsigned g = (unsigned)(units < nsm ? units : nsm);
-    kern<<<g, 256, Sh::SMEM, st>>>(tiles * 128, ntiles, nn * Sh::NC, K, dA, epi, m->d_err);
+    kern<<<g, NT, Sh::SMEM, st>>>(tiles * 128, ntiles, nn * Sh::NC, K, dA, epi, m->d_err);
     DP_CUDA(cudaGetLastError());
     return DP_OK;
 }
@@ -784,12 +797,12 @@ dp_status fwd(dp_model *m, dp_nlist *nl, const BoxDev &bx, int64_t p0, int64_t n
                                                     b.dig1, b.eA1, b.x1buf, b.Rbuf);
         DP_CUDA(cudaGetLastError());
         Fwd1Epi<O> e1{md, b.chunks, w, e, b.eA1, b.x1buf, act, b.x2buf, b.dig, b.eA};
-        DP_TRY((run_gemm<typename O::Sh1>(m, tiles, b.ntiles, 1, O::KA1, b.dig1, e1, st)));
+        DP_TRY((run_gemm<typename O::Sh1, Fwd1Epi<O>, O::NT1>(m, tiles, b.ntiles, 1, O::KA1, b.dig1, e1, st)));
     }
     {
         ProfScope ps(m->prof, PG_EMBED_FWD_L2, 1, st);
         FwdEpi<O> e2{md, b.chunks, w + O::WF1, e + O::NC, b.eA, b.x2buf, b.Rbuf, act, b.Tpart};
-        DP_TRY((run_gemm<typename O::Sh>(m, tiles, b.ntiles, O::NN, O::KA2, b.dig, e2, st)));
+        DP_TRY((run_gemm<typename O::Sh, FwdEpi<O>, O::NT2>(m, tiles, b.ntiles, O::NN, O::KA2, b.dig, e2, st)));
     }
     ProfScope ps(m->prof, PG_DESC, 1, st);
     k_ozf_T<O><<<(unsigned)nb, 128, 0, st>>>(md, nl->d_order, p0, nl->d_nnei, b.firstc, b.Tpart, T, D);
@@ -824,12 +837,12 @@ dp_status bwd(dp_model *m, dp_nlist *nl, const BoxDev &bx, int64_t nb, const dou
     {
         ProfScope ps(m->prof, PG_EMBED_BWD_L2, 1, st);
         Bwd3Epi<O> e3{md, b.chunks, w + O::WF1 + O::WF2, e, b.eA, act, b.x2buf, b.dzbuf, b.dig1, b.eA1};
-        DP_TRY((run_gemm<typename O::Sh1>(m, tiles, b.ntiles, 1, O::KP2, b.dig, e3, st)));
+        DP_TRY((run_gemm<typename O::Sh1, Bwd3Epi<O>, O::NT1>(m, tiles, b.ntiles, 1, O::KP2, b.dig, e3, st)));
     }
     ProfScope ps(m->prof, PG_EMBED_BWD, 1, st);
     Bwd4Epi<O> e4{md, bx, (const Pos4 *)nl->d_pos, nl->d_nlist, nl->d_nnei, b.chunks,
                   w + O::WF1 + O::WF2 + O::WB2, e, b.eA1, act, b.dzbuf, b.dRbuf, force, atom_virial};
-    DP_TRY((run_gemm<typename O::Sh1>(m, tiles, b.ntiles, 1, O::KP, b.dig1, e4, st)));
+    DP_TRY((run_gemm<typename O::Sh1, Bwd4Epi<O>, O::NT1>(m, tiles, b.ntiles, 1, O::KP, b.dig1, e4, st)));
     return DP_OK;
 }
 
