@@ -44,7 +44,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FFMA/clk x 2 F
 # (dram__bytes_read.sum + dram__bytes_write.sum), and the capture's summary file; valid while the
 # kernel is unchanged since the capture.
 NCU_TRAFFIC = {
-    ("fp64", "cu4000", "embed_fwd_l2"): (2.0806e9 + 1.2659e9, "profiles/fp64_cu4000_nve_step.md"),
+    ("fp64", "cu4000", "embed_fwd_l2"): (2.069e9 + 1.266e9, "profiles/fp64_cu4000_nve_step.md"),
     ("bf16", "cu4000", "embed_bwd"): (28.8e6, "profiles/bf16_cu4000_nve_step.md"),
 }
 
@@ -232,9 +232,9 @@ def run_mine(args, rank, world):
             roofline["traffic_source"] = "ncu, " + tr[1]
         if split_route and args.precision == "fp64":
             roofline["note"] = ("FP64-accurate algorithmic FLOP/s against the FP64 pipe; the multiply-adds of the "
-                                "embedding and first fitting layers run as exact split products on the tensor cores, "
-                                "so the fraction can exceed 1; the kernels are bound by the FP64 pipe of their "
-                                "epilogues (tanh, skip, contraction)")
+                                "embedding's hidden layers and of every fitting layer run as exact split products on "
+                                "the tensor cores, so the fraction can exceed 1; the kernel is bound by the FP64 pipe "
+                                "and the latency of its epilogue (tanh, skip, contraction)")
     step_s = ms * 1e-3 / args.steps
     value = step_s / (n * world)
     total_flop = sum(flops.values())
