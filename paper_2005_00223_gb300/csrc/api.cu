@@ -349,7 +349,9 @@ dp_status dp_model_create(const dp_model_config *cfg, uint64_t seed, dp_model **
     if (e == cudaSuccess) e = cudaMalloc((void **)&m->d_params32, sizeof(float) * m->nparams);
     if (e == cudaSuccess) e = cudaMalloc((void **)&m->d_paramsT32, sizeof(float) * m->nparams);
     if (e == cudaSuccess) e = cudaMalloc((void **)&m->d_flag, sizeof(int32_t) * 4);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&m->d_red, sizeof(double) * kRedParts * 10);
+    // the partial sums of the energy / virial reduction and its arrival counter (zeroed once)
+    if (e == cudaSuccess) e = cudaMalloc((void **)&m->d_red, sizeof(double) * (kRedParts * 10 + 1));
+    if (e == cudaSuccess) e = cudaMemset(m->d_red + kRedParts * 10, 0, sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc((void **)&m->d_err, sizeof(int32_t) * 4);
     if (e == cudaSuccess) e = cudaMemset(m->d_err, 0, sizeof(int32_t) * 4);
     if (e != cudaSuccess) st = cuda_fail(e, "dp_model_create");

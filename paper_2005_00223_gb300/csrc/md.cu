@@ -31,32 +31,34 @@ __global__ void k_kick(int64_t n, double *__restrict__ v, const double *__restri
     for (int k = 0; k < 3; ++k) v[3 * i + k] += s * f[3 * i + k];
 }
 
-// x += dt v, wrapped into [0, L); the packed position array is refreshed too.
-__global__ void k_drift(int64_t n, double *__restrict__ x, const double *__restrict__ v, const int32_t *__restrict__ type,
-                        double dt, BoxDev bx, Pos4 *__restrict__ pos, float4 *__restrict__ posf)
+// The first half kick v += (dt/2) F/m, the drift x += dt v wrapped into
+// [0, L) with the packed position arrays refreshed, and the displacement
+// check against the list's reference positions, one atom per thread.
+__global__ void k_kick_drift_check(int64_t n, double *__restrict__ v, const double *__restrict__ f,
+                                   const int32_t *__restrict__ type, const double *__restrict__ minv, double half_dt,
+                                   double *__restrict__ x, double dt, BoxDev bx, Pos4 *__restrict__ pos,
+                                   float4 *__restrict__ posf, const Pos4 *__restrict__ ref, double lim2,
+                                   int32_t *flags)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int ti = type[i];
+    const double s = half_dt * minv[ti];
     double p[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        double y = x[3 * i + k] + dt * v[3 * i + k];
+        const double vk = v[3 * i + k] + s * f[3 * i + k];
+        v[3 * i + k] = vk;
+        double y = x[3 * i + k] + dt * vk;
         y -= bx.L[k] * floor(y * bx.invL[k]);
         x[3 * i + k] = y;
         p[k] = y;
     }
-    pos[i] = Pos4{p[0], p[1], p[2], (double)type[i]};
-    posf[i] = wrapped_f32(p, type[i], bx);
-}
-
-// flags[1] = 1 when some atom moved more than half the skin since the last build.
-__global__ void k_disp_check(int64_t n, const Pos4 *__restrict__ pos, const Pos4 *__restrict__ ref, BoxDev bx,
-                             double lim2, int32_t *flags)
-{
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const Pos4 pi = Pos4{p[0], p[1], p[2], (double)ti};
+    pos[i] = pi;
+    posf[i] = wrapped_f32(p, ti, bx);
     double d[3];
-    double r = min_image_r(ref[i], pos[i], bx, d);
+    const double r = min_image_r(ref[i], pi, bx, d);
     if (r * r > lim2) flags[1] = 1;
 }
 
@@ -228,13 +230,11 @@ dp_status dp_md_step(dp_model *m, dp_md_state *s, int64_t nsteps, double dt_fs, 
     int64_t row = 0;
     for (int64_t k = 1; k <= nsteps; ++k) {
         {
-            ProfScope ps(m->prof, PG_MD, 3, st);
-            k_kick<<<nblk(n), 256, 0, st>>>(n, s->d_v, s->d_f, nl->d_type, s->d_minv, 0.5 * dt_fs);
-            k_drift<<<nblk(n), 256, 0, st>>>(n, s->d_x, s->d_v, nl->d_type, dt_fs, bx, (Pos4 *)nl->d_pos,
-                                                  (float4 *)nl->d_posf);
+            ProfScope ps(m->prof, PG_MD, 1, st);
             DP_CUDA(cudaMemsetAsync(nl->d_flags + 1, 0, sizeof(int32_t), st));
-            k_disp_check<<<nblk(n), 256, 0, st>>>(n, (const Pos4 *)nl->d_pos, (const Pos4 *)nl->d_ref, bx,
-                                              lim * lim, nl->d_flags);
+            k_kick_drift_check<<<nblk(n), 256, 0, st>>>(n, s->d_v, s->d_f, nl->d_type, s->d_minv, 0.5 * dt_fs, s->d_x,
+                                                        dt_fs, bx, (Pos4 *)nl->d_pos, (float4 *)nl->d_posf,
+                                                        (const Pos4 *)nl->d_ref, lim * lim, nl->d_flags);
         }
         DP_CUDA(cudaGetLastError());
         DP_TRY(nlist_build_device(nl, st, true));
@@ -373,13 +373,11 @@ dp_status dp_md_step_judged(dp_model *student, dp_model *teacher, dp_md_state *s
         dp_precision ap = use_teacher ? teacher_prec : student_prec;
         double *Wi = use_teacher ? Wi_t : Wi_s;
         {
-            ProfScope ps(student->prof, PG_MD, 3, st);
-            k_kick<<<nblk(n), 256, 0, st>>>(n, s->d_v, s->d_f, nl->d_type, s->d_minv, 0.5 * dt_fs);
-            k_drift<<<nblk(n), 256, 0, st>>>(n, s->d_x, s->d_v, nl->d_type, dt_fs, bx, (Pos4 *)nl->d_pos,
-                                                  (float4 *)nl->d_posf);
+            ProfScope ps(student->prof, PG_MD, 1, st);
             DP_CUDA(cudaMemsetAsync(nl->d_flags + 1, 0, sizeof(int32_t), st));
-            k_disp_check<<<nblk(n), 256, 0, st>>>(n, (const Pos4 *)nl->d_pos, (const Pos4 *)nl->d_ref, bx, lim * lim,
-                                                  nl->d_flags);
+            k_kick_drift_check<<<nblk(n), 256, 0, st>>>(n, s->d_v, s->d_f, nl->d_type, s->d_minv, 0.5 * dt_fs, s->d_x,
+                                                        dt_fs, bx, (Pos4 *)nl->d_pos, (float4 *)nl->d_posf,
+                                                        (const Pos4 *)nl->d_ref, lim * lim, nl->d_flags);
         }
         DP_CUDA(cudaGetLastError());
         DP_TRY(nlist_build_device(nl, st, true));

@@ -1,6 +1,7 @@
 // Deterministic reductions: E = sum_i E_i and W = sum_i W_i in a fixed order
 // (kRedParts blocks over contiguous atom ranges, strided partial sums and a
-// fixed tree in each, then one block over the partial sums), plus a scan of
+// fixed tree in each, then the last block to finish over the partial sums in
+// block order), plus a scan of
 // the forces for NaN / Inf.  E is summed in FP64 as Sec. 4.1.3 prescribes
 // for the mixed schemes too.
 #include <cuda_runtime.h>
@@ -29,11 +30,16 @@ __device__ __forceinline__ void block_tree(double (*s)[kRedThreads], double acc[
     }
 }
 
-__global__ void __launch_bounds__(kRedThreads) k_reduce_part(const double *__restrict__ Ei,
-                                                            const double *__restrict__ Wi, int64_t n,
-                                                            double *__restrict__ part)
+// One launch: kRedParts blocks form the partial sums over contiguous atom
+// ranges; the last block to finish (arrival counter after the partials)
+// sums them in block order with the same fixed tree and resets the counter.
+__global__ void __launch_bounds__(kRedThreads) k_reduce(const double *__restrict__ Ei, const double *__restrict__ Wi,
+                                                       int64_t n, double *__restrict__ part,
+                                                       unsigned int *__restrict__ counter, double *__restrict__ E,
+                                                       double *__restrict__ W)
 {
     __shared__ double s[10][kRedThreads];
+    __shared__ bool last;
     const int t = threadIdx.x;
     const int64_t per = (n + kRedParts - 1) / kRedParts;
     const int64_t b0 = blockIdx.x * per, b1 = b0 + per < n ? b0 + per : n;
@@ -49,25 +55,24 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_part(const double *__res
     }
     block_tree(s, acc);
     if (t < 10) part[blockIdx.x * 10 + t] = s[t][0];
-}
-
-__global__ void __launch_bounds__(kRedThreads) k_reduce_final(const double *__restrict__ part, bool has_w,
-                                                             double *__restrict__ E, double *__restrict__ W)
-{
-    __shared__ double s[10][kRedThreads];
-    const int t = threadIdx.x;
-    double acc[10];
+    __threadfence();
+    __syncthreads();
+    if (t == 0) last = atomicAdd(counter, 1u) == (unsigned)(kRedParts - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
 #pragma unroll
     for (int q = 0; q < 10; ++q) acc[q] = 0.0;
     for (int b = t; b < kRedParts; b += kRedThreads) {
 #pragma unroll
-        for (int q = 0; q < 10; ++q) acc[q] += part[b * 10 + q];
+        for (int q = 0; q < 10; ++q) acc[q] += __ldcg(part + b * 10 + q);
     }
     block_tree(s, acc);
     if (t == 0) {
         E[0] = s[0][0];
-        if (W && has_w)
+        if (W && Wi)
             for (int q = 0; q < 9; ++q) W[q] = s[1 + q][0];
+        *counter = 0u;
     }
 }
 
@@ -82,8 +87,9 @@ __global__ void k_nonfinite(const double *__restrict__ x, int64_t n, int32_t *fl
 dp_status reduce_energy_virial(const double *d_atom_energy, const double *d_atom_virial, int64_t n,
                                double *d_energy, double *d_virial, double *d_scratch, cudaStream_t st)
 {
-    k_reduce_part<<<kRedParts, kRedThreads, 0, st>>>(d_atom_energy, d_atom_virial, n, d_scratch);
-    k_reduce_final<<<1, kRedThreads, 0, st>>>(d_scratch, d_atom_virial != nullptr, d_energy, d_virial);
+    k_reduce<<<kRedParts, kRedThreads, 0, st>>>(d_atom_energy, d_atom_virial, n, d_scratch,
+                                                reinterpret_cast<unsigned int *>(d_scratch + kRedParts * 10),
+                                                d_energy, d_virial);
     DP_CUDA(cudaGetLastError());
     return DP_OK;
 }
