@@ -139,6 +139,11 @@ dp_status dp_model_set_stream(dp_model *m, void *stream);
  * the kernels launched and their summed device time (ms) since the clear.
  * dp_profile_group_name returns the group's name, NULL past the last. */
 dp_status dp_profile_enable(dp_model *m, int32_t on);
+/* dp_profile_select(m, mask) restricts the timing to the groups whose bit
+ * (1 << group) is set in mask (all groups by default), so that a timed run
+ * carries the events of the groups it reports and no others.  The mask
+ * outlives dp_profile_enable; counters already taken are kept. */
+dp_status dp_profile_select(dp_model *m, uint32_t group_mask);
 dp_status dp_profile_read(dp_model *m, int32_t group, int64_t *launches, double *ms);
 const char *dp_profile_group_name(int32_t group);
 

@@ -26,7 +26,7 @@ PRECISION = {"fp64": DP_FP64, "mix32": DP_MIX32, "bf16": DP_MIX_BF16, "fp16": DP
 # Every entry point declared in include/dp.h.
 EXPORTS = [
     "dp_status_string", "dp_last_error", "dp_model_create", "dp_model_n_params", "dp_model_get_params",
-    "dp_model_set_params", "dp_model_destroy", "dp_model_set_stream", "dp_profile_enable", "dp_profile_read",
+    "dp_model_set_params", "dp_model_destroy", "dp_model_set_stream", "dp_profile_enable", "dp_profile_select", "dp_profile_read",
     "dp_profile_group_name", "dp_nlist_build", "dp_nlist_update", "dp_nlist_get",
     "dp_nlist_destroy", "dp_nlist_update_dev", "dp_compute", "dp_compute_dev", "dp_md_state_create",
     "dp_md_step", "dp_md_state_get", "dp_md_state_destroy", "dp_param_grad", "dp_force_loss_grad",
@@ -71,6 +71,7 @@ def load(path: str = LIB_PATH):
             "dp_model_destroy": ([P], None),
             "dp_model_set_stream": ([P, P], C.c_int),
             "dp_profile_enable": ([P, I32], C.c_int),
+            "dp_profile_select": ([P, C.c_uint32], C.c_int),
             "dp_profile_read": ([P, I32, P, P], C.c_int),
             "dp_profile_group_name": ([I32], C.c_char_p),
             "dp_nlist_build": ([P, I64, P, P, P, D, D, I32, P], C.c_int),
@@ -181,6 +182,21 @@ def dp_model_set_stream(m, stream=None):
 
 def dp_profile_enable(m, on: bool = True):
     _check(load().dp_profile_enable(m, int(bool(on))), "dp_profile_enable")
+
+
+def dp_profile_select(m, groups=None):
+    """Time only the named groups (None: all of them) while profiling is on."""
+    if groups is None:
+        mask = 0xFFFFFFFF
+    else:
+        names, g = {}, 0
+        while (name := dp_profile_group_name(g)) is not None:
+            names[name] = g
+            g += 1
+        mask = 0
+        for name in groups:
+            mask |= 1 << names[name]
+    _check(load().dp_profile_select(m, mask), "dp_profile_select")
 
 
 def dp_profile_group_name(g: int):

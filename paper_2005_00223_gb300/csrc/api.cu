@@ -46,6 +46,7 @@ dp_status ensure_workspace(dp_model *m, size_t bytes)
     }
     DP_CUDA(cudaMalloc((void **)&m->ws, bytes));
     m->ws_bytes = bytes;
+    ++m->epoch;
     return DP_OK;
 }
 
@@ -86,6 +87,7 @@ dp_status ensure_aux(dp_model *m, int64_t n)
     size_t cnt = (size_t)(n > 0 ? n : 1) * (1 + 9 + 3 + 3) + 16;
     DP_CUDA(cudaMalloc((void **)&m->d_aux, sizeof(double) * cnt));
     m->aux_n = n;
+    ++m->epoch;
     return DP_OK;
 }
 
@@ -208,6 +210,7 @@ const char *dp_last_error(void) { return g_last_error.c_str(); }
 
 static dp_status upload_params(dp_model *m)
 {
+    ++m->epoch;
     m->oz_stale = true;
     m->oz_emb_stale = true;
     m->oz_fit_stale = true;

@@ -97,8 +97,11 @@ struct Prof {
         cudaEvent_t a, b;
     };
     bool on = false;
+    uint32_t mask = ~0u;          // groups that are timed while on
+    bool capturing = false;       // scopes record graph event nodes into captured
     std::vector<cudaEvent_t> pool;
     std::vector<Rec> pending;
+    std::vector<Rec> captured;
     int64_t launches[PG_COUNT] = {0};
     double ms[PG_COUNT] = {0};
     cudaEvent_t get();
@@ -161,6 +164,7 @@ struct dp_model {
     double *d_tscr = nullptr;         // scratch of the training calls
     int64_t tscr_n = -1;
     bool params_dirty = false;        // device parameters newer than the host copy
+    uint64_t epoch = 0;               // bumped whenever a buffer or parameter that launches capture changes
 };
 
 struct dp_nlist {
@@ -211,6 +215,21 @@ struct dp_md_state {
     int64_t step = 0;
     bool forces_valid = false;
     dp_precision forces_prec = DP_FP64;
+    // one MD step captured as a CUDA graph, replayed while its key holds
+    struct GraphScope {
+        int g, n;
+        cudaGraphNode_t na, nb;       // event-record nodes of the scope's two events
+        cudaEvent_t ea, eb;           // the events recorded at capture
+    };
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<GraphScope> graph_scopes;
+    dp_precision graph_prec = DP_FP64;
+    double graph_dt = 0.0;
+    uint64_t graph_epoch = 0;
+    bool graph_prof = false;
+    uint32_t graph_mask = 0;
+    std::string graph_env;
 };
 
 namespace dp {

@@ -4,9 +4,11 @@
 // evaluation, half kick, and thermo rows (KE, PE, T, P) every k steps.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
+#include <string>
 #include <vector>
 
 #include "dp_internal.cuh"
@@ -92,6 +94,159 @@ __global__ void __launch_bounds__(kThermoThreads) k_thermo(int64_t n, const doub
 
 inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
 
+// One velocity-Verlet step after the force of the previous one: half kick,
+// drift and displacement check, conditional list rebuild, formatting and
+// force evaluation, half kick.
+dp_status md_step_body(dp_model *m, dp_md_state *s, dp_precision prec, double dt_fs, const BoxDev &bx, double lim,
+                       double *Wi, cudaStream_t st)
+{
+    dp_nlist *nl = s->nl;
+    const int64_t n = s->n;
+    {
+        ProfScope ps(m->prof, PG_MD, 1, st);
+        DP_CUDA(cudaMemsetAsync(nl->d_flags + 1, 0, sizeof(int32_t), st));
+        k_kick_drift_check<<<nblk(n), 256, 0, st>>>(n, s->d_v, s->d_f, nl->d_type, s->d_minv, 0.5 * dt_fs, s->d_x,
+                                                    dt_fs, bx, (Pos4 *)nl->d_pos, (float4 *)nl->d_posf,
+                                                    (const Pos4 *)nl->d_ref, lim * lim, nl->d_flags);
+    }
+    DP_CUDA(cudaGetLastError());
+    DP_TRY(nlist_build_device(nl, st, true));
+    DP_TRY(compute_device(m, nl, nullptr, prec, s->d_scal, s->d_e, s->d_f, s->d_scal + 1, Wi, st));
+    {
+        ProfScope ps(m->prof, PG_MD, 1, st);
+        k_kick<<<nblk(n), 256, 0, st>>>(n, s->d_v, s->d_f, nl->d_type, s->d_minv, 0.5 * dt_fs);
+    }
+    DP_CUDA(cudaGetLastError());
+    return DP_OK;
+}
+
+// The launches of a step depend on the routing switches read from the
+// environment as well as on the model's buffers (m->epoch) and the call's
+// arguments; a captured step is replayed only while all of them are those
+// of its capture.
+std::string route_env()
+{
+    std::string k;
+    for (const char *v : {"DP_NO_OZAKI", "DP_OZ_MIN_ATOMS", "DP_SIMT_FIT", "DP_BATCH_ATOMS"}) {
+        const char *e = getenv(v);
+        k += e ? e : "-";
+        k += '|';
+    }
+    return k;
+}
+
+void graph_drop(dp_md_state *s)
+{
+    if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    s->graph_exec = nullptr;
+    s->graph = nullptr;
+    Prof *p = s->m ? s->m->prof : nullptr;
+    for (const auto &c : s->graph_scopes) {
+        if (p) {
+            p->pool.push_back(c.ea);
+            p->pool.push_back(c.eb);
+        } else {
+            cudaEventDestroy(c.ea);
+            cudaEventDestroy(c.eb);
+        }
+    }
+    s->graph_scopes.clear();
+}
+
+cudaGraphNode_t event_node(const std::vector<cudaGraphNode_t> &nodes, cudaEvent_t ev)
+{
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        cudaEvent_t e = nullptr;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeEventRecord &&
+            cudaGraphEventRecordNodeGetEvent(nd, &e) == cudaSuccess && e == ev)
+            return nd;
+    }
+    return nullptr;
+}
+
+// Captures one step (md_step_body) into s->graph_exec.  Returns false, with
+// the stream and the model as before, when the step cannot be captured; the
+// caller then keeps launching it directly.
+bool graph_capture(dp_model *m, dp_md_state *s, dp_precision prec, double dt_fs, const BoxDev &bx, double lim,
+                   double *Wi, cudaStream_t st)
+{
+    graph_drop(s);
+    Prof *p = m->prof;
+    const uint64_t ep = m->epoch;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    if (p) {
+        p->capturing = true;
+        p->captured.clear();
+    }
+    const dp_status body = md_step_body(m, s, prec, dt_fs, bx, lim, Wi, st);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &g);
+    std::vector<Prof::Rec> caps;
+    if (p) {
+        p->capturing = false;
+        caps.swap(p->captured);
+    }
+    bool ok = body == DP_OK && e == cudaSuccess && g != nullptr && m->epoch == ep;
+    cudaGraphExec_t x = nullptr;
+    if (ok) ok = cudaGraphInstantiate(&x, g, 0) == cudaSuccess;
+    std::vector<dp_md_state::GraphScope> scopes;
+    if (ok && !caps.empty()) {
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+        for (const Prof::Rec &r : caps) {
+            dp_md_state::GraphScope c{r.g, r.n, event_node(nodes, r.a), event_node(nodes, r.b), r.a, r.b};
+            ok = ok && c.na && c.nb;
+            scopes.push_back(c);
+        }
+    }
+    if (!ok) {
+        if (x) cudaGraphExecDestroy(x);
+        if (g) cudaGraphDestroy(g);
+        for (const Prof::Rec &r : caps) {
+            p->pool.push_back(r.a);
+            p->pool.push_back(r.b);
+        }
+        if (m->epoch != ep) {   // a buffer was set up inside the capture: redo its contents directly
+            m->oz_stale = true;
+            m->oz_emb_stale = true;
+            m->oz_fit_stale = true;
+        }
+        (void)cudaGetLastError();
+        return false;
+    }
+    s->graph = g;
+    s->graph_exec = x;
+    s->graph_scopes.swap(scopes);
+    s->graph_prec = prec;
+    s->graph_dt = dt_fs;
+    s->graph_epoch = m->epoch;
+    s->graph_prof = p && p->on;
+    s->graph_mask = p && p->on ? p->mask : 0u;
+    s->graph_env = route_env();
+    return true;
+}
+
+// One replay of the captured step, its timing events pointed at fresh ones.
+dp_status graph_step(dp_model *m, dp_md_state *s, cudaStream_t st)
+{
+    Prof *p = m->prof;
+    for (const auto &c : s->graph_scopes) {
+        cudaEvent_t a = p->get(), b = p->get();
+        DP_CUDA(cudaGraphExecEventRecordNodeSetEvent(s->graph_exec, c.na, a));
+        DP_CUDA(cudaGraphExecEventRecordNodeSetEvent(s->graph_exec, c.nb, b));
+        p->pending.push_back({c.g, c.n, a, b});
+    }
+    DP_CUDA(cudaGraphLaunch(s->graph_exec, st));
+    return DP_OK;
+}
+
 }  // namespace
 }  // namespace dp
 
@@ -103,6 +258,7 @@ void dp_md_state_destroy(dp_md_state *s)
 {
     if (!s) return;
     if (s->m && s->m->stream) cudaStreamSynchronize(s->m->stream);
+    graph_drop(s);
     dp_nlist_destroy(s->nl);
     cudaFree(s->d_x);
     cudaFree(s->d_v);
@@ -227,22 +383,22 @@ dp_status dp_md_step(dp_model *m, dp_md_state *s, int64_t nsteps, double dt_fs, 
         s->forces_prec = prec;
     }
     const double lim = 0.5 * nl->skin;
+    // Steps run as replays of one captured step (CUDA graph) unless
+    // DP_NO_GRAPH is set; a step is captured after one direct step of this
+    // call, so that every buffer and weight image it uses is in place.
+    const bool prof_on = m->prof && m->prof->on;
+    if (s->graph_exec && !(s->graph_prec == prec && s->graph_dt == dt_fs && s->graph_epoch == m->epoch &&
+                           s->graph_prof == prof_on && s->graph_mask == (prof_on ? m->prof->mask : 0u) &&
+                           s->graph_env == route_env()))
+        graph_drop(s);
+    const bool use_graph = getenv("DP_NO_GRAPH") == nullptr;
+    bool can_capture = use_graph;
     int64_t row = 0;
     for (int64_t k = 1; k <= nsteps; ++k) {
-        {
-            ProfScope ps(m->prof, PG_MD, 1, st);
-            DP_CUDA(cudaMemsetAsync(nl->d_flags + 1, 0, sizeof(int32_t), st));
-            k_kick_drift_check<<<nblk(n), 256, 0, st>>>(n, s->d_v, s->d_f, nl->d_type, s->d_minv, 0.5 * dt_fs, s->d_x,
-                                                        dt_fs, bx, (Pos4 *)nl->d_pos, (float4 *)nl->d_posf,
-                                                        (const Pos4 *)nl->d_ref, lim * lim, nl->d_flags);
-        }
-        DP_CUDA(cudaGetLastError());
-        DP_TRY(nlist_build_device(nl, st, true));
-        DP_TRY(compute_device(m, nl, nullptr, prec, s->d_scal, s->d_e, s->d_f, s->d_scal + 1, Wi, st));
-        {
-            ProfScope ps(m->prof, PG_MD, 1, st);
-            k_kick<<<nblk(n), 256, 0, st>>>(n, s->d_v, s->d_f, nl->d_type, s->d_minv, 0.5 * dt_fs);
-        }
+        if (can_capture && !s->graph_exec && k >= 2)
+            can_capture = graph_capture(m, s, prec, dt_fs, bx, lim, Wi, st);
+        if (use_graph && s->graph_exec) DP_TRY(graph_step(m, s, st));
+        else DP_TRY(md_step_body(m, s, prec, dt_fs, bx, lim, Wi, st));
         if (rows && k % thermo_every == 0 && row < rows) {
             ProfScope ps(m->prof, PG_THERMO, 1, st);
             k_thermo<<<1, kThermoThreads, 0, st>>>(n, s->d_v, nl->d_type, s->d_mass, s->d_scal, vol,

@@ -164,27 +164,45 @@ __global__ void k_candidates(int64_t n, const Pos4 *__restrict__ pos, BoxDev bx,
     if (i == 0 && lane == 0) atomicAdd(&flags[2], 1);
 }
 
+// FP32 value of a double rounded to nearest (ties away from zero) with
+// integer instructions; magnitudes below 2^-126 give 0.
+__device__ __forceinline__ float d2f_rn(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v) + (1ull << 28);
+    const int ex = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+    if (ex <= 0) return 0.0f;
+    return __uint_as_float((unsigned)(b >> 32 & 0x80000000u) | ((unsigned)ex << 23) | (unsigned)((b >> 29) & 0x7fffffu));
+}
+
 // Geometry record of a kept neighbor for the tensor-core path, from the
 // exact FP64 difference d and distance r: the switching function s(r) and
-// ds/dr in FP64, stored as FP32 (s, d/r) and (ds/dr, r).
+// ds/dr, stored as FP32 (s, d/r) and (ds/dr, r).  The record is computed in
+// FP32 from the rounded r and d; only the two offsets r - r_cs and r - r_c
+// are taken in FP64, so that u = (r - r_cs)/(r_c - r_cs) and 1 - u keep
+// full relative precision at both ends of the switching region, and the
+// quintic is evaluated in the factored form 1 - 10u^3 + 15u^4 - 6u^5 =
+// (1 - u)^3 (1 + 3u + 6u^2), whose factors have no cancellation on [0, 1].
+// Each field is within a few FP32 ulps of its exact value.
 __device__ __forceinline__ void env_record(const double d[3], double r, const ModelDev &md, float4 &ra, float2 &rb)
 {
-    const double ir = 1.0 / r;
-    double s, ds;
+    const float rf = d2f_rn(r);
+    const float irf = __frcp_rn(rf);
+    float s, ds;
     if (r < md.rcs) {
-        s = ir;
-        ds = -ir * ir;
+        s = irf;
+        ds = -irf * irf;
     } else {
-        const double u = (r - md.rcs) * md.inv_sw;
-        const double u2 = u * u, um = u - 1.0;
-        const double poly = fma(u2 * u, fma(fma(-6.0, u, 15.0), u, -10.0), 1.0);
-        const double dpoly = -30.0 * md.inv_sw * u2 * (um * um);
-        s = poly * ir;
-        ds = (dpoly - s) * ir;
+        const float isw = d2f_rn(md.inv_sw);
+        const float u = d2f_rn(__dsub_rn(r, md.rcs)) * isw;
+        const float um = d2f_rn(__dsub_rn(md.rcut, r)) * isw;   // 1 - u
+        const float u2 = u * u, um2 = um * um;
+        const float poly = um2 * um * fmaf(fmaf(6.0f, u, 3.0f), u, 1.0f);
+        const float dpoly = -30.0f * isw * u2 * um2;
+        s = poly * irf;
+        ds = (dpoly - s) * irf;
     }
-    const float irf = (float)ir;
-    ra = make_float4((float)s, (float)d[0] * irf, (float)d[1] * irf, (float)d[2] * irf);
-    rb = make_float2((float)ds, (float)r);
+    ra = make_float4(s, d2f_rn(d[0]) * irf, d2f_rn(d[1]) * irf, d2f_rn(d[2]) * irf);
+    rb = make_float2(ds, rf);
 }
 
 constexpr int kRecStage = 256;   // kept neighbors per atom whose records are staged in shared memory

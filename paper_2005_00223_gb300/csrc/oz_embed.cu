@@ -722,6 +722,7 @@ dp_status refresh(dp_model *m, cudaStream_t st)
         const size_t dig_bytes = (sizeof(__half) * O::WNET * nnet + 255) & ~(size_t)255;
         DP_CUDA(cudaMalloc(&m->d_ozw_emb, dig_bytes + sizeof(double) * O::AUG));
         DP_CUDA(cudaMalloc((void **)&m->d_oze_emb, sizeof(int) * O::ENET * nnet));
+        ++m->epoch;
         m->oz_emb_stale = true;
     }
     if (!m->oz_emb_stale) return DP_OK;

@@ -139,6 +139,7 @@ dp_status oz_fit_chain_refresh(dp_model *m, cudaStream_t st)
     if (!m->d_ozw_fit) {
         DP_CUDA(cudaMalloc(&m->d_ozw_fit, sizeof(__half) * 4 * per * md.ntypes));
         DP_CUDA(cudaMalloc((void **)&m->d_oze_fit, sizeof(int) * 4 * (size_t)F * md.ntypes));
+        ++m->epoch;
         m->oz_fit_stale = true;
     }
     if (!m->oz_fit_stale) return DP_OK;

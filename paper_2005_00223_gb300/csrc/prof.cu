@@ -49,20 +49,29 @@ Prof::~Prof()
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
 }
 
+// While a stream is captured into a graph the events become event-record
+// nodes of the graph (cudaEventRecordExternal); the MD loop points them at
+// fresh events before every replay.
+static void record(const Prof *p, cudaEvent_t e, cudaStream_t st)
+{
+    if (p->capturing) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
+}
+
 ProfScope::ProfScope(Prof *p_, int g_, int n_, cudaStream_t st_) : p(p_), g(g_), n(n_), st(st_)
 {
-    if (p && p->on) {
+    if (p && p->on && (p->mask >> g & 1u)) {
         a = p->get();
-        cudaEventRecord(a, st);
+        record(p, a, st);
     }
 }
 
 ProfScope::~ProfScope()
 {
-    if (p && p->on && a) {
+    if (a) {
         cudaEvent_t b = p->get();
-        cudaEventRecord(b, st);
-        p->pending.push_back({g, n, a, b});
+        record(p, b, st);
+        (p->capturing ? p->captured : p->pending).push_back({g, n, a, b});
     }
 }
 
@@ -97,6 +106,18 @@ dp_status dp_profile_enable(dp_model *m, int32_t on)
     DP_CUDA(cudaStreamSynchronize(m->stream));
     m->prof->clear();
     m->prof->on = on != 0;
+    return DP_OK;
+}
+
+dp_status dp_profile_select(dp_model *m, uint32_t group_mask)
+{
+    if (!m || !m->prof) {
+        set_error("dp_profile_select: NULL model");
+        return DP_ERR_ARG;
+    }
+    DP_CUDA(cudaStreamSynchronize(m->stream));
+    m->prof->drain();
+    m->prof->mask = group_mask;
     return DP_OK;
 }
 

@@ -685,6 +685,7 @@ dp_status oz_refresh_weights(dp_model *m, cudaStream_t st)
     if (!m->d_ozw) {
         DP_CUDA(cudaMalloc(&m->d_ozw, sizeof(__half) * oz_weight_halves(md) * md.ntypes));
         DP_CUDA(cudaMalloc((void **)&m->d_oze, sizeof(int) * (size_t)(f0 + nd) * md.ntypes));
+        ++m->epoch;
         m->oz_stale = true;
     }
     if (!m->oz_stale) return DP_OK;
@@ -837,7 +838,7 @@ dp_status compute_simt(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
             s = launch_batch<ShapePaper, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, ozs, ozes, st);
         if (s != DP_OK) return s;
     }
-    ProfScope ps(m->prof, PG_REDUCE, 2, st);
+    ProfScope ps(m->prof, PG_REDUCE, 1, st);
     return reduce_energy_virial(d_atom_energy, d_atom_virial, n, d_energy, d_virial, m->d_red, st);
 }
 

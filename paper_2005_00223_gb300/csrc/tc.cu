@@ -3,11 +3,13 @@
 // fp16 or bf16 operands in shared memory and FP32 accumulators in tensor
 // memory; the first embedding layer (K = 1, too small for the tensor cores),
 // tanh and its derivative run in FP32 on the CUDA cores, as the paper does.
-// The minimum image, the distance and the switching function s(r), ds/dr are
-// evaluated in FP64 once per evaluation by the formatting kernel, which
-// stores (s, u = d/r) and (ds/dr, r) per neighbor slot as FP32; here the
-// environment row R = (s, s u) and the chain dE/dR -> g_ij run in FP32, and
-// the force / virial accumulation is FP64.
+// The minimum image and the distance are evaluated in FP64 once per
+// evaluation by the formatting kernel, which stores (s, u = d/r) and
+// (ds/dr, r) per neighbor slot as FP32 (the switching function from the
+// FP64 distance in FP32 arithmetic, within a few FP32 ulps, far below the
+// 16-bit operands these values feed); here the environment row R = (s, s u)
+// and the chain dE/dR -> g_ij run in FP32, and the force / virial
+// accumulation is FP64.
 //
 // Work unit: a tile of 128 neighbor rows = 4 chunks of 32 rows, one chunk per
 // warp; every chunk is up to 32 neighbors of one type of one atom, and the 4
@@ -121,7 +123,7 @@ struct TileCtx {
 // One thread's row of a tile as read from global memory: the chunk entry,
 // the neighbor count of its (atom, type) block and the slot's neighbor
 // geometry (s, u = d/r and, for the backward pass, ds/dr, r and j; all
-// evaluated in FP64 by the formatting kernel).  Fetched one tile ahead: the
+// from the FP64 minimum image of the formatting kernel).  Fetched one tile ahead: the
 // slot loads do not wait for the count (they stay inside the type block's
 // sel slots), and the row's validity is applied when it is used.
 struct RowIn {
@@ -1418,7 +1420,7 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
                                                                      cnt, wimg, dT, d_force, d_atom_virial, m->d_err);
     }
     DP_CUDA(cudaGetLastError());
-    ProfScope ps(m->prof, PG_REDUCE, 2, st);
+    ProfScope ps(m->prof, PG_REDUCE, 1, st);
     return reduce_energy_virial(d_atom_energy, d_atom_virial, n, d_energy, d_virial, m->d_red, st);
 }
 

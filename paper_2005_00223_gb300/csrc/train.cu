@@ -245,6 +245,7 @@ dp_status dp_adam_step(dp_model *m, const double *d_grad, double lr, double beta
     DP_CUDA(cudaGetLastError());
     DP_TRY(refresh_params_device(m, st));
     m->params_dirty = true;
+    ++m->epoch;
     m->oz_stale = true;
     m->oz_emb_stale = true;
     m->oz_fit_stale = true;

@@ -67,3 +67,44 @@ def test_nve_energy_conservation_copper(dp):
     etot = th[:, 0] + th[:, 1]
     assert np.isfinite(th).all()
     assert np.abs(etot - etot[0]).max() < 1e-3 * np.abs(th[:, 0]).mean()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_graph_replay_matches_direct_launches(dp, prec):
+    """Steps replayed from one captured step (CUDA graph) against the same steps launched one by one
+    (DP_NO_GRAPH): same trajectory, same rebuilds, same per-group launch counts under profiling;
+    the second call reuses the capture and the profiling switch forces a new one."""
+    import os
+    cfg, p = _scaled_water_model(5)
+    coord, typ, box = dpsynth.water_box(5)
+    mass = np.array([dpsynth.MASS["O"], dpsynth.MASS["H"]])
+    vel = dpsynth.velocities(mass[typ], 600.0, 5)
+    m = dp.Model(cfg, 0, params=p)
+    runs = []
+    for direct in (True, False):
+        if direct:
+            os.environ["DP_NO_GRAPH"] = "1"
+        try:
+            st = dp.MDState(m, coord, vel, typ, mass, box, skin=0.05)
+            dp.dp_profile_enable(m.h, True)
+            th1 = st.step(7, 0.5, prec, thermo_every=1)
+            prof = dp.dp_profile_read(m.h)
+            dp.dp_profile_enable(m.h, False)
+            th2 = st.step(6, 0.5, prec, thermo_every=3)
+            th3 = st.step(4, 0.5, prec, thermo_every=2)
+            x, v, step, nreb = st.get()
+            st.close()
+        finally:
+            os.environ.pop("DP_NO_GRAPH", None)
+        runs.append((th1, th2, th3, x, v, step, nreb, {g: c[0] for g, c in prof.items()}))
+    a, b = runs
+    # the force and virial sums take atomics in whatever order the blocks run: run-to-run noise of
+    # the FP32 sums of MIX-16 (not the replay) sets its tolerance
+    tol = 1e-9 if prec == "fp64" else 1e-3
+    for k in range(3):
+        np.testing.assert_allclose(b[k], a[k], rtol=tol, atol=tol * np.abs(a[k]).max())
+    np.testing.assert_allclose(b[3], a[3], rtol=0, atol=tol * box[0, 0])
+    np.testing.assert_allclose(b[4], a[4], rtol=0, atol=tol * np.abs(a[4]).max())
+    assert a[5] == b[5] == 17
+    assert a[6] == b[6] and a[6] > 1          # rebuilds inside the replayed steps
+    assert a[7] == b[7]
