@@ -577,6 +577,8 @@ dp_status dp::nlist_create_internal(const dp_model *m, int64_t n, const int32_t 
         if (e == cudaSuccess) e = cudaMemcpyAsync(nl->d_order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(nl->d_flags, 0, sizeof(int32_t) * 4, st);
+    // cell counts start at zero; every build leaves them zero again
+    if (e == cudaSuccess) e = cudaMemsetAsync(nl->d_cell_cnt, 0, sizeof(int32_t) * (nl->ncell + 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(nl->d_ntrunc, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {

@@ -189,7 +189,7 @@ struct dp_nlist {
     int32_t *d_nlist = nullptr;       // [n][nsel]
     int32_t *d_nnei = nullptr;        // [n][ntypes] real neighbors kept per type
     unsigned long long *d_ntrunc = nullptr;
-    int32_t *d_flags = nullptr;       // [0] error bits, [1] rebuild needed, [2] rebuild count
+    int32_t *d_flags = nullptr;       // [0] error bits, [1] rebuild needed, [2] rebuild count, [3] block arrivals of a build
     double *d_pos = nullptr;          // [n][4] packed current coordinates (x, y, z, type)
     float *d_posf = nullptr;          // [n][4] FP32 copy of the coordinates (prefilter of the formatting)
     float *d_env = nullptr;           // tensor-core geometry (lazy): [n][nsel] float4 (s, u), then [n][nsel] float2 (ds/dr, r)

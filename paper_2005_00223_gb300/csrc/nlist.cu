@@ -45,41 +45,40 @@ __global__ void k_pack(int64_t n, const double *__restrict__ coord, const int32_
 // it is zero.
 __device__ __forceinline__ bool skip(const int32_t *flags, int cond) { return cond && flags[1] == 0; }
 
-__global__ void k_cell_zero(int64_t ncell, int32_t *cnt, const int32_t *flags, int cond)
-{
-    if (skip(flags, cond)) return;
-    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c <= ncell) cnt[c] = 0;
-}
-
-__global__ void k_cell_assign(int64_t n, const Pos4 *__restrict__ pos, BoxDev bx, int32_t *cell_of, int32_t *cnt,
-                              const int32_t *flags, int cond)
-{
-    if (skip(flags, cond)) return;
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    Pos4 p = pos[i];
-    int cx = cell_coord(p.x, bx.invL[0], bx.nc[0]);
-    int cy = cell_coord(p.y, bx.invL[1], bx.nc[1]);
-    int cz = cell_coord(p.z, bx.invL[2], bx.nc[2]);
-    // each frame has its own block of cells, so no candidate crosses frames
-    int c = (int)(i / bx.frame_n) * bx.ncell_f + (cx * bx.nc[1] + cy) * bx.nc[2] + cz;
-    cell_of[i] = c;
-    atomicAdd(&cnt[c], 1);
-}
-
-// Exclusive scan of the cell counts by one block; zeroes the counts so they
-// serve as fill cursors next.
-__global__ void k_cell_scan(int64_t ncell, int32_t *cnt, int32_t *start, const int32_t *flags, int cond)
+// Cell of every atom and the cell counts (atomics); the last block to finish
+// (arrival counter flags[3]) turns the counts into cell starts and zeroes
+// them for use as the fill cursor.  The counts are zero on entry: the
+// candidate kernel of the previous build (or the allocation) leaves them so.
+__global__ void __launch_bounds__(1024) k_cell_assign_scan(int64_t n, int64_t ncell, const Pos4 *__restrict__ pos,
+                                                          BoxDev bx, int32_t *cell_of, int32_t *cnt,
+                                                          int32_t *start, int32_t *flags, int cond)
 {
     if (skip(flags, cond)) return;
     __shared__ int32_t part[1024];
-    int tid = threadIdx.x, nt = blockDim.x;
-    int64_t per = (ncell + nt - 1) / nt;
-    int64_t b = tid * per, e = b + per < ncell ? b + per : ncell;
-    int32_t s = 0;
-    for (int64_t c = b; c < e; ++c) s += cnt[c];
-    part[tid] = s;
+    __shared__ bool last;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int64_t i = blockIdx.x * (int64_t)nt + tid;
+    if (i < n) {
+        Pos4 p = pos[i];
+        int cx = cell_coord(p.x, bx.invL[0], bx.nc[0]);
+        int cy = cell_coord(p.y, bx.invL[1], bx.nc[1]);
+        int cz = cell_coord(p.z, bx.invL[2], bx.nc[2]);
+        // each frame has its own block of cells, so no candidate crosses frames
+        int c = (int)(i / bx.frame_n) * bx.ncell_f + (cx * bx.nc[1] + cy) * bx.nc[2] + cz;
+        cell_of[i] = c;
+        atomicAdd(&cnt[c], 1);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) last = atomicAdd(reinterpret_cast<unsigned *>(flags + 3), 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int64_t per = (ncell + nt - 1) / nt;
+    const int64_t b = tid * per, e = b + per < ncell ? b + per : ncell;
+    int32_t sum = 0;
+    for (int64_t c = b; c < e; ++c) sum += __ldcg(cnt + c);
+    part[tid] = sum;
     __syncthreads();
     for (int off = 1; off < nt; off <<= 1) {
         int32_t v = tid >= off ? part[tid - off] : 0;
@@ -87,16 +86,16 @@ __global__ void k_cell_scan(int64_t ncell, int32_t *cnt, int32_t *start, const i
         part[tid] += v;
         __syncthreads();
     }
-    int32_t run = part[tid] - s;
+    int32_t run = part[tid] - sum;
     for (int64_t c = b; c < e; ++c) {
-        int32_t v = cnt[c];
+        int32_t v = __ldcg(cnt + c);
         start[c] = run;
         run += v;
         cnt[c] = 0;
     }
     if (tid == nt - 1) start[ncell] = part[tid];
+    if (tid == 0) flags[3] = 0;
 }
-
 __global__ void k_cell_fill(int64_t n, const int32_t *cell_of, const int32_t *start, int32_t *cursor,
                             int32_t *atoms, const int32_t *flags, int cond)
 {
@@ -112,9 +111,13 @@ __global__ void k_cell_fill(int64_t n, const int32_t *cell_of, const int32_t *st
 __global__ void k_candidates(int64_t n, const Pos4 *__restrict__ pos, BoxDev bx, double rlist,
                              const int32_t *__restrict__ cell_of, const int32_t *__restrict__ start,
                              const int32_t *__restrict__ atoms, int32_t cap, int32_t *__restrict__ cand,
-                             int32_t *__restrict__ cand_cnt, Pos4 *__restrict__ ref, int32_t *flags, int cond)
+                             int32_t *__restrict__ cand_cnt, Pos4 *__restrict__ ref, int32_t *cell_cnt,
+                             int64_t ncell, int32_t *flags, int cond)
 {
     if (skip(flags, cond)) return;
+    // the cell counts (the fill cursor, now complete) back to zero for the next build
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= ncell; c += (int64_t)gridDim.x * blockDim.x)
+        cell_cnt[c] = 0;
     const int lane = threadIdx.x & 31;
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
@@ -369,17 +372,15 @@ dp_status nlist_build_device(dp_nlist *nl, cudaStream_t st, bool conditional)
     BoxDev bx = make_box(nl);
     int cond = conditional ? 1 : 0;
     const Pos4 *pos = (const Pos4 *)nl->d_pos;
-    ProfScope ps(nl->m->prof, PG_BUILD, 5, st);
-    k_cell_zero<<<blocks_for(nl->ncell + 1, 256), 256, 0, st>>>(nl->ncell, nl->d_cell_cnt, nl->d_flags, cond);
-    k_cell_assign<<<blocks_for(nl->n, 256), 256, 0, st>>>(nl->n, pos, bx, nl->d_cell_of, nl->d_cell_cnt,
-                                                         nl->d_flags, cond);
-    k_cell_scan<<<1, 1024, 0, st>>>(nl->ncell, nl->d_cell_cnt, nl->d_cell_start, nl->d_flags, cond);
+    ProfScope ps(nl->m->prof, PG_BUILD, 3, st);
+    k_cell_assign_scan<<<blocks_for(nl->n, 1024), 1024, 0, st>>>(nl->n, nl->ncell, pos, bx, nl->d_cell_of,
+                                                              nl->d_cell_cnt, nl->d_cell_start, nl->d_flags, cond);
     k_cell_fill<<<blocks_for(nl->n, 256), 256, 0, st>>>(nl->n, nl->d_cell_of, nl->d_cell_start, nl->d_cell_cnt,
                                                        nl->d_cell_atoms, nl->d_flags, cond);
     k_candidates<<<blocks_for(nl->n * 32, 256), 256, 0, st>>>(nl->n, pos, bx, nl->rlist, nl->d_cell_of,
                                                              nl->d_cell_start, nl->d_cell_atoms, nl->cap,
                                                              nl->d_cand, nl->d_cand_cnt, (Pos4 *)nl->d_ref,
-                                                             nl->d_flags, cond);
+                                                             nl->d_cell_cnt, nl->ncell, nl->d_flags, cond);
     DP_CUDA(cudaGetLastError());
     return DP_OK;
 }

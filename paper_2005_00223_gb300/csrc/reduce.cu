@@ -1,7 +1,7 @@
 // Deterministic reductions: E = sum_i E_i and W = sum_i W_i in a fixed order
-// (kRedParts blocks over contiguous atom ranges, strided partial sums and a
-// fixed tree in each, then the last block to finish over the partial sums in
-// block order), plus a scan of
+// (up to 152 blocks over contiguous atom ranges, strided partial sums and a
+// fixed warp butterfly in each, then the last block to finish over the partial
+// sums in block order), plus a scan of
 // the forces for NaN / Inf.  E is summed in FP64 as Sec. 4.1.3 prescribes
 // for the mixed schemes too.
 #include <cuda_runtime.h>
@@ -14,38 +14,60 @@ namespace {
 
 constexpr int kRedThreads = 256;
 
-// Fixed-shape tree over the block's kRedThreads values of 10 sums.
-__device__ __forceinline__ void block_tree(double (*s)[kRedThreads], double acc[10])
+// Fixed-order sum over the block's threads of 10 values each, returned to
+// threads 0..9 (sum q at thread q).  Within a warp a butterfly
+// reduce-scatter over 16 slots (10 used): at each of 4 levels a lane keeps
+// half of its slots and adds the partner's copy of them, so after the last
+// exchange lanes 2q and 2q+1 hold the warp total of slot q; 16 FP64 adds per
+// lane instead of 50 for ten separate shuffle trees, and far fewer than a
+// shared-memory tree (GB300 runs FP64 at 1/64 of the FP32 rate).  The 8 warp
+// totals are then added in warp order.
+__device__ __forceinline__ double block_sum10(double v[16], double (*s)[10])
 {
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 #pragma unroll
-    for (int q = 0; q < 10; ++q) s[q][t] = acc[q];
-    __syncthreads();
-    for (int h = kRedThreads / 2; h > 0; h >>= 1) {
-        if (t < h) {
+    for (int lv = 0; lv < 4; ++lv) {
+        const int half = 8 >> lv, off = 16 >> lv;
+        const bool up = lane & off;
 #pragma unroll
-            for (int q = 0; q < 10; ++q) s[q][t] += s[q][t + h];
+        for (int i = 0; i < half; ++i) {
+            const double keep = up ? v[i + half] : v[i];
+            const double give = up ? v[i] : v[i + half];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, give, off);
         }
-        __syncthreads();
     }
+    const double tot = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+    const int q = (lane >> 1) & 15;
+    __syncthreads();   // s free from any earlier use
+    if (!(lane & 1) && q < 10) s[warp][q] = tot;
+    __syncthreads();
+    double x = 0.0;
+    if (t < 10) {
+        x = s[0][t];
+#pragma unroll
+        for (int w = 1; w < kRedThreads / 32; ++w) x += s[w][t];
+    }
+    return x;
 }
 
-// One launch: kRedParts blocks form the partial sums over contiguous atom
-// ranges; the last block to finish (arrival counter after the partials)
-// sums them in block order with the same fixed tree and resets the counter.
+// One launch: gridDim.x (<= kRedParts, a function of n) blocks form the
+// partial sums over contiguous atom ranges; the last block to finish
+// (arrival counter after the partials) sums them in block order the same
+// way and resets the counter.
 __global__ void __launch_bounds__(kRedThreads) k_reduce(const double *__restrict__ Ei, const double *__restrict__ Wi,
                                                        int64_t n, double *__restrict__ part,
                                                        unsigned int *__restrict__ counter, double *__restrict__ E,
                                                        double *__restrict__ W)
 {
-    __shared__ double s[10][kRedThreads];
+    __shared__ double s[kRedThreads / 32][10];
     __shared__ bool last;
     const int t = threadIdx.x;
-    const int64_t per = (n + kRedParts - 1) / kRedParts;
+    const int parts = gridDim.x;
+    const int64_t per = (n + parts - 1) / parts;
     const int64_t b0 = blockIdx.x * per, b1 = b0 + per < n ? b0 + per : n;
-    double acc[10];
+    double acc[16];
 #pragma unroll
-    for (int q = 0; q < 10; ++q) acc[q] = 0.0;
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
     for (int64_t i = b0 + t; i < b1; i += kRedThreads) {
         acc[0] += Ei[i];
         if (Wi) {
@@ -53,27 +75,24 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(const double *__restrict
             for (int q = 0; q < 9; ++q) acc[1 + q] += Wi[9 * i + q];
         }
     }
-    block_tree(s, acc);
-    if (t < 10) part[blockIdx.x * 10 + t] = s[t][0];
+    double x = block_sum10(acc, s);
+    if (t < 10) part[blockIdx.x * 10 + t] = x;
     __threadfence();
     __syncthreads();
-    if (t == 0) last = atomicAdd(counter, 1u) == (unsigned)(kRedParts - 1);
+    if (t == 0) last = atomicAdd(counter, 1u) == (unsigned)(parts - 1);
     __syncthreads();
     if (!last) return;
     __threadfence();
 #pragma unroll
-    for (int q = 0; q < 10; ++q) acc[q] = 0.0;
-    for (int b = t; b < kRedParts; b += kRedThreads) {
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    for (int b = t; b < parts; b += kRedThreads) {
 #pragma unroll
         for (int q = 0; q < 10; ++q) acc[q] += __ldcg(part + b * 10 + q);
     }
-    block_tree(s, acc);
-    if (t == 0) {
-        E[0] = s[0][0];
-        if (W && Wi)
-            for (int q = 0; q < 9; ++q) W[q] = s[1 + q][0];
-        *counter = 0u;
-    }
+    x = block_sum10(acc, s);
+    if (t == 0) E[0] = x;
+    if (t >= 1 && t < 10 && W && Wi) W[t - 1] = x;
+    if (t == 0) *counter = 0u;
 }
 
 __global__ void k_nonfinite(const double *__restrict__ x, int64_t n, int32_t *flag)
@@ -87,7 +106,10 @@ __global__ void k_nonfinite(const double *__restrict__ x, int64_t n, int32_t *fl
 dp_status reduce_energy_virial(const double *d_atom_energy, const double *d_atom_virial, int64_t n,
                                double *d_energy, double *d_virial, double *d_scratch, cudaStream_t st)
 {
-    k_reduce<<<kRedParts, kRedThreads, 0, st>>>(d_atom_energy, d_atom_virial, n, d_scratch,
+    // about 64 atoms per block up to one block per SM (152): the block sums dominate, not the loads
+    const int64_t want = (n + 63) / 64;
+    const unsigned parts = (unsigned)(want < 1 ? 1 : (want > 152 ? 152 : want));
+    k_reduce<<<parts, kRedThreads, 0, st>>>(d_atom_energy, d_atom_virial, n, d_scratch,
                                                 reinterpret_cast<unsigned int *>(d_scratch + kRedParts * 10),
                                                 d_energy, d_virial);
     DP_CUDA(cudaGetLastError());

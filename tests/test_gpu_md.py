@@ -98,13 +98,21 @@ def test_graph_replay_matches_direct_launches(dp, prec):
             os.environ.pop("DP_NO_GRAPH", None)
         runs.append((th1, th2, th3, x, v, step, nreb, {g: c[0] for g, c in prof.items()}))
     a, b = runs
-    # the force and virial sums take atomics in whatever order the blocks run: run-to-run noise of
-    # the FP32 sums of MIX-16 (not the replay) sets its tolerance
-    tol = 1e-9 if prec == "fp64" else 1e-3
-    for k in range(3):
-        np.testing.assert_allclose(b[k], a[k], rtol=tol, atol=tol * np.abs(a[k]).max())
-    np.testing.assert_allclose(b[3], a[3], rtol=0, atol=tol * box[0, 0])
-    np.testing.assert_allclose(b[4], a[4], rtol=0, atol=tol * np.abs(a[4]).max())
+    if prec == "fp64":
+        tol = 1e-9
+        for k in range(3):
+            np.testing.assert_allclose(b[k], a[k], rtol=tol, atol=tol * np.abs(a[k]).max())
+        np.testing.assert_allclose(b[3], a[3], rtol=0, atol=tol * box[0, 0])
+        np.testing.assert_allclose(b[4], a[4], rtol=0, atol=tol * np.abs(a[4]).max())
+    else:
+        # the force and virial sums take atomics in whatever order the blocks run, and a last-bit
+        # change of an FP32 value can flip the rounding of a 16-bit operand: run-to-run noise of
+        # MIX-16 (not the replay) sets the bound, on whole arrays
+        for k in (0, 1, 2, 4):
+            assert np.linalg.norm(b[k] - a[k]) <= 1e-3 * np.linalg.norm(a[k]), k
+        d = b[3] - a[3]
+        d -= box[0, 0] * np.rint(d / box[0, 0])
+        assert np.abs(d).max() < 1e-3   # A
     assert a[5] == b[5] == 17
     assert a[6] == b[6] and a[6] > 1          # rebuilds inside the replayed steps
     assert a[7] == b[7]

@@ -1,7 +1,7 @@
 """The FP64 kernels' tanh on the GPU against CUDA's tanh and the C library's.
 
 The device routine (degree-10 Taylor table, see test_tanh_table.py; the
-terms of degree 7-10, below 2^-34 of the result, summed in FP32) adds the
+terms of degree 6-10, below 2^-31 of the result, summed in FP32) adds the
 rounding of its Horner steps to the table's 0.77 ulp (about 1.1 ulp in all
 in a CPU emulation); CUDA's and the C library's tanh carry their own errors
 of about 1-2 ulp.  Agreement within
