@@ -6,6 +6,9 @@ binding with the same entry-point names, plus small owning wrappers.
 """
 from __future__ import annotations
 
+import atexit
+import weakref
+
 import numpy as np
 
 from . import _lib
@@ -24,12 +27,29 @@ def build(force: bool = False) -> str:
     return _build(force=force)
 
 
+# Live wrappers, released at interpreter exit in dependency order (MD states, then lists, then
+# models) while the library and the CUDA runtime are still intact: the module teardown of the
+# interpreter may otherwise destroy a model before the lists that refer to it.
+_LIVE = {"state": weakref.WeakSet(), "nlist": weakref.WeakSet(), "model": weakref.WeakSet()}
+
+
+@atexit.register
+def _release_all():
+    for kind in ("state", "nlist", "model"):
+        for obj in list(_LIVE[kind]):
+            try:
+                obj.close()
+            except Exception:
+                pass
+
+
 class Model:
     """Owning wrapper of a dp_model handle."""
 
     def __init__(self, cfg, seed: int = 0, params=None):
         self.cfg = cfg
         self.h = dp_model_create(cfg, seed)
+        _LIVE["model"].add(self)
         if params is not None:
             dp_model_set_params(self.h, params)
 
@@ -60,6 +80,7 @@ class NeighborList:
         self.model = model
         self.n = len(typ)
         self.h = dp_nlist_build(model.h, coord, typ, box, model.cfg.rcut if rcut is None else rcut, skin, cand_cap)
+        _LIVE["nlist"].add(self)
 
     @classmethod
     def frames(cls, model: Model, coords, typ, box, skin: float = 0.0, cand_cap: int = 0, rcut=None):
@@ -70,6 +91,7 @@ class NeighborList:
         self.n = coords.shape[0] * len(typ)
         self.h = dp_nlist_build_frames(model.h, coords, typ, box, model.cfg.rcut if rcut is None else rcut, skin,
                                        cand_cap)
+        _LIVE["nlist"].add(self)
         return self
 
     def update(self, coord, box):
@@ -100,6 +122,7 @@ class MDState:
         self.model = model
         self.n = len(typ)
         self.h = dp_md_state_create(model.h, coord, vel, typ, mass_by_type, box, skin, cand_cap)
+        _LIVE["state"].add(self)
 
     def step(self, nsteps: int, dt_fs: float, prec="fp64", thermo_every: int = 0):
         return dp_md_step(self.model.h, self.h, nsteps, dt_fs, prec, thermo_every)
