@@ -8,7 +8,7 @@ list rebuilt on the device when needed.  One step = half kick, drift,
 list check/rebuild, list formatting, energy/force/virial, half kick.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64]
-                  [--impl mine|reference] [--workload cu4000|cu108k|water192]
+                  [--impl mine|reference] [--workload cu4000|cu108k|water192|water12k]
 
 Prints one JSON line.  value = s/step/atom over the whole job (lower is
 better), timed with CUDA events on the library's stream, inputs resident
@@ -69,6 +69,16 @@ def workload(name: str, model: str = "full"):
     return cfg, coord, typ, box, mass, dt, desc
 
 
+# Initial temperature (K) and thermo interval (steps; None: one row at the end) of the timed MD.
+# water12k follows the paper's production protocol: 330 K, a thermo row every 20 steps (Sec. 5.1).
+MD_PROTOCOL = {"water12k": (330.0, 20)}
+
+
+def md_protocol(name: str, steps: int):
+    T, every = MD_PROTOCOL.get(name, (300.0, None))
+    return T, (every if every is not None and every <= steps else steps)
+
+
 def _workload(name: str):
     if name == "cu4000":
         cfg = dpsynth.copper_config()
@@ -80,6 +90,14 @@ def _workload(name: str):
         coord, typ, box = dpsynth.copper_fcc(1, ncell=30)
         mass = np.array([dpsynth.MASS["Cu"]])
         return cfg, coord, typ, box, mass, 1.0, "Cu FCC 30^3 cells, 108000 atoms, rcut 8, sel 512, 300 K, dt 1 fs"
+    if name == "water12k":
+        cfg = dpsynth.water_paper_config()
+        c, t, b = dpsynth.water_box(1)
+        coord, typ, box = dpsynth.replicate(c, t, b, (4, 4, 4))
+        mass = np.array([dpsynth.MASS["O"], dpsynth.MASS["H"]])
+        return cfg, coord, typ, box, mass, 0.5, ("4096 H2O (64-molecule box replicated 4x4x4), 12288 atoms, rcut 6, "
+                                                 "sel 48/96, nets 32-64-128 / 240-240-240 (the paper's water model "
+                                                 "and single-GPU system), 330 K, dt 0.5 fs, thermo every 20 steps")
     if name == "water192":
         cfg = dpsynth.water_config()
         coord, typ, box = dpsynth.water_box(1)
@@ -170,7 +188,8 @@ def run_mine(args, rank, world):
     torch.cuda.set_device(dev)
     cfg, coord, typ, box, mass, dt, desc = workload(args.workload, args.model)
     n = len(typ)
-    vel = dpsynth.velocities(mass[typ], 300.0, 1)
+    T0, thermo_every = md_protocol(args.workload, args.steps)
+    vel = dpsynth.velocities(mass[typ], T0, 1)
     model = dp.Model(cfg, seed=1)
     stream = torch.cuda.Stream(device=dev)
     dp.dp_model_set_stream(model.h, stream)
@@ -186,7 +205,7 @@ def run_mine(args, rank, world):
     dp.dp_profile_select(model.h, None)
     dp.dp_profile_enable(model.h, True)
     ev0.record(stream)
-    state.step(args.steps, dt, args.precision, thermo_every=args.steps)
+    state.step(args.steps, dt, args.precision, thermo_every=thermo_every)
     ev1.record(stream)
     torch.cuda.synchronize()
     ms_all = ev0.elapsed_time(ev1)
@@ -212,7 +231,7 @@ def run_mine(args, rank, world):
     time.sleep(0.3)
     dp.dp_profile_enable(model.h, True)
     ev0.record(stream)
-    th = state.step(args.steps, dt, args.precision, thermo_every=args.steps)
+    th = state.step(args.steps, dt, args.precision, thermo_every=thermo_every)
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
@@ -540,7 +559,7 @@ def cpu_baseline(args, budget_s=15.0):
     n = len(typ)
     params = dpsynth.model_params(cfg, 1)
     om = oracle.Model(cfg, params)
-    vel = dpsynth.velocities(mass[typ], 300.0, 1)
+    vel = dpsynth.velocities(mass[typ], md_protocol(args.workload, 1)[0], 1)
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
     om.md_nve(coord, vel, typ, mass, box, nsteps=1, dt=dt, thermo_every=0, nthreads=cores)
@@ -560,7 +579,7 @@ def run_reference(args, rank, world):
     cfg, coord, typ, box, mass, dt, desc = workload(args.workload, args.model)
     n = len(typ)
     om = oracle.Model(cfg, dpsynth.model_params(cfg, 1))
-    vel = dpsynth.velocities(mass[typ], 300.0, 1)
+    vel = dpsynth.velocities(mass[typ], md_protocol(args.workload, 1)[0], 1)
     cores = os.cpu_count() or 1
     x, v = coord, vel
     for _ in range(min(args.warmup, 1)):

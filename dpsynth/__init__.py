@@ -145,6 +145,13 @@ def water_config() -> ModelConfig:
     return ModelConfig(ntypes=2, rcut=6.0, rcut_smth=0.5, sel=(46, 92))
 
 
+def water_paper_config() -> ModelConfig:
+    """The paper's production water model (Sec. 5.1): r_c 6 A, 144 neighbors in all (read as O 48 /
+    H 96, the 1:2 split of the atom counts), embedding (32,64,128), fitting (240,240,240); r_cs 0.5 A
+    as in the water config."""
+    return ModelConfig(ntypes=2, rcut=6.0, rcut_smth=0.5, sel=(48, 96), embed=(32, 64, 128))
+
+
 def copper_config() -> ModelConfig:
     """Copper model: r_c 8 A, r_cs 2 A, sel 512, same net shapes, one type."""
     return ModelConfig(ntypes=1, rcut=8.0, rcut_smth=2.0, sel=(512,))

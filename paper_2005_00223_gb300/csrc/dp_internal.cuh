@@ -270,13 +270,16 @@ dp_status loss_terms_device(int64_t n, int64_t frame_n, const double *d_F, const
                             double *d_ab, double *d_lf, double *d_loss, cudaStream_t st);
 dp_status refresh_params_device(dp_model *m, cudaStream_t st);
 // FP64 products on the tensor cores (ozaki.cu): digits of the rows of an
-// FP64 matrix, and C = A B^T (+ bias) from the digits of A and of B.
+// FP64 matrix, and C = A B^T (+ bias) from the digits of A and of B, or
+// C += A B^T with accumulate (one more FP64 rounding: a product over a long
+// K is taken as a sum of products over K ranges, each with its own scales).
 template <int S, int BETA>
 dp_status oz_split(const double *X, int64_t ldx, int64_t rows, int64_t rows_pad, int K, int K_pad, int TR, int KC,
                    __half *dig, int *ex, cudaStream_t st);
 template <int S, int BETA, int NC, int KC>
 dp_status oz_gemm(const dp_model *m, int64_t M, int N, int K, const __half *dA, const int *eA, int64_t M_pad,
-                  const __half *dB, const int *eB, const double *bias, double *C, int64_t ldc, cudaStream_t st);
+                  const __half *dB, const int *eB, const double *bias, double *C, int64_t ldc, cudaStream_t st,
+                  bool accumulate = false);
 // Work list of the 32-neighbor chunks of positions [p0, p0 + nb) in tiles of
 // 4 chunks of one net (tc.cu): entry {atom, batch position, first slot,
 // net}, firstc [nb][ntypes], the tile count on the device.

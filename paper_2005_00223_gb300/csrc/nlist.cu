@@ -106,9 +106,15 @@ __global__ void k_cell_fill(int64_t n, const int32_t *cell_of, const int32_t *st
     atoms[start[c] + atomicAdd(&cursor[c], 1)] = (int32_t)i;
 }
 
-// One warp per atom: every j != i in the surrounding cells with
-// minimum-image distance < rlist.
-__global__ void k_candidates(int64_t n, const Pos4 *__restrict__ pos, BoxDev bx, double rlist,
+// One warp per atom: every j != i in the surrounding cells whose
+// minimum-image distance, in FP32 on the wrapped FP32 coordinates, is below
+// rlist + 2e-3 A.  The FP32 distance is within about 1e-4 A of the exact
+// one for boxes up to 400 A (coordinates rounded to 2^-24 L), so the list
+// holds every atom within
+// rlist (the skin criterion needs no more) plus a few just outside, which
+// the exact FP64 test of the formatting drops.
+__global__ void k_candidates(int64_t n, const Pos4 *__restrict__ pos, const float4 *__restrict__ posf, BoxDev bx,
+                             double rlist,
                              const int32_t *__restrict__ cell_of, const int32_t *__restrict__ start,
                              const int32_t *__restrict__ atoms, int32_t cap, int32_t *__restrict__ cand,
                              int32_t *__restrict__ cand_cnt, Pos4 *__restrict__ ref, int32_t *cell_cnt,
@@ -122,6 +128,10 @@ __global__ void k_candidates(int64_t n, const Pos4 *__restrict__ pos, BoxDev bx,
     const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
     const Pos4 pi = pos[i];
+    const float4 pf = posf[i];
+    const float Lf[3] = {(float)bx.L[0], (float)bx.L[1], (float)bx.L[2]};
+    const float iLf[3] = {(float)bx.invL[0], (float)bx.invL[1], (float)bx.invL[2]};
+    const float rpre = (float)rlist + 2e-3f;
     const int cf = cell_of[i];
     const int fbase = (cf / bx.ncell_f) * bx.ncell_f;      // first cell of this atom's frame
     const int c = cf - fbase;
@@ -149,8 +159,11 @@ __global__ void k_candidates(int64_t n, const Pos4 *__restrict__ pos, BoxDev bx,
                     if (p < s1) {
                         j = atoms[p];
                         if (j != i) {
-                            double d[3];
-                            ok = min_image_r(pi, pos[j], bx, d) < rlist;
+                            const float4 qf = posf[j];
+                            float df[3] = {qf.x - pf.x, qf.y - pf.y, qf.z - pf.z};
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) df[k] -= Lf[k] * rintf(df[k] * iLf[k]);
+                            ok = df[0] * df[0] + df[1] * df[1] + df[2] * df[2] < rpre * rpre;
                         }
                     }
                     unsigned m = __ballot_sync(0xffffffffu, ok);
@@ -178,34 +191,39 @@ __device__ __forceinline__ float d2f_rn(double v)
 }
 
 // Geometry record of a kept neighbor for the tensor-core path, from the
-// exact FP64 difference d and distance r: the switching function s(r) and
-// ds/dr, stored as FP32 (s, d/r) and (ds/dr, r).  The record is computed in
-// FP32 from the rounded r and d; only the two offsets r - r_cs and r - r_c
-// are taken in FP64, so that u = (r - r_cs)/(r_c - r_cs) and 1 - u keep
-// full relative precision at both ends of the switching region, and the
-// quintic is evaluated in the factored form 1 - 10u^3 + 15u^4 - 6u^5 =
-// (1 - u)^3 (1 + 3u + 6u^2), whose factors have no cancellation on [0, 1].
-// Each field is within a few FP32 ulps of its exact value.
+// exact FP64 difference d and distance r: the switching function s(r), its
+// derivative ds/dr and d/r evaluated in FP64 and stored rounded to FP32 as
+// (s, d/r) and (ds/dr, r).  1/r is the Newton-Raphson reciprocal in FP64
+// (y <- y + y (1 - r y), twice, from the FP32 reciprocal: the relative error
+// squares at each step, 2^-22 -> 2^-44 -> below the FP64 rounding), instead
+// of the general FP64 division; the quintic is evaluated in the factored
+// form 1 - 10u^3 + 15u^4 - 6u^5 = (1 - u)^3 (1 + 3u + 6u^2), with u and
+// 1 - u both taken from r directly, so neither end of the switching region
+// loses precision to cancellation.  The FP32 roundings use integer
+// instructions (d2f_rn), not the FP64 pipe.
 __device__ __forceinline__ void env_record(const double d[3], double r, const ModelDev &md, float4 &ra, float2 &rb)
 {
-    const float rf = d2f_rn(r);
-    const float irf = __frcp_rn(rf);
-    float s, ds;
+    const unsigned y0 = __float_as_uint(__frcp_rn(d2f_rn(r)));   // normal for 2^-126 < r < 2^126
+    double ir = __longlong_as_double((long long)(((unsigned long long)(y0 & 0x80000000u) << 32) |
+                                                 ((unsigned long long)(((y0 >> 23) & 0xffu) - 127 + 1023) << 52) |
+                                                 ((unsigned long long)(y0 & 0x7fffffu) << 29)));   // exact widening
+    ir = fma(ir, fma(-r, ir, 1.0), ir);
+    ir = fma(ir, fma(-r, ir, 1.0), ir);
+    double s, ds;
     if (r < md.rcs) {
-        s = irf;
-        ds = -irf * irf;
+        s = ir;
+        ds = -ir * ir;
     } else {
-        const float isw = d2f_rn(md.inv_sw);
-        const float u = d2f_rn(__dsub_rn(r, md.rcs)) * isw;
-        const float um = d2f_rn(__dsub_rn(md.rcut, r)) * isw;   // 1 - u
-        const float u2 = u * u, um2 = um * um;
-        const float poly = um2 * um * fmaf(fmaf(6.0f, u, 3.0f), u, 1.0f);
-        const float dpoly = -30.0f * isw * u2 * um2;
-        s = poly * irf;
-        ds = (dpoly - s) * irf;
+        const double u = (r - md.rcs) * md.inv_sw;
+        const double um = (md.rcut - r) * md.inv_sw;   // 1 - u
+        const double um2 = um * um;
+        const double poly = um2 * um * fma(fma(6.0, u, 3.0), u, 1.0);
+        const double dpoly = (-30.0 * md.inv_sw) * (u * u) * um2;
+        s = poly * ir;
+        ds = (dpoly - s) * ir;
     }
-    ra = make_float4(s, d2f_rn(d[0]) * irf, d2f_rn(d[1]) * irf, d2f_rn(d[2]) * irf);
-    rb = make_float2(ds, rf);
+    ra = make_float4(d2f_rn(s), d2f_rn(d[0] * ir), d2f_rn(d[1] * ir), d2f_rn(d[2] * ir));
+    rb = make_float2(d2f_rn(ds), d2f_rn(r));
 }
 
 constexpr int kRecStage = 256;   // kept neighbors per atom whose records are staged in shared memory
@@ -377,7 +395,8 @@ dp_status nlist_build_device(dp_nlist *nl, cudaStream_t st, bool conditional)
                                                               nl->d_cell_cnt, nl->d_cell_start, nl->d_flags, cond);
     k_cell_fill<<<blocks_for(nl->n, 256), 256, 0, st>>>(nl->n, nl->d_cell_of, nl->d_cell_start, nl->d_cell_cnt,
                                                        nl->d_cell_atoms, nl->d_flags, cond);
-    k_candidates<<<blocks_for(nl->n * 32, 256), 256, 0, st>>>(nl->n, pos, bx, nl->rlist, nl->d_cell_of,
+    k_candidates<<<blocks_for(nl->n * 32, 256), 256, 0, st>>>(nl->n, pos, (const float4 *)nl->d_posf, bx, nl->rlist,
+                                                             nl->d_cell_of,
                                                              nl->d_cell_start, nl->d_cell_atoms, nl->cap,
                                                              nl->d_cand, nl->d_cand_cnt, (Pos4 *)nl->d_ref,
                                                              nl->d_cell_cnt, nl->ncell, nl->d_flags, cond);

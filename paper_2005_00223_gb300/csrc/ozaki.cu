@@ -44,7 +44,7 @@ __global__ void k_oz_split(const double *__restrict__ X, int64_t ldx, int64_t ro
     }
 }
 
-// C [M][N] (leading dimension ldc) = value (+ bias [N]).
+// C [M][N] (leading dimension ldc) = value (+ bias [N]), or C += value.
 template <class Sh>
 struct PlainEpi {
     const __half *dB;
@@ -53,6 +53,7 @@ struct PlainEpi {
     const double *bias;
     double *C;
     int64_t ldc, M;
+    bool acc;
     __device__ const __half *b_unit(int64_t, int nchunk) const
     {
         return dB + (int64_t)nchunk * nk * Sh::S * Sh::NC * Sh::KC;
@@ -70,7 +71,7 @@ struct PlainEpi {
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
                     const double y = oz::acc_value<Sh>(H[c], L[c], er + eB[n0 + c0 + c]);
-                    out[c] = bias ? y + bias[n0 + c0 + c] : y;
+                    out[c] = acc ? out[c] + y : (bias ? y + bias[n0 + c0 + c] : y);
                 }
             }
         }
@@ -102,7 +103,8 @@ dp_status oz_split(const double *X, int64_t ldx, int64_t rows, int64_t rows_pad,
 // for NC rows and KC columns, scales eB [N]).
 template <int S, int BETA, int NC, int KC>
 dp_status oz_gemm(const dp_model *m, int64_t M, int N, int K, const __half *dA, const int *eA, int64_t M_pad,
-                  const __half *dB, const int *eB, const double *bias, double *C, int64_t ldc, cudaStream_t st)
+                  const __half *dB, const int *eB, const double *bias, double *C, int64_t ldc, cudaStream_t st,
+                  bool accumulate)
 {
     using Sh = oz::Shape<S, BETA, NC, KC>;
     if (M == 0) return DP_OK;
@@ -118,7 +120,7 @@ dp_status oz_gemm(const dp_model *m, int64_t M, int N, int K, const __half *dA, 
     DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
     const int64_t units = (M_pad / 128) * (N / NC);
     const unsigned grid = (unsigned)(units < nsm ? units : nsm);
-    PlainEpi<Sh> epi{dB, K / KC, eA, eB, bias, C, ldc, M};
+    PlainEpi<Sh> epi{dB, K / KC, eA, eB, bias, C, ldc, M, accumulate};
     auto kern = oz::k_gemm<Sh, PlainEpi<Sh>>;
     static bool attrs_set = false;   // per instantiation: once per process
     if (!attrs_set) {
@@ -141,10 +143,10 @@ template dp_status oz_split<8, 7>(const double *, int64_t, int64_t, int64_t, int
                                   cudaStream_t);
 template dp_status oz_gemm<9, 6, 48, 16>(const dp_model *, int64_t, int, int, const __half *, const int *, int64_t,
                                          const __half *, const int *, const double *, double *, int64_t,
-                                         cudaStream_t);
+                                         cudaStream_t, bool);
 template dp_status oz_gemm<8, 7, 64, 16>(const dp_model *, int64_t, int, int, const __half *, const int *, int64_t,
                                          const __half *, const int *, const double *, double *, int64_t,
-                                         cudaStream_t);
+                                         cudaStream_t, bool);
 
 }  // namespace dp
 

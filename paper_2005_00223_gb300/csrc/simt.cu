@@ -667,10 +667,20 @@ int64_t oz_min_atoms()
     return v ? atoll(v) : 1024;
 }
 
+// z1 = D W1 over K = nd is taken in kp ranges of kh columns (the last one
+// shorter), each at most 1808 long so that its FP32 digit sums stay exact
+// (9 digits of 6 bits: 9 K 2^10 <= 2^24), and summed in FP64.
+int oz_kparts(int nd, int *kh)
+{
+    const int kp = (nd + 1807) / 1808;
+    *kh = ((nd + kp - 1) / kp + 15) / 16 * 16;
+    return kp;
+}
+
 bool oz_fit_ok(const ModelDev &md)
 {
     const int f0 = md.fit.wout[0], nd = md.desc_dim;
-    return f0 % 48 == 0 && f0 <= 256 && nd % 64 == 0 && nd <= 1808 && getenv("DP_NO_OZAKI") == nullptr;
+    return f0 % 48 == 0 && f0 <= 256 && nd % 64 == 0 && getenv("DP_NO_OZAKI") == nullptr;
 }
 
 size_t oz_weight_halves(const ModelDev &md)
@@ -682,18 +692,24 @@ dp_status oz_refresh_weights(dp_model *m, cudaStream_t st)
 {
     const ModelDev &md = m->dev;
     const int f0 = md.fit.wout[0], nd = md.desc_dim;
+    int kh;
+    const int kp = oz_kparts(nd, &kh);
     if (!m->d_ozw) {
         DP_CUDA(cudaMalloc(&m->d_ozw, sizeof(__half) * oz_weight_halves(md) * md.ntypes));
-        DP_CUDA(cudaMalloc((void **)&m->d_oze, sizeof(int) * (size_t)(f0 + nd) * md.ntypes));
+        DP_CUDA(cudaMalloc((void **)&m->d_oze, sizeof(int) * (size_t)(kp * f0 + nd) * md.ntypes));
         ++m->epoch;
         m->oz_stale = true;
     }
     if (!m->oz_stale) return DP_OK;
     for (int t = 0; t < md.ntypes; ++t) {
         __half *wf = (__half *)m->d_ozw + oz_weight_halves(md) * t, *wb = wf + (size_t)kOzSF * f0 * nd;
-        int *ef = m->d_oze + (size_t)(f0 + nd) * t, *eb = ef + f0;
+        int *ef = m->d_oze + (size_t)(kp * f0 + nd) * t, *eb = ef + kp * f0;
         const int64_t W0 = md.fit_base + (int64_t)t * md.fit.size + md.fit.W[0];
-        DP_TRY((oz_split<kOzSF, kOzBF>(md.pT + W0, nd, f0, f0, nd, nd, 48, 16, wf, ef, st)));   // rows of W1^T
+        for (int q = 0, k0 = 0; q < kp; ++q, k0 += kh) {   // rows of W1^T, per K range
+            const int kq = nd - k0 < kh ? nd - k0 : kh;
+            DP_TRY((oz_split<kOzSF, kOzBF>(md.pT + W0 + k0, nd, f0, f0, kq, kq, 48, 16, wf + (size_t)kOzSF * f0 * k0,
+                                           ef + q * f0, st)));
+        }
         DP_TRY((oz_split<kOzSB, kOzBB>(md.p + W0, f0, nd, nd, f0, f0, 64, 16, wb, eb, st)));    // rows of W1
     }
     m->oz_stale = false;
@@ -720,17 +736,23 @@ dp_status fit_fp64_oz(dp_model *m, dp_nlist *nl, int t, int64_t p0, int64_t b, i
         scratch += (bytes + 255) & ~(size_t)255;
         return p;
     };
-    __half *da = (__half *)carve(sizeof(__half) * rows_pad * kOzSF * nd);
+    int kh;
+    const int kp = oz_kparts(nd, &kh);
+    __half *da = (__half *)carve(sizeof(__half) * rows_pad * kOzSF * kh);
     __half *db = (__half *)carve(sizeof(__half) * rows_pad * kOzSB * f0);
     int *ea = (int *)carve(sizeof(int) * rows_pad), *eb = (int *)carve(sizeof(int) * rows_pad);
     double *z1 = (double *)carve(sizeof(double) * count * f0), *dz1 = (double *)carve(sizeof(double) * count * f0);
     const __half *wf = (const __half *)m->d_ozw + oz_weight_halves(md) * t, *wb = wf + (size_t)kOzSF * f0 * nd;
-    const int *ef = m->d_oze + (size_t)(f0 + nd) * t, *eb2 = ef + f0;
+    const int *ef = m->d_oze + (size_t)(kp * f0 + nd) * t, *eb2 = ef + kp * f0;
     const double *b1 = md.p + md.fit_base + (int64_t)t * md.fit.size + md.fit.b[0];
     const bool chain = oz_fit_chain_ok(md);
-    ProfScope ps(m->prof, PG_FIT, chain ? 13 : 5, st);
-    DP_TRY((oz_split<kOzSF, kOzBF>(D + (b - p0) * nd, nd, count, rows_pad, nd, nd, 128, 16, da, ea, st)));
-    DP_TRY((oz_gemm<kOzSF, kOzBF, 48, 16>(m, count, f0, nd, da, ea, rows_pad, wf, ef, b1, z1, f0, st)));
+    ProfScope ps(m->prof, PG_FIT, (chain ? 13 : 5) + 2 * (kp - 1), st);
+    for (int q = 0, k0 = 0; q < kp; ++q, k0 += kh) {   // z1 = sum over the K ranges, the bias with the first
+        const int kq = nd - k0 < kh ? nd - k0 : kh;
+        DP_TRY((oz_split<kOzSF, kOzBF>(D + (b - p0) * nd + k0, nd, count, rows_pad, kq, kq, 128, 16, da, ea, st)));
+        DP_TRY((oz_gemm<kOzSF, kOzBF, 48, 16>(m, count, f0, kq, da, ea, rows_pad, wf + (size_t)kOzSF * f0 * k0,
+                                              ef + q * f0, b1, z1, f0, st, q > 0)));
+    }
     if (chain)   // the hidden layers after the first as split products too
         DP_TRY(oz_fit_chain(m, t, nl->d_order, b, count, z1, dz1, E_atom, scratch, st));
     else

@@ -3,13 +3,11 @@
 // fp16 or bf16 operands in shared memory and FP32 accumulators in tensor
 // memory; the first embedding layer (K = 1, too small for the tensor cores),
 // tanh and its derivative run in FP32 on the CUDA cores, as the paper does.
-// The minimum image and the distance are evaluated in FP64 once per
-// evaluation by the formatting kernel, which stores (s, u = d/r) and
-// (ds/dr, r) per neighbor slot as FP32 (the switching function from the
-// FP64 distance in FP32 arithmetic, within a few FP32 ulps, far below the
-// 16-bit operands these values feed); here the environment row R = (s, s u)
-// and the chain dE/dR -> g_ij run in FP32, and the force / virial
-// accumulation is FP64.
+// The minimum image, the distance and the switching function s(r), ds/dr are
+// evaluated in FP64 once per evaluation by the formatting kernel, which
+// stores (s, u = d/r) and (ds/dr, r) per neighbor slot as FP32; here the
+// environment row R = (s, s u) and the chain dE/dR -> g_ij run in FP32, and
+// the force / virial accumulation is FP64.
 //
 // Work unit: a tile of 128 neighbor rows = 4 chunks of 32 rows, one chunk per
 // warp; every chunk is up to 32 neighbors of one type of one atom, and the 4
@@ -123,7 +121,7 @@ struct TileCtx {
 // One thread's row of a tile as read from global memory: the chunk entry,
 // the neighbor count of its (atom, type) block and the slot's neighbor
 // geometry (s, u = d/r and, for the backward pass, ds/dr, r and j; all
-// from the FP64 minimum image of the formatting kernel).  Fetched one tile ahead: the
+// evaluated in FP64 by the formatting kernel).  Fetched one tile ahead: the
 // slot loads do not wait for the count (they stay inside the type block's
 // sel slots), and the row's validity is applied when it is used.
 struct RowIn {

@@ -81,6 +81,32 @@ def test_mix16_tensor_core_error_budget(dp, orc, prec, name, cfg, coord, typ, bo
     assert err["W_rel"] < 10 * u
 
 
+@pytest.mark.parametrize("prec", ["mix32", "bf16", "fp16"])
+def test_paper_water_model_error_budget(dp, orc, prec):
+    """The paper's production water model (embedding 32-64-128, 144 neighbors, Sec. 5.1) on the
+    mixed schemes: the 32-64-128 tensor-core embedding and 2048-wide fitting kernels against the
+    oracle, with the budgets above."""
+    cfg = dpsynth.water_paper_config()
+    coord, typ, box = dpsynth.water_box(4)
+    m = dp.Model(cfg, 1, params=dpsynth.model_params(cfg, 3))
+    nl = dp.NeighborList(m, coord, typ, box)
+    got = nl.compute(coord, box, prec)
+    ref = orc.Model(cfg, m.params).compute(coord, typ, box)
+    err = _errors(got, ref)
+    print("water192 paper model", prec, err)
+    assert np.isfinite(got[2]).all()
+    if prec == "mix32":
+        assert err["dE_rel"] < 1e-6 and err["dEi_max_rel"] < 1e-5
+        assert err["F_rmse_rel"] < 1e-5 and err["W_rel"] < 1e-5
+    else:
+        u = 2.0 ** -9 if prec == "bf16" else 2.0 ** -11
+        assert err["dE_per_sum_abs_Ei"] < 2 * u
+        assert err["dEi_max_rel"] < 4 * u
+        assert err["F_rmse_rel"] < 10 * u
+        assert err["W_rel"] < 10 * u
+    nl.close()
+
+
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 def test_mix16_student_shape_and_md(dp, prec):
     cfg = dpsynth.copper_student_config()
