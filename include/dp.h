@@ -301,7 +301,12 @@ dp_status dp_md_state_create(dp_model *m, int64_t n, const double *coord, const 
  * every thermo_every-th step one row (KE eV, PE eV, T K, P bar) is written
  * to thermo [nsteps/thermo_every][4] (NULL or thermo_every <= 0: none); T
  * uses 3n - 3 degrees of freedom and P = (2 KE + tr W)/(3V).  The host
- * synchronises once at the end.  Errors: as dp_compute, plus
+ * synchronises once at the end.  After the first step of a call the steps
+ * are replays of one captured step (a CUDA graph kept in the state and
+ * captured again when the precision, dt, the profiling selection, the
+ * model's buffers or parameters, or the DP_NO_OZAKI / DP_OZ_MIN_ATOMS /
+ * DP_SIMT_FIT / DP_BATCH_ATOMS switches change); DP_NO_GRAPH=1 launches
+ * every step directly.  Errors: as dp_compute, plus
  * DP_ERR_CAPACITY when a rebuild overflowed the candidate capacity (the
  * steps after the overflow used truncated lists and are not valid: create
  * the state again with a larger cand_cap). */
