@@ -72,7 +72,7 @@ struct ModelDev {
 
 // Kernel launch groups timed by the tracing calls (dp_profile_*).
 enum ProfGroup {
-    PG_BUILD = 0,     // cell grid and skin candidates (5 kernels)
+    PG_BUILD = 0,     // cell grid and skin candidates (3 kernels)
     PG_FORMAT,        // neighbor-list formatting
     PG_PACK,          // coordinate packing
     PG_EMBED_FWD,     // environment rows + embedding net + descriptor

@@ -71,6 +71,24 @@ struct TcShape {
     static constexpr uint32_t BWD_SCRATCH = 4 * 4 * E2 * 4;
     // at most two CTAs per SM (each holds 256 TMEM columns of the SM's 512)
     static constexpr uint32_t FWD_SMEM = GT_OFF + FWD_SCRATCH > 80 * 1024 ? GT_OFF + FWD_SCRATCH : 80 * 1024;
+    // Forward kernel layout: only W2^T, W3^T and the vectors of the image, then one region that holds
+    // A2 and A3 until the layer-3 MMA has read them and G^T afterwards (R^T after it); tensor memory
+    // reused layer by layer (z2, then z3, then the four chunks' T, all from column 0).
+    static constexpr uint32_t VEC_BYTES = (2 * K2 + N2 + N3) * 4;
+    static constexpr uint32_t F_VEC_OFF = B3B_OFF;
+    static constexpr uint32_t F_IMG = (F_VEC_OFF + VEC_BYTES + 1023) / 1024 * 1024;
+    static constexpr uint32_t F_A2_OFF = F_IMG, F_A3_OFF = F_A2_OFF + 128 * K2 * 2;
+    static constexpr uint32_t F_GT_OFF = F_IMG, F_RT_OFF = F_GT_OFF + 128 * 128 * 2;
+    static constexpr uint32_t F_ACT = 128 * K2 * 2 + 128 * N2 * 2;
+    static constexpr uint32_t F_CON = 128 * 128 * 2 + 16 * 128 * 2;
+    static constexpr uint32_t F_SMEM = F_IMG + (F_ACT > F_CON ? F_ACT : F_CON);
+    static constexpr uint32_t F_MAXC = (N2 > N3 ? N2 : N3) > 64 ? (N2 > N3 ? N2 : N3) : 64;
+    static constexpr uint32_t F_TCOLS = F_MAXC <= 32 ? 32 : F_MAXC <= 64 ? 64 : F_MAXC <= 128 ? 128 : 256;
+    static constexpr int F_BY_SMEM = (int)((227 * 1024) / (F_SMEM + 1024 + 256));   // + reserved + static
+    static constexpr int F_CTAS = F_BY_SMEM < 4 ? (F_BY_SMEM < (int)(512 / F_TCOLS) ? F_BY_SMEM : (int)(512 / F_TCOLS))
+                                                : (4 < (int)(512 / F_TCOLS) ? 4 : (int)(512 / F_TCOLS));
+    static_assert(F_RT_OFF + 16 * 128 * 2 <= F_SMEM && F_A3_OFF + 128 * N2 * 2 <= F_SMEM && F_CTAS >= 2,
+                  "forward layout");
     static constexpr uint32_t BWD_SMEM = X_OFF + BWD_SCRATCH > 80 * 1024 ? X_OFF + BWD_SCRATCH : 80 * 1024;
     static constexpr uint32_t TCOL = N2 + N3;                          // TMEM columns of the 4 chunks' T
     static_assert(N2 + N3 + 64 <= kTmemCols, "TMEM columns");
@@ -243,24 +261,22 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const 
                                                             const unsigned char *__restrict__ wimg,
                                                             float *__restrict__ T, int *err)
 {
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];   // no-swizzle operands and bulk copies: 16 B
     __shared__ __align__(8) uint64_t mbar_mma, mbar_w;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char *img = smem;
-    unsigned char *A2 = smem + S::A2_OFF;
-    unsigned char *A3 = smem + S::A3_OFF;
-    unsigned char *GT = smem + S::GT_OFF;
-    unsigned char *RT = smem + S::RT_OFF;
-    const float *vec = reinterpret_cast<const float *>(img + S::VEC_OFF);
-    for (int q = tid; q < (int)(S::FWD_SCRATCH / 16); q += kTcThreads)
-        reinterpret_cast<uint4 *>(GT)[q] = make_uint4(0u, 0u, 0u, 0u);
+    unsigned char *A2 = smem + S::F_A2_OFF;
+    unsigned char *A3 = smem + S::F_A3_OFF;
+    unsigned char *GT = smem + S::F_GT_OFF;   // over A2 and A3 (dead once the layer-3 MMA completed)
+    unsigned char *RT = smem + S::F_RT_OFF;
+    const float *vec = reinterpret_cast<const float *>(img + S::F_VEC_OFF);
     if (tid == 0) {
         tc::mbar_init(&mbar_mma, 1);
         tc::mbar_init(&mbar_w, 1);
         tc::mbar_init_fence();
     }
-    if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
+    if (warp == 0) tc::tmem_alloc(&tmem_base, S::F_TCOLS);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -278,9 +294,10 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const 
         const int net = in.net;
         const TileCtx ch = in.ch;
         if (net != cur_net) {
-            if (tid == 0) {
-                tc::mbar_expect_tx(&mbar_w, S::IMG);
-                tc::bulk_g2s(img, wimg + (size_t)net * S::IMG, S::IMG, &mbar_w);
+            if (tid == 0) {   // W2^T and W3^T, then the vectors right after them
+                tc::mbar_expect_tx(&mbar_w, S::B3B_OFF + S::VEC_BYTES);
+                tc::bulk_g2s(img, wimg + (size_t)net * S::IMG, S::B3B_OFF, &mbar_w);
+                tc::bulk_g2s(img + S::F_VEC_OFF, wimg + (size_t)net * S::IMG + S::VEC_OFF, S::VEC_BYTES, &mbar_w);
             }
             bool ok = tc::mbar_wait(&mbar_w, ph_w, kWaitLimit);
             ph_w ^= 1;
@@ -315,7 +332,7 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const 
         __syncthreads();
         if (tid == 0) {
             tc::fence_after_sync();
-            tc::mma_kloop(tmem + S::N2, tc::smem_u32(A3), tc::smem_u32(img + S::B3_OFF), S::N2, id3);
+            tc::mma_kloop(tmem, tc::smem_u32(A3), tc::smem_u32(img + S::B3_OFF), S::N2, id3);
             tc::mma_commit(&mbar_mma);
         }
         ok = tc::mbar_wait(&mbar_mma, ph_mma, kWaitLimit);
@@ -332,12 +349,18 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const 
             float y2[S::E1];
 #pragma unroll
             for (int k = 0; k < S::E1; ++k) y2[k] = skip_of<S::E0, S::E1>(t1, k) + t2[k];
+            // the row's R^T entries c = 0..15 (c >= 4 zero) and G^T entries m = 0..127 (m >= E2 zero)
+            // are all rewritten each tile: the region held A2 and A3 before
             *reinterpret_cast<uint4 *>(RT + tc::mnmaj_off(0, tid, 16)) =
                 make_uint4(pack2<0>(Rf[0], Rf[1]), pack2<0>(Rf[2], Rf[3]), 0u, 0u);
+            *reinterpret_cast<uint4 *>(RT + tc::mnmaj_off(8, tid, 16)) = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int c0 = S::N3; c0 < 128; c0 += 8)
+                *reinterpret_cast<uint4 *>(GT + tc::mnmaj_off(c0, tid, 128)) = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
             for (int c0 = 0; c0 < S::N3; c0 += 16) {
                 float z[16];
-                tc::tmem_ld16(taddr + S::N2 + c0, z);
+                tc::tmem_ld16(taddr + c0, z);
                 tc::tmem_ld_wait();
                 float g[16];
 #pragma unroll
@@ -359,8 +382,8 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const 
             // chunk q: T_q[m][c] = sum over its 32 rows of G[row][m] R[row][c]
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                tc::mma_kloop_mn(tmem + S::TCOL + 16 * q, tc::smem_u32(GT), 128, tc::smem_u32(RT), 16, 32 * q, 32,
-                                 idT, false);
+                tc::mma_kloop_mn(tmem + 16 * q, tc::smem_u32(GT), 128, tc::smem_u32(RT), 16, 32 * q, 32, idT,
+                                 false);
             tc::mma_commit(&mbar_mma);
         }
         ok = tc::mbar_wait(&mbar_mma, ph_mma, kWaitLimit);
@@ -376,7 +399,7 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const 
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 float v[4];
-                tc::tmem_ld4(taddr + S::TCOL + 16 * q, v);
+                tc::tmem_ld4(taddr + 16 * q, v);
                 tc::tmem_ld_wait();
                 const int atom = load_chunk(chunks, (int64_t)tile * 4 + q).x;
                 if (atom >= 0 && m < S::E2) {
@@ -392,7 +415,7 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const 
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+    if (warp == 0) tc::tmem_dealloc(tmem, S::F_TCOLS);
 }
 
 template <class S, int BF>
@@ -1388,11 +1411,12 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
                                               cb_gtab, chunks, nullptr);
     }
     DP_CUDA(cudaGetLastError());
-    DP_CUDA(cudaFuncSetAttribute(k_embed_fwd_tc<S, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::FWD_SMEM));
+    DP_CUDA(cudaFuncSetAttribute(k_embed_fwd_tc<S, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::F_SMEM));
+    DP_CUDA(cudaFuncSetAttribute(k_embed_fwd_tc<S, BF>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     DP_CUDA(cudaFuncSetAttribute(k_embed_bwd_tc<S, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::BWD_SMEM));
     {
         ProfScope ps(m->prof, PG_EMBED_FWD, 1, st);
-        k_embed_fwd_tc<S, BF><<<grid, kTcThreads, S::FWD_SMEM, st>>>(md, envA, nl->d_nlist, nl->d_nnei, chunks,
+        k_embed_fwd_tc<S, BF><<<(unsigned)(S::F_CTAS * nsm), kTcThreads, S::F_SMEM, st>>>(md, envA, nl->d_nlist, nl->d_nnei, chunks,
                                                                      cnt, wimg, T, m->d_err);
     }
     DP_CUDA(cudaGetLastError());
