@@ -90,6 +90,20 @@ struct TcShape {
     static_assert(F_RT_OFF + 16 * 128 * 2 <= F_SMEM && F_A3_OFF + 128 * N2 * 2 <= F_SMEM && F_CTAS >= 2,
                   "forward layout");
     static constexpr uint32_t BWD_SMEM = X_OFF + BWD_SCRATCH > 80 * 1024 ? X_OFF + BWD_SCRATCH : 80 * 1024;
+    // Backward kernel layout: the full image, then one region that holds A2 and A3 (the forward
+    // recomputation) until the layer-3 MMA has read them, dz3 (AB1) from the layer-3 epilogue until
+    // the dY2 MMA has read it, and dz2 in A3's place after that; then dE/dT per warp. Tensor memory
+    // reused from column 0 by every product; the skip terms of dY2 and dY1 are stored into the
+    // accumulator before their MMA, which adds onto them.
+    static constexpr uint32_t B_IMG = (IMG + 127) / 128 * 128;
+    static constexpr uint32_t B_A2_OFF = B_IMG, B_A3_OFF = B_A2_OFF + 128 * K2 * 2, B_AB1_OFF = B_IMG;
+    static constexpr uint32_t B_ACT = F_ACT > 128 * N3 * 2 ? F_ACT : 128 * N3 * 2;
+    static constexpr uint32_t B_X_OFF = B_IMG + B_ACT;
+    static constexpr uint32_t B_SMEM = B_X_OFF + BWD_SCRATCH;
+    static constexpr int B_BY_SMEM = (int)((227 * 1024) / (B_SMEM + 1024 + 256));
+    static constexpr int B_CTAS = B_BY_SMEM < 3 ? (B_BY_SMEM < (int)(512 / F_TCOLS) ? B_BY_SMEM : (int)(512 / F_TCOLS))
+                                                : (3 < (int)(512 / F_TCOLS) ? 3 : (int)(512 / F_TCOLS));
+    static_assert(B_CTAS >= 2 && B_A3_OFF + 128 * N2 * 2 <= B_X_OFF, "backward layout");
     static constexpr uint32_t TCOL = N2 + N3;                          // TMEM columns of the 4 chunks' T
     static_assert(N2 + N3 + 64 <= kTmemCols, "TMEM columns");
     static_assert(N3 <= 128 && 2 * FWD_SMEM <= 227 * 1024, "forward tile");
@@ -419,7 +433,7 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const 
 }
 
 template <class S, int BF>
-__global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, const float4 *__restrict__ envA,
+__global__ void __launch_bounds__(kTcThreads, S::B_CTAS >= 3 ? 3 : 1) k_embed_bwd_tc(ModelDev md, const float4 *__restrict__ envA,
                                                             const float2 *__restrict__ envB,
                                                             const int32_t *__restrict__ nlist,
                                                             const int32_t *__restrict__ nnei,
@@ -429,22 +443,28 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, const 
                                                             const float *__restrict__ dT, double *__restrict__ force,
                                                             double *__restrict__ atom_virial, int *err)
 {
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];   // no-swizzle operands and bulk copies: 16 B
     __shared__ __align__(8) uint64_t mbar_mma, mbar_w;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char *img = smem;
-    unsigned char *A2 = smem + S::A2_OFF;
-    unsigned char *A3 = smem + S::A3_OFF;     // forward layer-3 input, then dz2
-    unsigned char *AB1 = smem + S::AB1_OFF;   // dz3
-    float *sdT = reinterpret_cast<float *>(smem + S::X_OFF) + warp * 4 * S::E2;
+    unsigned char *A2 = smem + S::B_A2_OFF;
+    unsigned char *A3 = smem + S::B_A3_OFF;     // forward layer-3 input, then dz2
+    unsigned char *AB1 = smem + S::B_AB1_OFF;   // dz3, over A2 and A3
+    float *sdT = reinterpret_cast<float *>(smem + S::B_X_OFF) + warp * 4 * S::E2;
     const float *vec = reinterpret_cast<const float *>(img + S::VEC_OFF);
     if (tid == 0) {
         tc::mbar_init(&mbar_mma, 1);
         tc::mbar_init(&mbar_w, 1);
         tc::mbar_init_fence();
     }
-    if (warp == 0) tc::tmem_alloc(&tmem_base, kTmemCols);
+    // With three CTAs per SM (128 TMEM columns each) every product starts at column 0 and the skip
+    // terms of dY2 and dY1 go into the accumulator before their MMA; with two, the layer-3 and dY1
+    // products sit after column N2 and the skip terms stay in registers (fewer TMEM round trips)
+    constexpr bool kRes = S::B_CTAS >= 3;
+    constexpr uint32_t kCols = kRes ? S::F_TCOLS : (uint32_t)kTmemCols;
+    constexpr uint32_t kHi = kRes ? 0u : (uint32_t)S::N2;   // column of the layer-3 and dY1 products
+    if (warp == 0) tc::tmem_alloc(&tmem_base, kCols);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -501,7 +521,7 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, const 
         __syncthreads();
         if (tid == 0) {
             tc::fence_after_sync();
-            tc::mma_kloop(tmem + S::N2, tc::smem_u32(A3), tc::smem_u32(img + S::B3_OFF), S::N2, id3);
+            tc::mma_kloop(tmem + kHi, tc::smem_u32(A3), tc::smem_u32(img + S::B3_OFF), S::N2, id3);
             tc::mma_commit(&mbar_mma);
         }
         ok = tc::mbar_wait(&mbar_mma, ph_mma, kWaitLimit);
@@ -514,18 +534,20 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, const 
         // layer-3 epilogue fused with the start of the backward pass:
         //   G = skip(y2) + t3,  dG = dT R,  dR += dT^T G,  dz3 = dG (1 - t3^2)
         float dR[4] = {0.f, 0.f, 0.f, 0.f};
-        float res2[S::E1];
+        float res2[S::E1];   // skip terms of dE/dy2
 #pragma unroll
         for (int k = 0; k < S::E1; ++k) res2[k] = 0.f;
         {
             const float *b3 = vec + 2 * S::K2 + S::N2;
-            float y2[S::E1];
+            float y2[kRes ? 1 : S::E1];   // with two CTAs per SM the layer-2 outputs are materialised
+            if constexpr (!kRes) {
 #pragma unroll
-            for (int k = 0; k < S::E1; ++k) y2[k] = skip_of<S::E0, S::E1>(t1, k) + t2[k];
+                for (int k = 0; k < S::E1; ++k) y2[k] = skip_of<S::E0, S::E1>(t1, k) + t2[k];
+            }
 #pragma unroll
             for (int c0 = 0; c0 < S::N3; c0 += 16) {
                 float z[16];
-                tc::tmem_ld16(taddr + S::N2 + c0, z);
+                tc::tmem_ld16(taddr + kHi + c0, z);
                 tc::tmem_ld_wait();
                 float buf[16];
 #pragma unroll
@@ -534,7 +556,18 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, const 
                     float v = 0.f;
                     if (m < S::E2) {
                         const float t = tc::tanh_fast(z[u] + b3[m]);
-                        const float G = skip_of<S::E1, S::E2>(y2, m) + t;
+                        // skip of layer 3 from y2 = skip(t1) + t2 (with three CTAs per SM evaluated
+                        // where it is used)
+                        float sk = 0.f;
+                        if constexpr (kRes) {
+                            if (S::E2 == S::E1 || S::E2 == 2 * S::E1) {
+                                const int k2 = m % S::E1;
+                                sk = skip_of<S::E0, S::E1>(t1, k2) + t2[k2];
+                            }
+                        } else {
+                            sk = skip_of<S::E1, S::E2>(y2, m);
+                        }
+                        const float G = sk + t;
                         const float4 dt = *reinterpret_cast<const float4 *>(sdT + 4 * m);
                         dR[0] = fmaf(dt.x, G, dR[0]);
                         dR[1] = fmaf(dt.y, G, dR[1]);
@@ -550,6 +583,16 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, const 
                 st_row8<BF>(AB1, tid, c0, S::N3, buf);
                 st_row8<BF>(AB1, tid, c0 + 8, S::N3, buf + 8);
             }
+            if (kRes) {   // this row's layer-3 accumulators are all read: its dY2 columns start as the skip terms
+#pragma unroll
+                for (int c0 = 0; c0 < S::N2; c0 += 16) {
+                    uint32_t w[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) w[u] = __float_as_uint(c0 + u < S::E1 ? res2[c0 + u] : 0.f);
+                    tc::tmem_st16(taddr + c0, w);
+                }
+                tc::tmem_st_wait();
+            }
         }
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -557,7 +600,7 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, const 
         if (tid == 0) {
             tc::fence_after_sync();
             // dY2 = dz3 x W3^T: B rows are the outputs k of W3's input side (W3 [E1][E2] row-major)
-            tc::mma_kloop(tmem, tc::smem_u32(AB1), tc::smem_u32(img + S::B3B_OFF), S::N3, idb1);
+            tc::mma_kloop(tmem, tc::smem_u32(AB1), tc::smem_u32(img + S::B3B_OFF), S::N3, idb1, kRes);
             tc::mma_commit(&mbar_mma);
         }
         ok = tc::mbar_wait(&mbar_mma, ph_mma, kWaitLimit);
@@ -567,9 +610,10 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, const 
             break;
         }
         tc::fence_after_sync();
-        float res1[S::E0];
+        float res1[S::E0];   // skip terms of dE/dy1
 #pragma unroll
         for (int k = 0; k < S::E0; ++k) res1[k] = 0.f;
+        {
 #pragma unroll
         for (int c0 = 0; c0 < S::N2; c0 += 16) {
             float z[16];
@@ -581,7 +625,7 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, const 
                 const int k = c0 + u;
                 float v = 0.f;
                 if (k < S::E1) {
-                    const float dy2 = z[u] + res2[k];
+                    const float dy2 = kRes ? z[u] : z[u] + res2[k];   // kRes: started from the skip terms
                     v = dy2 * (1.f - t2[k] * t2[k]);
                     if (S::E1 == S::E0) res1[k] += dy2;
                     else if (S::E1 == 2 * S::E0) res1[k % S::E0] += dy2;
@@ -591,13 +635,24 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, const 
             st_row8<BF>(A3, tid, c0, S::N2, buf);
             st_row8<BF>(A3, tid, c0 + 8, S::N2, buf + 8);
         }
+        if (kRes) {   // this row's dY2 accumulators are all read: its dY1 columns start as the skip terms
+#pragma unroll
+            for (int c0 = 0; c0 < S::K2; c0 += 16) {
+                uint32_t w[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) w[u] = __float_as_uint(c0 + u < S::E0 ? res1[c0 + u] : 0.f);
+                tc::tmem_st16(taddr + c0, w);
+            }
+            tc::tmem_st_wait();
+        }
+        }
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
         if (tid == 0) {
             tc::fence_after_sync();
             // dY1 = dz2 x W2^T
-            tc::mma_kloop(tmem + S::N2, tc::smem_u32(A3), tc::smem_u32(img + S::B2B_OFF), S::N2, idb2);
+            tc::mma_kloop(tmem + kHi, tc::smem_u32(A3), tc::smem_u32(img + S::B2B_OFF), S::N2, idb2, kRes);
             tc::mma_commit(&mbar_mma);
         }
         ok = tc::mbar_wait(&mbar_mma, ph_mma, kWaitLimit);
@@ -613,13 +668,13 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, const 
 #pragma unroll
             for (int c0 = 0; c0 < S::K2; c0 += 16) {
                 float z[16];
-                tc::tmem_ld16(taddr + S::N2 + c0, z);
+                tc::tmem_ld16(taddr + kHi + c0, z);
                 tc::tmem_ld_wait();
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     const int k = c0 + u;
                     if (k < S::E0) {
-                        const float dy1 = z[u] + res1[k];
+                        const float dy1 = kRes ? z[u] : z[u] + res1[k];   // kRes: started from the skip terms
                         ds = fmaf(dy1 * (1.f - t1[k] * t1[k]), W1[k], ds);
                         if (S::E0 == 1) ds += dy1;
                         else if (S::E0 == 2) ds += dy1;
@@ -671,7 +726,7 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_bwd_tc(ModelDev md, const 
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tmem, kTmemCols);
+    if (warp == 0) tc::tmem_dealloc(tmem, kCols);
 }
 
 // Work list: for each (center type, neighbor type) group, the 32-neighbor
@@ -885,7 +940,7 @@ __global__ void __launch_bounds__(128, 1) k_fit_tc(ModelDev md, const int32_t *_
                                                   const unsigned char *__restrict__ img, double *__restrict__ E_atom,
                                                   float *__restrict__ dT, int *err)
 {
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar_t[2], bar_m[2];
     __shared__ uint32_t tmem_base;
     constexpr int F = S::F, KC = S::KC, M2 = S::M2, M1 = S::M1;
@@ -1401,7 +1456,6 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     }
     const float4 *envA = reinterpret_cast<const float4 *>(nl->d_env);
     const float2 *envB = reinterpret_cast<const float2 *>(nl->d_env + 4 * (size_t)n * md.nsel);
-    const unsigned grid = (unsigned)(2 * nsm);
     {
         ProfScope ps(m->prof, PG_CHUNKS, 3, st);
         k_cb_count<<<nb, kCbThreads, 0, st>>>(md, n, nl->d_order, nl->d_nnei, cb_loc, cb_bsum, nb);
@@ -1413,7 +1467,8 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     DP_CUDA(cudaGetLastError());
     DP_CUDA(cudaFuncSetAttribute(k_embed_fwd_tc<S, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::F_SMEM));
     DP_CUDA(cudaFuncSetAttribute(k_embed_fwd_tc<S, BF>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    DP_CUDA(cudaFuncSetAttribute(k_embed_bwd_tc<S, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::BWD_SMEM));
+    DP_CUDA(cudaFuncSetAttribute(k_embed_bwd_tc<S, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::B_SMEM));
+    DP_CUDA(cudaFuncSetAttribute(k_embed_bwd_tc<S, BF>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     {
         ProfScope ps(m->prof, PG_EMBED_FWD, 1, st);
         k_embed_fwd_tc<S, BF><<<(unsigned)(S::F_CTAS * nsm), kTcThreads, S::F_SMEM, st>>>(md, envA, nl->d_nlist, nl->d_nnei, chunks,
@@ -1438,7 +1493,7 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     }
     {
         ProfScope ps(m->prof, PG_EMBED_BWD, 1, st);
-        k_embed_bwd_tc<S, BF><<<grid, kTcThreads, S::BWD_SMEM, st>>>(md, envA, envB, nl->d_nlist, nl->d_nnei, chunks,
+        k_embed_bwd_tc<S, BF><<<(unsigned)(S::B_CTAS * nsm), kTcThreads, S::B_SMEM, st>>>(md, envA, envB, nl->d_nlist, nl->d_nnei, chunks,
                                                                      cnt, wimg, dT, d_force, d_atom_virial, m->d_err);
     }
     DP_CUDA(cudaGetLastError());

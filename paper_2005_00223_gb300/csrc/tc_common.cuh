@@ -57,14 +57,16 @@ __host__ __device__ __forceinline__ uint32_t kmaj_off(int r, int k, int K)
     return (uint32_t)((r >> 3) * (K >> 3) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
-// D[tmem] (+)= A[smem] * B[smem]^T over K (multiple of 16), M = 128; one thread issues.
-__device__ __forceinline__ void mma_kloop(uint32_t d_tmem, uint32_t a_saddr, uint32_t b_saddr, int K, uint32_t idesc)
+// D[tmem] = A[smem] * B[smem]^T over K (multiple of 16), M = 128, or D += A B^T
+// with accumulate; one thread issues.
+__device__ __forceinline__ void mma_kloop(uint32_t d_tmem, uint32_t a_saddr, uint32_t b_saddr, int K, uint32_t idesc,
+                                          bool accumulate = false)
 {
     const uint32_t sbo = (uint32_t)(K >> 3) * 128;
     for (int ks = 0; ks < (K >> 4); ++ks) {
         uint64_t ad = smem_desc(a_saddr + ks * 256, 128, sbo);
         uint64_t bd = smem_desc(b_saddr + ks * 256, 128, sbo);
-        uint32_t acc = ks > 0;
+        uint32_t acc = (accumulate || ks > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
