@@ -85,8 +85,8 @@ struct TcShape {
     static constexpr uint32_t F_MAXC = (N2 > N3 ? N2 : N3) > 64 ? (N2 > N3 ? N2 : N3) : 64;
     static constexpr uint32_t F_TCOLS = F_MAXC <= 32 ? 32 : F_MAXC <= 64 ? 64 : F_MAXC <= 128 ? 128 : 256;
     static constexpr int F_BY_SMEM = (int)((227 * 1024) / (F_SMEM + 1024 + 256));   // + reserved + static
-    static constexpr int F_CTAS = F_BY_SMEM < 4 ? (F_BY_SMEM < (int)(512 / F_TCOLS) ? F_BY_SMEM : (int)(512 / F_TCOLS))
-                                                : (4 < (int)(512 / F_TCOLS) ? 4 : (int)(512 / F_TCOLS));
+    static constexpr int cmin(int a, int b) { return a < b ? a : b; }
+    static constexpr int F_CTAS = cmin(cmin(F_BY_SMEM, (int)(512 / F_TCOLS)), 6);
     static_assert(F_RT_OFF + 16 * 128 * 2 <= F_SMEM && F_A3_OFF + 128 * N2 * 2 <= F_SMEM && F_CTAS >= 2,
                   "forward layout");
     static constexpr uint32_t BWD_SMEM = X_OFF + BWD_SCRATCH > 80 * 1024 ? X_OFF + BWD_SCRATCH : 80 * 1024;
@@ -101,8 +101,7 @@ struct TcShape {
     static constexpr uint32_t B_X_OFF = B_IMG + B_ACT;
     static constexpr uint32_t B_SMEM = B_X_OFF + BWD_SCRATCH;
     static constexpr int B_BY_SMEM = (int)((227 * 1024) / (B_SMEM + 1024 + 256));
-    static constexpr int B_CTAS = B_BY_SMEM < 3 ? (B_BY_SMEM < (int)(512 / F_TCOLS) ? B_BY_SMEM : (int)(512 / F_TCOLS))
-                                                : (3 < (int)(512 / F_TCOLS) ? 3 : (int)(512 / F_TCOLS));
+    static constexpr int B_CTAS = cmin(cmin(B_BY_SMEM, (int)(512 / F_TCOLS)), E2 <= 32 ? 4 : 3);
     static_assert(B_CTAS >= 2 && B_A3_OFF + 128 * N2 * 2 <= B_X_OFF, "backward layout");
     static constexpr uint32_t TCOL = N2 + N3;                          // TMEM columns of the 4 chunks' T
     static_assert(N2 + N3 + 64 <= kTmemCols, "TMEM columns");
@@ -433,7 +432,7 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const 
 }
 
 template <class S, int BF>
-__global__ void __launch_bounds__(kTcThreads, S::B_CTAS >= 3 ? 3 : 1) k_embed_bwd_tc(ModelDev md, const float4 *__restrict__ envA,
+__global__ void __launch_bounds__(kTcThreads, S::B_CTAS >= 3 ? S::B_CTAS : 1) k_embed_bwd_tc(ModelDev md, const float4 *__restrict__ envA,
                                                             const float2 *__restrict__ envB,
                                                             const int32_t *__restrict__ nlist,
                                                             const int32_t *__restrict__ nnei,
