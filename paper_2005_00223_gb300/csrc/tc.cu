@@ -58,19 +58,7 @@ struct TcShape {
     static constexpr uint32_t B2B_OFF = B3B_OFF + N2 * N3 * 2;         // W2   [K2][N2]
     static constexpr uint32_t VEC_OFF = B2B_OFF + K2 * N2 * 2;         // W1[K2], b1[K2], b2[N2], b3[N3] (FP32)
     static constexpr uint32_t IMG = VEC_OFF + (2 * K2 + N2 + N3) * 4;
-    // shared memory after the image
-    static constexpr uint32_t A2_OFF = IMG;                            // [128][K2]
-    static constexpr uint32_t A3_OFF = A2_OFF + 128 * K2 * 2;          // [128][N2]
-    static constexpr uint32_t AB1_OFF = A3_OFF + 128 * N2 * 2;         // [128][N3] (backward)
-    static constexpr uint32_t X_OFF = AB1_OFF + 128 * N3 * 2;          // backward: dT per warp (FP32)
-    // forward: the contraction T = G^T R as MMAs with MN-major fp16 operands,
-    // G^T [128 m][128 rows] and R [16 c][128 rows] (c >= 4 and m >= E2 stay 0)
-    static constexpr uint32_t GT_OFF = AB1_OFF;
-    static constexpr uint32_t RT_OFF = GT_OFF + 128 * 128 * 2;
-    static constexpr uint32_t FWD_SCRATCH = 128 * 128 * 2 + 16 * 128 * 2;
-    static constexpr uint32_t BWD_SCRATCH = 4 * 4 * E2 * 4;
-    // at most two CTAs per SM (each holds 256 TMEM columns of the SM's 512)
-    static constexpr uint32_t FWD_SMEM = GT_OFF + FWD_SCRATCH > 80 * 1024 ? GT_OFF + FWD_SCRATCH : 80 * 1024;
+    static constexpr uint32_t BWD_SCRATCH = 4 * 4 * E2 * 4;             // backward: dE/dT per warp (FP32)
     // Forward kernel layout: only W2^T, W3^T and the vectors of the image, then one region that holds
     // A2 and A3 until the layer-3 MMA has read them and G^T afterwards (R^T after it); tensor memory
     // reused layer by layer (z2, then z3, then the four chunks' T, all from column 0).
@@ -89,7 +77,6 @@ struct TcShape {
     static constexpr int F_CTAS = cmin(cmin(F_BY_SMEM, (int)(512 / F_TCOLS)), 6);
     static_assert(F_RT_OFF + 16 * 128 * 2 <= F_SMEM && F_A3_OFF + 128 * N2 * 2 <= F_SMEM && F_CTAS >= 2,
                   "forward layout");
-    static constexpr uint32_t BWD_SMEM = X_OFF + BWD_SCRATCH > 80 * 1024 ? X_OFF + BWD_SCRATCH : 80 * 1024;
     // Backward kernel layout: the full image, then one region that holds A2 and A3 (the forward
     // recomputation) until the layer-3 MMA has read them, dz3 (AB1) from the layer-3 epilogue until
     // the dY2 MMA has read it, and dz2 in A3's place after that; then dE/dT per warp. Tensor memory
@@ -103,9 +90,7 @@ struct TcShape {
     static constexpr int B_BY_SMEM = (int)((227 * 1024) / (B_SMEM + 1024 + 256));
     static constexpr int B_CTAS = cmin(cmin(B_BY_SMEM, (int)(512 / F_TCOLS)), E2 <= 32 ? 4 : 3);
     static_assert(B_CTAS >= 2 && B_A3_OFF + 128 * N2 * 2 <= B_X_OFF, "backward layout");
-    static constexpr uint32_t TCOL = N2 + N3;                          // TMEM columns of the 4 chunks' T
-    static_assert(N2 + N3 + 64 <= kTmemCols, "TMEM columns");
-    static_assert(N3 <= 128 && 2 * FWD_SMEM <= 227 * 1024, "forward tile");
+    static_assert(N3 <= 128, "forward tile");
 };
 
 using TcWater = TcShape<25, 50, 100>;
@@ -305,7 +290,6 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const 
         const RowIn in = nxt;
         nxt = fetch_row<false>(md, chunks, tile + gridDim.x, ntiles, warp, lane, nnei, nlist, envA, nullptr);
         const int net = in.net;
-        const TileCtx ch = in.ch;
         if (net != cur_net) {
             if (tid == 0) {   // W2^T and W3^T, then the vectors right after them
                 tc::mbar_expect_tx(&mbar_w, S::B3B_OFF + S::VEC_BYTES);
