@@ -528,22 +528,29 @@ def run_e2e(dp, model, cfg, coord, vel, typ, box, mass, dt, args, stream):
     minv = (9.648533212e-3 / mass[typ])[:, None]
     L = np.diag(box)
     nl = dp.NeighborList(model, x, typ, box, skin=2.0)
-    ref = x.copy()
     E, Ei, F, W = nl.compute(x, box, args.precision)
     steps = args.e2e_steps
+    hdm = 0.5 * dt * minv                       # half kick per unit force
+    disp = np.zeros_like(x)                     # displacement since the last list build
+    tmp = np.empty_like(x)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        v += 0.5 * dt * F * minv
-        x += dt * v
-        x -= L * np.floor(x / L)
-        d = x - ref
-        d -= L * np.rint(d / L)
-        if (d * d).sum(1).max() > 1.0:          # half the 2 A skin, squared
+        np.multiply(F, hdm, out=tmp)
+        v += tmp
+        np.multiply(v, dt, out=tmp)
+        x += tmp
+        disp += tmp
+        np.floor(np.divide(x, L, out=tmp), out=tmp)
+        tmp *= L
+        x -= tmp                                # wrapped into [0, L)
+        np.multiply(disp, disp, out=tmp)
+        if tmp.sum(1).max() > 1.0:              # half the 2 A skin, squared
             nl.update(x, box)
-            ref = x.copy()
+            disp[:] = 0.0
         E, Ei, F, W = nl.compute(x, box, args.precision)
-        v += 0.5 * dt * F * minv
+        np.multiply(F, hdm, out=tmp)
+        v += tmp
     t1 = time.perf_counter()
     nl.close()
     step_s = (t1 - t0) / steps

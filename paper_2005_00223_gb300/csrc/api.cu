@@ -429,6 +429,7 @@ void dp_model_destroy(dp_model *m)
     cudaFree(m->d_flag);
     cudaFree(m->d_red);
     cudaFree(m->d_err);
+    cudaFreeHost(m->h_stage);
     cudaFree(m->d_tcw);
     cudaFree(m->d_ozw);
     cudaFree(m->d_oze);
@@ -752,15 +753,25 @@ dp_status dp_compute(dp_model *m, dp_nlist *nl, const double *coord, const doubl
     DP_TRY(compute_device(m, nl, a.coord, prec, a.scal, a.Ei, a.F, a.scal + 1, a.Wi, st));
     DP_TRY(check_nonfinite(a.F, 3 * n, m->d_flag, st));
     DP_TRY(check_nonfinite(a.scal, 10, m->d_flag, st));
-    double scal[10];
-    int32_t flag = 0, derr = 0;
-    DP_CUDA(cudaMemcpyAsync(&derr, m->d_err, sizeof(derr), cudaMemcpyDeviceToHost, st));
-    std::vector<double> F(3 * n), Ei(atom_energy ? n : 0);
-    DP_CUDA(cudaMemcpyAsync(scal, a.scal, sizeof(scal), cudaMemcpyDeviceToHost, st));
-    DP_CUDA(cudaMemcpyAsync(&flag, m->d_flag, sizeof(flag), cudaMemcpyDeviceToHost, st));
-    if (n > 0) DP_CUDA(cudaMemcpyAsync(F.data(), a.F, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
-    if (atom_energy && n > 0) DP_CUDA(cudaMemcpyAsync(Ei.data(), a.Ei, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    // results into pinned staging (asynchronous copies), then into the caller's arrays
+    if (4 * n + 12 > m->h_stage_n) {
+        DP_CUDA(cudaStreamSynchronize(st));
+        cudaFreeHost(m->h_stage);
+        m->h_stage = nullptr;
+        m->h_stage_n = 0;
+        DP_CUDA(cudaMallocHost((void **)&m->h_stage, sizeof(double) * (size_t)(4 * n + 12)));
+        m->h_stage_n = 4 * n + 12;
+    }
+    double *hF = m->h_stage, *hEi = hF + 3 * n, *scal = hEi + n;   // scal [10], then two int32 words
+    int32_t *hfl = reinterpret_cast<int32_t *>(scal + 10);
+    DP_CUDA(cudaMemcpyAsync(hfl + 1, m->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    DP_CUDA(cudaMemcpyAsync(scal, a.scal, sizeof(double) * 10, cudaMemcpyDeviceToHost, st));
+    DP_CUDA(cudaMemcpyAsync(hfl, m->d_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    if (n > 0) DP_CUDA(cudaMemcpyAsync(hF, a.F, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+    if (atom_energy && n > 0) DP_CUDA(cudaMemcpyAsync(hEi, a.Ei, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
     DP_CUDA(cudaStreamSynchronize(st));
+    const int32_t flag = hfl[0], derr = hfl[1];
+    const double *F = hF, *Ei = hEi;
     if (derr) {
         cudaMemsetAsync(m->d_err, 0, sizeof(int32_t), st);
         set_error("a bounded device wait gave up (tensor-core pipeline); results are invalid");
@@ -769,8 +780,8 @@ dp_status dp_compute(dp_model *m, dp_nlist *nl, const double *coord, const doubl
     if (flag) { set_error("non-finite energy, virial or force"); return DP_ERR_NONFINITE; }
     *energy = scal[0];
     if (virial) memcpy(virial, scal + 1, 9 * sizeof(double));
-    if (n > 0) memcpy(force, F.data(), sizeof(double) * 3 * n);
-    if (atom_energy && n > 0) memcpy(atom_energy, Ei.data(), sizeof(double) * n);
+    if (n > 0) memcpy(force, F, sizeof(double) * 3 * n);
+    if (atom_energy && n > 0) memcpy(atom_energy, Ei, sizeof(double) * n);
     return DP_OK;
 }
 

@@ -140,7 +140,8 @@ struct dp_model {
     char *ws = nullptr;
     size_t ws_bytes = 0;
     double *d_scalar = nullptr;       // [16] pinned-reduction target on device
-    double *h_pinned = nullptr;       // [16] host pinned mirror
+    double *h_stage = nullptr;        // pinned host staging of dp_compute's results (grown on demand)
+    int64_t h_stage_n = 0;            // its size in doubles
     int64_t batch_atoms = 0;          // atoms per batch (0 = derived from the workspace budget)
     // per-atom scratch for the host-pointer calls: E_i [n], W_i [9n], F [3n], coord [3n], scalars [16]
     double *d_aux = nullptr;
