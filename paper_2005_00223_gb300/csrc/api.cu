@@ -429,7 +429,6 @@ void dp_model_destroy(dp_model *m)
     cudaFree(m->d_flag);
     cudaFree(m->d_red);
     cudaFree(m->d_err);
-    cudaFreeHost(m->h_stage);
     cudaFree(m->d_tcw);
     cudaFree(m->d_ozw);
     cudaFree(m->d_oze);
@@ -447,8 +446,19 @@ void dp_model_destroy(dp_model *m)
 
 // ------------------------------------------------------------ neighbor list
 
+static void nlist_graph_drop(dp_nlist *nl)
+{
+    if (nl->cgraph_exec) cudaGraphExecDestroy(nl->cgraph_exec);
+    if (nl->cgraph) cudaGraphDestroy(nl->cgraph);
+    nl->cgraph_exec = nullptr;
+    nl->cgraph = nullptr;
+}
+
 static void nlist_free(dp_nlist *nl)
 {
+    nlist_graph_drop(nl);
+    cudaFreeHost(nl->h_io);
+    nl->h_io = nullptr;
     cudaFree(nl->d_type);
     cudaFree(nl->d_cand);
     cudaFree(nl->d_cand_cnt);
@@ -748,30 +758,70 @@ dp_status dp_compute(dp_model *m, dp_nlist *nl, const double *coord, const doubl
     DP_TRY(ensure_aux(m, n));
     Aux a = aux_of(m);
     cudaStream_t st = m->stream;
-    if (n > 0) DP_CUDA(cudaMemcpyAsync(a.coord, coord, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
-    DP_CUDA(cudaMemsetAsync(m->d_flag, 0, sizeof(int32_t), st));
-    DP_TRY(compute_device(m, nl, a.coord, prec, a.scal, a.Ei, a.F, a.scal + 1, a.Wi, st));
-    DP_TRY(check_nonfinite(a.F, 3 * n, m->d_flag, st));
-    DP_TRY(check_nonfinite(a.scal, 10, m->d_flag, st));
-    // results into pinned staging (asynchronous copies), then into the caller's arrays
-    if (4 * n + 12 > m->h_stage_n) {
-        DP_CUDA(cudaStreamSynchronize(st));
-        cudaFreeHost(m->h_stage);
-        m->h_stage = nullptr;
-        m->h_stage_n = 0;
-        DP_CUDA(cudaMallocHost((void **)&m->h_stage, sizeof(double) * (size_t)(4 * n + 12)));
-        m->h_stage_n = 4 * n + 12;
-    }
-    double *hF = m->h_stage, *hEi = hF + 3 * n, *scal = hEi + n;   // scal [10], then two int32 words
+    if (!nl->h_io) DP_CUDA(cudaMallocHost((void **)&nl->h_io, sizeof(double) * (size_t)(7 * n + 12)));
+    double *hc = nl->h_io, *hF = hc + 3 * n, *hEi = hF + 3 * n, *scal = hEi + n;   // scal [10], two int32 words
     int32_t *hfl = reinterpret_cast<int32_t *>(scal + 10);
-    DP_CUDA(cudaMemcpyAsync(hfl + 1, m->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    DP_CUDA(cudaMemcpyAsync(scal, a.scal, sizeof(double) * 10, cudaMemcpyDeviceToHost, st));
-    DP_CUDA(cudaMemcpyAsync(hfl, m->d_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    if (n > 0) DP_CUDA(cudaMemcpyAsync(hF, a.F, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
-    if (atom_energy && n > 0) DP_CUDA(cudaMemcpyAsync(hEi, a.Ei, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    // the stream work of one evaluation between the pinned staging buffers
+    auto body = [&]() -> dp_status {
+        if (n > 0) DP_CUDA(cudaMemcpyAsync(a.coord, hc, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+        DP_CUDA(cudaMemsetAsync(m->d_flag, 0, sizeof(int32_t), st));
+        DP_TRY(compute_device(m, nl, a.coord, prec, a.scal, a.Ei, a.F, a.scal + 1, a.Wi, st));
+        DP_TRY(check_nonfinite(a.F, 3 * n, m->d_flag, st));
+        DP_TRY(check_nonfinite(a.scal, 10, m->d_flag, st));
+        DP_CUDA(cudaMemcpyAsync(hfl + 1, m->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        DP_CUDA(cudaMemcpyAsync(scal, a.scal, sizeof(double) * 10, cudaMemcpyDeviceToHost, st));
+        DP_CUDA(cudaMemcpyAsync(hfl, m->d_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        if (n > 0) {
+            DP_CUDA(cudaMemcpyAsync(hF, a.F, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+            DP_CUDA(cudaMemcpyAsync(hEi, a.Ei, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+        }
+        return DP_OK;
+    };
+    if (n > 0) memcpy(hc, coord, sizeof(double) * 3 * n);
+    // After one direct call with a key (precision, the model's buffers and parameters, the routing
+    // switches) the calls are replays of one captured graph; not while profiling or with DP_NO_GRAPH.
+    const bool use_graph = n > 0 && !(m->prof && m->prof->on) && getenv("DP_NO_GRAPH") == nullptr;
+    const std::string env = route_env();
+    if (!(nl->cgraph_prec == prec && nl->cgraph_epoch == m->epoch && nl->cgraph_env == env)) {
+        nlist_graph_drop(nl);
+        nl->cgraph_prec = prec;
+        nl->cgraph_epoch = m->epoch;
+        nl->cgraph_env = env;
+        nl->cgraph_direct = 0;
+    }
+    if (use_graph && !nl->cgraph_exec && nl->cgraph_direct >= 1) {
+        const uint64_t ep = m->epoch;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const dp_status bs = body();
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(st, &g);
+            cudaGraphExec_t x = nullptr;
+            const bool ok = bs == DP_OK && e == cudaSuccess && g != nullptr && m->epoch == ep &&
+                            cudaGraphInstantiate(&x, g, 0) == cudaSuccess;
+            if (ok) {
+                nl->cgraph = g;
+                nl->cgraph_exec = x;
+            } else {
+                if (x) cudaGraphExecDestroy(x);
+                if (g) cudaGraphDestroy(g);
+                if (m->epoch != ep) {   // a buffer was set up inside the capture: redo its contents directly
+                    m->oz_stale = true;
+                    m->oz_emb_stale = true;
+                    m->oz_fit_stale = true;
+                }
+                nl->cgraph_direct = -1000000;   // no further capture with this key
+            }
+        }
+        (void)cudaGetLastError();
+    }
+    if (use_graph && nl->cgraph_exec) {
+        DP_CUDA(cudaGraphLaunch(nl->cgraph_exec, st));
+    } else {
+        DP_TRY(body());
+        ++nl->cgraph_direct;
+    }
     DP_CUDA(cudaStreamSynchronize(st));
     const int32_t flag = hfl[0], derr = hfl[1];
-    const double *F = hF, *Ei = hEi;
     if (derr) {
         cudaMemsetAsync(m->d_err, 0, sizeof(int32_t), st);
         set_error("a bounded device wait gave up (tensor-core pipeline); results are invalid");
@@ -780,8 +830,8 @@ dp_status dp_compute(dp_model *m, dp_nlist *nl, const double *coord, const doubl
     if (flag) { set_error("non-finite energy, virial or force"); return DP_ERR_NONFINITE; }
     *energy = scal[0];
     if (virial) memcpy(virial, scal + 1, 9 * sizeof(double));
-    if (n > 0) memcpy(force, F, sizeof(double) * 3 * n);
-    if (atom_energy && n > 0) memcpy(atom_energy, Ei, sizeof(double) * n);
+    if (n > 0) memcpy(force, hF, sizeof(double) * 3 * n);
+    if (atom_energy && n > 0) memcpy(atom_energy, hEi, sizeof(double) * n);
     return DP_OK;
 }
 

@@ -140,8 +140,6 @@ struct dp_model {
     char *ws = nullptr;
     size_t ws_bytes = 0;
     double *d_scalar = nullptr;       // [16] pinned-reduction target on device
-    double *h_stage = nullptr;        // pinned host staging of dp_compute's results (grown on demand)
-    int64_t h_stage_n = 0;            // its size in doubles
     int64_t batch_atoms = 0;          // atoms per batch (0 = derived from the workspace budget)
     // per-atom scratch for the host-pointer calls: E_i [n], W_i [9n], F [3n], coord [3n], scalars [16]
     double *d_aux = nullptr;
@@ -197,6 +195,15 @@ struct dp_nlist {
     double *d_coord = nullptr;        // [n][3] staging for host-pointer calls
     int32_t *d_order = nullptr;       // [n] atom indices sorted by type (stable)
     std::vector<int64_t> type_count, type_off;
+    // dp_compute with host arrays as one captured graph (H2D of the coordinates from pinned staging,
+    // the evaluation, D2H of the results into it), replayed while its key holds
+    cudaGraph_t cgraph = nullptr;
+    cudaGraphExec_t cgraph_exec = nullptr;
+    dp_precision cgraph_prec = DP_FP64;
+    uint64_t cgraph_epoch = 0;
+    std::string cgraph_env;
+    int cgraph_direct = 0;            // direct calls with the current key (capture after the first)
+    double *h_io = nullptr;           // pinned: coord [3n], F [3n], E_i [n], E and W [10], two int32 flags
 };
 
 struct dp_md_state {
@@ -234,6 +241,9 @@ struct dp_md_state {
 };
 
 namespace dp {
+
+// Routing switches read from the environment (part of the key of a captured graph).
+std::string route_env();
 
 // Launchers (return DP_OK or an error after recording a message).
 dp_status nlist_build_device(dp_nlist *nl, cudaStream_t st, bool conditional);

@@ -120,6 +120,8 @@ dp_status md_step_body(dp_model *m, dp_md_state *s, dp_precision prec, double dt
     return DP_OK;
 }
 
+}  // namespace
+
 // The launches of a step depend on the routing switches read from the
 // environment as well as on the model's buffers (m->epoch) and the call's
 // arguments; a captured step is replayed only while all of them are those
@@ -134,6 +136,8 @@ std::string route_env()
     }
     return k;
 }
+
+namespace {
 
 void graph_drop(dp_md_state *s)
 {
