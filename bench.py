@@ -528,7 +528,8 @@ def run_e2e(dp, model, cfg, coord, vel, typ, box, mass, dt, args, stream):
     minv = (9.648533212e-3 / mass[typ])[:, None]
     L = np.diag(box)
     nl = dp.NeighborList(model, x, typ, box, skin=2.0)
-    E, Ei, F, W = nl.compute(x, box, args.precision)
+    for _ in range(2):   # untimed: the first call runs directly, the second captures the call's graph
+        E, Ei, F, W = nl.compute(x, box, args.precision)
     steps = args.e2e_steps
     hdm = 0.5 * dt * minv                       # half kick per unit force
     disp = np.zeros_like(x)                     # displacement since the last list build
