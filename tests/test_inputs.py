@@ -82,3 +82,21 @@ def test_velocities_exact_temperature_and_zero_momentum():
     ke = 0.5 * dpsynth.MVV2E * (mass[:, None] * v * v).sum()
     assert ke == np.float64(1.5 * (60 - 1) * dpsynth.KB_EV * 300.0) or \
         abs(ke / (1.5 * 59 * dpsynth.KB_EV * 300.0) - 1) < 1e-13
+
+
+def test_paper_water_model_and_system():
+    """The paper's production water model (Sec. 5.1: r_c 6 A, 144 neighbors, embedding 32-64-128,
+    fitting 240-240-240) and its 4,096-molecule single-GPU system as the 64-molecule box replicated
+    4 x 4 x 4; parameter count from the layer shapes."""
+    cfg = dpsynth.water_paper_config()
+    assert cfg.rcut == 6.0 and cfg.nsel == 144 and cfg.sel == (48, 96)
+    assert cfg.embed == (32, 64, 128) and cfg.fit == (240, 240, 240) and cfg.m2 == 16
+    emb = (1 * 32 + 32) + (32 * 64 + 64) + (64 * 128 + 128)
+    fit = (128 * 16 * 240 + 240) + 2 * (240 * 240 + 240) + (240 + 1)
+    assert dpsynth.n_params(cfg) == 4 * emb + 2 * fit
+    c, t, b = dpsynth.water_box(1)
+    coord, typ, box = dpsynth.replicate(c, t, b, (4, 4, 4))
+    assert coord.shape == (12288, 3) and (typ == 0).sum() == 4096
+    np.testing.assert_allclose(np.diag(box), 4 * 12.42)
+    # replica k of atom i sits at coord[i] + the replica's box offset
+    np.testing.assert_allclose(coord[5 * 192 + 7] - coord[7], [0.0, 12.42, 12.42])   # replica (0, 1, 1)
