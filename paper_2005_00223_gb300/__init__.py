@@ -14,7 +14,7 @@ import numpy as np
 from . import _lib
 from ._lib import (DP_FP64, DP_MIX32, DP_MIX_BF16, DP_MIX_FP16, DPError, EXPORTS, load,  # noqa: F401
                    dp_compute, dp_compute_dev, dp_md_state_create, dp_md_state_destroy, dp_md_state_get,
-                   dp_md_step, dp_model_create, dp_model_destroy, dp_model_get_params, dp_model_n_params,
+                   dp_md_step, dp_md_state_save, dp_md_state_load, dp_model_create, dp_model_destroy, dp_model_get_params, dp_model_n_params,
                    dp_model_set_params, dp_model_set_stream, dp_nlist_build, dp_nlist_destroy, dp_nlist_get,
                    dp_nlist_update, dp_profile_enable, dp_profile_group_name, dp_profile_read, dp_profile_select,
                    dp_nlist_update_dev, dp_param_grad, dp_force_loss_grad, dp_force_loss_grad_dev, dp_adam_step,
@@ -129,6 +129,19 @@ class MDState:
 
     def get(self):
         return dp_md_state_get(self.h, self.n)
+
+    def save(self, path):
+        """Checkpoint (coordinates, velocities, forces, step, box, types, masses) to a file."""
+        dp_md_state_save(self.h, path)
+
+    @classmethod
+    def load(cls, model: Model, path):
+        """Resume from a checkpoint written by save()."""
+        self = cls.__new__(cls)
+        self.model = model
+        self.h, self.n = dp_md_state_load(model.h, path)
+        _LIVE["state"].add(self)
+        return self
 
     def close(self):
         if self.h:

@@ -29,7 +29,7 @@ EXPORTS = [
     "dp_model_set_params", "dp_model_destroy", "dp_model_set_stream", "dp_profile_enable", "dp_profile_select", "dp_profile_read",
     "dp_profile_group_name", "dp_nlist_build", "dp_nlist_update", "dp_nlist_get",
     "dp_nlist_destroy", "dp_nlist_update_dev", "dp_compute", "dp_compute_dev", "dp_md_state_create",
-    "dp_md_step", "dp_md_state_get", "dp_md_state_destroy", "dp_param_grad", "dp_force_loss_grad",
+    "dp_md_step", "dp_md_state_get", "dp_md_state_save", "dp_md_state_load", "dp_md_state_destroy", "dp_param_grad", "dp_force_loss_grad",
     "dp_force_loss_grad_dev", "dp_adam_step", "dp_model_sync_params", "dp_md_step_judged",
     "dp_nlist_format_noalloc", "dp_tanh_f64_dev", "dp_nlist_build_frames", "dp_ozaki_dgemm_dev",
 ]
@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH):
             "dp_md_state_create": ([P, I64, P, P, P, P, P, D, I32, P], C.c_int),
             "dp_md_step": ([P, P, I64, D, C.c_int, I32, P], C.c_int),
             "dp_md_state_get": ([P, P, P, P, P], C.c_int),
+            "dp_md_state_save": ([P, C.c_char_p], C.c_int),
+            "dp_md_state_load": ([P, C.c_char_p, P], C.c_int),
             "dp_md_step_judged": ([P, P, P, I64, D, C.c_int, C.c_int, I32, D, P, P], C.c_int),
             "dp_md_state_destroy": ([P], None),
         }
@@ -378,6 +380,19 @@ def dp_md_step_judged(student, teacher, s, nsteps: int, dt_fs: float, student_pr
            "dp_md_step_judged")
     k = nsteps // judge_every
     return rm[:k], fb[:k]
+
+
+def dp_md_state_save(s, path: str):
+    """Checkpoint of the state to `path` (flat FP64 file, see include/dp.h)."""
+    _check(load().dp_md_state_save(s, os.fsencode(path)), "dp_md_state_save")
+
+
+def dp_md_state_load(m, path: str):
+    """A new MD state of model m from a checkpoint file; returns (handle, n)."""
+    h = C.c_void_p()
+    _check(load().dp_md_state_load(m, os.fsencode(path), C.byref(h)), "dp_md_state_load")
+    n = int(np.fromfile(path, dtype=np.float64, count=3)[2])
+    return h, n
 
 
 def dp_md_state_get(s, n: int):

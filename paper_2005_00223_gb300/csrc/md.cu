@@ -4,6 +4,7 @@
 // evaluation, half kick, and thermo rows (KE, PE, T, P) every k steps.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -435,6 +436,78 @@ dp_status dp_md_step(dp_model *m, dp_md_state *s, int64_t nsteps, double dt_fs, 
     }
     if (flag) { set_error("non-finite forces or coordinates during MD"); return DP_ERR_NONFINITE; }
     if (rows) memcpy(thermo, th.data(), sizeof(double) * 4 * rows);
+    return DP_OK;
+}
+
+dp_status dp_md_state_save(const dp_md_state *s, const char *path)
+{
+    if (!s || !path) { set_error("dp_md_state_save: NULL argument"); return DP_ERR_ARG; }
+    const int64_t n = s->n;
+    const int nt = s->m->ntypes;
+    cudaStream_t st = s->m->stream;
+    std::vector<double> buf(9 + 9 + nt + 10 * (size_t)n, 0.0);
+    double *h = buf.data();
+    double *box = h + 9, *mass = box + 9, *ty = mass + nt, *x = ty + n, *v = x + 3 * n, *f = v + 3 * n;
+    std::vector<int32_t> type(n > 0 ? n : 1);
+    DP_CUDA(cudaStreamSynchronize(st));
+    if (n > 0) {
+        DP_CUDA(cudaMemcpy(type.data(), s->nl->d_type, sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+        DP_CUDA(cudaMemcpy(x, s->d_x, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+        DP_CUDA(cudaMemcpy(v, s->d_v, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+        if (s->forces_valid) DP_CUDA(cudaMemcpy(f, s->d_f, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+    }
+    DP_CUDA(cudaMemcpy(mass, s->d_mass, sizeof(double) * nt, cudaMemcpyDeviceToHost));
+    const double hdr[9] = {(double)0x44504d44, 1.0, (double)n, (double)nt, (double)s->step, s->nl->skin,
+                           (double)s->nl->cap, s->forces_valid ? 1.0 : 0.0, (double)s->forces_prec};
+    memcpy(h, hdr, sizeof(hdr));
+    memcpy(box, s->box, sizeof(double) * 9);
+    for (int64_t i = 0; i < n; ++i) ty[i] = (double)type[i];
+    FILE *fp = fopen(path, "wb");
+    if (!fp) { set_error("dp_md_state_save: cannot open %s", path); return DP_ERR_ARG; }
+    const size_t wrote = fwrite(h, sizeof(double), buf.size(), fp);
+    const bool ok = fclose(fp) == 0 && wrote == buf.size();
+    if (!ok) { set_error("dp_md_state_save: cannot write %s", path); return DP_ERR_ARG; }
+    return DP_OK;
+}
+
+dp_status dp_md_state_load(dp_model *m, const char *path, dp_md_state **out)
+{
+    if (!m || !path || !out) { set_error("dp_md_state_load: NULL argument"); return DP_ERR_ARG; }
+    *out = nullptr;
+    FILE *fp = fopen(path, "rb");
+    if (!fp) { set_error("dp_md_state_load: cannot open %s", path); return DP_ERR_ARG; }
+    double hdr[9];
+    if (fread(hdr, sizeof(double), 9, fp) != 9 || hdr[0] != (double)0x44504d44 || hdr[1] != 1.0 || hdr[2] < 0 ||
+        hdr[3] != (double)m->ntypes || hdr[2] != floor(hdr[2])) {
+        fclose(fp);
+        set_error("dp_md_state_load: %s is not an MD checkpoint of this model's types", path);
+        return DP_ERR_ARG;
+    }
+    const int64_t n = (int64_t)hdr[2];
+    const int nt = m->ntypes;
+    std::vector<double> body(9 + nt + 10 * (size_t)n);
+    const size_t got = fread(body.data(), sizeof(double), body.size(), fp);
+    fclose(fp);
+    if (got != body.size()) { set_error("dp_md_state_load: %s is truncated", path); return DP_ERR_ARG; }
+    const double *box = body.data(), *mass = box + 9, *ty = mass + nt, *x = ty + n, *v = x + 3 * n, *f = v + 3 * n;
+    std::vector<int32_t> type(n > 0 ? n : 1);
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(ty[i] >= 0 && ty[i] < nt)) { set_error("dp_md_state_load: bad type of atom %lld", (long long)i); return DP_ERR_ARG; }
+        type[i] = (int32_t)ty[i];
+    }
+    dp_md_state *s = nullptr;
+    DP_TRY(dp_md_state_create(m, n, x, v, type.data(), mass, box, hdr[5], (int32_t)hdr[6], &s));
+    s->step = (int64_t)hdr[4];
+    if (hdr[7] == 1.0 && n > 0) {
+        const cudaError_t e = cudaMemcpy(s->d_f, f, sizeof(double) * 3 * n, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            dp_md_state_destroy(s);
+            return cuda_fail(e, "dp_md_state_load (forces)");
+        }
+        s->forces_valid = true;
+        s->forces_prec = (dp_precision)(int)hdr[8];
+    }
+    *out = s;
     return DP_OK;
 }
 

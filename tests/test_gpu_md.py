@@ -120,3 +120,37 @@ def test_graph_replay_matches_direct_launches(dp, prec):
     if prec == "fp64":
         assert a[6] == b[6]
     assert a[7] == b[7]
+
+
+def test_checkpoint_resume(dp, tmp_path):
+    """A state saved after 8 steps and resumed follows the uninterrupted run: the saved coordinates,
+    velocities and step come back bit for bit, and the resumed steps match the uninterrupted ones
+    within what the order of the force atomics leaves free; another model's types are refused."""
+    cfg, p = _scaled_water_model(5)
+    coord, typ, box = dpsynth.water_box(5)
+    mass = np.array([dpsynth.MASS["O"], dpsynth.MASS["H"]])
+    vel = dpsynth.velocities(mass[typ], 600.0, 5)
+    m = dp.Model(cfg, 0, params=p)
+    st = dp.MDState(m, coord, vel, typ, mass, box, skin=0.3)
+    st.step(8, 0.5, "fp64")
+    x8, v8, step8, _ = st.get()
+    path = str(tmp_path / "md.ckpt")
+    st.save(path)
+    th_a = st.step(12, 0.5, "fp64", thermo_every=4)
+    xa, va, stepa, _ = st.get()
+    r = dp.MDState.load(m, path)
+    x8r, v8r, step8r, _ = r.get()
+    np.testing.assert_array_equal(x8r, x8)
+    np.testing.assert_array_equal(v8r, v8)
+    assert step8r == step8 == 8
+    th_b = r.step(12, 0.5, "fp64", thermo_every=4)
+    xb, vb, stepb, _ = r.get()
+    assert stepb == stepa == 20
+    np.testing.assert_allclose(xb, xa, rtol=0, atol=1e-10 * box[0, 0])
+    np.testing.assert_allclose(vb, va, rtol=0, atol=1e-10 * np.abs(va).max())
+    np.testing.assert_allclose(th_b, th_a, rtol=1e-9)
+    r.close()
+    st.close()
+    cu = dp.Model(dpsynth.copper_config(), 0)
+    with pytest.raises(dp.DPError, match="DP_ERR_ARG"):
+        dp.MDState.load(cu, path)
