@@ -8,7 +8,7 @@ list rebuilt on the device when needed.  One step = half kick, drift,
 list check/rebuild, list formatting, energy/force/virial, half kick.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64]
-                  [--impl mine|reference] [--workload cu4000|cu108k|water192|water12k]
+                  [--impl mine|reference] [--workload cu4000|cu108k|water192|water12k|water1p5m]
 
 Prints one JSON line.  value = s/step/atom over the whole job (lower is
 better), timed with CUDA events on the library's stream, inputs resident
@@ -98,6 +98,13 @@ def _workload(name: str):
         return cfg, coord, typ, box, mass, 0.5, ("4096 H2O (64-molecule box replicated 4x4x4), 12288 atoms, rcut 6, "
                                                  "sel 48/96, nets 32-64-128 / 240-240-240 (the paper's water model "
                                                  "and single-GPU system), 330 K, dt 0.5 fs, thermo every 20 steps")
+    if name == "water1p5m":
+        cfg = dpsynth.water_config()
+        c, t, b = dpsynth.water_box(1)
+        coord, typ, box = dpsynth.replicate(c, t, b, (32, 16, 16))
+        mass = np.array([dpsynth.MASS["O"], dpsynth.MASS["H"]])
+        return cfg, coord, typ, box, mass, 0.5, ("64-molecule water box replicated 32x16x16, 1572864 atoms, rcut 6, "
+                                                 "sel 46/92, 300 K, dt 0.5 fs")
     if name == "water192":
         cfg = dpsynth.water_config()
         coord, typ, box = dpsynth.water_box(1)
