@@ -483,8 +483,17 @@ dp_status dp_md_state_load(dp_model *m, const char *path, dp_md_state **out)
         set_error("dp_md_state_load: %s is not an MD checkpoint of this model's types", path);
         return DP_ERR_ARG;
     }
-    const int64_t n = (int64_t)hdr[2];
+    const int64_t n = hdr[2] < 2147483648.0 ? (int64_t)hdr[2] : -1;
     const int nt = m->ntypes;
+    // the file must hold exactly the header and 9 + ntypes + 10 n values: checked before allocating
+    long end = -1;
+    if (n >= 0 && fseek(fp, 0, SEEK_END) == 0) end = ftell(fp);
+    if (n < 0 || end != (long)(sizeof(double) * (9 + 9 + nt + 10 * (size_t)n)) ||
+        fseek(fp, (long)(sizeof(double) * 9), SEEK_SET) != 0) {
+        fclose(fp);
+        set_error("dp_md_state_load: %s does not have the size its header gives", path);
+        return DP_ERR_ARG;
+    }
     std::vector<double> body(9 + nt + 10 * (size_t)n);
     const size_t got = fread(body.data(), sizeof(double), body.size(), fp);
     fclose(fp);
