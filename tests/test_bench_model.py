@@ -34,3 +34,26 @@ def test_md_protocols():
     assert bench.md_protocol("cu4000", 50) == (300.0, 50)
     assert bench.md_protocol("water12k", 100) == (330.0, 20)      # the paper's thermo interval and 330 K
     assert bench.md_protocol("water12k", 10) == (330.0, 10)       # fewer steps than one interval
+
+
+def test_workloads_match_their_descriptions():
+    """Atom counts, composition, density and box shape of every bench workload."""
+    import numpy as np
+    amu_g = 1.66053906660e-24
+    for name, n, dens in (("cu4000", 4000, 8.96), ("cu108k", 108000, 8.96), ("water192", 192, 1.0),
+                          ("water12k", 12288, 1.0), ("water1p5m", 1572864, 1.0)):
+        cfg, coord, typ, box, mass, dt, desc = bench.workload(name)
+        assert coord.shape == (n, 3) and typ.shape == (n,)
+        assert f"{n} atoms" in desc
+        assert np.all(box == np.diag(np.diag(box)))                       # orthorhombic boxes
+        frac = coord / np.diag(box)
+        assert frac.min() >= 0.0 and frac.max() < 1.0                     # wrapped into the box
+        counts = np.bincount(typ, minlength=cfg.ntypes)
+        if cfg.ntypes == 2:
+            assert counts[1] == 2 * counts[0]                             # H2O
+        rho = (counts * mass).sum() * amu_g / (np.prod(np.diag(box)) * 1e-24)
+        assert abs(rho - dens) < 0.05 * dens, (name, rho)
+        assert dt == (1.0 if cfg.ntypes == 1 else 0.5)
+    # the student is the copper model's
+    cfg, *_ = bench.workload("cu4000", model="student")
+    assert cfg.embed == (8, 16, 32)
