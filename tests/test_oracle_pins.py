@@ -432,6 +432,32 @@ def test_virial_periodic_diagonal_strain(orc):
         assert W[a, a] == pytest.approx(-dEde, rel=1e-6)
 
 
+def test_energy_and_force_vanish_smoothly_at_the_cutoff(orc):
+    """A neighbor crossing r_c changes E by O(delta^3) and F by O(delta^2) (s is C^2 with
+    s = s' = s'' = 0 at r_c, Sec. 2): a list cut-off or switch inconsistent with r_c breaks the scaling."""
+    cfg = _small_cfg(ntypes=1, rcut=6.0, rcs=1.0)
+    m = orc.Model(cfg, dpsynth.model_params(cfg, 21))
+    box = np.diag([60.0, 60.0, 60.0])
+    a = np.array([30.0, 30.0, 30.0])
+    typ = np.zeros(3, dtype=np.int32)
+
+    def at(r):
+        coord = np.array([a, a + [2.0, 0.3, -0.2], a + [-r * 0.8, r * 0.6, 0.0]])
+        E, _, F, _ = m.compute(coord, typ, box)
+        return E, F
+
+    E_out, F_out = at(cfg.rcut + 1e-3)
+    E_out2, F_out2 = at(cfg.rcut + 0.3)
+    assert E_out == E_out2 and np.array_equal(F_out, F_out2)      # outside: no interaction at all
+    assert np.all(F_out[2] == 0.0)
+    dE = {d: at(cfg.rcut - d)[0] - E_out for d in (1e-1, 1e-2)}   # 1e-3 would be near E's rounding
+    dF = {d: np.abs(at(cfg.rcut - d)[1][2]).max() for d in (1e-1, 1e-2, 1e-3)}
+    assert abs(dE[1e-1]) > 1e-12                                  # the neighbor does interact
+    assert 900 < dE[1e-1] / dE[1e-2] < 1100                       # cubic
+    for big, small in ((1e-1, 1e-2), (1e-2, 1e-3)):
+        assert 90 < dF[big] / dF[small] < 110                     # quadratic
+
+
 def test_translation_invariance(orc):
     cfg = dpsynth.water_config()
     m = orc.Model(cfg, dpsynth.model_params(cfg, 13))
