@@ -549,6 +549,28 @@ def test_md_free_flight_closed_form(orc):
     np.testing.assert_allclose(th[:, 3], pressure, rtol=1e-12)
 
 
+def test_md_pressure_is_minus_volume_derivative(orc):
+    """At rest the thermo pressure is -dE/dV (isotropic scaling of positions and box), in bar."""
+    cfg = _md_cfg()
+    p = dpsynth.model_params(cfg, 19)
+    for ti in range(2):
+        _view(p, cfg, f"fit[{ti}].W3")[:] *= 2000.0      # forces and virial well above rounding
+    m = orc.Model(cfg, p)
+    coord, typ, box = dpsynth.water_box(11)
+    mass = np.array([dpsynth.MASS["O"], dpsynth.MASS["H"]])
+    # one step of 1e-7 fs from rest: KE and the displacement are O(dt^2), far below the tolerance
+    _, _, th = m.md_nve(coord, np.zeros_like(coord), typ, mass, box, nsteps=1, dt=1e-7, thermo_every=1)
+    V = np.linalg.det(box)
+    h = 1e-5
+
+    def e_at(eps):
+        return m.energy(coord * (1 + eps), typ, box * (1 + eps))
+
+    dEdV = (8 * (e_at(h) - e_at(-h)) - (e_at(2 * h) - e_at(-2 * h))) / (12 * h) / (3 * V)
+    assert abs(dEdV) * 1.602176634e6 > 1.0                        # a pressure of more than 1 bar
+    assert th[0, 3] == pytest.approx(-dEdV * 1.602176634e6, rel=1e-6)
+
+
 @pytest.mark.slow
 def test_md_energy_error_scales_as_dt2(orc):
     """Velocity Verlet: the max total-energy deviation over a fixed time shrinks ~4x when dt halves."""
