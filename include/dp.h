@@ -331,7 +331,8 @@ dp_status dp_md_step_judged(dp_model *student, dp_model *teacher, dp_md_state *s
  * *step = steps taken so far, *n_rebuilds = list rebuilds so far (NULL ok). */
 dp_status dp_md_state_get(const dp_md_state *s, double *coord, double *vel, int64_t *step, int64_t *n_rebuilds);
 
-/* Checkpoint and resume of an MD state as one flat binary file of FP64
+/* Checkpoint and resume of an MD state (no counterpart in the paper, whose
+ * runs restart through the MD engine) as one flat binary file of FP64
  * values (host byte order): a header {magic 0x4450'4d44 ("DPMD"), version 1,
  * n, ntypes, step, skin, cand_cap, forces valid (0/1), their precision},
  * box [9], mass_by_type [ntypes], type [n], coord [n][3], vel [n][3], and
@@ -342,7 +343,9 @@ dp_status dp_md_state_get(const dp_md_state *s, double *coord, double *vel, int6
  * from the saved one (the skin list is rebuilt at the saved coordinates,
  * which changes when later rebuilds happen, not the formatted lists).
  * Errors: DP_ERR_ARG (NULL argument, a file that cannot be opened, read or
- * written, a bad header or a type mismatch), DP_ERR_CUDA, DP_ERR_OOM. */
+ * written, a bad header, a type mismatch, or a file whose size is not the
+ * one its header gives; checked before anything is allocated), DP_ERR_CUDA,
+ * DP_ERR_OOM. */
 dp_status dp_md_state_save(const dp_md_state *s, const char *path);
 dp_status dp_md_state_load(dp_model *m, const char *path, dp_md_state **out);
 
