@@ -32,3 +32,12 @@ def test_reference_arm_two_ranks_gloo():
     out = json.loads(lines[0])
     assert out["impl"] == "reference" and out["n_gpus"] == 2 and out["unit"] == "s/step/atom"
     assert out["value"] > 0 and out["cpu_baseline"]["kind"] == "oracle"
+    # the base contract's keys, with the reference arm's e2e (no host-device copies)
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert key in out, key
+    assert out["higher_is_better"] is False and out["steps"] == 1 and out["warmup"] == 0
+    assert out["config"]["workload"].startswith("64 H2O, 192 atoms")
+    assert out["e2e"] == {"value": out["value"], "unit": out["unit"], "h2d_bytes_per_step": 0,
+                          "d2h_bytes_per_step": 0}
+    assert out["cpu_baseline"]["value"] == out["value"] and out["cpu_baseline"]["cores"] >= 1
