@@ -458,6 +458,25 @@ def test_energy_and_force_vanish_smoothly_at_the_cutoff(orc):
         assert 90 < dF[big] / dF[small] < 110                     # quadratic
 
 
+@pytest.mark.parametrize("reps", [(2, 1, 1), (1, 1, 3)])
+def test_periodic_replica_is_extensive(orc, reps):
+    """Box edges >= 2 r_c: every replica of an atom sees the same images, so in the replicated
+    (non-cubic) box E and W scale by the replica count and F repeats; a minimum image taken along
+    the wrong edge, or a missed image, breaks it."""
+    cfg = dpsynth.copper_config()
+    m = orc.Model(cfg, dpsynth.model_params(cfg, 22))
+    coord, typ, box = dpsynth.copper_fcc(23, ncell=5)
+    assert box[0, 0] >= 2 * cfg.rcut
+    E, Ei, F, W = m.compute(coord, typ, box)
+    c2, t2, b2 = dpsynth.replicate(coord, typ, box, reps)
+    E2, Ei2, F2, W2 = m.compute(c2, t2, b2)
+    k = int(np.prod(reps))
+    assert E2 == pytest.approx(k * E, rel=1e-12)
+    np.testing.assert_allclose(Ei2, np.tile(Ei, k), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(F2, np.tile(F, (k, 1)), rtol=0, atol=1e-12 * np.abs(F).max())
+    np.testing.assert_allclose(W2, k * W, rtol=1e-11, atol=1e-12 * np.abs(W).max())
+
+
 def test_translation_invariance(orc):
     cfg = dpsynth.water_config()
     m = orc.Model(cfg, dpsynth.model_params(cfg, 13))
