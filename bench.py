@@ -305,6 +305,133 @@ def run_mine(args, rank, world):
     return out
 
 
+PATHS = ("fp64", "mix32", "bf16", "fp16", "student", "student_judged")
+JUDGE_EVERY = 10
+
+
+def _md_ms_per_step(dp, model, coord, vel, typ, mass, box, dt, prec, steps, warmup, stream):
+    """Device ms per NVE step of `steps` replayed steps after `warmup` (CUDA events on the model's stream)."""
+    import torch
+    state = dp.MDState(model, coord, vel, typ, mass, box, skin=2.0)
+    state.step(warmup, dt, prec)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    state.step(steps, dt, prec)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    state.close()
+    return ev0.elapsed_time(ev1) / steps
+
+
+def _errors(E, Ei, F, W, ref, n):
+    """Deviation of one evaluation (E, E_i, F, W) from the reference (E, E_i, F, W) of the same coordinates."""
+    Er, Eir, Fr, Wr = ref
+    frms = float(np.sqrt((Fr ** 2).sum(1).mean()))
+    rmse = float(np.sqrt(((F - Fr) ** 2).sum(1).mean()))
+    return {"force_rmse_eV_per_A": rmse, "force_rmse_rel": rmse / frms,
+            "force_rmse_at_1eV_per_A_scale": rmse / frms,
+            "force_max_abs_err_eV_per_A": float(np.sqrt(((F - Fr) ** 2).sum(1)).max()),
+            "energy_err_per_atom_eV": abs(E - Er) / n,
+            "atom_energy_max_abs_err_eV": float(np.abs(Ei - Eir).max()),
+            "virial_rel_err": float(np.abs(W - Wr).max() / np.abs(Wr).max()),
+            "meets_1e-3_eV_per_A": rmse <= 1e-3, "meets_1e-3_at_1eV_per_A_scale": rmse / frms <= 1e-3}
+
+
+def distil_student(dp, S, dev):
+    """Teacher (the seeded copper model) and a student distilled from its own MD, trained by libdp.
+
+    Teacher frames every 5 NVE steps at 300 K and 1,200 K on 4,000 atoms (24 per temperature),
+    800 Adam steps of one frame each with p_e = 1, p_f = 100 / RMS(F)^2 (the recipe of the
+    distillation test).  Returns (teacher, student, teacher RMS force of the frames)."""
+    cfg = dpsynth.copper_config()
+    teacher = dp.Model(cfg, 0, params=dpsynth.model_params(cfg, 1))
+    c4, t4, b4 = dpsynth.copper_fcc(1, ncell=10)
+    mass = np.array([dpsynth.MASS["Cu"]])
+    vels = [dpsynth.velocities(mass[t4], T, 10 + k) for k, T in enumerate((300.0, 1200.0))]
+    X, E, F = S.teacher_frames(teacher, c4, t4, b4, mass, vels, nframes=24, stride=5, dt_fs=1.0)
+    frms = float(np.sqrt((F ** 2).sum(-1).mean()))
+    stu = dp.Model(dpsynth.copper_student_config(), seed=2)
+    S.train(stu, t4, b4, X, E, F, steps=800, lr0=3e-3, lr1=1e-4, p_e=1.0, p_f=100.0 / frms ** 2)
+    return teacher, stu, frms
+
+
+def run_paths(args, name, steps, warmup, ref, ref_kind, fp64_ms=None, student=None):
+    """Every precision path and the student on one workload, in this process.
+
+    Per path: device ms per NVE step (CUDA events, graph-replayed steps), s/step/atom, ns/day, the
+    speed-up over the FP64 path, and the deviation of one evaluation at the initial coordinates
+    from `ref` (the FP64 oracle's evaluation of the same coordinates, or the FP64 GPU path's when
+    no oracle ran).  'student' is the distilled student's MD in BF16; 'student_judged' adds the
+    full model (BF16) as judge every 10 steps, driving the MD while the student's force RMSE
+    exceeds 0.1 x the full model's RMS force."""
+    import torch
+
+    import paper_2005_00223_gb300 as dp
+    from paper_2005_00223_gb300 import student as S
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    cfg, coord, typ, box, mass, dt, desc = workload(name)
+    n = len(typ)
+    vel = dpsynth.velocities(mass[typ], md_protocol(name, 1)[0], 1)
+    stream = torch.cuda.Stream(device=dev)
+    full = dp.Model(cfg, seed=1)
+    dp.dp_model_set_stream(full.h, stream)
+    if ref is None:   # no oracle evaluation: the FP64 path's (equal to the oracle's within 1e-10 in the GPU tests)
+        nl = dp.NeighborList(full, coord, typ, box)
+        ref = nl.compute(coord, box, "fp64")
+        nl.close()
+    out = {"workload": desc, "atoms": n, "steps": steps, "warmup": warmup, "error_reference": ref_kind,
+           "rms_force_eV_per_A": float(np.sqrt((ref[2] ** 2).sum(1).mean())), "paths": {}}
+    for p in args.paths:
+        if p.startswith("student") and (student is None or cfg.ntypes != 1):
+            continue
+        model, prec = (student[1], "bf16") if p.startswith("student") else (full, p)
+        if p.startswith("student"):
+            dp.dp_model_set_stream(model.h, stream)
+            dp.dp_model_set_stream(student[0].h, stream)
+        nl = dp.NeighborList(model, coord, typ, box)
+        E, Ei, F, W = nl.compute(coord, box, prec)
+        nl.close()
+        rec = {"precision": prec, "model": "student 8-16-32 / M2 8 / 64-64-64" if p.startswith("student") else
+               "full"}
+        if p == "fp64" and fp64_ms is not None:
+            ms = fp64_ms
+        elif p == "student_judged":
+            nlj = dp.NeighborList(student[0], coord, typ, box)
+            Fj = nlj.compute(coord, box, "bf16")[2]
+            nlj.close()
+            rmse_max = 0.1 * float(np.sqrt((Fj ** 2).sum(1).mean()))
+            st = dp.MDState(model, coord, vel, typ, mass, box, skin=2.0)
+            nj = max(JUDGE_EVERY, warmup // JUDGE_EVERY * JUDGE_EVERY)
+            dp.dp_md_step_judged(model.h, student[0].h, st.h, nj, dt, "bf16", "bf16", judge_every=JUDGE_EVERY,
+                                 rmse_max=rmse_max)
+            k = max(JUDGE_EVERY, steps // JUDGE_EVERY * JUDGE_EVERY)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            rm, fb = dp.dp_md_step_judged(model.h, student[0].h, st.h, k, dt, "bf16", "bf16",
+                                          judge_every=JUDGE_EVERY, rmse_max=rmse_max)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / k
+            st.close()
+            rec.update({"judge_every": JUDGE_EVERY, "judge_precision": "bf16", "rmse_max_eV_per_A": rmse_max,
+                        "judgements": int(len(rm)), "fallback_windows": int(fb.sum()),
+                        "judged_rmse_mean_eV_per_A": float(rm.mean()), "judged_rmse_max_eV_per_A": float(rm.max())})
+        else:
+            ms = _md_ms_per_step(dp, model, coord, vel, typ, mass, box, dt, prec, steps, warmup, stream)
+        step_s = ms * 1e-3
+        rec.update({"ms_per_step": ms, "s_per_step_atom": step_s / n, "ns_per_day": 86400.0 * dt * 1e-6 / step_s})
+        rec.update(_errors(E, Ei, F, W, ref, n))
+        out["paths"][p] = rec
+    f64 = out["paths"].get("fp64", {}).get("ms_per_step")
+    for rec in out["paths"].values():
+        rec["speedup_vs_fp64"] = (f64 / rec["ms_per_step"]) if f64 else None
+    full.close()
+    return out
+
+
 def grad_frames():
     """The training batch: 32 seeded 192-atom water frames with seeded reference labels."""
     cfg = dpsynth.water_config()
@@ -457,15 +584,7 @@ def run_judged(args, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    cfg = dpsynth.copper_config()
-    teacher = dp.Model(cfg, 0, params=dpsynth.model_params(cfg, 1))
-    c4, t4, b4 = dpsynth.copper_fcc(1, ncell=10)
-    mass = np.array([dpsynth.MASS["Cu"]])
-    vels = [dpsynth.velocities(mass[t4], T, 10 + k) for k, T in enumerate((300.0, 1200.0))]
-    X, E, F = S.teacher_frames(teacher, c4, t4, b4, mass, vels, nframes=24, stride=5, dt_fs=1.0)
-    frms = float(np.sqrt((F ** 2).sum(-1).mean()))
-    stu = dp.Model(dpsynth.copper_student_config(), seed=2)
-    S.train(stu, t4, b4, X, E, F, steps=800, lr0=3e-3, lr1=1e-4, p_e=1.0, p_f=100.0 / frms ** 2)
+    teacher, stu, _ = distil_student(dp, S, dev)
     _, coord, typ, box, mass, dt, desc = workload(args.workload)
     n = len(typ)
     vel = dpsynth.velocities(mass[typ], 300.0, 1)
@@ -567,49 +686,71 @@ def run_e2e(dp, model, cfg, coord, vel, typ, box, mass, dt, args, stream):
             "path": "dp_compute(host coord) -> host E, E_i, F, W; host velocity Verlet"}
 
 
-def cpu_baseline(args, budget_s=15.0):
-    """The FP64 oracle on the host cores: whole NVE steps of the same workload."""
+def cpu_baseline(args, name=None, budget_s=15.0, md_steps=True):
+    """The cpu_baseline leg: the FP64 oracle on the host cores, on the same workload.
+
+    Times one oracle evaluation (energy, forces, virial) of the initial coordinates and, with
+    md_steps, whole oracle NVE steps within about budget_s seconds.  Returns (baseline record,
+    the oracle's evaluation (E, E_i, F, W) of the initial coordinates): that evaluation is the
+    reference of the paths' error columns."""
     import oracle
-    cfg, coord, typ, box, mass, dt, desc = workload(args.workload, args.model)
+    name = name or args.workload
+    cfg, coord, typ, box, mass, dt, desc = workload(name, args.model)
     n = len(typ)
     params = dpsynth.model_params(cfg, 1)
     om = oracle.Model(cfg, params)
-    vel = dpsynth.velocities(mass[typ], md_protocol(args.workload, 1)[0], 1)
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    om.md_nve(coord, vel, typ, mass, box, nsteps=1, dt=dt, thermo_every=0, nthreads=cores)
-    one = time.perf_counter() - t0
-    steps = max(1, min(20, int(budget_s / max(one, 1e-3))))
+    E, Ei, F, W = om.compute(coord, typ, box, nthreads=cores)
+    one_eval = time.perf_counter() - t0
+    ref = (E, Ei, F, W)
+    if not md_steps:
+        return ({"value": one_eval / n, "unit": "s/step/atom", "cores": cores, "kind": "oracle",
+                 "sample": f"one FP64 oracle evaluation (energy, forces, virial) of the {desc} workload; "
+                           "an NVE step adds only the two half kicks and the drift"}, ref)
+    vel = dpsynth.velocities(mass[typ], md_protocol(name, 1)[0], 1)
+    steps = max(1, min(20, int(budget_s / max(one_eval, 1e-3))))
     t0 = time.perf_counter()
     om.md_nve(coord, vel, typ, mass, box, nsteps=steps, dt=dt, thermo_every=0, nthreads=cores)
     el = time.perf_counter() - t0
-    return {"value": el / steps / n, "unit": "s/step/atom", "cores": cores, "kind": "oracle",
-            "sample": f"{steps} full NVE steps of the {desc} workload (FP64 oracle, OpenMP over atoms)"}
+    return ({"value": el / steps / n, "unit": "s/step/atom", "cores": cores, "kind": "oracle",
+             "sample": f"{steps} full NVE steps of the {desc} workload (FP64 oracle, OpenMP over atoms)"}, ref)
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle's NVE steps on the host cores, same workload and metric.
+
+    args.warmup untimed oracle steps (at most 5), then args.steps timed ones.  The config carries
+    the same keys as the GPU arm's line."""
     if rank != 0:
         return None
     import oracle
     cfg, coord, typ, box, mass, dt, desc = workload(args.workload, args.model)
     n = len(typ)
     om = oracle.Model(cfg, dpsynth.model_params(cfg, 1))
+    nl, _, _ = om.nlist(coord, typ, box)
+    nnei_total = int((nl >= 0).sum())
     vel = dpsynth.velocities(mass[typ], md_protocol(args.workload, 1)[0], 1)
     cores = os.cpu_count() or 1
     x, v = coord, vel
-    for _ in range(min(args.warmup, 1)):
-        x, v, _ = om.md_nve(x, v, typ, mass, box, nsteps=1, dt=dt, thermo_every=0, nthreads=cores)
-    # each timed step is one full oracle NVE step, bounded to the workload's own size
+    warm = min(args.warmup, 5)
+    if warm > 0:
+        x, v, _ = om.md_nve(x, v, typ, mass, box, nsteps=warm, dt=dt, thermo_every=0, nthreads=cores)
     t0 = time.perf_counter()
     x, v, th = om.md_nve(x, v, typ, mass, box, nsteps=args.steps, dt=dt, thermo_every=args.steps, nthreads=cores)
     el = time.perf_counter() - t0
     value = el / args.steps / n
     base = {"value": value, "unit": "s/step/atom", "cores": cores, "kind": "oracle",
-            "sample": f"{args.steps} full NVE steps of the {desc} workload"}
+            "sample": f"{args.steps} full NVE steps of the {desc} workload after {warm} untimed ones"}
     return {"impl": "reference", "metric": "s/step/atom", "value": value, "unit": "s/step/atom", "n_gpus": world,
-            "steps": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": el * 1e3 / args.steps,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "atoms": n, "precision": "fp64"}, "cpu_baseline": base,
+            "steps": args.steps, "warmup": warm, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "ns_per_day": 86400.0 * dt * 1e-6 / (el / args.steps), "dtype": "f64", "precision": "fp64",
+            "data": "synthetic (seeded FCC copper / water, seeded random-init weights)",
+            "config": {"workload": desc, "atoms": n, "precision": "fp64", "real_neighbors": nnei_total,
+                       "l2": "host run (no GPU cache)", "parallelism": f"host, OpenMP over atoms on {cores} cores",
+                       "launch": "oracle NVE steps (plain C, FP64)", "profiling": "wall clock around the timed steps"},
+            "cpu_baseline": base,
             "e2e": {"value": value, "unit": "s/step/atom", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -624,10 +765,19 @@ def main():
     ap.add_argument("--model", default="full", choices=["full", "student"])
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--paths", default=",".join(PATHS),
+                    help="comma-separated paths timed beside the headline with their errors "
+                         "(fp64, mix32, bf16, fp16, student, student_judged), or 'none'")
+    ap.add_argument("--paths-workloads", default="cu4000,cu108k",
+                    help="workloads of the paths blocks when the headline is the default FP64 copper 4,000 line")
     ap.add_argument("--task", default="md", choices=["md", "grad", "judged"],
                     help="md: NVE steps (default); grad: force-loss parameter gradient over 32 water frames; "
                          "judged: distilled student MD judged by the full model")
     args = ap.parse_args()
+    args.paths = [] if args.paths in ("", "none") else [p for p in args.paths.split(",") if p]
+    for p in args.paths:
+        if p not in PATHS:
+            raise SystemExit(f"unknown path {p}")
     if args.warmup < 3 and args.impl == "mine":
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -643,13 +793,58 @@ def main():
         out = run_judged(args, rank, world)
     else:
         out = run_mine(args, rank, world)
+        ref = None
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(args)
+            out["cpu_baseline"], ref = cpu_baseline(args)
+        if rank == 0 and world == 1 and args.paths and args.model == "full":
+            out["paths"] = paths_blocks(args, out, ref)
     if rank == 0 and out is not None:
         print(json.dumps(out))
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()
+
+
+def paths_blocks(args, out, ref):
+    """The paths blocks: the headline workload, then (for the default copper 4,000 headline) the
+    other workloads of --paths-workloads, each with its own oracle reference when the cpu_baseline
+    leg runs."""
+    import torch
+
+    import paper_2005_00223_gb300 as dp
+    from paper_2005_00223_gb300 import student as S
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    student = None
+    if any(p.startswith("student") for p in args.paths):
+        t0 = time.perf_counter()
+        teacher, stu, frms = distil_student(dp, S, dev)
+        student = (teacher, stu)
+        distil_s = time.perf_counter() - t0
+    kind = "FP64 oracle (cpu_baseline leg)" if ref is not None else "FP64 GPU path (oracle not run)"
+    fp64_ms = out["ms_per_step"] if args.precision == "fp64" else None
+    blocks = {args.workload: run_paths(args, args.workload, args.steps, args.warmup, ref, kind, fp64_ms, student)}
+    if args.workload == "cu4000" and args.precision == "fp64":
+        for name in args.paths_workloads.split(","):
+            if not name or name == args.workload:
+                continue
+            ref2 = None
+            if not args.no_cpu_baseline:
+                base2, ref2 = cpu_baseline(args, name=name, md_steps=False)
+            steps = max(JUDGE_EVERY, min(args.steps, 10))
+            blocks[name] = run_paths(args, name, steps, min(args.warmup, 5), ref2,
+                                     "FP64 oracle (cpu_baseline leg)" if ref2 is not None else
+                                     "FP64 GPU path (oracle not run)", None, student)
+            if ref2 is not None:
+                blocks[name]["cpu_baseline"] = base2
+    if student is not None:
+        blocks["student_training"] = {
+            "teacher": "the seeded full copper model", "frames": "48 (24 every 5 NVE steps at 300 K and 1200 K, "
+            "4000 atoms)", "adam_steps": 800, "teacher_rms_force_eV_per_A": frms, "seconds": distil_s,
+            "kernels": "dp_md_step, dp_compute (labels), dp_force_loss_grad_dev, dp_adam_step"}
+        student[0].close()
+        student[1].close()
+    return blocks
 
 
 if __name__ == "__main__":

@@ -262,10 +262,42 @@ def dp_nlist_update_dev(nl, d_coord, stream=None):
     _check(load().dp_nlist_update_dev(nl, _ptr(d_coord), _stream(stream)), "dp_nlist_update_dev")
 
 
+def _check_dev_tensor(t, name: str, dtypes, numel: int):
+    """Raise ValueError unless t is a contiguous CUDA tensor on the current device with the given
+    dtype(s) and element count: the entry points behind this binding take raw device addresses."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a torch CUDA tensor, got {type(t).__name__}")
+    if t.device.type != "cuda" or t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: must live on the current CUDA device (cuda:{torch.cuda.current_device()}), "
+                         f"not {t.device}")
+    if t.dtype not in dtypes:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected {' or '.join(str(d) for d in dtypes)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if t.numel() != numel:
+        raise ValueError(f"{name}: {t.numel()} elements, expected {numel}")
+
+
 def dp_nlist_format_noalloc(d_coord, d_type, box, rcut: float, sel, d_nlist, d_ntrunc, d_status, stream=None):
-    """Formatted list into caller-owned device buffers; the library allocates nothing."""
+    """Formatted list into caller-owned device buffers; the library allocates nothing.
+
+    d_coord float64 [n][3], d_type int32 [n], d_nlist int32 [n][sum(sel)], d_ntrunc one int64 / uint64,
+    d_status one int32: contiguous CUDA tensors on the current device (checked here, ValueError
+    otherwise).  stream: a torch stream or raw handle; None = torch's current stream."""
+    import torch
     sel = _i32(sel)
-    _check(load().dp_nlist_format_noalloc(int(d_type.numel()), _ptr(d_coord), _ptr(d_type), _ptr(_box(box)),
+    if not isinstance(d_type, torch.Tensor):
+        raise ValueError("d_type: expected a torch CUDA tensor")
+    n = int(d_type.numel())
+    _check_dev_tensor(d_type, "d_type", (torch.int32,), n)
+    _check_dev_tensor(d_coord, "d_coord", (torch.float64,), 3 * n)
+    _check_dev_tensor(d_nlist, "d_nlist", (torch.int32,), n * int(sel.sum()))
+    _check_dev_tensor(d_ntrunc, "d_ntrunc", (torch.int64, getattr(torch, "uint64", torch.int64)), 1)
+    _check_dev_tensor(d_status, "d_status", (torch.int32,), 1)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(load().dp_nlist_format_noalloc(n, _ptr(d_coord), _ptr(d_type), _ptr(_box(box)),
                                           float(rcut), int(sel.size), _ptr(sel), _ptr(d_nlist), _ptr(d_ntrunc),
                                           _ptr(d_status), _stream(stream)), "dp_nlist_format_noalloc")
 

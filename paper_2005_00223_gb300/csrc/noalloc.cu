@@ -275,7 +275,9 @@ dp_status dp_nlist_format_noalloc(int64_t n, const double *d_coord, const int32_
     for (int k = 0; k < 3; ++k) {
         bx.L[k] = L[k];
         bx.invL[k] = 1.0 / L[k];
-        const int c = (int)floor(L[k] / rcut);
+        // cells wider than r_c by a relative margin far above the rounding of the binning
+        // (x * invL * nc), so two atoms closer than r_c are never binned two cells apart
+        const int c = (int)floor(L[k] / (rcut * (1.0 + 1e-9)));
         bx.nc[k] = c < 1 ? 1 : c;
         ncell *= bx.nc[k];
     }
