@@ -44,8 +44,17 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FFMA/clk x 2 F
 # (dram__bytes_read.sum + dram__bytes_write.sum), and the capture's summary file; valid while the
 # kernel is unchanged since the capture.
 NCU_TRAFFIC = {
-    ("fp64", "cu4000", "embed_fwd_l2"): (2.069e9 + 1.266e9, "profiles/fp64_cu4000_nve_step.md"),
+    ("fp64", "cu4000", "embed_fwd_l2"): (2.068e9 + 1.266e9, "profiles/fp64_embed_fwd_l2_pipes_cu4000.md"),
     ("bf16", "cu4000", "embed_bwd"): (28.79e6 + 0.12e6, "profiles/bf16_cu4000_nve_step.md"),
+}
+
+
+# FP64-pipe work of the dominant FP64 kernel: thread instructions executed on the FP64 pipe per real
+# neighbor (ncu sm__thread_inst_executed_pipe_fp64_pred_on.sum of one launch / the real neighbors of
+# the list), its tensor-pipe busy fraction, and the capture's summary file.  The kernel's multiply-adds
+# run on the tensor cores as exact split products; what bounds it is the FP64 pipe of its epilogue.
+NCU_FP64_PIPE = {
+    "embed_fwd_l2": (1.0752e9 / 718768, 0.0554, "profiles/fp64_embed_fwd_l2_pipes_cu4000.md"),
 }
 
 
@@ -270,11 +279,24 @@ def run_mine(args, rank, world):
         if tr is not None and args.model == "full":
             roofline["traffic"] = tr[0]
             roofline["traffic_source"] = "ncu, " + tr[1]
-        if split_route and args.precision == "fp64":
-            roofline["note"] = ("FP64-accurate algorithmic FLOP/s against the FP64 pipe; the multiply-adds of the "
-                                "embedding's hidden layers and of every fitting layer run as exact split products on "
-                                "the tensor cores, so the fraction can exceed 1; the kernel is bound by the FP64 pipe "
-                                "and the latency of its epilogue (tanh, skip, contraction)")
+        pipe = NCU_FP64_PIPE.get(top)
+        if split_route and args.precision == "fp64" and pipe is not None and args.model == "full":
+            # the FP64-pipe issue slots the kernel needs (ncu count per real neighbor, 2 FLOP each as for a
+            # DFMA) per second of its measured launch time, against the FP64 pipe's peak
+            fp64_equiv = dict(achieved=round(achieved, 4), frac_of_dfma_peak=round(achieved / peak, 4),
+                              note="algorithmic FP64-accurate FLOP of the layer (10,800 per real neighbor) per "
+                                   "second; above the FP64 peak because the multiply-adds run on the tensor "
+                                   "cores as exact split products")
+            work = 2.0 * pipe[0] * nnei_total / batches
+            achieved = work / (per_launch_ms * 1e-3) / 1e12
+            roofline.update({"achieved": round(achieved, 4), "frac": round(achieved / peak, 4),
+                             "work": "FP64-pipe thread instructions of the kernel (ncu count, %.1f per real "
+                                     "neighbor) x 2 FLOP, i.e. the FP64 pipe's busy time / the launch time" % pipe[0],
+                             "work_source": "ncu, " + pipe[2], "tensor_pipe_frac_ncu": pipe[1],
+                             "fp64_equivalent": fp64_equiv,
+                             "note": "the layer's multiply-adds run on the tensor cores (tensor pipe %.1f%% busy); "
+                                     "the FP64 work of the epilogue (tanh, skips, read-back of the split "
+                                     "products, contraction) bounds the kernel" % (100 * pipe[1])})
     step_s = ms * 1e-3 / args.steps
     value = step_s / (n * world)
     total_flop = sum(flops.values())
@@ -305,7 +327,7 @@ def run_mine(args, rank, world):
     return out
 
 
-PATHS = ("fp64", "mix32", "bf16", "fp16", "student", "student_judged")
+PATHS = ("fp64", "mix32", "bf16", "fp16", "bf16x3", "student", "student_judged")
 JUDGE_EVERY = 10
 
 
@@ -760,14 +782,14 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mix32", "bf16", "fp16"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mix32", "bf16", "fp16", "bf16x3"])
     ap.add_argument("--workload", default="cu4000")
     ap.add_argument("--model", default="full", choices=["full", "student"])
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--paths", default=",".join(PATHS),
                     help="comma-separated paths timed beside the headline with their errors "
-                         "(fp64, mix32, bf16, fp16, student, student_judged), or 'none'")
+                         "(fp64, mix32, bf16, fp16, bf16x3, student, student_judged), or 'none'")
     ap.add_argument("--paths-workloads", default="cu4000,cu108k",
                     help="workloads of the paths blocks when the headline is the default FP64 copper 4,000 line")
     ap.add_argument("--task", default="md", choices=["md", "grad", "judged"],

@@ -61,8 +61,14 @@ typedef enum {
  *   DP_MIX_BF16  MIX-16 with bf16 operands on the tensor cores, FP32
  *                accumulation; first embedding layer, tanh and the last
  *                fitting layer in FP32.
- *   DP_MIX_FP16  the same with fp16 operands. */
-typedef enum { DP_FP64 = 0, DP_MIX32 = 1, DP_MIX_BF16 = 2, DP_MIX_FP16 = 3 } dp_precision;
+ *   DP_MIX_FP16  the same with fp16 operands.
+ *   DP_MIX_BF16X3  the embedding net's products on the tensor cores with
+ *                FP32-class accuracy: every operand split into two bf16
+ *                terms (hi = bf16(x), lo = bf16(x - hi)) and each product
+ *                taken as hi hi + hi lo + lo hi (three MMAs, FP32
+ *                accumulation), tanh in FP32 (tanhf); descriptor and
+ *                fitting net in FP32 on the CUDA cores (as DP_MIX32). */
+typedef enum { DP_FP64 = 0, DP_MIX32 = 1, DP_MIX_BF16 = 2, DP_MIX_FP16 = 3, DP_MIX_BF16X3 = 4 } dp_precision;
 
 /* Model hyper-parameters (Sec. 2, Sec. 5.1).
  *   ntypes       number of atom types (1..8)
@@ -373,6 +379,19 @@ dp_status dp_tanh_f64_dev(int64_t n, const double *d_x, double *d_y, void *strea
  * DP_ERR_CUDA, DP_ERR_TIMEOUT. */
 dp_status dp_ozaki_dgemm_dev(dp_model *m, int64_t M, int32_t N, int32_t K, const double *d_A, const double *d_Bt,
                              double *d_C, void *stream);
+
+/* Test of the bounded device waits (no counterpart in the paper, which
+ * describes no failure handling).  which = 1 starves one wait of this
+ * model's later evaluations: the tensor-core (MIX-16) embedding kernel no
+ * longer issues the bulk copy of its weights, so its wait on that copy
+ * runs out after `polls` polls (1 .. 2^20) with nothing in flight; the
+ * kernel then sets the device error word, leaves its tile loop, frees its
+ * tensor memory and returns, and the host call reports DP_ERR_TIMEOUT.
+ * Every other wait keeps its default limit (about a second).  which = 0
+ * restores normal evaluation (polls ignored).  Host-side only: it takes
+ * effect at the next call and drops captured graphs of the model.
+ * Errors: DP_ERR_ARG (NULL model, unknown wait, polls out of range). */
+dp_status dp_test_starve_wait(dp_model *m, int32_t which, int64_t polls);
 
 #ifdef __cplusplus
 }

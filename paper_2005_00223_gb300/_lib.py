@@ -20,8 +20,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libdp.so")
 DP_OK = 0
 STATUS = {0: "DP_OK", -1: "DP_ERR_ARG", -2: "DP_ERR_CUDA", -3: "DP_ERR_OOM", -4: "DP_ERR_BOX",
           -5: "DP_ERR_CAPACITY", -6: "DP_ERR_TIMEOUT", -7: "DP_ERR_NONFINITE", -8: "DP_ERR_UNSUPPORTED"}
-DP_FP64, DP_MIX32, DP_MIX_BF16, DP_MIX_FP16 = 0, 1, 2, 3
-PRECISION = {"fp64": DP_FP64, "mix32": DP_MIX32, "bf16": DP_MIX_BF16, "fp16": DP_MIX_FP16}
+DP_FP64, DP_MIX32, DP_MIX_BF16, DP_MIX_FP16, DP_MIX_BF16X3 = 0, 1, 2, 3, 4
+PRECISION = {"fp64": DP_FP64, "mix32": DP_MIX32, "bf16": DP_MIX_BF16, "fp16": DP_MIX_FP16, "bf16x3": DP_MIX_BF16X3}
 
 # Every entry point declared in include/dp.h.
 EXPORTS = [
@@ -32,6 +32,7 @@ EXPORTS = [
     "dp_md_step", "dp_md_state_get", "dp_md_state_save", "dp_md_state_load", "dp_md_state_destroy", "dp_param_grad", "dp_force_loss_grad",
     "dp_force_loss_grad_dev", "dp_adam_step", "dp_model_sync_params", "dp_md_step_judged",
     "dp_nlist_format_noalloc", "dp_tanh_f64_dev", "dp_nlist_build_frames", "dp_ozaki_dgemm_dev",
+    "dp_test_starve_wait",
 ]
 
 
@@ -83,6 +84,7 @@ def load(path: str = LIB_PATH):
             "dp_tanh_f64_dev": ([I64, P, P, P], C.c_int),
             "dp_nlist_build_frames": ([P, I32, I64, P, P, P, D, D, I32, P], C.c_int),
             "dp_ozaki_dgemm_dev": ([P, I64, I32, I32, P, P, P, P], C.c_int),
+            "dp_test_starve_wait": ([P, I32, I64], C.c_int),
             "dp_param_grad": ([P, P, P, P, P, D, D, C.c_int, P, P, P], C.c_int),
             "dp_force_loss_grad": ([P, P, P, P, P, D, D, D, C.c_int, P, P], C.c_int),
             "dp_force_loss_grad_dev": ([P, P, P, P, P, P, D, D, C.c_int, P, P, P], C.c_int),
@@ -313,6 +315,11 @@ def dp_ozaki_dgemm_dev(m, d_A, d_Bt, d_C, stream=None):
     N = d_Bt.shape[0]
     _check(load().dp_ozaki_dgemm_dev(m, int(M), int(N), int(K), _ptr(d_A), _ptr(d_Bt), _ptr(d_C), _stream(stream)),
            "dp_ozaki_dgemm_dev")
+
+
+def dp_test_starve_wait(m, which: int, polls: int = 0):
+    """Starve one bounded device wait of the model's later evaluations (1), or restore (0)."""
+    _check(load().dp_test_starve_wait(m, int(which), int(polls)), "dp_test_starve_wait")
 
 
 def dp_nlist_destroy(nl):

@@ -111,7 +111,8 @@ dp_status compute_device(dp_model *m, dp_nlist *nl, const double *d_coord, dp_pr
                          double *d_atom_energy, double *d_force, double *d_virial, double *d_atom_virial,
                          cudaStream_t st)
 {
-    DP_TRY(nlist_format_device(m, nl, d_coord, st, prec == DP_MIX_BF16 || prec == DP_MIX_FP16));
+    DP_TRY(nlist_format_device(m, nl, d_coord, st,
+                               prec == DP_MIX_BF16 || prec == DP_MIX_FP16 || prec == DP_MIX_BF16X3));
     if (nl->n == 0) {
         DP_CUDA(cudaMemsetAsync(d_energy, 0, sizeof(double), st));
         if (d_virial) DP_CUDA(cudaMemsetAsync(d_virial, 0, 9 * sizeof(double), st));
@@ -126,6 +127,8 @@ dp_status compute_device(dp_model *m, dp_nlist *nl, const double *d_coord, dp_pr
         return compute_mix16(m, nl, 1, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
     case DP_MIX_FP16:
         return compute_mix16(m, nl, 0, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+    case DP_MIX_BF16X3:
+        return compute_mix_x3(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
     default:
         set_error("precision %d is not built into this library", (int)prec);
         return DP_ERR_UNSUPPORTED;
@@ -430,6 +433,7 @@ void dp_model_destroy(dp_model *m)
     cudaFree(m->d_red);
     cudaFree(m->d_err);
     cudaFree(m->d_tcw);
+    cudaFree(m->d_tcw_x3);
     cudaFree(m->d_ozw);
     cudaFree(m->d_oze);
     cudaFree(m->d_ozw_emb);
@@ -742,7 +746,7 @@ static dp_status compute_args(dp_model *m, dp_nlist *nl, const double box[9], dp
     if (nl->m != m) { set_error("the list was built for another model"); return DP_ERR_ARG; }
     if (!box) { set_error("box is NULL"); return DP_ERR_ARG; }
     if (!box_matches(nl, box)) { set_error("box differs from the list's box; build a new list"); return DP_ERR_ARG; }
-    if (prec != DP_FP64 && prec != DP_MIX32 && prec != DP_MIX_BF16 && prec != DP_MIX_FP16) {
+    if (prec != DP_FP64 && prec != DP_MIX32 && prec != DP_MIX_BF16 && prec != DP_MIX_FP16 && prec != DP_MIX_BF16X3) {
         set_error("unknown precision %d", (int)prec);
         return DP_ERR_ARG;
     }

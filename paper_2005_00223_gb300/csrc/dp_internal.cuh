@@ -68,7 +68,14 @@ struct ModelDev {
     const float *p32;               // FP32 copy (flat order)
     const float *pT32;              // FP32 transposed copy
     int act_stride;                 // doubles stored per neighbor for the backward pass
+    // Test of the bounded waits (dp_test_starve_wait): which wait is starved (0 = none) and the
+    // polls after which that one wait gives up.  Every other wait keeps its default limit.
+    int wait_test;
+    long long wait_short;
 };
+
+// Waits that dp_test_starve_wait can starve.
+enum WaitTest { WT_NONE = 0, WT_EMBED_FWD_WEIGHTS = 1 };
 
 // Kernel launch groups timed by the tracing calls (dp_profile_*).
 enum ProfGroup {
@@ -149,6 +156,7 @@ struct dp_model {
     int32_t *d_err = nullptr;         // [4] device error word (bounded waits that gave up)
     unsigned char *d_tcw = nullptr;   // packed fp16 and bf16 embedding weights for the tensor cores
     unsigned char *d_tcfit = nullptr; // packed fp16 and bf16 fitting weights for the tensor cores
+    unsigned char *d_tcw_x3 = nullptr; // packed split-bf16 (hi, lo) embedding weights (DP_MIX_BF16X3)
     void *d_ozw = nullptr;            // fp16 digits of the first fitting layer's weights (FP64 products on the tensor cores)
     int *d_oze = nullptr;             // their row scales
     bool oz_stale = true;             // digits older than the parameters
@@ -271,6 +279,9 @@ dp_status compute_mix16(dp_model *m, dp_nlist *nl, int bf16, double *d_energy, d
                         double *d_force, double *d_virial, double *d_atom_virial, cudaStream_t st);
 // FP32 fitting net over all atoms (type-sorted positions): D, dD [n][desc], E_i FP64.
 dp_status fit_f32(dp_model *m, dp_nlist *nl, const float *D, float *dD, double *d_atom_energy, cudaStream_t st);
+dp_status pack_x3_weights(dp_model *m);
+dp_status compute_mix_x3(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
+                         double *d_virial, double *d_atom_virial, cudaStream_t st);
 dp_status param_grad_device(dp_model *m, dp_nlist *nl, const double *d_v, const double *d_ab, dp_precision prec,
                             double *d_E_atom, double *d_Ed_atom, double *d_grad, cudaStream_t st);
 // Per frame f of a list (frames of frame_n atoms): v = F - F_ref, the frame's

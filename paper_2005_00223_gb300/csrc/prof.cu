@@ -86,6 +86,26 @@ static const char *kGroupNames[PG_COUNT] = {"nlist_build", "nlist_format", "pack
 
 extern "C" {
 
+dp_status dp_test_starve_wait(dp_model *m, int32_t which, int64_t polls)
+{
+    if (!m) {
+        set_error("dp_test_starve_wait: NULL model");
+        return DP_ERR_ARG;
+    }
+    if (which != WT_NONE && which != WT_EMBED_FWD_WEIGHTS) {
+        set_error("dp_test_starve_wait: unknown wait %d", (int)which);
+        return DP_ERR_ARG;
+    }
+    if (which != WT_NONE && (polls < 1 || polls > (1LL << 20))) {
+        set_error("dp_test_starve_wait: polls must be 1 .. 2^20");
+        return DP_ERR_ARG;
+    }
+    m->dev.wait_test = which;
+    m->dev.wait_short = which == WT_NONE ? 0 : polls;
+    ++m->epoch;   // captured graphs hold the old kernel arguments
+    return DP_OK;
+}
+
 dp_status dp_model_set_stream(dp_model *m, void *stream)
 {
     if (!m) {

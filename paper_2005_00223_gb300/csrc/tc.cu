@@ -36,219 +36,11 @@
 #include "dp_internal.cuh"
 #include "geom.cuh"
 #include "tc_common.cuh"
+#include "tc_embed.cuh"
 
 namespace dp {
 
 namespace {
-
-constexpr long kWaitLimit = 1L << 25;   // mbarrier polls (~1 s) before a kernel gives up
-constexpr int kTcThreads = 128;
-constexpr int kTmemCols = 256;
-
-template <int E0_, int E1_, int E2_>
-struct TcShape {
-    static constexpr int E0 = E0_, E1 = E1_, E2 = E2_;
-    static constexpr int K2 = (E0 + 15) / 16 * 16;   // layer-2 K (E0 padded)
-    static constexpr int N2 = (E1 + 15) / 16 * 16;   // layer-2 N, layer-3 K
-    static constexpr int N3 = (E2 + 15) / 16 * 16;   // layer-3 N
-    // packed weight image of one net (byte offsets; every part 16-byte aligned)
-    static constexpr uint32_t B2_OFF = 0;                              // W2^T [N2][K2]
-    static constexpr uint32_t B3_OFF = B2_OFF + N2 * K2 * 2;           // W3^T [N3][N2]
-    static constexpr uint32_t B3B_OFF = B3_OFF + N3 * N2 * 2;          // W3   [N2][N3]
-    static constexpr uint32_t B2B_OFF = B3B_OFF + N2 * N3 * 2;         // W2   [K2][N2]
-    static constexpr uint32_t VEC_OFF = B2B_OFF + K2 * N2 * 2;         // W1[K2], b1[K2], b2[N2], b3[N3] (FP32)
-    static constexpr uint32_t IMG = VEC_OFF + (2 * K2 + N2 + N3) * 4;
-    static constexpr uint32_t BWD_SCRATCH = 4 * 4 * E2 * 4;             // backward: dE/dT per warp (FP32)
-    // Forward kernel layout: only W2^T, W3^T and the vectors of the image, then one region that holds
-    // A2 and A3 until the layer-3 MMA has read them and G^T afterwards (R^T after it); tensor memory
-    // reused layer by layer (z2, then z3, then the four chunks' T, all from column 0).
-    static constexpr uint32_t VEC_BYTES = (2 * K2 + N2 + N3) * 4;
-    static constexpr uint32_t F_VEC_OFF = B3B_OFF;
-    static constexpr uint32_t F_IMG = (F_VEC_OFF + VEC_BYTES + 1023) / 1024 * 1024;
-    static constexpr uint32_t F_A2_OFF = F_IMG, F_A3_OFF = F_A2_OFF + 128 * K2 * 2;
-    static constexpr uint32_t F_GT_OFF = F_IMG, F_RT_OFF = F_GT_OFF + 128 * 128 * 2;
-    static constexpr uint32_t F_ACT = 128 * K2 * 2 + 128 * N2 * 2;
-    static constexpr uint32_t F_CON = 128 * 128 * 2 + 16 * 128 * 2;
-    static constexpr uint32_t F_SMEM = F_IMG + (F_ACT > F_CON ? F_ACT : F_CON);
-    static constexpr uint32_t F_MAXC = (N2 > N3 ? N2 : N3) > 64 ? (N2 > N3 ? N2 : N3) : 64;
-    static constexpr uint32_t F_TCOLS = F_MAXC <= 32 ? 32 : F_MAXC <= 64 ? 64 : F_MAXC <= 128 ? 128 : 256;
-    static constexpr int F_BY_SMEM = (int)((227 * 1024) / (F_SMEM + 1024 + 256));   // + reserved + static
-    static constexpr int cmin(int a, int b) { return a < b ? a : b; }
-    static constexpr int F_CTAS = cmin(cmin(F_BY_SMEM, (int)(512 / F_TCOLS)), 6);
-    static_assert(F_RT_OFF + 16 * 128 * 2 <= F_SMEM && F_A3_OFF + 128 * N2 * 2 <= F_SMEM && F_CTAS >= 2,
-                  "forward layout");
-    // Backward kernel layout: the full image, then one region that holds A2 and A3 (the forward
-    // recomputation) until the layer-3 MMA has read them, dz3 (AB1) from the layer-3 epilogue until
-    // the dY2 MMA has read it, and dz2 in A3's place after that; then dE/dT per warp. Tensor memory
-    // reused from column 0 by every product; the skip terms of dY2 and dY1 are stored into the
-    // accumulator before their MMA, which adds onto them.
-    static constexpr uint32_t B_IMG = (IMG + 127) / 128 * 128;
-    static constexpr uint32_t B_A2_OFF = B_IMG, B_A3_OFF = B_A2_OFF + 128 * K2 * 2, B_AB1_OFF = B_IMG;
-    static constexpr uint32_t B_ACT = F_ACT > 128 * N3 * 2 ? F_ACT : 128 * N3 * 2;
-    static constexpr uint32_t B_X_OFF = B_IMG + B_ACT;
-    static constexpr uint32_t B_SMEM = B_X_OFF + BWD_SCRATCH;
-    static constexpr int B_BY_SMEM = (int)((227 * 1024) / (B_SMEM + 1024 + 256));
-    static constexpr int B_CTAS = cmin(cmin(B_BY_SMEM, (int)(512 / F_TCOLS)), E2 <= 32 ? 4 : 3);
-    static_assert(B_CTAS >= 2 && B_A3_OFF + 128 * N2 * 2 <= B_X_OFF, "backward layout");
-    static_assert(N3 <= 128, "forward tile");
-};
-
-using TcWater = TcShape<25, 50, 100>;
-using TcStudent = TcShape<8, 16, 32>;
-using TcPaper = TcShape<32, 64, 128>;
-
-template <int BF>
-__device__ __forceinline__ uint32_t pack2(float a, float b)
-{
-    if (BF) {
-        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-        return *reinterpret_cast<uint32_t *>(&h);
-    } else {
-        __half2 h = __floats2half2_rn(a, b);
-        return *reinterpret_cast<uint32_t *>(&h);
-    }
-}
-
-// Writes 8 consecutive K values of one row into a K-major core-matrix tile.
-template <int BF>
-__device__ __forceinline__ void st_row8(unsigned char *tile, int row, int k0, int K, const float *v)
-{
-    uint4 q;
-    q.x = pack2<BF>(v[0], v[1]);
-    q.y = pack2<BF>(v[2], v[3]);
-    q.z = pack2<BF>(v[4], v[5]);
-    q.w = pack2<BF>(v[6], v[7]);
-    *reinterpret_cast<uint4 *>(tile + tc::kmaj_off(row, k0, K)) = q;
-}
-
-// Skip term of a hidden layer of widths win -> wout at output o (Fig. 1(e,f)).
-template <int WIN, int WOUT>
-__device__ __forceinline__ float skip_of(const float *x, int o)
-{
-    if (WOUT == WIN) return x[o];
-    if (WOUT == 2 * WIN) return x[o % WIN];
-    return 0.0f;
-}
-
-struct TileCtx {
-    int atom, tj, c0, net;
-};
-
-// One thread's row of a tile as read from global memory: the chunk entry,
-// the neighbor count of its (atom, type) block and the slot's neighbor
-// geometry (s, u = d/r and, for the backward pass, ds/dr, r and j; all
-// evaluated in FP64 by the formatting kernel).  Fetched one tile ahead: the
-// slot loads do not wait for the count (they stay inside the type block's
-// sel slots), and the row's validity is applied when it is used.
-struct RowIn {
-    TileCtx ch;
-    int net, cnt, j;
-    float4 a;
-    float2 b;
-};
-
-template <bool BWD>
-__device__ __forceinline__ RowIn fetch_row(const ModelDev &md, const int4 *__restrict__ chunks, int tile, int ntiles,
-                                           int warp, int lane, const int32_t *__restrict__ nnei,
-                                           const int32_t *__restrict__ nlist, const float4 *__restrict__ envA,
-                                           const float2 *__restrict__ envB)
-{
-    RowIn r;
-    r.ch = TileCtx{-1, 0, 0, 0};
-    r.net = -1;
-    r.cnt = 0;
-    r.j = -1;
-    r.a = make_float4(0.f, 0.f, 0.f, 0.f);
-    r.b = make_float2(0.f, 0.f);
-    if (tile >= ntiles) return r;
-    const int4 c4 = chunks[(int64_t)tile * 4 + warp];
-    r.net = chunks[(int64_t)tile * 4].w;
-    r.ch = TileCtx{c4.x, c4.y, c4.z, c4.w};
-    if (c4.x >= 0) {
-        const int k = c4.z + lane;
-        r.cnt = nnei[(int64_t)c4.x * md.ntypes + c4.y];
-        if (k < md.sel[c4.y]) {
-            const int64_t slot = (int64_t)c4.x * md.nsel + md.sel_off[c4.y] + k;
-            r.a = envA[slot];
-            if (BWD) {
-                r.b = envB[slot];
-                r.j = nlist[slot];
-            }
-        }
-    }
-    return r;
-}
-
-// The environment row Rf = (s, s u_x, s u_y, s u_z) of Eq. 4 and the
-// geometry of this thread's row (zero on padded rows), plus layer 1 in
-// FP32; writes the layer-1 output row into A2.
-template <class S, int BF, bool BWD>
-__device__ __forceinline__ void rows_layer1(const RowIn &in, int lane, int row, const float *vec, unsigned char *A2,
-                                            float Rf[4], float t1[S::E0], float geo[6], int &j, bool &valid)
-{
-    valid = in.ch.atom >= 0 && in.ch.c0 + lane < in.cnt;
-    const float4 a = valid ? in.a : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float2 b = valid ? in.b : make_float2(0.f, 0.f);
-    j = valid ? in.j : -1;
-    Rf[0] = a.x;
-    Rf[1] = a.x * a.y;
-    Rf[2] = a.x * a.z;
-    Rf[3] = a.x * a.w;
-    geo[0] = a.y;                          // u
-    geo[1] = a.z;
-    geo[2] = a.w;
-    geo[3] = b.x;                          // ds/dr
-    geo[4] = b.y;                          // r
-    geo[5] = (BWD && valid) ? a.x / b.y : 0.f;      // s/r
-    const float *W1 = vec, *b1 = vec + S::K2;
-    const float s = Rf[0];
-    float buf[8];
-#pragma unroll
-    for (int k0 = 0; k0 < S::K2; k0 += 8) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int k = k0 + u;
-            float v = 0.0f;
-            if (k < S::E0) {
-                v = tc::tanh_fast(fmaf(s, W1[k], b1[k]));
-                t1[k] = v;
-                if (S::E0 == 1 || S::E0 == 2) v += s;
-            }
-            buf[u] = v;
-        }
-        st_row8<BF>(A2, row, k0, S::K2, buf);
-    }
-}
-
-// Layer-2 epilogue: z2 from TMEM, y2 = skip(t1) + tanh(z2 + b2); writes A3.
-template <class S, int BF>
-__device__ __forceinline__ void epi_layer2(uint32_t taddr, const float *vec, const float t1[S::E0], float t2[S::E1],
-                                           unsigned char *A3, int row)
-{
-    const float *b2 = vec + 2 * S::K2;
-#pragma unroll
-    for (int c0 = 0; c0 < S::N2; c0 += 16) {
-        float z[16];
-        tc::tmem_ld16(taddr + c0, z);
-        tc::tmem_ld_wait();
-        float buf[16];
-#pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int k = c0 + u;
-            float v = 0.0f;
-            if (k < S::E1) {
-                const float t = tc::tanh_fast(z[u] + b2[k]);
-                t2[k] = t;
-                v = skip_of<S::E0, S::E1>(t1, k) + t;
-            }
-            buf[u] = v;
-        }
-        st_row8<BF>(A3, row, c0, S::N2, buf);
-        st_row8<BF>(A3, row, c0 + 8, S::N2, buf + 8);
-    }
-}
-
-__device__ __forceinline__ int4 load_chunk(const int4 *chunks, int64_t idx) { return chunks[idx]; }
 
 template <class S, int BF>
 __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const float4 *__restrict__ envA,
@@ -291,12 +83,15 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const 
         nxt = fetch_row<false>(md, chunks, tile + gridDim.x, ntiles, warp, lane, nnei, nlist, envA, nullptr);
         const int net = in.net;
         if (net != cur_net) {
-            if (tid == 0) {   // W2^T and W3^T, then the vectors right after them
+            // starved (test of the bounded waits): no copy is issued, so nothing is in flight
+            // when the wait below gives up
+            const bool starve = md.wait_test == WT_EMBED_FWD_WEIGHTS;
+            if (tid == 0 && !starve) {   // W2^T and W3^T, then the vectors right after them
                 tc::mbar_expect_tx(&mbar_w, S::B3B_OFF + S::VEC_BYTES);
                 tc::bulk_g2s(img, wimg + (size_t)net * S::IMG, S::B3B_OFF, &mbar_w);
                 tc::bulk_g2s(img + S::F_VEC_OFF, wimg + (size_t)net * S::IMG + S::VEC_OFF, S::VEC_BYTES, &mbar_w);
             }
-            bool ok = tc::mbar_wait(&mbar_w, ph_w, kWaitLimit);
+            bool ok = tc::mbar_wait(&mbar_w, ph_w, starve ? (long)md.wait_short : kWaitLimit);
             ph_w ^= 1;
             if (!__syncthreads_and(ok)) {
                 if (tid == 0) atomicOr(err, 1);
@@ -837,42 +632,6 @@ __global__ void __launch_bounds__(kCbThreads) k_cb_write(ModelDev md, int64_t n,
         if (firstc) firstc[p * md.ntypes + tj] = dst;
         for (int c = 0; c < nch; ++c) chunks[dst + c] = make_int4(a, firstc ? (int)p : tj, c * 32, net);
     }
-}
-
-// D[p] = T T<^T of atom order[p] (T scaled by 1/sum(sel)), flattened a*M2 + b.
-__global__ void k_desc_f32(ModelDev md, const int32_t *__restrict__ order, int64_t n, const float *__restrict__ T,
-                           float *__restrict__ D)
-{
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int nd = md.desc_dim;
-    if (q >= n * nd) return;
-    const int64_t p = q / nd;
-    const int r = (int)(q - p * nd), a = r / md.m2, b = r - a * md.m2;
-    const float *Ta = T + (int64_t)order[p] * 4 * md.m1;
-    const float s = (float)(md.inv_nsel * md.inv_nsel);
-    const float4 x = *reinterpret_cast<const float4 *>(Ta + 4 * a);
-    const float4 y = *reinterpret_cast<const float4 *>(Ta + 4 * b);
-    D[q] = (x.x * y.x + x.y * y.y + x.z * y.z + x.w * y.w) * s;
-}
-
-// dE/dT (times 1/sum(sel)) of atom order[p] from dE/dD: one thread per (m, c).
-__global__ void k_dT_f32(ModelDev md, const int32_t *__restrict__ order, int64_t n, const float *__restrict__ T,
-                         const float *__restrict__ dD, float *__restrict__ dT)
-{
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int nq = 4 * md.m1;
-    if (q >= n * nq) return;
-    const int64_t p = q / nq;
-    const int r = (int)(q - p * nq), m = r >> 2, c = r & 3;
-    const int a_id = order[p];
-    const float *Ta = T + (int64_t)a_id * nq;
-    const float *dDa = dD + p * md.desc_dim;
-    const float inv = (float)md.inv_nsel;
-    float acc = 0.f;
-    for (int b = 0; b < md.m2; ++b) acc = fmaf(dDa[m * md.m2 + b], Ta[4 * b + c], acc);
-    if (m < md.m2)
-        for (int a = 0; a < md.m1; ++a) acc = fmaf(dDa[a * md.m2 + m], Ta[4 * a + c], acc);
-    dT[(int64_t)a_id * nq + r] = acc * inv * inv;
 }
 
 // Fitting net of the MIX-16 scheme on the tensor cores (tcgen05), fused with
@@ -1534,6 +1293,7 @@ dp_status build_chunks_batch(dp_model *m, dp_nlist *nl, int64_t p0, int64_t nb, 
 dp_status pack_tc_weights(dp_model *m)
 {
     const int *e = m->dev.emb.wout;
+    if (m->d_tcw_x3) DP_TRY(pack_x3_weights(m));
     if (e[0] == 25) DP_TRY(pack_all<TcWater>(m));
     else if (e[0] == 8) DP_TRY(pack_all<TcStudent>(m));
     else DP_TRY(pack_all<TcPaper>(m));

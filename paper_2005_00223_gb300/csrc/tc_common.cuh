@@ -41,6 +41,15 @@ __host__ __device__ constexpr uint32_t idesc_f16_mn(int M, int N)
     return (1u << 4) | (1u << 15) | (1u << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor of kind::f16 with each operand K-major (0) or
+// MN-major (1, the transpose bits 15 and 16), FP32 accumulator, fp16 (bf16
+// = 0) or bf16 (bf16 = 1) operands, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_f16_major(int M, int N, int bf16, int a_mn, int b_mn)
+{
+    return (1u << 4) | ((uint32_t)bf16 << 7) | ((uint32_t)bf16 << 10) | ((uint32_t)a_mn << 15) |
+           ((uint32_t)b_mn << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 // Byte offset of element (mn, k) of an MN-major no-swizzle tile with MN rows:
 // core matrices of 8 K-rows x 16 bytes (8 consecutive MN elements); groups of
 // 8 MN elements 128 bytes apart (the descriptor's sbo), groups of 8 K-rows
@@ -84,6 +93,26 @@ __device__ __forceinline__ void mma_kloop_mn(uint32_t d_tmem, uint32_t a_saddr, 
         const int kg = (k0 >> 3) + 2 * ks;
         uint64_t ad = smem_desc(a_saddr + kg * lbo_a, lbo_a, 128);
         uint64_t bd = smem_desc(b_saddr + kg * lbo_b, lbo_b, 128);
+        uint32_t acc = (accumulate || ks > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    }
+}
+
+// D[tmem] (+)= A B^T with A K-major ([128][K], kmaj_off layout) and B
+// MN-major with MN extent NB (mnmaj_off layout), K a multiple of 16; M = 128.
+// A K-major tile [R][C] (kmaj_off with K = C) is, byte for byte, the
+// MN-major tile of its transpose (mnmaj_off with MN = C), so a weight tile
+// stored for x W^T serves as B of the transposed product as well.
+__device__ __forceinline__ void mma_kloop_bmn(uint32_t d_tmem, uint32_t a_saddr, uint32_t b_saddr, int NB, int K,
+                                              uint32_t idesc, bool accumulate)
+{
+    const uint32_t sbo_a = (uint32_t)(K >> 3) * 128, lbo_b = (uint32_t)(NB >> 3) * 128;
+    for (int ks = 0; ks < (K >> 4); ++ks) {
+        uint64_t ad = smem_desc(a_saddr + ks * 256, 128, sbo_a);
+        uint64_t bd = smem_desc(b_saddr + 2 * ks * lbo_b, lbo_b, 128);
         uint32_t acc = (accumulate || ks > 0) ? 1u : 0u;
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"

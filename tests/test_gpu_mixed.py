@@ -81,7 +81,38 @@ def test_mix16_tensor_core_error_budget(dp, orc, prec, name, cfg, coord, typ, bo
     assert err["W_rel"] < 10 * u
 
 
-@pytest.mark.parametrize("prec", ["mix32", "bf16", "fp16"])
+@pytest.mark.parametrize("name,cfg,coord,typ,box", systems(), ids=[s[0] for s in systems()])
+def test_split_bf16_tensor_core_error_budget(dp, orc, name, cfg, coord, typ, box):
+    """bf16x3 on tcgen05: every embedding product as hi hi + hi lo + lo hi of split bf16 operands
+    (16 significant bits, u = 2^-16), FP32 accumulation, tanhf; FP32 fitting net.  Budgets in units
+    of that u as for MIX-16, and the force criterion 1e-3 of the RMS force."""
+    m = dp.Model(cfg, 1, params=dpsynth.model_params(cfg, 1))
+    nl = dp.NeighborList(m, coord, typ, box)
+    got = nl.compute(coord, box, "bf16x3")
+    ref = orc.Model(cfg, m.params).compute(coord, typ, box)
+    err = _errors(got, ref)
+    print(name, "bf16x3", err)
+    assert np.isfinite(got[2]).all()
+    u = 2.0 ** -16
+    assert err["dE_per_sum_abs_Ei"] < 2 * u
+    assert err["dEi_max_rel"] < 4 * u
+    assert err["F_rmse_rel"] < 10 * u
+    assert err["W_rel"] < 10 * u
+    assert err["F_rmse_rel"] < 1e-3
+
+
+def test_split_bf16_md_runs(dp):
+    cfg = dpsynth.copper_config()
+    coord, typ, box = dpsynth.copper_fcc(1, ncell=10)
+    mass = np.array([dpsynth.MASS["Cu"]])
+    vel = dpsynth.velocities(mass[typ], 300.0, 1)
+    m = dp.Model(cfg, 1)
+    st = dp.MDState(m, coord, vel, typ, mass, box, skin=2.0)
+    th = st.step(20, 1.0, "bf16x3", thermo_every=10)
+    assert np.isfinite(th).all()
+
+
+@pytest.mark.parametrize("prec", ["mix32", "bf16", "fp16", "bf16x3"])
 def test_paper_water_model_error_budget(dp, orc, prec):
     """The paper's production water model (embedding 32-64-128, 144 neighbors, Sec. 5.1) on the
     mixed schemes: the 32-64-128 tensor-core embedding and 2048-wide fitting kernels against the
@@ -99,7 +130,7 @@ def test_paper_water_model_error_budget(dp, orc, prec):
         assert err["dE_rel"] < 1e-6 and err["dEi_max_rel"] < 1e-5
         assert err["F_rmse_rel"] < 1e-5 and err["W_rel"] < 1e-5
     else:
-        u = 2.0 ** -9 if prec == "bf16" else 2.0 ** -11
+        u = {"bf16": 2.0 ** -9, "fp16": 2.0 ** -11, "bf16x3": 2.0 ** -16}[prec]
         assert err["dE_per_sum_abs_Ei"] < 2 * u
         assert err["dEi_max_rel"] < 4 * u
         assert err["F_rmse_rel"] < 10 * u
