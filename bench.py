@@ -81,6 +81,9 @@ def workload(name: str, model: str = "full"):
 # Initial temperature (K) and thermo interval (steps; None: one row at the end) of the timed MD.
 # water12k follows the paper's production protocol: 330 K, a thermo row every 20 steps (Sec. 5.1).
 MD_PROTOCOL = {"water12k": (330.0, 20)}
+# Fixed-interval skin-list rebuilds (steps) on top of the displacement criterion; water12k follows the
+# paper's production protocol: a 2 A skin list built every 50 steps (Sec. 5.1).
+MD_REBUILD = {"water12k": 50}
 
 
 def md_protocol(name: str, steps: int):
@@ -214,6 +217,7 @@ def run_mine(args, rank, world):
     nnei_total = int((nlist0 >= 0).sum())
     nl0.close()
     state = dp.MDState(model, coord, vel, typ, mass, box, skin=2.0)
+    state.rebuild_every(MD_REBUILD.get(args.workload, 0))
     state.step(args.warmup, dt, args.precision)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     # Untimed pass of the same length with every kernel group bracketed by events: the per-group
@@ -331,10 +335,11 @@ PATHS = ("fp64", "mix32", "bf16", "fp16", "bf16x3", "student", "student_judged")
 JUDGE_EVERY = 10
 
 
-def _md_ms_per_step(dp, model, coord, vel, typ, mass, box, dt, prec, steps, warmup, stream):
+def _md_ms_per_step(dp, model, coord, vel, typ, mass, box, dt, prec, steps, warmup, stream, rebuild_every=0):
     """Device ms per NVE step of `steps` replayed steps after `warmup` (CUDA events on the model's stream)."""
     import torch
     state = dp.MDState(model, coord, vel, typ, mass, box, skin=2.0)
+    state.rebuild_every(rebuild_every)
     state.step(warmup, dt, prec)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -360,22 +365,35 @@ def _errors(E, Ei, F, W, ref, n):
             "meets_1e-3_eV_per_A": rmse <= 1e-3, "meets_1e-3_at_1eV_per_A_scale": rmse / frms <= 1e-3}
 
 
-def distil_student(dp, S, dev):
+def distil_student(dp, S, dev, temps=(300.0, 1200.0), frames_per_temp=24, adam_steps=800, md_prec="mix32",
+                   label_prec="mix32", frames_per_run=None, relative=False):
     """Teacher (the seeded copper model) and a student distilled from its own MD, trained by libdp.
 
-    Teacher frames every 5 NVE steps at 300 K and 1,200 K on 4,000 atoms (24 per temperature),
-    800 Adam steps of one frame each with p_e = 1, p_f = 100 / RMS(F)^2 (the recipe of the
-    distillation test).  Returns (teacher, student, teacher RMS force of the frames)."""
+    Teacher frames every 5 NVE steps on 4,000 atoms, frames_per_temp at each temperature (default 24
+    at 300 K and 1,200 K) from runs of frames_per_run frames (default: one run), each run starting at
+    the lattice with its own Maxwell-Boltzmann velocities; Adam steps of one frame each with
+    p_e = 1, p_f = 100 / RMS(F)^2, the learning rate decaying 3e-3 -> 1e-4 (the recipe of the
+    distillation test).  Short runs keep the seeded teacher near the lattice: its long runs at
+    900-1200 K leave it (a random-weight model has no physical minimum there).  relative: the force
+    weight of each frame is 100 / RMS(F_k)^2 instead (a relative force loss), so that the frames of
+    every temperature count alike although their force scales differ by orders.  Returns (teacher,
+    student, teacher RMS force of the frames, number of frames, RMS force per temperature)."""
     cfg = dpsynth.copper_config()
     teacher = dp.Model(cfg, 0, params=dpsynth.model_params(cfg, 1))
     c4, t4, b4 = dpsynth.copper_fcc(1, ncell=10)
     mass = np.array([dpsynth.MASS["Cu"]])
-    vels = [dpsynth.velocities(mass[t4], T, 10 + k) for k, T in enumerate((300.0, 1200.0))]
-    X, E, F = S.teacher_frames(teacher, c4, t4, b4, mass, vels, nframes=24, stride=5, dt_fs=1.0)
+    per_run = frames_per_run or frames_per_temp
+    runs = max(1, frames_per_temp // per_run)
+    vels = [dpsynth.velocities(mass[t4], T, 10 + k * 100003 + r) for k, T in enumerate(temps) for r in range(runs)]
+    X, E, F = S.teacher_frames(teacher, c4, t4, b4, mass, vels, nframes=per_run, stride=5, dt_fs=1.0,
+                               md_prec=md_prec, label_prec=label_prec)
     frms = float(np.sqrt((F ** 2).sum(-1).mean()))
+    per_t = F.reshape(len(temps), -1, *F.shape[1:])
+    frms_t = [float(np.sqrt((f ** 2).sum(-1).mean())) for f in per_t]
     stu = dp.Model(dpsynth.copper_student_config(), seed=2)
-    S.train(stu, t4, b4, X, E, F, steps=800, lr0=3e-3, lr1=1e-4, p_e=1.0, p_f=100.0 / frms ** 2)
-    return teacher, stu, frms
+    pf = 100.0 / ((F ** 2).sum(-1).mean(-1) if relative else frms ** 2)
+    S.train(stu, t4, b4, X, E, F, steps=adam_steps, lr0=3e-3, lr1=1e-4, p_e=1.0, p_f=pf)
+    return teacher, stu, frms, len(X), frms_t
 
 
 def run_paths(args, name, steps, warmup, ref, ref_kind, fp64_ms=None, student=None):
@@ -403,8 +421,19 @@ def run_paths(args, name, steps, warmup, ref, ref_kind, fp64_ms=None, student=No
         nl = dp.NeighborList(full, coord, typ, box)
         ref = nl.compute(coord, box, "fp64")
         nl.close()
+    nl = dp.NeighborList(full, coord, typ, box)
+    nnei_total = int((nl.get()[0] >= 0).sum())
+    nl.close()
+    work_real = sum(flops_per_group(cfg, nnei_total, n).values())
+    work_pad = sum(flops_per_group(cfg, n * cfg.nsel, n).values())
     out = {"workload": desc, "atoms": n, "steps": steps, "warmup": warmup, "error_reference": ref_kind,
-           "rms_force_eV_per_A": float(np.sqrt((ref[2] ** 2).sum(1).mean())), "paths": {}}
+           "rms_force_eV_per_A": float(np.sqrt((ref[2] ** 2).sum(1).mean())),
+           "rebuild_every": MD_REBUILD.get(name, 0),
+           "work": {"real_neighbors_per_atom": nnei_total / n, "mflop_per_atom_eval": work_real / n / 1e6,
+                    "mflop_per_atom_eval_if_padded_rows_counted": work_pad / n / 1e6,
+                    "counted": "multiply-adds x 2 of the embedding net (forward, input gradient), contraction, "
+                               "descriptor, fitting net (forward, input gradient) over real neighbors"},
+           "paths": {}}
     for p in args.paths:
         if p.startswith("student") and (student is None or cfg.ntypes != 1):
             continue
@@ -442,7 +471,8 @@ def run_paths(args, name, steps, warmup, ref, ref_kind, fp64_ms=None, student=No
                         "judgements": int(len(rm)), "fallback_windows": int(fb.sum()),
                         "judged_rmse_mean_eV_per_A": float(rm.mean()), "judged_rmse_max_eV_per_A": float(rm.max())})
         else:
-            ms = _md_ms_per_step(dp, model, coord, vel, typ, mass, box, dt, prec, steps, warmup, stream)
+            ms = _md_ms_per_step(dp, model, coord, vel, typ, mass, box, dt, prec, steps, warmup, stream,
+                                 MD_REBUILD.get(name, 0))
         step_s = ms * 1e-3
         rec.update({"ms_per_step": ms, "s_per_step_atom": step_s / n, "ns_per_day": 86400.0 * dt * 1e-6 / step_s})
         rec.update(_errors(E, Ei, F, W, ref, n))
@@ -593,11 +623,14 @@ def run_grad(args, rank, world):
 def run_judged(args, rank, world):
     """Distilled student MD judged by the full model every 10 steps.
 
-    Untimed: teacher frames from its own NVE at 300 K and 1,200 K on 4,000
-    atoms and 800 Adam steps of the student on them (the recipe of the
-    distillation test).  Timed: judged MD of the trained student on the
-    workload, the teacher evaluated at every judgement and taking over while
-    the student's force RMSE exceeds 0.1 x the teacher's RMS force.
+    Untimed: teacher frames every 5 steps of its own NVE at each of --temps on
+    4,000 atoms (--frames-per-temp each) and --adam-steps one-frame Adam steps
+    of the student on them.  Defaults: 300 K and 1,200 K, 24 frames each, 800
+    steps (the distillation test's recipe); the copper student workload of
+    the paper-scale run is 300/600/900/1200 K x 5,000 frames and 20,000 steps
+    on 108,000 atoms for 1,000 steps.  Timed: judged MD of the trained student
+    on the workload, the teacher evaluated at every judgement and taking over
+    while the student's force RMSE exceeds 0.1 x the teacher's RMS force.
     """
     import torch
 
@@ -606,7 +639,13 @@ def run_judged(args, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    teacher, stu, _ = distil_student(dp, S, dev)
+    temps = tuple(float(t) for t in args.temps.split(","))
+    t0 = time.perf_counter()
+    teacher, stu, frms_train, nframes, frms_t = distil_student(dp, S, dev, temps, args.frames_per_temp,
+                                                               args.adam_steps, args.teacher_md_precision,
+                                                               args.label_precision, args.frames_per_run,
+                                                               args.relative_force_loss)
+    distil_s = time.perf_counter() - t0
     _, coord, typ, box, mass, dt, desc = workload(args.workload)
     n = len(typ)
     vel = dpsynth.velocities(mass[typ], 300.0, 1)
@@ -656,7 +695,17 @@ def run_judged(args, rank, world):
             "ms_per_step": ms / steps, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "ns_per_day": 86400.0 * dt * 1e-6 / step_s, "dtype": args.precision, "precision": args.precision,
             "data": "synthetic (seeded FCC copper; student distilled from the seeded teacher's own MD)",
+            "distillation": {"temperatures_K": list(temps), "frames": nframes, "frame_stride_steps": 5,
+                             "frame_atoms": 4000, "teacher_md_precision": args.teacher_md_precision,
+                             "label_precision": args.label_precision, "adam_steps": args.adam_steps,
+                             "frames_per_run": args.frames_per_run or args.frames_per_temp,
+                             "force_loss": "relative (100 / RMS(F_k)^2 per frame)" if args.relative_force_loss
+                             else "100 / RMS(F)^2 over all frames",
+                             "teacher_rms_force_of_frames_eV_per_A": frms_train,
+                             "teacher_rms_force_per_temperature_eV_per_A": frms_t, "seconds": distil_s},
             "config": {"workload": desc, "atoms": n, "judge_every": every, "rmse_max_eV_per_A": rmse_max,
+                       "fallback_windows_at_0.05_eV_per_A": int((rm > 0.05).sum()),
+                       "student_rmse_mean_over_rms_force": float(rm.mean()) / (rmse_max / 0.1),
                        "teacher_rms_force_eV_per_A": rmse_max / 0.1, "judgements": int(len(rm)),
                        "fallback_windows": int(fb.sum()), "student_rmse_max": float(rm.max()),
                        "student_rmse_mean": float(rm.mean()), "parallelism": "1 GPU",
@@ -790,8 +839,17 @@ def main():
     ap.add_argument("--paths", default=",".join(PATHS),
                     help="comma-separated paths timed beside the headline with their errors "
                          "(fp64, mix32, bf16, fp16, bf16x3, student, student_judged), or 'none'")
-    ap.add_argument("--paths-workloads", default="cu4000,cu108k",
+    ap.add_argument("--paths-workloads", default="cu4000,cu108k,water12k",
                     help="workloads of the paths blocks when the headline is the default FP64 copper 4,000 line")
+    ap.add_argument("--temps", default="300,1200", help="judged task: teacher MD temperatures (K)")
+    ap.add_argument("--frames-per-temp", type=int, default=24, help="judged task: teacher frames per temperature")
+    ap.add_argument("--adam-steps", type=int, default=800, help="judged task: student training steps")
+    ap.add_argument("--relative-force-loss", action="store_true",
+                    help="judged task: weight each frame's force loss by 1 / its RMS force squared")
+    ap.add_argument("--frames-per-run", type=int, default=0,
+                    help="judged task: frames per teacher run (0: one run per temperature)")
+    ap.add_argument("--teacher-md-precision", default="mix32", help="judged task: precision of the teacher's MD")
+    ap.add_argument("--label-precision", default="mix32", help="judged task: precision of the teacher's labels")
     ap.add_argument("--task", default="md", choices=["md", "grad", "judged"],
                     help="md: NVE steps (default); grad: force-loss parameter gradient over 32 water frames; "
                          "judged: distilled student MD judged by the full model")
@@ -840,7 +898,7 @@ def paths_blocks(args, out, ref):
     student = None
     if any(p.startswith("student") for p in args.paths):
         t0 = time.perf_counter()
-        teacher, stu, frms = distil_student(dp, S, dev)
+        teacher, stu, frms, _, _ = distil_student(dp, S, dev)
         student = (teacher, stu)
         distil_s = time.perf_counter() - t0
     kind = "FP64 oracle (cpu_baseline leg)" if ref is not None else "FP64 GPU path (oracle not run)"
@@ -853,7 +911,7 @@ def paths_blocks(args, out, ref):
             ref2 = None
             if not args.no_cpu_baseline:
                 base2, ref2 = cpu_baseline(args, name=name, md_steps=False)
-            steps = max(JUDGE_EVERY, min(args.steps, 10))
+            steps = max(JUDGE_EVERY, min(args.steps, 10), MD_REBUILD.get(name, 0))
             blocks[name] = run_paths(args, name, steps, min(args.warmup, 5), ref2,
                                      "FP64 oracle (cpu_baseline leg)" if ref2 is not None else
                                      "FP64 GPU path (oracle not run)", None, student)

@@ -200,6 +200,39 @@ dp_status dp_nlist_get(const dp_nlist *nl, int32_t *nlist, int64_t *n_truncated)
 
 void dp_nlist_destroy(dp_nlist *nl);
 
+/* Ghost atoms of a spatial decomposition (Sec. 4.3: each rank evaluates
+ * the atoms of its sub-domain with the ghost atoms of a halo around it).
+ * Atoms [0, n_centers) of the list are centers; atoms [n_centers, n) are
+ * ghosts: they appear in the centers' neighbor rows but have no rows of
+ * their own (cleared after every format), so an evaluation gives them
+ * energy 0 and no virial, and their forces hold only the reactions
+ * F_j -= g_ij of the centers' pairs, which the caller returns to the
+ * ghosts' owners.  E and W sum over the centers.  n_centers = n (the
+ * default) restores a plain list.  The ghosts' coordinates must be images
+ * placed where the centers see them; with a slab along x the box's x edge
+ * must exceed the extended region by r_c so that no periodic image of a
+ * ghost reaches a center.  Errors: DP_ERR_ARG (NULL, n_centers outside
+ * 0..n). */
+dp_status dp_nlist_set_centers(dp_nlist *nl, int64_t n_centers);
+
+/* The halo of one side of a slab (Sec. 4.3): of the atoms d_coord [n][3]
+ * (device, FP64), d_type [n], those with lo <= x < hi, in index order, as
+ * d_idx [count] (their indices), d_out_coord [count][3] (x + shift_x, y, z:
+ * the positions in the receiving rank's frame) and d_out_type [count];
+ * *d_count = count (device int64).  At most cap are written (count may
+ * exceed cap: the caller then retries with more room).  Enqueued on
+ * `stream`.  Errors: DP_ERR_ARG, DP_ERR_CUDA. */
+dp_status dp_halo_select_dev(int64_t n, const double *d_coord, const int32_t *d_type, double lo, double hi,
+                             double shift_x, int64_t cap, int32_t *d_idx, double *d_out_coord, int32_t *d_out_type,
+                             int64_t *d_count, void *stream);
+
+/* The reverse halo: d_force[d_idx[k]] += d_f_ghost[k] (3 components) for
+ * k < m, all device memory; the indices of one call must be distinct (one
+ * call per halo side keeps the sums in a fixed order).  Enqueued on
+ * `stream`.  Errors: DP_ERR_ARG, DP_ERR_CUDA. */
+dp_status dp_halo_accumulate_dev(int64_t m, const int32_t *d_idx, const double *d_f_ghost, double *d_force,
+                                 void *stream);
+
 /* Formatted neighbor list that allocates no device memory.  The paper has
  * no counterpart: this entry point serves callers that cannot allocate
  * device memory, such as a host MD engine whose device memory belongs to
@@ -318,6 +351,16 @@ dp_status dp_md_state_create(dp_model *m, int64_t n, const double *coord, const 
  * the state again with a larger cand_cap). */
 dp_status dp_md_step(dp_model *m, dp_md_state *s, int64_t nsteps, double dt_fs, dp_precision prec,
                      int32_t thermo_every, double *thermo);
+
+/* Fixed-interval list rebuilds (Sec. 5.1: the paper's production runs
+ * build the neighbor list with a 2 A skin every 50 steps).  every > 0: the
+ * later steps of dp_md_step and dp_md_step_judged also rebuild the skin
+ * list at every every-th step, counted from this call, besides the
+ * rebuilds that the displacement criterion (an atom moved more than
+ * skin/2) triggers; every = 0 (the default): the displacement criterion
+ * alone.  Synchronises the model's stream.  Errors: DP_ERR_ARG (NULL
+ * state, every < 0), DP_ERR_CUDA, DP_ERR_OOM. */
+dp_status dp_md_set_rebuild_every(dp_md_state *s, int32_t every);
 
 /* The learned fast path with the full model as judge and fallback: nsteps
  * NVE steps of `s` (created with `student`) driven by the student's forces;

@@ -19,7 +19,8 @@ from ._lib import (DP_FP64, DP_MIX32, DP_MIX_BF16, DP_MIX_FP16, DPError, EXPORTS
                    dp_nlist_update, dp_profile_enable, dp_profile_group_name, dp_profile_read, dp_profile_select,
                    dp_nlist_update_dev, dp_param_grad, dp_force_loss_grad, dp_force_loss_grad_dev, dp_adam_step,
                    dp_model_sync_params, dp_md_step_judged, dp_nlist_format_noalloc, dp_tanh_f64_dev,
-                   dp_nlist_build_frames, dp_ozaki_dgemm_dev, dp_test_starve_wait)
+                   dp_nlist_build_frames, dp_ozaki_dgemm_dev, dp_test_starve_wait,
+                   dp_md_set_rebuild_every, dp_nlist_set_centers, dp_halo_select_dev, dp_halo_accumulate_dev)
 
 
 def build(force: bool = False) -> str:
@@ -129,6 +130,10 @@ class MDState:
 
     def get(self):
         return dp_md_state_get(self.h, self.n)
+
+    def rebuild_every(self, every: int):
+        """Also rebuild the skin list every `every` steps (0: only the displacement criterion)."""
+        dp_md_set_rebuild_every(self.h, every)
 
     def save(self, path):
         """Checkpoint (coordinates, velocities, forces, step, box, types, masses) to a file."""

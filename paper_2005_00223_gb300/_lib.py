@@ -32,7 +32,8 @@ EXPORTS = [
     "dp_md_step", "dp_md_state_get", "dp_md_state_save", "dp_md_state_load", "dp_md_state_destroy", "dp_param_grad", "dp_force_loss_grad",
     "dp_force_loss_grad_dev", "dp_adam_step", "dp_model_sync_params", "dp_md_step_judged",
     "dp_nlist_format_noalloc", "dp_tanh_f64_dev", "dp_nlist_build_frames", "dp_ozaki_dgemm_dev",
-    "dp_test_starve_wait",
+    "dp_test_starve_wait", "dp_md_set_rebuild_every", "dp_nlist_set_centers", "dp_halo_select_dev",
+    "dp_halo_accumulate_dev",
 ]
 
 
@@ -85,6 +86,10 @@ def load(path: str = LIB_PATH):
             "dp_nlist_build_frames": ([P, I32, I64, P, P, P, D, D, I32, P], C.c_int),
             "dp_ozaki_dgemm_dev": ([P, I64, I32, I32, P, P, P, P], C.c_int),
             "dp_test_starve_wait": ([P, I32, I64], C.c_int),
+            "dp_md_set_rebuild_every": ([P, I32], C.c_int),
+            "dp_nlist_set_centers": ([P, I64], C.c_int),
+            "dp_halo_select_dev": ([I64, P, P, D, D, D, I64, P, P, P, P, P], C.c_int),
+            "dp_halo_accumulate_dev": ([I64, P, P, P, P], C.c_int),
             "dp_param_grad": ([P, P, P, P, P, D, D, C.c_int, P, P, P], C.c_int),
             "dp_force_loss_grad": ([P, P, P, P, P, D, D, D, C.c_int, P, P], C.c_int),
             "dp_force_loss_grad_dev": ([P, P, P, P, P, P, D, D, C.c_int, P, P, P], C.c_int),
@@ -322,6 +327,25 @@ def dp_test_starve_wait(m, which: int, polls: int = 0):
     _check(load().dp_test_starve_wait(m, int(which), int(polls)), "dp_test_starve_wait")
 
 
+def dp_nlist_set_centers(nl, n_centers: int):
+    """Atoms [0, n_centers) are centers, the rest ghosts (neighbors only)."""
+    _check(load().dp_nlist_set_centers(nl, int(n_centers)), "dp_nlist_set_centers")
+
+
+def dp_halo_select_dev(d_coord, d_type, lo: float, hi: float, shift_x: float, d_idx, d_out_coord, d_out_type,
+                       d_count, stream=None):
+    """Atoms with lo <= x < hi, in index order, packed with x shifted (device tensors; cap = d_idx.numel())."""
+    _check(load().dp_halo_select_dev(int(d_type.numel()), _ptr(d_coord), _ptr(d_type), float(lo), float(hi),
+                                     float(shift_x), int(d_idx.numel()), _ptr(d_idx), _ptr(d_out_coord),
+                                     _ptr(d_out_type), _ptr(d_count), _stream(stream)), "dp_halo_select_dev")
+
+
+def dp_halo_accumulate_dev(d_idx, d_f_ghost, d_force, stream=None):
+    """d_force[d_idx[k]] += d_f_ghost[k] (device tensors, distinct indices)."""
+    _check(load().dp_halo_accumulate_dev(int(d_idx.numel()), _ptr(d_idx), _ptr(d_f_ghost), _ptr(d_force),
+                                         _stream(stream)), "dp_halo_accumulate_dev")
+
+
 def dp_nlist_destroy(nl):
     if nl:
         load().dp_nlist_destroy(nl)
@@ -419,6 +443,11 @@ def dp_md_step_judged(student, teacher, s, nsteps: int, dt_fs: float, student_pr
            "dp_md_step_judged")
     k = nsteps // judge_every
     return rm[:k], fb[:k]
+
+
+def dp_md_set_rebuild_every(s, every: int):
+    """Also rebuild the skin list every `every` MD steps (0: only when an atom moved > skin/2)."""
+    _check(load().dp_md_set_rebuild_every(s, int(every)), "dp_md_set_rebuild_every")
 
 
 def dp_md_state_save(s, path: str):

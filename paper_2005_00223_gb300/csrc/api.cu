@@ -118,21 +118,31 @@ dp_status compute_device(dp_model *m, dp_nlist *nl, const double *d_coord, dp_pr
         if (d_virial) DP_CUDA(cudaMemsetAsync(d_virial, 0, 9 * sizeof(double), st));
         return DP_OK;
     }
+    dp_status r = DP_OK;
     switch (prec) {
     case DP_FP64:
-        return compute_fp64(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+        r = compute_fp64(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+        break;
     case DP_MIX32:
-        return compute_mix32(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+        r = compute_mix32(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+        break;
     case DP_MIX_BF16:
-        return compute_mix16(m, nl, 1, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+        r = compute_mix16(m, nl, 1, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+        break;
     case DP_MIX_FP16:
-        return compute_mix16(m, nl, 0, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+        r = compute_mix16(m, nl, 0, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+        break;
     case DP_MIX_BF16X3:
-        return compute_mix_x3(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+        r = compute_mix_x3(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+        break;
     default:
         set_error("precision %d is not built into this library", (int)prec);
         return DP_ERR_UNSUPPORTED;
     }
+    const int64_t nc = centers_of(nl);
+    if (r == DP_OK && nc < nl->n)   // ghosts have no neighbors: their fitting-net values are not energies
+        DP_CUDA(cudaMemsetAsync(d_atom_energy + nc, 0, sizeof(double) * (size_t)(nl->n - nc), st));
+    return r;
 }
 
 // SplitMix64 (Steele, Lea and Flood 2014) and Box-Muller normals, cosine
@@ -450,13 +460,6 @@ void dp_model_destroy(dp_model *m)
 
 // ------------------------------------------------------------ neighbor list
 
-static void nlist_graph_drop(dp_nlist *nl)
-{
-    if (nl->cgraph_exec) cudaGraphExecDestroy(nl->cgraph_exec);
-    if (nl->cgraph) cudaGraphDestroy(nl->cgraph);
-    nl->cgraph_exec = nullptr;
-    nl->cgraph = nullptr;
-}
 
 static void nlist_free(dp_nlist *nl)
 {

@@ -177,6 +177,7 @@ struct dp_model {
 struct dp_nlist {
     const dp_model *m = nullptr;
     int64_t n = 0;
+    int64_t n_centers = -1;           // atoms [0, n_centers) are centers; the rest are ghosts (-1: all)
     double rcut = 0, skin = 0, rlist = 0;
     int32_t cap = 0;
     double L[3] = {0, 0, 0};
@@ -226,6 +227,8 @@ struct dp_md_state {
     double *d_e = nullptr;            // [n] atom energies
     double *d_scal = nullptr;         // [16]: E, W[9], KE, ...
     double *d_thermo = nullptr;       // ring of thermo rows
+    unsigned long long *d_steps = nullptr;   // steps since the fixed-interval rebuilds were switched on
+    int32_t rebuild_every = 0;        // > 0: also rebuild the skin list every that many steps
     int64_t thermo_cap = 0;
     double box[9] = {0};
     int64_t step = 0;
@@ -280,6 +283,11 @@ dp_status compute_mix16(dp_model *m, dp_nlist *nl, int bf16, double *d_energy, d
 // FP32 fitting net over all atoms (type-sorted positions): D, dD [n][desc], E_i FP64.
 dp_status fit_f32(dp_model *m, dp_nlist *nl, const float *D, float *dD, double *d_atom_energy, cudaStream_t st);
 dp_status pack_x3_weights(dp_model *m);
+// Ghost atoms of a spatial decomposition (dp_nlist_set_centers): their list rows are cleared after each
+// format, so they appear only as neighbors.
+dp_status clear_ghost_rows(const dp_model *m, dp_nlist *nl, cudaStream_t st);
+void nlist_graph_drop(dp_nlist *nl);   // drops the captured host-array evaluation of a list
+inline int64_t centers_of(const dp_nlist *nl) { return nl->n_centers >= 0 ? nl->n_centers : nl->n; }
 dp_status compute_mix_x3(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
                          double *d_virial, double *d_atom_virial, cudaStream_t st);
 dp_status param_grad_device(dp_model *m, dp_nlist *nl, const double *d_v, const double *d_ab, dp_precision prec,

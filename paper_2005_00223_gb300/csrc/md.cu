@@ -41,9 +41,14 @@ __global__ void k_kick_drift_check(int64_t n, double *__restrict__ v, const doub
                                    const int32_t *__restrict__ type, const double *__restrict__ minv, double half_dt,
                                    double *__restrict__ x, double dt, BoxDev bx, Pos4 *__restrict__ pos,
                                    float4 *__restrict__ posf, const Pos4 *__restrict__ ref, double lim2,
-                                   int32_t *flags)
+                                   int32_t *flags, unsigned long long *steps, int every)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i == 0 && every > 0) {   // fixed-interval rebuilds: every `every`-th step builds the list again
+        const unsigned long long c = *steps + 1;
+        *steps = c;
+        if (c % (unsigned long long)every == 0) flags[1] = 1;
+    }
     if (i >= n) return;
     const int ti = type[i];
     const double s = half_dt * minv[ti];
@@ -108,7 +113,8 @@ dp_status md_step_body(dp_model *m, dp_md_state *s, dp_precision prec, double dt
         DP_CUDA(cudaMemsetAsync(nl->d_flags + 1, 0, sizeof(int32_t), st));
         k_kick_drift_check<<<nblk(n), 256, 0, st>>>(n, s->d_v, s->d_f, nl->d_type, s->d_minv, 0.5 * dt_fs, s->d_x,
                                                     dt_fs, bx, (Pos4 *)nl->d_pos, (float4 *)nl->d_posf,
-                                                    (const Pos4 *)nl->d_ref, lim * lim, nl->d_flags);
+                                                    (const Pos4 *)nl->d_ref, lim * lim, nl->d_flags, s->d_steps,
+                                                    s->rebuild_every);
     }
     DP_CUDA(cudaGetLastError());
     DP_TRY(nlist_build_device(nl, st, true));
@@ -273,7 +279,23 @@ void dp_md_state_destroy(dp_md_state *s)
     cudaFree(s->d_e);
     cudaFree(s->d_scal);
     cudaFree(s->d_thermo);
+    cudaFree(s->d_steps);
     delete s;
+}
+
+dp_status dp_md_set_rebuild_every(dp_md_state *s, int32_t every)
+{
+    if (!s || every < 0) {
+        set_error("dp_md_set_rebuild_every: NULL state or negative interval");
+        return DP_ERR_ARG;
+    }
+    cudaStream_t st = s->m->stream;
+    if (every > 0 && !s->d_steps) DP_CUDA(cudaMalloc((void **)&s->d_steps, sizeof(unsigned long long)));
+    if (s->d_steps) DP_CUDA(cudaMemsetAsync(s->d_steps, 0, sizeof(unsigned long long), st));
+    if (every != s->rebuild_every) graph_drop(s);   // the interval is an argument of the captured step
+    s->rebuild_every = every;
+    DP_CUDA(cudaStreamSynchronize(st));
+    return DP_OK;
 }
 
 dp_status dp_md_state_create(dp_model *m, int64_t n, const double *coord, const double *vel, const int32_t *type,
@@ -619,7 +641,8 @@ dp_status dp_md_step_judged(dp_model *student, dp_model *teacher, dp_md_state *s
             DP_CUDA(cudaMemsetAsync(nl->d_flags + 1, 0, sizeof(int32_t), st));
             k_kick_drift_check<<<nblk(n), 256, 0, st>>>(n, s->d_v, s->d_f, nl->d_type, s->d_minv, 0.5 * dt_fs, s->d_x,
                                                         dt_fs, bx, (Pos4 *)nl->d_pos, (float4 *)nl->d_posf,
-                                                        (const Pos4 *)nl->d_ref, lim * lim, nl->d_flags);
+                                                        (const Pos4 *)nl->d_ref, lim * lim, nl->d_flags,
+                                                        s->d_steps, s->rebuild_every);
         }
         DP_CUDA(cudaGetLastError());
         DP_TRY(nlist_build_device(nl, st, true));

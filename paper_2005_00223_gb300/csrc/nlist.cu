@@ -426,6 +426,7 @@ dp_status nlist_format_device(const dp_model *m, dp_nlist *nl, const double *d_c
         nl->n, (const Pos4 *)nl->d_pos, (const float4 *)nl->d_posf, bx, m->dev, nl->d_cand, nl->d_cand_cnt, nl->cap,
         nl->d_nlist, nl->d_nnei, nl->d_ntrunc, with_env ? nl->d_env : nullptr);
     DP_CUDA(cudaGetLastError());
+    if (centers_of(nl) < nl->n) DP_TRY(clear_ghost_rows(m, nl, st));
     return DP_OK;
 }
 

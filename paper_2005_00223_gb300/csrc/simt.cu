@@ -861,7 +861,7 @@ dp_status compute_simt(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
         if (s != DP_OK) return s;
     }
     ProfScope ps(m->prof, PG_REDUCE, 1, st);
-    return reduce_energy_virial(d_atom_energy, d_atom_virial, n, d_energy, d_virial, m->d_red, st);
+    return reduce_energy_virial(d_atom_energy, d_atom_virial, centers_of(nl), d_energy, d_virial, m->d_red, st);
 }
 
 }  // namespace

@@ -1240,7 +1240,7 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     }
     DP_CUDA(cudaGetLastError());
     ProfScope ps(m->prof, PG_REDUCE, 1, st);
-    return reduce_energy_virial(d_atom_energy, d_atom_virial, n, d_energy, d_virial, m->d_red, st);
+    return reduce_energy_virial(d_atom_energy, d_atom_virial, centers_of(nl), d_energy, d_virial, m->d_red, st);
 }
 
 }  // namespace

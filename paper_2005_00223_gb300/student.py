@@ -43,7 +43,9 @@ def train(student: Model, typ, box, coords, energies, forces, steps: int, lr0: f
           p_e: float = 1.0, p_f: float = 100.0, prec="mix32", seed: int = 0, log_every: int = 50):
     """Adam on the force-matching loss, one frame per step, lr decaying exponentially lr0 -> lr1.
 
-    Returns the list of (step, mean loss over the last log_every steps).
+    p_f: one force weight for every frame, or an array of one weight per frame (e.g. 1 / RMS(F_k)^2 for
+    a relative force loss over frames whose force scales differ).  Returns the list of (step, mean loss
+    over the last log_every steps).
     """
     import torch
     dev = torch.device("cuda")
@@ -55,6 +57,7 @@ def train(student: Model, typ, box, coords, energies, forces, steps: int, lr0: f
     nparams = _lib.dp_model_n_params(student.h)
     grad = torch.zeros(nparams, dtype=torch.float64, device=dev)
     loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    pf = np.broadcast_to(np.asarray(p_f, dtype=np.float64), (len(coords),))
     nl = NeighborList(student, coords[0], typ, box, skin=0.0)
     rng = np.random.default_rng(seed)
     order = rng.permutation(len(coords))
@@ -65,8 +68,8 @@ def train(student: Model, typ, box, coords, energies, forces, steps: int, lr0: f
             order = rng.permutation(len(coords))
         _lib.dp_nlist_update_dev(nl.h, X[k], stream)
         grad.zero_()
-        _lib.dp_force_loss_grad_dev(student.h, nl.h, X[k], box, Fr[k], Er[k:k + 1], p_e, p_f, prec, loss, grad,
-                                    stream)
+        _lib.dp_force_loss_grad_dev(student.h, nl.h, X[k], box, Fr[k], Er[k:k + 1], p_e, float(pf[k]), prec, loss,
+                                    grad, stream)
         lr = lr0 * math.exp(math.log(lr1 / lr0) * s / max(steps - 1, 1))
         _lib.dp_adam_step(student.h, grad, lr, 0.9, 0.999, 1e-8, s + 1, stream)
         if (s + 1) % log_every == 0:

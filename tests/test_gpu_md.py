@@ -55,6 +55,35 @@ def test_nve_matches_oracle(dp, orc, skin, route):
     np.testing.assert_allclose(th, thr, rtol=1e-9)
 
 
+def test_fixed_interval_rebuilds_match_oracle(dp, orc):
+    """The paper's protocol (a list rebuild every N steps, Sec. 5.1) on top of the displacement
+    criterion: copper at 300 K moves far less than skin/2 in 20 fs, so the extra rebuilds are exactly
+    those of the interval, and the trajectory still matches the oracle's."""
+    cfg = dpsynth.copper_config()
+    coord, typ, box = dpsynth.copper_fcc(1, ncell=5)
+    mass = np.array([dpsynth.MASS["Cu"]])
+    vel = dpsynth.velocities(mass[typ], 300.0, 5)
+    p = dpsynth.model_params(cfg, 1)
+    m = dp.Model(cfg, 0, params=p)
+    counts = []
+    for every in (0, 5):
+        st = dp.MDState(m, coord, vel, typ, mass, box, skin=2.0)
+        st.rebuild_every(every)
+        st.step(3, 1.0, "fp64")      # direct step, capture, replays
+        st.step(17, 1.0, "fp64")
+        x, v, step, nreb = st.get()
+        counts.append(nreb)
+        st.close()
+    assert counts[1] - counts[0] == 4   # steps 5, 10, 15, 20
+    xr, vr, _ = orc.Model(cfg, p).md_nve(coord, vel, typ, mass, box, nsteps=20, dt=1.0, thermo_every=20)
+    d = x - xr
+    d -= box[0, 0] * np.rint(d / box[0, 0])
+    assert np.abs(d).max() < 1e-9
+    np.testing.assert_allclose(v, vr, rtol=0, atol=1e-9 * np.abs(vr).max())
+    with pytest.raises(dp.DPError):
+        dp.dp_md_set_rebuild_every(None, 5)
+
+
 def test_nve_energy_conservation_copper(dp):
     """Copper 4,000 atoms, 300 K: total energy drift small against KE fluctuations."""
     cfg = dpsynth.copper_config()
