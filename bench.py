@@ -715,6 +715,70 @@ def run_judged(args, rank, world):
             "gpu_launches": int(sum(v[0] for v in prof.values())), "clocks": clocks, "e2e": None}
 
 
+SWEEP = ((32, 64, 128), (64, 128, 256), (128, 256, 512), (256, 512, 1024), (512, 1024, 2048))
+
+
+def run_sweep(args, rank, world):
+    """Embedding-width sweep (Sec. 6, "Network size"): copper 4,000 atoms, r_c 8 A, sel 512, M2 16,
+    fitting 240-240-240, MIX-16 bf16, nets (w, 2w, 4w) from the paper's 32-64-128 to its largest
+    512-1024-2048 (last-layer matrices 64 x 128 .. 1024 x 2048).  Per net: device ms per NVE step
+    (graph-replayed steps, CUDA events), the algorithmic work per atom and evaluation, and the
+    achieved FLOP/s of the embedding kernels and of the whole step against the measured bf16 peak."""
+    import torch
+
+    import paper_2005_00223_gb300 as dp
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    coord, typ, box = dpsynth.copper_fcc(1, ncell=10)
+    mass = np.array([dpsynth.MASS["Cu"]])
+    vel = dpsynth.velocities(mass[typ], 300.0, 1)
+    n = len(typ)
+    peak, src = tensor_peak()
+    points = []
+    for emb in SWEEP:
+        cfg = dpsynth.ModelConfig(ntypes=1, rcut=8.0, rcut_smth=2.0, sel=(512,), embed=emb)
+        model = dp.Model(cfg, seed=1)
+        stream = torch.cuda.Stream(device=dev)
+        dp.dp_model_set_stream(model.h, stream)
+        nl = dp.NeighborList(model, coord, typ, box)
+        nnei = int((nl.get()[0] >= 0).sum())
+        nl.close()
+        fl = flops_per_group(cfg, nnei, n)
+        steps = max(3, min(args.steps, 10 if emb[0] >= 256 else args.steps))
+        state = dp.MDState(model, coord, vel, typ, mass, box, skin=2.0)
+        state.step(max(3, min(args.warmup, 5)), 1.0, "bf16")
+        dp.dp_profile_select(model.h, None)
+        dp.dp_profile_enable(model.h, True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        state.step(steps, 1.0, "bf16")
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / steps
+        prof = dp.dp_profile_read(model.h)
+        dp.dp_profile_enable(model.h, False)
+        state.close()
+        emb_ms = (prof.get("embed_fwd", (0, 0.0))[1] + prof.get("embed_bwd", (0, 0.0))[1]) / steps
+        emb_fl = fl["embed_fwd"] + fl["embed_bwd"]
+        total = sum(fl.values())
+        points.append({"embed": list(emb), "last_layer": f"{emb[1]} x {emb[2]}",
+                       "path": "fused per-tile kernels (tc.cu)" if emb[0] < 64 else "layer-wise GEMMs (wide.cu)",
+                       "ms_per_step": ms, "s_per_step_atom": ms * 1e-3 / n, "mflop_per_atom_eval": total / n / 1e6,
+                       "step_tflops": total / (ms * 1e-3) / 1e12, "step_frac_of_peak": total / (ms * 1e-3) / 1e12 / peak,
+                       "embedding_ms": emb_ms, "embedding_tflops": emb_fl / (emb_ms * 1e-3) / 1e12 if emb_ms else None,
+                       "embedding_frac_of_peak": emb_fl / (emb_ms * 1e-3) / 1e12 / peak if emb_ms else None,
+                       "embedding_share_of_step": emb_ms / ms, "steps": steps})
+        model.close()
+    return {"metric": "embedding-width sweep: s/step/atom and FLOP/s (MIX-16 bf16)", "unit": "TFLOP/s",
+            "value": points[-1]["step_tflops"], "higher_is_better": True, "n_gpus": world, "dtype": "bf16",
+            "data": "synthetic (seeded FCC copper, seeded random-init weights)",
+            "config": {"workload": "Cu FCC 10^3 cells, 4000 atoms, rcut 8, sel 512, M2 16, fitting 240-240-240, "
+                                   "300 K, dt 1 fs", "atoms": n},
+            "peak": {"tflops": peak, "source": src}, "points": points}
+
+
 def run_e2e(dp, model, cfg, coord, vel, typ, box, mass, dt, args, stream):
     """dp_compute with host buffers every step; velocity Verlet on the host."""
     import torch
@@ -850,7 +914,7 @@ def main():
                     help="judged task: frames per teacher run (0: one run per temperature)")
     ap.add_argument("--teacher-md-precision", default="mix32", help="judged task: precision of the teacher's MD")
     ap.add_argument("--label-precision", default="mix32", help="judged task: precision of the teacher's labels")
-    ap.add_argument("--task", default="md", choices=["md", "grad", "judged"],
+    ap.add_argument("--task", default="md", choices=["md", "grad", "judged", "sweep"],
                     help="md: NVE steps (default); grad: force-loss parameter gradient over 32 water frames; "
                          "judged: distilled student MD judged by the full model")
     args = ap.parse_args()
@@ -871,6 +935,8 @@ def main():
         out = run_grad(args, rank, world)
     elif args.task == "judged":
         out = run_judged(args, rank, world)
+    elif args.task == "sweep":
+        out = run_sweep(args, rank, world)
     else:
         out = run_mine(args, rank, world)
         ref = None

@@ -119,6 +119,14 @@ dp_status compute_device(dp_model *m, dp_nlist *nl, const double *d_coord, dp_pr
         return DP_OK;
     }
     dp_status r = DP_OK;
+    if (embed_is_wide(m->n_embed, m->embed)) {   // the wide nets run in MIX-16 with bf16 operands only
+        if (prec != DP_MIX_BF16) {
+            set_error("embedding nets wider than 32-64-128 run in DP_MIX_BF16 only");
+            return DP_ERR_UNSUPPORTED;
+        }
+        r = compute_wide(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+        prec = DP_PRECISION_DONE;
+    }
     switch (prec) {
     case DP_FP64:
         r = compute_fp64(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
@@ -134,6 +142,8 @@ dp_status compute_device(dp_model *m, dp_nlist *nl, const double *d_coord, dp_pr
         break;
     case DP_MIX_BF16X3:
         r = compute_mix_x3(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+        break;
+    case DP_PRECISION_DONE:
         break;
     default:
         set_error("precision %d is not built into this library", (int)prec);
@@ -444,6 +454,8 @@ void dp_model_destroy(dp_model *m)
     cudaFree(m->d_err);
     cudaFree(m->d_tcw);
     cudaFree(m->d_tcw_x3);
+    cudaFree(m->d_tcfit_x3);
+    cudaFree(m->d_wide);
     cudaFree(m->d_ozw);
     cudaFree(m->d_oze);
     cudaFree(m->d_ozw_emb);

@@ -157,6 +157,8 @@ struct dp_model {
     unsigned char *d_tcw = nullptr;   // packed fp16 and bf16 embedding weights for the tensor cores
     unsigned char *d_tcfit = nullptr; // packed fp16 and bf16 fitting weights for the tensor cores
     unsigned char *d_tcw_x3 = nullptr; // packed split-bf16 (hi, lo) embedding weights (DP_MIX_BF16X3)
+    unsigned char *d_tcfit_x3 = nullptr; // packed split-bf16 fitting weights (DP_MIX_BF16X3)
+    unsigned char *d_wide = nullptr;  // bf16 weights of the wide embedding nets (W2^T, W3^T, W3, W2, vectors)
     void *d_ozw = nullptr;            // fp16 digits of the first fitting layer's weights (FP64 products on the tensor cores)
     int *d_oze = nullptr;             // their row scales
     bool oz_stale = true;             // digits older than the parameters
@@ -283,6 +285,15 @@ dp_status compute_mix16(dp_model *m, dp_nlist *nl, int bf16, double *d_energy, d
 // FP32 fitting net over all atoms (type-sorted positions): D, dD [n][desc], E_i FP64.
 dp_status fit_f32(dp_model *m, dp_nlist *nl, const float *D, float *dD, double *d_atom_energy, cudaStream_t st);
 dp_status pack_x3_weights(dp_model *m);
+// Marks an evaluation already dispatched (compute_device).
+constexpr dp_precision DP_PRECISION_DONE = (dp_precision)1000;
+// Wide embedding nets (w, 2w, 4w), w = 64 .. 512, layer by layer on the tensor cores (wide.cu).
+bool embed_is_wide(int n_embed, const int *e);
+dp_status pack_wide_weights(dp_model *m);
+dp_status compute_wide(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
+                       double *d_virial, double *d_atom_virial, cudaStream_t st);
+// The MIX-16 fitting net (bf16 operands) of tc.cu, for the wide path.
+dp_status fit_mix16_bf16(dp_model *m, dp_nlist *nl, const float *T, double *E_atom, float *dT, cudaStream_t st);
 // Ghost atoms of a spatial decomposition (dp_nlist_set_centers): their list rows are cleared after each
 // format, so they appear only as neighbors.
 dp_status clear_ghost_rows(const dp_model *m, dp_nlist *nl, cudaStream_t st);

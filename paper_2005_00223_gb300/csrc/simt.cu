@@ -871,7 +871,7 @@ bool embed_shape_supported(int n_embed, const int *e)
 {
     if (n_embed != 3) return false;
     return (e[0] == 25 && e[1] == 50 && e[2] == 100) || (e[0] == 8 && e[1] == 16 && e[2] == 32) ||
-           (e[0] == 32 && e[1] == 64 && e[2] == 128);
+           (e[0] == 32 && e[1] == 64 && e[2] == 128) || embed_is_wide(n_embed, e);
 }
 
 size_t fp64_bytes_per_atom(const ModelDev &md)

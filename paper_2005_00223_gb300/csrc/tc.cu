@@ -219,12 +219,25 @@ __global__ void __launch_bounds__(kTcThreads, S::B_CTAS >= 3 ? S::B_CTAS : 1) k_
                                                             const int *__restrict__ ntiles_ptr,
                                                             const unsigned char *__restrict__ wimg,
                                                             const float *__restrict__ dT, double *__restrict__ force,
-                                                            double *__restrict__ atom_virial, int *err)
+                                                            double *__restrict__ atom_virial, int *err,
+                                                            const unsigned *__restrict__ dT_max)
 {
     extern __shared__ __align__(128) unsigned char smem[];   // no-swizzle operands and bulk copies: 16 B
     __shared__ __align__(8) uint64_t mbar_mma, mbar_w;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // fp16 operands: dE/dT (which carries 1/sum(sel)^2) is scaled by a power of two 2^-e so that its
+    // largest entry lies in [1, 2), keeping dz3 and dz2 in fp16's normal range; g is scaled back
+    // exactly before the force and virial sums (bf16 has FP32's range and needs no scaling)
+    float gscale = 1.f, ginv = 1.f;
+    if (BF == 0 && dT_max != nullptr) {
+        const unsigned bits = *dT_max;
+        const int e = (int)((bits >> 23) & 0xffu) - 127;
+        if (bits != 0u && e > -126 && e < 127) {
+            gscale = __int_as_float((127 - e) << 23);
+            ginv = __int_as_float((127 + e) << 23);
+        }
+    }
     unsigned char *img = smem;
     unsigned char *A2 = smem + S::B_A2_OFF;
     unsigned char *A3 = smem + S::B_A3_OFF;     // forward layer-3 input, then dz2
@@ -273,7 +286,8 @@ __global__ void __launch_bounds__(kTcThreads, S::B_CTAS >= 3 ? S::B_CTAS : 1) k_
             cur_net = net;
         }
         // dE/dT of this warp's atom (already scaled by 1/sum(sel))
-        for (int q = lane; q < 4 * S::E2; q += 32) sdT[q] = ch.atom >= 0 ? dT[(int64_t)ch.atom * 4 * S::E2 + q] : 0.f;
+        for (int q = lane; q < 4 * S::E2; q += 32)
+            sdT[q] = ch.atom >= 0 ? dT[(int64_t)ch.atom * 4 * S::E2 + q] * gscale : 0.f;
         float Rf[4], t1[S::E0], t2[S::E1], geo[6];
         int j;
         bool valid;
@@ -471,7 +485,7 @@ __global__ void __launch_bounds__(kTcThreads, S::B_CTAS >= 3 ? S::B_CTAS : 1) k_
             const float ud = geo[0] * dR[1] + geo[1] * dR[2] + geo[2] * dR[3];
             const float cu = fmaf(geo[3] - geo[5], ud, dR0 * geo[3]);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) gv[k] = fmaf(cu, geo[k], geo[5] * dR[1 + k]);
+            for (int k = 0; k < 3; ++k) gv[k] = fmaf(cu, geo[k], geo[5] * dR[1 + k]) * ginv;
 #pragma unroll
             for (int k = 0; k < 3; ++k) atomicAdd(&force[3 * (int64_t)j + k], -(double)gv[k]);
 #pragma unroll
@@ -505,6 +519,22 @@ __global__ void __launch_bounds__(kTcThreads, S::B_CTAS >= 3 ? S::B_CTAS : 1) k_
     __syncthreads();
     tc::fence_after_sync();
     if (warp == 0) tc::tmem_dealloc(tmem, kCols);
+}
+
+// *out = bit pattern of max |x| over x [n] (non-negative floats order like their bits); *out zeroed
+// by the caller.
+__global__ void k_absmax_bits(int64_t n, const float *__restrict__ x, unsigned *out)
+{
+    unsigned m = 0u;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned b = __float_as_uint(fabsf(x[i]));
+        m = b > m ? b : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned v = __shfl_xor_sync(0xffffffffu, m, o);
+        m = v > m ? v : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
 // Work list: for each (center type, neighbor type) group, the 32-neighbor
@@ -1096,6 +1126,11 @@ dp_status pack_fit_all(dp_model *m)
 using FitWater = FitShape<100, 16, 240>;
 using FitStudent = FitShape<32, 8, 64>;
 using FitPaper = FitShape<128, 16, 240>;
+// descriptors of the wide embedding nets (M1 = 4w, wide.cu)
+using FitW256 = FitShape<256, 16, 240>;
+using FitW512 = FitShape<512, 16, 240>;
+using FitW1024 = FitShape<1024, 16, 240>;
+using FitW2048 = FitShape<2048, 16, 240>;
 
 // The fused tensor-core fitting kernel covers three equal hidden widths F
 // after a plain first layer (the configs' 240-240-240 and 64-64-64).
@@ -1106,6 +1141,12 @@ int fit_tc_kind(const ModelDev &md)
     if (md.m1 == 100 && md.m2 == 16 && F == 240) return 1;
     if (md.m1 == 32 && md.m2 == 8 && F == 64) return 2;
     if (md.m1 == 128 && md.m2 == 16 && F == 240) return 3;
+    if (md.m2 == 16 && F == 240) {
+        if (md.m1 == 256) return 4;
+        if (md.m1 == 512) return 5;
+        if (md.m1 == 1024) return 6;
+        if (md.m1 == 2048) return 7;
+    }
     return 0;
 }
 
@@ -1136,8 +1177,19 @@ dp_status fit_tc(dp_model *m, dp_nlist *nl, const float *T, int grid, double *E_
     case 1: return launch_fit_tc<FitWater, BF>(m, nl, T, grid, E_atom, dT, st);
     case 2: return launch_fit_tc<FitStudent, BF>(m, nl, T, grid, E_atom, dT, st);
     case 3: return launch_fit_tc<FitPaper, BF>(m, nl, T, grid, E_atom, dT, st);
-    default: set_error("no tensor-core fitting kernel for this shape"); return DP_ERR_UNSUPPORTED;
+    default: break;
     }
+    if constexpr (BF == 1) {   // the wide nets' descriptors (bf16 only)
+        switch (fit_tc_kind(m->dev)) {
+        case 4: return launch_fit_tc<FitW256, 1>(m, nl, T, grid, E_atom, dT, st);
+        case 5: return launch_fit_tc<FitW512, 1>(m, nl, T, grid, E_atom, dT, st);
+        case 6: return launch_fit_tc<FitW1024, 1>(m, nl, T, grid, E_atom, dT, st);
+        case 7: return launch_fit_tc<FitW2048, 1>(m, nl, T, grid, E_atom, dT, st);
+        default: break;
+        }
+    }
+    set_error("no tensor-core fitting kernel for this shape");
+    return DP_ERR_UNSUPPORTED;
 }
 
 template <class S, int BF>
@@ -1157,6 +1209,7 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     sz(sizeof(float) * md.desc_dim * n);
     sz(sizeof(int4) * max_chunks);
     sz(sizeof(int) * 4);
+    sz(sizeof(unsigned) * 4);   // max |dE/dT| (fp16 gradient scaling)
     const int nb = (int)((n + kCbThreads - 1) / kCbThreads);
     sz(sizeof(int) * (size_t)md.ntypes * n);             // chunk-count scans
     sz(sizeof(int) * (size_t)2 * md.ntypes * nb);        // block sums and offsets
@@ -1179,6 +1232,7 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     float *dD = (float *)carve(sizeof(float) * md.desc_dim * n);
     int4 *chunks = (int4 *)carve(sizeof(int4) * max_chunks);
     int *cnt = (int *)carve(sizeof(int) * 4);
+    unsigned *dT_max = (unsigned *)carve(sizeof(unsigned) * 4);
     int *cb_loc = (int *)carve(sizeof(int) * (size_t)md.ntypes * n);
     int *cb_bsum = (int *)carve(sizeof(int) * (size_t)2 * md.ntypes * nb);
     int *cb_boff = cb_bsum + (size_t)md.ntypes * nb;
@@ -1233,10 +1287,17 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
         }
         DP_CUDA(cudaGetLastError());
     }
+    if (BF == 0) {   // the scale of dE/dT for the fp16 backward operands
+        ProfScope ps(m->prof, PG_DESC, 1, st);
+        DP_CUDA(cudaMemsetAsync(dT_max, 0, sizeof(unsigned), st));
+        k_absmax_bits<<<(unsigned)(2 * nsm), 256, 0, st>>>(nq, dT, dT_max);
+        DP_CUDA(cudaGetLastError());
+    }
     {
         ProfScope ps(m->prof, PG_EMBED_BWD, 1, st);
         k_embed_bwd_tc<S, BF><<<(unsigned)(S::B_CTAS * nsm), kTcThreads, S::B_SMEM, st>>>(md, envA, envB, nl->d_nlist, nl->d_nnei, chunks,
-                                                                     cnt, wimg, dT, d_force, d_atom_virial, m->d_err);
+                                                                     cnt, wimg, dT, d_force, d_atom_virial, m->d_err,
+                                                                     BF == 0 ? dT_max : nullptr);
     }
     DP_CUDA(cudaGetLastError());
     ProfScope ps(m->prof, PG_REDUCE, 1, st);
@@ -1293,16 +1354,31 @@ dp_status build_chunks_batch(dp_model *m, dp_nlist *nl, int64_t p0, int64_t nb, 
 dp_status pack_tc_weights(dp_model *m)
 {
     const int *e = m->dev.emb.wout;
-    if (m->d_tcw_x3) DP_TRY(pack_x3_weights(m));
-    if (e[0] == 25) DP_TRY(pack_all<TcWater>(m));
-    else if (e[0] == 8) DP_TRY(pack_all<TcStudent>(m));
-    else DP_TRY(pack_all<TcPaper>(m));
+    if (embed_is_wide(m->n_embed, m->embed)) {
+        if (m->d_wide) DP_TRY(pack_wide_weights(m));
+    } else {
+        if (m->d_tcw_x3) DP_TRY(pack_x3_weights(m));
+        if (e[0] == 25) DP_TRY(pack_all<TcWater>(m));
+        else if (e[0] == 8) DP_TRY(pack_all<TcStudent>(m));
+        else DP_TRY(pack_all<TcPaper>(m));
+    }
     switch (fit_tc_kind(m->dev)) {
     case 1: return pack_fit_all<FitWater>(m);
     case 2: return pack_fit_all<FitStudent>(m);
     case 3: return pack_fit_all<FitPaper>(m);
+    case 4: return pack_fit_all<FitW256>(m);
+    case 5: return pack_fit_all<FitW512>(m);
+    case 6: return pack_fit_all<FitW1024>(m);
+    case 7: return pack_fit_all<FitW2048>(m);
     default: return DP_OK;
     }
+}
+
+dp_status fit_mix16_bf16(dp_model *m, dp_nlist *nl, const float *T, double *E_atom, float *dT, cudaStream_t st)
+{
+    int nsm = 0;
+    DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
+    return fit_tc<1>(m, nl, T, nsm, E_atom, dT, st);
 }
 
 dp_status compute_mix16(dp_model *m, dp_nlist *nl, int bf16, double *d_energy, double *d_atom_energy,

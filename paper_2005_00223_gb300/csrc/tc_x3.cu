@@ -28,6 +28,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <vector>
@@ -591,6 +592,487 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_bwd_x3(ModelDev md, const 
     if (warp == 0) tc::tmem_dealloc(tmem, X::B_TCOLS);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Fitting net in split bf16 on the tensor cores, fused with the descriptor and its adjoint (the
+// structure of the MIX-16 fitting kernel in tc.cu: one CTA per SM walks tiles of 128 atoms of one
+// center type, thread = atom row, accumulators in tensor memory).  The hi and lo weight tiles do not
+// fit in shared memory whole, so every product streams its B operand in chunks (hi and lo of a chunk
+// in one bulk copy) through a two-stage ring, the copy of chunk c + 1 overlapping the MMAs of chunk c;
+// the A operand (D in K chunks for layer 1, else the 128 x F activations) is written hi and lo.
+// tanh is tanhf; the derivative factors (1 - t1^2, 1 - t2^2) wait in tensor memory as 16-bit fixed
+// point pairs (absolute error 2^-17 of a value in [0, 1]).
+
+template <int M1_, int M2_, int F_>
+struct FitX3 {
+    static constexpr int M1 = M1_, M2 = M2_, F = F_, D = M1_ * M2_;
+    static constexpr int KC1 = 32, NK1 = D / KC1;                   // layer-1 K chunks
+    static constexpr int KC2 = (F % 48 == 0) ? 48 : 32, NK2 = F / KC2;   // K chunks of the F x F products
+    static constexpr int NC = 32, NB1 = D / NC;                     // N chunks of dE/dD = dz1 W1^T
+    static constexpr uint32_t C1 = F * KC1 * 4, C2 = F * KC2 * 4, CB1 = NC * F * 4;   // chunk bytes, hi + lo
+    // global image per center type: chunks of W1^T [F][KC1], W2^T, W3^T [F][KC2] (K = input),
+    // W3, W2 [F][KC2] (K = output), W1 [NC][F]; then b1, b2, b3, w_out [F], b_out (FP32)
+    static constexpr uint32_t W1T = 0, W2T = W1T + NK1 * C1, W3T = W2T + NK2 * C2, W3B = W3T + NK2 * C2,
+                              W2B = W3B + NK2 * C2, W1B = W2B + NK2 * C2, VEC = W1B + NB1 * CB1,
+                              VEC_BYTES = (4 * F + 4) * 4, IMG = VEC + VEC_BYTES;
+    static constexpr uint32_t cmax(uint32_t a, uint32_t b) { return a > b ? a : b; }
+    static constexpr uint32_t STAGE = cmax(cmax(C1, C2), CB1);
+    static constexpr uint32_t ACT = 2 * 128 * F * 2;                // activations hi | lo
+    static constexpr uint32_t DCH = 2 * 128 * KC1 * 2;              // one D chunk hi | lo
+    static constexpr uint32_t A_BYTES = cmax(ACT, 2 * DCH);
+    static constexpr uint32_t A_OFF = 0, B_OFF = A_BYTES, V_OFF = B_OFF + 2 * STAGE, SMEM = V_OFF + VEC_BYTES;
+    static_assert(D % KC1 == 0 && F % KC2 == 0 && D % NC == 0 && NC % M2_ == 0 && KC1 % M2_ == 0 &&
+                      16 % M2_ == 0 && F_ % 16 == 0 && F_ <= 256 && IMG % 16 == 0 && STAGE % 16 == 0,
+                  "fitting tile shape");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+using FitX3Water = FitX3<100, 16, 240>;
+using FitX3Student = FitX3<32, 8, 64>;
+using FitX3Paper = FitX3<128, 16, 240>;
+
+// D (+)= A B^T over K (multiple of 16) with explicit strides between 8-row groups of A and B (K-major).
+__device__ __forceinline__ void mma_k_sbo(uint32_t d, uint32_t a, uint32_t a_sbo, uint32_t b, uint32_t b_sbo, int K,
+                                          uint32_t id, bool acc0)
+{
+    for (int ks = 0; ks < (K >> 4); ++ks) {
+        const uint64_t ad = tc::smem_desc(a + ks * 256, 128, a_sbo);
+        const uint64_t bd = tc::smem_desc(b + ks * 256, 128, b_sbo);
+        const uint32_t acc = (acc0 || ks > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+            "l"(ad), "l"(bd), "r"(id), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ uint32_t unorm16_pair(float a, float b)
+{
+    const uint32_t qa = __float2uint_rn(fminf(fmaxf(a, 0.f), 1.f) * 65535.f);
+    const uint32_t qb = __float2uint_rn(fminf(fmaxf(b, 0.f), 1.f) * 65535.f);
+    return qa | (qb << 16);
+}
+
+template <class S>
+__global__ void __launch_bounds__(128, 1) k_fit_x3(ModelDev md, const int32_t *__restrict__ order, int64_t pos_begin,
+                                                  int64_t count, const float *__restrict__ T,
+                                                  const unsigned char *__restrict__ img, double *__restrict__ E_atom,
+                                                  float *__restrict__ dT, int *err)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_t[2], bar_m[2];
+    __shared__ uint32_t tmem_base;
+    constexpr int F = S::F, KC1 = S::KC1, KC2 = S::KC2, M2 = S::M2, M1 = S::M1;
+    constexpr int AK = KC1 / M2;   // rows a of T per layer-1 chunk
+    const int tid = threadIdx.x, warp = tid >> 5;
+    unsigned char *Ah = smem + S::A_OFF, *Al = Ah + 128 * F * 2;
+    unsigned char *Bst = smem + S::B_OFF;
+    float *vec = reinterpret_cast<float *>(smem + S::V_OFF);
+    const float *b1 = vec, *b2 = vec + F, *b3 = vec + 2 * F, *wo = vec + 3 * F;
+    if (tid == 0) {
+        for (int q = 0; q < 2; ++q) {
+            tc::mbar_init(&bar_t[q], 1);
+            tc::mbar_init(&bar_m[q], 1);
+        }
+        tc::mbar_init_fence();
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
+    {
+        const float *gv = reinterpret_cast<const float *>(img + S::VEC);
+        for (int q = tid; q < 4 * F + 4; q += 128) vec[q] = gv[q];
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tm = tmem_base;
+    const uint32_t trow = tm + ((uint32_t)(warp * 32) << 16);
+    const uint32_t tsc = trow + 256;   // t1 (FP32), then the derivative factors (1 - t1^2, 1 - t2^2)
+    const float bout = vec[4 * F];
+    const float inv2 = (float)(md.inv_nsel * md.inv_nsel);
+    const uint32_t idF = tc::idesc_f16(128, F, 1), idN = tc::idesc_f16(128, S::NC, 1);
+    uint32_t ph_t[2] = {0, 0}, ph_m[2] = {0, 0};
+    bool loaded[2] = {false, false}, pend[2] = {false, false};
+    bool dead = false;
+    const int64_t ntiles = (count + 127) / 128;
+    auto waitv = [&](uint64_t *bar, uint32_t &ph) {
+        const bool ok = tc::mbar_wait(bar, ph, kWaitLimit);
+        ph ^= 1;
+        return __syncthreads_and(ok) != 0;
+    };
+    auto issue = [&](int s, uint32_t off, uint32_t bytes) {
+        if (tid == 0) {
+            tc::mbar_expect_tx(&bar_t[s], bytes);
+            tc::bulk_g2s(Bst + s * S::STAGE, img + off, bytes, &bar_t[s]);
+        }
+        loaded[s] = true;
+    };
+    auto free_stage = [&](int s) {   // the MMAs that read stage s are done
+        if (pend[s]) {
+            pend[s] = false;
+            if (!waitv(&bar_m[s], ph_m[s])) return false;
+        }
+        return true;
+    };
+    auto arrived = [&](int s) {   // the chunk copied into stage s is in shared memory
+        loaded[s] = false;
+        return waitv(&bar_t[s], ph_t[s]);
+    };
+    auto mma3_chunk = [&](uint32_t d, const unsigned char *ah, const unsigned char *al, uint32_t a_sbo, int s,
+                          uint32_t half, uint32_t b_sbo, int K, uint32_t id, bool acc0) {
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t bh = tc::smem_u32(Bst + s * S::STAGE), bl = bh + half;
+            mma_k_sbo(d, tc::smem_u32(ah), a_sbo, bh, b_sbo, K, id, acc0);
+            mma_k_sbo(d, tc::smem_u32(ah), a_sbo, bl, b_sbo, K, id, true);
+            mma_k_sbo(d, tc::smem_u32(al), a_sbo, bh, b_sbo, K, id, true);
+            tc::mma_commit(&bar_m[s]);
+        }
+        pend[s] = true;
+    };
+    // d (+)= (the resident activations, K = F) x the B chunks at img + off + c * C2 (K chunks of KC2),
+    // after every thread's A writes
+    auto gemm_res = [&](uint32_t d, uint32_t off, bool acc0) -> bool {
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        issue(0, off, S::C2);
+        for (int c = 0; c < S::NK2; ++c) {
+            const int s = c & 1;
+            if (c + 1 < S::NK2) {
+                if (!free_stage(1 - s)) return false;
+                issue(1 - s, off + (uint32_t)(c + 1) * S::C2, S::C2);
+            }
+            if (!arrived(s)) return false;
+            mma3_chunk(d, Ah + c * (KC2 / 8) * 128, Al + c * (KC2 / 8) * 128, (F / 8) * 128, s, F * KC2 * 2,
+                       (KC2 / 8) * 128, KC2, idF, acc0 || c > 0);
+        }
+        for (int s = 0; s < 2; ++s)
+            if (!free_stage(s)) return false;
+        tc::fence_after_sync();
+        return true;
+    };
+    for (int64_t tile = blockIdx.x; tile < ntiles && !dead; tile += gridDim.x) {
+        const int64_t r0 = tile * 128 + tid;
+        const bool valid = r0 < count;
+        const int atom = valid ? order[pos_begin + r0] : 0;
+        const float4 *Ta = reinterpret_cast<const float4 *>(T + (int64_t)atom * 4 * M1);
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 tb[M2];
+#pragma unroll
+        for (int b = 0; b < M2; ++b) tb[b] = valid ? Ta[b] : zero4;
+        // ---- layer 1: z1 = D W1 in K chunks of KC1; D built chunk by chunk (hi, lo) while the tensor
+        // core runs the previous chunk
+        issue(0, S::W1T, S::C1);
+        for (int c = 0; c < S::NK1 && !dead; ++c) {
+            const int s = c & 1;
+            unsigned char *sh = smem + S::A_OFF + s * S::DCH, *sl = sh + 128 * KC1 * 2;
+            float4 cur[AK];
+#pragma unroll
+            for (int q = 0; q < AK; ++q) cur[q] = valid ? Ta[c * AK + q] : zero4;
+#pragma unroll
+            for (int c8 = 0; c8 < KC1; c8 += 8) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float4 ta = cur[(c8 + u) / M2];
+                    const float4 t2 = tb[(c8 + u) % M2];
+                    v[u] = (ta.x * t2.x + ta.y * t2.y + ta.z * t2.z + ta.w * t2.w) * inv2;
+                }
+                st8_k(sh, sl, tid, c8, KC1, v);
+            }
+            tc::fence_async_smem();
+            if (c + 1 < S::NK1) {
+                if (!free_stage(1 - s)) { dead = true; break; }
+                issue(1 - s, S::W1T + (uint32_t)(c + 1) * S::C1, S::C1);
+            }
+            tc::fence_before_sync();
+            __syncthreads();
+            if (!arrived(s)) { dead = true; break; }
+            mma3_chunk(tm, sh, sl, (KC1 / 8) * 128, s, F * KC1 * 2, (KC1 / 8) * 128, KC1, idF, c > 0);
+        }
+        for (int s = 0; s < 2 && !dead; ++s)
+            if (!free_stage(s)) dead = true;
+        if (dead) break;
+        tc::fence_after_sync();
+        // layer-1 epilogue: t1 = tanh(z1 + b1) (plain layer), kept in tensor memory for layer 2
+#pragma unroll 1
+        for (int c0 = 0; c0 < F; c0 += 16) {
+            float z[16], v[16];
+            uint32_t w[16];
+            tc::tmem_ld16(trow + c0, z);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                v[u] = tanhf(z[u] + b1[c0 + u]);
+                w[u] = __float_as_uint(v[u]);
+            }
+            tc::tmem_st16(tsc + c0, w);
+            st8_k(Ah, Al, tid, c0, F, v);
+            st8_k(Ah, Al, tid, c0 + 8, F, v + 8);
+        }
+        tc::tmem_st_wait();
+        if (!gemm_res(tm, S::W2T, false)) { dead = true; break; }
+        // layer-2 epilogue: y2 = t1 + t2; E gets y2 . w now (y3 = y2 + t3); the derivative factors of
+        // layers 1 and 2 replace t1
+        float e = 0.f;
+#pragma unroll 1
+        for (int c0 = 0; c0 < F; c0 += 16) {
+            float z[16], t1[16], v[16];
+            uint32_t w[16];
+            tc::tmem_ld16(trow + c0, z);
+            tc::tmem_ld16(tsc + c0, t1);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int k = c0 + u;
+                const float t = tanhf(z[u] + b2[k]);
+                v[u] = t1[u] + t;
+                e = fmaf(v[u], wo[k], e);
+                w[u] = unorm16_pair(1.f - t1[u] * t1[u], 1.f - t * t);
+            }
+            tc::tmem_st16(tsc + c0, w);
+            st8_k(Ah, Al, tid, c0, F, v);
+            st8_k(Ah, Al, tid, c0 + 8, F, v + 8);
+        }
+        tc::tmem_st_wait();
+        if (!gemm_res(tm, S::W3T, false)) { dead = true; break; }
+        // layer-3 epilogue: E_i = (y2 + t3) . w + b (FP32), dz3 = w (1 - t3^2)
+#pragma unroll 1
+        for (int c0 = 0; c0 < F; c0 += 16) {
+            float z[16], v[16];
+            tc::tmem_ld16(trow + c0, z);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int k = c0 + u;
+                const float t = tanhf(z[u] + b3[k]);
+                e = fmaf(t, wo[k], e);
+                v[u] = wo[k] * (1.f - t * t);
+            }
+            st8_k(Ah, Al, tid, c0, F, v);
+            st8_k(Ah, Al, tid, c0 + 8, F, v + 8);
+        }
+        if (valid) E_atom[atom] = (double)(e + bout);
+        if (!gemm_res(tm, S::W3B, false)) { dead = true; break; }
+        // dE/dy2 epilogue: dy2 = dz3 W3^T + w (skip of layer 3), dz2 = dy2 (1 - t2^2); dy2 goes back
+        // into the accumulator, so that the next product adds dz2 W2^T to it (the skip of layer 2)
+#pragma unroll 1
+        for (int c0 = 0; c0 < F; c0 += 16) {
+            float z[16], v[16];
+            uint32_t w[16], pk[16];
+            tc::tmem_ld16(trow + c0, z);
+            tc::tmem_ld16(tsc + c0, reinterpret_cast<float *>(pk));
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const float dy2 = z[u] + wo[c0 + u];
+                v[u] = dy2 * ((float)(pk[u] >> 16) * (1.f / 65535.f));
+                w[u] = __float_as_uint(dy2);
+            }
+            tc::tmem_st16(trow + c0, w);
+            st8_k(Ah, Al, tid, c0, F, v);
+            st8_k(Ah, Al, tid, c0 + 8, F, v + 8);
+        }
+        tc::tmem_st_wait();
+        if (!gemm_res(tm, S::W2B, true)) { dead = true; break; }
+        // dE/dy1 epilogue: dy1 = dy2 + dz2 W2^T (from the accumulator), dz1 = dy1 (1 - t1^2)
+#pragma unroll 1
+        for (int c0 = 0; c0 < F; c0 += 16) {
+            float z[16], v[16];
+            uint32_t pk[16];
+            tc::tmem_ld16(trow + c0, z);
+            tc::tmem_ld16(tsc + c0, reinterpret_cast<float *>(pk));
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int u = 0; u < 16; ++u) v[u] = z[u] * ((float)(pk[u] & 0xffffu) * (1.f / 65535.f));
+            st8_k(Ah, Al, tid, c0, F, v);
+            st8_k(Ah, Al, tid, c0 + 8, F, v + 8);
+        }
+        // dE/dD = dz1 W1^T in N chunks of NC, folded into dE/dT as soon as each chunk is read
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        float4 dtb[M2];
+#pragma unroll
+        for (int b = 0; b < M2; ++b) dtb[b] = zero4;
+        float4 *dTa = reinterpret_cast<float4 *>(dT + (int64_t)atom * 4 * M1);
+        issue(0, S::W1B, S::CB1);
+        for (int j = 0; j < S::NB1 && !dead; ++j) {
+            const int s = j & 1;
+            if (j + 1 < S::NB1) {
+                if (!free_stage(1 - s)) { dead = true; break; }
+                issue(1 - s, S::W1B + (uint32_t)(j + 1) * S::CB1, S::CB1);
+            }
+            if (!arrived(s)) { dead = true; break; }
+            const uint32_t reg = (uint32_t)s * 256;
+            mma3_chunk(tm + reg, Ah, Al, (F / 8) * 128, s, S::NC * F * 2, (F / 8) * 128, F, idN, false);
+            if (!free_stage(s)) { dead = true; break; }
+            tc::fence_after_sync();
+            constexpr int HS = M2 < 16 ? M2 : 16;
+            const int a0 = (j * S::NC) / M2;
+#pragma unroll
+            for (int c0 = 0; c0 < S::NC; c0 += 16) {
+                float z[16];
+                tc::tmem_ld16(trow + reg + c0, z);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int h = 0; h < 16; h += HS) {
+                    const int a = a0 + (c0 + h) / M2;
+                    const float4 ta = valid ? Ta[a] : zero4;
+                    float4 acc = zero4;
+#pragma unroll
+                    for (int u = 0; u < HS; ++u) {
+                        const int b = (c0 + h + u) % M2;
+                        const float dd = z[h + u];
+                        acc.x = fmaf(dd, tb[b].x, acc.x);
+                        acc.y = fmaf(dd, tb[b].y, acc.y);
+                        acc.z = fmaf(dd, tb[b].z, acc.z);
+                        acc.w = fmaf(dd, tb[b].w, acc.w);
+                        dtb[b].x = fmaf(dd, ta.x, dtb[b].x);
+                        dtb[b].y = fmaf(dd, ta.y, dtb[b].y);
+                        dtb[b].z = fmaf(dd, ta.z, dtb[b].z);
+                        dtb[b].w = fmaf(dd, ta.w, dtb[b].w);
+                    }
+                    if (valid) dTa[a] = make_float4(acc.x * inv2, acc.y * inv2, acc.z * inv2, acc.w * inv2);
+                }
+            }
+        }
+        if (dead) break;
+        if (valid) {
+#pragma unroll
+            for (int b = 0; b < M2; ++b) {
+                float4 o = dTa[b];
+                o.x += dtb[b].x * inv2;
+                o.y += dtb[b].y * inv2;
+                o.z += dtb[b].z * inv2;
+                o.w += dtb[b].w * inv2;
+                dTa[b] = o;
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    if (dead) {
+        // a wait gave up: flag it, then wait (bounded again) for this CTA's own copies and products
+        // still in flight before the tensor memory is freed
+        if (tid == 0) {
+            atomicOr(err, 1);
+            for (int s = 0; s < 2; ++s) {
+                if (loaded[s]) tc::mbar_wait(&bar_t[s], ph_t[s], kWaitLimit);
+                if (pend[s]) tc::mbar_wait(&bar_m[s], ph_m[s], kWaitLimit);
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tm, 512);
+}
+
+// hi and lo of w at element (r, k) of a K-major tile with K columns, in a chunk whose lo half starts
+// `half` bytes after its hi half.
+inline void put_x3(unsigned char *chunk, uint32_t half, int r, int k, int K, double w)
+{
+    const __nv_bfloat16 h = __double2bfloat16(w);
+    const __nv_bfloat16 l = __double2bfloat16(w - (double)__bfloat162float(h));
+    memcpy(chunk + tc::kmaj_off(r, k, K), &h, 2);
+    memcpy(chunk + half + tc::kmaj_off(r, k, K), &l, 2);
+}
+
+template <class FS>
+void pack_fit_x3(const double *p, const NetLayout &L, unsigned char *out)
+{
+    memset(out, 0, FS::IMG);
+    constexpr int F = FS::F, KC1 = FS::KC1, KC2 = FS::KC2, NC = FS::NC;
+    const double *W1 = p + L.W[0], *W2 = p + L.W[1], *W3 = p + L.W[2];
+    for (int d = 0; d < FS::D; ++d)
+        for (int o = 0; o < F; ++o) {
+            const double w = W1[(int64_t)d * F + o];
+            put_x3(out + FS::W1T + (uint32_t)(d / KC1) * FS::C1, F * KC1 * 2, o, d % KC1, KC1, w);   // [o][d]
+            put_x3(out + FS::W1B + (uint32_t)(d / NC) * FS::CB1, NC * F * 2, d % NC, o, F, w);       // [d][o]
+        }
+    for (int k = 0; k < F; ++k)
+        for (int o = 0; o < F; ++o) {
+            const double w2 = W2[k * F + o], w3 = W3[k * F + o];
+            put_x3(out + FS::W2T + (uint32_t)(k / KC2) * FS::C2, F * KC2 * 2, o, k % KC2, KC2, w2);   // [o][k]
+            put_x3(out + FS::W3T + (uint32_t)(k / KC2) * FS::C2, F * KC2 * 2, o, k % KC2, KC2, w3);
+            put_x3(out + FS::W2B + (uint32_t)(o / KC2) * FS::C2, F * KC2 * 2, k, o % KC2, KC2, w2);   // [k][o]
+            put_x3(out + FS::W3B + (uint32_t)(o / KC2) * FS::C2, F * KC2 * 2, k, o % KC2, KC2, w3);
+        }
+    float *vec = reinterpret_cast<float *>(out + FS::VEC);
+    for (int k = 0; k < F; ++k) {
+        vec[k] = (float)p[L.b[0] + k];
+        vec[F + k] = (float)p[L.b[1] + k];
+        vec[2 * F + k] = (float)p[L.b[2] + k];
+        vec[3 * F + k] = (float)p[L.W[3] + k];
+    }
+    vec[4 * F] = (float)p[L.b[3]];
+}
+
+// 1, 2, 3: the fitting shapes with a split-bf16 tensor-core kernel (three equal hidden widths after a
+// plain first layer); 0: none (the FP32 CUDA-core fitting net is used).
+int fit_x3_kind(const ModelDev &md)
+{
+    if (md.n_fit != 3 || md.fit.wout[0] != md.fit.wout[1] || md.fit.wout[1] != md.fit.wout[2]) return 0;
+    const int F = md.fit.wout[0];
+    if (md.m1 == 100 && md.m2 == 16 && F == 240) return 1;
+    if (md.m1 == 32 && md.m2 == 8 && F == 64) return 2;
+    if (md.m1 == 128 && md.m2 == 16 && F == 240) return 3;
+    return 0;
+}
+
+template <class FS>
+dp_status pack_fit_x3_all(dp_model *m)
+{
+    const ModelDev &md = m->dev;
+    std::vector<unsigned char> img((size_t)md.ntypes * FS::IMG);
+    for (int t = 0; t < md.ntypes; ++t)
+        pack_fit_x3<FS>(m->h_params.data() + md.fit_base + t * md.fit.size, md.fit, img.data() + (size_t)t * FS::IMG);
+    if (!m->d_tcfit_x3) DP_CUDA(cudaMalloc((void **)&m->d_tcfit_x3, img.size()));
+    DP_CUDA(cudaMemcpyAsync(m->d_tcfit_x3, img.data(), img.size(), cudaMemcpyHostToDevice, m->stream));
+    DP_CUDA(cudaStreamSynchronize(m->stream));
+    return DP_OK;
+}
+
+dp_status pack_fit_x3_weights(dp_model *m)
+{
+    switch (fit_x3_kind(m->dev)) {
+    case 1: return pack_fit_x3_all<FitX3Water>(m);
+    case 2: return pack_fit_x3_all<FitX3Student>(m);
+    case 3: return pack_fit_x3_all<FitX3Paper>(m);
+    default: return DP_OK;
+    }
+}
+
+template <class FS>
+dp_status launch_fit_x3(dp_model *m, dp_nlist *nl, const float *T, int grid, double *E_atom, float *dT,
+                        cudaStream_t st)
+{
+    const ModelDev &md = m->dev;
+    DP_CUDA(cudaFuncSetAttribute(k_fit_x3<FS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FS::SMEM));
+    for (int t = 0; t < md.ntypes; ++t) {
+        const int64_t b = nl->type_off[t], cnt = nl->type_count[t];
+        if (cnt <= 0) continue;
+        const int64_t tiles = (cnt + 127) / 128;
+        const unsigned g = (unsigned)(tiles < grid ? tiles : grid);
+        ProfScope ps(m->prof, PG_FIT, 1, st);
+        k_fit_x3<FS><<<g, 128, FS::SMEM, st>>>(md, nl->d_order, b, cnt, T, m->d_tcfit_x3 + (size_t)t * FS::IMG,
+                                               E_atom, dT, m->d_err);
+        DP_CUDA(cudaGetLastError());
+    }
+    return DP_OK;
+}
+
+dp_status fit_x3(dp_model *m, dp_nlist *nl, const float *T, int grid, double *E_atom, float *dT, cudaStream_t st)
+{
+    if (!m->d_tcfit_x3) DP_TRY(pack_fit_x3_weights(m));
+    switch (fit_x3_kind(m->dev)) {
+    case 1: return launch_fit_x3<FitX3Water>(m, nl, T, grid, E_atom, dT, st);
+    case 2: return launch_fit_x3<FitX3Student>(m, nl, T, grid, E_atom, dT, st);
+    case 3: return launch_fit_x3<FitX3Paper>(m, nl, T, grid, E_atom, dT, st);
+    default: set_error("no split-bf16 fitting kernel for this shape"); return DP_ERR_UNSUPPORTED;
+    }
+}
+
 // Packed weights of one net: hi = bf16(w), lo = bf16(w - hi) with w the FP64 weight (so lo also
 // carries what an FP32 rounding of w would lose below 2^-16).
 template <class S>
@@ -694,17 +1176,21 @@ dp_status run_x3(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
     }
     DP_CUDA(cudaGetLastError());
     const int64_t nd = (int64_t)md.desc_dim * n, nq = (int64_t)4 * md.m1 * n;
-    {
-        ProfScope ps(m->prof, PG_DESC, 1, st);
-        k_desc_f32<<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(md, nl->d_order, n, T, D);
+    if (fit_x3_kind(md) != 0 && getenv("DP_SIMT_FIT") == nullptr) {
+        DP_TRY(fit_x3(m, nl, T, nsm, d_atom_energy, dT, st));
+    } else {
+        {
+            ProfScope ps(m->prof, PG_DESC, 1, st);
+            k_desc_f32<<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(md, nl->d_order, n, T, D);
+        }
+        DP_CUDA(cudaGetLastError());
+        DP_TRY(fit_f32(m, nl, D, dD, d_atom_energy, st));
+        {
+            ProfScope ps(m->prof, PG_DESC, 1, st);
+            k_dT_f32<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(md, nl->d_order, n, T, dD, dT);
+        }
+        DP_CUDA(cudaGetLastError());
     }
-    DP_CUDA(cudaGetLastError());
-    DP_TRY(fit_f32(m, nl, D, dD, d_atom_energy, st));
-    {
-        ProfScope ps(m->prof, PG_DESC, 1, st);
-        k_dT_f32<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(md, nl->d_order, n, T, dD, dT);
-    }
-    DP_CUDA(cudaGetLastError());
     {
         ProfScope ps(m->prof, PG_EMBED_BWD, 1, st);
         k_embed_bwd_x3<S><<<(unsigned)(X::B_CTAS * nsm), kTcThreads, X::B_SMEM, st>>>(
@@ -720,9 +1206,10 @@ dp_status run_x3(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
 dp_status pack_x3_weights(dp_model *m)
 {
     const int *e = m->dev.emb.wout;
-    if (e[0] == 25) return pack_x3<TcWater>(m);
-    if (e[0] == 8) return pack_x3<TcStudent>(m);
-    return pack_x3<TcPaper>(m);
+    if (e[0] == 25) DP_TRY(pack_x3<TcWater>(m));
+    else if (e[0] == 8) DP_TRY(pack_x3<TcStudent>(m));
+    else DP_TRY(pack_x3<TcPaper>(m));
+    return m->d_tcfit_x3 ? pack_fit_x3_weights(m) : DP_OK;
 }
 
 dp_status compute_mix_x3(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,

@@ -1,0 +1,648 @@
+// Wide embedding nets on the tensor cores, layer by layer (Sec. 6, "Network size": the paper sweeps
+// the embedding net up to a 1024 x 2048 last-layer matrix, where its MIX-16 throughput kept rising).
+//
+// Nets (w, 2w, 4w) with w = 64 .. 512 (last layers 128 x 256 .. 1024 x 2048) in MIX-16 with bf16
+// operands.  At these widths the activations of a 128-row tile (up to 3.5 K values per row) no longer
+// fit beside the weights in shared and tensor memory, so the fused per-tile kernels of tc.cu give way
+// to one tensor-core GEMM per layer with the activations in HBM; the products are large enough
+// (up to 2 M multiply-adds per row for the last layer) that the GEMMs, not the activation traffic,
+// bound the step.  The rows are the tiles of the MIX-16 work list (128 rows of one net, 4 chunks of
+// up to 32 neighbors of one atom).  Per evaluation:
+//   k_wide_l1   t1 = tanh(s W1 + b1) -> Y1 (bf16)                                   CUDA cores
+//   GEMM FWD2   z2 = Y1 W2;  t2 = tanh(z2 + b2) -> T2, y2 = (y1, y1) + t2 -> Y2           tcgen05
+//   GEMM FWD3   z3 = Y2 W3;  t3 -> T3, G = (y2, y2) + t3; T_q += G^T R per chunk         tcgen05
+//   fitting net (tc.cu), dE/dT
+//   k_wide_b1   dG = dT R, dR = dT^T G, dz3 = dG (1 - t3^2) -> DZ3                        CUDA cores
+//   GEMM BWD3   dy2 = dz3 W3^T + skip(dG) -> DY2 (FP32), dz2 = dy2 (1 - t2^2) -> DZ2        tcgen05
+//   GEMM BWD2   dy1 = dz2 W2^T + skip(dy2); ds += sum_k dy1 (1 - t1^2) W1_k                 tcgen05
+//   k_wide_force g_ij from ds and dR, FP64 force and virial atomics                        CUDA cores
+// The GEMM kernel: persistent CTAs over (tile, 256-column block) units; all 128 threads stream the
+// K chunks (64 wide) of A (the tile's 128 rows) and B (the block's rows of the net's weight matrix)
+// into a three-stage ring with cp.async (16-byte copies placed straight into the core-matrix layout
+// of the MMA operands); one thread issues the M = 128, N = 256 MMAs into a tensor-memory accumulator;
+// every thread then runs the layer's epilogue for its row.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "dp_internal.cuh"
+#include "tc_common.cuh"
+
+namespace dp {
+
+namespace {
+
+constexpr long kWaitW = 1L << 25;   // mbarrier polls (~1 s) before a kernel gives up
+constexpr int kWK = 64;             // K chunk
+constexpr int kWNB = 256;           // columns per unit
+constexpr int kWStages = 3;
+constexpr uint32_t kWA = 128 * kWK * 2, kWB = kWNB * kWK * 2, kWStage = kWA + kWB;
+constexpr uint32_t kWGT = kWNB * 128 * 2, kWRT = 16 * 128 * 2;   // contraction operands (FWD3)
+constexpr uint32_t kWSmem = kWStages * kWStage + kWGT + kWRT;
+static_assert(kWSmem <= 227 * 1024, "shared memory");
+
+enum WideKind { WK_FWD2 = 0, WK_FWD3 = 1, WK_BWD3 = 2, WK_BWD2 = 3 };
+
+struct WideArgs {
+    int E0, E1, E2;
+    uint32_t img;                       // bytes of one net's weight image
+    uint32_t oW2T, oW3T, oW3, oW2, oVec;   // offsets in the image
+    const int4 *chunks;
+    const int *ntiles;
+    const int32_t *nnei, *nlist;
+    const float4 *envA;
+    const float2 *envB;
+    const unsigned char *wimg;
+    __nv_bfloat16 *Y1, *T2, *Y2, *T3, *DZ3, *DZ2;
+    float *DY2, *DR, *DS;
+    float *T;                           // [n][E2][4], accumulated (times 1, scaled by 1/sum(sel) later)
+    const float *dT;                    // [n][E2][4], already scaled by 1/sum(sel)
+    double *force, *atom_virial;
+    int *err;
+};
+
+// The row `r` (0..127) of tile `tile`: its chunk entry, validity, geometry and neighbor.
+struct WRow {
+    int atom, net, j;
+    bool valid;
+    float4 a;   // s, u
+    float2 b;   // ds/dr, r
+};
+
+__device__ __forceinline__ WRow wide_row(const ModelDev &md, const WideArgs &w, int64_t tile, int r)
+{
+    WRow o;
+    const int4 c4 = w.chunks[tile * 4 + (r >> 5)];
+    o.net = w.chunks[tile * 4].w;
+    o.atom = c4.x;
+    o.valid = false;
+    o.j = -1;
+    o.a = make_float4(0.f, 0.f, 0.f, 0.f);
+    o.b = make_float2(0.f, 0.f);
+    if (c4.x >= 0) {
+        const int k = c4.z + (r & 31);
+        if (k < w.nnei[(int64_t)c4.x * md.ntypes + c4.y]) {
+            const int64_t slot = (int64_t)c4.x * md.nsel + md.sel_off[c4.y] + k;
+            o.valid = true;
+            o.a = w.envA[slot];
+            o.b = w.envB[slot];
+            o.j = w.nlist[slot];
+        }
+    }
+    return o;
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ uint32_t bf2(float a, float b)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+__device__ __forceinline__ float2 unbf2(uint32_t v) { return __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&v)); }
+
+// 16 bf16 values of a row-major bf16 array as floats.
+__device__ __forceinline__ void ld16(const __nv_bfloat16 *p, float *v)
+{
+    const uint4 a = *reinterpret_cast<const uint4 *>(p), b = *reinterpret_cast<const uint4 *>(p + 8);
+    const uint32_t q[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float2 f = unbf2(q[i]);
+        v[2 * i] = f.x;
+        v[2 * i + 1] = f.y;
+    }
+}
+__device__ __forceinline__ void st16(__nv_bfloat16 *p, const float *v)
+{
+    *reinterpret_cast<uint4 *>(p) = make_uint4(bf2(v[0], v[1]), bf2(v[2], v[3]), bf2(v[4], v[5]), bf2(v[6], v[7]));
+    *reinterpret_cast<uint4 *>(p + 8) =
+        make_uint4(bf2(v[8], v[9]), bf2(v[10], v[11]), bf2(v[12], v[13]), bf2(v[14], v[15]));
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_m[kWStages], bar_c;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // A [rows][K] and B [N][K] of the product (row-major bf16), K and N of the layer
+    const int K = KIND == WK_FWD2 ? w.E0 : KIND == WK_FWD3 ? w.E1 : KIND == WK_BWD3 ? w.E2 : w.E1;
+    const int N = KIND == WK_FWD2 ? w.E1 : KIND == WK_FWD3 ? w.E2 : KIND == WK_BWD3 ? w.E1 : w.E0;
+    const __nv_bfloat16 *A = KIND == WK_FWD2 ? w.Y1 : KIND == WK_FWD3 ? w.Y2 : KIND == WK_BWD3 ? w.DZ3 : w.DZ2;
+    const uint32_t oB = KIND == WK_FWD2 ? w.oW2T : KIND == WK_FWD3 ? w.oW3T : KIND == WK_BWD3 ? w.oW3 : w.oW2;
+    if (tid == 0) {
+        for (int q = 0; q < kWStages; ++q) tc::mbar_init(&bar_m[q], 1);
+        tc::mbar_init(&bar_c, 1);
+        tc::mbar_init_fence();
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    uint32_t ph_m[kWStages] = {0, 0, 0}, ph_c = 0;
+    const int nk = K / kWK, nblk = (N + kWNB - 1) / kWNB;
+    const int64_t ntiles = *w.ntiles, units = ntiles * nblk;
+    bool dead = false;
+    auto wait_all = [&](uint64_t *bar, uint32_t &ph) {
+        const bool ok = tc::mbar_wait(bar, ph, kWaitW);
+        ph ^= 1;
+        return __syncthreads_and(ok) != 0;
+    };
+    for (int64_t u = blockIdx.x; u < units && !dead; u += gridDim.x) {
+        const int64_t tile = u / nblk;
+        const int nb = (int)(u - tile * nblk);
+        const int nbc = N - nb * kWNB < kWNB ? N - nb * kWNB : kWNB;
+        const int net = w.chunks[tile * 4].w;
+        const __nv_bfloat16 *Ab = A + (tile * 128) * (int64_t)K;
+        const __nv_bfloat16 *Bb =
+            reinterpret_cast<const __nv_bfloat16 *>(w.wimg + (size_t)net * w.img + oB) + (int64_t)nb * kWNB * K;
+        // one K chunk of A (this thread's row) and of B (rows tid, tid + 128) into stage s
+        auto load = [&](int kc, int s) {
+            unsigned char *sa = smem + s * kWStage, *sb = sa + kWA;
+            const __nv_bfloat16 *ar = Ab + (int64_t)tid * K + kc * kWK;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) cp_async16(sa + tc::kmaj_off(tid, 8 * q, kWK), ar + 8 * q);
+            for (int rb = tid; rb < nbc; rb += 128) {
+                const __nv_bfloat16 *br = Bb + (int64_t)rb * K + kc * kWK;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) cp_async16(sb + tc::kmaj_off(rb, 8 * q, kWK), br + 8 * q);
+            }
+        };
+        const uint32_t id = tc::idesc_f16(128, nbc, 1);
+#pragma unroll
+        for (int p = 0; p < kWStages - 1; ++p) {
+            if (p < nk) load(p, p);
+            cp_commit();
+        }
+        for (int kc = 0; kc < nk; ++kc) {
+            const int s = kc % kWStages;
+            cp_wait<kWStages - 2>();          // chunk kc has landed (this thread's copies)
+            tc::fence_async_smem();           // ... and is visible to the tensor core
+            tc::fence_before_sync();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after_sync();
+                const uint32_t sa = tc::smem_u32(smem + s * kWStage), sb = sa + kWA;
+                for (int ks = 0; ks < kWK / 16; ++ks) {
+                    const uint64_t ad = tc::smem_desc(sa + ks * 256, 128, (kWK / 8) * 128);
+                    const uint64_t bd = tc::smem_desc(sb + ks * 256, 128, (kWK / 8) * 128);
+                    const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(id), "r"(acc));
+                }
+                tc::mma_commit(&bar_m[s]);
+            }
+            // the stage of chunk kc + kWStages - 1 was read by the MMAs of chunk kc - 1
+            const int kn = kc + kWStages - 1;
+            if (kn < nk) {
+                const int sn = kn % kWStages;
+                if (kc >= 1 && !wait_all(&bar_m[sn], ph_m[sn])) { dead = true; break; }
+                load(kn, sn);
+            }
+            cp_commit();
+        }
+        if (dead) break;
+        // the MMAs not waited for yet: chunks max(0, nk - kWStages) .. nk - 1, in order
+        for (int kc = nk - kWStages > 0 ? nk - kWStages : 0; kc < nk; ++kc) {
+            const int s = kc % kWStages;
+            if (!wait_all(&bar_m[s], ph_m[s])) { dead = true; break; }
+        }
+        if (dead) break;
+        tc::fence_after_sync();
+        // ---------------------------------------------------------------- epilogues (thread = row)
+        const WRow row = wide_row(md, w, tile, tid);
+        const int64_t gr = tile * 128 + tid;
+        const float *vec = reinterpret_cast<const float *>(w.wimg + (size_t)net * w.img + w.oVec);
+        const float *W1 = vec, *b1 = vec + w.E0, *b2 = vec + 2 * w.E0, *b3 = b2 + w.E1;
+        if constexpr (KIND == WK_FWD2) {
+            for (int c0 = 0; c0 < nbc; c0 += 16) {
+                const int k0 = nb * kWNB + c0;
+                float z[16], y1[16], t[16], y[16];
+                tc::tmem_ld16(taddr + c0, z);
+                tc::tmem_ld_wait();
+                ld16(w.Y1 + gr * w.E0 + (k0 % w.E0), y1);   // skip: y2 = (y1, y1) + t2
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    t[i] = tc::tanh_fast(z[i] + b2[k0 + i]);
+                    y[i] = y1[i] + t[i];
+                }
+                st16(w.T2 + gr * w.E1 + k0, t);
+                st16(w.Y2 + gr * w.E1 + k0, y);
+            }
+        } else if constexpr (KIND == WK_FWD3) {
+            unsigned char *GT = smem + kWStages * kWStage, *RT = GT + kWGT;
+            {
+                const float s = row.valid ? row.a.x : 0.f;
+                float r8[8] = {s, s * row.a.y, s * row.a.z, s * row.a.w, 0.f, 0.f, 0.f, 0.f};
+                if (!row.valid) r8[1] = r8[2] = r8[3] = 0.f;
+                *reinterpret_cast<uint4 *>(RT + tc::mnmaj_off(0, tid, 16)) =
+                    make_uint4(bf2(r8[0], r8[1]), bf2(r8[2], r8[3]), 0u, 0u);
+                *reinterpret_cast<uint4 *>(RT + tc::mnmaj_off(8, tid, 16)) = make_uint4(0u, 0u, 0u, 0u);
+            }
+            for (int c0 = 0; c0 < nbc; c0 += 16) {
+                const int m0 = nb * kWNB + c0;
+                float z[16], y2[16], t[16], g[16];
+                tc::tmem_ld16(taddr + c0, z);
+                tc::tmem_ld_wait();
+                ld16(w.Y2 + gr * w.E1 + (m0 % w.E1), y2);   // skip: G = (y2, y2) + t3
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    t[i] = tc::tanh_fast(z[i] + b3[m0 + i]);
+                    g[i] = y2[i] + t[i];
+                }
+                st16(w.T3 + gr * w.E2 + m0, t);
+                *reinterpret_cast<uint4 *>(GT + tc::mnmaj_off(c0, tid, kWNB)) =
+                    make_uint4(bf2(g[0], g[1]), bf2(g[2], g[3]), bf2(g[4], g[5]), bf2(g[6], g[7]));
+                *reinterpret_cast<uint4 *>(GT + tc::mnmaj_off(c0 + 8, tid, kWNB)) =
+                    make_uint4(bf2(g[8], g[9]), bf2(g[10], g[11]), bf2(g[12], g[13]), bf2(g[14], g[15]));
+            }
+            tc::fence_async_smem();
+            tc::fence_before_sync();
+            __syncthreads();
+            // T_q[m][c] = sum over chunk q's 32 rows of G[row][m] R[row][c], for the block's channels in
+            // halves of 128 (tensor-memory columns 256 + 16 (4 h + q))
+            if (tid == 0) {
+                tc::fence_after_sync();
+                const uint32_t idT = tc::idesc_f16_major(128, 16, 1, 1, 1);
+                for (int h = 0; h < nbc / 128; ++h)
+                    for (int q = 0; q < 4; ++q)
+                        tc::mma_kloop_mn(tmem + 256 + 16 * (4 * h + q), tc::smem_u32(GT) + 2048 * h, kWNB,
+                                         tc::smem_u32(RT), 16, 32 * q, 32, idT, false);
+                tc::mma_commit(&bar_c);
+            }
+            if (!wait_all(&bar_c, ph_c)) { dead = true; break; }
+            tc::fence_after_sync();
+            for (int h = 0; h < nbc / 128; ++h) {
+                const int m = nb * kWNB + 128 * h + warp * 32 + lane;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float v[4];
+                    tc::tmem_ld4(taddr + 256 + 16 * (4 * h + q), v);
+                    tc::tmem_ld_wait();
+                    const int atom = w.chunks[tile * 4 + q].x;
+                    if (atom >= 0) {
+                        float *Tm = w.T + ((int64_t)atom * w.E2 + m) * 4;
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) atomicAdd(Tm + c, v[c]);
+                    }
+                }
+            }
+        } else if constexpr (KIND == WK_BWD3) {
+            const float s = row.valid ? row.a.x : 0.f;
+            const float R[4] = {s, s * row.a.y, s * row.a.z, s * row.a.w};
+            const float4 *dTa = reinterpret_cast<const float4 *>(w.dT + (int64_t)(row.atom >= 0 ? row.atom : 0) * w.E2 * 4);
+            for (int c0 = 0; c0 < nbc; c0 += 16) {
+                const int k0 = nb * kWNB + c0;
+                float z[16], t2[16], dz[16];
+                tc::tmem_ld16(taddr + c0, z);
+                tc::tmem_ld_wait();
+                ld16(w.T2 + gr * w.E1 + k0, t2);
+                float dy[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    // skip of layer 3: dG[k] + dG[k + E1], dG[m] = dT[m] . R
+                    float sk = 0.f;
+                    if (row.valid) {
+                        const float4 a = dTa[k0 + i], b = dTa[k0 + i + w.E1];
+                        sk = a.x * R[0] + a.y * R[1] + a.z * R[2] + a.w * R[3] + b.x * R[0] + b.y * R[1] +
+                             b.z * R[2] + b.w * R[3];
+                    }
+                    dy[i] = z[i] + sk;
+                    dz[i] = dy[i] * (1.f - t2[i] * t2[i]);
+                }
+                st16(w.DZ2 + gr * w.E1 + k0, dz);
+                float4 *d4 = reinterpret_cast<float4 *>(w.DY2 + gr * w.E1 + k0);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) d4[i] = make_float4(dy[4 * i], dy[4 * i + 1], dy[4 * i + 2], dy[4 * i + 3]);
+            }
+        } else {   // WK_BWD2
+            const float s = row.valid ? row.a.x : 0.f;
+            float ds = 0.f;
+            for (int c0 = 0; c0 < nbc; c0 += 16) {
+                const int k0 = nb * kWNB + c0;
+                float z[16];
+                tc::tmem_ld16(taddr + c0, z);
+                tc::tmem_ld_wait();
+                const float4 *a4 = reinterpret_cast<const float4 *>(w.DY2 + gr * w.E1 + k0);
+                const float4 *b4 = reinterpret_cast<const float4 *>(w.DY2 + gr * w.E1 + k0 + w.E0);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float4 a = a4[i], b = b4[i];
+                    const float sk[4] = {a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w};   // skip of layer 2
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int k = k0 + 4 * i + e;
+                        const float t1 = tc::tanh_fast(fmaf(s, W1[k], b1[k]));
+                        ds = fmaf((z[4 * i + e] + sk[e]) * (1.f - t1 * t1), W1[k], ds);
+                    }
+                }
+            }
+            if (row.valid) atomicAdd(w.DS + gr, ds);
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    if (dead && tid == 0) atomicOr(w.err, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
+// Layer 1 (1 -> E0, plain since E0 >= 64): one warp per row, lanes over the outputs.
+__global__ void k_wide_l1(ModelDev md, WideArgs w, int64_t max_rows)
+{
+    const int64_t gr = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gr >= max_rows || gr >= (int64_t)(*w.ntiles) * 128) return;
+    const WRow row = wide_row(md, w, gr >> 7, (int)(gr & 127));
+    const float *vec = reinterpret_cast<const float *>(w.wimg + (size_t)row.net * w.img + w.oVec);
+    const float s = row.valid ? row.a.x : 0.f;
+    for (int k = 2 * lane; k < w.E0; k += 64) {
+        const float t0 = tc::tanh_fast(fmaf(s, vec[k], vec[w.E0 + k]));
+        const float t1 = tc::tanh_fast(fmaf(s, vec[k + 1], vec[w.E0 + k + 1]));
+        *reinterpret_cast<uint32_t *>(w.Y1 + gr * w.E0 + k) = bf2(t0, t1);
+    }
+}
+
+// Start of the backward pass per row (one warp, lanes over the channels m):
+//   dG = dT R, G = (y2, y2) + t3, dR = dT^T G (warp sum), dz3 = dG (1 - t3^2) -> DZ3.
+__global__ void k_wide_b1(ModelDev md, WideArgs w, int64_t max_rows)
+{
+    const int64_t gr = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gr >= max_rows || gr >= (int64_t)(*w.ntiles) * 128) return;
+    const WRow row = wide_row(md, w, gr >> 7, (int)(gr & 127));
+    float dR[4] = {0.f, 0.f, 0.f, 0.f};
+    const float s = row.valid ? row.a.x : 0.f;
+    const float R[4] = {s, s * row.a.y, s * row.a.z, s * row.a.w};
+    const float4 *dTa = reinterpret_cast<const float4 *>(w.dT + (int64_t)(row.atom >= 0 ? row.atom : 0) * w.E2 * 4);
+    for (int m = 2 * lane; m < w.E2; m += 64) {
+        const float2 t3 = unbf2(*reinterpret_cast<const uint32_t *>(w.T3 + gr * w.E2 + m));
+        const float2 y2 = unbf2(*reinterpret_cast<const uint32_t *>(w.Y2 + gr * w.E1 + (m % w.E1)));
+        float dz[2] = {0.f, 0.f};
+        if (row.valid) {
+            const float tt[2] = {t3.x, t3.y}, yy[2] = {y2.x, y2.y};
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float4 d = dTa[m + e];
+                const float G = yy[e] + tt[e];
+                dR[0] = fmaf(d.x, G, dR[0]);
+                dR[1] = fmaf(d.y, G, dR[1]);
+                dR[2] = fmaf(d.z, G, dR[2]);
+                dR[3] = fmaf(d.w, G, dR[3]);
+                const float dG = d.x * R[0] + d.y * R[1] + d.z * R[2] + d.w * R[3];
+                dz[e] = dG * (1.f - tt[e] * tt[e]);
+            }
+        }
+        *reinterpret_cast<uint32_t *>(w.DZ3 + gr * w.E2 + m) = bf2(dz[0], dz[1]);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        for (int o = 16; o > 0; o >>= 1) dR[c] += __shfl_xor_sync(0xffffffffu, dR[c], o);
+    if (lane == 0) *reinterpret_cast<float4 *>(w.DR + 4 * gr) = make_float4(dR[0], dR[1], dR[2], dR[3]);
+}
+
+// g_ij = (dR/dr_ij)^T dE/dR from ds and dR (R = (s, s u), u = d/r):
+//   g = u (dR0 s' + (s' - s/r) u.dR') + (s/r) dR'; F_j -= g, F_i += g, W_i -= d (x) g (FP64 atomics);
+// one block per tile, a warp per chunk (one atom).
+__global__ void __launch_bounds__(128) k_wide_force(ModelDev md, WideArgs w)
+{
+    const int64_t tile = blockIdx.x;
+    if (tile >= *w.ntiles) return;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const WRow row = wide_row(md, w, tile, tid);
+    const int64_t gr = tile * 128 + tid;
+    float gv[3] = {0.f, 0.f, 0.f}, vir[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) vir[q] = 0.f;
+    if (row.valid) {
+        const float4 dr = *reinterpret_cast<const float4 *>(w.DR + 4 * gr);
+        const float u[3] = {row.a.y, row.a.z, row.a.w}, dsdr = row.b.x, r = row.b.y, s = row.a.x;
+        const float sr = s / r;
+        const float dR0 = dr.x + w.DS[gr];
+        const float ud = u[0] * dr.y + u[1] * dr.z + u[2] * dr.w;
+        const float cu = fmaf(dsdr - sr, ud, dR0 * dsdr);
+        const float dRp[3] = {dr.y, dr.z, dr.w};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gv[k] = fmaf(cu, u[k], sr * dRp[k]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) atomicAdd(&w.force[3 * (int64_t)row.j + k], -(double)gv[k]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) vir[3 * a + b] = -(r * u[a]) * gv[b];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        for (int o = 16; o > 0; o >>= 1) gv[k] += __shfl_xor_sync(0xffffffffu, gv[k], o);
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+        for (int o = 16; o > 0; o >>= 1) vir[q] += __shfl_xor_sync(0xffffffffu, vir[q], o);
+    const int atom = w.chunks[tile * 4 + (tid >> 5)].x;
+    if (atom >= 0) {
+        if (lane < 3) {
+            const float v = lane == 0 ? gv[0] : (lane == 1 ? gv[1] : gv[2]);
+            atomicAdd(&w.force[3 * (int64_t)atom + lane], (double)v);
+        }
+        if (lane < 9) {
+            float v = 0.f;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) v = (q == lane) ? vir[q] : v;
+            atomicAdd(&w.atom_virial[9 * (int64_t)atom + lane], (double)v);
+        }
+    }
+}
+
+struct WideLayout {
+    int E0, E1, E2;
+    uint32_t oW2T, oW3T, oW3, oW2, oVec, img;
+};
+
+WideLayout wide_layout(const ModelDev &md)
+{
+    WideLayout L;
+    L.E0 = md.emb.wout[0];
+    L.E1 = md.emb.wout[1];
+    L.E2 = md.emb.wout[2];
+    L.oW2T = 0;
+    L.oW3T = L.oW2T + (uint32_t)L.E1 * L.E0 * 2;
+    L.oW3 = L.oW3T + (uint32_t)L.E2 * L.E1 * 2;
+    L.oW2 = L.oW3 + (uint32_t)L.E1 * L.E2 * 2;
+    L.oVec = L.oW2 + (uint32_t)L.E0 * L.E1 * 2;
+    L.img = L.oVec + (uint32_t)(2 * L.E0 + L.E1 + L.E2) * 4;
+    return L;
+}
+
+}  // namespace
+
+// Nets (w, 2w, 4w), w = 64, 128, 256, 512: the wide path of this file.
+bool embed_is_wide(int n_embed, const int *e)
+{
+    if (n_embed != 3) return false;
+    const int b = e[0];
+    return (b == 64 || b == 128 || b == 256 || b == 512) && e[1] == 2 * b && e[2] == 4 * b;
+}
+
+dp_status pack_wide_weights(dp_model *m)
+{
+    const ModelDev &md = m->dev;
+    const WideLayout L = wide_layout(md);
+    const int nn = m->ntypes * m->ntypes;
+    std::vector<unsigned char> img((size_t)nn * L.img, 0);
+    auto bf = [](double v) {
+        const __nv_bfloat16 h = __double2bfloat16(v);
+        uint16_t u;
+        memcpy(&u, &h, 2);
+        return u;
+    };
+    for (int q = 0; q < nn; ++q) {
+        const double *p = m->h_params.data() + md.emb_base + q * md.emb.size;
+        unsigned char *o = img.data() + (size_t)q * L.img;
+        uint16_t *w2t = reinterpret_cast<uint16_t *>(o + L.oW2T), *w3t = reinterpret_cast<uint16_t *>(o + L.oW3T);
+        uint16_t *w3 = reinterpret_cast<uint16_t *>(o + L.oW3), *w2 = reinterpret_cast<uint16_t *>(o + L.oW2);
+        const double *W1 = p + md.emb.W[0], *b1 = p + md.emb.b[0], *W2 = p + md.emb.W[1], *b2 = p + md.emb.b[1];
+        const double *W3 = p + md.emb.W[2], *b3 = p + md.emb.b[2];
+        for (int a = 0; a < L.E0; ++a)
+            for (int b = 0; b < L.E1; ++b) {
+                w2[(size_t)a * L.E1 + b] = bf(W2[(size_t)a * L.E1 + b]);    // W2 [E0][E1]
+                w2t[(size_t)b * L.E0 + a] = bf(W2[(size_t)a * L.E1 + b]);   // W2^T [E1][E0]
+            }
+        for (int a = 0; a < L.E1; ++a)
+            for (int b = 0; b < L.E2; ++b) {
+                w3[(size_t)a * L.E2 + b] = bf(W3[(size_t)a * L.E2 + b]);
+                w3t[(size_t)b * L.E1 + a] = bf(W3[(size_t)a * L.E2 + b]);
+            }
+        float *vec = reinterpret_cast<float *>(o + L.oVec);
+        for (int k = 0; k < L.E0; ++k) {
+            vec[k] = (float)W1[k];
+            vec[L.E0 + k] = (float)b1[k];
+        }
+        for (int k = 0; k < L.E1; ++k) vec[2 * L.E0 + k] = (float)b2[k];
+        for (int k = 0; k < L.E2; ++k) vec[2 * L.E0 + L.E1 + k] = (float)b3[k];
+    }
+    if (!m->d_wide) DP_CUDA(cudaMalloc((void **)&m->d_wide, img.size()));
+    DP_CUDA(cudaMemcpyAsync(m->d_wide, img.data(), img.size(), cudaMemcpyHostToDevice, m->stream));
+    DP_CUDA(cudaStreamSynchronize(m->stream));
+    return DP_OK;
+}
+
+dp_status compute_wide(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
+                       double *d_virial, double *d_atom_virial, cudaStream_t st)
+{
+    const ModelDev &md = m->dev;
+    const WideLayout L = wide_layout(md);
+    const int64_t n = nl->n;
+    const int nn = md.ntypes * md.ntypes;
+    const int64_t max_chunks = n * md.chunks_per_atom + 4 * nn + 4;
+    const int64_t max_rows = max_chunks * 32;   // 4 chunks of 32 rows per tile
+    if (!nl->d_env) {
+        set_error("wide embedding path needs the neighbor geometry of the formatting kernel");
+        return DP_ERR_ARG;
+    }
+    if (!m->d_wide) DP_TRY(pack_wide_weights(m));
+    size_t need = 0;
+    auto sz = [&](size_t b) { need += (b + 255) & ~(size_t)255; };
+    sz(sizeof(float) * 4 * md.m1 * n);
+    sz(sizeof(float) * 4 * md.m1 * n);
+    sz(sizeof(int4) * max_chunks);
+    sz(sizeof(int) * 4);
+    sz(chunks_batch_scratch(md, n));
+    sz(2 * (size_t)max_rows * L.E0);        // Y1
+    sz(2 * (size_t)max_rows * L.E1 * 3);    // T2, Y2, DZ2
+    sz(2 * (size_t)max_rows * L.E2 * 2);    // T3, DZ3
+    sz(4 * (size_t)max_rows * L.E1);        // DY2
+    sz(4 * (size_t)max_rows * 5);           // DR, DS
+    DP_TRY(ensure_workspace(m, need));
+    char *wp = m->ws;
+    auto carve = [&](size_t bytes) {
+        char *p = wp;
+        wp += (bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    WideArgs a;
+    a.E0 = L.E0;
+    a.E1 = L.E1;
+    a.E2 = L.E2;
+    a.img = L.img;
+    a.oW2T = L.oW2T;
+    a.oW3T = L.oW3T;
+    a.oW3 = L.oW3;
+    a.oW2 = L.oW2;
+    a.oVec = L.oVec;
+    a.T = (float *)carve(sizeof(float) * 4 * md.m1 * n);
+    float *dT = (float *)carve(sizeof(float) * 4 * md.m1 * n);
+    a.dT = dT;
+    int4 *chunks = (int4 *)carve(sizeof(int4) * max_chunks);
+    int *cnt = (int *)carve(sizeof(int) * 4);
+    char *scratch = carve(chunks_batch_scratch(md, n));
+    a.Y1 = (__nv_bfloat16 *)carve(2 * (size_t)max_rows * L.E0);
+    a.T2 = (__nv_bfloat16 *)carve(2 * (size_t)max_rows * L.E1);
+    a.Y2 = (__nv_bfloat16 *)carve(2 * (size_t)max_rows * L.E1);
+    a.DZ2 = (__nv_bfloat16 *)carve(2 * (size_t)max_rows * L.E1);
+    a.T3 = (__nv_bfloat16 *)carve(2 * (size_t)max_rows * L.E2);
+    a.DZ3 = (__nv_bfloat16 *)carve(2 * (size_t)max_rows * L.E2);
+    a.DY2 = (float *)carve(4 * (size_t)max_rows * L.E1);
+    a.DR = (float *)carve(4 * (size_t)max_rows * 4);
+    a.DS = (float *)carve(4 * (size_t)max_rows);
+    a.chunks = chunks;
+    a.ntiles = cnt;
+    a.nnei = nl->d_nnei;
+    a.nlist = nl->d_nlist;
+    a.envA = reinterpret_cast<const float4 *>(nl->d_env);
+    a.envB = reinterpret_cast<const float2 *>(nl->d_env + 4 * (size_t)n * md.nsel);
+    a.wimg = m->d_wide;
+    a.force = d_force;
+    a.atom_virial = d_atom_virial;
+    a.err = m->d_err;
+    int nsm = 0;
+    DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
+    DP_CUDA(cudaMemsetAsync(a.T, 0, sizeof(float) * 4 * md.m1 * n, st));
+    DP_CUDA(cudaMemsetAsync(a.DS, 0, 4 * (size_t)max_rows, st));
+    DP_CUDA(cudaMemsetAsync(d_force, 0, sizeof(double) * 3 * n, st));
+    DP_CUDA(cudaMemsetAsync(d_atom_virial, 0, sizeof(double) * 9 * n, st));
+    {
+        ProfScope ps(m->prof, PG_CHUNKS, 3, st);
+        DP_TRY(build_chunks_batch(m, nl, 0, n, chunks, nullptr, cnt, scratch, st));
+    }
+    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_FWD2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
+    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_FWD3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
+    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_BWD3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
+    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_BWD2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
+    const unsigned rb = (unsigned)((max_rows * 32 + 255) / 256);
+    {
+        ProfScope ps(m->prof, PG_EMBED_FWD, 3, st);
+        k_wide_l1<<<rb, 256, 0, st>>>(md, a, max_rows);
+        k_wide_gemm<WK_FWD2><<<nsm, 128, kWSmem, st>>>(md, a);
+        k_wide_gemm<WK_FWD3><<<nsm, 128, kWSmem, st>>>(md, a);
+    }
+    DP_CUDA(cudaGetLastError());
+    DP_TRY(fit_mix16_bf16(m, nl, a.T, d_atom_energy, dT, st));
+    {
+        ProfScope ps(m->prof, PG_EMBED_BWD, 4, st);
+        k_wide_b1<<<rb, 256, 0, st>>>(md, a, max_rows);
+        k_wide_gemm<WK_BWD3><<<nsm, 128, kWSmem, st>>>(md, a);
+        k_wide_gemm<WK_BWD2><<<nsm, 128, kWSmem, st>>>(md, a);
+        k_wide_force<<<(unsigned)(max_chunks / 4 + 1), 128, 0, st>>>(md, a);
+    }
+    DP_CUDA(cudaGetLastError());
+    ProfScope ps(m->prof, PG_REDUCE, 1, st);
+    return reduce_energy_virial(d_atom_energy, d_atom_virial, centers_of(nl), d_energy, d_virial, m->d_red, st);
+}
+
+}  // namespace dp
