@@ -67,8 +67,15 @@ typedef enum {
  *                terms (hi = bf16(x), lo = bf16(x - hi)) and each product
  *                taken as hi hi + hi lo + lo hi (three MMAs, FP32
  *                accumulation), tanh in FP32 (tanhf); descriptor and
- *                fitting net in FP32 on the CUDA cores (as DP_MIX32). */
-typedef enum { DP_FP64 = 0, DP_MIX32 = 1, DP_MIX_BF16 = 2, DP_MIX_FP16 = 3, DP_MIX_BF16X3 = 4 } dp_precision;
+ *                fitting net in FP32 on the CUDA cores (as DP_MIX32).
+ *   DP_MIX_FP8   the wide embedding nets (w, 2w, 4w), w = 64 .. 512, with
+ *                the products of layers 2 and 3 and their input gradients
+ *                on e4m3 operands (tcgen05 kind::f8f6f4, FP32 accumulation;
+ *                weights quantised with a power-of-two scale per row, the
+ *                backward operands with one power-of-two scale); all else as
+ *                DP_MIX_BF16.  Other nets: DP_ERR_UNSUPPORTED. */
+typedef enum { DP_FP64 = 0, DP_MIX32 = 1, DP_MIX_BF16 = 2, DP_MIX_FP16 = 3, DP_MIX_BF16X3 = 4,
+               DP_MIX_FP8 = 5 } dp_precision;
 
 /* Model hyper-parameters (Sec. 2, Sec. 5.1).
  *   ntypes       number of atom types (1..8)

@@ -20,8 +20,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libdp.so")
 DP_OK = 0
 STATUS = {0: "DP_OK", -1: "DP_ERR_ARG", -2: "DP_ERR_CUDA", -3: "DP_ERR_OOM", -4: "DP_ERR_BOX",
           -5: "DP_ERR_CAPACITY", -6: "DP_ERR_TIMEOUT", -7: "DP_ERR_NONFINITE", -8: "DP_ERR_UNSUPPORTED"}
-DP_FP64, DP_MIX32, DP_MIX_BF16, DP_MIX_FP16, DP_MIX_BF16X3 = 0, 1, 2, 3, 4
-PRECISION = {"fp64": DP_FP64, "mix32": DP_MIX32, "bf16": DP_MIX_BF16, "fp16": DP_MIX_FP16, "bf16x3": DP_MIX_BF16X3}
+DP_FP64, DP_MIX32, DP_MIX_BF16, DP_MIX_FP16, DP_MIX_BF16X3, DP_MIX_FP8 = 0, 1, 2, 3, 4, 5
+PRECISION = {"fp64": DP_FP64, "mix32": DP_MIX32, "bf16": DP_MIX_BF16, "fp16": DP_MIX_FP16, "bf16x3": DP_MIX_BF16X3,
+             "fp8": DP_MIX_FP8}
 
 # Every entry point declared in include/dp.h.
 EXPORTS = [

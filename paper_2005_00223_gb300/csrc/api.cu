@@ -112,20 +112,24 @@ dp_status compute_device(dp_model *m, dp_nlist *nl, const double *d_coord, dp_pr
                          cudaStream_t st)
 {
     DP_TRY(nlist_format_device(m, nl, d_coord, st,
-                               prec == DP_MIX_BF16 || prec == DP_MIX_FP16 || prec == DP_MIX_BF16X3));
+                               prec == DP_MIX_BF16 || prec == DP_MIX_FP16 || prec == DP_MIX_BF16X3 ||
+                                   prec == DP_MIX_FP8));
     if (nl->n == 0) {
         DP_CUDA(cudaMemsetAsync(d_energy, 0, sizeof(double), st));
         if (d_virial) DP_CUDA(cudaMemsetAsync(d_virial, 0, 9 * sizeof(double), st));
         return DP_OK;
     }
     dp_status r = DP_OK;
-    if (embed_is_wide(m->n_embed, m->embed)) {   // the wide nets run in MIX-16 with bf16 operands only
-        if (prec != DP_MIX_BF16) {
-            set_error("embedding nets wider than 32-64-128 run in DP_MIX_BF16 only");
+    if (embed_is_wide(m->n_embed, m->embed)) {   // the wide nets run in MIX-16 (bf16) or FP8 only
+        if (prec != DP_MIX_BF16 && prec != DP_MIX_FP8) {
+            set_error("embedding nets wider than 32-64-128 run in DP_MIX_BF16 or DP_MIX_FP8 only");
             return DP_ERR_UNSUPPORTED;
         }
-        r = compute_wide(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
+        r = compute_wide(m, nl, prec == DP_MIX_FP8, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
         prec = DP_PRECISION_DONE;
+    } else if (prec == DP_MIX_FP8) {
+        set_error("DP_MIX_FP8 covers the wide embedding nets (w, 2w, 4w), w = 64 .. 512, only");
+        return DP_ERR_UNSUPPORTED;
     }
     switch (prec) {
     case DP_FP64:
@@ -456,6 +460,7 @@ void dp_model_destroy(dp_model *m)
     cudaFree(m->d_tcw_x3);
     cudaFree(m->d_tcfit_x3);
     cudaFree(m->d_wide);
+    cudaFree(m->d_wide_q);
     cudaFree(m->d_ozw);
     cudaFree(m->d_oze);
     cudaFree(m->d_ozw_emb);
@@ -761,7 +766,8 @@ static dp_status compute_args(dp_model *m, dp_nlist *nl, const double box[9], dp
     if (nl->m != m) { set_error("the list was built for another model"); return DP_ERR_ARG; }
     if (!box) { set_error("box is NULL"); return DP_ERR_ARG; }
     if (!box_matches(nl, box)) { set_error("box differs from the list's box; build a new list"); return DP_ERR_ARG; }
-    if (prec != DP_FP64 && prec != DP_MIX32 && prec != DP_MIX_BF16 && prec != DP_MIX_FP16 && prec != DP_MIX_BF16X3) {
+    if (prec != DP_FP64 && prec != DP_MIX32 && prec != DP_MIX_BF16 && prec != DP_MIX_FP16 && prec != DP_MIX_BF16X3 &&
+        prec != DP_MIX_FP8) {
         set_error("unknown precision %d", (int)prec);
         return DP_ERR_ARG;
     }

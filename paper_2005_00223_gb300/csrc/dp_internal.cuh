@@ -159,6 +159,7 @@ struct dp_model {
     unsigned char *d_tcw_x3 = nullptr; // packed split-bf16 (hi, lo) embedding weights (DP_MIX_BF16X3)
     unsigned char *d_tcfit_x3 = nullptr; // packed split-bf16 fitting weights (DP_MIX_BF16X3)
     unsigned char *d_wide = nullptr;  // bf16 weights of the wide embedding nets (W2^T, W3^T, W3, W2, vectors)
+    unsigned char *d_wide_q = nullptr;   // their e4m3 copies with row scales (DP_MIX_FP8)
     void *d_ozw = nullptr;            // fp16 digits of the first fitting layer's weights (FP64 products on the tensor cores)
     int *d_oze = nullptr;             // their row scales
     bool oz_stale = true;             // digits older than the parameters
@@ -290,7 +291,7 @@ constexpr dp_precision DP_PRECISION_DONE = (dp_precision)1000;
 // Wide embedding nets (w, 2w, 4w), w = 64 .. 512, layer by layer on the tensor cores (wide.cu).
 bool embed_is_wide(int n_embed, const int *e);
 dp_status pack_wide_weights(dp_model *m);
-dp_status compute_wide(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
+dp_status compute_wide(dp_model *m, dp_nlist *nl, int fp8, double *d_energy, double *d_atom_energy, double *d_force,
                        double *d_virial, double *d_atom_virial, cudaStream_t st);
 // The MIX-16 fitting net (bf16 operands) of tc.cu, for the wide path.
 dp_status fit_mix16_bf16(dp_model *m, dp_nlist *nl, const float *T, double *E_atom, float *dT, cudaStream_t st);

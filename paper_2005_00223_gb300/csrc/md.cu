@@ -381,7 +381,8 @@ dp_status dp_md_step(dp_model *m, dp_md_state *s, int64_t nsteps, double dt_fs, 
 {
     if (!m || !s || s->m != m) { set_error("dp_md_step: NULL or mismatched handle"); return DP_ERR_ARG; }
     if (nsteps < 0 || !(dt_fs > 0) || !isfinite(dt_fs)) { set_error("need nsteps >= 0 and dt > 0"); return DP_ERR_ARG; }
-    if (prec != DP_FP64 && prec != DP_MIX32 && prec != DP_MIX_BF16 && prec != DP_MIX_FP16 && prec != DP_MIX_BF16X3) {
+    if (prec != DP_FP64 && prec != DP_MIX32 && prec != DP_MIX_BF16 && prec != DP_MIX_FP16 && prec != DP_MIX_BF16X3 &&
+        prec != DP_MIX_FP8) {
         set_error("unknown precision %d", (int)prec);
         return DP_ERR_ARG;
     }

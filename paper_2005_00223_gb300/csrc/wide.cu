@@ -21,7 +21,15 @@
 // into a three-stage ring with cp.async (16-byte copies placed straight into the core-matrix layout
 // of the MMA operands); one thread issues the M = 128, N = 256 MMAs into a tensor-memory accumulator;
 // every thread then runs the layer's epilogue for its row.
+//
+// FP8 (precision DP_MIX_FP8, beyond the paper's MIX-16): the same GEMMs with e4m3 operands
+// (tcgen05 kind::f8f6f4, FP32 accumulation).  The producing epilogues write an e4m3 copy of each GEMM
+// input beside the bf16 values that the skips and derivatives read; the weights are quantised once per
+// parameter upload with a power-of-two scale per row (its largest entry in (224, 448]), undone in the
+// consuming epilogue; the backward inputs carry dE/dT scaled by a power of two 2^(3-e), e the exponent
+// of its largest entry, undone (exactly) on g before the force and virial sums.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -50,6 +58,11 @@ struct WideArgs {
     int E0, E1, E2;
     uint32_t img;                       // bytes of one net's weight image
     uint32_t oW2T, oW3T, oW3, oW2, oVec;   // offsets in the image
+    // FP8: one net's e4m3 image (the same four matrices, then their row scales 1/s as FP32)
+    uint32_t qimg, qW2T, qW3T, qW3, qW2, qS2T, qS3T, qS3, qS2;
+    const unsigned char *wq;
+    unsigned char *Y1q, *Y2q, *DZ3q, *DZ2q;   // e4m3 copies of the GEMM inputs
+    const unsigned *gbits;              // bits of max |dE/dT| (FP8: backward scaling), or null
     const int4 *chunks;
     const int *ntiles;
     const int32_t *nnei, *nlist;
@@ -129,7 +142,39 @@ __device__ __forceinline__ void st16(__nv_bfloat16 *p, const float *v)
         make_uint4(bf2(v[8], v[9]), bf2(v[10], v[11]), bf2(v[12], v[13]), bf2(v[14], v[15]));
 }
 
-template <int KIND>
+// 2^(3-e) and its inverse for e the exponent of max |dE/dT| (bits of a non-negative float); 1, 1 when
+// there is nothing to scale.
+__device__ __forceinline__ void grad_scale(const unsigned *bits, float &s, float &inv)
+{
+    s = inv = 1.f;
+    if (bits == nullptr) return;
+    const unsigned b = *bits;
+    const int e = (int)((b >> 23) & 0xffu) - 127 - 3;
+    if (b != 0u && e > -120 && e < 120) {
+        s = __int_as_float((127 - e) << 23);
+        inv = __int_as_float((127 + e) << 23);
+    }
+}
+
+// 16 floats as e4m3 (saturating) at p (16-byte aligned).
+__device__ __forceinline__ void st16q(unsigned char *p, const float *v)
+{
+    uint32_t q[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __nv_fp8x2_storage_t a = __nv_cvt_float2_to_fp8x2(make_float2(v[4 * i], v[4 * i + 1]), __NV_SATFINITE, __NV_E4M3);
+        const __nv_fp8x2_storage_t b = __nv_cvt_float2_to_fp8x2(make_float2(v[4 * i + 2], v[4 * i + 3]), __NV_SATFINITE, __NV_E4M3);
+        q[i] = (uint32_t)a | ((uint32_t)b << 16);
+    }
+    *reinterpret_cast<uint4 *>(p) = make_uint4(q[0], q[1], q[2], q[3]);
+}
+
+__device__ __forceinline__ uint16_t q2(float a, float b)
+{
+    return (uint16_t)__nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+}
+
+template <int KIND, int Q>
 __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -139,8 +184,14 @@ __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
     // A [rows][K] and B [N][K] of the product (row-major bf16), K and N of the layer
     const int K = KIND == WK_FWD2 ? w.E0 : KIND == WK_FWD3 ? w.E1 : KIND == WK_BWD3 ? w.E2 : w.E1;
     const int N = KIND == WK_FWD2 ? w.E1 : KIND == WK_FWD3 ? w.E2 : KIND == WK_BWD3 ? w.E1 : w.E0;
-    const __nv_bfloat16 *A = KIND == WK_FWD2 ? w.Y1 : KIND == WK_FWD3 ? w.Y2 : KIND == WK_BWD3 ? w.DZ3 : w.DZ2;
-    const uint32_t oB = KIND == WK_FWD2 ? w.oW2T : KIND == WK_FWD3 ? w.oW3T : KIND == WK_BWD3 ? w.oW3 : w.oW2;
+    constexpr int ES = Q ? 1 : 2;          // bytes per operand element
+    constexpr int SEG = kWK * ES / 16;     // 16-byte segments per row of a K chunk
+    const unsigned char *A = Q ? (KIND == WK_FWD2 ? w.Y1q : KIND == WK_FWD3 ? w.Y2q : KIND == WK_BWD3 ? w.DZ3q : w.DZ2q)
+                               : reinterpret_cast<const unsigned char *>(
+                                     KIND == WK_FWD2 ? w.Y1 : KIND == WK_FWD3 ? w.Y2 : KIND == WK_BWD3 ? w.DZ3 : w.DZ2);
+    const uint32_t oB = Q ? (KIND == WK_FWD2 ? w.qW2T : KIND == WK_FWD3 ? w.qW3T : KIND == WK_BWD3 ? w.qW3 : w.qW2)
+                          : (KIND == WK_FWD2 ? w.oW2T : KIND == WK_FWD3 ? w.oW3T : KIND == WK_BWD3 ? w.oW3 : w.oW2);
+    const uint32_t oS = KIND == WK_FWD2 ? w.qS2T : KIND == WK_FWD3 ? w.qS3T : KIND == WK_BWD3 ? w.qS3 : w.qS2;
     if (tid == 0) {
         for (int q = 0; q < kWStages; ++q) tc::mbar_init(&bar_m[q], 1);
         tc::mbar_init(&bar_c, 1);
@@ -166,22 +217,26 @@ __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
         const int nb = (int)(u - tile * nblk);
         const int nbc = N - nb * kWNB < kWNB ? N - nb * kWNB : kWNB;
         const int net = w.chunks[tile * 4].w;
-        const __nv_bfloat16 *Ab = A + (tile * 128) * (int64_t)K;
-        const __nv_bfloat16 *Bb =
-            reinterpret_cast<const __nv_bfloat16 *>(w.wimg + (size_t)net * w.img + oB) + (int64_t)nb * kWNB * K;
-        // one K chunk of A (this thread's row) and of B (rows tid, tid + 128) into stage s
+        const int64_t rowb = (int64_t)K * ES;   // bytes per row of A and B
+        const unsigned char *Ab = A + (tile * 128) * rowb;
+        const unsigned char *Bb = (Q ? w.wq + (size_t)net * w.qimg : w.wimg + (size_t)net * w.img) + oB +
+                                  (int64_t)nb * kWNB * rowb;
+        // one K chunk of A (this thread's row) and of B (rows tid, tid + 128) into stage s: 16-byte
+        // segments straight into the K-major core-matrix layout (8 rows x 16 bytes)
         auto load = [&](int kc, int s) {
             unsigned char *sa = smem + s * kWStage, *sb = sa + kWA;
-            const __nv_bfloat16 *ar = Ab + (int64_t)tid * K + kc * kWK;
+            const unsigned char *ar = Ab + tid * rowb + kc * kWK * ES;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) cp_async16(sa + tc::kmaj_off(tid, 8 * q, kWK), ar + 8 * q);
+            for (int q = 0; q < SEG; ++q) cp_async16(sa + tc::kmaj_off(tid, 8 * q, 8 * SEG), ar + 16 * q);
             for (int rb = tid; rb < nbc; rb += 128) {
-                const __nv_bfloat16 *br = Bb + (int64_t)rb * K + kc * kWK;
+                const unsigned char *br = Bb + rb * rowb + kc * kWK * ES;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) cp_async16(sb + tc::kmaj_off(rb, 8 * q, kWK), br + 8 * q);
+                for (int q = 0; q < SEG; ++q) cp_async16(sb + tc::kmaj_off(rb, 8 * q, 8 * SEG), br + 16 * q);
             }
         };
-        const uint32_t id = tc::idesc_f16(128, nbc, 1);
+        // kind::f16 bf16 x bf16, or kind::f8f6f4 e4m3 x e4m3 (format codes 0), FP32 accumulator
+        const uint32_t id = Q ? ((1u << 4) | ((uint32_t)(nbc >> 3) << 17) | ((uint32_t)(128 >> 4) << 24))
+                              : tc::idesc_f16(128, nbc, 1);
 #pragma unroll
         for (int p = 0; p < kWStages - 1; ++p) {
             if (p < nk) load(p, p);
@@ -196,14 +251,21 @@ __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
             if (tid == 0) {
                 tc::fence_after_sync();
                 const uint32_t sa = tc::smem_u32(smem + s * kWStage), sb = sa + kWA;
-                for (int ks = 0; ks < kWK / 16; ++ks) {
-                    const uint64_t ad = tc::smem_desc(sa + ks * 256, 128, (kWK / 8) * 128);
-                    const uint64_t bd = tc::smem_desc(sb + ks * 256, 128, (kWK / 8) * 128);
+                // one MMA step covers 32 bytes of K (16 bf16 or 32 e4m3): two core matrices
+                for (int ks = 0; ks < SEG / 2; ++ks) {
+                    const uint64_t ad = tc::smem_desc(sa + ks * 256, 128, SEG * 128);
+                    const uint64_t bd = tc::smem_desc(sb + ks * 256, 128, SEG * 128);
                     const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-                        "l"(ad), "l"(bd), "r"(id), "r"(acc));
+                    if (Q)
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                            "l"(ad), "l"(bd), "r"(id), "r"(acc));
+                    else
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                            "l"(ad), "l"(bd), "r"(id), "r"(acc));
                 }
                 tc::mma_commit(&bar_m[s]);
             }
@@ -229,12 +291,23 @@ __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
         const int64_t gr = tile * 128 + tid;
         const float *vec = reinterpret_cast<const float *>(w.wimg + (size_t)net * w.img + w.oVec);
         const float *W1 = vec, *b1 = vec + w.E0, *b2 = vec + 2 * w.E0, *b3 = b2 + w.E1;
+        // FP8: the accumulator of column n carries the weight row's scale s_n; inv_s[n] = 1 / s_n
+        const float *inv_s = Q ? reinterpret_cast<const float *>(w.wq + (size_t)net * w.qimg + oS) + nb * kWNB : nullptr;
+        auto acc16 = [&](int c0, float *z) {
+            tc::tmem_ld16(taddr + c0, z);
+            tc::tmem_ld_wait();
+            if (Q) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) z[i] *= inv_s[c0 + i];
+            }
+        };
+        float gs = 1.f, gi = 1.f;   // FP8: the backward scaling of dE/dT (DZ3, DY2, DZ2 carry it)
+        if (Q) grad_scale(w.gbits, gs, gi);
         if constexpr (KIND == WK_FWD2) {
             for (int c0 = 0; c0 < nbc; c0 += 16) {
                 const int k0 = nb * kWNB + c0;
                 float z[16], y1[16], t[16], y[16];
-                tc::tmem_ld16(taddr + c0, z);
-                tc::tmem_ld_wait();
+                acc16(c0, z);
                 ld16(w.Y1 + gr * w.E0 + (k0 % w.E0), y1);   // skip: y2 = (y1, y1) + t2
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
@@ -243,6 +316,7 @@ __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
                 }
                 st16(w.T2 + gr * w.E1 + k0, t);
                 st16(w.Y2 + gr * w.E1 + k0, y);
+                if (Q) st16q(w.Y2q + gr * w.E1 + k0, y);
             }
         } else if constexpr (KIND == WK_FWD3) {
             unsigned char *GT = smem + kWStages * kWStage, *RT = GT + kWGT;
@@ -257,8 +331,7 @@ __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
             for (int c0 = 0; c0 < nbc; c0 += 16) {
                 const int m0 = nb * kWNB + c0;
                 float z[16], y2[16], t[16], g[16];
-                tc::tmem_ld16(taddr + c0, z);
-                tc::tmem_ld_wait();
+                acc16(c0, z);
                 ld16(w.Y2 + gr * w.E1 + (m0 % w.E1), y2);   // skip: G = (y2, y2) + t3
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
@@ -309,8 +382,7 @@ __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
             for (int c0 = 0; c0 < nbc; c0 += 16) {
                 const int k0 = nb * kWNB + c0;
                 float z[16], t2[16], dz[16];
-                tc::tmem_ld16(taddr + c0, z);
-                tc::tmem_ld_wait();
+                acc16(c0, z);
                 ld16(w.T2 + gr * w.E1 + k0, t2);
                 float dy[16];
 #pragma unroll
@@ -322,10 +394,11 @@ __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
                         sk = a.x * R[0] + a.y * R[1] + a.z * R[2] + a.w * R[3] + b.x * R[0] + b.y * R[1] +
                              b.z * R[2] + b.w * R[3];
                     }
-                    dy[i] = z[i] + sk;
+                    dy[i] = z[i] + sk * gs;
                     dz[i] = dy[i] * (1.f - t2[i] * t2[i]);
                 }
-                st16(w.DZ2 + gr * w.E1 + k0, dz);
+                if (Q) st16q(w.DZ2q + gr * w.E1 + k0, dz);
+                else st16(w.DZ2 + gr * w.E1 + k0, dz);
                 float4 *d4 = reinterpret_cast<float4 *>(w.DY2 + gr * w.E1 + k0);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) d4[i] = make_float4(dy[4 * i], dy[4 * i + 1], dy[4 * i + 2], dy[4 * i + 3]);
@@ -336,8 +409,7 @@ __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
             for (int c0 = 0; c0 < nbc; c0 += 16) {
                 const int k0 = nb * kWNB + c0;
                 float z[16];
-                tc::tmem_ld16(taddr + c0, z);
-                tc::tmem_ld_wait();
+                acc16(c0, z);
                 const float4 *a4 = reinterpret_cast<const float4 *>(w.DY2 + gr * w.E1 + k0);
                 const float4 *b4 = reinterpret_cast<const float4 *>(w.DY2 + gr * w.E1 + k0 + w.E0);
 #pragma unroll
@@ -365,6 +437,7 @@ __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
 }
 
 // Layer 1 (1 -> E0, plain since E0 >= 64): one warp per row, lanes over the outputs.
+template <int Q>
 __global__ void k_wide_l1(ModelDev md, WideArgs w, int64_t max_rows)
 {
     const int64_t gr = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -377,11 +450,13 @@ __global__ void k_wide_l1(ModelDev md, WideArgs w, int64_t max_rows)
         const float t0 = tc::tanh_fast(fmaf(s, vec[k], vec[w.E0 + k]));
         const float t1 = tc::tanh_fast(fmaf(s, vec[k + 1], vec[w.E0 + k + 1]));
         *reinterpret_cast<uint32_t *>(w.Y1 + gr * w.E0 + k) = bf2(t0, t1);
+        if (Q) *reinterpret_cast<uint16_t *>(w.Y1q + gr * w.E0 + k) = q2(t0, t1);
     }
 }
 
 // Start of the backward pass per row (one warp, lanes over the channels m):
 //   dG = dT R, G = (y2, y2) + t3, dR = dT^T G (warp sum), dz3 = dG (1 - t3^2) -> DZ3.
+template <int Q>
 __global__ void k_wide_b1(ModelDev md, WideArgs w, int64_t max_rows)
 {
     const int64_t gr = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -392,6 +467,8 @@ __global__ void k_wide_b1(ModelDev md, WideArgs w, int64_t max_rows)
     const float s = row.valid ? row.a.x : 0.f;
     const float R[4] = {s, s * row.a.y, s * row.a.z, s * row.a.w};
     const float4 *dTa = reinterpret_cast<const float4 *>(w.dT + (int64_t)(row.atom >= 0 ? row.atom : 0) * w.E2 * 4);
+    float gs = 1.f, gi = 1.f;
+    if (Q) grad_scale(w.gbits, gs, gi);
     for (int m = 2 * lane; m < w.E2; m += 64) {
         const float2 t3 = unbf2(*reinterpret_cast<const uint32_t *>(w.T3 + gr * w.E2 + m));
         const float2 y2 = unbf2(*reinterpret_cast<const uint32_t *>(w.Y2 + gr * w.E1 + (m % w.E1)));
@@ -407,20 +484,24 @@ __global__ void k_wide_b1(ModelDev md, WideArgs w, int64_t max_rows)
                 dR[2] = fmaf(d.z, G, dR[2]);
                 dR[3] = fmaf(d.w, G, dR[3]);
                 const float dG = d.x * R[0] + d.y * R[1] + d.z * R[2] + d.w * R[3];
-                dz[e] = dG * (1.f - tt[e] * tt[e]);
+                dz[e] = dG * (1.f - tt[e] * tt[e]) * gs;
             }
         }
-        *reinterpret_cast<uint32_t *>(w.DZ3 + gr * w.E2 + m) = bf2(dz[0], dz[1]);
+        if (Q) *reinterpret_cast<uint16_t *>(w.DZ3q + gr * w.E2 + m) = q2(dz[0], dz[1]);
+        else *reinterpret_cast<uint32_t *>(w.DZ3 + gr * w.E2 + m) = bf2(dz[0], dz[1]);
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
+    for (int c = 0; c < 4; ++c) {
         for (int o = 16; o > 0; o >>= 1) dR[c] += __shfl_xor_sync(0xffffffffu, dR[c], o);
+        dR[c] *= gs;
+    }
     if (lane == 0) *reinterpret_cast<float4 *>(w.DR + 4 * gr) = make_float4(dR[0], dR[1], dR[2], dR[3]);
 }
 
 // g_ij = (dR/dr_ij)^T dE/dR from ds and dR (R = (s, s u), u = d/r):
 //   g = u (dR0 s' + (s' - s/r) u.dR') + (s/r) dR'; F_j -= g, F_i += g, W_i -= d (x) g (FP64 atomics);
 // one block per tile, a warp per chunk (one atom).
+template <int Q>
 __global__ void __launch_bounds__(128) k_wide_force(ModelDev md, WideArgs w)
 {
     const int64_t tile = blockIdx.x;
@@ -439,8 +520,10 @@ __global__ void __launch_bounds__(128) k_wide_force(ModelDev md, WideArgs w)
         const float ud = u[0] * dr.y + u[1] * dr.z + u[2] * dr.w;
         const float cu = fmaf(dsdr - sr, ud, dR0 * dsdr);
         const float dRp[3] = {dr.y, dr.z, dr.w};
+        float gs = 1.f, gi = 1.f;
+        if (Q) grad_scale(w.gbits, gs, gi);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) gv[k] = fmaf(cu, u[k], sr * dRp[k]);
+        for (int k = 0; k < 3; ++k) gv[k] = fmaf(cu, u[k], sr * dRp[k]) * gi;
 #pragma unroll
         for (int k = 0; k < 3; ++k) atomicAdd(&w.force[3 * (int64_t)row.j + k], -(double)gv[k]);
 #pragma unroll
@@ -469,9 +552,25 @@ __global__ void __launch_bounds__(128) k_wide_force(ModelDev md, WideArgs w)
     }
 }
 
+// *out = bits of max |x| over x [n] (non-negative floats order like their bits); *out zeroed first.
+__global__ void k_wide_absmax(int64_t n, const float *__restrict__ x, unsigned *out)
+{
+    unsigned m = 0u;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned b = __float_as_uint(fabsf(x[i]));
+        m = b > m ? b : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned v = __shfl_xor_sync(0xffffffffu, m, o);
+        m = v > m ? v : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
 struct WideLayout {
     int E0, E1, E2;
     uint32_t oW2T, oW3T, oW3, oW2, oVec, img;
+    uint32_t qW2T, qW3T, qW3, qW2, qS2T, qS3T, qS3, qS2, qimg;   // FP8 image: e4m3 matrices, then 1 / row scale
 };
 
 WideLayout wide_layout(const ModelDev &md)
@@ -486,7 +585,33 @@ WideLayout wide_layout(const ModelDev &md)
     L.oW2 = L.oW3 + (uint32_t)L.E1 * L.E2 * 2;
     L.oVec = L.oW2 + (uint32_t)L.E0 * L.E1 * 2;
     L.img = L.oVec + (uint32_t)(2 * L.E0 + L.E1 + L.E2) * 4;
+    L.qW2T = 0;
+    L.qW3T = L.qW2T + (uint32_t)L.E1 * L.E0;
+    L.qW3 = L.qW3T + (uint32_t)L.E2 * L.E1;
+    L.qW2 = L.qW3 + (uint32_t)L.E1 * L.E2;
+    L.qS2T = L.qW2 + (uint32_t)L.E0 * L.E1;
+    L.qS3T = L.qS2T + (uint32_t)L.E1 * 4;
+    L.qS3 = L.qS3T + (uint32_t)L.E2 * 4;
+    L.qS2 = L.qS3 + (uint32_t)L.E1 * 4;
+    L.qimg = L.qS2 + (uint32_t)L.E0 * 4;
     return L;
+}
+
+// rows x cols row-major FP64 matrix M (element (r, c) = M[r * rs + c * cs]) as e4m3 rows scaled by a
+// power of two s_r (largest |entry| of the row times s_r in (224, 448]); inv[r] = 1 / s_r.
+void quant_rows(const double *M, int rows, int cols, int64_t rs, int64_t cs, unsigned char *q, float *inv)
+{
+    for (int r = 0; r < rows; ++r) {
+        double mx = 0.0;
+        for (int c = 0; c < cols; ++c) mx = fmax(mx, fabs(M[r * rs + c * cs]));
+        const int e = mx > 0.0 ? (int)floor(log2(448.0 / mx)) : 0;
+        const double s = ldexp(1.0, e);
+        inv[r] = (float)ldexp(1.0, -e);
+        for (int c = 0; c < cols; ++c) {
+            const __nv_fp8_e4m3 v((float)(M[r * rs + c * cs] * s));
+            q[(size_t)r * cols + c] = (unsigned char)v.__x;
+        }
+    }
 }
 
 }  // namespace
@@ -538,12 +663,28 @@ dp_status pack_wide_weights(dp_model *m)
     }
     if (!m->d_wide) DP_CUDA(cudaMalloc((void **)&m->d_wide, img.size()));
     DP_CUDA(cudaMemcpyAsync(m->d_wide, img.data(), img.size(), cudaMemcpyHostToDevice, m->stream));
+    // the e4m3 image of the same matrices (rows of W2^T, W3^T, W3, W2)
+    std::vector<unsigned char> qi((size_t)nn * L.qimg, 0);
+    for (int q = 0; q < nn; ++q) {
+        const double *p = m->h_params.data() + md.emb_base + q * md.emb.size;
+        unsigned char *o = qi.data() + (size_t)q * L.qimg;
+        const double *W2 = p + md.emb.W[1], *W3 = p + md.emb.W[2];
+        quant_rows(W2, L.E1, L.E0, 1, L.E1, o + L.qW2T, reinterpret_cast<float *>(o + L.qS2T));   // W2^T
+        quant_rows(W3, L.E2, L.E1, 1, L.E2, o + L.qW3T, reinterpret_cast<float *>(o + L.qS3T));   // W3^T
+        quant_rows(W3, L.E1, L.E2, L.E2, 1, o + L.qW3, reinterpret_cast<float *>(o + L.qS3));     // W3
+        quant_rows(W2, L.E0, L.E1, L.E1, 1, o + L.qW2, reinterpret_cast<float *>(o + L.qS2));     // W2
+    }
+    if (!m->d_wide_q) DP_CUDA(cudaMalloc((void **)&m->d_wide_q, qi.size()));
+    DP_CUDA(cudaMemcpyAsync(m->d_wide_q, qi.data(), qi.size(), cudaMemcpyHostToDevice, m->stream));
     DP_CUDA(cudaStreamSynchronize(m->stream));
     return DP_OK;
 }
 
-dp_status compute_wide(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
-                       double *d_virial, double *d_atom_virial, cudaStream_t st)
+namespace {
+
+template <int Q>
+dp_status run_wide(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
+                   double *d_virial, double *d_atom_virial, cudaStream_t st)
 {
     const ModelDev &md = m->dev;
     const WideLayout L = wide_layout(md);
@@ -562,12 +703,18 @@ dp_status compute_wide(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
     sz(sizeof(float) * 4 * md.m1 * n);
     sz(sizeof(int4) * max_chunks);
     sz(sizeof(int) * 4);
+    sz(sizeof(unsigned) * 4);
     sz(chunks_batch_scratch(md, n));
     sz(2 * (size_t)max_rows * L.E0);        // Y1
     sz(2 * (size_t)max_rows * L.E1 * 3);    // T2, Y2, DZ2
     sz(2 * (size_t)max_rows * L.E2 * 2);    // T3, DZ3
     sz(4 * (size_t)max_rows * L.E1);        // DY2
     sz(4 * (size_t)max_rows * 5);           // DR, DS
+    if (Q) {
+        sz((size_t)max_rows * L.E0);        // e4m3 Y1, Y2, DZ3, DZ2
+        sz((size_t)max_rows * L.E1 * 2);
+        sz((size_t)max_rows * L.E2);
+    }
     DP_TRY(ensure_workspace(m, need));
     char *wp = m->ws;
     auto carve = [&](size_t bytes) {
@@ -575,7 +722,7 @@ dp_status compute_wide(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
         wp += (bytes + 255) & ~(size_t)255;
         return p;
     };
-    WideArgs a;
+    WideArgs a{};
     a.E0 = L.E0;
     a.E1 = L.E1;
     a.E2 = L.E2;
@@ -585,11 +732,23 @@ dp_status compute_wide(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
     a.oW3 = L.oW3;
     a.oW2 = L.oW2;
     a.oVec = L.oVec;
+    a.qimg = L.qimg;
+    a.qW2T = L.qW2T;
+    a.qW3T = L.qW3T;
+    a.qW3 = L.qW3;
+    a.qW2 = L.qW2;
+    a.qS2T = L.qS2T;
+    a.qS3T = L.qS3T;
+    a.qS3 = L.qS3;
+    a.qS2 = L.qS2;
+    a.wq = m->d_wide_q;
     a.T = (float *)carve(sizeof(float) * 4 * md.m1 * n);
     float *dT = (float *)carve(sizeof(float) * 4 * md.m1 * n);
     a.dT = dT;
     int4 *chunks = (int4 *)carve(sizeof(int4) * max_chunks);
     int *cnt = (int *)carve(sizeof(int) * 4);
+    unsigned *gbits = (unsigned *)carve(sizeof(unsigned) * 4);
+    a.gbits = Q ? gbits : nullptr;
     char *scratch = carve(chunks_batch_scratch(md, n));
     a.Y1 = (__nv_bfloat16 *)carve(2 * (size_t)max_rows * L.E0);
     a.T2 = (__nv_bfloat16 *)carve(2 * (size_t)max_rows * L.E1);
@@ -600,6 +759,12 @@ dp_status compute_wide(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
     a.DY2 = (float *)carve(4 * (size_t)max_rows * L.E1);
     a.DR = (float *)carve(4 * (size_t)max_rows * 4);
     a.DS = (float *)carve(4 * (size_t)max_rows);
+    if (Q) {
+        a.Y1q = (unsigned char *)carve((size_t)max_rows * L.E0);
+        a.Y2q = (unsigned char *)carve((size_t)max_rows * L.E1);
+        a.DZ2q = (unsigned char *)carve((size_t)max_rows * L.E1);
+        a.DZ3q = (unsigned char *)carve((size_t)max_rows * L.E2);
+    }
     a.chunks = chunks;
     a.ntiles = cnt;
     a.nnei = nl->d_nnei;
@@ -620,29 +785,44 @@ dp_status compute_wide(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
         ProfScope ps(m->prof, PG_CHUNKS, 3, st);
         DP_TRY(build_chunks_batch(m, nl, 0, n, chunks, nullptr, cnt, scratch, st));
     }
-    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_FWD2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
-    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_FWD3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
-    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_BWD3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
-    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_BWD2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
+    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_FWD2, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
+    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_FWD3, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
+    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_BWD3, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
+    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_BWD2, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
     const unsigned rb = (unsigned)((max_rows * 32 + 255) / 256);
     {
         ProfScope ps(m->prof, PG_EMBED_FWD, 3, st);
-        k_wide_l1<<<rb, 256, 0, st>>>(md, a, max_rows);
-        k_wide_gemm<WK_FWD2><<<nsm, 128, kWSmem, st>>>(md, a);
-        k_wide_gemm<WK_FWD3><<<nsm, 128, kWSmem, st>>>(md, a);
+        k_wide_l1<Q><<<rb, 256, 0, st>>>(md, a, max_rows);
+        k_wide_gemm<WK_FWD2, Q><<<nsm, 128, kWSmem, st>>>(md, a);
+        k_wide_gemm<WK_FWD3, Q><<<nsm, 128, kWSmem, st>>>(md, a);
     }
     DP_CUDA(cudaGetLastError());
     DP_TRY(fit_mix16_bf16(m, nl, a.T, d_atom_energy, dT, st));
+    if (Q) {   // the scale of dE/dT for the e4m3 backward operands
+        ProfScope ps(m->prof, PG_DESC, 1, st);
+        DP_CUDA(cudaMemsetAsync(gbits, 0, sizeof(unsigned), st));
+        k_wide_absmax<<<(unsigned)(2 * nsm), 256, 0, st>>>((int64_t)4 * md.m1 * n, dT, gbits);
+        DP_CUDA(cudaGetLastError());
+    }
     {
         ProfScope ps(m->prof, PG_EMBED_BWD, 4, st);
-        k_wide_b1<<<rb, 256, 0, st>>>(md, a, max_rows);
-        k_wide_gemm<WK_BWD3><<<nsm, 128, kWSmem, st>>>(md, a);
-        k_wide_gemm<WK_BWD2><<<nsm, 128, kWSmem, st>>>(md, a);
-        k_wide_force<<<(unsigned)(max_chunks / 4 + 1), 128, 0, st>>>(md, a);
+        k_wide_b1<Q><<<rb, 256, 0, st>>>(md, a, max_rows);
+        k_wide_gemm<WK_BWD3, Q><<<nsm, 128, kWSmem, st>>>(md, a);
+        k_wide_gemm<WK_BWD2, Q><<<nsm, 128, kWSmem, st>>>(md, a);
+        k_wide_force<Q><<<(unsigned)(max_chunks / 4 + 1), 128, 0, st>>>(md, a);
     }
     DP_CUDA(cudaGetLastError());
     ProfScope ps(m->prof, PG_REDUCE, 1, st);
     return reduce_energy_virial(d_atom_energy, d_atom_virial, centers_of(nl), d_energy, d_virial, m->d_red, st);
+}
+
+}  // namespace
+
+dp_status compute_wide(dp_model *m, dp_nlist *nl, int fp8, double *d_energy, double *d_atom_energy, double *d_force,
+                       double *d_virial, double *d_atom_virial, cudaStream_t st)
+{
+    return fp8 ? run_wide<1>(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st)
+               : run_wide<0>(m, nl, d_energy, d_atom_energy, d_force, d_virial, d_atom_virial, st);
 }
 
 }  // namespace dp

@@ -56,6 +56,29 @@ def test_wide_nets_match_oracle(dp, orc, w):
         m.close()
 
 
+@pytest.mark.parametrize("w", [64, 256])
+def test_wide_nets_fp8_against_oracle(dp, orc, w):
+    """The same nets with e4m3 operands in the layer-2/3 products (DP_MIX_FP8).  e4m3 keeps 3 mantissa
+    bits (u8 = 2^-4); the errors are stated in units of u8 and bounded at the level of one rounding of
+    the operands (forces within 2 u8 of the RMS force, energy within u8 / 4 of sum |E_i|); the
+    printout records them against bf16's."""
+    u8 = 2.0 ** -4
+    name, cfg, coord, typ, box = _systems(w)[0]
+    params = dpsynth.model_params(cfg, 4)
+    m = dp.Model(cfg, 1, params=params)
+    nl = dp.NeighborList(m, coord, typ, box)
+    E, Ei, F, W = nl.compute(coord, box, "fp8")
+    Eb, _, Fb, _ = nl.compute(coord, box, "bf16")
+    Er, Eir, Fr, Wr = orc.Model(cfg, params).compute(coord, typ, box)
+    f8 = np.sqrt(((F - Fr) ** 2).sum(1).mean()) / rms(Fr)
+    fb = np.sqrt(((Fb - Fr) ** 2).sum(1).mean()) / rms(Fr)
+    e8 = abs(E - Er) / np.abs(Eir).sum()
+    print(name, cfg.embed, "fp8 force", f8, "bf16 force", fb, "fp8 energy", e8)
+    assert np.isfinite(F).all() and np.isfinite(E)
+    assert f8 < 2 * u8 and e8 < u8 / 4
+    assert np.abs(W - Wr).max() / np.abs(Wr).max() < 2 * u8
+
+
 def test_wide_nets_other_precisions_are_rejected(dp):
     cfg = dpsynth.ModelConfig(ntypes=1, rcut=4.0, rcut_smth=1.0, sel=(32,), embed=(64, 128, 256))
     coord, typ, box = dpsynth.copper_fcc(3, ncell=3)
@@ -64,6 +87,13 @@ def test_wide_nets_other_precisions_are_rejected(dp):
     for prec in ("fp64", "mix32", "fp16", "bf16x3"):
         with pytest.raises(dp.DPError, match="DP_ERR_UNSUPPORTED"):
             nl.compute(coord, box, prec)
+    # and FP8 is for the wide nets only
+    cfg2 = dpsynth.copper_config()
+    c2, t2, b2 = dpsynth.copper_fcc(1, ncell=5)
+    m2 = dp.Model(cfg2, 1)
+    nl2 = dp.NeighborList(m2, c2, t2, b2)
+    with pytest.raises(dp.DPError, match="DP_ERR_UNSUPPORTED"):
+        nl2.compute(c2, b2, "fp8")
 
 
 def test_wide_md_runs(dp):
