@@ -746,7 +746,7 @@ def run_sweep(args, rank, world):
     n = len(typ)
     peak, src = tensor_peak()
     points = []
-    for emb, prec in [(e, "bf16") for e in SWEEP] + [(e, "fp8") for e in SWEEP if e[0] >= 64]:
+    for emb, prec in [(e, "bf16") for e in SWEEP] + [(e, "fp8") for e in SWEEP if e[0] >= 128]:
         cfg = dpsynth.ModelConfig(ntypes=1, rcut=8.0, rcut_smth=2.0, sel=(512,), embed=emb)
         model = dp.Model(cfg, seed=1)
         stream = torch.cuda.Stream(device=dev)

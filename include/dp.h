@@ -68,7 +68,7 @@ typedef enum {
  *                taken as hi hi + hi lo + lo hi (three MMAs, FP32
  *                accumulation), tanh in FP32 (tanhf); descriptor and
  *                fitting net in FP32 on the CUDA cores (as DP_MIX32).
- *   DP_MIX_FP8   the wide embedding nets (w, 2w, 4w), w = 64 .. 512, with
+ *   DP_MIX_FP8   the wide embedding nets (w, 2w, 4w), w = 128 .. 512, with
  *                the products of layers 2 and 3 and their input gradients
  *                on e4m3 operands (tcgen05 kind::f8f6f4, FP32 accumulation;
  *                weights quantised with a power-of-two scale per row, the

@@ -44,15 +44,34 @@ namespace dp {
 namespace {
 
 constexpr long kWaitW = 1L << 25;   // mbarrier polls (~1 s) before a kernel gives up
-constexpr int kWK = 64;             // K chunk
+constexpr int kWChunkB = 128;       // bytes of K per row in one chunk (64 bf16 or 128 e4m3)
 constexpr int kWNB = 256;           // columns per unit
-constexpr int kWStages = 3;
-constexpr uint32_t kWA = 128 * kWK * 2, kWB = kWNB * kWK * 2, kWStage = kWA + kWB;
+constexpr uint32_t kWA = 128 * kWChunkB, kWB = kWNB * kWChunkB, kWStage = kWA + kWB;
 constexpr uint32_t kWGT = kWNB * 128 * 2, kWRT = 16 * 128 * 2;   // contraction operands (FWD3)
-constexpr uint32_t kWSmem = kWStages * kWStage + kWGT + kWRT;
-static_assert(kWSmem <= 227 * 1024, "shared memory");
 
 enum WideKind { WK_FWD2 = 0, WK_FWD3 = 1, WK_BWD3 = 2, WK_BWD2 = 3 };
+
+// Stages of the copy / MMA ring and shared memory of a GEMM kind (FWD3 also holds the contraction's
+// G^T and R^T).
+template <int KIND>
+constexpr int wide_stages() { return KIND == WK_FWD3 ? 3 : 4; }
+template <int KIND>
+constexpr uint32_t wide_smem() { return wide_stages<KIND>() * kWStage + (KIND == WK_FWD3 ? kWGT + kWRT : 0u); }
+static_assert(wide_smem<WK_FWD3>() <= 227 * 1024 && wide_smem<WK_FWD2>() <= 227 * 1024, "shared memory");
+
+// Byte offset of element (row, k) of a [rows][K] GEMM operand with es-byte elements stored pre-tiled:
+// blocks of rows_blk rows x 128 bytes of K, block (row / rows_blk, K chunk) at
+// ((row / rows_blk) nk + chunk) rows_blk 128, each block in the K-major core-matrix layout of the MMA
+// operands (8 rows x 16 bytes), so that one bulk copy moves a chunk of a tile.
+__host__ __device__ __forceinline__ size_t wtile_off(int64_t row, int rows_blk, int k, int K, int es)
+{
+    const int ke = kWChunkB / es, nk = K / ke;
+    const int64_t rb = row / rows_blk;
+    const int r = (int)(row - rb * rows_blk);
+    const int kc = k / ke, kb = (k - kc * ke) * es;
+    return ((size_t)rb * nk + kc) * (size_t)rows_blk * kWChunkB +
+           (size_t)((r >> 3) * 1024 + (kb >> 4) * 128 + (r & 7) * 16 + (kb & 15));
+}
 
 struct WideArgs {
     int E0, E1, E2;
@@ -108,13 +127,6 @@ __device__ __forceinline__ WRow wide_row(const ModelDev &md, const WideArgs &w, 
     return o;
 }
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ uint32_t bf2(float a, float b)
 {
@@ -123,10 +135,11 @@ __device__ __forceinline__ uint32_t bf2(float a, float b)
 }
 __device__ __forceinline__ float2 unbf2(uint32_t v) { return __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&v)); }
 
-// 16 bf16 values of a row-major bf16 array as floats.
-__device__ __forceinline__ void ld16(const __nv_bfloat16 *p, float *v)
+// 16 bf16 values as floats: 8 at p and 8 at p + step (step = 8: contiguous; 64: the next 16-byte
+// segment of a pre-tiled operand).
+__device__ __forceinline__ void ld16(const __nv_bfloat16 *p, float *v, int step = 8)
 {
-    const uint4 a = *reinterpret_cast<const uint4 *>(p), b = *reinterpret_cast<const uint4 *>(p + 8);
+    const uint4 a = *reinterpret_cast<const uint4 *>(p), b = *reinterpret_cast<const uint4 *>(p + step);
     const uint32_t q[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -135,11 +148,21 @@ __device__ __forceinline__ void ld16(const __nv_bfloat16 *p, float *v)
         v[2 * i + 1] = f.y;
     }
 }
-__device__ __forceinline__ void st16(__nv_bfloat16 *p, const float *v)
+__device__ __forceinline__ void st16(__nv_bfloat16 *p, const float *v, int step = 8)
 {
     *reinterpret_cast<uint4 *>(p) = make_uint4(bf2(v[0], v[1]), bf2(v[2], v[3]), bf2(v[4], v[5]), bf2(v[6], v[7]));
-    *reinterpret_cast<uint4 *>(p + 8) =
+    *reinterpret_cast<uint4 *>(p + step) =
         make_uint4(bf2(v[8], v[9]), bf2(v[10], v[11]), bf2(v[12], v[13]), bf2(v[14], v[15]));
+}
+
+// Element (row, k) of a pre-tiled activation (128-row blocks) of width K.
+__device__ __forceinline__ __nv_bfloat16 *tb16(__nv_bfloat16 *base, int64_t row, int k, int K)
+{
+    return reinterpret_cast<__nv_bfloat16 *>(reinterpret_cast<unsigned char *>(base) + wtile_off(row, 128, k, K, 2));
+}
+__device__ __forceinline__ unsigned char *tq8(unsigned char *base, int64_t row, int k, int K)
+{
+    return base + wtile_off(row, 128, k, K, 1);
 }
 
 // 2^(3-e) and its inverse for e the exponent of max |dE/dT| (bits of a non-negative float); 1, 1 when
@@ -177,15 +200,17 @@ __device__ __forceinline__ uint16_t q2(float a, float b)
 template <int KIND, int Q>
 __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
 {
+    constexpr int S = wide_stages<KIND>();
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar_m[kWStages], bar_c;
+    __shared__ __align__(8) uint64_t bar_full[S], bar_empty[S], bar_done, bar_c;
     __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // A [rows][K] and B [N][K] of the product (row-major bf16), K and N of the layer
+    // A [rows][K] (the layer input, pre-tiled in 128-row blocks) and B [N][K] (the net's weight matrix,
+    // pre-tiled in blocks of min(N, 256) rows)
     const int K = KIND == WK_FWD2 ? w.E0 : KIND == WK_FWD3 ? w.E1 : KIND == WK_BWD3 ? w.E2 : w.E1;
     const int N = KIND == WK_FWD2 ? w.E1 : KIND == WK_FWD3 ? w.E2 : KIND == WK_BWD3 ? w.E1 : w.E0;
     constexpr int ES = Q ? 1 : 2;          // bytes per operand element
-    constexpr int SEG = kWK * ES / 16;     // 16-byte segments per row of a K chunk
     const unsigned char *A = Q ? (KIND == WK_FWD2 ? w.Y1q : KIND == WK_FWD3 ? w.Y2q : KIND == WK_BWD3 ? w.DZ3q : w.DZ2q)
                                : reinterpret_cast<const unsigned char *>(
                                      KIND == WK_FWD2 ? w.Y1 : KIND == WK_FWD3 ? w.Y2 : KIND == WK_BWD3 ? w.DZ3 : w.DZ2);
@@ -193,9 +218,14 @@ __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
                           : (KIND == WK_FWD2 ? w.oW2T : KIND == WK_FWD3 ? w.oW3T : KIND == WK_BWD3 ? w.oW3 : w.oW2);
     const uint32_t oS = KIND == WK_FWD2 ? w.qS2T : KIND == WK_FWD3 ? w.qS3T : KIND == WK_BWD3 ? w.qS3 : w.qS2;
     if (tid == 0) {
-        for (int q = 0; q < kWStages; ++q) tc::mbar_init(&bar_m[q], 1);
+        for (int q = 0; q < S; ++q) {
+            tc::mbar_init(&bar_full[q], 1);
+            tc::mbar_init(&bar_empty[q], 1);
+        }
+        tc::mbar_init(&bar_done, 1);
         tc::mbar_init(&bar_c, 1);
         tc::mbar_init_fence();
+        s_fail = 0;
     }
     if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
     tc::fence_before_sync();
@@ -203,8 +233,16 @@ __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-    uint32_t ph_m[kWStages] = {0, 0, 0}, ph_c = 0;
-    const int nk = K / kWK, nblk = (N + kWNB - 1) / kWNB;
+    // copy / MMA ring state, kept by thread 0: phases, and which stages hold a copy or an MMA whose
+    // completion has not been waited for
+    uint32_t ph_f[S], ph_e[S], ph_d = 0, ph_c = 0;
+    bool loaded[S], busy[S];
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        ph_f[q] = ph_e[q] = 0;
+        loaded[q] = busy[q] = false;
+    }
+    const int nk = K * ES / kWChunkB, nbr = N < kWNB ? N : kWNB, nblk = N / nbr;
     const int64_t ntiles = *w.ntiles, units = ntiles * nblk;
     bool dead = false;
     auto wait_all = [&](uint64_t *bar, uint32_t &ph) {
@@ -212,50 +250,54 @@ __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
         ph ^= 1;
         return __syncthreads_and(ok) != 0;
     };
+    // kind::f16 bf16 x bf16, or kind::f8f6f4 e4m3 x e4m3 (format codes 0), FP32 accumulator
+    const uint32_t id = Q ? ((1u << 4) | ((uint32_t)(nbr >> 3) << 17) | ((uint32_t)(128 >> 4) << 24))
+                          : tc::idesc_f16(128, nbr, 1);
+    const uint32_t bbytes = (uint32_t)nbr * kWChunkB;
     for (int64_t u = blockIdx.x; u < units && !dead; u += gridDim.x) {
         const int64_t tile = u / nblk;
         const int nb = (int)(u - tile * nblk);
-        const int nbc = N - nb * kWNB < kWNB ? N - nb * kWNB : kWNB;
+        const int nbc = nbr;
         const int net = w.chunks[tile * 4].w;
-        const int64_t rowb = (int64_t)K * ES;   // bytes per row of A and B
-        const unsigned char *Ab = A + (tile * 128) * rowb;
+        const unsigned char *Ab = A + (size_t)tile * nk * kWA;
         const unsigned char *Bb = (Q ? w.wq + (size_t)net * w.qimg : w.wimg + (size_t)net * w.img) + oB +
-                                  (int64_t)nb * kWNB * rowb;
-        // one K chunk of A (this thread's row) and of B (rows tid, tid + 128) into stage s: 16-byte
-        // segments straight into the K-major core-matrix layout (8 rows x 16 bytes)
-        auto load = [&](int kc, int s) {
-            unsigned char *sa = smem + s * kWStage, *sb = sa + kWA;
-            const unsigned char *ar = Ab + tid * rowb + kc * kWK * ES;
-#pragma unroll
-            for (int q = 0; q < SEG; ++q) cp_async16(sa + tc::kmaj_off(tid, 8 * q, 8 * SEG), ar + 16 * q);
-            for (int rb = tid; rb < nbc; rb += 128) {
-                const unsigned char *br = Bb + rb * rowb + kc * kWK * ES;
-#pragma unroll
-                for (int q = 0; q < SEG; ++q) cp_async16(sb + tc::kmaj_off(rb, 8 * q, 8 * SEG), br + 16 * q);
+                                  (size_t)nb * nk * bbytes;
+        if (tid == 0) {
+            // producer and MMA issuer: chunk c's A and B blocks by two bulk copies into stage c % S;
+            // the copies run S - 1 chunks ahead of the MMAs
+            bool ok = true;
+            auto stage_free = [&](int q) {
+                if (busy[q]) {
+                    busy[q] = false;
+                    if (!tc::mbar_wait(&bar_empty[q], ph_e[q], kWaitW)) return false;
+                    ph_e[q] ^= 1;
+                }
+                return true;
+            };
+            auto issue = [&](int c) {
+                const int q = c % S;
+                unsigned char *sa = smem + q * kWStage;
+                tc::mbar_expect_tx(&bar_full[q], kWA + bbytes);
+                tc::bulk_g2s(sa, Ab + (size_t)c * kWA, kWA, &bar_full[q]);
+                tc::bulk_g2s(sa + kWA, Bb + (size_t)c * bbytes, bbytes, &bar_full[q]);
+                loaded[q] = true;
+            };
+            for (int c = 0; c < S - 1 && c < nk && ok; ++c) {
+                ok = stage_free(c % S);
+                if (ok) issue(c);
             }
-        };
-        // kind::f16 bf16 x bf16, or kind::f8f6f4 e4m3 x e4m3 (format codes 0), FP32 accumulator
-        const uint32_t id = Q ? ((1u << 4) | ((uint32_t)(nbc >> 3) << 17) | ((uint32_t)(128 >> 4) << 24))
-                              : tc::idesc_f16(128, nbc, 1);
-#pragma unroll
-        for (int p = 0; p < kWStages - 1; ++p) {
-            if (p < nk) load(p, p);
-            cp_commit();
-        }
-        for (int kc = 0; kc < nk; ++kc) {
-            const int s = kc % kWStages;
-            cp_wait<kWStages - 2>();          // chunk kc has landed (this thread's copies)
-            tc::fence_async_smem();           // ... and is visible to the tensor core
-            tc::fence_before_sync();
-            __syncthreads();
-            if (tid == 0) {
+            for (int c = 0; c < nk && ok; ++c) {
+                const int q = c % S;
+                loaded[q] = false;
+                if (!tc::mbar_wait(&bar_full[q], ph_f[q], kWaitW)) { ok = false; break; }
+                ph_f[q] ^= 1;
                 tc::fence_after_sync();
-                const uint32_t sa = tc::smem_u32(smem + s * kWStage), sb = sa + kWA;
+                const uint32_t sa = tc::smem_u32(smem + q * kWStage), sb = sa + kWA;
                 // one MMA step covers 32 bytes of K (16 bf16 or 32 e4m3): two core matrices
-                for (int ks = 0; ks < SEG / 2; ++ks) {
-                    const uint64_t ad = tc::smem_desc(sa + ks * 256, 128, SEG * 128);
-                    const uint64_t bd = tc::smem_desc(sb + ks * 256, 128, SEG * 128);
-                    const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+                for (int ks = 0; ks < kWChunkB / 32; ++ks) {
+                    const uint64_t ad = tc::smem_desc(sa + ks * 256, 128, 1024);
+                    const uint64_t bd = tc::smem_desc(sb + ks * 256, 128, 1024);
+                    const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
                     if (Q)
                         asm volatile(
                             "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
@@ -267,24 +309,21 @@ __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
                             "l"(ad), "l"(bd), "r"(id), "r"(acc));
                 }
-                tc::mma_commit(&bar_m[s]);
+                tc::mma_commit(&bar_empty[q]);
+                busy[q] = true;
+                const int cn = c + S - 1;   // its stage held chunk c - 1, whose MMAs were issued before
+                if (cn < nk) {
+                    if (!stage_free(cn % S)) { ok = false; break; }
+                    issue(cn);
+                }
             }
-            // the stage of chunk kc + kWStages - 1 was read by the MMAs of chunk kc - 1
-            const int kn = kc + kWStages - 1;
-            if (kn < nk) {
-                const int sn = kn % kWStages;
-                if (kc >= 1 && !wait_all(&bar_m[sn], ph_m[sn])) { dead = true; break; }
-                load(kn, sn);
-            }
-            cp_commit();
+            if (ok) tc::mma_commit(&bar_done);   // arrives once every MMA of the unit has completed
+            else s_fail = 1;
         }
-        if (dead) break;
-        // the MMAs not waited for yet: chunks max(0, nk - kWStages) .. nk - 1, in order
-        for (int kc = nk - kWStages > 0 ? nk - kWStages : 0; kc < nk; ++kc) {
-            const int s = kc % kWStages;
-            if (!wait_all(&bar_m[s], ph_m[s])) { dead = true; break; }
-        }
-        if (dead) break;
+        // every thread: the accumulator is complete (or thread 0 gave up: then no arrival comes)
+        const bool done_ok = tc::mbar_wait(&bar_done, ph_d, s_fail ? 1 : kWaitW);
+        ph_d ^= 1;
+        if (!__syncthreads_and(done_ok && !s_fail)) { dead = true; break; }
         tc::fence_after_sync();
         // ---------------------------------------------------------------- epilogues (thread = row)
         const WRow row = wide_row(md, w, tile, tid);
@@ -308,18 +347,18 @@ __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
                 const int k0 = nb * kWNB + c0;
                 float z[16], y1[16], t[16], y[16];
                 acc16(c0, z);
-                ld16(w.Y1 + gr * w.E0 + (k0 % w.E0), y1);   // skip: y2 = (y1, y1) + t2
+                ld16(tb16(w.Y1, gr, k0 % w.E0, w.E0), y1, 64);   // skip: y2 = (y1, y1) + t2
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     t[i] = tc::tanh_fast(z[i] + b2[k0 + i]);
                     y[i] = y1[i] + t[i];
                 }
                 st16(w.T2 + gr * w.E1 + k0, t);
-                st16(w.Y2 + gr * w.E1 + k0, y);
-                if (Q) st16q(w.Y2q + gr * w.E1 + k0, y);
+                st16(tb16(w.Y2, gr, k0, w.E1), y, 64);
+                if (Q) st16q(tq8(w.Y2q, gr, k0, w.E1), y);
             }
         } else if constexpr (KIND == WK_FWD3) {
-            unsigned char *GT = smem + kWStages * kWStage, *RT = GT + kWGT;
+            unsigned char *GT = smem + S * kWStage, *RT = GT + kWGT;
             {
                 const float s = row.valid ? row.a.x : 0.f;
                 float r8[8] = {s, s * row.a.y, s * row.a.z, s * row.a.w, 0.f, 0.f, 0.f, 0.f};
@@ -332,7 +371,7 @@ __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
                 const int m0 = nb * kWNB + c0;
                 float z[16], y2[16], t[16], g[16];
                 acc16(c0, z);
-                ld16(w.Y2 + gr * w.E1 + (m0 % w.E1), y2);   // skip: G = (y2, y2) + t3
+                ld16(tb16(w.Y2, gr, m0 % w.E1, w.E1), y2, 64);   // skip: G = (y2, y2) + t3
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     t[i] = tc::tanh_fast(z[i] + b3[m0 + i]);
@@ -397,8 +436,8 @@ __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
                     dy[i] = z[i] + sk * gs;
                     dz[i] = dy[i] * (1.f - t2[i] * t2[i]);
                 }
-                if (Q) st16q(w.DZ2q + gr * w.E1 + k0, dz);
-                else st16(w.DZ2 + gr * w.E1 + k0, dz);
+                if (Q) st16q(tq8(w.DZ2q, gr, k0, w.E1), dz);
+                else st16(tb16(w.DZ2, gr, k0, w.E1), dz, 64);
                 float4 *d4 = reinterpret_cast<float4 *>(w.DY2 + gr * w.E1 + k0);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) d4[i] = make_float4(dy[4 * i], dy[4 * i + 1], dy[4 * i + 2], dy[4 * i + 3]);
@@ -429,7 +468,15 @@ __global__ void __launch_bounds__(128, 1) k_wide_gemm(ModelDev md, WideArgs w)
         tc::fence_before_sync();
         __syncthreads();
     }
-    if (dead && tid == 0) atomicOr(w.err, 1);
+    if (dead && tid == 0) {
+        // a wait gave up: flag it, then wait (bounded again) for this CTA's copies and products in
+        // flight before the tensor memory is freed
+        atomicOr(w.err, 1);
+        for (int q = 0; q < S; ++q) {
+            if (loaded[q]) tc::mbar_wait(&bar_full[q], ph_f[q], kWaitW);
+            if (busy[q]) tc::mbar_wait(&bar_empty[q], ph_e[q], kWaitW);
+        }
+    }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
@@ -449,8 +496,8 @@ __global__ void k_wide_l1(ModelDev md, WideArgs w, int64_t max_rows)
     for (int k = 2 * lane; k < w.E0; k += 64) {
         const float t0 = tc::tanh_fast(fmaf(s, vec[k], vec[w.E0 + k]));
         const float t1 = tc::tanh_fast(fmaf(s, vec[k + 1], vec[w.E0 + k + 1]));
-        *reinterpret_cast<uint32_t *>(w.Y1 + gr * w.E0 + k) = bf2(t0, t1);
-        if (Q) *reinterpret_cast<uint16_t *>(w.Y1q + gr * w.E0 + k) = q2(t0, t1);
+        *reinterpret_cast<uint32_t *>(tb16(w.Y1, gr, k, w.E0)) = bf2(t0, t1);
+        if (Q) *reinterpret_cast<uint16_t *>(tq8(w.Y1q, gr, k, w.E0)) = q2(t0, t1);
     }
 }
 
@@ -471,7 +518,7 @@ __global__ void k_wide_b1(ModelDev md, WideArgs w, int64_t max_rows)
     if (Q) grad_scale(w.gbits, gs, gi);
     for (int m = 2 * lane; m < w.E2; m += 64) {
         const float2 t3 = unbf2(*reinterpret_cast<const uint32_t *>(w.T3 + gr * w.E2 + m));
-        const float2 y2 = unbf2(*reinterpret_cast<const uint32_t *>(w.Y2 + gr * w.E1 + (m % w.E1)));
+        const float2 y2 = unbf2(*reinterpret_cast<const uint32_t *>(tb16(w.Y2, gr, m % w.E1, w.E1)));
         float dz[2] = {0.f, 0.f};
         if (row.valid) {
             const float tt[2] = {t3.x, t3.y}, yy[2] = {y2.x, y2.y};
@@ -487,8 +534,8 @@ __global__ void k_wide_b1(ModelDev md, WideArgs w, int64_t max_rows)
                 dz[e] = dG * (1.f - tt[e] * tt[e]) * gs;
             }
         }
-        if (Q) *reinterpret_cast<uint16_t *>(w.DZ3q + gr * w.E2 + m) = q2(dz[0], dz[1]);
-        else *reinterpret_cast<uint32_t *>(w.DZ3 + gr * w.E2 + m) = bf2(dz[0], dz[1]);
+        if (Q) *reinterpret_cast<uint16_t *>(tq8(w.DZ3q, gr, m, w.E2)) = q2(dz[0], dz[1]);
+        else *reinterpret_cast<uint32_t *>(tb16(w.DZ3, gr, m, w.E2)) = bf2(dz[0], dz[1]);
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -597,10 +644,12 @@ WideLayout wide_layout(const ModelDev &md)
     return L;
 }
 
-// rows x cols row-major FP64 matrix M (element (r, c) = M[r * rs + c * cs]) as e4m3 rows scaled by a
-// power of two s_r (largest |entry| of the row times s_r in (224, 448]); inv[r] = 1 / s_r.
+// rows x cols FP64 matrix M (element (r, c) = M[r * rs + c * cs]) as e4m3 rows scaled by a power of
+// two s_r (largest |entry| of the row times s_r in (224, 448]), pre-tiled like the bf16 matrices;
+// inv[r] = 1 / s_r.
 void quant_rows(const double *M, int rows, int cols, int64_t rs, int64_t cs, unsigned char *q, float *inv)
 {
+    const int rb = rows < kWNB ? rows : kWNB;
     for (int r = 0; r < rows; ++r) {
         double mx = 0.0;
         for (int c = 0; c < cols; ++c) mx = fmax(mx, fabs(M[r * rs + c * cs]));
@@ -609,7 +658,7 @@ void quant_rows(const double *M, int rows, int cols, int64_t rs, int64_t cs, uns
         inv[r] = (float)ldexp(1.0, -e);
         for (int c = 0; c < cols; ++c) {
             const __nv_fp8_e4m3 v((float)(M[r * rs + c * cs] * s));
-            q[(size_t)r * cols + c] = (unsigned char)v.__x;
+            q[wtile_off(r, rb, c, cols, 1)] = (unsigned char)v.__x;
         }
     }
 }
@@ -639,19 +688,22 @@ dp_status pack_wide_weights(dp_model *m)
     for (int q = 0; q < nn; ++q) {
         const double *p = m->h_params.data() + md.emb_base + q * md.emb.size;
         unsigned char *o = img.data() + (size_t)q * L.img;
-        uint16_t *w2t = reinterpret_cast<uint16_t *>(o + L.oW2T), *w3t = reinterpret_cast<uint16_t *>(o + L.oW3T);
-        uint16_t *w3 = reinterpret_cast<uint16_t *>(o + L.oW3), *w2 = reinterpret_cast<uint16_t *>(o + L.oW2);
+        // element (r, c) of a rows x cols matrix at its pre-tiled place (blocks of min(rows, 256) rows)
+        auto put = [&](uint32_t off, int rows, int cols, int r, int c, double v) {
+            const uint16_t b = bf(v);
+            memcpy(o + off + wtile_off(r, rows < kWNB ? rows : kWNB, c, cols, 2), &b, 2);
+        };
         const double *W1 = p + md.emb.W[0], *b1 = p + md.emb.b[0], *W2 = p + md.emb.W[1], *b2 = p + md.emb.b[1];
         const double *W3 = p + md.emb.W[2], *b3 = p + md.emb.b[2];
         for (int a = 0; a < L.E0; ++a)
             for (int b = 0; b < L.E1; ++b) {
-                w2[(size_t)a * L.E1 + b] = bf(W2[(size_t)a * L.E1 + b]);    // W2 [E0][E1]
-                w2t[(size_t)b * L.E0 + a] = bf(W2[(size_t)a * L.E1 + b]);   // W2^T [E1][E0]
+                put(L.oW2, L.E0, L.E1, a, b, W2[(size_t)a * L.E1 + b]);    // W2 [E0][E1]
+                put(L.oW2T, L.E1, L.E0, b, a, W2[(size_t)a * L.E1 + b]);   // W2^T [E1][E0]
             }
         for (int a = 0; a < L.E1; ++a)
             for (int b = 0; b < L.E2; ++b) {
-                w3[(size_t)a * L.E2 + b] = bf(W3[(size_t)a * L.E2 + b]);
-                w3t[(size_t)b * L.E1 + a] = bf(W3[(size_t)a * L.E2 + b]);
+                put(L.oW3, L.E1, L.E2, a, b, W3[(size_t)a * L.E2 + b]);
+                put(L.oW3T, L.E2, L.E1, b, a, W3[(size_t)a * L.E2 + b]);
             }
         float *vec = reinterpret_cast<float *>(o + L.oVec);
         for (int k = 0; k < L.E0; ++k) {
@@ -688,6 +740,10 @@ dp_status run_wide(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_e
 {
     const ModelDev &md = m->dev;
     const WideLayout L = wide_layout(md);
+    if (Q && L.E0 % 128 != 0) {   // e4m3 K chunks are 128 wide
+        set_error("DP_MIX_FP8 needs embedding nets (w, 2w, 4w) with w >= 128");
+        return DP_ERR_UNSUPPORTED;
+    }
     const int64_t n = nl->n;
     const int nn = md.ntypes * md.ntypes;
     const int64_t max_chunks = n * md.chunks_per_atom + 4 * nn + 4;
@@ -785,16 +841,16 @@ dp_status run_wide(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_e
         ProfScope ps(m->prof, PG_CHUNKS, 3, st);
         DP_TRY(build_chunks_batch(m, nl, 0, n, chunks, nullptr, cnt, scratch, st));
     }
-    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_FWD2, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
-    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_FWD3, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
-    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_BWD3, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
-    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_BWD2, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWSmem));
+    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_FWD2, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem<WK_FWD2>()));
+    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_FWD3, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem<WK_FWD3>()));
+    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_BWD3, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem<WK_BWD3>()));
+    DP_CUDA(cudaFuncSetAttribute(k_wide_gemm<WK_BWD2, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wide_smem<WK_BWD2>()));
     const unsigned rb = (unsigned)((max_rows * 32 + 255) / 256);
     {
         ProfScope ps(m->prof, PG_EMBED_FWD, 3, st);
         k_wide_l1<Q><<<rb, 256, 0, st>>>(md, a, max_rows);
-        k_wide_gemm<WK_FWD2, Q><<<nsm, 128, kWSmem, st>>>(md, a);
-        k_wide_gemm<WK_FWD3, Q><<<nsm, 128, kWSmem, st>>>(md, a);
+        k_wide_gemm<WK_FWD2, Q><<<nsm, 128, wide_smem<WK_FWD2>(), st>>>(md, a);
+        k_wide_gemm<WK_FWD3, Q><<<nsm, 128, wide_smem<WK_FWD3>(), st>>>(md, a);
     }
     DP_CUDA(cudaGetLastError());
     DP_TRY(fit_mix16_bf16(m, nl, a.T, d_atom_energy, dT, st));
@@ -807,8 +863,8 @@ dp_status run_wide(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_e
     {
         ProfScope ps(m->prof, PG_EMBED_BWD, 4, st);
         k_wide_b1<Q><<<rb, 256, 0, st>>>(md, a, max_rows);
-        k_wide_gemm<WK_BWD3, Q><<<nsm, 128, kWSmem, st>>>(md, a);
-        k_wide_gemm<WK_BWD2, Q><<<nsm, 128, kWSmem, st>>>(md, a);
+        k_wide_gemm<WK_BWD3, Q><<<nsm, 128, wide_smem<WK_BWD3>(), st>>>(md, a);
+        k_wide_gemm<WK_BWD2, Q><<<nsm, 128, wide_smem<WK_BWD2>(), st>>>(md, a);
         k_wide_force<Q><<<(unsigned)(max_chunks / 4 + 1), 128, 0, st>>>(md, a);
     }
     DP_CUDA(cudaGetLastError());
