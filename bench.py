@@ -746,7 +746,11 @@ def run_sweep(args, rank, world):
     n = len(typ)
     peak, src = tensor_peak()
     points = []
-    for emb, prec in [(e, "bf16") for e in SWEEP] + [(e, "fp8") for e in SWEEP if e[0] >= 128]:
+    widths = [int(v) for v in args.sweep_widths.split(",")] if args.sweep_widths else [e[0] for e in SWEEP]
+    precs = args.sweep_precisions.split(",")
+    todo = [(e, "bf16") for e in SWEEP if e[0] in widths and "bf16" in precs]
+    todo += [(e, "fp8") for e in SWEEP if e[0] >= 128 and e[0] in widths and "fp8" in precs]
+    for emb, prec in todo:
         cfg = dpsynth.ModelConfig(ntypes=1, rcut=8.0, rcut_smth=2.0, sel=(512,), embed=emb)
         model = dp.Model(cfg, seed=1)
         stream = torch.cuda.Stream(device=dev)
@@ -928,6 +932,9 @@ def main():
                          "per temperature (comma-separated)")
     ap.add_argument("--teacher-md-precision", default="mix32", help="judged task: precision of the teacher's MD")
     ap.add_argument("--label-precision", default="mix32", help="judged task: precision of the teacher's labels")
+    ap.add_argument("--sweep-widths", default="", help="sweep task: first widths w of the nets (w, 2w, 4w) to run "
+                    "(comma-separated; default all)")
+    ap.add_argument("--sweep-precisions", default="bf16,fp8", help="sweep task: bf16 and/or fp8")
     ap.add_argument("--task", default="md", choices=["md", "grad", "judged", "sweep"],
                     help="md: NVE steps (default); grad: force-loss parameter gradient over 32 water frames; "
                          "judged: distilled student MD judged by the full model")
