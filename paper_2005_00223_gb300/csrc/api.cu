@@ -459,6 +459,7 @@ void dp_model_destroy(dp_model *m)
     cudaFree(m->d_tcw);
     cudaFree(m->d_tcw_x3);
     cudaFree(m->d_tcfit_x3);
+    for (unsigned char *p : m->d_fitcl) cudaFree(p);
     cudaFree(m->d_wide);
     cudaFree(m->d_wide_q);
     cudaFree(m->d_ozw);

@@ -158,6 +158,7 @@ struct dp_model {
     unsigned char *d_tcfit = nullptr; // packed fp16 and bf16 fitting weights for the tensor cores
     unsigned char *d_tcw_x3 = nullptr; // packed split-bf16 (hi, lo) embedding weights (DP_MIX_BF16X3)
     unsigned char *d_tcfit_x3 = nullptr; // packed split-bf16 fitting weights (DP_MIX_BF16X3)
+    unsigned char *d_fitcl[3] = {nullptr, nullptr, nullptr};   // cluster fitting kernel: fp16, bf16, split-bf16 images
     unsigned char *d_wide = nullptr;  // bf16 weights of the wide embedding nets (W2^T, W3^T, W3, W2, vectors)
     unsigned char *d_wide_q = nullptr;   // their e4m3 copies with row scales (DP_MIX_FP8)
     void *d_ozw = nullptr;            // fp16 digits of the first fitting layer's weights (FP64 products on the tensor cores)
@@ -295,6 +296,13 @@ dp_status compute_wide(dp_model *m, dp_nlist *nl, int fp8, double *d_energy, dou
                        double *d_virial, double *d_atom_virial, cudaStream_t st);
 // The MIX-16 fitting net (bf16 operands) of tc.cu, for the wide path.
 dp_status fit_mix16_bf16(dp_model *m, dp_nlist *nl, const float *T, double *E_atom, float *dT, cudaStream_t st);
+// Fitting net + descriptor adjoint on the tensor cores with a tile split over a thread-block cluster
+// (fit_cluster.cu); mode 0 fp16, 1 bf16, 2 split bf16.  DP_ERR_UNSUPPORTED (no error text) for shapes
+// it does not cover, which the single-CTA kernels then take.  DP_FIT_ONE_CTA selects those always.
+bool fit_cluster_enabled();
+dp_status fit_cluster(dp_model *m, dp_nlist *nl, int mode, const float *T, double *E_atom, float *dT,
+                      cudaStream_t st);
+dp_status pack_fit_cluster_weights(dp_model *m);   // repacks the images already in use
 // Ghost atoms of a spatial decomposition (dp_nlist_set_centers): their list rows are cleared after each
 // format, so they appear only as neighbors.
 dp_status clear_ghost_rows(const dp_model *m, dp_nlist *nl, cudaStream_t st);

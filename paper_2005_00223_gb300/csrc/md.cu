@@ -136,7 +136,7 @@ dp_status md_step_body(dp_model *m, dp_md_state *s, dp_precision prec, double dt
 std::string route_env()
 {
     std::string k;
-    for (const char *v : {"DP_NO_OZAKI", "DP_OZ_MIN_ATOMS", "DP_SIMT_FIT", "DP_BATCH_ATOMS"}) {
+    for (const char *v : {"DP_NO_OZAKI", "DP_OZ_MIN_ATOMS", "DP_SIMT_FIT", "DP_BATCH_ATOMS", "DP_FIT_ONE_CTA"}) {
         const char *e = getenv(v);
         k += e ? e : "-";
         k += '|';

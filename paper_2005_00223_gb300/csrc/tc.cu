@@ -1173,6 +1173,10 @@ template <int BF>
 dp_status fit_tc(dp_model *m, dp_nlist *nl, const float *T, int grid, double *E_atom, float *dT,
                  cudaStream_t st)
 {
+    if (fit_cluster_enabled()) {
+        const dp_status s = fit_cluster(m, nl, BF, T, E_atom, dT, st);
+        if (s != DP_ERR_UNSUPPORTED) return s;
+    }
     switch (fit_tc_kind(m->dev)) {
     case 1: return launch_fit_tc<FitWater, BF>(m, nl, T, grid, E_atom, dT, st);
     case 2: return launch_fit_tc<FitStudent, BF>(m, nl, T, grid, E_atom, dT, st);
@@ -1354,6 +1358,7 @@ dp_status build_chunks_batch(dp_model *m, dp_nlist *nl, int64_t p0, int64_t nb, 
 dp_status pack_tc_weights(dp_model *m)
 {
     const int *e = m->dev.emb.wout;
+    DP_TRY(pack_fit_cluster_weights(m));
     if (embed_is_wide(m->n_embed, m->embed)) {
         if (m->d_wide) DP_TRY(pack_wide_weights(m));
     } else {

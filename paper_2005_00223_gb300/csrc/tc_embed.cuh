@@ -263,6 +263,49 @@ __global__ void k_dT_f32(ModelDev md, const int32_t *__restrict__ order, int64_t
     dT[(int64_t)a_id * nq + r] = acc * inv * inv;
 }
 
+// hi = bf16(x), lo = bf16(x - hi) of two values, packed as bf16 pairs.
+__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<uint32_t *>(&h);
+    lo = *reinterpret_cast<uint32_t *>(&l);
+}
+
+// 8 consecutive K values of one row into the hi and lo K-major tiles.
+__device__ __forceinline__ void st8_k(unsigned char *hi, unsigned char *lo, int row, int k0, int K, const float *v)
+{
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) split2(v[2 * q], v[2 * q + 1], h[q], l[q]);
+    const uint32_t off = tc::kmaj_off(row, k0, K);
+    *reinterpret_cast<uint4 *>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4 *>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// D (+)= A B^T over K (multiple of 16) with explicit strides between 8-row groups of A and B (K-major).
+__device__ __forceinline__ void mma_k_sbo(uint32_t d, uint32_t a, uint32_t a_sbo, uint32_t b, uint32_t b_sbo, int K,
+                                          uint32_t id, bool acc0)
+{
+    for (int ks = 0; ks < (K >> 4); ++ks) {
+        const uint64_t ad = tc::smem_desc(a + ks * 256, 128, a_sbo);
+        const uint64_t bd = tc::smem_desc(b + ks * 256, 128, b_sbo);
+        const uint32_t acc = (acc0 || ks > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+            "l"(ad), "l"(bd), "r"(id), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ uint32_t unorm16_pair(float a, float b)
+{
+    const uint32_t qa = __float2uint_rn(fminf(fmaxf(a, 0.f), 1.f) * 65535.f);
+    const uint32_t qb = __float2uint_rn(fminf(fmaxf(b, 0.f), 1.f) * 65535.f);
+    return qa | (qb << 16);
+}
+
 }  // namespace
 
 }  // namespace dp

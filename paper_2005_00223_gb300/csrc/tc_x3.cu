@@ -78,27 +78,6 @@ struct X3 {
     static_assert(B_A3L + 128 * S::N2 * 2 <= B_X && F_RTL + 16 * 128 * 2 <= F_SMEM, "layout");
 };
 
-// hi = bf16(x), lo = bf16(x - hi) of two values, packed as bf16 pairs.
-__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo)
-{
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    const float2 hf = __bfloat1622float2(h);
-    __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
-    hi = *reinterpret_cast<uint32_t *>(&h);
-    lo = *reinterpret_cast<uint32_t *>(&l);
-}
-
-// 8 consecutive K values of one row into the hi and lo K-major tiles.
-__device__ __forceinline__ void st8_k(unsigned char *hi, unsigned char *lo, int row, int k0, int K, const float *v)
-{
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) split2(v[2 * q], v[2 * q + 1], h[q], l[q]);
-    const uint32_t off = tc::kmaj_off(row, k0, K);
-    *reinterpret_cast<uint4 *>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4 *>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
-}
-
 // 8 consecutive MN values (mn0 .. mn0 + 7) of K-row k into the hi and lo MN-major tiles.
 __device__ __forceinline__ void st8_mn(unsigned char *hi, unsigned char *lo, int mn0, int k, int MN, const float *v)
 {
@@ -630,28 +609,6 @@ using FitX3Water = FitX3<100, 16, 240>;
 using FitX3Student = FitX3<32, 8, 64>;
 using FitX3Paper = FitX3<128, 16, 240>;
 
-// D (+)= A B^T over K (multiple of 16) with explicit strides between 8-row groups of A and B (K-major).
-__device__ __forceinline__ void mma_k_sbo(uint32_t d, uint32_t a, uint32_t a_sbo, uint32_t b, uint32_t b_sbo, int K,
-                                          uint32_t id, bool acc0)
-{
-    for (int ks = 0; ks < (K >> 4); ++ks) {
-        const uint64_t ad = tc::smem_desc(a + ks * 256, 128, a_sbo);
-        const uint64_t bd = tc::smem_desc(b + ks * 256, 128, b_sbo);
-        const uint32_t acc = (acc0 || ks > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-            "l"(ad), "l"(bd), "r"(id), "r"(acc));
-    }
-}
-
-__device__ __forceinline__ uint32_t unorm16_pair(float a, float b)
-{
-    const uint32_t qa = __float2uint_rn(fminf(fmaxf(a, 0.f), 1.f) * 65535.f);
-    const uint32_t qb = __float2uint_rn(fminf(fmaxf(b, 0.f), 1.f) * 65535.f);
-    return qa | (qb << 16);
-}
-
 template <class S>
 __global__ void __launch_bounds__(128, 1) k_fit_x3(ModelDev md, const int32_t *__restrict__ order, int64_t pos_begin,
                                                   int64_t count, const float *__restrict__ T,
@@ -1064,6 +1021,10 @@ dp_status launch_fit_x3(dp_model *m, dp_nlist *nl, const float *T, int grid, dou
 
 dp_status fit_x3(dp_model *m, dp_nlist *nl, const float *T, int grid, double *E_atom, float *dT, cudaStream_t st)
 {
+    if (fit_cluster_enabled()) {
+        const dp_status s = fit_cluster(m, nl, 2, T, E_atom, dT, st);
+        if (s != DP_ERR_UNSUPPORTED) return s;
+    }
     if (!m->d_tcfit_x3) DP_TRY(pack_fit_x3_weights(m));
     switch (fit_x3_kind(m->dev)) {
     case 1: return launch_fit_x3<FitX3Water>(m, nl, T, grid, E_atom, dT, st);
