@@ -143,6 +143,23 @@ void dp_model_destroy(dp_model *m);
  * switches back.  The caller keeps the stream alive while the model uses it. */
 dp_status dp_model_set_stream(dp_model *m, void *stream);
 
+/* Deterministic force accumulation (on = 1; 0 = off, the default).  The FP64
+ * and MIX-32 evaluations then add the pair terms g_ij into the forces
+ * (F_i = -dE/dx_i of Sec. 2.2 as sums over the neighbor pairs) and the per-chunk virial
+ * terms as exact fixed-point numbers with 64 fractional bits in 64-bit integer
+ * limbs, whose sums do not depend on the order in which the GPU's threads add
+ * them: forces, energies and virials of an evaluation are then the same bit
+ * for bit from run to run, and an MD run resumed from a checkpoint
+ * (dp_md_state_save / _load) follows the uninterrupted one bit for bit.
+ * Contributions are truncated below 2^-64 (in the units of the force), and
+ * each force must stay below 2^62 in magnitude.  Costs three integer atomics
+ * per contribution where one FP64 atomic was used, and 288 bytes of device
+ * memory per atom of the neighbor list.  The tensor-core precisions
+ * (DP_MIX_BF16, _FP16, _BF16X3, _FP8) accumulate the descriptor with FP32
+ * atomics and stay reproducible only to their rounding; the flag does not
+ * change them.  DP_ERR_ARG for a NULL model or on outside {0, 1}. */
+dp_status dp_model_set_deterministic(dp_model *m, int32_t on);
+
 /* ------------------------------------------------------------- tracing */
 
 /* Kernel timing: while enabled, every kernel launch group of this model is

@@ -15,7 +15,7 @@ from . import _lib
 from ._lib import (DP_FP64, DP_MIX32, DP_MIX_BF16, DP_MIX_FP16, DPError, EXPORTS, load,  # noqa: F401
                    dp_compute, dp_compute_dev, dp_md_state_create, dp_md_state_destroy, dp_md_state_get,
                    dp_md_step, dp_md_state_save, dp_md_state_load, dp_model_create, dp_model_destroy, dp_model_get_params, dp_model_n_params,
-                   dp_model_set_params, dp_model_set_stream, dp_nlist_build, dp_nlist_destroy, dp_nlist_get,
+                   dp_model_set_params, dp_model_set_stream, dp_model_set_deterministic, dp_nlist_build, dp_nlist_destroy, dp_nlist_get,
                    dp_nlist_update, dp_profile_enable, dp_profile_group_name, dp_profile_read, dp_profile_select,
                    dp_nlist_update_dev, dp_param_grad, dp_force_loss_grad, dp_force_loss_grad_dev, dp_adam_step,
                    dp_model_sync_params, dp_md_step_judged, dp_nlist_format_noalloc, dp_tanh_f64_dev,
@@ -47,12 +47,14 @@ def _release_all():
 class Model:
     """Owning wrapper of a dp_model handle."""
 
-    def __init__(self, cfg, seed: int = 0, params=None):
+    def __init__(self, cfg, seed: int = 0, params=None, deterministic: bool = False):
         self.cfg = cfg
         self.h = dp_model_create(cfg, seed)
         _LIVE["model"].add(self)
         if params is not None:
             dp_model_set_params(self.h, params)
+        if deterministic:
+            dp_model_set_deterministic(self.h, True)
 
     @property
     def params(self):

@@ -27,7 +27,7 @@ PRECISION = {"fp64": DP_FP64, "mix32": DP_MIX32, "bf16": DP_MIX_BF16, "fp16": DP
 # Every entry point declared in include/dp.h.
 EXPORTS = [
     "dp_status_string", "dp_last_error", "dp_model_create", "dp_model_n_params", "dp_model_get_params",
-    "dp_model_set_params", "dp_model_destroy", "dp_model_set_stream", "dp_profile_enable", "dp_profile_select", "dp_profile_read",
+    "dp_model_set_params", "dp_model_destroy", "dp_model_set_stream", "dp_model_set_deterministic", "dp_profile_enable", "dp_profile_select", "dp_profile_read",
     "dp_profile_group_name", "dp_nlist_build", "dp_nlist_update", "dp_nlist_get",
     "dp_nlist_destroy", "dp_nlist_update_dev", "dp_compute", "dp_compute_dev", "dp_md_state_create",
     "dp_md_step", "dp_md_state_get", "dp_md_state_save", "dp_md_state_load", "dp_md_state_destroy", "dp_param_grad", "dp_force_loss_grad",
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
             "dp_model_set_params": ([P, P, I64], C.c_int),
             "dp_model_destroy": ([P], None),
             "dp_model_set_stream": ([P, P], C.c_int),
+            "dp_model_set_deterministic": ([P, I32], C.c_int),
             "dp_profile_enable": ([P, I32], C.c_int),
             "dp_profile_select": ([P, C.c_uint32], C.c_int),
             "dp_profile_read": ([P, I32, P, P], C.c_int),
@@ -182,6 +183,10 @@ def dp_model_set_params(m, flat):
 def dp_model_destroy(m):
     if m:
         load().dp_model_destroy(m)
+
+
+def dp_model_set_deterministic(m, on: bool = True):
+    _check(load().dp_model_set_deterministic(m, 1 if on else 0), "dp_model_set_deterministic")
 
 
 def dp_model_set_stream(m, stream=None):

@@ -499,6 +499,7 @@ static void nlist_free(dp_nlist *nl)
     cudaFree(nl->d_pos);
     cudaFree(nl->d_posf);
     cudaFree(nl->d_env);
+    cudaFree(nl->d_fx);
     cudaFree(nl->d_coord);
     cudaFree(nl->d_order);
 }

@@ -72,7 +72,33 @@ struct ModelDev {
     // polls after which that one wait gives up.  Every other wait keeps its default limit.
     int wait_test;
     long long wait_short;
+    // Deterministic mode (dp_model_set_deterministic): the force and per-atom virial scatters add
+    // into these fixed-point limb arrays (3 limbs per value) instead of FP64 atomics; null: FP64
+    // atomics.  Set for the duration of one evaluation.
+    unsigned long long *fx, *fxv;
 };
+
+// Order-independent accumulation of v: an exact fixed-point number with 64 fractional bits, its
+// integer part and two 32-bit fraction limbs each summed by an integer atomic (integer sums
+// commute, so the total does not depend on the order of the additions); bits of v below 2^-64 are
+// dropped (truncated towards minus infinity).  |v| must stay below 2^62.
+__device__ __forceinline__ void fx_add(unsigned long long *l, double v)
+{
+    const double ip = floor(v);
+    const double r = (v - ip) * 4294967296.0;   // the fraction times 2^32: exact
+    const double hi = floor(r);
+    const double lo = floor((r - hi) * 4294967296.0);
+    atomicAdd(l, (unsigned long long)(long long)ip);
+    atomicAdd(l + 1, (unsigned long long)hi);
+    atomicAdd(l + 2, (unsigned long long)lo);
+}
+
+// acc[idx] += v: into the limbs lx (deterministic mode) or by an FP64 atomic.
+__device__ __forceinline__ void acc_add(unsigned long long *lx, double *acc, int64_t idx, double v)
+{
+    if (lx) fx_add(lx + 3 * idx, v);
+    else atomicAdd(acc + idx, v);
+}
 
 // Waits that dp_test_starve_wait can starve.
 enum WaitTest { WT_NONE = 0, WT_EMBED_FWD_WEIGHTS = 1 };
@@ -176,6 +202,7 @@ struct dp_model {
     int64_t tscr_n = -1;
     bool params_dirty = false;        // device parameters newer than the host copy
     uint64_t epoch = 0;               // bumped whenever a buffer or parameter that launches capture changes
+    int32_t deterministic = 0;        // fixed-point force / virial scatters on the FP64 and MIX-32 routes
 };
 
 struct dp_nlist {
@@ -217,6 +244,8 @@ struct dp_nlist {
     std::string cgraph_env;
     int cgraph_direct = 0;            // direct calls with the current key (capture after the first)
     double *h_io = nullptr;           // pinned: coord [3n], F [3n], E_i [n], E and W [10], two int32 flags
+    unsigned long long *d_fx = nullptr;   // deterministic mode: limbs of F [3n][3], then of W_i [9n][3]
+    size_t fx_cap = 0;
 };
 
 struct dp_md_state {
@@ -303,6 +332,8 @@ bool fit_cluster_enabled();
 dp_status fit_cluster(dp_model *m, dp_nlist *nl, int mode, const float *T, double *E_atom, float *dT,
                       cudaStream_t st);
 dp_status pack_fit_cluster_weights(dp_model *m);   // repacks the images already in use
+// out[i] = the value of limbs l[3i .. 3i + 2] (fx_add), i < count, in FP64.
+dp_status fx_finish(int64_t count, const unsigned long long *l, double *out, cudaStream_t st);
 // Ghost atoms of a spatial decomposition (dp_nlist_set_centers): their list rows are cleared after each
 // format, so they appear only as neighbors.
 dp_status clear_ghost_rows(const dp_model *m, dp_nlist *nl, cudaStream_t st);

@@ -27,6 +27,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <type_traits>
 #include <vector>
 
 #include "dp_internal.cuh"
@@ -83,6 +84,21 @@ __device__ __forceinline__ float cl_ld4(uint32_t addr)
     float v;
     asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
     return v;
+}
+
+// d (+)= A B^T over KS steps of K = 16 (K-major no-swizzle operands): the descriptors of the first step
+// advance by 256 bytes (16 in their address field, which cannot carry below 256 KB) per step.
+template <int KS>
+__device__ __forceinline__ void mma_steps(uint32_t d, uint64_t ad, uint64_t bd, uint32_t id, uint32_t acc0)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(ad), "l"(bd), "r"(id), "r"(acc0));
+#pragma unroll
+    for (int ks = 1; ks < KS; ++ks)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.eq.u32 p, 0, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+            "l"(ad + 16u * ks), "l"(bd + 16u * ks), "r"(id));
 }
 
 // Tile shape: descriptor M1 x M2 (D = M1 M2 columns), hidden width F, NS CTAs per cluster, P operand
@@ -339,30 +355,35 @@ __global__ void __launch_bounds__(192, 1) k_fit_cl(ModelDev md, const int32_t *_
         uint32_t x = 0;        // exchanges (aready phases)
         uint32_t cd = 0;       // dE/dD blocks
         int lc = -1;           // the last chunk whose products were committed
-        // d (+)= A B^T with the next weight chunk (B_rows x K) as B; three products in split mode
-        auto chunk = [&](uint32_t d, uint32_t a, uint32_t a_plane, uint32_t a_sbo, uint32_t b_rows, int K,
-                         uint32_t id, bool acc0) -> bool {
+        // d (+)= A B^T with the next weight chunk (B_ROWS x K) as B; three products in split mode
+        auto chunk = [&](auto kc, auto brows, uint32_t d, uint32_t a, uint32_t a_plane, uint32_t a_sbo, uint32_t id,
+                         bool acc0) -> bool {
+            constexpr int K = decltype(kc)::value, B_ROWS = decltype(brows)::value;
             const int s = g % SB;
             if (!wait(&bar_full[s], (uint32_t)(g / SB) & 1u)) return false;
             tc::fence_after_sync();
-            const uint32_t b = b_u32 + (uint32_t)s * S::STAGE, b_sbo = (uint32_t)(K / 8) * 128,
-                           b_plane = b_rows * (uint32_t)K * 2;
-            mma_k_sbo(d, a, a_sbo, b, b_sbo, K, id, acc0);
+            const uint32_t b = b_u32 + (uint32_t)s * S::STAGE;
+            const uint64_t ad = tc::smem_desc(a, 128, a_sbo), bd = tc::smem_desc(b, 128, (K / 8) * 128);
+            mma_steps<K / 16>(d, ad, bd, id, acc0 ? 1u : 0u);
             if constexpr (P == 2) {
-                mma_k_sbo(d, a, a_sbo, b + b_plane, b_sbo, K, id, true);
-                mma_k_sbo(d, a + a_plane, a_sbo, b, b_sbo, K, id, true);
+                mma_steps<K / 16>(d, ad, bd + (uint64_t)((B_ROWS * K * 2) >> 4), id, 1u);
+                mma_steps<K / 16>(d, ad + (uint64_t)(a_plane >> 4), bd, id, 1u);
             }
             tc::mma_commit(&bar_empty[s]);
             lc = g++;
             return true;
         };
+        using KC1_t = std::integral_constant<int, KC1>;
+        using KC2_t = std::integral_constant<int, KC2>;
+        using FS_t = std::integral_constant<int, FS>;
+        using NBW_t = std::integral_constant<int, NBW>;
         // acc (+)= A (K = F, the columns of all CTAs) x the next NK2 weight chunks, once A is complete
         auto gemm_res = [&](bool acc0) -> bool {
             if (!wait(&bar_aready, x++ & 1u, true)) return false;
             tc::fence_async_smem();
             tc::fence_after_sync();
             for (int c = 0; c < NK2; ++c)
-                if (!chunk(tm, a_u32 + (uint32_t)c * (KC2 / 8) * 128, 128 * F * 2, (F / 8) * 128, FS, KC2, idS,
+                if (!chunk(KC2_t{}, FS_t{}, tm, a_u32 + (uint32_t)c * (KC2 / 8) * 128, 128 * F * 2, (F / 8) * 128, idS,
                            acc0 || c > 0))
                     return false;
             tc::mma_commit(&bar_acc);
@@ -375,7 +396,7 @@ __global__ void __launch_bounds__(192, 1) k_fit_cl(ModelDev md, const int32_t *_
                 ok = wait(&bar_dfull[sa], (ca / SA) & 1u);
                 if (!ok) break;
                 tc::fence_after_sync();
-                ok = chunk(tm, a_u32 + (uint32_t)sa * S::DCH, 128 * KC1 * 2, (KC1 / 8) * 128, FS, KC1, idS, c > 0);
+                ok = chunk(KC1_t{}, FS_t{}, tm, a_u32 + (uint32_t)sa * S::DCH, 128 * KC1 * 2, (KC1 / 8) * 128, idS, c > 0);
                 if (!ok) break;
                 tc::mma_commit(&bar_dfree[sa]);
             }
@@ -390,8 +411,8 @@ __global__ void __launch_bounds__(192, 1) k_fit_cl(ModelDev md, const int32_t *_
                 if (!ok) break;
                 tc::fence_after_sync();
                 for (int c = 0; c < NK2 && ok; ++c)
-                    ok = chunk(tm + 256 + buf * NBW, a_u32 + (uint32_t)c * (KC2 / 8) * 128, 128 * F * 2, (F / 8) * 128,
-                               NBW, KC2, idB, c > 0);
+                    ok = chunk(KC2_t{}, NBW_t{}, tm + 256 + buf * NBW, a_u32 + (uint32_t)c * (KC2 / 8) * 128, 128 * F * 2,
+                               (F / 8) * 128, idB, c > 0);
                 if (ok) tc::mma_commit(&bar_dready[buf]);
             }
             if (!ok) break;
@@ -428,9 +449,12 @@ __global__ void __launch_bounds__(192, 1) k_fit_cl(ModelDev md, const int32_t *_
             const bool valid = r0 < count;
             const int atom = valid ? order[pos_begin + r0] : 0;
             const float4 *Ta = reinterpret_cast<const float4 *>(T + (int64_t)atom * 4 * M1);
-            float4 tb[M2];   // rows b < M2 of T (the T< factor), scaled by 1/sum(sel)^2 for D
+            float4 tb[M2];   // rows b < M2 of T (the T< factor) times 1/sum(sel)^2
 #pragma unroll
-            for (int b = 0; b < M2; ++b) tb[b] = valid ? Ta[b] : zero4;
+            for (int b = 0; b < M2; ++b) {
+                const float4 t = valid ? Ta[b] : zero4;
+                tb[b] = make_float4(t.x * inv2, t.y * inv2, t.z * inv2, t.w * inv2);
+            }
             // the peers have read this CTA's partial sums of the previous tile (in the A region)
             if (it > 0 && !dead()) wait(&bar_partd, (uint32_t)(it - 1) & 1u, true);
             // ---- layer 1: D (times 1/sum(sel)^2) into a ring of SA stages, T rows PF chunks ahead
@@ -463,7 +487,7 @@ __global__ void __launch_bounds__(192, 1) k_fit_cl(ModelDev md, const int32_t *_
                             for (int u = 0; u < 8; ++u) {
                                 const float4 ta = cur[(c8 + u) / M2];
                                 const float4 t2 = tb[(c8 + u) % M2];
-                                v[u] = (ta.x * t2.x + ta.y * t2.y + ta.z * t2.z + ta.w * t2.w) * inv2;
+                                v[u] = ta.x * t2.x + ta.y * t2.y + ta.z * t2.z + ta.w * t2.w;
                             }
                             st8(Ds, 128 * KC1 * 2, c8, KC1, v);
                         }
@@ -626,7 +650,7 @@ __global__ void __launch_bounds__(192, 1) k_fit_cl(ModelDev md, const int32_t *_
                                     dtb[b].z = fmaf(dd, ta.z, dtb[b].z);
                                     dtb[b].w = fmaf(dd, ta.w, dtb[b].w);
                                 }
-                                if (valid) dTa[a] = make_float4(acc.x * inv2, acc.y * inv2, acc.z * inv2, acc.w * inv2);
+                                if (valid) dTa[a] = acc;
                             }
                         }
                     }

@@ -623,7 +623,7 @@ struct Bwd4Epi {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 fi[k] = gv[k];
-                atomicAdd(&force[3 * (int64_t)j + k], -gv[k]);
+                acc_add(md.fx, force, 3 * (int64_t)j + k, -gv[k]);
             }
 #pragma unroll
             for (int x = 0; x < 3; ++x)
@@ -638,9 +638,9 @@ struct Bwd4Epi {
             for (int o = 16; o > 0; o >>= 1) vir[q] += __shfl_xor_sync(0xffffffffu, vir[q], o);
         if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) atomicAdd(&force[3 * (int64_t)a + k], fi[k]);
+            for (int k = 0; k < 3; ++k) acc_add(md.fx, force, 3 * (int64_t)a + k, fi[k]);
 #pragma unroll
-            for (int q = 0; q < 9; ++q) atomicAdd(&atom_virial[9 * (int64_t)a + q], vir[q]);
+            for (int q = 0; q < 9; ++q) acc_add(md.fxv, atom_virial, 9 * (int64_t)a + q, vir[q]);
         }
         (void)E0;
     }

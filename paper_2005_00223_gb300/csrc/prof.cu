@@ -117,6 +117,19 @@ dp_status dp_model_set_stream(dp_model *m, void *stream)
     return DP_OK;
 }
 
+dp_status dp_model_set_deterministic(dp_model *m, int32_t on)
+{
+    if (!m || (on != 0 && on != 1)) {
+        set_error("dp_model_set_deterministic: NULL model or on not 0 / 1");
+        return DP_ERR_ARG;
+    }
+    if (m->deterministic != on) {
+        m->deterministic = on;
+        ++m->epoch;   // captured evaluations and MD steps are re-captured
+    }
+    return DP_OK;
+}
+
 dp_status dp_profile_enable(dp_model *m, int32_t on)
 {
     if (!m || !m->prof) {

@@ -101,6 +101,17 @@ __global__ void k_nonfinite(const double *__restrict__ x, int64_t n, int32_t *fl
     if (i < n && !isfinite(x[i])) atomicOr(flag, 1);
 }
 
+// The FP64 value of each fixed-point accumulator (fx_add): integer part plus the two fraction limbs
+// scaled by 2^-32 and 2^-64, summed in that order (each limb sum is exact; the conversions and the
+// two additions round the same way every time).
+__global__ void k_fx_finish(int64_t count, const unsigned long long *__restrict__ l, double *__restrict__ out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const unsigned long long *v = l + 3 * i;
+    out[i] = (double)(long long)v[0] + (double)v[1] * 0x1p-32 + (double)v[2] * 0x1p-64;
+}
+
 }  // namespace
 
 dp_status reduce_energy_virial(const double *d_atom_energy, const double *d_atom_virial, int64_t n,
@@ -120,6 +131,14 @@ dp_status check_nonfinite(const double *d_x, int64_t n, int32_t *d_flag, cudaStr
 {
     if (n == 0) return DP_OK;
     k_nonfinite<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d_x, n, d_flag);
+    DP_CUDA(cudaGetLastError());
+    return DP_OK;
+}
+
+dp_status fx_finish(int64_t count, const unsigned long long *l, double *out, cudaStream_t st)
+{
+    if (count <= 0) return DP_OK;
+    k_fx_finish<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, l, out);
     DP_CUDA(cudaGetLastError());
     return DP_OK;
 }

@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(S::NT) k_embed_bwd(ModelDev md, BoxDev bx, con
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     fi[k] += gv[k];
-                    atomicAdd(&force[3 * (int64_t)j + k], -gv[k]);
+                    acc_add(md.fx, force, 3 * (int64_t)j + k, -gv[k]);
                 }
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
@@ -540,7 +540,7 @@ __global__ void __launch_bounds__(S::NT) k_embed_bwd(ModelDev md, BoxDev bx, con
             for (int s = 16; s > 0; s >>= 1) vir[q] += __shfl_xor_sync(0xffffffffu, vir[q], s);
         if (n == 0) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) atomicAdd(&force[3 * (int64_t)i + k], fi[k]);
+            for (int k = 0; k < 3; ++k) acc_add(md.fx, force, 3 * (int64_t)i + k, fi[k]);
         }
         if (n < 9 && atom_virial) {
             double v = 0.0;
@@ -847,6 +847,25 @@ dp_status compute_simt(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
     char *ozes = ozemb ? carve(oz_emb_bytes(md, B)) : nullptr;
     DP_CUDA(cudaMemsetAsync(d_force, 0, sizeof(double) * 3 * n, st));
     if (ozemb) DP_CUDA(cudaMemsetAsync(d_atom_virial, 0, sizeof(double) * 9 * n, st));   // accumulated per chunk
+    // deterministic mode: the scatters go to fixed-point limbs (F, and W_i where it is accumulated
+    // per chunk), converted to FP64 after the last batch
+    struct LimbScope {
+        ModelDev &d;
+        ~LimbScope() { d.fx = d.fxv = nullptr; }
+    } limb_scope{m->dev};
+    if (m->deterministic) {
+        const size_t need = (size_t)36 * (size_t)n;
+        if (nl->fx_cap < need) {
+            cudaFree(nl->d_fx);
+            nl->d_fx = nullptr;
+            nl->fx_cap = 0;
+            DP_CUDA(cudaMalloc((void **)&nl->d_fx, need * sizeof(unsigned long long)));
+            nl->fx_cap = need;
+        }
+        DP_CUDA(cudaMemsetAsync(nl->d_fx, 0, need * sizeof(unsigned long long), st));
+        m->dev.fx = nl->d_fx;
+        m->dev.fxv = ozemb ? nl->d_fx + (size_t)9 * n : nullptr;
+    }
     BoxDev bx = make_box(nl);
     const int *e = md.emb.wout;
     for (int64_t p0 = 0; p0 < n; p0 += B) {
@@ -859,6 +878,10 @@ dp_status compute_simt(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
         else
             s = launch_batch<ShapePaper, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, ozs, ozes, st);
         if (s != DP_OK) return s;
+    }
+    if (m->dev.fx) {
+        DP_TRY(fx_finish(3 * n, m->dev.fx, d_force, st));
+        if (m->dev.fxv) DP_TRY(fx_finish(9 * n, m->dev.fxv, d_atom_virial, st));
     }
     ProfScope ps(m->prof, PG_REDUCE, 1, st);
     return reduce_energy_virial(d_atom_energy, d_atom_virial, centers_of(nl), d_energy, d_virial, m->d_red, st);

@@ -151,6 +151,47 @@ def test_graph_replay_matches_direct_launches(dp, prec):
     assert a[7] == b[7]
 
 
+@pytest.mark.parametrize("route", ["simt", "split"])
+def test_checkpoint_resume_bit_for_bit_when_deterministic(dp, tmp_path, route):
+    """With deterministic force accumulation the resumed run repeats the uninterrupted one exactly:
+    coordinates, velocities and thermo rows, on the one-CTA-per-atom and the split-product FP64
+    routes, across device list rebuilds (skin 0.3 A)."""
+    cfg, p = _scaled_water_model(5)
+    coord, typ, box = dpsynth.water_box(5)
+    mass = np.array([dpsynth.MASS["O"], dpsynth.MASS["H"]])
+    vel = dpsynth.velocities(mass[typ], 600.0, 5)
+    import os
+    if route == "split":
+        os.environ["DP_OZ_MIN_ATOMS"] = "0"
+    try:
+        m = dp.Model(cfg, 0, params=p, deterministic=True)
+        st = dp.MDState(m, coord, vel, typ, mass, box, skin=0.3)
+        st.step(8, 0.5, "fp64")
+        path = str(tmp_path / "md.ckpt")
+        st.save(path)
+        th_a = st.step(12, 0.5, "fp64", thermo_every=4)
+        xa, va, stepa, nra = st.get()
+        r = dp.MDState.load(m, path)
+        th_b = r.step(12, 0.5, "fp64", thermo_every=4)
+        xb, vb, stepb, _ = r.get()
+        # and a second uninterrupted run from the start
+        st2 = dp.MDState(m, coord, vel, typ, mass, box, skin=0.3)
+        th_c = st2.step(20, 0.5, "fp64", thermo_every=4)
+        xc, vc, _, _ = st2.get()
+    finally:
+        os.environ.pop("DP_OZ_MIN_ATOMS", None)
+    assert stepb == stepa == 20 and nra > 1
+    np.testing.assert_array_equal(xb, xa)
+    np.testing.assert_array_equal(vb, va)
+    np.testing.assert_array_equal(th_b, th_a)
+    np.testing.assert_array_equal(xc, xa)
+    np.testing.assert_array_equal(vc, va)
+    np.testing.assert_array_equal(th_c[-len(th_a):], th_a)
+    for x in (r, st, st2):
+        x.close()
+    m.close()
+
+
 def test_checkpoint_resume(dp, tmp_path):
     """A state saved after 8 steps and resumed follows the uninterrupted run: the saved coordinates,
     velocities and step come back bit for bit, and the resumed steps match the uninterrupted ones
