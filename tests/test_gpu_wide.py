@@ -58,9 +58,13 @@ def test_wide_nets_match_oracle(dp, orc, w):
         print(name, cfg.embed, err)
         assert np.isfinite(F).all()
         assert err["dE"] < 2 * U and err["dEi"] < 4 * U and err["F"] < 20 * U and err["W"] < 10 * U
-        # a second call (graph replay of the evaluation) gives the same result up to atomics order
+        # a second call (graph replay of the evaluation) gives the same result up to the order of the
+        # FP32 atomic additions into the descriptor sums: each E_i then moves by at most about
+        # sum(sel) x 2^-24 of its size, so the total by that fraction of sum |E_i| (not of |E|, which
+        # can be far smaller than the sum of its terms)
         E2, _, F2, _ = nl.compute(coord, box, "bf16")
-        assert abs(E2 - E) <= 1e-6 * abs(E) and np.abs(F2 - F).max() <= 1e-4 * rms(F)
+        assert abs(E2 - E) <= sum(cfg.sel) * 2.0 ** -24 * np.abs(Eir).sum()
+        assert np.abs(F2 - F).max() <= 1e-4 * rms(F)
         nl.close()
         m.close()
 
