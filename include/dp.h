@@ -460,6 +460,24 @@ dp_status dp_ozaki_dgemm_dev(dp_model *m, int64_t M, int32_t N, int32_t K, const
  * Errors: DP_ERR_ARG (NULL model, unknown wait, polls out of range). */
 dp_status dp_test_starve_wait(dp_model *m, int32_t which, int64_t polls);
 
+/* Bounds-checked debug build (no counterpart in the paper; the stand-in for a
+ * device memory checker).  A library compiled with -DDP_BOUNDS_CHECK checks
+ * every index that its kernels read from memory or derive from coordinates
+ * (neighbor indexes of the candidate and formatted lists, cell indexes and
+ * cell-list slots, atoms of the tensor-core work lists, type ids read back
+ * from packed keys) against the buffer it addresses before using it; a bad
+ * index is not used (the neighbor counts as padding, the access is skipped)
+ * and the first one is recorded.  dp_bounds_checked() returns 1 for such a
+ * library and 0 for the default build.  dp_bounds_read() synchronises the
+ * device and writes rec[0] = number of bad indexes since the last clear,
+ * rec[1] = site of the first (1 type id, 2 cell index, 3 cell-list slot,
+ * 4 candidate atom, 5 formatted-list neighbor, 6 work-list atom), rec[2] =
+ * the index, rec[3] = the limit it broke; clear != 0 zeroes the record
+ * afterwards.  In the default build rec is all zeros.  rec: caller-owned
+ * host array of 4.  Errors: DP_ERR_ARG (NULL rec), DP_ERR_CUDA. */
+int32_t dp_bounds_checked(void);
+dp_status dp_bounds_read(int64_t *rec, int32_t clear);
+
 #ifdef __cplusplus
 }
 #endif

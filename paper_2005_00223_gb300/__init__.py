@@ -20,12 +20,13 @@ from ._lib import (DP_FP64, DP_MIX32, DP_MIX_BF16, DP_MIX_FP16, DPError, EXPORTS
                    dp_nlist_update_dev, dp_param_grad, dp_force_loss_grad, dp_force_loss_grad_dev, dp_adam_step,
                    dp_model_sync_params, dp_md_step_judged, dp_nlist_format_noalloc, dp_tanh_f64_dev,
                    dp_nlist_build_frames, dp_ozaki_dgemm_dev, dp_test_starve_wait,
-                   dp_md_set_rebuild_every, dp_nlist_set_centers, dp_halo_select_dev, dp_halo_accumulate_dev)
+                   dp_md_set_rebuild_every, dp_nlist_set_centers, dp_halo_select_dev, dp_halo_accumulate_dev,
+                   dp_bounds_checked, dp_bounds_read)
 
 
-def build(force: bool = False) -> str:
-    from .build import build as _build
-    return _build(force=force)
+def build(force: bool = False, bounds_check: bool = False) -> str:
+    from .builder import build as _build
+    return _build(force=force, bounds_check=bounds_check)
 
 
 # Live wrappers, released at interpreter exit in dependency order (MD states, then lists, then

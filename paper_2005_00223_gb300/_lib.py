@@ -16,6 +16,9 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libdp.so")
+# The bounds-checked debug build (build(bounds_check=True)); a process selects it by setting
+# DP_LIBRARY=bounds before its first load().
+BOUNDS_LIB_PATH = os.path.join(_HERE, "_build_bounds", "libdp.so")
 
 DP_OK = 0
 STATUS = {0: "DP_OK", -1: "DP_ERR_ARG", -2: "DP_ERR_CUDA", -3: "DP_ERR_OOM", -4: "DP_ERR_BOX",
@@ -34,7 +37,7 @@ EXPORTS = [
     "dp_force_loss_grad_dev", "dp_adam_step", "dp_model_sync_params", "dp_md_step_judged",
     "dp_nlist_format_noalloc", "dp_tanh_f64_dev", "dp_nlist_build_frames", "dp_ozaki_dgemm_dev",
     "dp_test_starve_wait", "dp_md_set_rebuild_every", "dp_nlist_set_centers", "dp_halo_select_dev",
-    "dp_halo_accumulate_dev",
+    "dp_halo_accumulate_dev", "dp_bounds_checked", "dp_bounds_read",
 ]
 
 
@@ -54,12 +57,14 @@ _lock = threading.Lock()
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libdp.so; raises if it has not been built."""
+def load(path: str = None):
+    """Load libdp.so (the bounds-checked build when DP_LIBRARY=bounds); raises if it has not been built."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
+        if path is None:
+            path = BOUNDS_LIB_PATH if os.environ.get("DP_LIBRARY") == "bounds" else LIB_PATH
         if not os.path.exists(path):
             raise RuntimeError(f"libdp is not built ({path} missing): run paper_2005_00223_gb300.build()")
         lib = C.CDLL(path)
@@ -88,6 +93,8 @@ def load(path: str = LIB_PATH):
             "dp_nlist_build_frames": ([P, I32, I64, P, P, P, D, D, I32, P], C.c_int),
             "dp_ozaki_dgemm_dev": ([P, I64, I32, I32, P, P, P, P], C.c_int),
             "dp_test_starve_wait": ([P, I32, I64], C.c_int),
+            "dp_bounds_checked": ([], C.c_int32),
+            "dp_bounds_read": ([P, I32], C.c_int),
             "dp_md_set_rebuild_every": ([P, I32], C.c_int),
             "dp_nlist_set_centers": ([P, I64], C.c_int),
             "dp_halo_select_dev": ([I64, P, P, D, D, D, I64, P, P, P, P, P], C.c_int),
@@ -331,6 +338,18 @@ def dp_ozaki_dgemm_dev(m, d_A, d_Bt, d_C, stream=None):
 def dp_test_starve_wait(m, which: int, polls: int = 0):
     """Starve one bounded device wait of the model's later evaluations (1), or restore (0)."""
     _check(load().dp_test_starve_wait(m, int(which), int(polls)), "dp_test_starve_wait")
+
+
+def dp_bounds_checked() -> bool:
+    """True when the loaded library is the bounds-checked debug build."""
+    return bool(load().dp_bounds_checked())
+
+
+def dp_bounds_read(clear: bool = True):
+    """(count, site, index, limit) of the bad indexes the bounds-checked build found (zeros otherwise)."""
+    rec = np.zeros(4, dtype=np.int64)
+    _check(load().dp_bounds_read(_ptr(rec), int(bool(clear))), "dp_bounds_read")
+    return tuple(int(v) for v in rec)
 
 
 def dp_nlist_set_centers(nl, n_centers: int):

@@ -1,4 +1,7 @@
-"""Build step of libdp: nvcc for sm_103a, one object per .cu file in parallel, linked into _build/libdp.so."""
+"""Build step of libdp: nvcc for sm_103a, one object per .cu file in parallel, linked into _build/libdp.so.
+
+build(bounds_check=True) makes the bounds-checked debug build (-DDP_BOUNDS_CHECK) in _build_bounds/.
+"""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -11,7 +14,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
-LIB = os.path.join(OUT, "libdp.so")
+OUT_BOUNDS = os.path.join(HERE, "_build_bounds")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]
@@ -31,8 +34,11 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, bounds_check: bool = False) -> str:
+    out = OUT_BOUNDS if bounds_check else OUT
+    lib = os.path.join(out, "libdp.so")
+    flags = FLAGS + (["-DDP_BOUNDS_CHECK"] if bounds_check else [])
+    os.makedirs(out, exist_ok=True)
     nvcc = _nvcc()
     sources = sorted(glob.glob(os.path.join(SRC, "*.cu")))
     headers = sorted(glob.glob(os.path.join(SRC, "*.cuh"))) + sorted(glob.glob(os.path.join(SRC, "*.inc"))) + [
@@ -40,10 +46,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = []
     jobs = []
     for src in sources:
-        obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
-            cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+            cmd = [nvcc, *ARCH, *flags, "-c", src, "-o", obj]
             jobs.append(cmd)
 
     def run(cmd):
@@ -57,16 +63,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
                     sys.stderr.write(r.stdout + r.stderr)
                 if r.returncode != 0:
                     raise RuntimeError(f"nvcc failed: {' '.join(cmd)}")
-    if force or _stale(LIB, objs):
-        tmp = LIB + f".{os.getpid()}.tmp"
+    if force or _stale(lib, objs):
+        tmp = lib + f".{os.getpid()}.tmp"
         cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link failed")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, bounds_check="--bounds-check" in sys.argv))

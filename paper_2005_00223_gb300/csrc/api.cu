@@ -111,6 +111,7 @@ dp_status compute_device(dp_model *m, dp_nlist *nl, const double *d_coord, dp_pr
                          double *d_atom_energy, double *d_force, double *d_virial, double *d_atom_virial,
                          cudaStream_t st)
 {
+    m->dev.n_list = nl->n;
     DP_TRY(nlist_format_device(m, nl, d_coord, st,
                                prec == DP_MIX_BF16 || prec == DP_MIX_FP16 || prec == DP_MIX_BF16X3 ||
                                    prec == DP_MIX_FP8));

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/dp.h"
+#include "bounds.cuh"
 
 namespace dp {
 
@@ -76,6 +77,9 @@ struct ModelDev {
     // into these fixed-point limb arrays (3 limbs per value) instead of FP64 atomics; null: FP64
     // atomics.  Set for the duration of one evaluation.
     unsigned long long *fx, *fxv;
+    // Atoms of the list being evaluated (centers and ghosts), set at the start of each evaluation:
+    // the limit of the neighbor indexes that the bounds-checked build checks.
+    int64_t n_list;
 };
 
 // Order-independent accumulation of v: an exact fixed-point number with 64 fractional bits, its

@@ -73,8 +73,8 @@ __device__ __forceinline__ void env_tangent(const ModelDev &md, const BoxDev &bx
                                             int c0, int cnt, int n, Real *sR, Real *sRd)
 {
     double R[4] = {0, 0, 0, 0}, Rd[4] = {0, 0, 0, 0};
-    if (c0 + n < cnt) {
-        const int j = nlist[(int64_t)i * md.nsel + md.sel_off[tj] + c0 + n];
+    const int j = c0 + n < cnt ? nlist[(int64_t)i * md.nsel + md.sel_off[tj] + c0 + n] : -1;
+    if (c0 + n < cnt && DP_IDX_OK(j, md.n_list, BS_NLIST_J)) {
         double d[3], J[12];
         const double r = min_image_r(pi, pos[j], bx, d);
         env_row(d, r, md.rcs, md.rcut, R, J);
@@ -734,6 +734,7 @@ template <class S, typename Real>
 dp_status run_grad(dp_model *m, dp_nlist *nl, const double *d_v, const double *d_ab, double *d_E_atom,
                    double *d_Ed_atom, double *d_grad, cudaStream_t st)
 {
+    m->dev.n_list = nl->n;
     const ModelDev &md = m->dev;
     const int64_t n = nl->n;
     const FitRec fr = make_fit_rec(md);
@@ -798,6 +799,8 @@ dp_status run_grad(dp_model *m, dp_nlist *nl, const double *d_v, const double *d
 }
 
 }  // namespace
+
+DP_BOUNDS_ACCESSOR(bounds_read_grad)
 
 dp_status param_grad_device(dp_model *m, dp_nlist *nl, const double *d_v, const double *d_ab, dp_precision prec,
                             double *d_E_atom, double *d_Ed_atom, double *d_grad, cudaStream_t st)

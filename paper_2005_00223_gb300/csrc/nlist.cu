@@ -65,8 +65,9 @@ __global__ void __launch_bounds__(1024) k_cell_assign_scan(int64_t n, int64_t nc
         int cz = cell_coord(p.z, bx.invL[2], bx.nc[2]);
         // each frame has its own block of cells, so no candidate crosses frames
         int c = (int)(i / bx.frame_n) * bx.ncell_f + (cx * bx.nc[1] + cy) * bx.nc[2] + cz;
+        if (!DP_IDX_OK(c, ncell, BS_CELL)) c = -1;
         cell_of[i] = c;
-        atomicAdd(&cnt[c], 1);
+        if (c >= 0) atomicAdd(&cnt[c], 1);
     }
     __threadfence();
     __syncthreads();
@@ -96,14 +97,16 @@ __global__ void __launch_bounds__(1024) k_cell_assign_scan(int64_t n, int64_t nc
     if (tid == nt - 1) start[ncell] = part[tid];
     if (tid == 0) flags[3] = 0;
 }
-__global__ void k_cell_fill(int64_t n, const int32_t *cell_of, const int32_t *start, int32_t *cursor,
+__global__ void k_cell_fill(int64_t n, int64_t ncell, const int32_t *cell_of, const int32_t *start, int32_t *cursor,
                             int32_t *atoms, const int32_t *flags, int cond)
 {
     if (skip(flags, cond)) return;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     int c = cell_of[i];
-    atoms[start[c] + atomicAdd(&cursor[c], 1)] = (int32_t)i;
+    if (!DP_IDX_OK(c, ncell, BS_CELL)) return;
+    const int64_t slot = start[c] + atomicAdd(&cursor[c], 1);
+    if (DP_IDX_OK(slot, n, BS_CELL_SLOT)) atoms[slot] = (int32_t)i;
 }
 
 // One warp per atom: every j != i in the surrounding cells whose
@@ -133,6 +136,10 @@ __global__ void k_candidates(int64_t n, const Pos4 *__restrict__ pos, const floa
     const float iLf[3] = {(float)bx.invL[0], (float)bx.invL[1], (float)bx.invL[2]};
     const float rpre = (float)rlist + 2e-3f;
     const int cf = cell_of[i];
+    if (!DP_IDX_OK(cf, ncell, BS_CELL)) {
+        if (lane == 0) cand_cnt[i] = 0;
+        return;
+    }
     const int fbase = (cf / bx.ncell_f) * bx.ncell_f;      // first cell of this atom's frame
     const int c = cf - fbase;
     const int c3[3] = {c / (bx.nc[1] * bx.nc[2]), (c / bx.nc[2]) % bx.nc[1], c % bx.nc[2]};
@@ -158,7 +165,7 @@ __global__ void k_candidates(int64_t n, const Pos4 *__restrict__ pos, const floa
                     int32_t j = -1;
                     if (p < s1) {
                         j = atoms[p];
-                        if (j != i) {
+                        if (j != i && DP_IDX_OK(j, n, BS_CAND_J)) {
                             const float4 qf = posf[j];
                             float df[3] = {qf.x - pf.x, qf.y - pf.y, qf.z - pf.z};
 #pragma unroll
@@ -274,7 +281,7 @@ __global__ void k_format(int64_t n, const Pos4 *__restrict__ pos, const float4 *
             const int c = base + lane;
             bool pass = false;
             uint32_t e = 0;
-            if (c < nc) {
+            if (c < nc && DP_IDX_OK(row[c], n, BS_CAND_J)) {
                 const int32_t j = row[c];
                 const float4 qf = posf[j];
                 float df[3] = {qf.x - pf.x, qf.y - pf.y, qf.z - pf.z};
@@ -337,6 +344,7 @@ __global__ void k_format(int64_t n, const Pos4 *__restrict__ pos, const float4 *
         int rank = 0;
         for (int q = 0; q < nk; ++q) rank += keys[q] < k;
         int t = (int)(k >> 56);
+        if (!DP_IDX_OK(t, md.ntypes, BS_TYPE)) continue;
         int local = rank - tstart[t];
         if (local < md.sel[t]) {
             const int slot = md.sel_off[t] + local;
@@ -372,6 +380,8 @@ inline unsigned blocks_for(int64_t work, int per) { return (unsigned)((work + pe
 
 }  // namespace
 
+DP_BOUNDS_ACCESSOR(bounds_read_nlist)
+
 dp_status pack_positions(dp_nlist *nl, const double *d_coord, cudaStream_t st)
 {
     if (nl->n == 0) return DP_OK;
@@ -393,7 +403,7 @@ dp_status nlist_build_device(dp_nlist *nl, cudaStream_t st, bool conditional)
     ProfScope ps(nl->m->prof, PG_BUILD, 3, st);
     k_cell_assign_scan<<<blocks_for(nl->n, 1024), 1024, 0, st>>>(nl->n, nl->ncell, pos, bx, nl->d_cell_of,
                                                               nl->d_cell_cnt, nl->d_cell_start, nl->d_flags, cond);
-    k_cell_fill<<<blocks_for(nl->n, 256), 256, 0, st>>>(nl->n, nl->d_cell_of, nl->d_cell_start, nl->d_cell_cnt,
+    k_cell_fill<<<blocks_for(nl->n, 256), 256, 0, st>>>(nl->n, nl->ncell, nl->d_cell_of, nl->d_cell_start, nl->d_cell_cnt,
                                                        nl->d_cell_atoms, nl->d_flags, cond);
     k_candidates<<<blocks_for(nl->n * 32, 256), 256, 0, st>>>(nl->n, pos, (const float4 *)nl->d_posf, bx, nl->rlist,
                                                              nl->d_cell_of,

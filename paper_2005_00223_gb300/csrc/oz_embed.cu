@@ -137,12 +137,14 @@ __global__ void __launch_bounds__(128) k_ozf_front(ModelDev md, BoxDev bx, const
             cur = net;
         }
         const int4 c4 = chunks[(int64_t)t * 4 + warp];
-        const int a = c4.x, tj = net % md.ntypes;
+        int a = c4.x;
+        if (a >= 0 && !DP_IDX_OK(a, md.n_list, BS_CHUNK_ATOM)) a = -1;
+        const int tj = net % md.ntypes;
         const int cnt = a >= 0 ? nnei[(int64_t)a * md.ntypes + tj] : 0;
         const bool valid = c4.z + lane < cnt;
         double R[4] = {0.0, 0.0, 0.0, 0.0};
-        if (valid) {
-            const int j = nlist[(int64_t)a * md.nsel + md.sel_off[tj] + c4.z + lane];
+        const int j = valid ? nlist[(int64_t)a * md.nsel + md.sel_off[tj] + c4.z + lane] : -1;
+        if (valid && DP_IDX_OK(j, md.n_list, BS_NLIST_J)) {
             double d[3], J[12];
             const double r = min_image_r(pos[a], pos[j], bx, d);
             env_row(d, r, md.rcs, md.rcut, R, J);
@@ -589,6 +591,7 @@ struct Bwd4Epi {
         const int warp = tid >> 5, lane = tid & 31, quarter = warp & 3, part = warp >> 2;
         const int4 c4 = chunks[tile * 4 + quarter];
         if (c4.x < 0) return;   // a padding chunk: the quarter's warps skip
+        if (!DP_IDX_OK(c4.x, md.n_list, BS_CHUNK_ATOM)) return;
         const int a = c4.x, net = c4.w, tj = net % md.ntypes;
         const int rt = quarter * 32 + lane;
         const int64_t row = tile * 128 + rt;
@@ -608,12 +611,12 @@ struct Bwd4Epi {
         double fi[3] = {0.0, 0.0, 0.0}, vir[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) vir[q] = 0.0;
-        if (valid) {
+        const int j = valid ? nlist[(int64_t)a * md.nsel + md.sel_off[tj] + c4.z + lane] : -1;
+        if (valid && DP_IDX_OK(j, md.n_list, BS_NLIST_J)) {
             double dR[4];
 #pragma unroll
             for (int c = 0; c < 4; ++c) dR[c] = dRbuf[(tile * 4 + c) * 128 + rt];
             dR[0] += ds;
-            const int j = nlist[(int64_t)a * md.nsel + md.sel_off[tj] + c4.z + lane];
             double d[3], Rr[4], J[12];
             const double r = min_image_r(pos[a], pos[j], bx, d);
             env_row(d, r, md.rcs, md.rcut, Rr, J);
@@ -862,6 +865,8 @@ int shape_of(const ModelDev &md)
 }
 
 }  // namespace
+
+DP_BOUNDS_ACCESSOR(bounds_read_oz_embed)
 
 bool oz_emb_ok(const ModelDev &md) { return shape_of(md) != 0 && getenv("DP_NO_OZAKI") == nullptr; }
 

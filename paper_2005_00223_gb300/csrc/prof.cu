@@ -106,6 +106,39 @@ dp_status dp_test_starve_wait(dp_model *m, int32_t which, int64_t polls)
     return DP_OK;
 }
 
+int32_t dp_bounds_checked(void)
+{
+#ifdef DP_BOUNDS_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+dp_status dp_bounds_read(int64_t *rec, int32_t clear)
+{
+    if (!rec) {
+        set_error("dp_bounds_read: NULL record");
+        return DP_ERR_ARG;
+    }
+    DP_CUDA(cudaDeviceSynchronize());
+    cudaError_t (*const readers[])(unsigned long long *, bool) = {
+        bounds_read_nlist, bounds_read_simt, bounds_read_oz_embed, bounds_read_tc,
+        bounds_read_tc_x3, bounds_read_wide, bounds_read_grad};
+    unsigned long long total = 0, first[4] = {0ull, 0ull, 0ull, 0ull};
+    for (auto rd : readers) {
+        unsigned long long r[4];
+        DP_CUDA(rd(r, clear != 0));
+        if (r[0] && !total) {
+            for (int k = 1; k < 4; ++k) first[k] = r[k];
+        }
+        total += r[0];
+    }
+    rec[0] = (int64_t)total;
+    for (int k = 1; k < 4; ++k) rec[k] = (int64_t)first[k];
+    return DP_OK;
+}
+
 dp_status dp_model_set_stream(dp_model *m, void *stream)
 {
     if (!m) {

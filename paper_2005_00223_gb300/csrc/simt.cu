@@ -141,9 +141,11 @@ __global__ void __launch_bounds__(S::NT) k_embed_fwd(ModelDev md, BoxDev bx, con
                 double R[4] = {0.0, 0.0, 0.0, 0.0};
                 if (c0 + n < cnt) {
                     int j = nlist[(int64_t)i * md.nsel + md.sel_off[tj] + c0 + n];
-                    double d[3], J[12];
-                    double r = min_image_r(pi, pos[j], bx, d);
-                    env_row(d, r, md.rcs, md.rcut, R, J);
+                    if (DP_IDX_OK(j, md.n_list, BS_NLIST_J)) {
+                        double d[3], J[12];
+                        double r = min_image_r(pi, pos[j], bx, d);
+                        env_row(d, r, md.rcs, md.rcut, R, J);
+                    }
                 }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) sR[n * 4 + c] = (Real)R[c];
@@ -448,8 +450,12 @@ __global__ void __launch_bounds__(S::NT) k_embed_bwd(ModelDev md, BoxDev bx, con
                 for (int q = 0; q < 12; ++q) J[q] = 0.0;
                 if (c0 + n < cnt) {
                     j = nlist[(int64_t)i * md.nsel + md.sel_off[tj] + c0 + n];
-                    double r = min_image_r(pi, pos[j], bx, d);
-                    env_row(d, r, md.rcs, md.rcut, R, J);
+                    if (DP_IDX_OK(j, md.n_list, BS_NLIST_J)) {
+                        double r = min_image_r(pi, pos[j], bx, d);
+                        env_row(d, r, md.rcs, md.rcut, R, J);
+                    } else {
+                        j = -1;
+                    }
                 }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) sR[n * 4 + c] = (Real)R[c];
@@ -521,7 +527,7 @@ __global__ void __launch_bounds__(S::NT) k_embed_bwd(ModelDev md, BoxDev bx, con
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     fi[k] += gv[k];
-                    acc_add(md.fx, force, 3 * (int64_t)j + k, -gv[k]);
+                    if (j >= 0) acc_add(md.fx, force, 3 * (int64_t)j + k, -gv[k]);
                 }
 #pragma unroll
                 for (int a = 0; a < 3; ++a)
@@ -888,6 +894,8 @@ dp_status compute_simt(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
 }
 
 }  // namespace
+
+DP_BOUNDS_ACCESSOR(bounds_read_simt)
 
 // Embedding shapes compiled into the SIMT and tensor-core kernels.
 bool embed_shape_supported(int n_embed, const int *e)

@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_tc(ModelDev md, const 
                 tc::tmem_ld4(taddr + 16 * q, v);
                 tc::tmem_ld_wait();
                 const int atom = load_chunk(chunks, (int64_t)tile * 4 + q).x;
-                if (atom >= 0 && m < S::E2) {
+                if (atom >= 0 && m < S::E2 && DP_IDX_OK(atom, md.n_list, BS_CHUNK_ATOM)) {
                     float *Tm = T + (int64_t)atom * 4 * S::E2 + 4 * m;
 #pragma unroll
                     for (int c = 0; c < 4; ++c) atomicAdd(Tm + c, v[c]);
@@ -1309,6 +1309,8 @@ dp_status run_tc(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
 }
 
 }  // namespace
+
+DP_BOUNDS_ACCESSOR(bounds_read_tc)
 
 // Scratch of build_chunks_batch for nb positions.
 size_t chunks_batch_scratch(const ModelDev &md, int64_t nb)

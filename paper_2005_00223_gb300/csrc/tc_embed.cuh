@@ -141,7 +141,9 @@ __device__ __forceinline__ RowIn fetch_row(const ModelDev &md, const int4 *__res
     const int4 c4 = chunks[(int64_t)tile * 4 + warp];
     r.net = chunks[(int64_t)tile * 4].w;
     r.ch = TileCtx{c4.x, c4.y, c4.z, c4.w};
-    if (c4.x >= 0) {
+    if (c4.x >= 0 && !(DP_IDX_OK(c4.x, md.n_list, BS_CHUNK_ATOM) && DP_IDX_OK(c4.y, md.ntypes, BS_TYPE)))
+        r.ch.atom = -1;   // bounds-checked build: a bad chunk is treated as padding
+    if (r.ch.atom >= 0) {
         const int k = c4.z + lane;
         r.cnt = nnei[(int64_t)c4.x * md.ntypes + c4.y];
         if (k < md.sel[c4.y]) {
@@ -150,6 +152,7 @@ __device__ __forceinline__ RowIn fetch_row(const ModelDev &md, const int4 *__res
             if (BWD) {
                 r.b = envB[slot];
                 r.j = nlist[slot];
+                if (r.j >= 0 && !DP_IDX_OK(r.j, md.n_list, BS_NLIST_J)) r.j = -2;   // bounds-checked build
             }
         }
     }
@@ -163,7 +166,8 @@ template <class S, int BF, bool BWD>
 __device__ __forceinline__ void rows_layer1(const RowIn &in, int lane, int row, const float *vec, unsigned char *A2,
                                             float Rf[4], float t1[S::E0], float geo[6], int &j, bool &valid)
 {
-    valid = in.ch.atom >= 0 && in.ch.c0 + lane < in.cnt;
+    // (j = -2 only in the bounds-checked build: a neighbor index outside the list, not used)
+    valid = in.ch.atom >= 0 && in.ch.c0 + lane < in.cnt && in.j != -2;
     const float4 a = valid ? in.a : make_float4(0.f, 0.f, 0.f, 0.f);
     const float2 b = valid ? in.b : make_float2(0.f, 0.f);
     j = valid ? in.j : -1;

@@ -115,7 +115,8 @@ __device__ __forceinline__ void rows_layer1_x3(const RowIn &in, int lane, int ro
                                                unsigned char *A2L, float Rf[4], float t1[S::E0], float geo[6], int &j,
                                                bool &valid)
 {
-    valid = in.ch.atom >= 0 && in.ch.c0 + lane < in.cnt;
+    // (j = -2 only in the bounds-checked build: a neighbor index outside the list, not used)
+    valid = in.ch.atom >= 0 && in.ch.c0 + lane < in.cnt && in.j != -2;
     const float4 a = valid ? in.a : make_float4(0.f, 0.f, 0.f, 0.f);
     const float2 b = valid ? in.b : make_float2(0.f, 0.f);
     j = valid ? in.j : -1;
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(kTcThreads) k_embed_fwd_x3(ModelDev md, const 
                 tc::tmem_ld4(taddr + 16 * q, v);
                 tc::tmem_ld_wait();
                 const int atom = load_chunk(chunks, (int64_t)tile * 4 + q).x;
-                if (atom >= 0 && m < S::E2) {
+                if (atom >= 0 && m < S::E2 && DP_IDX_OK(atom, md.n_list, BS_CHUNK_ATOM)) {
                     float *Tm = T + (int64_t)atom * 4 * S::E2 + 4 * m;
 #pragma unroll
                     for (int c = 0; c < 4; ++c) atomicAdd(Tm + c, v[c]);
@@ -1163,6 +1164,8 @@ dp_status run_x3(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_ene
 }
 
 }  // namespace
+
+DP_BOUNDS_ACCESSOR(bounds_read_tc_x3)
 
 dp_status pack_x3_weights(dp_model *m)
 {

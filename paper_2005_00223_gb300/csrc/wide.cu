@@ -114,14 +114,18 @@ __device__ __forceinline__ WRow wide_row(const ModelDev &md, const WideArgs &w, 
     o.j = -1;
     o.a = make_float4(0.f, 0.f, 0.f, 0.f);
     o.b = make_float2(0.f, 0.f);
-    if (c4.x >= 0) {
+    if (c4.x >= 0 && !(DP_IDX_OK(c4.x, md.n_list, BS_CHUNK_ATOM) && DP_IDX_OK(c4.y, md.ntypes, BS_TYPE)))
+        o.atom = -1;   // bounds-checked build: a bad chunk is treated as padding
+    if (o.atom >= 0) {
         const int k = c4.z + (r & 31);
         if (k < w.nnei[(int64_t)c4.x * md.ntypes + c4.y]) {
             const int64_t slot = (int64_t)c4.x * md.nsel + md.sel_off[c4.y] + k;
-            o.valid = true;
-            o.a = w.envA[slot];
-            o.b = w.envB[slot];
             o.j = w.nlist[slot];
+            o.valid = DP_IDX_OK(o.j, md.n_list, BS_NLIST_J);
+            if (o.valid) {
+                o.a = w.envA[slot];
+                o.b = w.envB[slot];
+            }
         }
     }
     return o;
@@ -584,7 +588,7 @@ __global__ void __launch_bounds__(128) k_wide_force(ModelDev md, WideArgs w)
 #pragma unroll
     for (int q = 0; q < 9; ++q)
         for (int o = 16; o > 0; o >>= 1) vir[q] += __shfl_xor_sync(0xffffffffu, vir[q], o);
-    const int atom = w.chunks[tile * 4 + (tid >> 5)].x;
+    const int atom = row.atom;
     if (atom >= 0) {
         if (lane < 3) {
             const float v = lane == 0 ? gv[0] : (lane == 1 ? gv[1] : gv[2]);
@@ -873,6 +877,8 @@ dp_status run_wide(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_e
 }
 
 }  // namespace
+
+DP_BOUNDS_ACCESSOR(bounds_read_wide)
 
 dp_status compute_wide(dp_model *m, dp_nlist *nl, int fp8, double *d_energy, double *d_atom_energy, double *d_force,
                        double *d_virial, double *d_atom_virial, cudaStream_t st)

@@ -2,6 +2,7 @@
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -53,3 +54,18 @@ def test_missing_library_fails_loudly(tmp_path):
             _lib.load(str(tmp_path / "nope.so"))
     finally:
         _lib._lib = saved
+
+
+def test_bounds_checked_build_compiles_and_reports_itself():
+    """The debug build with every index check compiled in builds for sm_103a and exports the same
+    entry points; dp_bounds_checked() tells the two builds apart without a GPU."""
+    import paper_2005_00223_gb300 as pkg
+    path = pkg.build(bounds_check=True)
+    assert path.endswith(os.path.join("_build_bounds", "libdp.so"))
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (dp_[a-z0-9_]+)$", out, flags=re.M))
+    assert not [d for d in _declared() if d not in exported]
+    code = ("import ctypes, sys; a = ctypes.CDLL(sys.argv[1]); b = ctypes.CDLL(sys.argv[2]); "
+            "print(a.dp_bounds_checked(), b.dp_bounds_checked())")
+    r = subprocess.run([sys.executable, "-c", code, path, pkg.build()], capture_output=True, text=True, check=True)
+    assert r.stdout.split() == ["1", "0"]
