@@ -30,7 +30,7 @@ __all__ = [
     "SplitMix64", "ModelConfig", "water_config", "copper_config",
     "copper_student_config", "param_shapes", "n_params", "model_params", "scale_output",
     "water_box", "replicate", "copper_fcc", "velocities", "MASS",
-    "KB_EV", "MVV2E",
+    "KB_EV", "MVV2E", "morse_copper", "MORSE_CU", "morse_frames",
 ]
 
 # Boltzmann constant in eV/K and the factor that turns amu*A^2/fs^2 into eV
@@ -346,3 +346,68 @@ def velocities(mass: np.ndarray, temperature: float, seed: int) -> np.ndarray:
     if t_now > 0:
         v *= math.sqrt(temperature / t_now)
     return v
+
+
+# Morse pair potential of copper, V(r) = D (exp(-2 a (r - r0)) - 2 exp(-a (r - r0))), with the
+# parameters of Girifalco and Weizer, "Application of the Morse potential function to cubic metals",
+# Phys. Rev. 114, 687 (1959): D in eV, a in 1/A, r0 in A.
+MORSE_CU = {"D": 0.3429, "a": 1.3588, "r0": 2.866}
+
+
+def morse_copper(coord: np.ndarray, box: np.ndarray, rcut: float = 8.0, chunk: int = 256):
+    """Energy (eV) and forces (eV/A) of copper under the Morse pair potential, shifted-force at rcut.
+
+    A classical reference for labels only: a stand-in for the first-principles data the paper's
+    models are fitted to, used to fit the full copper model once so that its own MD stays a crystal
+    (a seeded random-weight model has no stable lattice).  It is not part of the method.  Pairs under
+    the minimum image of the orthorhombic box; V_sf(r) = V(r) - V(rc) - (r - rc) V'(rc) for r < rc,
+    so energy and force both vanish at rc.  Rows of `chunk` atoms at a time (O(n^2) pairs).
+    """
+    D, a, r0 = MORSE_CU["D"], MORSE_CU["a"], MORSE_CU["r0"]
+    x = np.asarray(coord, dtype=np.float64)
+    n = x.shape[0]
+    L = np.diag(np.asarray(box, dtype=np.float64))
+
+    def v_dv(r):
+        e1 = np.exp(-a * (r - r0))
+        return D * (e1 * e1 - 2.0 * e1), -2.0 * a * D * (e1 * e1 - e1)
+
+    vc, dvc = v_dv(np.float64(rcut))
+    energy = 0.0
+    force = np.zeros((n, 3))
+    for i0 in range(0, n, chunk):
+        i1 = min(n, i0 + chunk)
+        d = x[None, :, :] - x[i0:i1, None, :]          # r_j - r_i
+        d -= L * np.rint(d / L)
+        r = np.sqrt((d * d).sum(-1))
+        idx = np.arange(i0, i1)
+        r[idx - i0, idx] = np.inf
+        m = r < rcut
+        rr = np.where(m, r, rcut)
+        v, dv = v_dv(rr)
+        vsf = np.where(m, v - vc - (rr - rcut) * dvc, 0.0)
+        dvsf = np.where(m, dv - dvc, 0.0)
+        energy += 0.5 * float(vsf.sum())
+        # dE/dr_i = sum_j V'(r_ij) (r_i - r_j) / r_ij, F_i = -dE/dr_i
+        force[i0:i1] = ((dvsf / rr)[:, :, None] * d).sum(1)
+    return energy, force
+
+
+def morse_frames(nframes: int, seed: int = 100, ncell: int = 5, sigma_min: float = 0.02, sigma_max: float = 0.18):
+    """Labelled copper frames for fitting a model to the Morse reference (morse_copper).
+
+    Frame k is the FCC supercell of `ncell`^3 cells (a = 3.634 A) with seeded N(0, sigma_k^2)
+    displacements, sigma_k spread over [sigma_min, sigma_max] by the golden-ratio sequence (about
+    the thermal displacements of a copper crystal from 50 K to 2,000 K).  Returns (coords [F, n, 3],
+    energies [F], forces [F, n, 3], types [n], box [3, 3]).
+    """
+    xs, es, fs = [], [], []
+    typ = box = None
+    for k in range(nframes):
+        sig = sigma_min + (sigma_max - sigma_min) * ((k * 0.6180339887498949) % 1.0)
+        c, typ, box = copper_fcc(seed + k, ncell=ncell, sigma=sig)
+        e, f = morse_copper(c, box)
+        xs.append(c)
+        es.append(e)
+        fs.append(f)
+    return np.array(xs), np.array(es), np.array(fs), typ, box

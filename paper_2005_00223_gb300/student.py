@@ -16,18 +16,19 @@ from . import MDState, Model, NeighborList, _lib
 
 
 def teacher_frames(teacher: Model, coord, typ, box, mass_by_type, velocities, nframes: int, stride: int,
-                   dt_fs: float, md_prec="mix32", label_prec="mix32", skin: float = 2.0):
+                   dt_fs: float, md_prec="mix32", label_prec="mix32", skin: float = 2.0, return_temps: bool = False):
     """Frames sampled every `stride` NVE steps of the teacher, one run per initial velocity set.
 
     Returns (coords [F, n, 3], energies [F], forces [F, n, 3]) as numpy arrays, labelled by the
-    teacher in `label_prec`.
+    teacher in `label_prec`; with return_temps also the instantaneous temperature (K) of each frame.
     """
-    xs, es, fs = [], [], []
+    xs, es, fs, ts = [], [], [], []
     for vel in velocities:
         st = MDState(teacher, coord, vel, typ, mass_by_type, box, skin=skin)
         nl = NeighborList(teacher, coord, typ, box, skin=skin)
         for _ in range(nframes):
-            st.step(stride, dt_fs, md_prec)
+            th = st.step(stride, dt_fs, md_prec, thermo_every=stride)
+            ts.append(float(np.asarray(th)[-1][2]))
             x, _, _, _ = st.get()
             nl.update(x, box)
             E, _, F, _ = nl.compute(x, box, label_prec)
@@ -36,6 +37,8 @@ def teacher_frames(teacher: Model, coord, typ, box, mass_by_type, velocities, nf
             fs.append(F)
         st.close()
         nl.close()
+    if return_temps:
+        return np.array(xs), np.array(es), np.array(fs), np.array(ts)
     return np.array(xs), np.array(es), np.array(fs)
 
 
@@ -81,6 +84,37 @@ def train(student: Model, typ, box, coords, energies, forces, steps: int, lr0: f
     _lib.dp_model_sync_params(student.h)
     _lib.dp_model_set_stream(student.h, None)
     return log
+
+
+def fit_to_reference(model: Model, coords, energies, forces, typ, box, steps: int, lr0: float = 2e-3,
+                     lr1: float = 2e-5, p_e: float = 0.02, p_f: float = 100.0, segments: int = 4, prec="mix32"):
+    """Fits a full model to labelled reference frames (e.g. a classical potential's) with the same
+    kernels as the distillation: one-frame Adam steps on the force-matching loss, the learning rate
+    decaying lr0 -> lr1 over `segments` restarts of train() (each reshuffles the frames).  A large
+    force weight against a small energy weight (p_f / p_e = 5,000) fits the forces first, as
+    DeePMD-kit's training schedule starts.  Returns the concatenated loss log."""
+    log = []
+    per = max(1, steps // segments)
+    for k in range(segments):
+        a = lr0 * (lr1 / lr0) ** (k / segments)
+        z = lr0 * (lr1 / lr0) ** ((k + 1) / segments)
+        log += train(model, typ, box, coords, energies, forces, steps=per, lr0=a, lr1=z, p_e=p_e, p_f=p_f,
+                     prec=prec, seed=k, log_every=max(1, per // 5))
+    return log
+
+
+def force_rmse_vs_labels(model: Model, coords, forces, typ, box, prec="mix32"):
+    """Force RMSE of a model against labelled frames, and the RMS of the labels."""
+    nl = NeighborList(model, coords[0], typ, box)
+    se, sf, cnt = 0.0, 0.0, 0
+    for x, f in zip(coords, forces):
+        nl.update(x, box)
+        F = nl.compute(x, box, prec)[2]
+        se += float(((F - f) ** 2).sum())
+        sf += float((f ** 2).sum())
+        cnt += len(typ)
+    nl.close()
+    return math.sqrt(se / cnt), math.sqrt(sf / cnt)
 
 
 def force_rmse(a: Model, b: Model, coords, typ, box, prec_a="mix32", prec_b="mix32"):

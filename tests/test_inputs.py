@@ -100,3 +100,28 @@ def test_paper_water_model_and_system():
     np.testing.assert_allclose(np.diag(box), 4 * 12.42)
     # replica k of atom i sits at coord[i] + the replica's box offset
     np.testing.assert_allclose(coord[5 * 192 + 7] - coord[7], [0.0, 12.42, 12.42])   # replica (0, 1, 1)
+
+
+def test_morse_reference_forces_are_minus_energy_gradient():
+    """The Morse copper reference used to fit config 4's teacher: forces are minus the central
+    differences of its energy, they sum to zero, the perfect lattice is force free, and the
+    shifted-force form takes energy and force of a pair to zero at the cut-off."""
+    c, t, b = dpsynth.copper_fcc(3, ncell=5, sigma=0.1)
+    E, F = dpsynth.morse_copper(c, b)
+    assert np.abs(F.sum(0)).max() < 1e-10
+    h = 1e-5
+    for i, k in ((7, 0), (123, 1), (401, 2)):
+        cp, cm = c.copy(), c.copy()
+        cp[i, k] += h
+        cm[i, k] -= h
+        fd = -(dpsynth.morse_copper(cp, b)[0] - dpsynth.morse_copper(cm, b)[0]) / (2 * h)
+        assert abs(fd - F[i, k]) < 1e-6 * max(1.0, abs(F[i, k]))
+    c0, _, _ = dpsynth.copper_fcc(3, ncell=5, sigma=0.0)
+    assert np.abs(dpsynth.morse_copper(c0, b)[1]).max() < 1e-10
+    box = np.diag([30.0, 30.0, 30.0])
+    for r in (8.0 - 1e-9, 8.0 + 1e-9):
+        pair = np.array([[1.0, 1.0, 1.0], [1.0 + r, 1.0, 1.0]])
+        e2, f2 = dpsynth.morse_copper(pair, box)
+        assert abs(e2) < 1e-12 and np.abs(f2).max() < 1e-9
+    frames = dpsynth.morse_frames(4)
+    assert frames[0].shape == (4, 500, 3) and frames[2].shape == (4, 500, 3)
