@@ -11,7 +11,7 @@
 // list (its own limits are checked on the host and flagged on the device).
 //
 // Each translation unit keeps its own record, a file-scope device array {count of bad indexes,
-// site, index, limit}; dp_bounds_read() (api.cu) collects and clears them.  In the default build
+// site, index, limit}; dp_bounds_read() (prof.cu) collects and clears them.  In the default build
 // every check is the constant `true` and the records hold zeros.
 #pragma once
 

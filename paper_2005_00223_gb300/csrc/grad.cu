@@ -21,7 +21,8 @@
 //   k_jvp_fit     A atoms per CTA: fitting primal + tangent, E_i, Edot_i,
 //                 reverse with (alpha, beta) -> D_bar, D'_bar; keeps layer
 //                 inputs and pre-activation adjoints for k_fit_wgrad.
-//   k_fit_wgrad   thread per fitting parameter: sums over the atoms of a type.
+//   k_fit_wgrad   the fitting net's weight gradient as tiled GEMMs over the atoms of
+//                 a type (split over chunks of atoms), k_fit_wgrad_reduce the chunks.
 //   k_jvp_bwd     persistent CTAs over atoms: T_bar, T'_bar, then per chunk
 //                 recompute the embedding primal + tangent and run it in
 //                 reverse, accumulating the embedding gradient in a private
@@ -416,52 +417,131 @@ __global__ void __launch_bounds__(256) k_jvp_fit(ModelDev md, FitRec fr, int ti,
     }
 }
 
-// One thread per parameter of the fitting net of type ti; sums over the
-// atoms of that type and adds into grad (FP64).
+// Weight gradient of the fitting net of type ti as GEMMs over the atoms.  For each layer k,
+// with the bias as one more input row of constant 1:
+//   W_bar[i][o] = sum_a x[a][i] z_bar[a][o] + x'[a][i] z'_bar[a][o],  b_bar[o] = sum_a z_bar[a][o],
+// and for the linear output layer x = y, z_bar = alpha_frame(a), x' = y', z'_bar = beta.
+// Work: 64 x 64 tiles of (inputs + 1) x outputs of every layer (WgPlan) times chunks of the
+// atoms; each thread holds a 4 x 4 block of the tile, stages 16 atoms of x, x', z_bar, z'_bar in
+// shared memory at a time and accumulates in Real over its chunk; the chunk's partial sums go to
+// part[chunk][parameter] (FP64) and k_fit_wgrad_reduce adds the chunks in a fixed order.
+constexpr int kWgTile = 64, kWgAtoms = 16, kWgThreads = 256;
+
+struct WgPlan {
+    int nlayers;                  // hidden layers + the output layer
+    int tiles_in[kMaxFit + 1];    // tiles over win + 1 (the bias row)
+    int tiles_out[kMaxFit + 1];
+    int start[kMaxFit + 2];       // first tile of each layer
+    int chunk;                    // atoms per chunk
+};
+
+WgPlan make_wg_plan(const ModelDev &md)
+{
+    WgPlan p{};
+    p.nlayers = md.n_fit + 1;
+    p.start[0] = 0;
+    for (int k = 0; k < p.nlayers; ++k) {
+        p.tiles_in[k] = (md.fit.win[k] + 1 + kWgTile - 1) / kWgTile;
+        p.tiles_out[k] = (md.fit.wout[k] + kWgTile - 1) / kWgTile;
+        p.start[k + 1] = p.start[k] + p.tiles_in[k] * p.tiles_out[k];
+    }
+    return p;
+}
+
 template <typename Real>
-__global__ void k_fit_wgrad(ModelDev md, FitRec fr, int ti, const int32_t *__restrict__ order, int64_t pos_begin,
-                            int64_t count, const double *__restrict__ ab, int64_t frame_n,
-                            const Real *__restrict__ D, const Real *__restrict__ Dd, const Real *__restrict__ rec,
-                            double *__restrict__ grad)
+__global__ void __launch_bounds__(kWgThreads) k_fit_wgrad(ModelDev md, FitRec fr, WgPlan pl,
+                                                          const int32_t *__restrict__ order, int64_t pos_begin,
+                                                          int64_t count, const double *__restrict__ ab,
+                                                          int64_t frame_n, const Real *__restrict__ D,
+                                                          const Real *__restrict__ Dd, const Real *__restrict__ rec,
+                                                          double *__restrict__ part)
+{
+    __shared__ __align__(16) Real sX[kWgAtoms][kWgTile], sXd[kWgAtoms][kWgTile];
+    __shared__ __align__(16) Real sZ[kWgAtoms][kWgTile], sZd[kWgAtoms][kWgTile];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    int k = 0;
+    while (k + 1 < pl.nlayers && (int)blockIdx.x >= pl.start[k + 1]) ++k;
+    const int tt = (int)blockIdx.x - pl.start[k];
+    const int in0 = (tt / pl.tiles_out[k]) * kWgTile, o0 = (tt % pl.tiles_out[k]) * kWgTile;
+    const int win = md.fit.win[k], wout = md.fit.wout[k], nd = md.desc_dim;
+    const bool last = k == md.n_fit;
+    const int64_t a_begin = (int64_t)blockIdx.y * pl.chunk;
+    const int64_t a_end = a_begin + pl.chunk < count ? a_begin + pl.chunk : count;
+    Real acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = Real(0);
+    for (int64_t a0 = a_begin; a0 < a_end; a0 += kWgAtoms) {
+        __syncthreads();
+        // stage x, x' (inputs in0 ..) and z_bar, z'_bar (outputs o0 ..) of kWgAtoms atoms
+        for (int e = tid; e < 4 * kWgAtoms * kWgTile; e += kWgThreads) {
+            const int arr = e / (kWgAtoms * kWgTile), rem = e - arr * (kWgAtoms * kWgTile);
+            const int aa = rem / kWgTile, col = rem - aa * kWgTile;
+            const int64_t pa = pos_begin + a0 + aa;
+            Real v = Real(0);
+            if (a0 + aa < a_end) {
+                const Real *R = rec + pa * fr.size;
+                if (arr < 2) {   // x or x' at input in0 + col; the row win is the bias input
+                    const int i = in0 + col;
+                    if (i < win) {
+                        if (last) v = R[(arr == 0 ? fr.yl : fr.yld) + i];
+                        else if (k == 0) v = (arr == 0 ? D : Dd)[pa * nd + i];
+                        else v = R[(arr == 0 ? fr.x[k] : fr.xd[k]) + i];
+                    } else if (i == win && arr == 0) {
+                        v = Real(1);
+                    }
+                } else {         // z_bar or z'_bar at output o0 + col
+                    const int o = o0 + col;
+                    if (o < wout) {
+                        if (last) v = arr == 2 ? (Real)ab[1 + order[pa] / frame_n] : (Real)ab[0];
+                        else v = R[(arr == 2 ? fr.zb[k] : fr.zdb[k]) + o];
+                    }
+                }
+            }
+            Real *dst = arr == 0 ? &sX[0][0] : arr == 1 ? &sXd[0][0] : arr == 2 ? &sZ[0][0] : &sZd[0][0];
+            dst[rem] = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int aa = 0; aa < kWgAtoms; ++aa) {
+            Real x[4], xd[4], z[4], zd[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                x[r] = sX[aa][4 * ty + r];
+                xd[r] = sXd[aa][4 * ty + r];
+                z[r] = sZ[aa][4 * tx + r];
+                zd[r] = sZd[aa][4 * tx + r];
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fma(x[r], z[c], fma(xd[r], zd[c], acc[r][c]));
+        }
+    }
+    double *pc = part + (int64_t)blockIdx.y * md.fit.size;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = in0 + 4 * ty + r;
+        if (i > win) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int o = o0 + 4 * tx + c;
+            if (o >= wout) continue;
+            const int64_t q = i < win ? md.fit.W[k] + (int64_t)i * wout + o : md.fit.b[k] + o;
+            pc[q] = (double)acc[r][c];
+        }
+    }
+}
+
+// grad[fitting net ti] += the chunks' partial sums, added in chunk order.
+__global__ void k_fit_wgrad_reduce(ModelDev md, int ti, const double *__restrict__ part, int nchunks,
+                                   double *__restrict__ grad)
 {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= md.fit.size) return;
-    const int nd = md.desc_dim;
     double acc = 0.0;
-    int layer = -1, isb = 0, in = 0, out = 0;
-    for (int k = 0; k <= md.n_fit; ++k) {
-        if (q >= md.fit.W[k] && q < md.fit.b[k]) {
-            layer = k;
-            in = (int)((q - md.fit.W[k]) / md.fit.wout[k]);
-            out = (int)((q - md.fit.W[k]) % md.fit.wout[k]);
-        } else if (q >= md.fit.b[k] && q < md.fit.b[k] + md.fit.wout[k]) {
-            layer = k;
-            isb = 1;
-            out = (int)(q - md.fit.b[k]);
-        }
-    }
-    if (layer < 0) return;
-    if (layer == md.n_fit) {
-        // output layer: w_bar = sum alpha y + beta y', b_bar = alpha * count
-        if (isb) {
-            for (int64_t a = 0; a < count; ++a) acc += ab[1 + order[pos_begin + a] / frame_n];
-        } else {
-            for (int64_t a = 0; a < count; ++a) {
-                const Real *R = rec + (pos_begin + a) * fr.size;
-                acc += ab[1 + order[pos_begin + a] / frame_n] * (double)R[fr.yl + in] + ab[0] * (double)R[fr.yld + in];
-            }
-        }
-    } else if (isb) {
-        for (int64_t a = 0; a < count; ++a) acc += (double)rec[(pos_begin + a) * fr.size + fr.zb[layer] + out];
-    } else {
-        for (int64_t a = 0; a < count; ++a) {
-            const int64_t pa = pos_begin + a;
-            const Real *R = rec + pa * fr.size;
-            const Real x = layer == 0 ? D[pa * nd + in] : R[fr.x[layer] + in];
-            const Real xd = layer == 0 ? Dd[pa * nd + in] : R[fr.xd[layer] + in];
-            acc += (double)x * (double)R[fr.zb[layer] + out] + (double)xd * (double)R[fr.zdb[layer] + out];
-        }
-    }
+    for (int c = 0; c < nchunks; ++c) acc += part[(int64_t)c * md.fit.size + q];
     grad[md.fit_base + (int64_t)ti * md.fit.size + q] += acc;
 }
 
@@ -748,6 +828,15 @@ dp_status run_grad(dp_model *m, dp_nlist *nl, const double *d_v, const double *d
     sz(sizeof(Real) * md.desc_dim * n * 4);
     sz(sizeof(Real) * (size_t)fr.size * n);
     sz(sizeof(Real) * emb_len * nslices);
+    // fitting weight gradient: chunks of atoms so that the tiles x chunks fill the GPU
+    const WgPlan plan0 = make_wg_plan(md);
+    const int wg_tiles = plan0.start[plan0.nlayers];
+    auto wg_chunks = [&](int64_t cnt) {
+        const int64_t want = (4 * (int64_t)nsm + wg_tiles - 1) / wg_tiles;
+        const int64_t most = (cnt + kWgAtoms - 1) / kWgAtoms;
+        return want < 1 ? 1 : (want > most ? (most < 1 ? 1 : most) : want);
+    };
+    sz(sizeof(double) * (size_t)wg_chunks(n) * md.fit.size);
     DP_TRY(ensure_workspace(m, need));
     char *w = m->ws;
     auto carve = [&](size_t bytes) {
@@ -760,6 +849,7 @@ dp_status run_grad(dp_model *m, dp_nlist *nl, const double *d_v, const double *d
     Real *Dd = D + md.desc_dim * n, *Db = Dd + md.desc_dim * n, *Ddb = Db + md.desc_dim * n;
     Real *rec = (Real *)carve(sizeof(Real) * (size_t)fr.size * n);
     Real *gpriv = (Real *)carve(sizeof(Real) * emb_len * nslices);
+    double *wg_part = (double *)carve(sizeof(double) * (size_t)wg_chunks(n) * md.fit.size);
     DP_CUDA(cudaMemsetAsync(gpriv, 0, sizeof(Real) * emb_len * nslices, st));
     BoxDev bx = make_box(nl);
     const Pos4 *pos = (const Pos4 *)nl->d_pos;
@@ -783,8 +873,14 @@ dp_status run_grad(dp_model *m, dp_nlist *nl, const double *d_v, const double *d
         else
             k_jvp_fit<Real, 4><<<(unsigned)((cnt + 3) / 4), 256, 0, st>>>(md, fr, t, nl->d_order, b, cnt, d_ab, fn, D,
                                                                          Dd, rec, d_E_atom, d_Ed_atom, Db, Ddb);
-        k_fit_wgrad<Real><<<(unsigned)((md.fit.size + 255) / 256), 256, 0, st>>>(md, fr, t, nl->d_order, b, cnt,
-                                                                                d_ab, fn, D, Dd, rec, d_grad);
+        WgPlan plan = plan0;
+        int64_t nch = wg_chunks(cnt);
+        const int64_t per = ((cnt + nch - 1) / nch + kWgAtoms - 1) / kWgAtoms * kWgAtoms;
+        nch = (cnt + per - 1) / per;
+        plan.chunk = (int)per;
+        k_fit_wgrad<Real><<<dim3((unsigned)wg_tiles, (unsigned)nch), kWgThreads, 0, st>>>(
+            md, fr, plan, nl->d_order, b, cnt, d_ab, fn, D, Dd, rec, wg_part);
+        k_fit_wgrad_reduce<<<(unsigned)((md.fit.size + 255) / 256), 256, 0, st>>>(md, t, wg_part, (int)nch, d_grad);
         DP_CUDA(cudaGetLastError());
     }
     {

@@ -62,3 +62,66 @@ def test_student_distillation_and_judge(dp):
             assert fb.all()
         else:
             assert fb.sum() < len(fb)
+
+
+def test_teacher_fitted_to_reference_keeps_a_crystal_and_distils(dp):
+    """The full copper model fitted to the Morse copper reference by the library's own training
+    kernels (fit_to_reference) becomes a teacher whose NVE stays an FCC crystal with forces of a real
+    metal (~1 eV/A), which the seeded model is not.  Checked: the held-out force error against the
+    reference drops from 100% to a few percent; 400 NVE steps on 4,000 atoms conserve the energy and
+    keep every atom near its lattice site; a student distilled from this teacher's frames has a far
+    lower judged force error than the untrained student, which the judge rejects at every judgement
+    at config 4's absolute 0.05 eV/A threshold."""
+    from paper_2005_00223_gb300 import student as S
+    X, E, F, t5, b5 = dpsynth.morse_frames(272)
+    cfg = dpsynth.copper_config()
+    teacher = dp.Model(cfg, 0, params=dpsynth.model_params(cfg, 1))
+    r0, frms = S.force_rmse_vs_labels(teacher, X[256:], F[256:], t5, b5)
+    S.fit_to_reference(teacher, X[:256], E[:256], F[:256], t5, b5, steps=5000)
+    r1, _ = S.force_rmse_vs_labels(teacher, X[256:], F[256:], t5, b5)
+    print(f"Morse fit: held-out RMS F {frms:.3f} eV/A, force RMSE {r0:.3f} -> {r1:.4f} eV/A ({r1 / frms:.4f})")
+    assert r0 > 0.9 * frms and r1 < 0.05 * frms
+    # NVE of the fitted teacher from the displaced lattice at 300 K
+    coord, typ, box = dpsynth.copper_fcc(1, ncell=10)
+    lattice, _, _ = dpsynth.copper_fcc(1, ncell=10, sigma=0.0)
+    mass = np.array([dpsynth.MASS["Cu"]])
+    st = dp.MDState(teacher, coord, dpsynth.velocities(mass[typ], 300.0, 1), typ, mass, box, skin=2.0)
+    th = np.asarray(st.step(400, 1.0, "bf16x3", thermo_every=100))
+    x, _, _, _ = st.get()
+    st.close()
+    etot = th[:, 0] + th[:, 1]
+    L = np.diag(box)
+    d = x - lattice
+    d -= L * np.rint(d / L)
+    msd = float((d ** 2).sum(1).mean())
+    print("fitted teacher NVE: T", th[:, 2], "E_tot spread per atom", np.ptp(etot) / len(typ), "RMS displacement",
+          np.sqrt(msd))
+    assert np.isfinite(th).all() and np.ptp(etot) / len(typ) < 1e-4
+    assert np.sqrt(msd) < 0.3 and np.sqrt((d ** 2).sum(1)).max() < 1.0
+    # distillation on its frames (500 atoms, runs from the lattice at 2 T) and the judge at 0.05 eV/A
+    lattice, typ, box = dpsynth.copper_fcc(1, ncell=5, sigma=0.0)
+    vels = [dpsynth.velocities(mass[typ], 2 * T, 10 + k) for k, T in enumerate((300.0, 1200.0))]
+    Xs, Es, Fs = S.teacher_frames(teacher, lattice, typ, box, mass, vels, nframes=24, stride=5, dt_fs=1.0,
+                                  md_prec="bf16x3", label_prec="bf16x3")
+    test_idx = np.r_[20:24, 44:48]
+    train_idx = np.setdiff1d(np.arange(len(Xs)), test_idx)
+    stu = dp.Model(dpsynth.copper_student_config(), seed=2)
+    s0, fr = S.force_rmse(stu, teacher, Xs[test_idx], typ, box, "mix32", "bf16x3")
+    S.train(stu, typ, box, Xs[train_idx], Es[train_idx], Fs[train_idx], steps=5000, lr0=3e-3, lr1=1e-4,
+            p_e=1.0, p_f=100.0 / fr ** 2)
+    s1, _ = S.force_rmse(stu, teacher, Xs[test_idx], typ, box, "mix32", "bf16x3")
+    print(f"student on the fitted teacher: RMS F {fr:.3f}, force RMSE {s0:.3f} -> {s1:.4f} eV/A")
+    assert s1 < 0.3 * s0
+    fresh = dp.Model(dpsynth.copper_student_config(), seed=2)
+    judged = []
+    for model in (fresh, stu):
+        st = dp.MDState(model, lattice, vels[0], typ, mass, box, skin=2.0)
+        rm, fb = dp.dp_md_step_judged(model.h, teacher.h, st.h, 60, 1.0, "bf16", "bf16x3", judge_every=10,
+                                      rmse_max=0.05)
+        st.close()
+        print("judged at 0.05 eV/A:", rm, fb)
+        assert len(rm) == 6 and np.isfinite(rm).all()
+        judged.append((rm, fb))
+    # the untrained student is rejected at every judgement; the trained one's judged error is far lower
+    assert judged[0][1].all()
+    assert judged[1][0].mean() < 0.5 * judged[0][0].mean()
