@@ -549,6 +549,82 @@ def grad_flops(cfg, nnei_total: int, n: int):
     return 3 * sum(f.values())
 
 
+def run_train(args, rank, world):
+    """Device time per training step (one-frame force-loss gradient + Adam, MIX-32) of the two
+    training runs of config 4: the full copper model on 500-atom Morse-labelled frames (the teacher
+    fit) and the copper student on 4,000-atom frames (the distillation).  --warmup untimed steps,
+    then --steps timed with CUDA events on the training stream; per-group times from the library's
+    tracing (param_grad covers the gradient kernels)."""
+    import torch
+
+    import paper_2005_00223_gb300 as dp
+    from paper_2005_00223_gb300 import _lib
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def time_steps(model, typ, box, X, E, F, p_e, p_f):
+        Xd = torch.tensor(X, dtype=torch.float64, device=dev)
+        Fd = torch.tensor(F, dtype=torch.float64, device=dev)
+        Ed = torch.tensor(E, dtype=torch.float64, device=dev)
+        nparams = _lib.dp_model_n_params(model.h)
+        grad = torch.zeros(nparams, dtype=torch.float64, device=dev)
+        loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        _lib.dp_model_set_stream(model.h, stream)
+        nl = dp.NeighborList(model, X[0], typ, box)
+
+        def step(s):
+            k = s % len(X)
+            _lib.dp_nlist_update_dev(nl.h, Xd[k], stream)
+            grad.zero_()
+            _lib.dp_force_loss_grad_dev(model.h, nl.h, Xd[k], box, Fd[k], Ed[k:k + 1], p_e, p_f, "mix32", loss,
+                                        grad, stream)
+            _lib.dp_adam_step(model.h, grad, 1e-4, 0.9, 0.999, 1e-8, s + 1, stream)
+
+        for s in range(args.warmup):
+            step(s)
+        dp.dp_profile_enable(model.h, True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for s in range(args.warmup, args.warmup + args.steps):
+            step(s)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        prof = dp.dp_profile_read(model.h)
+        dp.dp_profile_enable(model.h, False)
+        nl.close()
+        _lib.dp_model_set_stream(model.h, None)
+        return ev0.elapsed_time(ev1) / args.steps, {g: {"launches": v[0], "ms_total": round(v[1], 4)}
+                                                    for g, v in prof.items() if v[0] > 0}
+
+    sampler = ClockSampler()
+    sampler.start()
+    cfg = dpsynth.copper_config()
+    X, E, F, t5, b5 = dpsynth.morse_frames(16)
+    full = dp.Model(cfg, 0, params=dpsynth.model_params(cfg, 1))
+    ms_full, g_full = time_steps(full, t5, b5, X, E, F, 0.02, 100.0)
+    full.close()
+    c4, t4, b4 = dpsynth.copper_fcc(1, ncell=10)
+    F4 = np.zeros((4,) + c4.shape)
+    X4 = np.array([dpsynth.copper_fcc(1 + k, ncell=10)[0] for k in range(4)])
+    stu = dp.Model(dpsynth.copper_student_config(), seed=2)
+    ms_stu, g_stu = time_steps(stu, t4, b4, X4, np.zeros(4), F4, 1.0, 100.0)
+    stu.close()
+    clocks = sampler.stop()
+    return {"metric": "ms per training step (force-loss gradient + Adam, MIX-32)", "value": ms_full,
+            "unit": "ms/step", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_full,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded FCC copper; Morse-labelled frames for the full model)",
+            "config": {"workload": "full copper model on 500-atom frames (teacher fit) and copper student on "
+                                   "4,000-atom frames (distillation)", "parallelism": "1 GPU"},
+            "full_model_500_atoms": {"ms_per_step": ms_full, "kernel_groups": g_full},
+            "student_4000_atoms": {"ms_per_step": ms_stu, "kernel_groups": g_stu},
+            "gpu_launches": int(sum(v["launches"] for v in g_full.values()) + sum(v["launches"] for v in g_stu.values())),
+            "clocks": clocks, "e2e": None}
+
+
 def run_grad(args, rank, world):
     """Parameter gradient of the force-matching loss over 32 water frames of 192 atoms, one batched call."""
     import torch
@@ -1005,9 +1081,10 @@ def main():
     ap.add_argument("--sweep-widths", default="", help="sweep task: first widths w of the nets (w, 2w, 4w) to run "
                     "(comma-separated; default all)")
     ap.add_argument("--sweep-precisions", default="bf16,fp8", help="sweep task: bf16 and/or fp8")
-    ap.add_argument("--task", default="md", choices=["md", "grad", "judged", "sweep"],
+    ap.add_argument("--task", default="md", choices=["md", "grad", "judged", "sweep", "train"],
                     help="md: NVE steps (default); grad: force-loss parameter gradient over 32 water frames; "
-                         "judged: distilled student MD judged by the full model")
+                         "judged: distilled student MD judged by the full model; train: training steps of "
+                         "config 4's teacher fit and distillation")
     args = ap.parse_args()
     args.paths = [] if args.paths in ("", "none") else [p for p in args.paths.split(",") if p]
     for p in args.paths:
@@ -1028,6 +1105,8 @@ def main():
         out = run_judged(args, rank, world)
     elif args.task == "sweep":
         out = run_sweep(args, rank, world)
+    elif args.task == "train":
+        out = run_train(args, rank, world)
     else:
         out = run_mine(args, rank, world)
         ref = None

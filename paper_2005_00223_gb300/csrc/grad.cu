@@ -579,12 +579,49 @@ __device__ __forceinline__ void layer_rev(const Real *W, const Real *X, const Re
         Zdb[o * LD + n] = zdb;
     }
     __syncthreads();
-    for (int e = tid; e < WIN * WOUT; e += NT) {
-        const int k = e / WOUT, o = e - k * WOUT;
-        Real acc = Real(0);
+    // W_bar in 4 x 4 blocks of (input k, output o) where there are enough blocks for every thread:
+    // each row's 4 + 4 inputs and 4 + 4 adjoints feed 32 multiply-adds (one shared-memory load per
+    // two multiply-adds instead of two per one); smaller layers keep one entry per thread
+    constexpr int KB = (WIN + 3) / 4, OB = (WOUT + 3) / 4;
+    if (KB * OB < NT) {
+        for (int e = tid; e < WIN * WOUT; e += NT) {
+            const int k = e / WOUT, o = e - k * WOUT;
+            Real acc = Real(0);
 #pragma unroll 8
-        for (int nn = 0; nn < 32; ++nn) acc += X[k * LD + nn] * Zb[o * LD + nn] + Xd[k * LD + nn] * Zdb[o * LD + nn];
-        gW[e] += acc;
+            for (int nn = 0; nn < 32; ++nn) acc += X[k * LD + nn] * Zb[o * LD + nn] + Xd[k * LD + nn] * Zdb[o * LD + nn];
+            gW[e] += acc;
+        }
+    } else {
+        for (int blk = tid; blk < KB * OB; blk += NT) {
+            const int k0 = (blk / OB) * 4, q0 = (blk % OB) * 4;
+            Real acc[4][4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = Real(0);
+#pragma unroll 2
+            for (int nn = 0; nn < 32; ++nn) {
+                Real x[4], xd[4], zb[4], zdb[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int k = k0 + r < WIN ? k0 + r : WIN - 1;
+                    const int o = q0 + r < WOUT ? q0 + r : WOUT - 1;
+                    x[r] = X[k * LD + nn];
+                    xd[r] = Xd[k * LD + nn];
+                    zb[r] = Zb[o * LD + nn];
+                    zdb[r] = Zdb[o * LD + nn];
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[r][c] += x[r] * zb[c] + xd[r] * zdb[c];
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (k0 + r < WIN && q0 + c < WOUT) gW[(k0 + r) * WOUT + q0 + c] += acc[r][c];
+        }
     }
     for (int o = tid; o < WOUT; o += NT) {
         Real acc = Real(0);
