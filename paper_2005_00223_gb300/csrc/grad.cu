@@ -31,6 +31,8 @@
 //                 slice per CTA.
 //   k_grad_reduce the private slices, summed in a fixed order.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <math.h>
 
 #include "dp_internal.cuh"
@@ -891,7 +893,17 @@ dp_status run_grad(dp_model *m, dp_nlist *nl, const double *d_v, const double *d
     const FitRec fr = make_fit_rec(md);
     int nsm = 0;
     DP_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, m->device));
-    const int nslices = nsm;
+    // the embedding reverse runs as many persistent CTAs as fit on the SMs at once (each with its own
+    // gradient slice): one CTA of a few warps per SM leaves its chains of small products and barriers
+    // exposed
+    const size_t sf = fwd_smem<S, Real>(md), sb = bwd_smem<S, Real>(md);
+    DP_CUDA(cudaFuncSetAttribute(k_jvp_fwd<S, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
+    DP_CUDA(cudaFuncSetAttribute(k_jvp_bwd<S, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
+    int per_sm = 1;
+    DP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jvp_bwd<S, Real>, S::NT, sb));
+    per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
+    const int64_t bwd_atoms = n > 0 ? n : 1;
+    const int nslices = (int)std::min<int64_t>((int64_t)nsm * per_sm, bwd_atoms);
     const int64_t emb_len = (int64_t)md.ntypes * md.ntypes * md.emb.size;
     size_t need = 0;
     auto sz = [&](size_t b) { need += (b + 255) & ~(size_t)255; };
@@ -924,9 +936,6 @@ dp_status run_grad(dp_model *m, dp_nlist *nl, const double *d_v, const double *d
     DP_CUDA(cudaMemsetAsync(gpriv, 0, sizeof(Real) * emb_len * nslices, st));
     BoxDev bx = make_box(nl);
     const Pos4 *pos = (const Pos4 *)nl->d_pos;
-    const size_t sf = fwd_smem<S, Real>(md), sb = bwd_smem<S, Real>(md);
-    DP_CUDA(cudaFuncSetAttribute(k_jvp_fwd<S, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
-    DP_CUDA(cudaFuncSetAttribute(k_jvp_bwd<S, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
     {
         ProfScope ps(m->prof, PG_GRAD, 1, st);
         k_jvp_fwd<S, Real><<<(unsigned)n, S::NT, sf, st>>>(md, bx, nl->d_order, pos, nl->d_nlist, nl->d_nnei, d_v, T,
