@@ -36,6 +36,7 @@
 #include <math.h>
 
 #include "dp_internal.cuh"
+#include "fit_gemm.cuh"
 #include "geom.cuh"
 #include "tanh64.cuh"
 
@@ -231,225 +232,8 @@ __global__ void __launch_bounds__(S::NT) k_jvp_fwd(ModelDev md, BoxDev bx, const
     }
 }
 
-// Offsets (in Real) of the per-atom fitting record: for each hidden layer k,
-// its input x and x' (layer 0 reads D and D' instead), t, z', z_bar, z'_bar;
-// then the last hidden output y and y' and two adjoint ping-pong vectors.
-struct FitRec {
-    int x[kMaxFit + 1], xd[kMaxFit + 1], t[kMaxFit + 1], zd[kMaxFit + 1], zb[kMaxFit + 1], zdb[kMaxFit + 1];
-    int yl, yld, a0, a0d, a1, a1d;
-    int size;
-};
-
-FitRec make_fit_rec(const ModelDev &md)
-{
-    FitRec r{};
-    int off = 0, wmax = 0;
-    for (int k = 0; k < md.n_fit; ++k) {
-        const int win = md.fit.win[k], wout = md.fit.wout[k];
-        wmax = wmax > wout ? wmax : wout;
-        if (k > 0) {
-            r.x[k] = off; off += win;
-            r.xd[k] = off; off += win;
-        }
-        r.t[k] = off; off += wout;
-        r.zd[k] = off; off += wout;
-        r.zb[k] = off; off += wout;
-        r.zdb[k] = off; off += wout;
-    }
-    const int wl = md.fit.wout[md.n_fit - 1];
-    r.yl = off; off += wl;
-    r.yld = off; off += wl;
-    r.a0 = off; off += wmax;
-    r.a0d = off; off += wmax;
-    r.a1 = off; off += wmax;
-    r.a1d = off; off += wmax;
-    r.size = off;
-    return r;
-}
-
-// The fitting net's primal + tangent forward and its reverse as tiled GEMMs over the atoms of a type
-// (a CTA per atom would stream every weight row from L2 once per atom).  Per hidden layer k:
-//   forward  Z = X W + b, Z' = X' W (X = D for k = 0, else the layer input in rec), then per entry
-//            t = tanh(z), y = skip(x) + t, y' = skip(x') + (1 - t^2) z' -> rec;
-//   reverse  X_bar = Z_bar W^T + skip^T(Y_bar), X'_bar = Z'_bar W^T + skip^T(Y'_bar) -> the other
-//            adjoint buffer of rec, or D_bar / D'_bar for k = 0,
-// with k_fit_out (E_i, Edot_i and the output layer's adjoints) between them and k_fit_zbar
-// (z_bar, z'_bar from the output adjoints) before each reverse GEMM.  rec ends up holding every
-// layer's inputs, t, z', z_bar and z'_bar, which k_fit_wgrad reads.  Tiles of BM atoms x 64
-// columns with threads of 4 x 4 (primal and tangent share every B element), K staged 16 at a time in
-// shared memory.
-constexpr int kFgM = 32, kFgN = 64, kFgK = 16, kFgThreads = 128;
-
-// Host side: the device parameters (flat order, or with every W transposed) in the precision Real.
-template <typename Real>
-const Real *fit_params(const ModelDev &md, bool transposed)
-{
-    if constexpr (sizeof(Real) == sizeof(double)) return transposed ? md.pT : md.p;
-    else return transposed ? md.pT32 : md.p32;
-}
-
-enum FitGemmMode { FG_FWD = 0, FG_REV = 1 };
-
-struct FitGemmArgs {
-    const void *A, *Ad;        // [atom][K] at row stride lda (Real)
-    int64_t lda;
-    const void *B;             // [K][N] row-major (Real)
-    const void *bias;          // FG_FWD: [N]
-    int M, N, K;
-    int k;                     // layer
-    int64_t pos_begin;
-    int yb, ydb, xb, xdb;      // FG_REV: adjoint buffer offsets in rec
-};
-
-template <typename Real, int MODE>
-__global__ void __launch_bounds__(kFgThreads) k_fit_gemm(ModelDev md, FitRec fr, FitGemmArgs g,
-                                                         Real *__restrict__ rec, Real *__restrict__ Db,
-                                                         Real *__restrict__ Ddb)
-{
-    __shared__ __align__(16) Real sA[kFgK][kFgM], sAd[kFgK][kFgM], sB[kFgK][kFgN];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;   // 16 column groups x 8 row groups
-    const int m0 = blockIdx.x * kFgM, n0 = blockIdx.y * kFgN;
-    const Real *A = reinterpret_cast<const Real *>(g.A), *Ad = reinterpret_cast<const Real *>(g.Ad);
-    const Real *B = reinterpret_cast<const Real *>(g.B);
-    Real acc[4][4], accd[4][4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = accd[r][c] = Real(0);
-    for (int k0 = 0; k0 < g.K; k0 += kFgK) {
-        __syncthreads();
-        for (int e = tid; e < kFgM * kFgK; e += kFgThreads) {
-            const int a = e / kFgK, kk = e - a * kFgK;
-            const bool ok = m0 + a < g.M && k0 + kk < g.K;
-            const int64_t off = (g.pos_begin + m0 + a) * g.lda + k0 + kk;
-            sA[kk][a] = ok ? A[off] : Real(0);
-            sAd[kk][a] = ok ? Ad[off] : Real(0);
-        }
-        for (int e = tid; e < kFgK * kFgN; e += kFgThreads) {
-            const int kk = e / kFgN, c = e - kk * kFgN;
-            sB[kk][c] = (k0 + kk < g.K && n0 + c < g.N) ? B[(int64_t)(k0 + kk) * g.N + n0 + c] : Real(0);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < kFgK; ++kk) {
-            Real a[4], ad[4], b[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                a[r] = sA[kk][4 * ty + r];
-                ad[r] = sAd[kk][4 * ty + r];
-                b[r] = sB[kk][4 * tx + r];
-            }
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    acc[r][c] = fma(a[r], b[c], acc[r][c]);
-                    accd[r][c] = fma(ad[r], b[c], accd[r][c]);
-                }
-        }
-    }
-    const int k = g.k, win = md.fit.win[k], wout = md.fit.wout[k], nd = md.desc_dim;
-    const bool skip1 = wout == win, skip2 = wout == 2 * win;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int a = m0 + 4 * ty + r;
-        if (a >= g.M) continue;
-        const int64_t pa = g.pos_begin + a;
-        Real *R = rec + pa * fr.size;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int j = n0 + 4 * tx + c;
-            if (j >= g.N) continue;
-            if (MODE == FG_FWD) {
-                const Real t = g_tanh(acc[r][c] + reinterpret_cast<const Real *>(g.bias)[j]);
-                const Real zd = accd[r][c];
-                Real sx = Real(0), sxd = Real(0);
-                if (skip1 || skip2) {
-                    const int oi = j % win;
-                    sx = A[pa * g.lda + oi];
-                    sxd = Ad[pa * g.lda + oi];
-                }
-                R[fr.t[k] + j] = t;
-                R[fr.zd[k] + j] = zd;
-                const Real y = sx + t, yd = sxd + (Real(1) - t * t) * zd;
-                if (k + 1 < md.n_fit) {
-                    R[fr.x[k + 1] + j] = y;
-                    R[fr.xd[k + 1] + j] = yd;
-                } else {
-                    R[fr.yl + j] = y;
-                    R[fr.yld + j] = yd;
-                }
-            } else {
-                Real s1 = acc[r][c], s2 = accd[r][c];
-                if (skip1) {
-                    s1 += R[g.yb + j];
-                    s2 += R[g.ydb + j];
-                } else if (skip2) {
-                    s1 += R[g.yb + j] + R[g.yb + j + win];
-                    s2 += R[g.ydb + j] + R[g.ydb + j + win];
-                }
-                if (k == 0) {
-                    Db[pa * nd + j] = s1;
-                    Ddb[pa * nd + j] = s2;
-                } else {
-                    R[g.xb + j] = s1;
-                    R[g.xdb + j] = s2;
-                }
-            }
-        }
-    }
-}
-
-// Output layer of the fitting net (one warp per atom): E_i = y . w + b, Edot_i = y' . w, and the
-// output adjoints of the last hidden layer, alpha_frame w and beta w, into rec's first adjoint buffer.
-template <typename Real>
-__global__ void __launch_bounds__(256) k_fit_out(ModelDev md, FitRec fr, int ti, const int32_t *__restrict__ order,
-                                                int64_t pos_begin, int64_t count, const double *__restrict__ ab,
-                                                int64_t frame_n, Real *__restrict__ rec, double *__restrict__ E_atom,
-                                                double *__restrict__ Ed_atom)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (a >= count) return;
-    const Real *net = P_of<Real>(md) + md.fit_base + (int64_t)ti * md.fit.size;
-    const int wl = md.fit.wout[md.n_fit - 1];
-    const Real *Wout = net + md.fit.W[md.n_fit];
-    const int64_t pa = pos_begin + a;
-    Real *R = rec + pa * fr.size;
-    const Real alpha = (Real)ab[1 + order[pa] / frame_n], beta = (Real)ab[0];
-    Real e = Real(0), ed = Real(0);
-    for (int o = lane; o < wl; o += 32) {
-        const Real w = Wout[o];
-        e += R[fr.yl + o] * w;
-        ed += R[fr.yld + o] * w;
-        R[fr.a0 + o] = alpha * w;
-        R[fr.a0d + o] = beta * w;
-    }
-    for (int s = 16; s > 0; s >>= 1) {
-        e += __shfl_xor_sync(0xffffffffu, e, s);
-        ed += __shfl_xor_sync(0xffffffffu, ed, s);
-    }
-    if (lane == 0) {
-        E_atom[order[pa]] = (double)(e + net[md.fit.b[md.n_fit]]);
-        Ed_atom[order[pa]] = (double)ed;
-    }
-}
-
-// z_bar = (y_bar + y'_bar z' (-2 t)) (1 - t^2), z'_bar = y'_bar (1 - t^2) of layer k for every atom.
-template <typename Real>
-__global__ void k_fit_zbar(ModelDev md, FitRec fr, int k, int yb, int ydb, int64_t pos_begin, int64_t count,
-                           Real *__restrict__ rec)
-{
-    const int wout = md.fit.wout[k];
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= count * wout) return;
-    const int64_t a = q / wout;
-    const int o = (int)(q - a * wout);
-    Real *R = rec + (pos_begin + a) * fr.size;
-    const Real t = R[fr.t[k] + o], g1 = Real(1) - t * t;
-    R[fr.zb[k] + o] = (R[yb + o] + R[ydb + o] * R[fr.zd[k] + o] * (Real(-2) * t)) * g1;
-    R[fr.zdb[k] + o] = R[ydb + o] * g1;
-}
+using fitg::FitRec;
+using fitg::make_fit_rec;
 
 // Weight gradient of the fitting net of type ti as GEMMs over the atoms.  For each layer k,
 // with the bias as one more input row of constant 1:
@@ -948,48 +732,8 @@ dp_status run_grad(dp_model *m, dp_nlist *nl, const double *d_v, const double *d
         ProfScope ps(m->prof, PG_GRAD, 2, st);
         const int64_t fn = nl->frame_n > 0 ? nl->frame_n : n;
         // fitting net: primal + tangent forward, output layer, reverse, as tiled GEMMs over the atoms
-        const Real *fnet = fit_params<Real>(md, false) + md.fit_base + (int64_t)t * md.fit.size;
-        const Real *fnetT = fit_params<Real>(md, true) + md.fit_base + (int64_t)t * md.fit.size;
-        const unsigned mt = (unsigned)((cnt + kFgM - 1) / kFgM);
-        for (int k = 0; k < md.n_fit; ++k) {
-            FitGemmArgs g{};
-            g.A = k == 0 ? (const void *)D : (const void *)(rec + fr.x[k]);
-            g.Ad = k == 0 ? (const void *)Dd : (const void *)(rec + fr.xd[k]);
-            g.lda = k == 0 ? md.desc_dim : fr.size;
-            g.B = fnet + md.fit.W[k];
-            g.bias = fnet + md.fit.b[k];
-            g.M = (int)cnt;
-            g.N = md.fit.wout[k];
-            g.K = md.fit.win[k];
-            g.k = k;
-            g.pos_begin = b;
-            k_fit_gemm<Real, FG_FWD><<<dim3(mt, (unsigned)((g.N + kFgN - 1) / kFgN)), kFgThreads, 0, st>>>(
-                md, fr, g, rec, Db, Ddb);
-        }
-        k_fit_out<Real><<<(unsigned)((cnt * 32 + 255) / 256), 256, 0, st>>>(md, fr, t, nl->d_order, b, cnt, d_ab, fn,
-                                                                            rec, d_E_atom, d_Ed_atom);
-        int cur = 0;   // adjoint buffer holding the current layer's output adjoints
-        for (int k = md.n_fit - 1; k >= 0; --k) {
-            FitGemmArgs g{};
-            g.yb = cur ? fr.a1 : fr.a0;
-            g.ydb = cur ? fr.a1d : fr.a0d;
-            g.xb = cur ? fr.a0 : fr.a1;
-            g.xdb = cur ? fr.a0d : fr.a1d;
-            const int64_t nz = cnt * md.fit.wout[k];
-            k_fit_zbar<Real><<<(unsigned)((nz + 255) / 256), 256, 0, st>>>(md, fr, k, g.yb, g.ydb, b, cnt, rec);
-            g.A = rec + fr.zb[k];
-            g.Ad = rec + fr.zdb[k];
-            g.lda = fr.size;
-            g.B = fnetT + md.fit.W[k];   // W^T: [wout][win]
-            g.M = (int)cnt;
-            g.N = md.fit.win[k];
-            g.K = md.fit.wout[k];
-            g.k = k;
-            g.pos_begin = b;
-            k_fit_gemm<Real, FG_REV><<<dim3(mt, (unsigned)((g.N + kFgN - 1) / kFgN)), kFgThreads, 0, st>>>(
-                md, fr, g, rec, Db, Ddb);
-            cur ^= 1;
-        }
+        fitg::fit_net_run<Real, true>(md, fr, t, nl->d_order, b, 0, cnt, d_ab, fn, D, Dd, rec, d_E_atom, d_Ed_atom,
+                                      Db, Ddb, st);
         WgPlan plan = plan0;
         int64_t nch = wg_chunks(cnt);
         const int64_t per = ((cnt + nch - 1) / nch + kWgAtoms - 1) / kWgAtoms * kWgAtoms;

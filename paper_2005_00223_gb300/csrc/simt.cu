@@ -30,6 +30,7 @@
 #include <math.h>
 
 #include "dp_internal.cuh"
+#include "fit_gemm.cuh"
 #include "geom.cuh"
 #include "tanh64.cuh"
 
@@ -651,10 +652,21 @@ dp_status launch_fit_oz(dp_model *m, const int32_t *order, int t, int64_t p0, in
 // serve more atoms).  Otherwise A in 6..9 minimises (waves x A) with the
 // CTAs that fit on an SM at once, since the kernel is arithmetic bound and a
 // partly filled last wave idles SMs.
+//
+// MIX-32 (frec given): the layers as tiled GEMMs over the type's atoms instead (fit_gemm.cuh), with
+// the per-atom record frec [batch][FitRec size] holding each layer's inputs, t and adjoints.
 template <typename Real>
 dp_status launch_fit(dp_model *m, const int32_t *order, int t, int64_t p0, int64_t b, int64_t count, const Real *D, Real *dD,
-                     double *E_atom, cudaStream_t st)
+                     double *E_atom, Real *frec, cudaStream_t st)
 {
+    if (frec) {
+        const ModelDev &md = m->dev;
+        ProfScope ps(m->prof, PG_FIT, 3 * md.n_fit + 1, st);
+        fitg::fit_net_run<Real, false>(md, fitg::make_fit_rec(md), t, order, b, p0, count, nullptr, 1, D, nullptr,
+                                       frec, E_atom, nullptr, dD, nullptr, st);
+        DP_CUDA(cudaGetLastError());
+        return DP_OK;
+    }
     ProfScope ps(m->prof, PG_FIT, 1, st);
     return launch_fit_oz<Real, false>(m, order, t, p0, b, count, D, dD, E_atom, nullptr, nullptr, st);
 }
@@ -771,7 +783,7 @@ dp_status fit_fp64_oz(dp_model *m, dp_nlist *nl, int t, int64_t p0, int64_t b, i
 template <class S, typename Real>
 dp_status launch_batch(dp_model *m, dp_nlist *nl, BoxDev bx, int64_t p0, int64_t nb, Real *T, Real *D, Real *dD,
                        Real *act, double *E_atom, double *force, double *atom_virial, char *oz_scratch,
-                       char *ozemb_scratch, cudaStream_t st)
+                       char *ozemb_scratch, Real *frec, cudaStream_t st)
 {
     const ModelDev &md = m->dev;
     size_t sf = embed_fwd_smem<S, Real>(md), sb = embed_bwd_smem<S, Real>(md);
@@ -794,7 +806,7 @@ dp_status launch_batch(dp_model *m, dp_nlist *nl, BoxDev bx, int64_t p0, int64_t
         if (oz_scratch && e - b >= oz_min_atoms())
             DP_TRY(fit_fp64_oz(m, nl, t, p0, b, e - b, (const double *)D, (double *)dD, E_atom, oz_scratch, st));
         else
-            DP_TRY(launch_fit<Real>(m, nl->d_order, t, p0, b, e - b, D, dD, E_atom, st));
+            DP_TRY(launch_fit<Real>(m, nl->d_order, t, p0, b, e - b, D, dD, E_atom, frec, st));
     }
     if (ozemb_scratch) {
         DP_TRY(oz_emb_bwd(m, nl, bx, nb, (const double *)T, (const double *)dD, (const double *)act, force,
@@ -837,8 +849,10 @@ dp_status compute_simt(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
     if (oz) DP_TRY(oz_refresh_weights(m, st));
     if (oz && oz_fit_chain_ok(md)) DP_TRY(oz_fit_chain_refresh(m, st));
     if (ozemb) DP_TRY(oz_emb_refresh(m, st));
-    DP_TRY(ensure_workspace(m, per_atom * (size_t)B + 256 * 5 + (oz ? oz_bytes(md, B) : 0) +
-                                   (ozemb ? oz_emb_bytes(md, B) : 0)));
+    // MIX-32: the fitting net runs as GEMMs over the atoms with a per-atom record (fit_gemm.cuh)
+    const size_t frec_bytes = sizeof(Real) == sizeof(float) ? sizeof(Real) * (size_t)fitg::make_fit_rec(md).size * B : 0;
+    DP_TRY(ensure_workspace(m, per_atom * (size_t)B + 256 * 6 + (oz ? oz_bytes(md, B) : 0) +
+                                   (ozemb ? oz_emb_bytes(md, B) : 0) + frec_bytes));
     char *w = m->ws;
     auto carve = [&](size_t bytes) {
         char *p = w;
@@ -851,6 +865,7 @@ dp_status compute_simt(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
     Real *act = (Real *)carve(sizeof(Real) * (size_t)md.chunks_per_atom * md.act_stride * 32 * B);
     char *ozs = oz ? carve(oz_bytes(md, B)) : nullptr;
     char *ozes = ozemb ? carve(oz_emb_bytes(md, B)) : nullptr;
+    Real *frec = frec_bytes ? (Real *)carve(frec_bytes) : nullptr;
     DP_CUDA(cudaMemsetAsync(d_force, 0, sizeof(double) * 3 * n, st));
     if (ozemb) DP_CUDA(cudaMemsetAsync(d_atom_virial, 0, sizeof(double) * 9 * n, st));   // accumulated per chunk
     // deterministic mode: the scatters go to fixed-point limbs (F, and W_i where it is accumulated
@@ -878,11 +893,11 @@ dp_status compute_simt(dp_model *m, dp_nlist *nl, double *d_energy, double *d_at
         int64_t nb = n - p0 < B ? n - p0 : B;
         dp_status s;
         if (e[0] == 25)
-            s = launch_batch<ShapeWater, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, ozs, ozes, st);
+            s = launch_batch<ShapeWater, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, ozs, ozes, frec, st);
         else if (e[0] == 8)
-            s = launch_batch<ShapeStudent, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, ozs, ozes, st);
+            s = launch_batch<ShapeStudent, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, ozs, ozes, frec, st);
         else
-            s = launch_batch<ShapePaper, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, ozs, ozes, st);
+            s = launch_batch<ShapePaper, Real>(m, nl, bx, p0, nb, T, D, dD, act, d_atom_energy, d_force, d_atom_virial, ozs, ozes, frec, st);
         if (s != DP_OK) return s;
     }
     if (m->dev.fx) {
@@ -923,7 +938,7 @@ dp_status fit_f32(dp_model *m, dp_nlist *nl, const float *D, float *dD, double *
     for (int t = 0; t < md.ntypes; ++t) {
         const int64_t b = nl->type_off[t], cnt = nl->type_count[t];
         if (cnt <= 0) continue;
-        DP_TRY(launch_fit<float>(m, nl->d_order, t, 0, b, cnt, D, dD, d_atom_energy, st));
+        DP_TRY(launch_fit<float>(m, nl->d_order, t, 0, b, cnt, D, dD, d_atom_energy, nullptr, st));
     }
     return DP_OK;
 }
