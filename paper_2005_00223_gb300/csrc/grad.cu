@@ -590,13 +590,25 @@ __global__ void __launch_bounds__(S::NT) k_jvp_bwd(ModelDev md, BoxDev bx, const
 
 // grad[emb part] += sum over the private slices, in slice order.
 template <typename Real>
-__global__ void k_grad_reduce(const Real *__restrict__ gpriv, int nslices, int64_t len, double *__restrict__ grad)
+__global__ void __launch_bounds__(256) k_grad_reduce(const Real *__restrict__ gpriv, int nslices, int64_t len,
+                                                     double *__restrict__ grad)
 {
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= len) return;
+    // 32 entries per block, the slices split over 8 groups (group g sums slices g, g + 8, ...); the
+    // group sums are added in group order, so the result does not depend on the scheduling
+    __shared__ double part[8][32];
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const int64_t q = blockIdx.x * (int64_t)32 + lane;
     double acc = 0.0;
-    for (int s = 0; s < nslices; ++s) acc += (double)gpriv[(int64_t)s * len + q];
-    grad[q] += acc;
+    if (q < len)
+        for (int s = grp; s < nslices; s += 8) acc += (double)gpriv[(int64_t)s * len + q];
+    part[grp][lane] = acc;
+    __syncthreads();
+    if (grp == 0 && q < len) {
+        double sum = 0.0;
+#pragma unroll
+        for (int g = 0; g < 8; ++g) sum += part[g][lane];
+        grad[q] += sum;
+    }
 }
 
 // Per frame (one block each, fixed-order sums): v = F - F_ref, the frame's
@@ -748,7 +760,7 @@ dp_status run_grad(dp_model *m, dp_nlist *nl, const double *d_v, const double *d
         ProfScope ps(m->prof, PG_GRAD, 2, st);
         k_jvp_bwd<S, Real><<<(unsigned)nslices, S::NT, sb, st>>>(md, bx, nl->d_order, n, pos, nl->d_nlist,
                                                                  nl->d_nnei, d_v, T, Td, Db, Ddb, gpriv);
-        k_grad_reduce<Real><<<(unsigned)((emb_len + 255) / 256), 256, 0, st>>>(gpriv, nslices, emb_len,
+        k_grad_reduce<Real><<<(unsigned)((emb_len + 31) / 32), 256, 0, st>>>(gpriv, nslices, emb_len,
                                                                                d_grad + md.emb_base);
     }
     DP_CUDA(cudaGetLastError());
