@@ -15,6 +15,7 @@ struct __align__(32) Pos4 {
 
 struct BoxDev {
     double L[3], invL[3];
+    float invLf[3];       // (float) invL: the FP32 estimate of the image index in min_image_r
     int nc[3];
     int ncell_f;          // cells of one frame
     int64_t frame_n;      // atoms per frame (frame of atom i = i / frame_n)
@@ -26,6 +27,7 @@ inline BoxDev make_box(const dp_nlist *nl)
     for (int k = 0; k < 3; ++k) {
         b.L[k] = nl->L[k];
         b.invL[k] = 1.0 / nl->L[k];
+        b.invLf[k] = (float)b.invL[k];
         b.nc[k] = nl->nc[k];
     }
     b.ncell_f = (int)nl->ncell_frame;
@@ -33,19 +35,42 @@ inline BoxDev make_box(const dp_nlist *nl)
     return b;
 }
 
+// dk - L rint(dk invL) with the FP64 operations of min_image_r, taking the image index from an FP32
+// estimate where that is safe.  The estimate xf = dk' invLf, dk' = dk truncated to its leading 20
+// mantissa bits by integer operations (no FP64 instruction), is within 2^-19 |x| of x = dk invL; for
+// |xf| <= 2 that is below 4e-6, so where xf is more than 1e-5 away from a half-integer rint(x) =
+// rintf(xf) exactly, and the index 0 or +-1 gives the FP64 result with at most one subtraction
+// (L (+-1) is exact).  Near a half-integer, for larger indices, and for huge or non-finite dk the FP64
+// operations run as written.
+__device__ __forceinline__ double min_image_k(double dk, double L, double invL, float invLf)
+{
+    const int hi = __double2hiint(dk);
+    const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;   // FP32 exponent field of dk
+    if (e < 140) {                                       // |dk| < 2^13 (and not inf / nan)
+        const float xf = e > 0 ? __int_as_float((hi & (int)0x80000000) | (e << 23) | ((hi & 0xfffff) << 3)) * invLf
+                               : 0.f;
+        const float nf = rintf(xf);
+        if (fabsf(xf) <= 2.f && fabsf(fabsf(xf - nf) - 0.5f) > 1e-5f) {
+            // index 0: dk itself, except -0, which the FP64 form turns into +0 (-0 - -0 = +0)
+            if (nf == 0.f) return __double_as_longlong(dk) == (long long)0x8000000000000000ULL ? 0.0 : dk;
+            if (nf == 1.f) return __dsub_rn(dk, L);
+            if (nf == -1.f) return __dadd_rn(dk, L);
+        }
+    }
+    return __dsub_rn(dk, __dmul_rn(L, rint(__dmul_rn(dk, invL))));
+}
+
 // d = r_b - r_a under minimum image: d_k = (b_k - a_k) - L_k rint((b_k - a_k) / L_k)
 // with 1/L_k precomputed; returns r = sqrt((dx dx + dy dy) + dz dz).  Every
-// operation is individually rounded (no contraction into multiply-adds).
+// operation is individually rounded (no contraction into multiply-adds); the
+// image index comes from an FP32 estimate where that gives the same result
+// (min_image_k).
 __device__ __forceinline__ double min_image_r(const Pos4 a, const Pos4 b, const BoxDev &bx, double d[3])
 {
     const double pa[3] = {a.x, a.y, a.z};
     const double pb[3] = {b.x, b.y, b.z};
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        double dk = __dsub_rn(pb[k], pa[k]);
-        double nk = rint(__dmul_rn(dk, bx.invL[k]));
-        d[k] = __dsub_rn(dk, __dmul_rn(bx.L[k], nk));
-    }
+    for (int k = 0; k < 3; ++k) d[k] = min_image_k(__dsub_rn(pb[k], pa[k]), bx.L[k], bx.invL[k], bx.invLf[k]);
     double r2 = __dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1]));
     r2 = __dadd_rn(r2, __dmul_rn(d[2], d[2]));
     return __dsqrt_rn(r2);

@@ -133,7 +133,7 @@ __global__ void k_candidates(int64_t n, const Pos4 *__restrict__ pos, const floa
     const Pos4 pi = pos[i];
     const float4 pf = posf[i];
     const float Lf[3] = {(float)bx.L[0], (float)bx.L[1], (float)bx.L[2]};
-    const float iLf[3] = {(float)bx.invL[0], (float)bx.invL[1], (float)bx.invL[2]};
+    const float iLf[3] = {bx.invLf[0], bx.invLf[1], bx.invLf[2]};
     const float rpre = (float)rlist + 2e-3f;
     const int cf = cell_of[i];
     if (!DP_IDX_OK(cf, ncell, BS_CELL)) {
@@ -275,7 +275,7 @@ __global__ void k_format(int64_t n, const Pos4 *__restrict__ pos, const float4 *
     int nf = 0;
     {
         const float Lf[3] = {(float)bx.L[0], (float)bx.L[1], (float)bx.L[2]};
-        const float iLf[3] = {(float)bx.invL[0], (float)bx.invL[1], (float)bx.invL[2]};
+        const float iLf[3] = {bx.invLf[0], bx.invLf[1], bx.invLf[2]};
         const float rpre = (float)md.rcut + 2e-3f;
         for (int base = 0; base < nc; base += 32) {
             const int c = base + lane;
