@@ -107,14 +107,27 @@ static Aux aux_of(dp_model *m)
     return a;
 }
 
+// Precisions whose kernels read the formatting kernel's FP64-derived geometry records.
+static bool uses_env_records(dp_precision p)
+{
+    return p == DP_MIX_BF16 || p == DP_MIX_FP16 || p == DP_MIX_BF16X3 || p == DP_MIX_FP8;
+}
+
+bool format_shared(const dp_model *a, dp_precision pa, const dp_model *b, dp_precision pb)
+{
+    // the geometry records carry s(r) and ds/dr, which depend on r_cs as well
+    if (a->dev.rcut != b->dev.rcut || a->dev.rcs != b->dev.rcs || a->dev.ntypes != b->dev.ntypes) return false;
+    for (int t = 0; t < a->dev.ntypes; ++t)
+        if (a->dev.sel[t] != b->dev.sel[t]) return false;
+    return !uses_env_records(pb) || uses_env_records(pa);
+}
+
 dp_status compute_device(dp_model *m, dp_nlist *nl, const double *d_coord, dp_precision prec, double *d_energy,
                          double *d_atom_energy, double *d_force, double *d_virial, double *d_atom_virial,
-                         cudaStream_t st)
+                         cudaStream_t st, bool reformat)
 {
     m->dev.n_list = nl->n;
-    DP_TRY(nlist_format_device(m, nl, d_coord, st,
-                               prec == DP_MIX_BF16 || prec == DP_MIX_FP16 || prec == DP_MIX_BF16X3 ||
-                                   prec == DP_MIX_FP8));
+    if (reformat) DP_TRY(nlist_format_device(m, nl, d_coord, st, uses_env_records(prec)));
     if (nl->n == 0) {
         DP_CUDA(cudaMemsetAsync(d_energy, 0, sizeof(double), st));
         if (d_virial) DP_CUDA(cudaMemsetAsync(d_virial, 0, 9 * sizeof(double), st));

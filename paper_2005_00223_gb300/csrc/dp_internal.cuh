@@ -309,10 +309,15 @@ bool embed_shape_supported(int n_embed, const int *e);
 size_t fp64_bytes_per_atom(const ModelDev &md);
 dp_status compute_mix32(dp_model *m, dp_nlist *nl, double *d_energy, double *d_atom_energy, double *d_force,
                         double *d_virial, double *d_atom_virial, cudaStream_t st);
-// Full evaluation on device data: pack, format, compute in the requested precision.
+// Full evaluation on device data: pack, format, compute in the requested precision.  reformat = false
+// reuses the formatted list (and geometry records) of the evaluation just before it on the same
+// coordinates; the caller guarantees it was formatted for the same r_c, types and sel (format_shared).
 dp_status compute_device(dp_model *m, dp_nlist *nl, const double *d_coord, dp_precision prec, double *d_energy,
                          double *d_atom_energy, double *d_force, double *d_virial, double *d_atom_virial,
-                         cudaStream_t st);
+                         cudaStream_t st, bool reformat = true);
+// True when a list formatted for model a in precision pa also serves model b in precision pb: the same
+// r_c, r_cs, number of types and sel, and geometry records present if pb reads them.
+bool format_shared(const dp_model *a, dp_precision pa, const dp_model *b, dp_precision pb);
 dp_status check_box(const double box[9], double rcut, double L[3]);
 dp_status pack_tc_weights(dp_model *m);
 dp_status compute_mix16(dp_model *m, dp_nlist *nl, int bf16, double *d_energy, double *d_atom_energy,

@@ -659,9 +659,11 @@ dp_status dp_md_step_judged(dp_model *student, dp_model *teacher, dp_md_state *s
             double *Fs = use_teacher ? Ft : s->d_f;
             double *Fteach = use_teacher ? s->d_f : Ft;
             if (use_teacher) {
-                DP_TRY(compute_device(student, nl, nullptr, student_prec, St + 1, Et, Ft, St + 2, Wi_s, st));
+                DP_TRY(compute_device(student, nl, nullptr, student_prec, St + 1, Et, Ft, St + 2, Wi_s, st,
+                                      !format_shared(teacher, teacher_prec, student, student_prec)));
             } else {
-                DP_TRY(compute_device(teacher, nl, nullptr, teacher_prec, St + 1, Et, Ft, St + 2, Wi_t, st));
+                DP_TRY(compute_device(teacher, nl, nullptr, teacher_prec, St + 1, Et, Ft, St + 2, Wi_t, st,
+                                      !format_shared(student, student_prec, teacher, teacher_prec)));
             }
             k_force_rmse<<<1, 512, 0, st>>>(n, Fs, Fteach, St);
             DP_CUDA(cudaGetLastError());

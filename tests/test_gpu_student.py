@@ -125,3 +125,26 @@ def test_teacher_fitted_to_reference_keeps_a_crystal_and_distils(dp):
     # the untrained student is rejected at every judgement; the trained one's judged error is far lower
     assert judged[0][1].all()
     assert judged[1][0].mean() < 0.5 * judged[0][0].mean()
+
+
+@pytest.mark.parametrize("student_prec,teacher_prec", [("bf16", "bf16x3"), ("mix32", "bf16")])
+def test_judgement_equals_separate_evaluations(dp, student_prec, teacher_prec):
+    """The judge evaluates the full model on the list the student's step just formatted (shared when
+    r_c, r_cs, types and sel agree and the geometry records the judge reads are there, else formatted
+    again).  Its logged force RMSE equals the RMSE of the two models' forces evaluated separately at
+    the same coordinates, to the run-to-run noise of the FP32 atomics."""
+    cfg = dpsynth.copper_config()
+    teacher = dp.Model(cfg, 0, params=dpsynth.model_params(cfg, 1))
+    stu = dp.Model(dpsynth.copper_student_config(), seed=2)
+    coord, typ, box = dpsynth.copper_fcc(1, ncell=5)
+    mass = np.array([dpsynth.MASS["Cu"]])
+    st = dp.MDState(stu, coord, dpsynth.velocities(mass[typ], 300.0, 1), typ, mass, box, skin=2.0)
+    rm, _ = dp.dp_md_step_judged(stu.h, teacher.h, st.h, 10, 1.0, student_prec, teacher_prec, judge_every=10,
+                                 rmse_max=1e9)
+    x, _, _, _ = st.get()
+    st.close()
+    Fs = dp.NeighborList(stu, x, typ, box).compute(x, box, student_prec)[2]
+    Ft = dp.NeighborList(teacher, x, typ, box).compute(x, box, teacher_prec)[2]
+    ref = float(np.sqrt(((Fs - Ft) ** 2).sum(1).mean()))
+    print(student_prec, teacher_prec, rm, ref)
+    assert len(rm) == 1 and abs(rm[0] - ref) <= 1e-3 * ref
