@@ -233,7 +233,7 @@ __device__ __forceinline__ void env_record(const double d[3], double r, const Mo
     rb = make_float2(d2f_rn(ds), d2f_rn(r));
 }
 
-constexpr int kRecStage = 256;   // kept neighbors per atom whose records are staged in shared memory
+constexpr int kRecStage = 192;   // kept neighbors per atom whose records are staged in shared memory
 
 // One warp per atom, three stages.  (A) FP32 prefilter on wrapped FP32
 // coordinates: candidates within r_c plus a margin far above its error are
