@@ -45,7 +45,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FFMA/clk x 2 F
 # kernel is unchanged since the capture.
 NCU_TRAFFIC = {
     ("fp64", "cu4000", "embed_fwd_l2"): (2.068e9 + 1.266e9, "profiles/fp64_embed_fwd_l2_pipes_cu4000.md"),
-    ("bf16", "cu4000", "embed_bwd"): (28.79e6 + 0.12e6, "profiles/bf16_cu4000_nve_step.md"),
+    ("bf16", "cu4000", "embed_bwd"): (28.80e6 + 0.06e6, "profiles/bf16_cu4000_nve_step.md"),
 }
 
 
