@@ -86,23 +86,42 @@ __device__ __forceinline__ float4 wrapped_f32(const double *x, int32_t type, con
     return make_float4(w[0], w[1], w[2], __int_as_float(type));
 }
 
+// 1/r for 2^-126 < r < 2^126 by two Newton-Raphson steps y <- y + y (1 - r y) in FP64 from the FP32
+// hardware reciprocal estimate (relative error about 2^-23, then 2^-46, then below the FP64 rounding):
+// four FP64 operations instead of a correctly rounded FP64 division (within an ulp of it).  The FP32
+// argument is r truncated to 24 bits and the estimate is widened exactly, with integer instructions.
+__device__ __forceinline__ double recip_nr(double r)
+{
+    const long long b = __double_as_longlong(r);
+    const int ex = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+    const float rf = __uint_as_float((unsigned)((unsigned long long)b >> 32 & 0x80000000u) | ((unsigned)ex << 23) |
+                                     (unsigned)(((unsigned long long)b >> 29) & 0x7fffffu));
+    float yf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(rf));
+    const unsigned u = __float_as_uint(yf);
+    double y = __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
+                                                ((unsigned long long)(((u >> 23) & 0xffu) - 127 + 1023) << 52) |
+                                                ((unsigned long long)(u & 0x7fffffu) << 29)));
+    y = fma(y, fma(-r, y, 1.0), y);
+    return fma(y, fma(-r, y, 1.0), y);
+}
+
 // Switching function of the environment matrix: s = 1/r below r_cs,
 // (1/r)(u^3(-6u^2 + 15u - 10) + 1) with u = (r - r_cs)/(r_c - r_cs) up to
 // r_c, 0 beyond; *ds = ds/dr.  The quintic is twice continuously
-// differentiable at both ends (order-2 smoothness of Sec. 2).
-__device__ __forceinline__ double switch_fn(double r, double rcs, double rc, double *ds)
+// differentiable at both ends (order-2 smoothness of Sec. 2).  ir = 1/r,
+// inv_sw = 1/(r_c - r_cs).
+__device__ __forceinline__ double switch_fn(double r, double ir, double rcs, double rc, double inv_sw, double *ds)
 {
     if (r < rcs) {
-        double ir = 1.0 / r;
         *ds = -ir * ir;
         return ir;
     }
     if (r < rc) {
-        double ir = 1.0 / r;
-        double u = (r - rcs) / (rc - rcs);
+        double u = (r - rcs) * inv_sw;
         double u2 = u * u;
         double poly = u2 * u * (-6.0 * u2 + 15.0 * u - 10.0) + 1.0;
-        double dpoly = -30.0 * u2 * (u - 1.0) * (u - 1.0) / (rc - rcs);
+        double dpoly = -30.0 * u2 * (u - 1.0) * (u - 1.0) * inv_sw;
         *ds = (dpoly - poly * ir) * ir;
         return poly * ir;
     }
@@ -111,12 +130,13 @@ __device__ __forceinline__ double switch_fn(double r, double rcs, double rc, dou
 }
 
 // Environment-matrix row R = (s, s dx/r, s dy/r, s dz/r) and its Jacobian
-// J[c][k] = dR_c / dd_k (row-major 4 x 3).
-__device__ __forceinline__ void env_row(const double d[3], double r, double rcs, double rc, double R[4], double J[12])
+// J[c][k] = dR_c / dd_k (row-major 4 x 3); inv_sw = 1/(r_c - r_cs).
+__device__ __forceinline__ void env_row(const double d[3], double r, double rcs, double rc, double inv_sw, double R[4],
+                                        double J[12])
 {
     double ds;
-    double s = switch_fn(r, rcs, rc, &ds);
-    double ir = 1.0 / r;
+    const double ir = recip_nr(r);
+    double s = switch_fn(r, ir, rcs, rc, inv_sw, &ds);
     double sr = s * ir;
     double dsr = (ds - sr) * ir;          // d(s/r)/dr
     R[0] = s;

@@ -77,7 +77,7 @@ __device__ __forceinline__ void env_tangent(const ModelDev &md, const BoxDev &bx
     if (c0 + n < cnt && DP_IDX_OK(j, md.n_list, BS_NLIST_J)) {
         double d[3], J[12];
         const double r = min_image_r(pi, pos[j], bx, d);
-        env_row(d, r, md.rcs, md.rcut, R, J);
+        env_row(d, r, md.rcs, md.rcut, md.inv_sw, R, J);
         double dd[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) dd[k] = v[3 * (int64_t)j + k] - v[3 * (int64_t)i + k];

@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(128) k_ozf_front(ModelDev md, BoxDev bx, const
         if (valid && DP_IDX_OK(j, md.n_list, BS_NLIST_J)) {
             double d[3], J[12];
             const double r = min_image_r(pos[a], pos[j], bx, d);
-            env_row(d, r, md.rcs, md.rcut, R, J);
+            env_row(d, r, md.rcs, md.rcut, md.inv_sw, R, J);
         }
         const int64_t row = (int64_t)t * 128 + tid;
 #pragma unroll
@@ -619,7 +619,7 @@ struct Bwd4Epi {
             dR[0] += ds;
             double d[3], Rr[4], J[12];
             const double r = min_image_r(pos[a], pos[j], bx, d);
-            env_row(d, r, md.rcs, md.rcut, Rr, J);
+            env_row(d, r, md.rcs, md.rcut, md.inv_sw, Rr, J);
             double gv[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) gv[k] = dR[0] * J[k] + dR[1] * J[3 + k] + dR[2] * J[6 + k] + dR[3] * J[9 + k];

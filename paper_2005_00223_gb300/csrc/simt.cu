@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(S::NT) k_embed_fwd(ModelDev md, BoxDev bx, con
                     if (DP_IDX_OK(j, md.n_list, BS_NLIST_J)) {
                         double d[3], J[12];
                         double r = min_image_r(pi, pos[j], bx, d);
-                        env_row(d, r, md.rcs, md.rcut, R, J);
+                        env_row(d, r, md.rcs, md.rcut, md.inv_sw, R, J);
                     }
                 }
 #pragma unroll
@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(S::NT) k_embed_bwd(ModelDev md, BoxDev bx, con
                     j = nlist[(int64_t)i * md.nsel + md.sel_off[tj] + c0 + n];
                     if (DP_IDX_OK(j, md.n_list, BS_NLIST_J)) {
                         double r = min_image_r(pi, pos[j], bx, d);
-                        env_row(d, r, md.rcs, md.rcut, R, J);
+                        env_row(d, r, md.rcs, md.rcut, md.inv_sw, R, J);
                     } else {
                         j = -1;
                     }
