@@ -201,21 +201,16 @@ __device__ __forceinline__ float d2f_rn(double v)
 // exact FP64 difference d and distance r: the switching function s(r), its
 // derivative ds/dr and d/r evaluated in FP64 and stored rounded to FP32 as
 // (s, d/r) and (ds/dr, r).  1/r is the Newton-Raphson reciprocal in FP64
-// (y <- y + y (1 - r y), twice, from the FP32 reciprocal: the relative error
-// squares at each step, 2^-22 -> 2^-44 -> below the FP64 rounding), instead
-// of the general FP64 division; the quintic is evaluated in the factored
+// (recip_nr: two steps from the FP32 estimate, the relative error squaring
+// at each step to below the FP64 rounding), instead of the general FP64
+// division; the quintic is evaluated in the factored
 // form 1 - 10u^3 + 15u^4 - 6u^5 = (1 - u)^3 (1 + 3u + 6u^2), with u and
 // 1 - u both taken from r directly, so neither end of the switching region
 // loses precision to cancellation.  The FP32 roundings use integer
 // instructions (d2f_rn), not the FP64 pipe.
 __device__ __forceinline__ void env_record(const double d[3], double r, const ModelDev &md, float4 &ra, float2 &rb)
 {
-    const unsigned y0 = __float_as_uint(__frcp_rn(d2f_rn(r)));   // normal for 2^-126 < r < 2^126
-    double ir = __longlong_as_double((long long)(((unsigned long long)(y0 & 0x80000000u) << 32) |
-                                                 ((unsigned long long)(((y0 >> 23) & 0xffu) - 127 + 1023) << 52) |
-                                                 ((unsigned long long)(y0 & 0x7fffffu) << 29)));   // exact widening
-    ir = fma(ir, fma(-r, ir, 1.0), ir);
-    ir = fma(ir, fma(-r, ir, 1.0), ir);
+    const double ir = recip_nr(r);
     double s, ds;
     if (r < md.rcs) {
         s = ir;
